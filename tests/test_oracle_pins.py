@@ -1,0 +1,583 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here calls the CUDA library: each test checks the oracle against a closed
+form, an independent library routine (numpy's Philox, scipy's filters, numpy's
+median), brute force, or an invariant that the paper's method must satisfy.
+"""
+
+import ctypes as C
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.ndimage as ndi
+
+import oracle
+from synth import make_workload, plane_scene, tiny_scene, Camera, camera_pose
+from synth.scenes import default_params
+
+SQRT2 = math.sqrt(2.0)
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def axis_camera(f=0.05, N=1.4, d=10.0, ws=0.036, pos=(0.0, 0.0, 0.0), prev_pos=None, frame=0):
+    pose = camera_pose(pos, pitch_deg=0.0)
+    prev = camera_pose(prev_pos, pitch_deg=0.0) if prev_pos is not None else None
+    return Camera.from_poses(dict(f_m=f, f_number=N, focus_m=d, sensor_w_m=ws), pose, prev, frame)
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def seg_fraction(tau):
+    """Share of a unit disk on the far side of the chord at signed offset tau."""
+    if tau >= 1.0:
+        return 0.0
+    if tau <= -1.0:
+        return 1.0
+    return (math.acos(tau) - tau * math.sqrt(1.0 - tau * tau)) / math.pi
+
+
+# ---------------------------------------------------------------------------
+# Section 3.3, Eq. 6 and the thin-lens CoC
+# ---------------------------------------------------------------------------
+
+LENSES = [(0.05, 1.4, 15.0, 256), (0.035, 2.0, 20.0, 1920), (0.085, 1.2, 20.0, 3840)]
+
+
+@pytest.mark.parametrize("f,N,d,W", LENSES)
+def test_coc_zero_at_focus_and_eq6_bounds(f, N, d, W):
+    cam = axis_camera(f, N, d)
+    assert oracle.coc(cam, W, f32(d)) == 0.0
+    zn, zf = oracle.zof_bounds(cam, W)
+    assert zn < f32(d)
+    assert abs(abs(oracle.coc(cam, W, zn)) - SQRT2) <= 1e-12 * SQRT2
+    assert oracle.coc(cam, W, zn) < 0.0
+    if math.isfinite(zf):
+        assert abs(oracle.coc(cam, W, zf) - SQRT2) <= 1e-12 * SQRT2
+    else:
+        assert oracle.coc(cam, W, 1e300) <= SQRT2
+    # inside the zone |c| < sqrt2, outside larger
+    assert abs(oracle.coc(cam, W, 0.5 * (zn + f32(d)))) < SQRT2
+    assert abs(oracle.coc(cam, W, 0.9 * zn)) > SQRT2
+
+
+@pytest.mark.parametrize("f,N,d,W", LENSES)
+def test_coc_matches_lens_equation(f, N, d, W):
+    """Independent derivation: the image of depth z focuses at v_z = f z / (z - f);
+    the sensor sits at v = f d / (d - f); the blur spot on the sensor has diameter
+    a (v - v_z) / v_z by similar triangles (negative when v_z > v, i.e. near)."""
+    cam = axis_camera(f, N, d)
+    f, N, d, ws = f32(f), f32(N), f32(d), 0.036
+    ws = f32(ws)
+    a = f / N
+    v = f * d / (d - f)
+    for z in [0.3, 0.5, 1.0, 2.7, 9.9, d, 33.0, 1e3, 1e5]:
+        vz = f * z / (z - f)
+        ref = a * (v - vz) / vz * W / ws
+        got = oracle.coc(cam, W, z)
+        assert abs(got - ref) <= 1e-10 * max(1.0, abs(ref)), (z, got, ref)
+    # limit at infinity: a f / (d - f) in sensor units
+    cinf = a * f / (d - f) * W / ws
+    assert abs(oracle.coc(cam, W, 1e14) - cinf) <= 1e-9 * cinf
+
+
+# ---------------------------------------------------------------------------
+# Philox4x64-10 against numpy's independent implementation
+# ---------------------------------------------------------------------------
+
+def test_philox_matches_numpy():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        ctr = [int(x) for x in rng.integers(1, 2 ** 63, size=4, dtype=np.int64)]
+        key = [int(x) for x in rng.integers(0, 2 ** 63, size=2, dtype=np.int64)]
+        mine = oracle.philox4x64(ctr, key)
+        # numpy's Philox increments its counter before each block
+        c = list(ctr)
+        c[0] -= 1
+        ref = np.random.Philox(counter=c, key=key).random_raw(4)
+        assert list(mine) == list(ref)
+
+
+def test_philox_lens_uniforms_chi2():
+    n = 40000
+    u = np.empty(n)
+    for i in range(n):
+        x = oracle.philox4x64([i, 3, 7, 0], [1001, 0])
+        u[i] = (int(x[0]) >> 40) * 2.0 ** -24
+    hist, _ = np.histogram(u, bins=64, range=(0, 1))
+    e = n / 64
+    chi2 = ((hist - e) ** 2 / e).sum()
+    assert chi2 < 120.0          # 63 dof: p ~ 1e-5 at 120
+
+
+# ---------------------------------------------------------------------------
+# closest hit: BVH vs all triangles
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 64, 200])
+def test_bvh_equals_brute_force(n):
+    sc = tiny_scene(100 + n, n)
+    os_ = oracle.Scene(sc)
+    rng = np.random.default_rng(n)
+    tv = sc.tri_vertices().astype(np.float64)
+    targets = list(rng.uniform([-1.5, -1.5, 1.5], [1.5, 1.5, 4.5], size=(400, 3)))
+    # aim exactly at vertices and edge midpoints (shared-edge and coplanar ties)
+    for t in tv[-4:]:
+        targets += [t[0], t[1], t[2], 0.5 * (t[0] + t[1]), 0.5 * (t[0] + t[2]), t.mean(0)]
+    for T in targets:
+        o = rng.uniform(-0.3, 0.3, 3)
+        o[2] = 0.0
+        d = np.asarray(T) - o
+        d /= np.linalg.norm(d)
+        assert os_.closest(o, d) == os_.closest(o, d, brute=True)
+
+
+def test_bvh_equals_brute_force_c1_scene():
+    w = make_workload("c1")
+    os_ = oracle.Scene(w.scene)
+    cam = w.camera(0)
+    rng = np.random.default_rng(1)
+    hits = 0
+    for _ in range(1500):
+        x, y = rng.uniform(0, w.W), rng.uniform(0, w.H)
+        d = oracle.pixel_dir(cam, w.W, w.H, x, y)
+        o = np.asarray(cam.pos, dtype=np.float64) + rng.uniform(-0.02, 0.02, 3)
+        a = os_.closest(o, d)
+        assert a == os_.closest(o, d, brute=True)
+        hits += a[0] >= 0
+    assert hits > 1000
+
+
+def test_near_tie_classifier():
+    sc = tiny_scene(3, 4, ties=True)          # exactly the shared-edge quad and the coplanar pair
+    os_ = oracle.Scene(sc)
+    o = np.zeros(3)
+    # the quad (z = 3) is split along its diagonal (-0.5,-0.5)-(0.5,0.5): aim at the diagonal
+    d = np.array([0.1, 0.1, 3.0]); d /= np.linalg.norm(d)
+    assert os_.near_tie(o, d, 0, 1)
+    # well inside triangle 0 (below the diagonal) vs triangle 1: not a tie
+    d = np.array([0.4, -0.45, 3.0]); d /= np.linalg.norm(d)
+    prim, _ = os_.closest(o, d)
+    assert prim == 0
+    assert not os_.near_tie(o, d, 0, 1)
+    # interior hit vs a miss: not a tie; grazing the quad's outer edge: a tie
+    assert not os_.near_tie(o, d, 0, -1)
+    d = np.array([0.5, 0.0, 3.0]); d /= np.linalg.norm(d)
+    assert os_.near_tie(o, d, 0, -1)
+    # coplanar overlapping triangles at equal distance: a depth tie
+    d = np.array([0.0, 0.0, 2.5]); d /= np.linalg.norm(d)
+    assert os_.near_tie(o, d, 2, 3)
+
+
+# ---------------------------------------------------------------------------
+# G-buffer producer
+# ---------------------------------------------------------------------------
+
+def test_gbuffer_fronto_parallel_plane():
+    sc = oracle.Scene(plane_scene([(5.0, "full", 0.0, 0)]))
+    cam = axis_camera()
+    prm = default_params()
+    gb = oracle.gbuffer(sc, cam, prm, 32, 16)
+    assert np.all(gb["prim"] == 0)
+    assert np.allclose(gb["depth"], 5.0, rtol=0, atol=1e-12)
+    assert np.allclose(gb["normal"], [0, 0, -1], atol=1e-15)
+    alb = np.zeros(3)
+    oracle.lib().or_albedo(prm["albedo_seed"], 0, alb.ctypes.data_as(C.c_void_p))
+    assert np.all((alb >= 0.1) & (alb <= 0.9))
+    l = np.asarray(prm["light_dir"], dtype=np.float32).astype(np.float64)
+    l /= np.linalg.norm(l)
+    lam = max(0.0, -np.dot([0, 0, -1], l))
+    want = alb * (f32(prm["k_a"]) + f32(prm["k_d"]) * lam)
+    assert np.allclose(gb["color"], want, atol=1e-12)
+
+
+def test_gbuffer_ground_plane_depth_closed_form():
+    """Camera at height h, pitched down: a ray with direction dir meets y = 0 at
+    t = h / -dir_y; its depth along the optical axis is t (dir . fwd)."""
+    sc = oracle.Scene(_ground_only())
+    pose = camera_pose((0.0, 1.5, 0.0), pitch_deg=20.0)
+    cam = Camera.from_poses(dict(f_m=0.05, f_number=2.0, focus_m=10.0, sensor_w_m=0.036), pose)
+    W, H = 40, 30
+    gb = oracle.gbuffer(sc, cam, default_params(), W, H)
+    fwd = np.asarray(cam.fwd, dtype=np.float64)
+    n_hit = 0
+    for j in range(H):
+        for i in range(W):
+            d = oracle.pixel_dir(cam, W, H, i + 0.5, j + 0.5)
+            if d[1] < -1e-3:
+                t = f32(1.5) / -d[1]
+                assert abs(gb["depth"][j, i] - t * np.dot(d, fwd)) <= 1e-9 * t
+                n_hit += 1
+            else:
+                assert gb["prim"][j, i] < 0 and np.isinf(gb["depth"][j, i])
+    assert n_hit > 100
+
+
+def _ground_only():
+    from synth.scenes import _Builder, ground
+    b = _Builder(3)
+    b.add("ground", *ground())
+    return b.build()
+
+
+# ---------------------------------------------------------------------------
+# ray-traced layer: aperture -> 0 is a pinhole render
+# ---------------------------------------------------------------------------
+
+def test_aperture_zero_is_pinhole():
+    w = make_workload("c1")
+    sc = oracle.Scene(w.scene)
+    cam = w.camera(0)
+    cam.f_number = 1e30                     # a = f / N -> 0
+    prm = dict(w.params, mask_near_hpx=0.0, spp=1)
+    gb = oracle.gbuffer(sc, cam, prm, w.W, w.H)
+    g32 = oracle.gbuffer_f32(gb)
+    fr = oracle.frame(sc, cam, prm, w.W, w.H, g32)
+    assert np.all(fr["nrays"] == 1)
+    # the half-resolution pinhole render shoots through the same sensor points
+    half = oracle.gbuffer(sc, cam, prm, w.W // 2, w.H // 2)
+    prim = fr["ray_prim"][..., 0]
+    mism = np.argwhere(prim != half["prim"])
+    for (j, i) in mism:
+        o, d = oracle.lens_ray(cam, prm, w.W, w.H, i, j, 0)
+        assert sc.near_tie(o, d, prim[j, i], half["prim"][j, i])
+    assert len(mism) <= 2
+    ok = prim == half["prim"]
+    col = fr["rt"][..., 2:5] + fr["rt"][..., 5:8]
+    assert np.abs(col[ok] - half["color"][ok]).max() < 1e-12
+    assert np.abs(fr["rt"][..., 1]).max() < 1e-20          # nothing is out of focus
+    # zero aperture: the composite is the sharp image (Eq. 6 holds everywhere)
+    assert np.abs(fr["out"][..., :3] - g32["color"][..., :3]).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# ray-traced layer: partial occlusion and the thin-lens integral (closed forms)
+# ---------------------------------------------------------------------------
+
+def _lens_geometry(W, f=0.05, N=1.4, d=10.0, ws=0.036):
+    f, N, d, ws = f32(f), f32(N), f32(d), f32(ws)
+    v = f * d / (d - f)
+    return dict(A=0.5 * f / N, F=W * v / ws, d=d)
+
+
+def test_partial_occlusion_circular_segment():
+    """A foreground half-plane x > 0 at z1 = 1 m in front of a background plane at
+    20 m, focus at 10 m.  The ray from lens point L towards the focus point P_f
+    crosses z1 at x = L_x (1 - s) + P_fx s with s = z1 / d, so it is blocked iff
+    L_x > -P_fx s / (1 - s): a circular segment of the lens disk."""
+    W, H, spp = 512, 4, 4096
+    sc = oracle.Scene(plane_scene([(1.0, "right", 0.0, 0), (20.0, "full", 0.0, 0)]))
+    cam = axis_camera()
+    prm = default_params(spp=spp, mask_near_hpx=0.0, max_coc_px=64.0)
+    gb = oracle.gbuffer(sc, cam, prm, W, H)
+    col_fg, col_bg = gb["color"][0, -1], gb["color"][0, 0]
+    assert gb["prim"][0, -1] == 0 and gb["prim"][0, 0] == 1
+    fr = oracle.frame(sc, cam, prm, W, H, oracle.gbuffer_f32(gb))
+    g = _lens_geometry(W)
+    s = 1.0 / g["d"]
+    checked = 0
+    for i in range(W // 2 // 2 - 12, W // 2 // 2 + 12):
+        Pfx = g["d"] * ((2 * i + 1) - W / 2) / g["F"]
+        tau = (-Pfx * s / (1 - s)) / g["A"]
+        p = seg_fraction(tau)
+        sig = math.sqrt(p * (1 - p) / spp)
+        for j in range(H // 2):
+            h = fr["rt"][j, i, 1]
+            assert abs(h - p) <= 4.5 * sig + 1e-3, (i, tau, h, p)
+            colr = fr["rt"][j, i, 2:5] + fr["rt"][j, i, 5:8]
+            assert np.allclose(colr, h * col_fg + (1 - h) * col_bg, atol=1e-12)
+            assert np.allclose(fr["rt"][j, i, 2:5], h * col_fg, atol=1e-12)
+            checked += 1
+    assert checked == 48
+
+
+def test_thin_lens_step_edge_behind_focus():
+    """A coplanar colour step at z = 30 m (behind the 10 m focus plane): the ray
+    lands at x = L_x (1 - s) + P_fx s, s = 3, so it lands right of the edge iff
+    L_x < 1.5 P_fx -- the step is blurred by the disk of the thin-lens integral."""
+    W, H, spp = 512, 4, 4096
+    sc = oracle.Scene(plane_scene([(30.0, "left", 0.0, 0), (30.0, "right", 0.0, 0)]))
+    cam = axis_camera()
+    prm = default_params(spp=spp, mask_near_hpx=0.0, max_coc_px=64.0)
+    gb = oracle.gbuffer(sc, cam, prm, W, H)
+    fr = oracle.frame(sc, cam, prm, W, H, oracle.gbuffer_f32(gb))
+    g = _lens_geometry(W)
+    s = 30.0 / g["d"]
+    for i in range(W // 4 - 16, W // 4 + 16):
+        Pfx = g["d"] * ((2 * i + 1) - W / 2) / g["F"]
+        tau0 = Pfx * s / (s - 1.0)
+        p_right = 1.0 - seg_fraction(tau0 / g["A"])
+        sig = math.sqrt(p_right * (1 - p_right) / spp)
+        for j in range(H // 2):
+            rays = fr["ray_prim"][j, i]
+            got = np.mean(rays == 1)
+            assert np.all((rays == 0) | (rays == 1))
+            assert abs(got - p_right) <= 4.5 * sig + 1e-3, (i, got, p_right)
+            assert fr["rt"][j, i, 1] == 0.0             # far field only
+
+
+# ---------------------------------------------------------------------------
+# post-process invariants and library cross-checks
+# ---------------------------------------------------------------------------
+
+def _run_stage_frame(name="c2", W=200, H=112, **over):
+    w = make_workload(name, W=W, H=H)
+    sc = oracle.Scene(w.scene)
+    cam = w.camera(0)
+    prm = dict(w.params, **over)
+    gb = oracle.gbuffer(sc, cam, prm, W, H)
+    g32 = oracle.gbuffer_f32(gb)
+    return w, sc, cam, prm, g32, oracle.frame(sc, cam, prm, W, H, g32)
+
+
+def test_uniform_colour_is_fixed_point_of_post_process():
+    w, sc, cam, prm, g32, _ = _run_stage_frame()
+    g = dict(g32)
+    g["color"] = np.empty_like(g32["color"])
+    g["color"][...] = np.float32([0.3, 0.55, 0.7, 1.0])
+    fr = oracle.frame(sc, cam, prm, w.W, w.H, g)
+    want = np.float32([0.3, 0.55, 0.7]).astype(np.float64)
+    for k in ("pp_in", "pre", "main_out", "pp_med"):
+        assert np.abs(fr[k][..., :3] - want).max() < 1e-12, k
+    assert np.abs(fr["main_out"][..., 3]).max() == 0.0         # no bright samples
+
+
+def test_downscale_and_tiles_by_definition():
+    w, sc, cam, prm, g32, fr = _run_stage_frame(W=202, H=114)
+    H2, W2 = w.H // 2, w.W // 2
+    col = g32["color"][..., :3].astype(np.float64).reshape(H2, 2, W2, 2, 3).mean(axis=(1, 3))
+    assert np.abs(fr["pp_in"][..., :3] - col).max() < 1e-12
+    z = np.minimum(g32["depth"].astype(np.float64), prm["z_far_m"]).reshape(H2, 2, W2, 2)
+    assert np.array_equal(fr["z_h"], z.min(axis=(1, 3)))
+    rmax = prm["max_coc_px"] / 2
+    for (j, i) in [(0, 0), (H2 - 1, W2 - 1), (17, 33), (40, 90)]:
+        want = np.clip(oracle.coc(cam, w.W, fr["z_h"][j, i]) / 4.0, -rmax, rmax)
+        assert abs(fr["pp_in"][j, i, 3] - want) < 1e-12
+    # tile max (ragged: 101 x 57 hpx in 8 x 8 tiles) and dilation vs scipy
+    T = prm["tile"]
+    rho = fr["pp_in"][..., 3]
+    TH, TW = fr["tile_raw"].shape[:2]
+    pad = np.full((TH * T, TW * T), np.nan)
+    pad[:H2, :W2] = rho
+    blocks = pad.reshape(TH, T, TW, T)
+    assert np.array_equal(fr["tile_raw"][..., 0], np.nanmax(np.maximum(0, -blocks), axis=(1, 3)))
+    assert np.array_equal(fr["tile_raw"][..., 1], np.nanmax(np.abs(blocks), axis=(1, 3)))
+    K = math.ceil(rmax / T)
+    for c in range(2):
+        ref = ndi.maximum_filter(fr["tile_raw"][..., c], size=2 * K + 1, mode="constant", cval=0.0)
+        assert np.array_equal(fr["tile_dil"][..., c], ref)
+
+
+def test_median_is_exact_selection():
+    rng = np.random.default_rng(0)
+    L = oracle.lib()
+    for k in range(1, 10):
+        for _ in range(50):
+            v = rng.normal(size=9)
+            out = np.zeros(1)
+            L.or_median9(v.ctypes.data_as(C.c_void_p), k, out.ctypes.data_as(C.c_void_p))
+            if k % 2:
+                assert out[0] == np.median(v[:k])
+            else:
+                assert out[0] == np.sort(v[:k])[(k - 1) // 2]
+    # the PP median postfilter equals scipy's 3x3 median with edge replication
+    w, sc, cam, prm, g32, fr = _run_stage_frame(W=98, H=66)
+    for c in range(4):
+        ref = ndi.median_filter(fr["main_out"][..., c], size=3, mode="nearest")
+        assert np.array_equal(fr["pp_med"][..., c], ref)
+
+
+def test_binomial_and_sobel_vs_scipy_and_ramp():
+    L = oracle.lib()
+    rng = np.random.default_rng(2)
+    img = rng.normal(size=(23, 31))
+    out = np.zeros_like(img)
+    L.or_binomial5(img.ctypes.data_as(C.c_void_p), 31, 23, 1, out.ctypes.data_as(C.c_void_p))
+    b = np.array([1, 4, 6, 4, 1.0]) / 16
+    assert np.allclose(out, ndi.correlate(img, np.outer(b, b), mode="nearest"), atol=1e-13)
+    gx, gy = np.zeros_like(img), np.zeros_like(img)
+    L.or_sobel5(img.ctypes.data_as(C.c_void_p), 31, 23, 1, 0, gx.ctypes.data_as(C.c_void_p),
+                gy.ctypes.data_as(C.c_void_p))
+    sm = np.array([1, 4, 6, 4, 1.0])
+    dv = np.array([-1, -2, 0, 2, 1.0])
+    assert np.allclose(gx, ndi.correlate(img, np.outer(sm, dv) / 128, mode="nearest"), atol=1e-13)
+    assert np.allclose(gy, ndi.correlate(img, np.outer(dv, sm) / 128, mode="nearest"), atol=1e-13)
+    # a linear ramp of slope 0.37 per pixel (away from the clamped border)
+    jj, ii = np.mgrid[0:23, 0:31]
+    ramp = 0.37 * ii - 1.1 * jj + 4.0
+    L.or_sobel5(ramp.ctypes.data_as(C.c_void_p), 31, 23, 1, 0, gx.ctypes.data_as(C.c_void_p),
+                gy.ctypes.data_as(C.c_void_p))
+    assert np.allclose(gx[2:-2, 2:-2], 0.37, atol=1e-13)
+    assert np.allclose(gy[2:-2, 2:-2], -1.1, atol=1e-13)
+
+
+def test_mask_counts():
+    w, sc, cam, prm, g32, fr = _run_stage_frame()
+    T = prm["tile"]
+    near = np.repeat(np.repeat(fr["tile_dil"][..., 0], T, 0), T, 1)[:w.H // 2, :w.W // 2]
+    assert np.array_equal(fr["nrays"] > 0, near >= f32(prm["mask_near_hpx"]))
+    assert set(np.unique(fr["nrays"])) <= {0, prm["spp"]}
+    # a fronto-parallel plane has no edges: x_n = 0 away from the border
+    sc2 = oracle.Scene(plane_scene([(5.0, "full", 0.0, 0)]))
+    cam2 = axis_camera()
+    prm2 = default_params(ray_mode=1, m=10)
+    gb = oracle.gbuffer(sc2, cam2, prm2, 64, 48)
+    fr2 = oracle.frame(sc2, cam2, prm2, 64, 48, oracle.gbuffer_f32(gb))
+    assert np.abs(fr2["xn"]).max() < 1e-12
+    # adaptive mode: 1 <= n <= m, n = ceil(x_f) where masked
+    w, sc, cam, prm, g32, fr = _run_stage_frame(ray_mode=1, m=10)
+    msk = fr["nrays"] > 0
+    assert fr["nrays"].max() <= 10
+    assert np.array_equal(fr["nrays"][msk], np.clip(np.ceil(fr["xf"][msk]), 1, 10).astype(np.int32))
+    # Eq. 3 / Eq. 4 ranges
+    assert fr["xn"].min() >= 0 and fr["xn"].max() <= 1
+    assert fr["xf"].max() <= 10
+
+
+# ---------------------------------------------------------------------------
+# temporal accumulation
+# ---------------------------------------------------------------------------
+
+def _accumulate(cam, prm, W, H, z_h, rt, nrays, hist_in, has):
+    L = oracle.lib()
+    H2, W2 = H // 2, W // 2
+    N = W2 * H2
+    hist_out, crt, ct, var = np.zeros(12 * N), np.zeros((H2, W2, 4)), np.zeros((H2, W2)), np.zeros((H2, W2))
+    c, p = oracle.camera(cam), oracle.params(prm)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    L.or_accumulate(C.byref(c), C.byref(p), W, H, vp(z_h), vp(rt), vp(nrays), vp(hist_in), int(has),
+                    vp(hist_out), vp(crt), vp(ct), vp(var))
+    return hist_out, crt, ct, var
+
+
+def _rt_field(H2, W2, colour, h, cn=2.0, cf=3.0):
+    rt = np.zeros((H2, W2, 14))
+    rt[..., 0] = 1
+    rt[..., 1] = h
+    rt[..., 2:5] = h * np.asarray(colour)
+    rt[..., 5:8] = (1 - h) * np.asarray(colour)
+    rt[..., 8] = h * cn
+    rt[..., 9] = (1 - h) * cf
+    return rt
+
+
+def test_ema_closed_form_static_camera():
+    W, H = 48, 32
+    H2, W2 = H // 2, W // 2
+    cam = axis_camera()
+    prm = default_params()
+    alpha = f32(prm["alpha"])
+    z_h = np.full((H2, W2), 5.0)
+    nr = np.ones((H2, W2), dtype=np.int32)
+    A, B = np.array([0.9, 0.2, 0.4]), np.array([0.1, 0.6, 0.3])
+    hist, crt, ct, var = _accumulate(cam, prm, W, H, z_h, _rt_field(H2, W2, A, 0.25), nr, np.zeros(12 * W2 * H2), 0)
+    assert np.allclose(crt[..., :3], A, atol=1e-15)
+    assert np.all(var == 0.0)
+    for k in range(1, 9):
+        hist, crt, ct, var = _accumulate(cam, prm, W, H, z_h, _rt_field(H2, W2, B, 0.25), nr, hist, 1)
+        want = alpha ** k * A + (1 - alpha ** k) * B
+        assert np.abs(crt[..., :3] - want).max() < 1e-12, k
+        assert np.abs(crt[..., 3] - 0.25).max() < 1e-12
+        assert np.abs(ct - (0.25 * 2 + 0.75 * 3)).max() < 1e-12
+    # luminance moments of a sequence (lum A, then lum B k times)
+    la = 0.2126 * A[0] + 0.7152 * A[1] + 0.0722 * A[2]
+    lb = 0.2126 * B[0] + 0.7152 * B[1] + 0.0722 * B[2]
+    wa = alpha ** 8
+    m1, m2 = wa * la + (1 - wa) * lb, wa * la * la + (1 - wa) * lb * lb
+    assert np.abs(var - (m2 - m1 * m1)).max() < 1e-12
+
+
+def test_reprojection_integer_shift():
+    """Move the camera sideways so that a plane at 5 m shifts by one half-resolution
+    pixel: every pixel's history comes from its right-hand neighbour."""
+    W, H = 64, 32
+    H2, W2 = H // 2, W // 2
+    g = _lens_geometry(W)
+    delta = f32(2.0 * 5.0 / g["F"])              # 2 full-res px at depth 5 m
+    cam = axis_camera(pos=(delta, 0.0, 0.0), prev_pos=(0.0, 0.0, 0.0))
+    prm = default_params()
+    am = f32(prm["alpha_motion"])
+    z_h = np.full((H2, W2), 5.0)
+    nr = np.ones((H2, W2), dtype=np.int32)
+    hist = np.zeros((H2, W2, 12))
+    ii = np.arange(W2)[None, :] + 0 * np.arange(H2)[:, None]
+    hist[..., 0] = ii * 0.01 + 0.1                # An red varies with x
+    hist[..., 6] = 1.0                           # h = 1, g = 0 (valid)
+    cur = _rt_field(H2, W2, [0.5, 0.5, 0.5], 1.0)
+    hout, crt, ct, var = _accumulate(cam, prm, W, H, z_h, cur, nr, hist.reshape(-1), 1)
+    hout = hout.reshape(H2, W2, 12)
+    want = am * hist[:, 1:, 0] + (1 - am) * 0.5
+    assert np.abs(hout[:, :-1, 0] - want).max() < 1e-6
+    # the last column reprojects outside the image: no history, the current value
+    assert np.abs(hout[:, -1, 0] - 0.5).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# reconstruction and composite
+# ---------------------------------------------------------------------------
+
+def test_recon_blend_limits():
+    L = oracle.lib()
+    W2, H2 = 40, 24
+    rng = np.random.default_rng(4)
+    med = np.concatenate([rng.uniform(0, 1, (H2, W2, 3)), rng.uniform(0, 1, (H2, W2, 1))], -1)
+    ct = rng.uniform(0, 8, (H2, W2))
+    nr = np.ones((H2, W2), dtype=np.int32)
+    nr[:, :5] = 0
+    med[:, :5] = 0
+    prm = oracle.params(default_params())
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    out = np.zeros_like(med)
+    L.or_recon(C.byref(prm), W2, H2, vp(med), vp(ct), vp(np.zeros((H2, W2))), vp(nr), vp(out))
+    assert np.array_equal(out, med)                     # b = 0 (Eq. 5) keeps the pixel
+    uni = np.zeros_like(med)
+    uni[:, 5:] = [0.2, 0.4, 0.6, 0.3]
+    L.or_recon(C.byref(prm), W2, H2, vp(uni), vp(ct), vp(np.full((H2, W2), 1.0)), vp(nr), vp(out))
+    assert np.abs(out[:, 5:] - [0.2, 0.4, 0.6, 0.3]).max() < 1e-12   # normalised filter
+    assert np.all(out[:, :5] == 0)
+
+
+def test_composite_special_cases():
+    L = oracle.lib()
+    W, H = 512, 8            # at this width c(0.3 m) ~ -83 px and c(1e4 m) ~ +2.5 px
+    W2, H2 = W // 2, H // 2
+    cam = axis_camera()
+    prm = default_params()
+    P, S, R = np.array([0.2, 0.3, 0.4]), np.array([0.9, 0.8, 0.7]), np.array([0.5, 0.1, 0.6])
+    color4 = np.zeros((H, W, 4), dtype=np.float32)
+    color4[..., :3] = S
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+
+    def run(z, bright, h, rays):
+        depth = np.full((H, W), z, dtype=np.float32)
+        pp = np.zeros((H2, W2, 4)); pp[..., :3] = P; pp[..., 3] = bright
+        rc = np.zeros((H2, W2, 4)); rc[..., :3] = R; rc[..., 3] = h
+        nr = np.full((H2, W2), rays, dtype=np.int32)
+        out = np.zeros((H, W, 4))
+        L.or_composite(C.byref(oracle.camera(cam)), C.byref(oracle.params(prm)), W, H, vp(color4),
+                       vp(depth), vp(pp), vp(rc), vp(nr), vp(out))
+        return out[..., :3].astype(np.float32).astype(np.float64)
+
+    S32, P32, R32 = (np.float32(x).astype(np.float64) for x in (S, P, R))
+    tol = 1e-6
+    assert np.abs(run(10.0, 0.5, 0.5, 1) - S32).max() < tol             # in focus: sharp
+    assert np.abs(run(0.3, 0.0, 0.5, 0) - P32).max() < tol              # no rays: PP
+    assert np.abs(run(0.3, 0.0, 0.5, 1) - R32).max() < tol              # near, not bright: RT
+    assert np.abs(run(0.3, 1.0, 0.5, 1) - P32).max() < tol              # near, bright: PP
+    assert np.abs(run(1e4, 0.0, 0.0, 1) - R32).max() < tol              # far, h = 0: RT
+    assert np.abs(run(1e4, 0.0, 0.3, 1) - P32).max() < tol              # far, h >= 0.3: PP
+    mid = run(1e4, 0.0, 0.15, 1)                                        # smoothstep(0.5) = 0.5
+    assert np.abs(mid - 0.5 * (R32 + P32)).max() < tol
+
+
+def test_default_params_are_the_papers():
+    with open(os.path.join(HERE, "golden", "paper_constants.json")) as fh:
+        g = json.load(fh)
+    p = default_params()
+    for k in ("s", "var_w_mask", "alpha", "var_w_recon", "b_max", "h_edge", "lod_scale",
+              "lod_max", "depth_range_m"):
+        assert p[k] == g[k]["value"], k
