@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the hybrid depth-of-field pass (one JSON line on stdout).
+
+A step is one frame of the pass (dof_frame: CoC, tiles, prefilter, 81-tap gather,
+median, ray mask + compaction, thin-lens rays through the device BVH, accumulation,
+variance blur, median, mips, reconstruction, composite) on the 1920x1080 workload:
+495,802-triangle lawn scene, 35 mm f/2 focused at 20 m, CoC radius <= 32 px, 1 spp,
+16-frame camera dolly.  The 16 G-buffers (produced on the device beforehand) are
+cycled, so each step reads inputs that are not in L2 (16 x 41 MB > 129 MB L2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1|c2|c3] [--impl ours|reference]
+
+N > 1 (torchrun): every rank renders its own session (replicas; the sessions are
+independent, there is no data exchange); the value is all ranks' frames over the
+max-over-ranks time.  --impl reference times the FP64 oracle on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hybrid-DoF frames/s at 1080p/4K, %HBM roofline; served p50/p99 frame latency"
+CYCLE = 16
+
+# Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
+# half-resolution pixel N, per masked pixel M, per full-resolution pixel P.
+BYTES = {
+    "k_downscale_tiles": ("N", 100.0),   # 4 x (colour 16 + depth 4) read, pp_in 16 + z 4 written
+    "k_prefilter": ("N", 32.0),
+    "k_main_filter": ("N", 36.0),        # pre 16 + z 4 read, 16 written (neighbour taps from cache)
+    "k_median_pp": ("N", 32.0),
+    "k_mask_compact": ("N", 8.0),
+    "k_trace": ("M", 72.0),              # queue + count read, 4 x float4 written (BVH reads hit L2)
+    "k_accumulate": ("N", 192.0),        # rt 64 + z 4 + nrays 4 + history 48 read; history 48 + 24 written
+    "k_var_blur": ("N", 8.0),
+    "k_median_rt": ("N", 36.0),
+    "k_mips": ("N", 64.0),
+    "k_recon": ("N", 44.0),
+    "k_composite": ("P", 45.0),          # colour 16 + depth 4 read, 16 written, + hpx inputs / 4
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, budget_s=15.0, steps=None):
+    """Time oracle frames on full-width bands of the workload's frame (same scene,
+    lens and camera path).  Returns (frames/s scaled to the full frame, description,
+    threads, per-step list)."""
+    import oracle
+    oracle.build()
+    osc = oracle.Scene(w.scene)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    H_band = max(16, (w.H // 8) // 2 * 2)
+    from synth import make_workload
+    band = make_workload(w.name, W=w.W, H=H_band)
+    cams = [band.camera(k % band.n_frames) for k in range(CYCLE)]
+    gbs = {}
+    times = []
+    t_total = time.time()
+    n = 0
+    while True:
+        k = n % min(CYCLE, band.n_frames)
+        if k not in gbs:
+            gbs[k] = oracle.gbuffer_f32(oracle.gbuffer(osc, cams[k], band.params, band.W, band.H))
+        hist = oracle.History(band.W, band.H)
+        t0 = time.perf_counter()
+        oracle.frame(osc, cams[k], band.params, band.W, band.H, gbs[k], hist, keep_rays=False)
+        times.append(time.perf_counter() - t0)
+        n += 1
+        if steps is not None:
+            if n >= steps:
+                break
+        elif time.time() - t_total > budget_s or n >= 8:
+            break
+    frac = (band.W * band.H) / (w.W * w.H)
+    per_frame = statistics.median(times) / frac
+    desc = (f"{w.W}x{H_band} bands (1/{round(1 / frac)} of a {w.W}x{w.H} frame) of the same scene and lens, "
+            f"{len(times)} frames, oracle frame only (G-buffer precomputed), scaled to a full frame")
+    return 1.0 / per_frame, desc, threads, times, frac
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2210_06158_gb300 import _build, dof
+    from synth import make_workload
+
+    _build.build()
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = make_workload(args.config, session=rank)
+    prm = dict(w.params)
+    spp = int(prm["spp"])
+    ctx = dof.Context(local)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    scene = dof.Scene(ctx, w.scene)
+    bvh_ms = (time.perf_counter() - t0) * 1e3
+    info = scene.info()
+
+    # G-buffers of the dolly (A0, on the device)
+    gbs = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for k in range(CYCLE):
+        gbs.append(dof.gbuffer(ctx, scene, w.camera(k % w.n_frames), prm, w.W, w.H))
+    ev1.record()
+    torch.cuda.synchronize()
+    gbuf_ms = ev0.elapsed_time(ev1) / CYCLE
+    for g in gbs:
+        del g["prim"]
+    pstruct = dof.params_struct(prm)
+
+    def cam_for(step):
+        c = w.camera(step % CYCLE % w.n_frames)
+        c.frame_index = step
+        return dof.camera_struct(c)
+
+    cams = [cam_for(s) for s in range(args.warmup + args.steps)]
+    out = torch.empty((w.H, w.W, 4), dtype=torch.float32, device=dev)
+    hist = dof.History(ctx, w.W, w.H, max_rays=spp)
+
+    def step(s, h, g=None):
+        gb = g if g is not None else gbs[s % CYCLE]
+        dof.frame(ctx, scene, gb, None, None, h, out, cam_struct=cams[s], params_s=pstruct)
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    for s in range(args.warmup):
+        step(s, hist)
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    # ---- timed region (device events on the launching stream)
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e_start.record(stream)
+        for s in range(args.warmup, args.warmup + args.steps):
+            step(s, hist)
+        e_end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    ms = e_start.elapsed_time(e_end)
+    st = hist.stats()
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # ---- instrumented pass: per-kernel device times over the same kind of steps
+    htime = dof.History(ctx, w.W, w.H, max_rays=spp, timing=True)
+    for s in range(args.warmup):
+        step(s, htime)
+    htime.kernel_times()
+    ktot = {k: 0.0 for k in dof.KERNELS}
+    nk = 0
+    rays = masked = 0
+    s = args.warmup
+    while s < args.warmup + args.steps:
+        for _ in range(min(32, args.warmup + args.steps - s)):
+            step(s, htime)
+            s += 1
+        km, n = htime.kernel_times()
+        for k, v in km.items():
+            ktot[k] += v
+        nk += n
+        fs = htime.stats()
+        rays += fs.rays
+        masked += fs.masked_pixels
+    kavg = {k: v / nk for k, v in ktot.items()}
+    n_samples = math.ceil(args.steps / 32)
+    rays_per_frame = rays / n_samples
+    masked_per_frame = masked / n_samples
+
+    # ---- end to end through the C ABI with host buffers
+    pin = []
+    for g in gbs:
+        pin.append(dict(color=g["color"].cpu().pin_memory(), depth=g["depth"].cpu().pin_memory()))
+    hout = torch.empty((w.H, w.W, 4), dtype=torch.float32).pin_memory()
+    stage = dict(color=torch.empty_like(gbs[0]["color"]), depth=torch.empty_like(gbs[0]["depth"]))
+    he = dof.History(ctx, w.W, w.H, max_rays=spp)
+    h2d = pin[0]["color"].numel() * 4 + pin[0]["depth"].numel() * 4
+    d2h = hout.numel() * 4
+
+    def e2e_step(s):
+        p = pin[s % CYCLE]
+        stage["color"].copy_(p["color"], non_blocking=True)
+        stage["depth"].copy_(p["depth"], non_blocking=True)
+        step(s, he, stage)
+        hout.copy_(out, non_blocking=True)
+
+    for s in range(args.warmup):
+        e2e_step(s)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.warmup, args.warmup + args.steps):
+        e2e_step(s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_e2e], dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": world * args.steps / (ms_e2e / 1e3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    N = (w.W // 2) * (w.H // 2)
+    units = {"N": N, "M": masked_per_frame, "P": w.W * w.H}
+    dom = max(kavg, key=lambda k: kavg[k])
+    kern = {}
+    for k, v in kavg.items():
+        if v <= 0:
+            continue
+        e = {"ms": round(v, 5), "share": round(v / sum(kavg.values()), 4)}
+        if k in BYTES:
+            u, b = BYTES[k]
+            e["gbs"] = round(units[u] * b / (v * 1e-3) / 1e9, 1)
+        kern[k] = e
+    if dom in BYTES:
+        u, b = BYTES[dom]
+        algo = units[u] * b
+        achieved = algo / (kavg[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes": int(algo)}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    # image passes together (streaming kernels only) vs HBM
+    img = [k for k in BYTES if k != "k_trace" and kavg.get(k, 0) > 0]
+    img_bytes = sum(units[BYTES[k][0]] * BYTES[k][1] for k in img)
+    img_ms = sum(kavg[k] for k in img)
+    res = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=world, steps=args.steps,
+               warmup=args.warmup, ms_per_step=round(ms_per_step, 4), higher_is_better=True, scaling="weak",
+               vs_baseline=None, dtype="f32", data="synthetic",
+               config=dict(workload=f"{w.name}: {w.W}x{w.H}, {info.n_tris} triangles (lawn + box field), "
+                                    f"{w.intr['f_m'] * 1000:.0f} mm f/{w.intr['f_number']:g} focus "
+                                    f"{w.intr['focus_m']:g} m, CoC radius <= {prm['max_coc_px']:g} px, {spp} spp, "
+                                    f"16-frame dolly",
+                           resolution=[w.W, w.H], triangles=info.n_tris, spp=spp, bvh_depth=info.depth,
+                           parallelism="replicas" if world > 1 else "single-gpu",
+                           l2="inputs larger than L2: 16 distinct G-buffers cycled (16 x 41 MB)"),
+               roofline=roof, e2e=e2e,
+               # per frame: 5 post-process, mask, trace, 2 temporal, RT median, 4 mip, recon, composite
+               # (+ 2 edge kernels in adaptive mode)
+               gpu_launches=(16 + (2 if int(prm["ray_mode"]) == 1 else 0)) * args.steps,
+               clocks=clk.summary(), kernel_ms=kern,
+               image_passes={"ms": round(img_ms, 4), "gbs": round(img_bytes / (img_ms * 1e-3) / 1e9, 1),
+                             "frac_of_hbm": round(img_bytes / (img_ms * 1e-3) / 1e9 / hbm_peak, 4)},
+               mrays_per_s=round(rays_per_frame / (kavg.get("k_trace", 0) * 1e-3) / 1e6, 1)
+               if kavg.get("k_trace", 0) > 0 else None,
+               rays_per_frame=int(rays_per_frame), mask_fraction=round(masked_per_frame / N, 4),
+               bvh_build_ms=round(bvh_ms, 2), gbuffer_ms=round(gbuf_ms, 3),
+               device_status=int(st.device_status))
+    return res, w
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    rank = int(os.environ.get("RANK", 0))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        from synth import make_workload
+        w = make_workload(args.config)
+        fps, desc, threads, times, frac = oracle_sample(w, steps=args.warmup + args.steps if args.steps <= 16 else None)
+        timed = times[min(len(times) - 1, args.warmup):] or times
+        ms = statistics.median(timed) / frac * 1e3
+        line = dict(metric=METRIC, value=round(1e3 / ms, 5), unit="frames/s", n_gpus=world, steps=len(timed),
+                    warmup=min(args.warmup, len(times) - len(timed)), ms_per_step=round(ms, 2),
+                    higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                    impl="reference",
+                    config=dict(workload=f"{w.name}: {w.W}x{w.H} (FP64 oracle on the host cores)"),
+                    cpu_baseline=dict(value=round(1e3 / ms, 5), unit="frames/s", cores=threads, kind="oracle",
+                                      sample=desc),
+                    e2e=dict(value=round(1e3 / ms, 5), unit="frames/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+        print(json.dumps(line), flush=True)
+        return 0
+
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("gloo")
+    res, w = run_ours(args, rank, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        fps, desc, threads, times, frac = oracle_sample(w)
+        res["cpu_baseline"] = dict(value=round(fps, 5), unit="frames/s", cores=threads, kind="oracle", sample=desc)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,235 @@
+/*
+ * dof.h -- C ABI of libdof, the GB300 (sm_103a) implementation of the per-frame
+ * hybrid depth-of-field pass of Tan, Chua, Biette and Bhojan, "A Hybrid System for
+ * Real-Time Rendering of Depth of Field Effect in Games" (arXiv 2210.06158).
+ *
+ * One frame (Section 3, Fig. 1): thin-lens circle of confusion from the G-buffer
+ * depth, half-resolution gather bokeh (prefilter, 81-tap main filter, median), a ray
+ * mask of the blurred-foreground region, thin-lens rays for the masked pixels through
+ * a device-built BVH, temporal accumulation with reprojection, median and spatial
+ * reconstruction of the ray-traced layer, and the CoC-driven composite.
+ *
+ * Conventions
+ *  - All image pointers are DEVICE pointers owned by the caller, row-major and
+ *    densely packed (row pitch = width * element size) unless a pitch is given.
+ *  - Scene geometry passed to dof_scene_upload is in HOST memory and is copied.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls enqueue work on it and return without synchronising, except where stated.
+ *  - Errors found on the host are returned synchronously as a negative DOF_ERR_*
+ *    code, with a message from dof_last_error() (thread-local).  Errors raised on the
+ *    device (bounded waits that ran out, failed internal checks) are recorded in a
+ *    device status word and reported by the next call on the same context, or by
+ *    dof_frame_stats().
+ *  - Lengths are in metres, image coordinates in pixels with (0,0) the top-left
+ *    pixel's corner; depth is the distance along the camera's forward axis.
+ */
+#ifndef DOF_H
+#define DOF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------------ */
+#define DOF_OK                 0
+#define DOF_ERR_INVALID_ARG   -1   /* null pointer, odd or zero size, d <= f, N <= 0, ... */
+#define DOF_ERR_OOM           -2   /* device allocation failed */
+#define DOF_ERR_BUDGET        -3   /* allocation would exceed the context's memory budget */
+#define DOF_ERR_CUDA          -4   /* a CUDA runtime call failed (see dof_last_error) */
+#define DOF_ERR_TIMEOUT       -5   /* a bounded device wait ran out */
+#define DOF_ERR_DEVICE_CHECK  -6   /* an internal device-side check failed */
+#define DOF_ERR_MISMATCH      -7   /* history bound to another size / scene */
+
+/* ---- image formats ----------------------------------------------------------- */
+#define DOF_FMT_F32 0              /* colour/normal float4 (rgb/xyz + unused), depth float */
+
+/* ---- parameters -------------------------------------------------------------- */
+
+/* Thin-lens camera (Section 3.3 below Eq. 6: focal length f, aperture a = f/N, focus
+ * distance d, sensor width w_s) and the pose of this and of the previous frame.  The
+ * pose is an orthonormal basis: `fwd` the optical axis, `right`/`up` the image x / -y
+ * axes.  The focal length in pixels is F = W v / w_s with v = f d / (d - f). */
+typedef struct {
+    float f_m, f_number, focus_m, sensor_w_m;
+    float pos[3], right[3], up[3], fwd[3];
+    float prev_pos[3], prev_right[3], prev_up[3], prev_fwd[3];
+    uint32_t frame_index;          /* Philox counter word (lens samples differ per frame) */
+} DofCamera;
+
+/* Method constants.  Defaults (dof_params_default) are the paper's values where it
+ * gives one: s = 0.8 (Section 4.2, Eq. 2), 1e5 (Eq. 4), alpha = 0.95 (Section 3.2.3),
+ * 2000 and 0.9 (Eq. 5), 0.3 (Eq. 7), 0.05 and 3 (Eq. 8), 10 cm (Section 4.2). */
+typedef struct {
+    float s;                /* Eq. 2 scale */
+    float var_w_mask;       /* Eq. 4 variance weight */
+    uint32_t m;             /* Eq. 4 ray budget per pixel (adaptive mode), <= DOF_MAX_RAYS */
+    uint32_t spp;           /* rays per masked pixel (fixed mode), 1..DOF_MAX_RAYS */
+    uint32_t ray_mode;      /* 0 fixed spp, 1 adaptive (Eq. 4) */
+    float depth_range_m;    /* main-filter depth range */
+    float alpha;            /* EMA blend factor */
+    float alpha_motion;     /* EMA blend factor while the camera moves */
+    float var_w_recon;      /* Eq. 5 weight */
+    float b_max;            /* Eq. 5 clamp */
+    float h_edge;           /* Eq. 7 smoothstep edge */
+    float lod_scale;        /* Eq. 8 slope */
+    float lod_max;          /* Eq. 8 clamp (<= 3) */
+    float max_coc_px;       /* CoC radius clamp in full-resolution px (>= 1, <= 256) */
+    float zof_ramp_px;      /* width of the continuous zone-of-focus test (Eq. 6) */
+    float cover_ramp_px;    /* width of the continuous coverage test D (Eq. 1) */
+    float bright_lum;       /* luminance above which a sample counts as bright bokeh */
+    float bright_ramp;      /* ... ramp width */
+    float mask_near_hpx;    /* ray mask threshold on the dilated near CoC radius (hpx) */
+    float z_far_m;          /* depth that stands for "no geometry" (sky) */
+    uint32_t tile;          /* max-CoC tile size in half-resolution px: must be 8 */
+    uint32_t albedo_seed;   /* hash seed of the per-triangle albedo */
+    uint64_t seed;          /* Philox key word 0 */
+    uint64_t session;       /* Philox key word 1 */
+    float light_dir[3];     /* direction the light travels */
+    float k_a, k_d;         /* ambient and Lambert coefficients */
+    float sky[3];           /* radiance of rays that hit nothing */
+    float emit;             /* radiance scale of material 1 (emitters) */
+} DofParams;
+
+#define DOF_MAX_RAYS 64
+
+typedef struct {
+    const float *color;     /* W*H float4: sharp all-in-focus colour (rgb, unused) */
+    const float *depth;     /* W*H float: depth along the optical axis, +inf = sky */
+    const float *normal;    /* W*H float4: surface normal (xyz, unused); read in adaptive mode */
+    uint32_t width, height; /* full resolution, both even and >= 2 */
+    uint32_t fmt;           /* DOF_FMT_F32 */
+} DofGBuffer;
+
+typedef struct DofCtx DofCtx;
+typedef struct DofScene DofScene;
+typedef struct DofHistory DofHistory;
+
+typedef struct {
+    uint32_t n_tris, n_nodes, depth, stack_limit;
+    uint64_t device_bytes;
+    float bounds_lo[3], bounds_hi[3];
+} DofSceneInfo;
+
+typedef struct {
+    uint64_t frames;           /* frames run on this history */
+    uint32_t masked_pixels;    /* last frame: half-resolution pixels with rays */
+    uint32_t rays;             /* last frame: rays traced */
+    int32_t device_status;     /* DOF_OK or the first device-side error */
+    uint32_t pad;
+} DofFrameStats;
+
+/* ---- context ----------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes (0 = unlimited) caps
+ * the device memory that scenes and histories of this context may hold; an upload or
+ * history that would exceed it fails with DOF_ERR_BUDGET.  Owns nothing of the
+ * caller's. */
+int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out);
+void dof_ctx_destroy(DofCtx *ctx);
+/* bytes currently held by the context's scenes and histories */
+size_t dof_ctx_bytes_in_use(const DofCtx *ctx);
+
+/* Fill `p` with the defaults above (1 spp fixed mode, 16 px radius clamp). */
+void dof_params_default(DofParams *p);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char *dof_last_error(void);
+
+/* ---- scene (Section 4.2: the acceleration structure) ------------------------- */
+
+/* Upload a triangle scene and build its BVH on the device: an LBVH (Karras 2012) over
+ * 30-bit Morton codes of the triangle centroids, two child boxes per node.
+ *   xyz      host, n_verts * 3 floats
+ *   tri_idx  host, n_tris * 3 vertex indices (< n_verts, checked)
+ *   tri_mat  host, n_tris material ids (0 diffuse with hash albedo, 1 emitter), or NULL
+ * The call copies the data, builds on `stream` and synchronises that stream before
+ * returning (the scene is then immutable and usable from any stream).  The library
+ * owns the returned scene; release it with dof_scene_destroy. */
+int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts, const uint32_t *tri_idx,
+                     const uint32_t *tri_mat, uint32_t n_tris, void *stream, DofScene **out);
+void dof_scene_destroy(DofScene *scene);
+int dof_scene_info(const DofScene *scene, DofSceneInfo *info);
+
+/* ---- G-buffer producer (input harness, Section 3 deferred shading) ----------- */
+
+/* Pinhole primary visibility of `scene` through the camera's lens centre at each
+ * full-resolution pixel centre: colour (float4, shaded as the rays of dof_frame,
+ * sky on a miss), depth (float, +inf on a miss), normal (float4, face normal turned
+ * towards the camera, 0 on a miss), prim (int32 triangle id, -1 on a miss; may be
+ * NULL).  All outputs are caller-owned device buffers of width*height elements. */
+int dof_gbuffer(DofCtx *ctx, const DofScene *scene, const DofCamera *cam, const DofParams *p,
+                uint32_t width, uint32_t height, float *color, float *depth, float *normal,
+                int32_t *prim, void *stream);
+
+/* ---- per-session history (Section 3.2.3) ------------------------------------- */
+
+#define DOF_HIST_RECORD_RAYS 1u   /* also keep each ray's hit triangle id (tests) */
+#define DOF_HIST_TIMING      2u   /* record a CUDA event after every kernel of a frame */
+
+/* Session state for width x height frames: accumulated ray-traced layer (FP32),
+ * blurred variance, and the per-frame work buffers of the pass.  max_rays (1..64)
+ * bounds spp / m of the frames run on it.  Owned by the library. */
+int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, uint32_t max_rays,
+                       uint32_t flags, DofHistory **out);
+void dof_history_destroy(DofHistory *hist);
+/* forget the accumulated history (the next frame restarts accumulation) */
+int dof_history_reset(DofHistory *hist);
+
+/* ---- one frame ----------------------------------------------------------------- */
+
+/* Run the hybrid depth-of-field pass for one frame on `stream`:
+ *   gbuf   the frame's G-buffer (device, caller-owned, read only)
+ *   cam    camera of this frame and pose of the previous one (host struct)
+ *   p      method parameters (host struct)
+ *   hist   the session's history: read and updated in place (the pass is
+ *          stream-ordered; frames of one history must not overlap)
+ *   out    device, width*height float4: composited image (rgb, 1)
+ * Host-side validation errors return before anything is enqueued. */
+int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *gbuf, const DofCamera *cam,
+              const DofParams *p, DofHistory *hist, float *out, void *stream);
+
+/* Synchronise `stream` and report the last frame's counters and the device status. */
+int dof_frame_stats(DofHistory *hist, void *stream, DofFrameStats *out);
+
+/* Kernels of one frame, in launch order (DOF_HIST_TIMING brackets each with events). */
+enum {
+    DOF_K_DOWNSCALE = 0, DOF_K_DILATE, DOF_K_PREFILTER, DOF_K_MAIN, DOF_K_MEDIAN_PP, DOF_K_EDGES,
+    DOF_K_MASK, DOF_K_TRACE, DOF_K_ACCUM, DOF_K_VAR_BLUR, DOF_K_MEDIAN_RT, DOF_K_MIPS, DOF_K_RECON,
+    DOF_K_COMPOSITE, DOF_K_COUNT
+};
+/* For a history created with DOF_HIST_TIMING: synchronise `stream`, add the device
+ * time (ms) each kernel took, summed over the frames recorded since the previous call
+ * (at most 64), to ms[0..DOF_K_COUNT-1] after zeroing it, and return that frame
+ * count in *frames.  Kernels not launched in a frame (e.g. EDGES in fixed mode)
+ * count 0. */
+int dof_kernel_times(DofHistory *hist, void *stream, float *ms, uint32_t *frames);
+
+/* ---- inspection (tests, tools) ------------------------------------------------- */
+
+/* Intermediate buffers of the last frame, for parity tests.  Element layouts (N = W/2 *
+ * H/2 half-resolution pixels, row-major; TW x TH = ceil(W/2/8) x ceil(H/2/8) tiles):
+ *   PP_IN  float4 N  (rgb, rho)         Z_H     float N
+ *   TILES  float2 TW*TH (near, |rho|)   TILES_DIL float2 TW*TH
+ *   PRE    float4 N  (rgb, rho)         MAIN    float4 N (rgb, bright)
+ *   PP_MED float4 N                      XN, XF  float N (adaptive mode only)
+ *   NRAYS  int32 N                        RAY_PRIM int32 N*max_rays (DOF_HIST_RECORD_RAYS)
+ *   RT     float4 4N: planes (An, h), (Af, n), (Bn, Bf, Fw, 0), (Pfar, 0)
+ *   CRT    float4 N (rgb, h)             CT, VAR, VAR_BLUR float N
+ *   RT_MED float4 N                       RECON   float4 N (rgb, h)
+ *   HIST   float4 3N: planes (An, h), (Af, g), (Bn, Bf, mu1, mu2)
+ * *dev_ptr is owned by the history and valid until the next call that uses it. */
+enum {
+    DOF_BUF_PP_IN = 0, DOF_BUF_Z_H, DOF_BUF_TILES, DOF_BUF_TILES_DIL, DOF_BUF_PRE,
+    DOF_BUF_MAIN, DOF_BUF_PP_MED, DOF_BUF_XN, DOF_BUF_XF, DOF_BUF_NRAYS, DOF_BUF_RAY_PRIM,
+    DOF_BUF_RT, DOF_BUF_CRT, DOF_BUF_CT, DOF_BUF_VAR, DOF_BUF_VAR_BLUR, DOF_BUF_RT_MED,
+    DOF_BUF_RECON, DOF_BUF_HIST, DOF_BUF_COUNT
+};
+int dof_debug_buffer(DofHistory *hist, int which, void **dev_ptr, size_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,516 @@
+// C ABI of libdof (include/dof.h): contexts, scenes, histories, and the per-frame
+// orchestration of the pass on one CUDA stream.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "dof_internal.cuh"
+
+int post_init_tables();
+int recon_init_tables();
+
+// ---------------------------------------------------------------------------
+// errors and allocation
+// ---------------------------------------------------------------------------
+
+static thread_local char g_err[512] = "";
+
+int dof_set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int dof_cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return DOF_OK;
+    cudaGetLastError();
+    int code = e == cudaErrorMemoryAllocation ? DOF_ERR_OOM : DOF_ERR_CUDA;
+    return dof_set_error(code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int dof_alloc(DofCtx *ctx, size_t bytes, void **ptr, size_t *acc) {
+    *ptr = nullptr;
+    if (bytes == 0) return DOF_OK;
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return dof_set_error(DOF_ERR_BUDGET, "allocation of %zu bytes exceeds the budget (%zu of %zu in use)", bytes,
+                             ctx->in_use, ctx->budget);
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return dof_cuda_check(e, "cudaMalloc");
+    }
+    ctx->in_use += bytes;
+    if (acc) *acc += bytes;
+    return DOF_OK;
+}
+
+void dof_free(DofCtx *ctx, void *ptr, size_t bytes) {
+    if (!ptr) return;
+    cudaFree(ptr);
+    ctx->in_use -= bytes;
+}
+
+namespace {
+
+// makes `dev` current for the duration of an API call and restores the caller's device
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite3(const float *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+int make_cam(const DofCamera *c, uint32_t W, uint32_t H, DevCam &o) {
+    if (!(c->f_m > 0.f) || !(c->f_number > 0.f) || !(c->sensor_w_m > 0.f) || !(c->focus_m > c->f_m) ||
+        !isfinite(c->f_m) || !isfinite(c->focus_m) || !isfinite(c->sensor_w_m))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "camera: need f > 0, N > 0, w_s > 0 and focus > f");
+    const float *vs[8] = {c->pos, c->right, c->up, c->fwd, c->prev_pos, c->prev_right, c->prev_up, c->prev_fwd};
+    for (auto v : vs)
+        if (!finite3(v)) return dof_set_error(DOF_ERR_INVALID_ARG, "camera: pose is not finite");
+    double f = c->f_m, N = c->f_number, d = c->focus_m, ws = c->sensor_w_m;
+    double a = f / N, v = f * d / (d - f), F = (double)W * v / ws;
+    auto f3 = [](const float *x) { return make_float3(x[0], x[1], x[2]); };
+    o.O = f3(c->pos); o.R = f3(c->right); o.U = f3(c->up); o.F = f3(c->fwd);
+    o.pO = f3(c->prev_pos); o.pR = f3(c->prev_right); o.pU = f3(c->prev_up); o.pF = f3(c->prev_fwd);
+    o.Fpx = (float)F;
+    o.invF = (float)(1.0 / F);
+    o.cocK = (float)(a * f * (double)W / (ws * (d - f)));
+    o.d = c->focus_m;
+    o.lens_r = (float)(0.5 * a);
+    o.halfW = 0.5f * (float)W;
+    o.halfH = 0.5f * (float)H;
+    o.W = (int)W; o.H = (int)H; o.W2 = (int)W / 2; o.H2 = (int)H / 2;
+    o.frame = c->frame_index;
+    o.moved = memcmp(c->pos, c->prev_pos, 12) || memcmp(c->right, c->prev_right, 12) ||
+              memcmp(c->up, c->prev_up, 12) || memcmp(c->fwd, c->prev_fwd, 12);
+    return DOF_OK;
+}
+
+int make_params(const DofParams *p, uint32_t W, uint32_t H, uint32_t max_rays, DevParams &o) {
+    if (p->tile != 8) return dof_set_error(DOF_ERR_INVALID_ARG, "params: tile must be 8");
+    if (p->ray_mode > 1) return dof_set_error(DOF_ERR_INVALID_ARG, "params: ray_mode must be 0 or 1");
+    if (p->ray_mode == 0 && (p->spp < 1 || p->spp > max_rays))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "params: spp %u outside 1..%u", p->spp, max_rays);
+    if (p->ray_mode == 1 && (p->m < 1 || p->m > max_rays))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "params: m %u outside 1..%u", p->m, max_rays);
+    if (!(p->max_coc_px >= 1.f && p->max_coc_px <= 256.f))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "params: max_coc_px must be in [1, 256]");
+    if (!(p->lod_max >= 0.f && p->lod_max <= 3.f))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "params: lod_max must be in [0, 3]");
+    if (!(p->depth_range_m > 0.f) || !(p->cover_ramp_px > 0.f) || !(p->zof_ramp_px > 0.f) ||
+        !(p->bright_ramp > 0.f) || !(p->h_edge > 0.f) || !(p->z_far_m > 0.f))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "params: ranges and ramps must be positive");
+    double l = sqrt((double)p->light_dir[0] * p->light_dir[0] + (double)p->light_dir[1] * p->light_dir[1] +
+                    (double)p->light_dir[2] * p->light_dir[2]);
+    if (!(l > 0.0)) return dof_set_error(DOF_ERR_INVALID_ARG, "params: light_dir is zero");
+    o.s = p->s; o.var_w_mask = p->var_w_mask; o.m = (float)p->m;
+    o.spp = (int)p->spp; o.ray_mode = (int)p->ray_mode;
+    o.inv_depth_range = (float)(1.0 / p->depth_range_m);
+    o.alpha = p->alpha; o.alpha_motion = p->alpha_motion;
+    o.var_w_recon = p->var_w_recon; o.b_max = p->b_max; o.h_edge = p->h_edge;
+    o.lod_scale = p->lod_scale; o.lod_max = p->lod_max;
+    o.rmax_hpx = 0.5f * p->max_coc_px;
+    o.zof_ramp = p->zof_ramp_px;
+    o.inv_cover_ramp = (float)(1.0 / p->cover_ramp_px);
+    o.bright_lum = p->bright_lum;
+    o.inv_bright_ramp = (float)(1.0 / p->bright_ramp);
+    o.mask_near_hpx = p->mask_near_hpx;
+    o.z_far = p->z_far_m;
+    o.albedo_seed = p->albedo_seed;
+    o.seed = p->seed; o.session = p->session;
+    o.light = make_float3((float)(p->light_dir[0] / l), (float)(p->light_dir[1] / l), (float)(p->light_dir[2] / l));
+    o.k_a = p->k_a; o.k_d = p->k_d; o.emit = p->emit;
+    o.sky = make_float3(p->sky[0], p->sky[1], p->sky[2]);
+    uint32_t W2 = W / 2, H2 = H / 2;
+    o.tiles_w = (int)((W2 + 7) / 8);
+    o.tiles_h = (int)((H2 + 7) / 8);
+    o.dil_k = (int)ceil(0.5 * (double)p->max_coc_px / 8.0);
+    return DOF_OK;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+extern "C" const char *dof_last_error(void) { return g_err; }
+
+extern "C" void dof_params_default(DofParams *p) {
+    memset(p, 0, sizeof(*p));
+    p->s = 0.8f; p->var_w_mask = 1e5f; p->m = 10; p->spp = 1; p->ray_mode = 0;
+    p->depth_range_m = 0.10f; p->alpha = 0.95f; p->alpha_motion = 0.8f;
+    p->var_w_recon = 2000.f; p->b_max = 0.9f; p->h_edge = 0.3f;
+    p->lod_scale = 0.05f; p->lod_max = 3.f; p->max_coc_px = 16.f;
+    p->zof_ramp_px = 0.25f; p->cover_ramp_px = 1.f; p->bright_lum = 4.f; p->bright_ramp = 1.f;
+    p->mask_near_hpx = 0.5f; p->z_far_m = 1e5f; p->tile = 8; p->albedo_seed = 1;
+    p->seed = 1; p->session = 0;
+    p->light_dir[0] = 0.3f; p->light_dir[1] = -1.f; p->light_dir[2] = 0.5f;
+    p->k_a = 0.1f; p->k_d = 1.f;
+    p->sky[0] = 0.5f; p->sky[1] = 0.6f; p->sky[2] = 0.8f;
+    p->emit = 8.f;
+}
+
+extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out) {
+    if (!out) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_ctx_create: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return dof_cuda_check(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_ctx_create: no device %d", device);
+    DeviceGuard g(device);
+    DofCtx *c = new DofCtx();
+    c->device = device;
+    c->budget = mem_budget_bytes;
+    c->in_use = 0;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return dof_set_error(DOF_ERR_OOM, "dof_ctx_create: status word");
+    }
+    if (post_init_tables() != 0 || recon_init_tables() != 0) {
+        cudaFree(c->d_status);
+        delete c;
+        return dof_set_error(DOF_ERR_CUDA, "dof_ctx_create: uploading filter tables failed");
+    }
+    *out = c;
+    return DOF_OK;
+}
+
+extern "C" void dof_ctx_destroy(DofCtx *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+extern "C" size_t dof_ctx_bytes_in_use(const DofCtx *ctx) { return ctx ? ctx->in_use : 0; }
+
+// ---------------------------------------------------------------------------
+// scene
+// ---------------------------------------------------------------------------
+
+extern "C" int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts, const uint32_t *tri_idx,
+                                const uint32_t *tri_mat, uint32_t n_tris, void *stream, DofScene **out) {
+    if (!ctx || !out || (n_tris && (!xyz || !tri_idx || !n_verts)))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_scene_upload: null argument");
+    if (n_tris > (1u << 30)) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_scene_upload: too many triangles");
+    *out = nullptr;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    DofScene *s = new DofScene();
+    memset(s, 0, sizeof(*s));
+    s->ctx = ctx;
+    s->n_tris = n_tris;
+    s->n_nodes = n_tris >= 2 ? n_tris - 1 : 0;
+    int rc = DOF_OK;
+    float *d_xyz = nullptr;
+    uint32_t *d_idx = nullptr, *d_mat = nullptr;
+    if (n_tris == 0) { s->depth = 0; *out = s; return DOF_OK; }
+    rc = dof_alloc(ctx, sizeof(float4) * 3 * (size_t)n_tris, (void **)&s->tris, &s->bytes);
+    if (rc == DOF_OK && s->n_nodes) rc = dof_alloc(ctx, sizeof(BvhNode) * (size_t)s->n_nodes, (void **)&s->nodes, &s->bytes);
+    if (rc == DOF_OK) rc = dof_cuda_check(cudaMalloc(&d_xyz, sizeof(float) * 3 * (size_t)n_verts), "scene vertices");
+    if (rc == DOF_OK) rc = dof_cuda_check(cudaMalloc(&d_idx, sizeof(uint32_t) * 3 * (size_t)n_tris), "scene indices");
+    if (rc == DOF_OK && tri_mat) rc = dof_cuda_check(cudaMalloc(&d_mat, sizeof(uint32_t) * (size_t)n_tris), "scene materials");
+    if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_xyz, xyz, sizeof(float) * 3 * (size_t)n_verts, cudaMemcpyHostToDevice, st), "upload");
+    if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_idx, tri_idx, sizeof(uint32_t) * 3 * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
+    if (rc == DOF_OK && tri_mat) rc = dof_cuda_check(cudaMemcpyAsync(d_mat, tri_mat, sizeof(uint32_t) * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
+    if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, st);
+    cudaFree(d_xyz); cudaFree(d_idx); cudaFree(d_mat);
+    if (rc != DOF_OK) {
+        dof_free(ctx, s->tris, sizeof(float4) * 3 * (size_t)n_tris);
+        dof_free(ctx, s->nodes, sizeof(BvhNode) * (size_t)s->n_nodes);
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return DOF_OK;
+}
+
+extern "C" void dof_scene_destroy(DofScene *s) {
+    if (!s) return;
+    DeviceGuard g(s->ctx->device);
+    dof_free(s->ctx, s->tris, sizeof(float4) * 3 * (size_t)s->n_tris);
+    dof_free(s->ctx, s->nodes, sizeof(BvhNode) * (size_t)s->n_nodes);
+    delete s;
+}
+
+extern "C" int dof_scene_info(const DofScene *s, DofSceneInfo *info) {
+    if (!s || !info) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_scene_info: null argument");
+    info->n_tris = s->n_tris;
+    info->n_nodes = s->n_nodes;
+    info->depth = s->depth;
+    info->stack_limit = 64;
+    info->device_bytes = s->bytes;
+    for (int k = 0; k < 3; k++) { info->bounds_lo[k] = s->lo[k]; info->bounds_hi[k] = s->hi[k]; }
+    return DOF_OK;
+}
+
+static SceneDev scene_dev(const DofScene *s) {
+    SceneDev d;
+    d.nodes = s->nodes;
+    d.tris = s->tris;
+    d.n_tris = (int)s->n_tris;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// G-buffer producer
+// ---------------------------------------------------------------------------
+
+extern "C" int dof_gbuffer(DofCtx *ctx, const DofScene *scene, const DofCamera *cam, const DofParams *p,
+                           uint32_t width, uint32_t height, float *color, float *depth, float *normal, int32_t *prim,
+                           void *stream) {
+    if (!ctx || !scene || !cam || !p || !color || !depth || !normal)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_gbuffer: null argument");
+    if (width < 2 || height < 2 || (width & 1) || (height & 1))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_gbuffer: size must be even and >= 2");
+    if (!aligned(color, 16) || !aligned(normal, 16) || !aligned(depth, 8))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_gbuffer: misaligned output");
+    DeviceGuard g(ctx->device);
+    DevCam dc;
+    DevParams dp;
+    int rc = make_cam(cam, width, height, dc);
+    if (rc) return rc;
+    rc = make_params(p, width, height, DOF_MAX_RAYS, dp);
+    if (rc) return rc;
+    launch_primary(dc, dp, scene_dev(scene), reinterpret_cast<float4 *>(color), depth,
+                   reinterpret_cast<float4 *>(normal), prim, ctx->d_status, (cudaStream_t)stream);
+    return dof_cuda_check(cudaGetLastError(), "dof_gbuffer launch");
+}
+
+// ---------------------------------------------------------------------------
+// history
+// ---------------------------------------------------------------------------
+
+static void history_free(DofHistory *h) {
+    DofCtx *c = h->ctx;
+    size_t N = h->N, T = (size_t)h->TW * h->TH;
+    dof_free(c, h->pp_in, 16 * N); dof_free(c, h->pre, 16 * N); dof_free(c, h->main_, 16 * N);
+    dof_free(c, h->pp_med, 16 * N); dof_free(c, h->n_h, 16 * N);
+    dof_free(c, h->z_h, 4 * N); dof_free(c, h->xn, 4 * N); dof_free(c, h->xf, 4 * N);
+    dof_free(c, h->tiles, 8 * T); dof_free(c, h->tiles_dil, 8 * T);
+    dof_free(c, h->nrays, 4 * N); dof_free(c, h->queue, 4 * N); dof_free(c, h->counters, 16);
+    dof_free(c, h->ray_prim, 4 * N * h->max_rays);
+    dof_free(c, h->rt, 64 * N); dof_free(c, h->crt, 16 * N); dof_free(c, h->rt_med, 16 * N);
+    dof_free(c, h->recon, 16 * N); dof_free(c, h->ct, 4 * N); dof_free(c, h->var, 4 * N);
+    for (int l = 0; l < 4; l++) {
+        size_t n = (size_t)h->mip_w[l] * h->mip_h[l];
+        dof_free(c, h->mip0[l], 16 * n);
+        dof_free(c, h->mip1[l], 8 * n);
+    }
+    for (int k = 0; k < 2; k++) {
+        dof_free(c, h->hist[k], 48 * N);
+        dof_free(c, h->var_blur[k], 4 * N);
+    }
+    if (h->ev) {
+        for (int k = 0; k < kTimingSlots * (DOF_K_COUNT + 1); k++)
+            if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+        delete[] h->ev;
+        h->ev = nullptr;
+    }
+}
+
+extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, uint32_t max_rays, uint32_t flags,
+                                  DofHistory **out) {
+    if (!ctx || !out) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_create: null argument");
+    *out = nullptr;
+    if (width < 2 || height < 2 || (width & 1) || (height & 1) || width > 16384 || height > 16384)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_create: size must be even, 2..16384");
+    if (max_rays < 1 || max_rays > DOF_MAX_RAYS)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_create: max_rays must be 1..%d", DOF_MAX_RAYS);
+    DeviceGuard g(ctx->device);
+    DofHistory *h = new DofHistory();
+    memset(h, 0, sizeof(*h));
+    h->ctx = ctx;
+    h->W = width; h->H = height; h->W2 = width / 2; h->H2 = height / 2;
+    h->N = h->W2 * h->H2;
+    h->TW = (h->W2 + 7) / 8; h->TH = (h->H2 + 7) / 8;
+    h->max_rays = max_rays;
+    h->flags = flags;
+    size_t N = h->N, T = (size_t)h->TW * h->TH;
+    h->mip_w[0] = (int)h->W2; h->mip_h[0] = (int)h->H2;
+    for (int l = 1; l < 4; l++) { h->mip_w[l] = (h->mip_w[l - 1] + 1) / 2; h->mip_h[l] = (h->mip_h[l - 1] + 1) / 2; }
+    int rc = DOF_OK;
+    auto A = [&](void **p, size_t b) { if (rc == DOF_OK) rc = dof_alloc(ctx, b, p, &h->bytes); };
+    A((void **)&h->pp_in, 16 * N); A((void **)&h->pre, 16 * N); A((void **)&h->main_, 16 * N);
+    A((void **)&h->pp_med, 16 * N); A((void **)&h->n_h, 16 * N);
+    A((void **)&h->z_h, 4 * N); A((void **)&h->xn, 4 * N); A((void **)&h->xf, 4 * N);
+    A((void **)&h->tiles, 8 * T); A((void **)&h->tiles_dil, 8 * T);
+    A((void **)&h->nrays, 4 * N); A((void **)&h->queue, 4 * N); A((void **)&h->counters, 16);
+    if (flags & DOF_HIST_RECORD_RAYS) A((void **)&h->ray_prim, 4 * N * max_rays);
+    A((void **)&h->rt, 64 * N); A((void **)&h->crt, 16 * N); A((void **)&h->rt_med, 16 * N);
+    A((void **)&h->recon, 16 * N); A((void **)&h->ct, 4 * N); A((void **)&h->var, 4 * N);
+    for (int l = 0; l < 4; l++) {
+        size_t n = (size_t)h->mip_w[l] * h->mip_h[l];
+        A((void **)&h->mip0[l], 16 * n);
+        A((void **)&h->mip1[l], 8 * n);
+    }
+    for (int k = 0; k < 2; k++) {
+        A((void **)&h->hist[k], 48 * N);
+        A((void **)&h->var_blur[k], 4 * N);
+    }
+    if (rc == DOF_OK) {
+        // history starts empty; the remaining buffers are defined before use each frame
+        for (int k = 0; k < 2 && rc == DOF_OK; k++) {
+            rc = dof_cuda_check(cudaMemset(h->hist[k], 0, 48 * N), "history clear");
+            if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->var_blur[k], 0, 4 * N), "history clear");
+        }
+        if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->xf, 0, 4 * N), "history clear");
+        if (rc == DOF_OK && h->ray_prim) rc = dof_cuda_check(cudaMemset(h->ray_prim, 0xFF, 4 * N * max_rays), "clear");
+    }
+    if (rc == DOF_OK && (flags & DOF_HIST_TIMING)) {
+        int n = kTimingSlots * (DOF_K_COUNT + 1);
+        h->ev = new cudaEvent_t[n]();
+        for (int k = 0; k < n && rc == DOF_OK; k++) rc = dof_cuda_check(cudaEventCreate(&h->ev[k]), "timing events");
+    }
+    if (rc != DOF_OK) {
+        history_free(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return DOF_OK;
+}
+
+extern "C" void dof_history_destroy(DofHistory *h) {
+    if (!h) return;
+    DeviceGuard g(h->ctx->device);
+    history_free(h);
+    delete h;
+}
+
+extern "C" int dof_history_reset(DofHistory *h) {
+    if (!h) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_reset: null history");
+    h->valid = 0;
+    return DOF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// frame
+// ---------------------------------------------------------------------------
+
+extern "C" int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *gb, const DofCamera *cam,
+                         const DofParams *p, DofHistory *h, float *out, void *stream) {
+    if (!ctx || !scene || !gb || !cam || !p || !h || !out)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: null argument");
+    if (h->ctx != ctx || scene->ctx != ctx) return dof_set_error(DOF_ERR_MISMATCH, "dof_frame: objects of another context");
+    if (gb->width != h->W || gb->height != h->H)
+        return dof_set_error(DOF_ERR_MISMATCH, "dof_frame: G-buffer %ux%u, history %ux%u", gb->width, gb->height, h->W, h->H);
+    if (gb->fmt != DOF_FMT_F32) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: unsupported G-buffer format");
+    if (!gb->color || !gb->depth || (p->ray_mode == 1 && !gb->normal))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: G-buffer plane is NULL");
+    if (!aligned(gb->color, 16) || !aligned(gb->depth, 8) || (gb->normal && !aligned(gb->normal, 16)) || !aligned(out, 16))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: misaligned buffer");
+    DevCam dc;
+    DevParams dp;
+    int rc = make_cam(cam, h->W, h->H, dc);
+    if (rc) return rc;
+    rc = make_params(p, h->W, h->H, h->max_rays, dp);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = dof_cuda_check(cudaMemsetAsync(h->counters, 0, 3 * sizeof(uint32_t), st), "dof_frame counters");
+    if (rc) return rc;
+    if (h->ev && h->ev_used < kTimingSlots) {
+        // a kernel that is not launched this frame gets an event right after its predecessor's
+        for (int k = 0; k <= DOF_K_COUNT; k++) cudaEventRecord(h->ev[h->ev_slot * (DOF_K_COUNT + 1) + k], st);
+    }
+    launch_post(dc, dp, gb, h, st);
+    launch_mask(dc, dp, gb, h, st);
+    launch_trace(dc, dp, scene_dev(scene), h, ctx->sm_count, st);
+    launch_temporal(dc, dp, h, st);
+    launch_recon(dc, dp, gb, h, reinterpret_cast<float4 *>(out), st);
+    rc = dof_cuda_check(cudaGetLastError(), "dof_frame launch");
+    if (rc) return rc;
+    h->cur ^= 1;
+    h->valid = 1;
+    h->frames++;
+    if (h->ev && h->ev_used < kTimingSlots) {
+        h->ev_slot = (h->ev_slot + 1) % kTimingSlots;
+        h->ev_used++;
+    }
+    return DOF_OK;
+}
+
+extern "C" int dof_kernel_times(DofHistory *h, void *stream, float *ms, uint32_t *frames) {
+    if (!h || !ms || !frames) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_kernel_times: null argument");
+    if (!h->ev) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_kernel_times: history has no DOF_HIST_TIMING");
+    DeviceGuard g(h->ctx->device);
+    int rc = dof_cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "dof_kernel_times sync");
+    if (rc) return rc;
+    for (int k = 0; k < DOF_K_COUNT; k++) ms[k] = 0.f;
+    int first = (h->ev_slot - h->ev_used + kTimingSlots) % kTimingSlots;
+    for (int f = 0; f < h->ev_used; f++) {
+        int s = (first + f) % kTimingSlots;
+        for (int k = 0; k < DOF_K_COUNT; k++) {
+            float t = 0.f;
+            rc = dof_cuda_check(cudaEventElapsedTime(&t, h->ev[s * (DOF_K_COUNT + 1) + k],
+                                                     h->ev[s * (DOF_K_COUNT + 1) + k + 1]), "cudaEventElapsedTime");
+            if (rc) return rc;
+            ms[k] += t;
+        }
+    }
+    *frames = (uint32_t)h->ev_used;
+    h->ev_used = 0;
+    return DOF_OK;
+}
+
+extern "C" int dof_frame_stats(DofHistory *h, void *stream, DofFrameStats *out) {
+    if (!h || !out) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame_stats: null argument");
+    DeviceGuard g(h->ctx->device);
+    uint32_t c[4];
+    int rc = dof_cuda_check(cudaMemcpyAsync(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost, (cudaStream_t)stream),
+                            "dof_frame_stats");
+    if (rc == DOF_OK) rc = dof_cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "dof_frame_stats sync");
+    if (rc) return rc;
+    out->frames = h->frames;
+    out->masked_pixels = c[0];
+    out->rays = c[1];
+    out->device_status = c[3] ? DOF_ERR_DEVICE_CHECK : DOF_OK;
+    out->pad = 0;
+    return DOF_OK;
+}
+
+extern "C" int dof_debug_buffer(DofHistory *h, int which, void **ptr, size_t *bytes) {
+    if (!h || !ptr || !bytes) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_debug_buffer: null argument");
+    size_t N = h->N, T = (size_t)h->TW * h->TH;
+    int last = h->cur;   // after a frame, `cur` holds the newest history
+    switch (which) {
+        case DOF_BUF_PP_IN: *ptr = h->pp_in; *bytes = 16 * N; break;
+        case DOF_BUF_Z_H: *ptr = h->z_h; *bytes = 4 * N; break;
+        case DOF_BUF_TILES: *ptr = h->tiles; *bytes = 8 * T; break;
+        case DOF_BUF_TILES_DIL: *ptr = h->tiles_dil; *bytes = 8 * T; break;
+        case DOF_BUF_PRE: *ptr = h->pre; *bytes = 16 * N; break;
+        case DOF_BUF_MAIN: *ptr = h->main_; *bytes = 16 * N; break;
+        case DOF_BUF_PP_MED: *ptr = h->pp_med; *bytes = 16 * N; break;
+        case DOF_BUF_XN: *ptr = h->xn; *bytes = 4 * N; break;
+        case DOF_BUF_XF: *ptr = h->xf; *bytes = 4 * N; break;
+        case DOF_BUF_NRAYS: *ptr = h->nrays; *bytes = 4 * N; break;
+        case DOF_BUF_RAY_PRIM: *ptr = h->ray_prim; *bytes = h->ray_prim ? 4 * N * h->max_rays : 0; break;
+        case DOF_BUF_RT: *ptr = h->rt; *bytes = 64 * N; break;
+        case DOF_BUF_CRT: *ptr = h->crt; *bytes = 16 * N; break;
+        case DOF_BUF_CT: *ptr = h->ct; *bytes = 4 * N; break;
+        case DOF_BUF_VAR: *ptr = h->var; *bytes = 4 * N; break;
+        case DOF_BUF_VAR_BLUR: *ptr = h->var_blur[last]; *bytes = 4 * N; break;
+        case DOF_BUF_RT_MED: *ptr = h->rt_med; *bytes = 16 * N; break;
+        case DOF_BUF_RECON: *ptr = h->recon; *bytes = 16 * N; break;
+        case DOF_BUF_HIST: *ptr = h->hist[last]; *bytes = 48 * N; break;
+        default: return dof_set_error(DOF_ERR_INVALID_ARG, "dof_debug_buffer: unknown buffer %d", which);
+    }
+    return DOF_OK;
+}

@@ -1,0 +1,175 @@
+// Internal declarations of libdof (GB300 / sm_103a): device-side parameter blocks,
+// small FP32 helpers shared by the kernels, and the host objects behind the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/dof.h"
+
+// ---------------------------------------------------------------------------
+// device parameter blocks (passed by value to kernels)
+// ---------------------------------------------------------------------------
+
+struct DevCam {
+    float3 O, R, U, F;          // current pose
+    float3 pO, pR, pU, pF;      // previous pose
+    float invF;                 // 1 / focal length in full-resolution pixels
+    float Fpx;                  // focal length in full-resolution pixels
+    float cocK;                 // c(z) = cocK * (z - d) / z  (signed diameter, fpx)
+    float d;                    // focus distance
+    float lens_r;               // aperture radius a / 2
+    float halfW, halfH;         // W / 2, H / 2
+    int W, H, W2, H2;
+    uint32_t frame;
+    int moved;
+};
+
+struct DevParams {
+    float s, var_w_mask, m;
+    int spp, ray_mode;
+    float inv_depth_range, alpha, alpha_motion, var_w_recon, b_max, h_edge;
+    float lod_scale, lod_max, rmax_hpx, zof_ramp, inv_cover_ramp, bright_lum, inv_bright_ramp;
+    float mask_near_hpx, z_far;
+    uint32_t albedo_seed;
+    unsigned long long seed, session;
+    float3 light;               // normalised light travel direction
+    float k_a, k_d, emit;
+    float3 sky;
+    int tiles_w, tiles_h, dil_k;
+};
+
+// ---------------------------------------------------------------------------
+// scene (device-built LBVH)
+// ---------------------------------------------------------------------------
+
+// BVH node: boxes of both children and their references.  A reference r >= 0 is an
+// internal node, r < 0 the leaf holding sorted triangle ~r.
+struct __align__(16) BvhNode {
+    float4 a;   // child0 lo.xyz, child0 hi.x
+    float4 b;   // child0 hi.yz, child1 lo.xy
+    float4 c;   // child1 lo.z, child1 hi.xyz
+    int4 r;     // child0 ref, child1 ref, unused, unused
+};
+
+struct SceneDev {
+    const BvhNode *nodes;        // n_tris - 1 internal nodes (root = 0) when n_tris >= 2
+    const float4 *tris;          // 3 float4 per sorted triangle: v0 (w = prim id bits), v1, v2 (w = material bits)
+    int n_tris;
+};
+
+// ---------------------------------------------------------------------------
+// host objects
+// ---------------------------------------------------------------------------
+
+struct DofCtx {
+    int device;
+    size_t budget, in_use;
+    int sm_count;
+    uint32_t *d_status;            // device status word of context-level launches
+};
+
+struct DofScene {
+    DofCtx *ctx;
+    uint32_t n_tris, n_nodes, depth;
+    BvhNode *nodes;
+    float4 *tris;
+    size_t bytes;
+    float lo[3], hi[3];
+};
+
+struct DofHistory {
+    DofCtx *ctx;
+    uint32_t W, H, W2, H2, N, TW, TH, max_rays, flags;
+    size_t bytes;
+    uint64_t frames;
+    int valid;                     // a previous frame exists
+    int cur;                       // which history buffer holds the latest frame
+    // per-frame work buffers
+    float4 *pp_in, *pre, *main_, *pp_med, *n_h;
+    float *z_h, *xn, *xf;
+    float2 *tiles, *tiles_dil;
+    int32_t *nrays;
+    uint32_t *queue;               // masked pixel indices
+    uint32_t *counters;            // [0] queue length, [1] rays, [2] work cursor, [3] device status
+    int32_t *ray_prim;
+    float4 *rt;                    // 4 planes of N
+    float4 *crt, *rt_med, *recon;
+    float *ct, *var;
+    float4 *mip0[4];               // (rgb, h) * valid per level
+    float2 *mip1[4];               // (c_t, 1) * valid per level
+    int mip_w[4], mip_h[4];
+    // persistent state (ping-pong)
+    float4 *hist[2];               // 3 planes of N each
+    float *var_blur[2];
+    uint32_t host_counters[4];
+    // per-kernel timing ring (DOF_HIST_TIMING)
+    cudaEvent_t *ev;               // kTimingSlots x (DOF_K_COUNT + 1)
+    int ev_slot, ev_used;
+};
+
+constexpr int kTimingSlots = 64;
+
+// record the event that closes kernel `k` of the current frame (no-op without timing)
+inline void tmark(DofHistory *h, int k, cudaStream_t st) {
+    if (h->ev && h->ev_used < kTimingSlots) cudaEventRecord(h->ev[h->ev_slot * (DOF_K_COUNT + 1) + k + 1], st);
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+int dof_set_error(int code, const char *fmt, ...);
+int dof_cuda_check(cudaError_t e, const char *what);
+int dof_alloc(DofCtx *ctx, size_t bytes, void **ptr, size_t *acc);
+void dof_free(DofCtx *ctx, void *ptr, size_t bytes);
+
+// launch wrappers (one per kernel group, defined in the .cu files)
+int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const uint32_t *d_idx,
+                     const uint32_t *d_mat, cudaStream_t st);
+void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *color, float *depth,
+                    float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st);
+void launch_post(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h,
+                 cudaStream_t st);
+void launch_mask(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h,
+                 cudaStream_t st);
+void launch_trace(const DevCam &cam, const DevParams &p, SceneDev sc, DofHistory *h, int sm_count,
+                  cudaStream_t st);
+void launch_temporal(const DevCam &cam, const DevParams &p, DofHistory *h, cudaStream_t st);
+void launch_recon(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h,
+                  float4 *out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+
+#ifdef __CUDACC__
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize(float3 v) { return rsqrtf(dot(v, v)) * v; }
+__device__ __forceinline__ float sat(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return a + t * (b - a); }
+__device__ __forceinline__ float lum709(float r, float g, float b) { return 0.2126f * r + 0.7152f * g + 0.0722f * b; }
+
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 f4scale(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
+__device__ __forceinline__ float4 f4fma(float s, float4 a, float4 acc) {
+    return make_float4(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y), fmaf(s, a.z, acc.z), fmaf(s, a.w, acc.w));
+}
+
+// signed CoC diameter (full-resolution px) of depth z
+__device__ __forceinline__ float coc_of(const DevCam &c, float z) { return c.cocK * (z - c.d) / z; }
+
+// direction through sensor point (x, y) (full-resolution px) and the lens centre
+__device__ __forceinline__ float3 pixel_dir(const DevCam &c, float x, float y) {
+    float sx = (x - c.halfW) * c.invF, sy = (y - c.halfH) * c.invF;
+    return normalize(make_float3(c.F.x + sx * c.R.x - sy * c.U.x, c.F.y + sx * c.R.y - sy * c.U.y,
+                                 c.F.z + sx * c.R.z - sy * c.U.z));
+}
+#endif

@@ -1,0 +1,81 @@
+// Gather-filter helpers of libdof shared by the post-process and reconstruction
+// kernels: tap tables in constant memory, software bilinear fetches (FP32 weights;
+// texture-unit filtering is not used because its weights are low-precision fixed
+// point), and the median-of-9 min/max network.
+#pragma once
+
+#include <math.h>
+
+#include "dof_internal.cuh"
+
+// unit offsets (cos, sin) of the 8 prefilter taps (angles k pi / 4)
+static __constant__ float2 c_pre8[8];
+// 81-tap ring kernel: (cos, sin, radius fraction) -- centre, then rings k = 1..4 of
+// 8k taps at angles 2 pi m / (8k) and radius k / 4
+static __constant__ float3 c_ring81[81];
+
+// Fill this translation unit's copy of the tables (computed in double, rounded once).
+static inline int upload_filter_tables() {
+    float2 pre[8];
+    for (int k = 0; k < 8; k++) pre[k] = make_float2((float)cos(k * M_PI / 4.0), (float)sin(k * M_PI / 4.0));
+    float3 ring[81];
+    ring[0] = make_float3(0.f, 0.f, 0.f);
+    int t = 1;
+    for (int k = 1; k <= 4; k++)
+        for (int m = 0; m < 8 * k; m++, t++) {
+            double th = 2.0 * M_PI * m / (8.0 * k);
+            ring[t] = make_float3((float)cos(th), (float)sin(th), (float)(k / 4.0));
+        }
+    cudaError_t e1 = cudaMemcpyToSymbol(c_pre8, pre, sizeof(pre));
+    cudaError_t e2 = cudaMemcpyToSymbol(c_ring81, ring, sizeof(ring));
+    return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : -1;
+}
+
+#ifdef __CUDACC__
+// bilinear fetch, clamp-to-edge, texel centres at integer coordinates
+__device__ __forceinline__ float4 bilinear4(const float4 *__restrict__ img, int w, int h, float x, float y) {
+    float xf = floorf(x), yf = floorf(y);
+    float fx = x - xf, fy = y - yf;
+    int x0 = (int)xf, y0 = (int)yf;
+    int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
+    int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
+    float4 a = __ldg(&img[(size_t)ya * w + xa]), b = __ldg(&img[(size_t)ya * w + xb]);
+    float4 c = __ldg(&img[(size_t)yb * w + xa]), d = __ldg(&img[(size_t)yb * w + xb]);
+    float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+    return f4fma(w11, d, f4fma(w01, c, f4fma(w10, b, f4scale(w00, a))));
+}
+
+__device__ __forceinline__ void bilinear4z(const float4 *__restrict__ img, const float *__restrict__ z, int w, int h,
+                                           float x, float y, float4 &out, float &zo) {
+    float xf = floorf(x), yf = floorf(y);
+    float fx = x - xf, fy = y - yf;
+    int x0 = (int)xf, y0 = (int)yf;
+    int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
+    int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
+    size_t qa = (size_t)ya * w, qb = (size_t)yb * w;
+    float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+    out = f4fma(w11, __ldg(&img[qb + xb]), f4fma(w01, __ldg(&img[qb + xa]),
+                f4fma(w10, __ldg(&img[qa + xb]), f4scale(w00, __ldg(&img[qa + xa])))));
+    zo = w00 * __ldg(&z[qa + xa]) + w10 * __ldg(&z[qa + xb]) + w01 * __ldg(&z[qb + xa]) + w11 * __ldg(&z[qb + xb]);
+}
+
+__device__ __forceinline__ void cx4(float4 &a, float4 &b) {
+    float4 lo = make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
+    float4 hi = make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+    a = lo;
+    b = hi;
+}
+
+// per-channel median of 9 by the 19-exchange min/max network (Paeth; the GPU median
+// of Smith 1996 cited in Section 3.1.3)
+__device__ __forceinline__ float4 median9(float4 *p) {
+    cx4(p[1], p[2]); cx4(p[4], p[5]); cx4(p[7], p[8]);
+    cx4(p[0], p[1]); cx4(p[3], p[4]); cx4(p[6], p[7]);
+    cx4(p[1], p[2]); cx4(p[4], p[5]); cx4(p[7], p[8]);
+    cx4(p[0], p[3]); cx4(p[5], p[8]); cx4(p[4], p[7]);
+    cx4(p[3], p[6]); cx4(p[1], p[4]); cx4(p[2], p[5]);
+    cx4(p[4], p[7]); cx4(p[4], p[2]); cx4(p[6], p[4]);
+    cx4(p[4], p[2]);
+    return p[4];
+}
+#endif

@@ -1,0 +1,163 @@
+// Post-process stage of libdof (Section 3.1): CoC + 2x2 downscale + tile max,
+// tile dilation, 9-tap bilateral prefilter, 81-tap main gather filter (Eq. 1), and the
+// 3x3 median postfilter (a 19-exchange min/max network, Section 3.1.3).
+#include "dof_internal.cuh"
+#include "filters.cuh"
+
+namespace {
+
+// A1: one 8x8 block per tile of half-resolution pixels.  Colour = mean of the 2x2
+// full-resolution block, depth = the nearest of the four (clamped to z_far), CoC
+// radius rho = clamp(c(z)/4) and normal of that sample; tile max of near and |rho|.
+__global__ void __launch_bounds__(64) k_downscale_tiles(DevCam cam, DevParams p, const float4 *__restrict__ color,
+                                                        const float *__restrict__ depth,
+                                                        const float4 *__restrict__ normal, float4 *pp_in,
+                                                        float *z_h, float4 *n_h, float2 *tiles) {
+    int i = blockIdx.x * 8 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    float nm = 0.f, am = 0.f;
+    if (i < cam.W2 && j < cam.H2) {
+        size_t f0 = (size_t)(2 * j) * cam.W + 2 * i, f1 = f0 + cam.W;
+        float4 c0 = __ldg(&color[f0]), c1 = __ldg(&color[f0 + 1]), c2 = __ldg(&color[f1]), c3 = __ldg(&color[f1 + 1]);
+        float2 d01 = __ldg(reinterpret_cast<const float2 *>(&depth[f0]));
+        float2 d23 = __ldg(reinterpret_cast<const float2 *>(&depth[f1]));
+        float z[4] = {fminf(d01.x, p.z_far), fminf(d01.y, p.z_far), fminf(d23.x, p.z_far), fminf(d23.y, p.z_far)};
+        int k = 0;
+#pragma unroll
+        for (int m = 1; m < 4; m++)
+            if (z[m] < z[k]) k = m;
+        float zm = z[k];
+        float rho = fminf(fmaxf(0.25f * coc_of(cam, zm), -p.rmax_hpx), p.rmax_hpx);
+        size_t q = (size_t)j * cam.W2 + i;
+        pp_in[q] = make_float4(0.25f * (c0.x + c1.x + c2.x + c3.x), 0.25f * (c0.y + c1.y + c2.y + c3.y),
+                               0.25f * (c0.z + c1.z + c2.z + c3.z), rho);
+        z_h[q] = zm;
+        if (p.ray_mode == 1) {
+            size_t fk = (k < 2 ? f0 : f1) + (k & 1);
+            n_h[q] = __ldg(&normal[fk]);
+        }
+        nm = fmaxf(0.f, -rho);
+        am = fabsf(rho);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        nm = fmaxf(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+    }
+    __shared__ float2 red[2];
+    int t = threadIdx.y * 8 + threadIdx.x;
+    if ((t & 31) == 0) red[t >> 5] = make_float2(nm, am);
+    __syncthreads();
+    if (t == 0) tiles[blockIdx.y * p.tiles_w + blockIdx.x] = make_float2(fmaxf(red[0].x, red[1].x), fmaxf(red[0].y, red[1].y));
+}
+
+// A2: max over the (2K+1)^2 tile neighbourhood
+__global__ void k_tile_dilate(DevParams p, const float2 *tiles, float2 *dil) {
+    int tx = blockIdx.x * blockDim.x + threadIdx.x, ty = blockIdx.y * blockDim.y + threadIdx.y;
+    if (tx >= p.tiles_w || ty >= p.tiles_h) return;
+    float nm = 0.f, am = 0.f;
+    for (int y = max(ty - p.dil_k, 0); y <= min(ty + p.dil_k, p.tiles_h - 1); y++)
+        for (int x = max(tx - p.dil_k, 0); x <= min(tx + p.dil_k, p.tiles_w - 1); x++) {
+            float2 v = __ldg(&tiles[y * p.tiles_w + x]);
+            nm = fmaxf(nm, v.x);
+            am = fmaxf(am, v.y);
+        }
+    dil[ty * p.tiles_w + tx] = make_float2(nm, am);
+}
+
+// A3: 9-tap bilateral prefilter, radius max(R/8, sqrt(2)/2), taps at angles k pi/4
+__global__ void k_prefilter(int W2, int H2, DevParams p, const float4 *__restrict__ pp_in,
+                            const float2 *__restrict__ dil, float4 *pre) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    size_t q = (size_t)j * W2 + i;
+    float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
+    float rp = fmaxf(R * 0.125f, 0.70710678118654752f);
+    float4 c0 = __ldg(&pp_in[q]);
+    float inv = 1.f / fmaxf(1.f, fabsf(c0.w));
+    float ax = c0.x, ay = c0.y, az = c0.z, ws = 1.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        float2 u = c_pre8[k];
+        float4 s = bilinear4(pp_in, W2, H2, i + rp * u.x, j + rp * u.y);
+        float w = sat(1.f - fabsf(s.w - c0.w) * inv);
+        ax += w * s.x; ay += w * s.y; az += w * s.z; ws += w;
+    }
+    float r = 1.f / ws;
+    pre[q] = make_float4(ax * r, ay * r, az * r, c0.w);
+}
+
+// A4: 81-tap main filter (Eq. 1).  Rings k = 1..4 of 8k taps at radius kR/4 of the
+// dilated max CoC R; foreground/background weights with the coverage ramp D and
+// sampleAlpha; normalised weighted sum plus the share of bright samples.
+__global__ void __launch_bounds__(256) k_main_filter(int W2, int H2, DevParams p, const float4 *__restrict__ pre,
+                                                     const float *__restrict__ z_h, const float2 *__restrict__ dil,
+                                                     float4 *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    size_t q = (size_t)j * W2 + i;
+    float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
+    float z0 = __ldg(&z_h[q]);
+    float r0 = fabsf(__ldg(&pre[q]).w);
+    const float kInvSqrtPi = 0.56418958354775628f, kInvPi = 0.31830988618379067f;
+    float ax = 0.f, ay = 0.f, az = 0.f, bright = 0.f, wsum = 0.f;
+#pragma unroll 3
+    for (int t = 0; t < 81; t++) {
+        float3 u = c_ring81[t];
+        float dist = u.z * R;
+        float x = i + dist * u.x, y = j + dist * u.y;
+        float4 s;
+        float zi;
+        bilinear4z(pre, z_h, W2, H2, x, y, s, zi);
+        float ri = fabsf(s.w);
+        float wf = sat((z0 - zi) * p.inv_depth_range);
+        float rr = fmaxf(ri, kInvSqrtPi);
+        float a = kInvPi / (rr * rr);
+        float Df = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
+        float Db = sat((fminf(ri, r0) - dist) * p.inv_cover_ramp + 0.5f);
+        float W = (wf * Df + (1.f - wf) * Db) * a;
+        ax += W * s.x; ay += W * s.y; az += W * s.z;
+        bright += W * sat((lum709(s.x, s.y, s.z) - p.bright_lum) * p.inv_bright_ramp);
+        wsum += W;
+    }
+    float r = 1.f / wsum;
+    out[q] = make_float4(ax * r, ay * r, az * r, bright * r);
+}
+
+// A5: per-channel 3x3 median (clamp-to-edge)
+__global__ void k_median_pp(int W2, int H2, const float4 *__restrict__ src, float4 *dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    float4 v[9];
+    int n = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++) {
+        int y = min(max(j + dy, 0), H2 - 1);
+#pragma unroll
+        for (int dx = -1; dx <= 1; dx++) {
+            int x = min(max(i + dx, 0), W2 - 1);
+            v[n++] = __ldg(&src[(size_t)y * W2 + x]);
+        }
+    }
+    dst[(size_t)j * W2 + i] = median9(v);
+}
+
+}  // namespace
+
+int post_init_tables() { return upload_filter_tables(); }
+
+void launch_post(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h, cudaStream_t st) {
+    dim3 b8(8, 8), gt(h->TW, h->TH);
+    k_downscale_tiles<<<gt, b8, 0, st>>>(cam, p, reinterpret_cast<const float4 *>(g->color), g->depth,
+                                         reinterpret_cast<const float4 *>(g->normal), h->pp_in, h->z_h, h->n_h,
+                                         h->tiles);
+    tmark(h, DOF_K_DOWNSCALE, st);
+    dim3 bt(16, 16), gtd((h->TW + 15) / 16, (h->TH + 15) / 16);
+    k_tile_dilate<<<gtd, bt, 0, st>>>(p, h->tiles, h->tiles_dil);
+    tmark(h, DOF_K_DILATE, st);
+    dim3 b(32, 8), gh((h->W2 + 31) / 32, (h->H2 + 7) / 8);
+    k_prefilter<<<gh, b, 0, st>>>(h->W2, h->H2, p, h->pp_in, h->tiles_dil, h->pre);
+    tmark(h, DOF_K_PREFILTER, st);
+    k_main_filter<<<gh, b, 0, st>>>(h->W2, h->H2, p, h->pre, h->z_h, h->tiles_dil, h->main_);
+    tmark(h, DOF_K_MAIN, st);
+    k_median_pp<<<gh, b, 0, st>>>(h->W2, h->H2, h->main_, h->pp_med);
+    tmark(h, DOF_K_MEDIAN_PP, st);
+}

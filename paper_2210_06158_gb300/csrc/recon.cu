@@ -1,0 +1,216 @@
+// Reconstruction and composite of libdof: 3x3 median of the ray-traced colour over
+// pixels with rays, mip pyramid of the premultiplied layer, 81-tap spatial
+// reconstruction at LOD clamp(0.05 c_t, 0, 3) blended by b = clamp(2000 sigma^2, 0,
+// 0.9) (Section 3.2.4, Eq. 5, Eq. 8), and the per-pixel composite of sharp,
+// post-processed and ray-traced colour (Section 3.3, Eq. 6, Eq. 7).
+#include "dof_internal.cuh"
+#include "filters.cuh"
+
+namespace {
+
+// A10: lower median over the valid 3x3 neighbours: invalid slots are padded with
+// -inf / +inf so the median-of-9 network selects index (k-1)/2 of the k valid values
+__global__ void k_median_rt(int W2, int H2, const float4 *__restrict__ crt, const int32_t *__restrict__ nrays,
+                            float4 *dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    size_t q = (size_t)j * W2 + i;
+    if (__ldg(&nrays[q]) <= 0) { dst[q] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+    float4 v[9];
+    bool ok[9];
+    int k = 0, n = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+        for (int dx = -1; dx <= 1; dx++) {
+            int x = i + dx, y = j + dy;
+            bool in = x >= 0 && y >= 0 && x < W2 && y < H2;
+            size_t qn = in ? (size_t)y * W2 + x : q;
+            ok[n] = in && __ldg(&nrays[qn]) > 0;
+            v[n] = __ldg(&crt[qn]);
+            k += ok[n];
+            n++;
+        }
+    int lows = 4 - (k - 1) / 2;   // -inf pads; the rest of the invalid slots get +inf
+#pragma unroll
+    for (int m = 0; m < 9; m++)
+        if (!ok[m]) {
+            float pad = lows > 0 ? -INFINITY : INFINITY;
+            lows--;
+            v[m] = make_float4(pad, pad, pad, pad);
+        }
+    float4 med = median9(v);
+    dst[q] = make_float4(med.x, med.y, med.z, __ldg(&crt[q]).w);
+}
+
+// A11: mip level 0 = (rgb, h) * v and (c_t, 1) * v
+__global__ void k_mip0(int W2, int H2, const float4 *__restrict__ med, const float *__restrict__ ct,
+                       const int32_t *__restrict__ nrays, float4 *m0, float2 *m1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    size_t q = (size_t)j * W2 + i;
+    float v = __ldg(&nrays[q]) > 0 ? 1.f : 0.f;
+    m0[q] = f4scale(v, __ldg(&med[q]));
+    m1[q] = make_float2(v * __ldg(&ct[q]), v);
+}
+
+// 2x2 box average (clamp-to-edge for odd sizes)
+__global__ void k_mip_down(int w, int h, const float4 *__restrict__ s0, const float2 *__restrict__ s1, int wn,
+                           int hn, float4 *d0, float2 *d1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= wn || j >= hn) return;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 b = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        int x = min(2 * i + (t & 1), w - 1), y = min(2 * j + (t >> 1), h - 1);
+        size_t q = (size_t)y * w + x;
+        a = f4add(a, __ldg(&s0[q]));
+        float2 c = __ldg(&s1[q]);
+        b.x += c.x; b.y += c.y;
+    }
+    d0[(size_t)j * wn + i] = f4scale(0.25f, a);
+    d1[(size_t)j * wn + i] = make_float2(0.25f * b.x, 0.25f * b.y);
+}
+
+struct Mips {
+    const float4 *m0[4];
+    const float2 *m1[4];
+    int w[4], h[4], L;
+};
+
+__device__ __forceinline__ void bilin_mip(const Mips &M, int l, float x, float y, float4 &a, float2 &b) {
+    float s = 1.f / (float)(1 << l);
+    float xl = (x + 0.5f) * s - 0.5f, yl = (y + 0.5f) * s - 0.5f;
+    int w = M.w[l], h = M.h[l];
+    float xf = floorf(xl), yf = floorf(yl);
+    float fx = xl - xf, fy = yl - yf;
+    int x0 = (int)xf, y0 = (int)yf;
+    int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
+    int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
+    float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+    size_t qa = (size_t)ya * w, qb = (size_t)yb * w;
+    a = f4fma(w11, __ldg(&M.m0[l][qb + xb]), f4fma(w01, __ldg(&M.m0[l][qb + xa]),
+              f4fma(w10, __ldg(&M.m0[l][qa + xb]), f4scale(w00, __ldg(&M.m0[l][qa + xa])))));
+    float2 c00 = __ldg(&M.m1[l][qa + xa]), c10 = __ldg(&M.m1[l][qa + xb]);
+    float2 c01 = __ldg(&M.m1[l][qb + xa]), c11 = __ldg(&M.m1[l][qb + xb]);
+    b = make_float2(w00 * c00.x + w10 * c10.x + w01 * c01.x + w11 * c11.x,
+                    w00 * c00.y + w10 * c10.y + w01 * c01.y + w11 * c11.y);
+}
+
+// A11: reconstruction
+__global__ void __launch_bounds__(256) k_recon(int W2, int H2, DevParams p, Mips M, const float4 *__restrict__ med,
+                                               const float *__restrict__ ct, const float *__restrict__ var_blur,
+                                               const int32_t *__restrict__ nrays, float4 *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    size_t q = (size_t)j * W2 + i;
+    if (__ldg(&nrays[q]) <= 0) { out[q] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+    float R = __ldg(&ct[q]);
+    float lod = fminf(fmaxf(R * p.lod_scale, 0.f), p.lod_max);
+    int l0 = (int)floorf(lod);
+    float t = lod - (float)l0;
+    if (l0 >= M.L - 1) { l0 = M.L - 1; t = 0.f; }
+    int l1 = min(l0 + 1, M.L - 1);
+    float4 num = make_float4(0.f, 0.f, 0.f, 0.f);
+    float den = 0.f;
+#pragma unroll 3
+    for (int k = 0; k < 81; k++) {
+        float3 u = c_ring81[k];
+        float dist = u.z * R;
+        float x = i + dist * u.x, y = j + dist * u.y;
+        float4 a0, a1;
+        float2 b0, b1;
+        bilin_mip(M, l0, x, y, a0, b0);
+        bilin_mip(M, l1, x, y, a1, b1);
+        float4 S = f4fma(t, a1, f4scale(1.f - t, a0));
+        float Sc = (1.f - t) * b0.x + t * b1.x, Sv = (1.f - t) * b0.y + t * b1.y;
+        float ri = Sv > 0.f ? Sc / Sv : 0.f;
+        float D = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
+        num = f4fma(D, S, num);
+        den += D * Sv;
+    }
+    float4 o = __ldg(&med[q]);
+    float b = fminf(fmaxf(__ldg(&var_blur[q]) * p.var_w_recon, 0.f), p.b_max);
+    float4 f = den > 0.f ? f4scale(1.f / den, num) : o;
+    out[q] = make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b));
+}
+
+// A12: composite per full-resolution pixel
+__global__ void __launch_bounds__(256) k_composite(DevCam cam, DevParams p, const float4 *__restrict__ color,
+                                                   const float *__restrict__ depth, const float4 *__restrict__ pp_med,
+                                                   const float4 *__restrict__ recon, const int32_t *__restrict__ nrays,
+                                                   float4 *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= cam.W || j >= cam.H) return;
+    size_t f = (size_t)j * cam.W + i;
+    float z = fminf(__ldg(&depth[f]), p.z_far);
+    float c = coc_of(cam, z);
+    float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
+    float xh = 0.5f * (i + 0.5f) - 0.5f, yh = 0.5f * (j + 0.5f) - 0.5f;
+    const int W2 = cam.W2, H2 = cam.H2;
+    float4 pp = bilinear4(pp_med, W2, H2, xh, yh);
+    float xf = floorf(xh), yf = floorf(yh);
+    float fx = xh - xf, fy = yh - yf;
+    int x0 = (int)xf, y0 = (int)yf;
+    float4 rt = make_float4(0.f, 0.f, 0.f, 0.f);
+    float cov = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        int dx = t & 1, dy = t >> 1;
+        int x = min(max(x0 + dx, 0), W2 - 1), y = min(max(y0 + dy, 0), H2 - 1);
+        size_t q = (size_t)y * W2 + x;
+        if (__ldg(&nrays[q]) <= 0) continue;
+        float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
+        rt = f4fma(w, __ldg(&recon[q]), rt);
+        cov += w;
+    }
+    float4 s = __ldg(&color[f]);
+    float bx = pp.x, by = pp.y, bz = pp.z;
+    if (cov > 0.f) {
+        float ic = 1.f / cov;
+        float rx = rt.x * ic, ry = rt.y * ic, rz = rt.z * ic, hh = rt.w * ic;
+        float tb;
+        if (c < 0.f) {
+            tb = pp.w;
+        } else {
+            float u = sat(hh / p.h_edge);
+            tb = u * u * (3.f - 2.f * u);
+        }
+        bx = lerpf(pp.x, lerpf(rx, pp.x, tb), cov);
+        by = lerpf(pp.y, lerpf(ry, pp.y, tb), cov);
+        bz = lerpf(pp.z, lerpf(rz, pp.z, tb), cov);
+    }
+    out[f] = make_float4(lerpf(bx, s.x, ws), lerpf(by, s.y, ws), lerpf(bz, s.z, ws), 1.f);
+}
+
+}  // namespace
+
+int recon_init_tables() { return upload_filter_tables(); }
+
+void launch_recon(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h, float4 *out,
+                  cudaStream_t st) {
+    dim3 b(32, 8), gh((h->W2 + 31) / 32, (h->H2 + 7) / 8);
+    k_median_rt<<<gh, b, 0, st>>>(h->W2, h->H2, h->crt, h->nrays, h->rt_med);
+    tmark(h, DOF_K_MEDIAN_RT, st);
+    k_mip0<<<gh, b, 0, st>>>(h->W2, h->H2, h->rt_med, h->ct, h->nrays, h->mip0[0], h->mip1[0]);
+    Mips M;
+    M.L = (int)ceilf(p.lod_max) + 1;
+    if (M.L > 4) M.L = 4;
+    if (M.L < 1) M.L = 1;
+    for (int l = 0; l < 4; l++) {
+        M.m0[l] = h->mip0[l]; M.m1[l] = h->mip1[l]; M.w[l] = h->mip_w[l]; M.h[l] = h->mip_h[l];
+    }
+    for (int l = 1; l < M.L; l++) {
+        dim3 gl((h->mip_w[l] + 31) / 32, (h->mip_h[l] + 7) / 8);
+        k_mip_down<<<gl, b, 0, st>>>(h->mip_w[l - 1], h->mip_h[l - 1], h->mip0[l - 1], h->mip1[l - 1], h->mip_w[l],
+                                     h->mip_h[l], h->mip0[l], h->mip1[l]);
+    }
+    tmark(h, DOF_K_MIPS, st);
+    k_recon<<<gh, b, 0, st>>>(h->W2, h->H2, p, M, h->rt_med, h->ct, h->var_blur[h->cur ^ 1], h->nrays, h->recon);
+    tmark(h, DOF_K_RECON, st);
+    dim3 gf((h->W + 31) / 32, (h->H + 7) / 8);
+    k_composite<<<gf, b, 0, st>>>(cam, p, reinterpret_cast<const float4 *>(g->color), g->depth, h->pp_med, h->recon,
+                                  h->nrays, out);
+    tmark(h, DOF_K_COMPOSITE, st);
+}

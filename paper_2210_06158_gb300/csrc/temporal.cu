@@ -1,0 +1,159 @@
+// Temporal accumulation and reprojection of the ray-traced layer (Section 3.2.3):
+// near field reprojected with the G-buffer surface, far field from the mean far-hit
+// position (3x3 neighbour fallback), an exponential moving average whose history
+// weight is the covered share of the bilinear footprint, merge on the hit ratio,
+// luminance moments and variance; then the 5x5 binomial blur of the variance.
+#include "dof_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ bool project_prev(const DevCam &c, float3 X, float &xh, float &yh) {
+    float3 rel = X - c.pO;
+    float zc = dot(rel, c.pF);
+    if (!(zc > 0.f)) return false;
+    float iz = c.Fpx / zc;
+    float x = c.halfW + dot(rel, c.pR) * iz;
+    float y = c.halfH - dot(rel, c.pU) * iz;
+    xh = 0.5f * x - 0.5f;
+    yh = 0.5f * y - 0.5f;
+    return fabsf(xh) < 1e7f && fabsf(yh) < 1e7f;
+}
+
+struct NearH { float4 a; float bn, m1, m2; };   // (An, h), Bn, mu1, mu2
+struct FarH { float4 a; float bf; };            // (Af, g), Bf
+
+// bilinear history fetch with dropped taps (outside, or without history)
+template <bool NEAR>
+__device__ __forceinline__ float fetch(const float4 *__restrict__ H0, const float4 *__restrict__ H1,
+                                       const float4 *__restrict__ H2, int W2, int H2n, float x, float y,
+                                       NearH &nh, FarH &fh) {
+    float xf = floorf(x), yf = floorf(y);
+    float fx = x - xf, fy = y - yf;
+    int x0 = (int)xf, y0 = (int)yf;
+    float wsum = 0.f;
+    nh.a = make_float4(0.f, 0.f, 0.f, 0.f); nh.bn = nh.m1 = nh.m2 = 0.f;
+    fh.a = nh.a; fh.bf = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        int dx = t & 1, dy = t >> 1;
+        int xi = x0 + dx, yi = y0 + dy;
+        if (xi < 0 || yi < 0 || xi >= W2 || yi >= H2n) continue;
+        size_t q = (size_t)yi * W2 + xi;
+        float4 h0 = __ldg(&H0[q]), h1 = __ldg(&H1[q]);
+        if (!(h0.w + h1.w > 0.f)) continue;
+        float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
+        float4 h2 = __ldg(&H2[q]);
+        if (NEAR) {
+            nh.a = f4fma(w, h0, nh.a);
+            nh.bn += w * h2.x; nh.m1 += w * h2.z; nh.m2 += w * h2.w;
+        } else {
+            fh.a = f4fma(w, h1, fh.a);
+            fh.bf += w * h2.y;
+        }
+        wsum += w;
+    }
+    return wsum;
+}
+
+__global__ void __launch_bounds__(256) k_accumulate(DevCam cam, DevParams p, const float *__restrict__ z_h,
+                                                    const float4 *__restrict__ rt, const int32_t *__restrict__ nrays,
+                                                    const float4 *__restrict__ hin, int has_hist, float4 *hout,
+                                                    float4 *crt, float *ct, float *var) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int W2 = cam.W2, H2 = cam.H2;
+    if (i >= W2 || j >= H2) return;
+    const size_t N = (size_t)W2 * H2, q = (size_t)j * W2 + i;
+    if (__ldg(&nrays[q]) <= 0) {
+        float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        hout[q] = zero; hout[N + q] = zero; hout[2 * N + q] = zero;
+        crt[q] = zero; ct[q] = 0.f; var[q] = 0.f;
+        return;
+    }
+    float4 rA = __ldg(&rt[q]), rB = __ldg(&rt[N + q]), rC = __ldg(&rt[2 * N + q]);
+    float h = rA.w, g = 1.f - h;
+    float L = lum709(rA.x + rB.x, rA.y + rB.y, rA.z + rB.z);
+    float3 dp = pixel_dir(cam, 2.f * i + 1.f, 2.f * j + 1.f);
+    float3 Xn = cam.O + (__ldg(&z_h[q]) / dot(dp, cam.F)) * dp;
+    float3 Xf;
+    if (rC.z > 0.f) {
+        float4 d = __ldg(&rt[3 * N + q]);
+        Xf = make_float3(d.x, d.y, d.z);
+    } else {
+        float3 acc = make_float3(0.f, 0.f, 0.f);
+        int cnt = 0;
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int x = i + dx, y = j + dy;
+                if (x < 0 || y < 0 || x >= W2 || y >= H2) continue;
+                size_t qn = (size_t)y * W2 + x;
+                if (__ldg(&nrays[qn]) > 0 && __ldg(&rt[2 * N + qn]).z > 0.f) {
+                    float4 d = __ldg(&rt[3 * N + qn]);
+                    acc = acc + make_float3(d.x, d.y, d.z);
+                    cnt++;
+                }
+            }
+        Xf = cnt ? (1.f / (float)cnt) * acc : Xn;
+    }
+    NearH nh;
+    FarH fh, fdummy;
+    NearH ndummy;
+    float Wn = 0.f, Wf = 0.f, xh, yh;
+    nh.a = make_float4(0.f, 0.f, 0.f, 0.f); nh.bn = nh.m1 = nh.m2 = 0.f;
+    fh.a = nh.a; fh.bf = 0.f;
+    if (has_hist) {
+        const float4 *H0 = hin, *H1 = hin + N, *H2p = hin + 2 * N;
+        if (project_prev(cam, Xn, xh, yh)) Wn = fetch<true>(H0, H1, H2p, W2, H2, xh, yh, nh, fdummy);
+        if (project_prev(cam, Xf, xh, yh)) Wf = fetch<false>(H0, H1, H2p, W2, H2, xh, yh, ndummy, fh);
+    }
+    const float a = cam.moved ? p.alpha_motion : p.alpha;
+    const float kn = 1.f - a * Wn, kf = 1.f - a * Wf;
+    float4 An = make_float4(a * nh.a.x + kn * rA.x, a * nh.a.y + kn * rA.y, a * nh.a.z + kn * rA.z,
+                            a * nh.a.w + kn * h);
+    float4 Af = make_float4(a * fh.a.x + kf * rB.x, a * fh.a.y + kf * rB.y, a * fh.a.z + kf * rB.z,
+                            a * fh.a.w + kf * g);
+    float Bn = a * nh.bn + kn * rC.x, Bf = a * fh.bf + kf * rC.y;
+    float m1 = a * nh.m1 + kn * L, m2 = a * nh.m2 + kn * L * L;
+    hout[q] = An;
+    hout[N + q] = Af;
+    hout[2 * N + q] = make_float4(Bn, Bf, m1, m2);
+    var[q] = fmaxf(0.f, m2 - m1 * m1);
+    if (!cam.moved) {
+        float r = 1.f / (An.w + Af.w);
+        crt[q] = make_float4((An.x + Af.x) * r, (An.y + Af.y) * r, (An.z + Af.z) * r, An.w * r);
+        ct[q] = (Bn + Bf) * r;
+    } else {
+        float rn = An.w > 0.f ? 1.f / An.w : 0.f, rf = Af.w > 0.f ? 1.f / Af.w : 0.f;
+        crt[q] = make_float4(h * An.x * rn + (1.f - h) * Af.x * rf, h * An.y * rn + (1.f - h) * Af.y * rf,
+                             h * An.z * rn + (1.f - h) * Af.z * rf, h);
+        ct[q] = h * Bn * rn + (1.f - h) * Bf * rf;
+    }
+}
+
+// 5x5 binomial blur of the variance, clamp-to-edge
+__global__ void k_var_blur(int W2, int H2, const float *__restrict__ v, float *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    const float b[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
+    float acc = 0.f;
+#pragma unroll
+    for (int dy = -2; dy <= 2; dy++) {
+        int y = min(max(j + dy, 0), H2 - 1);
+        float row = 0.f;
+#pragma unroll
+        for (int dx = -2; dx <= 2; dx++) row += b[dx + 2] * __ldg(&v[(size_t)y * W2 + min(max(i + dx, 0), W2 - 1)]);
+        acc += b[dy + 2] * row;
+    }
+    out[(size_t)j * W2 + i] = acc * (1.f / 256.f);
+}
+
+}  // namespace
+
+void launch_temporal(const DevCam &cam, const DevParams &p, DofHistory *h, cudaStream_t st) {
+    dim3 b(32, 8), g((h->W2 + 31) / 32, (h->H2 + 7) / 8);
+    int nxt = h->cur ^ 1;
+    k_accumulate<<<g, b, 0, st>>>(cam, p, h->z_h, h->rt, h->nrays, h->hist[h->cur], h->valid, h->hist[nxt], h->crt,
+                                  h->ct, h->var);
+    tmark(h, DOF_K_ACCUM, st);
+    k_var_blur<<<g, b, 0, st>>>(h->W2, h->H2, h->var, h->var_blur[nxt]);
+    tmark(h, DOF_K_VAR_BLUR, st);
+}

@@ -1,0 +1,389 @@
+// Ray side of libdof: G-buffer producer (pinhole primary visibility), ray mask with
+// warp-aggregated compaction into a ray queue (Section 3.2.1, Eq. 2-4), and the
+// persistent thin-lens ray kernel (Section 3.2.2): Philox lens samples, closest hit
+// through the LBVH, Lambert shading and the per-pixel near/far split.
+#include "dof_internal.cuh"
+
+namespace {
+
+constexpr int kStack = 64;   // >= the LBVH depth bound (checked at upload)
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC 2011); only the first two output words are used
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox2(unsigned long long c0, unsigned long long c1,
+                                        unsigned long long c2, unsigned long long c3,
+                                        unsigned long long k0, unsigned long long k1,
+                                        unsigned long long &o0, unsigned long long &o1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        unsigned long long hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        unsigned long long hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        unsigned long long y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+        c0 = y0; c1 = lo1; c2 = y2; c3 = lo0;
+    }
+    o0 = c0; o1 = c1;
+}
+
+// ---------------------------------------------------------------------------
+// ray / box / triangle
+// ---------------------------------------------------------------------------
+struct Ray {
+    float3 o, d, inv;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
+    Ray r;
+    r.o = o; r.d = d;
+    auto safe = [](float x) { return fabsf(x) < 1e-30f ? copysignf(1e-30f, x) : x; };
+    r.inv = make_float3(1.f / safe(d.x), 1.f / safe(d.y), 1.f / safe(d.z));
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (comp(d, kz) < 0.f) { int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    float dz = comp(d, kz);
+    r.Sx = comp(d, kx) / dz;
+    r.Sy = comp(d, ky) / dz;
+    r.Sz = 1.f / dz;
+    return r;
+}
+
+// slab test, conservative by a few ulps so rounding never culls a hit on the surface
+__device__ __forceinline__ bool box_hit(const Ray &r, float3 lo, float3 hi, float tbest, float &tent) {
+    float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
+    float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
+    float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tbest));
+    tent = tmin;
+    return tmin <= tmax * 1.0000005f;
+}
+
+// Watertight ray/triangle test (Woop, Benthin and Wald, JCGT 2013): shear the
+// vertices into ray space, evaluate the three edge functions (without FMA
+// contraction, so a shared edge evaluates to exact negatives), double precision only
+// when an edge function is exactly zero.  Returns t > 0 or -1.
+__device__ __forceinline__ float tri_hit(const Ray &r, float4 v0, float4 v1, float4 v2) {
+    float3 A = make_float3(v0.x - r.o.x, v0.y - r.o.y, v0.z - r.o.z);
+    float3 B = make_float3(v1.x - r.o.x, v1.y - r.o.y, v1.z - r.o.z);
+    float3 C = make_float3(v2.x - r.o.x, v2.y - r.o.y, v2.z - r.o.z);
+    float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
+    float Ax = __fsub_rn(comp(A, r.kx), __fmul_rn(r.Sx, Akz));
+    float Ay = __fsub_rn(comp(A, r.ky), __fmul_rn(r.Sy, Akz));
+    float Bx = __fsub_rn(comp(B, r.kx), __fmul_rn(r.Sx, Bkz));
+    float By = __fsub_rn(comp(B, r.ky), __fmul_rn(r.Sy, Bkz));
+    float Cx = __fsub_rn(comp(C, r.kx), __fmul_rn(r.Sx, Ckz));
+    float Cy = __fsub_rn(comp(C, r.ky), __fmul_rn(r.Sy, Ckz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.f || V == 0.f || W == 0.f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return -1.f;
+    float det = U + V + W;
+    if (det == 0.f) return -1.f;
+    float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+    float t = T / det;
+    return t > 0.f ? t : -1.f;
+}
+
+struct HitRec {
+    float t;
+    int prim;   // original triangle id, -1 = miss
+    int k;      // sorted index
+};
+
+// closest hit = lexicographic min of (t, prim id); boxes with entry == best are kept.
+// A reference outside the tree, a full stack or more steps than a valid tree can take
+// set the status word and end the query (no fault, no endless loop).
+__device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status) {
+    HitRec h{INFINITY, -1, -1};
+    if (sc.n_tris <= 0) return h;
+    int stack[kStack];
+    int sp = 0;
+    int node = sc.n_tris >= 2 ? 0 : ~0;
+    const int n_nodes = sc.n_tris - 1;
+    const long long max_steps = 4ll * sc.n_tris + 64;
+    for (long long steps = 0;; steps++) {
+        if (steps > max_steps || node >= n_nodes || (node < 0 && ~node >= sc.n_tris)) {
+            atomicOr(status, 2u);
+            break;
+        }
+        if (node >= 0) {
+            const float4 *np = reinterpret_cast<const float4 *>(sc.nodes + node);
+            float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+            int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
+            float t0, t1;
+            bool h0 = box_hit(r, make_float3(a.x, a.y, a.z), make_float3(a.w, b.x, b.y), h.t, t0);
+            bool h1 = box_hit(r, make_float3(b.z, b.w, c.x), make_float3(c.y, c.z, c.w), h.t, t1);
+            if (h0 && h1) {
+                int nearc = t0 <= t1 ? ref.x : ref.y, farc = t0 <= t1 ? ref.y : ref.x;
+                if (sp < kStack) stack[sp++] = farc;
+                else atomicOr(status, 1u);
+                node = nearc;
+                continue;
+            }
+            if (h0) { node = ref.x; continue; }
+            if (h1) { node = ref.y; continue; }
+        } else {
+            int k = ~node;
+            const float4 *tp = sc.tris + 3 * (size_t)k;
+            float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+            float t = tri_hit(r, v0, v1, v2);
+            if (t > 0.f) {
+                int prim = __float_as_int(v0.w);
+                if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    return h;
+}
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+    return h;
+}
+
+// colour of a hit: per-triangle hash albedo, Lambert + ambient under one directional
+// light (material 1: emitter); also the face normal turned towards the ray
+__device__ __forceinline__ float3 shade(const DevParams &p, const SceneDev &sc, const HitRec &h, float3 dir,
+                                        float3 &n) {
+    const float4 *tp = sc.tris + 3 * (size_t)h.k;
+    float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+    n = normalize(cross(make_float3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z),
+                        make_float3(v2.x - v0.x, v2.y - v0.y, v2.z - v0.z)));
+    if (dot(n, dir) > 0.f) n = -1.f * n;
+    uint32_t base = fmix32(p.albedo_seed);
+    float alb[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        uint32_t hh = fmix32(base ^ (uint32_t)(3 * h.prim + c));
+        alb[c] = 0.1f + 0.8f * ((float)(hh >> 8) * 5.9604644775390625e-8f);
+    }
+    if (__float_as_int(v2.w) == 1) return make_float3(p.emit * alb[0], p.emit * alb[1], p.emit * alb[2]);
+    float lam = fmaxf(0.f, -dot(n, p.light));
+    float k = p.k_a + p.k_d * lam;
+    return make_float3(alb[0] * k, alb[1] * k, alb[2] * k);
+}
+
+// ---------------------------------------------------------------------------
+// A0: G-buffer producer
+// ---------------------------------------------------------------------------
+__global__ void k_primary(DevCam cam, DevParams p, SceneDev sc, float4 *color, float *depth, float4 *normal,
+                          int32_t *prim, uint32_t *status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= cam.W || j >= cam.H) return;
+    size_t q = (size_t)j * cam.W + i;
+    float3 d = pixel_dir(cam, i + 0.5f, j + 0.5f);
+    Ray r = make_ray(cam.O, d);
+    HitRec h = closest_hit(sc, r, status);
+    if (prim) prim[q] = h.prim;
+    if (h.prim < 0) {
+        color[q] = make_float4(p.sky.x, p.sky.y, p.sky.z, 1.f);
+        depth[q] = INFINITY;
+        normal[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    float3 n;
+    float3 col = shade(p, sc, h, d, n);
+    color[q] = make_float4(col.x, col.y, col.z, 1.f);
+    depth[q] = h.t * dot(d, cam.F);
+    normal[q] = make_float4(n.x, n.y, n.z, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// A6: edge measure for the adaptive ray count (Eq. 2, Eq. 3)
+// ---------------------------------------------------------------------------
+// 5x5 binomial blur of (z, n.xyz) packed as float4, clamp-to-edge
+__global__ void k_blur_zn(int W2, int H2, const float *z_h, const float4 *n_h, float4 *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    const float b[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int dy = -2; dy <= 2; dy++) {
+        int y = min(max(j + dy, 0), H2 - 1);
+        for (int dx = -2; dx <= 2; dx++) {
+            int x = min(max(i + dx, 0), W2 - 1);
+            size_t q = (size_t)y * W2 + x;
+            float w = b[dx + 2] * b[dy + 2];
+            float4 n = __ldg(&n_h[q]);
+            acc = f4fma(w, make_float4(__ldg(&z_h[q]), n.x, n.y, n.z), acc);
+        }
+    }
+    out[(size_t)j * W2 + i] = f4scale(1.f / 256.f, acc);
+}
+
+// 5x5 Sobel ([-1 -2 0 2 1] x [1 4 6 4 1] / 128) -> x_n (Eq. 2, 3) and x_f (Eq. 4)
+__global__ void k_edges(int W2, int H2, const float4 *zn, const float *var_prev, int has_prev, DevParams p,
+                        float *xn, float *xf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= W2 || j >= H2) return;
+    const float sm[5] = {1.f, 4.f, 6.f, 4.f, 1.f}, dv[5] = {-1.f, -2.f, 0.f, 2.f, 1.f};
+    float4 gx = make_float4(0.f, 0.f, 0.f, 0.f), gy = gx;
+    for (int dy = -2; dy <= 2; dy++) {
+        int y = min(max(j + dy, 0), H2 - 1);
+        for (int dx = -2; dx <= 2; dx++) {
+            int x = min(max(i + dx, 0), W2 - 1);
+            float4 v = __ldg(&zn[(size_t)y * W2 + x]);
+            gx = f4fma(dv[dx + 2] * sm[dy + 2], v, gx);
+            gy = f4fma(sm[dx + 2] * dv[dy + 2], v, gy);
+        }
+    }
+    gx = f4scale(1.f / 128.f, gx);
+    gy = f4scale(1.f / 128.f, gy);
+    size_t q = (size_t)j * W2 + i;
+    float zc = __ldg(&zn[q]).x;
+    float dd = sqrtf(gx.x * gx.x + gy.x * gy.x) / zc;
+    float dn = sqrtf(gx.y * gx.y + gx.z * gx.z + gx.w * gx.w + gy.y * gy.y + gy.z * gy.z + gy.w * gy.w);
+    float x = (dd + dn) * p.s;
+    float x_n = sat(1.f - 1.f / (x + 1.f));
+    float s2 = has_prev ? __ldg(&var_prev[q]) : 0.f;
+    xn[q] = x_n;
+    xf[q] = sat(x_n + s2 * p.var_w_mask) * p.m;
+}
+
+// ---------------------------------------------------------------------------
+// A6: mask, ray count, warp-aggregated compaction of masked pixels
+// ---------------------------------------------------------------------------
+__global__ void k_mask_compact(int W2, int H2, DevParams p, const float2 *tiles_dil, const float *xf,
+                               int32_t *nrays, uint32_t *queue, uint32_t *counters) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    bool inside = i < W2 && j < H2;
+    int n = 0;
+    uint32_t q = 0;
+    if (inside) {
+        q = (uint32_t)j * W2 + i;
+        float near_max = __ldg(&tiles_dil[(j >> 3) * p.tiles_w + (i >> 3)]).x;
+        if (near_max >= p.mask_near_hpx) {
+            if (p.ray_mode == 0) n = p.spp;
+            else n = (int)fminf(fmaxf(ceilf(__ldg(&xf[q])), 1.f), p.m);
+        }
+        nrays[q] = n;
+    }
+    unsigned lane = threadIdx.x + threadIdx.y * blockDim.x;
+    lane &= 31;
+    unsigned ball = __ballot_sync(0xffffffffu, n > 0);
+    int rays = n;
+    for (int o = 16; o > 0; o >>= 1) rays += __shfl_xor_sync(0xffffffffu, rays, o);
+    uint32_t base = 0;
+    if (lane == 0 && ball) {
+        base = atomicAdd(&counters[0], (uint32_t)__popc(ball));
+        atomicAdd(&counters[1], (uint32_t)rays);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (n > 0) queue[base + __popc(ball & ((1u << lane) - 1u))] = q;
+}
+
+// ---------------------------------------------------------------------------
+// A8: persistent thin-lens ray kernel (one lane per masked pixel, its rays in
+// sample order; warps fetch 32 queue entries at a time)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_trace(DevCam cam, DevParams p, SceneDev sc, const uint32_t *queue,
+                                               const int32_t *nrays, uint32_t *counters, float4 *rt,
+                                               int32_t *ray_prim, int max_rays) {
+    const unsigned lane = threadIdx.x & 31;
+    const uint32_t count = *((volatile uint32_t *)&counters[0]);
+    const size_t N = (size_t)cam.W2 * cam.H2;
+    const float inv_sqrt2 = 0.70710678118654752f;
+    while (true) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&counters[2], 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= count) break;
+        uint32_t e = base + lane;
+        if (e >= count) continue;   // base < count is warp-uniform: every lane reaches the next fetch
+        uint32_t q = queue[e];
+        int n = nrays[q];
+        int i = (int)(q % (uint32_t)cam.W2), j = (int)(q / (uint32_t)cam.W2);
+        float3 dp = pixel_dir(cam, 2.f * i + 1.f, 2.f * j + 1.f);
+        float tf = cam.d / dot(dp, cam.F);
+        float3 Pf = cam.O + tf * dp;
+        float Sw = 0.f, Bn = 0.f, Bf = 0.f, Fw = 0.f;
+        float3 An = make_float3(0.f, 0.f, 0.f), Af = An, Pfar = An;
+        for (int s = 0; s < n; s++) {
+            unsigned long long x0, x1;
+            philox2(q, (unsigned long long)s, cam.frame, 0ull, p.seed, p.session, x0, x1);
+            float u1 = (float)(x0 >> 40) * 5.9604644775390625e-8f;
+            float u2 = (float)(x1 >> 40) * 5.9604644775390625e-8f;
+            float rr = cam.lens_r * sqrtf(u1), sn, cs;
+            sincospif(2.f * u2, &sn, &cs);
+            float lx = rr * cs, ly = rr * sn;
+            float3 L = cam.O + lx * cam.R + ly * cam.U;
+            float3 dir = normalize(Pf - L);
+            Ray r = make_ray(L, dir);
+            HitRec h = closest_hit(sc, r, &counters[3]);
+            float3 col;
+            float z;
+            if (h.prim >= 0) {
+                float3 nrm;
+                col = shade(p, sc, h, dir, nrm);
+                z = fminf(h.t * dot(dir, cam.F), p.z_far);
+            } else {
+                col = p.sky;
+                z = p.z_far;
+            }
+            float c = coc_of(cam, z);
+            float rho = fabsf(fminf(fmaxf(0.25f * c, -p.rmax_hpx), p.rmax_hpx));
+            float w = sat(-c * inv_sqrt2);
+            if (ray_prim && s < max_rays) ray_prim[(size_t)q * max_rays + s] = h.prim;
+            Sw += w;
+            An = An + w * col;
+            Af = Af + (1.f - w) * col;
+            Bn += w * rho;
+            Bf += (1.f - w) * rho;
+            if (h.prim >= 0) {
+                Pfar = Pfar + (1.f - w) * (L + h.t * dir);
+                Fw += 1.f - w;
+            }
+        }
+        float inv_n = 1.f / (float)n;
+        float invF = Fw > 0.f ? 1.f / Fw : 0.f;
+        rt[q] = make_float4(An.x * inv_n, An.y * inv_n, An.z * inv_n, Sw * inv_n);
+        rt[N + q] = make_float4(Af.x * inv_n, Af.y * inv_n, Af.z * inv_n, (float)n);
+        rt[2 * N + q] = make_float4(Bn * inv_n, Bf * inv_n, Fw, 0.f);
+        rt[3 * N + q] = make_float4(Pfar.x * invF, Pfar.y * invF, Pfar.z * invF, 0.f);
+    }
+}
+
+}  // namespace
+
+void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *color, float *depth,
+                    float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st) {
+    dim3 b(16, 8), g((cam.W + 15) / 16, (cam.H + 7) / 8);
+    k_primary<<<g, b, 0, st>>>(cam, p, sc, color, depth, normal, prim, status);
+}
+
+void launch_mask(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h, cudaStream_t st) {
+    (void)g;
+    dim3 b(32, 8), gr((h->W2 + 31) / 32, (h->H2 + 7) / 8);
+    if (p.ray_mode == 1) {
+        float4 *zn = h->crt;   // scratch: crt is only written later, by the accumulation
+        k_blur_zn<<<gr, b, 0, st>>>(h->W2, h->H2, h->z_h, h->n_h, zn);
+        k_edges<<<gr, b, 0, st>>>(h->W2, h->H2, zn, h->var_blur[h->cur], h->valid, p, h->xn, h->xf);
+    }
+    tmark(h, DOF_K_EDGES, st);
+    k_mask_compact<<<gr, b, 0, st>>>(h->W2, h->H2, p, h->tiles_dil, h->xf, h->nrays, h->queue, h->counters);
+    tmark(h, DOF_K_MASK, st);
+}
+
+void launch_trace(const DevCam &cam, const DevParams &p, SceneDev sc, DofHistory *h, int sm_count,
+                  cudaStream_t st) {
+    int blocks = sm_count * 8;
+    k_trace<<<blocks, 128, 0, st>>>(cam, p, sc, h->queue, h->nrays, h->counters, h->rt,
+                                    (h->flags & DOF_HIST_RECORD_RAYS) ? h->ray_prim : nullptr, (int)h->max_rays);
+    tmark(h, DOF_K_TRACE, st);
+}

@@ -1,0 +1,323 @@
+"""Thin Python binding of libdof (include/dof.h): ctypes marshalling only.
+
+Every step of the pass runs in the CUDA library; torch is used for device memory
+(tensors whose data pointers are handed to the library) and for the current CUDA
+stream.  There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import threading
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+_LIB_PATH = _PKG / "_lib" / "libdof.so"
+_lib = None
+_lock = threading.Lock()
+
+DOF_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "BUDGET", -4: "CUDA", -5: "TIMEOUT",
+          -6: "DEVICE_CHECK", -7: "MISMATCH"}
+DOF_HIST_RECORD_RAYS = 1
+DOF_HIST_TIMING = 2
+KERNELS = ["k_downscale_tiles", "k_tile_dilate", "k_prefilter", "k_main_filter", "k_median_pp", "k_edges",
+           "k_mask_compact", "k_trace", "k_accumulate", "k_var_blur", "k_median_rt", "k_mips", "k_recon",
+           "k_composite"]
+BUF = dict(PP_IN=0, Z_H=1, TILES=2, TILES_DIL=3, PRE=4, MAIN=5, PP_MED=6, XN=7, XF=8,
+           NRAYS=9, RAY_PRIM=10, RT=11, CRT=12, CT=13, VAR=14, VAR_BLUR=15, RT_MED=16,
+           RECON=17, HIST=18)
+
+
+class DofError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdof error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_f3 = C.c_float * 3
+
+
+class DofCamera(C.Structure):
+    _fields_ = [("f_m", C.c_float), ("f_number", C.c_float), ("focus_m", C.c_float),
+                ("sensor_w_m", C.c_float), ("pos", _f3), ("right", _f3), ("up", _f3), ("fwd", _f3),
+                ("prev_pos", _f3), ("prev_right", _f3), ("prev_up", _f3), ("prev_fwd", _f3),
+                ("frame_index", C.c_uint32)]
+
+
+class DofParams(C.Structure):
+    _fields_ = [("s", C.c_float), ("var_w_mask", C.c_float), ("m", C.c_uint32), ("spp", C.c_uint32),
+                ("ray_mode", C.c_uint32), ("depth_range_m", C.c_float), ("alpha", C.c_float),
+                ("alpha_motion", C.c_float), ("var_w_recon", C.c_float), ("b_max", C.c_float),
+                ("h_edge", C.c_float), ("lod_scale", C.c_float), ("lod_max", C.c_float),
+                ("max_coc_px", C.c_float), ("zof_ramp_px", C.c_float), ("cover_ramp_px", C.c_float),
+                ("bright_lum", C.c_float), ("bright_ramp", C.c_float), ("mask_near_hpx", C.c_float),
+                ("z_far_m", C.c_float), ("tile", C.c_uint32), ("albedo_seed", C.c_uint32),
+                ("seed", C.c_uint64), ("session", C.c_uint64), ("light_dir", _f3), ("k_a", C.c_float),
+                ("k_d", C.c_float), ("sky", _f3), ("emit", C.c_float)]
+
+
+class DofGBuffer(C.Structure):
+    _fields_ = [("color", C.c_void_p), ("depth", C.c_void_p), ("normal", C.c_void_p),
+                ("width", C.c_uint32), ("height", C.c_uint32), ("fmt", C.c_uint32)]
+
+
+class DofSceneInfo(C.Structure):
+    _fields_ = [("n_tris", C.c_uint32), ("n_nodes", C.c_uint32), ("depth", C.c_uint32),
+                ("stack_limit", C.c_uint32), ("device_bytes", C.c_uint64),
+                ("bounds_lo", _f3), ("bounds_hi", _f3)]
+
+
+class DofFrameStats(C.Structure):
+    _fields_ = [("frames", C.c_uint64), ("masked_pixels", C.c_uint32), ("rays", C.c_uint32),
+                ("device_status", C.c_int32), ("pad", C.c_uint32)]
+
+
+# every symbol the header declares, with its signature
+_SIGS = {
+    "dof_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
+    "dof_ctx_destroy": (None, [C.c_void_p]),
+    "dof_ctx_bytes_in_use": (C.c_size_t, [C.c_void_p]),
+    "dof_params_default": (None, [C.POINTER(DofParams)]),
+    "dof_last_error": (C.c_char_p, []),
+    "dof_scene_upload": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint32,
+                                   C.c_void_p, C.POINTER(C.c_void_p)]),
+    "dof_scene_destroy": (None, [C.c_void_p]),
+    "dof_scene_info": (C.c_int, [C.c_void_p, C.POINTER(DofSceneInfo)]),
+    "dof_gbuffer": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofCamera), C.POINTER(DofParams), C.c_uint32,
+                              C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dof_history_create": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                     C.POINTER(C.c_void_p)]),
+    "dof_history_destroy": (None, [C.c_void_p]),
+    "dof_history_reset": (C.c_int, [C.c_void_p]),
+    "dof_frame": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofGBuffer), C.POINTER(DofCamera),
+                            C.POINTER(DofParams), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dof_frame_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofFrameStats)]),
+    "dof_debug_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    "dof_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
+}
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libdof.so (built in-tree by `_build.build()`); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _LIB_PATH.exists():
+                raise RuntimeError(f"libdof.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+            L = C.CDLL(str(_LIB_PATH))
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != DOF_OK:
+        raise DofError(rc, lib().dof_last_error().decode())
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# structures from the shared input generators
+# ---------------------------------------------------------------------------
+
+def camera_struct(cam) -> DofCamera:
+    c = DofCamera()
+    c.f_m, c.f_number, c.focus_m, c.sensor_w_m = cam.f_m, cam.f_number, cam.focus_m, cam.sensor_w_m
+    for name in ("pos", "right", "up", "fwd", "prev_pos", "prev_right", "prev_up", "prev_fwd"):
+        setattr(c, name, _f3(*[float(x) for x in np.asarray(getattr(cam, name), dtype=np.float32)]))
+    c.frame_index = int(cam.frame_index)
+    return c
+
+
+def params_struct(p: dict) -> DofParams:
+    o = DofParams()
+    lib().dof_params_default(C.byref(o))
+    for k in ("s", "var_w_mask", "depth_range_m", "alpha", "alpha_motion", "var_w_recon", "b_max", "h_edge",
+              "lod_scale", "lod_max", "max_coc_px", "zof_ramp_px", "cover_ramp_px", "bright_lum",
+              "bright_ramp", "mask_near_hpx", "z_far_m", "k_a", "k_d", "emit"):
+        if k in p:
+            setattr(o, k, float(p[k]))
+    for k in ("m", "spp", "ray_mode", "tile", "seed", "session"):
+        if k in p:
+            setattr(o, k, int(p[k]))
+    if "albedo_seed" in p:
+        o.albedo_seed = int(p["albedo_seed"]) & 0xFFFFFFFF
+    if "light_dir" in p:
+        o.light_dir = _f3(*[float(x) for x in p["light_dir"]])
+    if "sky" in p:
+        o.sky = _f3(*[float(x) for x in p["sky"]])
+    return o
+
+
+# ---------------------------------------------------------------------------
+# objects
+# ---------------------------------------------------------------------------
+
+class Context:
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self.ptr = C.c_void_p()
+        _check(lib().dof_ctx_create(int(device), int(mem_budget_bytes), C.byref(self.ptr)))
+        self.device = device
+
+    def close(self):
+        if self.ptr:
+            lib().dof_ctx_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def bytes_in_use(self) -> int:
+        return int(lib().dof_ctx_bytes_in_use(self.ptr))
+
+
+class Scene:
+    """Device scene + LBVH.  `scene` is a synth.Scene (host arrays, copied)."""
+
+    def __init__(self, ctx: Context, scene, stream=None):
+        self.ctx = ctx
+        v = np.ascontiguousarray(scene.verts, dtype=np.float32)
+        t = np.ascontiguousarray(scene.tris, dtype=np.uint32)
+        m = np.ascontiguousarray(scene.mat, dtype=np.uint32)
+        self.ptr = C.c_void_p()
+        _check(lib().dof_scene_upload(ctx.ptr, v.ctypes.data_as(C.c_void_p), v.shape[0],
+                                      t.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                                      t.shape[0], _stream_ptr(stream), C.byref(self.ptr)))
+
+    def info(self) -> DofSceneInfo:
+        i = DofSceneInfo()
+        _check(lib().dof_scene_info(self.ptr, C.byref(i)))
+        return i
+
+    def close(self):
+        if self.ptr:
+            lib().dof_scene_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class History:
+    def __init__(self, ctx: Context, width: int, height: int, max_rays: int = 1, record_rays: bool = False,
+                 timing: bool = False):
+        self.ctx = ctx
+        self.width, self.height, self.max_rays = width, height, max_rays
+        self.ptr = C.c_void_p()
+        flags = (DOF_HIST_RECORD_RAYS if record_rays else 0) | (DOF_HIST_TIMING if timing else 0)
+        _check(lib().dof_history_create(ctx.ptr, width, height, max_rays, flags, C.byref(self.ptr)))
+
+    def reset(self):
+        _check(lib().dof_history_reset(self.ptr))
+
+    def stats(self, stream=None) -> DofFrameStats:
+        s = DofFrameStats()
+        _check(lib().dof_frame_stats(self.ptr, _stream_ptr(stream), C.byref(s)))
+        return s
+
+    def kernel_times(self, stream=None):
+        """(dict kernel -> summed ms, frames) since the previous call (DOF_HIST_TIMING)."""
+        ms = (C.c_float * len(KERNELS))()
+        n = C.c_uint32()
+        _check(lib().dof_kernel_times(self.ptr, _stream_ptr(stream), ms, C.byref(n)))
+        return {k: float(ms[i]) for i, k in enumerate(KERNELS)}, int(n.value)
+
+    def buffer(self, name: str):
+        """(device pointer, bytes) of an intermediate buffer of the last frame."""
+        p, n = C.c_void_p(), C.c_size_t()
+        _check(lib().dof_debug_buffer(self.ptr, BUF[name], C.byref(p), C.byref(n)))
+        return p.value, n.value
+
+    def read(self, name: str, dtype=np.float32, shape=None):
+        """Copy an intermediate buffer to a numpy array (synchronous)."""
+        import torch
+        p, n = self.buffer(name)
+        out = torch.empty(n, dtype=torch.uint8)
+        if n:
+            torch.cuda.synchronize()
+            cudart = torch.cuda.cudart()
+            rc = cudart.cudaMemcpy(out.data_ptr(), p, n, 2)   # device -> host
+            if int(rc) != 0:
+                raise RuntimeError(f"cudaMemcpy failed ({rc})")
+        a = out.numpy().view(dtype)
+        return a.reshape(shape) if shape is not None else a
+
+    def close(self):
+        if self.ptr:
+            lib().dof_history_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gbuffer(ctx: Context, scene: Scene, cam, params: dict, width: int, height: int, out=None, stream=None):
+    """G-buffer producer on the device; returns dict of torch tensors (color, depth,
+    normal, prim)."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    if out is None:
+        out = dict(color=torch.empty((height, width, 4), dtype=torch.float32, device=dev),
+                   depth=torch.empty((height, width), dtype=torch.float32, device=dev),
+                   normal=torch.empty((height, width, 4), dtype=torch.float32, device=dev),
+                   prim=torch.empty((height, width), dtype=torch.int32, device=dev))
+    c, p = camera_struct(cam), params_struct(params)
+    _check(lib().dof_gbuffer(ctx.ptr, scene.ptr, C.byref(c), C.byref(p), width, height, _ptr(out["color"]),
+                             _ptr(out["depth"]), _ptr(out["normal"]), _ptr(out.get("prim")), _stream_ptr(stream)))
+    return out
+
+
+def gbuffer_struct(color, depth, normal=None) -> DofGBuffer:
+    g = DofGBuffer()
+    g.color = color.data_ptr()
+    g.depth = depth.data_ptr()
+    g.normal = normal.data_ptr() if normal is not None else None
+    g.height, g.width = int(depth.shape[0]), int(depth.shape[1])
+    g.fmt = 0
+    return g
+
+
+def frame(ctx: Context, scene: Scene, gbuf: dict, cam, params, hist: History, out=None, stream=None,
+          cam_struct: DofCamera | None = None, params_s: DofParams | None = None):
+    """Run one frame of the pass.  gbuf: dict of device tensors (color HxWx4, depth HxW,
+    normal HxWx4); returns the output tensor (HxWx4 float32)."""
+    import torch
+    H, W = gbuf["depth"].shape
+    if out is None:
+        out = torch.empty((H, W, 4), dtype=torch.float32, device=gbuf["depth"].device)
+    g = gbuffer_struct(gbuf["color"], gbuf["depth"], gbuf.get("normal"))
+    c = cam_struct if cam_struct is not None else camera_struct(cam)
+    p = params_s if params_s is not None else params_struct(params)
+    _check(lib().dof_frame(ctx.ptr, scene.ptr, C.byref(g), C.byref(c), C.byref(p), hist.ptr, _ptr(out),
+                           _stream_ptr(stream)))
+    return out

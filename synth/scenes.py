@@ -158,6 +158,9 @@ class _Builder:
         self.parts[name] = self.parts.get(name, 0) + len(tris)
 
     def build(self) -> Scene:
+        if not self.v:
+            return Scene(verts=np.zeros((0, 3), np.float32), tris=np.zeros((0, 3), np.uint32),
+                         mat=np.zeros(0, np.uint32), seed=self.seed, parts={})
         return Scene(verts=np.concatenate(self.v).astype(np.float32),
                      tris=np.concatenate(self.t).astype(np.uint32),
                      mat=np.concatenate(self.m), seed=self.seed, parts=self.parts)

@@ -1,0 +1,172 @@
+"""Helpers of the GPU parity tests: run the CUDA path (through the C ABI) and the FP64
+oracle on the same seeded inputs and compare them element by element.
+
+Tolerance accounting
+  * hit ids: bit-exact, except rays the oracle classifies as floating-point near
+    ties (an edge graze or equal depths within 1e-5 relative); every mismatch must
+    classify, and the fraction is reported (target <= 1e-4 of rays);
+  * images: max |d| <= 2e-3 and PSNR >= 50 dB in linear RGB; the max excludes the
+    taint cone of mismatched rays (the pixel, the reconstruction footprint, the
+    median and the upsampling, carried through the history by the motion), whose
+    share is reported;
+  * intermediates: tighter bounds from the FP32 arithmetic (see each test).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.ndimage as ndi
+
+import oracle
+
+SQRT2 = math.sqrt(2.0)
+
+
+def psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+class GpuRunner:
+    """One session on the CUDA path: scene + history, frames through dof_frame."""
+
+    def __init__(self, workload, params=None, max_rays=None, record_rays=True, ctx=None):
+        import torch
+        from paper_2210_06158_gb300 import dof
+        self.dof, self.torch = dof, torch
+        self.w = workload
+        self.params = dict(params or workload.params)
+        mr = max_rays or oracle.max_rays(self.params)
+        self.ctx = ctx or dof.Context(0)
+        self.scene = dof.Scene(self.ctx, workload.scene)
+        self.hist = dof.History(self.ctx, workload.W, workload.H, max_rays=mr, record_rays=record_rays)
+        self.max_rays = mr
+        self.dev = torch.device("cuda", 0)
+
+    def frame(self, cam, gb32, read=True):
+        torch = self.torch
+        g = {k: torch.from_numpy(np.ascontiguousarray(v)).to(self.dev) for k, v in gb32.items()}
+        out = self.dof.frame(self.ctx, self.scene, g, cam, self.params, self.hist)
+        torch.cuda.synchronize()
+        res = dict(out=out.cpu().numpy())
+        if read:
+            res.update(self.read_all())
+        res["stats"] = self.hist.stats()
+        return res
+
+    def read_all(self):
+        H2, W2 = self.w.H // 2, self.w.W // 2
+        N = H2 * W2
+        T = int(self.params["tile"])
+        TH, TW = -(-H2 // T), -(-W2 // T)
+        h = self.hist
+        r = {}
+        r["pp_in"] = h.read("PP_IN", shape=(H2, W2, 4))
+        r["z_h"] = h.read("Z_H", shape=(H2, W2))
+        r["tile_raw"] = h.read("TILES", shape=(TH, TW, 2))
+        r["tile_dil"] = h.read("TILES_DIL", shape=(TH, TW, 2))
+        r["pre"] = h.read("PRE", shape=(H2, W2, 4))
+        r["main_out"] = h.read("MAIN", shape=(H2, W2, 4))
+        r["pp_med"] = h.read("PP_MED", shape=(H2, W2, 4))
+        r["xn"] = h.read("XN", shape=(H2, W2))
+        r["xf"] = h.read("XF", shape=(H2, W2))
+        r["nrays"] = h.read("NRAYS", np.int32, shape=(H2, W2))
+        rp = h.read("RAY_PRIM", np.int32)
+        r["ray_prim"] = rp.reshape(H2, W2, self.max_rays) if rp.size else None
+        rt = h.read("RT", shape=(4, H2, W2, 4))
+        o = np.zeros((H2, W2, 14), np.float32)
+        o[..., 0] = rt[1, ..., 3]
+        o[..., 1] = rt[0, ..., 3]
+        o[..., 2:5] = rt[0, ..., :3]
+        o[..., 5:8] = rt[1, ..., :3]
+        o[..., 8] = rt[2, ..., 0]
+        o[..., 9] = rt[2, ..., 1]
+        o[..., 10:13] = rt[3, ..., :3]
+        o[..., 13] = rt[2, ..., 2]
+        r["rt"] = o
+        r["crt"] = h.read("CRT", shape=(H2, W2, 4))
+        r["ct"] = h.read("CT", shape=(H2, W2))
+        r["var"] = h.read("VAR", shape=(H2, W2))
+        r["var_blur"] = h.read("VAR_BLUR", shape=(H2, W2))
+        r["rt_med"] = h.read("RT_MED", shape=(H2, W2, 4))
+        r["recon"] = h.read("RECON", shape=(H2, W2, 4))
+        hh = h.read("HIST", shape=(3, H2, W2, 4))
+        hist = np.zeros((H2, W2, 12), np.float32)
+        hist[..., 0:3] = hh[0, ..., :3]
+        hist[..., 3:6] = hh[1, ..., :3]
+        hist[..., 6] = hh[0, ..., 3]
+        hist[..., 7] = hh[1, ..., 3]
+        hist[..., 8:12] = hh[2]
+        r["hist"] = hist
+        return r
+
+
+def oracle_inputs(w, frame_idx, osc=None):
+    osc = osc or oracle.Scene(w.scene)
+    cam = w.camera(frame_idx)
+    gb = oracle.gbuffer(osc, cam, w.params, w.W, w.H)
+    return osc, cam, oracle.gbuffer_f32(gb)
+
+
+def classify_hits(osc, w, params, cam, gpu, ref):
+    """Returns (n_rays, n_mismatch, n_unclassified, mismatch mask per hpx)."""
+    nr = ref["nrays"]
+    H2, W2 = nr.shape
+    mism = np.zeros((H2, W2), bool)
+    n_rays = int(nr.sum())
+    n_mis = n_bad = 0
+    gp, op = gpu["ray_prim"], ref["ray_prim"]
+    mr = min(gp.shape[2], op.shape[2])
+    for s in range(mr):
+        valid = nr > s
+        diff = valid & (gp[..., s] != op[..., s])
+        for (j, i) in np.argwhere(diff):
+            n_mis += 1
+            o, d = oracle.lens_ray(cam, params, w.W, w.H, i, j, s)
+            if not osc.near_tie(o, d, int(gp[j, i, s]), int(op[j, i, s])):
+                n_bad += 1
+            mism[j, i] = True
+    return n_rays, n_mis, n_bad, mism
+
+
+def threshold_ties(ref, params, cam, w):
+    """hpx whose rays' CoC lies within 1e-5 of the far-weight boundary c = -sqrt2, and
+    tiles whose dilated near radius is within 1e-5 of the mask threshold."""
+    H2, W2 = ref["nrays"].shape
+    out = np.zeros((H2, W2), bool)
+    if "ray_c" in ref:
+        c = ref["ray_c"]
+        k = np.arange(c.shape[2])[None, None, :] < ref["nrays"][..., None]
+        near = k & (np.abs(c + SQRT2) <= 1e-5 * SQRT2)
+        out |= near.any(-1)
+    T = int(params["tile"])
+    thr = float(np.float32(params["mask_near_hpx"]))
+    tie_t = np.abs(ref["tile_dil"][..., 0] - thr) <= 1e-5 * max(thr, 1e-3)
+    out |= np.repeat(np.repeat(tie_t, T, 0), T, 1)[:H2, :W2]
+    return out
+
+
+def taint_radius(params):
+    rmax = 0.5 * float(params["max_coc_px"])
+    lod = min(float(params["lod_max"]), rmax * float(params["lod_scale"]))
+    return int(math.ceil(rmax)) + 2 ** (int(math.ceil(lod)) + 1) + 2
+
+
+def dilate(mask, r):
+    if r <= 0 or not mask.any():
+        return mask.copy()
+    return ndi.binary_dilation(mask, structure=np.ones((2 * r + 1, 2 * r + 1), bool))
+
+
+def full_res(mask_h, W, H):
+    m = np.repeat(np.repeat(mask_h, 2, 0), 2, 1)[:H, :W]
+    return dilate(m, 2)
+
+
+def max_abs(a, b, mask=None):
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))
+    if mask is not None:
+        d = d[~mask] if d.ndim == mask.ndim else d[~mask]
+    return float(d.max()) if d.size else 0.0

@@ -1,0 +1,277 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded
+inputs: every intermediate of the frame, hit ids, and the final image."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_workload, plane_scene, tiny_scene, Camera, camera_pose
+from synth.scenes import Workload, default_params
+
+from parity import (GpuRunner, classify_hits, dilate, full_res, max_abs, oracle_inputs, psnr,
+                    taint_radius, threshold_ties)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2210_06158_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
+    """Frames 0..n-1 of workload w on both sides; asserts parity frame by frame."""
+    params = dict(params or w.params)
+    w.params = params
+    osc = oracle.Scene(w.scene)
+    gpu = GpuRunner(w, params)
+    ohist = oracle.History(w.W, w.H)
+    H2, W2 = w.H // 2, w.W // 2
+    rt_r = taint_radius(params)
+    taint_h = np.zeros((H2, W2), bool)
+    stats = []
+    for k in range(n_frames):
+        cam = w.camera(k)
+        gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, params, w.W, w.H))
+        ref = oracle.frame(osc, cam, params, w.W, w.H, gb, ohist)
+        got = gpu.frame(cam, gb)
+        # ---- post-process: same FP32 inputs on both sides
+        assert np.array_equal(got["z_h"], ref["z_h"].astype(np.float32))
+        assert max_abs(got["pp_in"][..., :3], ref["pp_in"][..., :3]) < 1e-6
+        assert max_abs(got["pp_in"][..., 3], ref["pp_in"][..., 3]) < 2e-5
+        assert max_abs(got["tile_raw"], ref["tile_raw"]) < 2e-5
+        assert max_abs(got["tile_dil"], ref["tile_dil"]) < 2e-5
+        e_pre = max_abs(got["pre"], ref["pre"])
+        e_main = max_abs(got["main_out"], ref["main_out"])
+        e_med = max_abs(got["pp_med"], ref["pp_med"])
+        assert e_pre < 1e-4 and e_main < 5e-4 and e_med < 5e-4, (e_pre, e_main, e_med)
+        # ---- mask: exact outside threshold ties
+        ties = threshold_ties(ref, params, cam, w)
+        assert np.array_equal(got["nrays"][~ties], ref["nrays"][~ties])
+        if int(params["ray_mode"]) == 1:
+            assert max_abs(got["xn"], ref["xn"]) < 1e-4
+        st = got["stats"]
+        assert st.device_status == 0
+        assert st.rays == int(got["nrays"].sum())
+        # ---- hit ids
+        n_rays, n_mis, n_bad, mism = classify_hits(osc, w, params, cam, got, ref)
+        assert n_bad == 0, f"{n_bad} hit-id mismatches are not FP near ties"
+        # ---- taint cone, carried through the history
+        seed = mism | ties | (got["nrays"] != ref["nrays"])
+        taint_h = dilate(dilate(taint_h, 2) | seed, rt_r)
+        ok = ~taint_h
+        m = (ref["nrays"] > 0) & ok
+        e_rt = max_abs(got["rt"][..., 1:10][m], ref["rt"][..., 1:10][m]) if m.any() else 0.0
+        both_far = m & (got["rt"][..., 13] > 0) & (ref["rt"][..., 13] > 0)
+        e_pf = (max_abs(got["rt"][..., 10:13][both_far], ref["rt"][..., 10:13][both_far]) /
+                max(1.0, float(np.abs(ref["rt"][..., 10:13][both_far]).max()))) if both_far.any() else 0.0
+        assert e_rt < 1e-4 and e_pf < 1e-4, (e_rt, e_pf)
+        e_crt = max_abs(got["crt"][ok], ref["crt"][ok])
+        e_ct = max_abs(got["ct"][ok], ref["ct"][ok])
+        e_hist = max_abs(got["hist"][ok], ref["hist"][ok])
+        e_var = max_abs(got["var_blur"][ok], ref["var_blur"][ok])
+        e_rtm = max_abs(got["rt_med"][ok], ref["rt_med"][ok])
+        e_rec = max_abs(got["recon"][ok], ref["recon"][ok])
+        assert e_crt < 5e-4 and e_hist < 5e-4 and e_rtm < 5e-4 and e_rec < 1e-3, (e_crt, e_hist, e_rtm, e_rec)
+        assert e_ct < 1e-3 and e_var < 1e-5, (e_ct, e_var)
+        # ---- final image (linear RGB)
+        taint_f = full_res(taint_h, w.W, w.H)
+        e_out = max_abs(got["out"][..., :3][~taint_f], ref["out"][..., :3][~taint_f])
+        p = psnr(got["out"][..., :3], ref["out"][..., :3])
+        assert e_out <= tol_img, e_out
+        assert p >= 50.0, p
+        s = dict(frame=k, rays=n_rays, mismatches=n_mis, tainted=float(taint_f.mean()), max_out=e_out, psnr=p,
+                 pre=e_pre, main=e_main, rt=e_rt, crt=e_crt, recon=e_rec)
+        stats.append(s)
+        if report is not None:
+            report.append(s)
+    return stats
+
+
+def _print(stats, name):
+    for s in stats:
+        print(f"[{name}] " + " ".join(f"{k}={v:.3g}" if isinstance(v, float) else f"{k}={v}" for k, v in s.items()))
+
+
+def test_gbuffer_matches_oracle():
+    from paper_2210_06158_gb300 import dof
+    import torch
+    for name, W, H in [("c1", 256, 144), ("c2", 322, 182)]:
+        w = make_workload(name, W=W, H=H)
+        cam = w.camera(0)
+        osc = oracle.Scene(w.scene)
+        ref = oracle.gbuffer(osc, cam, w.params, W, H)
+        ctx = dof.Context(0)
+        sc = dof.Scene(ctx, w.scene)
+        got = dof.gbuffer(ctx, sc, cam, w.params, W, H)
+        torch.cuda.synchronize()
+        prim = got["prim"].cpu().numpy()
+        bad = np.argwhere(prim != ref["prim"])
+        for (j, i) in bad:
+            d = oracle.pixel_dir(cam, W, H, i + 0.5, j + 0.5)
+            assert osc.near_tie(np.asarray(cam.pos, np.float64), d, int(prim[j, i]), int(ref["prim"][j, i]))
+        assert len(bad) <= max(2, 1e-4 * W * H)
+        ok = prim == ref["prim"]
+        hit = ok & (prim >= 0)
+        col = got["color"].cpu().numpy()[..., :3]
+        assert max_abs(col[ok], ref["color"][ok]) < 1e-5
+        dep = got["depth"].cpu().numpy()
+        rel = np.abs(dep[hit] - ref["depth"][hit]) / ref["depth"][hit]
+        assert rel.max() < 2e-5
+        assert np.all(np.isinf(dep[ok & (prim < 0)]))
+        assert max_abs(got["normal"].cpu().numpy()[..., :3][ok], ref["normal"][ok]) < 1e-5
+
+
+def test_gpu_hits_equal_brute_force_on_tiny_scenes():
+    """G-buffer ids against the oracle's all-triangle loop (no BVH on either side
+    decides the answer), incl. shared-edge and coplanar ties; 0, 1 and 2 triangles."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    ctx = dof.Context(0)
+    pose = camera_pose((0.0, 0.0, 0.0), pitch_deg=0.0)
+    cam = Camera.from_poses(dict(f_m=0.05, f_number=2.0, focus_m=3.0, sensor_w_m=0.036), pose)
+    W, H = 96, 64
+    for n in [0, 1, 2, 7, 64, 200]:
+        s = tiny_scene(500 + n, n, ties=n >= 8)
+        osc = oracle.Scene(s)
+        sc = dof.Scene(ctx, s)
+        got = dof.gbuffer(ctx, sc, cam, default_params(), W, H)
+        torch.cuda.synchronize()
+        prim = got["prim"].cpu().numpy()
+        n_bad = 0
+        for j in range(H):
+            for i in range(W):
+                d = oracle.pixel_dir(cam, W, H, i + 0.5, j + 0.5)
+                o = np.zeros(3)
+                want, _ = osc.closest(o, d, brute=True)
+                if prim[j, i] != want and not osc.near_tie(o, d, int(prim[j, i]), want):
+                    n_bad += 1
+        assert n_bad == 0, (n, n_bad)
+
+
+def test_frame_parity_c1():
+    stats = run_sequence(make_workload("c1"))
+    _print(stats, "c1")
+
+
+def test_frame_parity_ragged_dolly_with_history():
+    """The lawn scene at 250x142 (125x71 hpx: ragged 8x8 tiles in both directions),
+    4 frames of the dolly: camera motion, reprojection, history."""
+    w = make_workload("c2", W=250, H=142, n_frames=4)
+    stats = run_sequence(w, 4)
+    _print(stats, "c2-250x142")
+
+
+def test_frame_parity_static_accumulation():
+    """Static camera over 4 frames (the EMA at 0.95 with new lens samples per frame)."""
+    w = make_workload("c1", W=160, H=90)
+    w.poses = [w.poses[0]] * 4
+    stats = run_sequence(w, 4)
+    _print(stats, "c1-static")
+
+
+def test_frame_parity_4spp_c3_lens():
+    w = make_workload("c3", W=384, H=216, n_frames=2)
+    stats = run_sequence(w, 2)
+    _print(stats, "c3-384x216")
+
+
+def test_frame_parity_adaptive_ray_count():
+    """Eq. 4 adaptive mode: Sobel edge measure and the previous frame's variance."""
+    w = make_workload("c1", W=192, H=108)
+    w.poses = [w.poses[0]] * 3
+    prm = dict(w.params, ray_mode=1, m=6)
+    stats = run_sequence(w, 3, prm)
+    _print(stats, "c1-adaptive")
+
+
+def test_edge_cases_tiny_empty_single():
+    # 2x2 image (one half-resolution pixel), 4x2, an empty scene, a one-triangle scene
+    for W, H, scene in [(2, 2, None), (4, 2, None), (64, 36, "empty"), (64, 36, "one")]:
+        w = make_workload("c1", W=W, H=H)
+        if scene == "empty":
+            sc = tiny_scene(1, 0, ties=False)
+            w._scene = sc
+        elif scene == "one":
+            w._scene = plane_scene([(2.0, "right", 0.0, 0)])
+        prm = dict(w.params, mask_near_hpx=0.0)
+        run_sequence(w, 1, prm)
+
+
+def test_max_spp_and_history_reset():
+    from paper_2210_06158_gb300 import dof
+    w = make_workload("c1", W=64, H=36)
+    prm = dict(w.params, spp=64, mask_near_hpx=0.0)
+    run_sequence(w, 1, prm)
+    # reset: the next frame equals a first frame
+    osc, cam, gb = oracle_inputs(w, 0)
+    g = GpuRunner(w, w.params)
+    a = g.frame(cam, gb)["out"]
+    g.frame(cam, gb)
+    g.hist.reset()
+    b = g.frame(cam, gb)["out"]
+    assert np.array_equal(a, b)
+
+
+def test_determinism_bit_identical():
+    w = make_workload("c2", W=320, H=180, n_frames=2)
+    osc = oracle.Scene(w.scene)
+    outs = []
+    for _ in range(2):
+        g = GpuRunner(w, w.params)
+        seq = []
+        for k in range(2):
+            cam = w.camera(k)
+            gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, w.params, w.W, w.H))
+            seq.append(g.frame(cam, gb, read=False)["out"])
+        outs.append(seq)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_host_validation_errors():
+    from paper_2210_06158_gb300 import dof
+    import torch
+    ctx = dof.Context(0)
+    w = make_workload("c1", W=64, H=36)
+    sc = dof.Scene(ctx, w.scene)
+    h = dof.History(ctx, 64, 36, max_rays=1)
+    dev = torch.device("cuda", 0)
+    gb = dict(color=torch.zeros((36, 64, 4), device=dev), depth=torch.ones((36, 64), device=dev))
+    cam = w.camera(0)
+    with pytest.raises(dof.DofError) as e:
+        dof.frame(ctx, sc, gb, cam, dict(w.params, spp=2), h)
+    assert e.value.code == -1
+    bad = w.camera(0)
+    bad.focus_m = 0.01
+    with pytest.raises(dof.DofError) as e:
+        dof.frame(ctx, sc, gb, bad, w.params, h)
+    assert e.value.code == -1
+    gb2 = dict(color=torch.zeros((38, 64, 4), device=dev), depth=torch.ones((38, 64), device=dev))
+    with pytest.raises(dof.DofError) as e:
+        dof.frame(ctx, sc, gb2, cam, w.params, h)
+    assert e.value.code == -7
+    with pytest.raises(dof.DofError) as e:
+        dof.History(ctx, 63, 36)
+    assert e.value.code == -1
+    small = dof.Context(0, mem_budget_bytes=1 << 16)
+    with pytest.raises(dof.DofError) as e:
+        dof.History(small, 640, 360)
+    assert e.value.code == -3
+    assert small.bytes_in_use == 0
+
+
+@pytest.mark.slow
+def test_full_size_c2_two_frames():
+    """1920x1080, 495,802 triangles, 1 spp, frames 0 and 1 of the dolly, in the launch
+    configuration the benchmark times."""
+    w = make_workload("c2", n_frames=2)
+    stats = run_sequence(w, 2)
+    _print(stats, "c2-full")
+    tot = sum(s["rays"] for s in stats)
+    mis = sum(s["mismatches"] for s in stats)
+    assert mis <= max(2, 1e-4 * tot), (mis, tot)
