@@ -219,7 +219,7 @@ int dof_kernel_times(DofHistory *hist, void *stream, float *ms, uint32_t *frames
  *   RT     float4 4N: planes (An, h), (Af, n), (Bn, Bf, Fw, 0), (Pfar, 0)
  *   CRT    float4 N (rgb, h)             CT, VAR, VAR_BLUR float N
  *   RT_MED float4 N                       RECON   float4 N (rgb, h)
- *   HIST   float4 3N: planes (An, h), (Af, g), (Bn, Bf, mu1, mu2)
+ *   HIST   float4 3N: planes (An, h), (Af, g), (Bn, Bf, mu1, var) -- luminance mean and variance
  * *dev_ptr is owned by the history and valid until the next call that uses it. */
 enum {
     DOF_BUF_PP_IN = 0, DOF_BUF_Z_H, DOF_BUF_TILES, DOF_BUF_TILES_DIL, DOF_BUF_PRE,
@@ -228,6 +228,9 @@ enum {
     DOF_BUF_RECON, DOF_BUF_HIST, DOF_BUF_COUNT
 };
 int dof_debug_buffer(DofHistory *hist, int which, void **dev_ptr, size_t *bytes);
+/* Synchronous copy of intermediate buffer `which` into caller-owned host memory of
+ * `bytes` bytes (must equal the buffer's size); waits for all work on the device. */
+int dof_debug_read(DofHistory *hist, int which, void *host_dst, size_t bytes);
 
 #ifdef __cplusplus
 }

@@ -288,6 +288,7 @@ extern "C" int dof_gbuffer(DofCtx *ctx, const DofScene *scene, const DofCamera *
     if (rc) return rc;
     rc = make_params(p, width, height, DOF_MAX_RAYS, dp);
     if (rc) return rc;
+    cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
     launch_primary(dc, dp, scene_dev(scene), reinterpret_cast<float4 *>(color), depth,
                    reinterpret_cast<float4 *>(normal), prim, ctx->d_status, (cudaStream_t)stream);
     return dof_cuda_check(cudaGetLastError(), "dof_gbuffer launch");
@@ -371,6 +372,7 @@ extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, 
             if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->var_blur[k], 0, 4 * N), "history clear");
         }
         if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->xf, 0, 4 * N), "history clear");
+        if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->counters, 0, 16), "history clear");
         if (rc == DOF_OK && h->ray_prim) rc = dof_cuda_check(cudaMemset(h->ray_prim, 0xFF, 4 * N * max_rays), "clear");
     }
     if (rc == DOF_OK && (flags & DOF_HIST_TIMING)) {
@@ -424,6 +426,7 @@ extern "C" int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *g
     if (rc) return rc;
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
+    cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
     rc = dof_cuda_check(cudaMemsetAsync(h->counters, 0, 3 * sizeof(uint32_t), st), "dof_frame counters");
     if (rc) return rc;
     if (h->ev && h->ev_used < kTimingSlots) {
@@ -513,4 +516,18 @@ extern "C" int dof_debug_buffer(DofHistory *h, int which, void **ptr, size_t *by
         default: return dof_set_error(DOF_ERR_INVALID_ARG, "dof_debug_buffer: unknown buffer %d", which);
     }
     return DOF_OK;
+}
+
+extern "C" int dof_debug_read(DofHistory *h, int which, void *dst, size_t bytes) {
+    void *src = nullptr;
+    size_t n = 0;
+    int rc = dof_debug_buffer(h, which, &src, &n);
+    if (rc) return rc;
+    if (!dst && bytes) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_debug_read: null destination");
+    if (bytes != n) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_debug_read: %zu bytes requested, buffer has %zu", bytes, n);
+    if (!n) return DOF_OK;
+    DeviceGuard g(h->ctx->device);
+    rc = dof_cuda_check(cudaDeviceSynchronize(), "dof_debug_read sync");
+    if (rc) return rc;
+    return dof_cuda_check(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost), "dof_debug_read");
 }

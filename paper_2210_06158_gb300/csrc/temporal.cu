@@ -7,8 +7,8 @@
 
 namespace {
 
-__device__ __forceinline__ bool project_prev(const DevCam &c, float3 X, float &xh, float &yh) {
-    float3 rel = X - c.pO;
+// rel = the point relative to the previous lens centre
+__device__ __forceinline__ bool project_prev(const DevCam &c, float3 rel, float &xh, float &yh) {
     float zc = dot(rel, c.pF);
     if (!(zc > 0.f)) return false;
     float iz = c.Fpx / zc;
@@ -19,7 +19,13 @@ __device__ __forceinline__ bool project_prev(const DevCam &c, float3 X, float &x
     return fabsf(xh) < 1e7f && fabsf(yh) < 1e7f;
 }
 
-struct NearH { float4 a; float bn, m1, m2; };   // (An, h), Bn, mu1, mu2
+struct NearH {
+    float4 a;          // sum w (An, h)
+    float bn, m1;      // sum w Bn, sum w mu1
+    float wv[4], x[4]; // per tap: w, and its (mu1, variance) for the second variance pass
+    float v[4];
+    int n;
+};
 struct FarH { float4 a; float bf; };            // (Af, g), Bf
 
 // bilinear history fetch with dropped taps (outside, or without history)
@@ -31,8 +37,6 @@ __device__ __forceinline__ float fetch(const float4 *__restrict__ H0, const floa
     float fx = x - xf, fy = y - yf;
     int x0 = (int)xf, y0 = (int)yf;
     float wsum = 0.f;
-    nh.a = make_float4(0.f, 0.f, 0.f, 0.f); nh.bn = nh.m1 = nh.m2 = 0.f;
-    fh.a = nh.a; fh.bf = 0.f;
 #pragma unroll
     for (int t = 0; t < 4; t++) {
         int dx = t & 1, dy = t >> 1;
@@ -45,7 +49,9 @@ __device__ __forceinline__ float fetch(const float4 *__restrict__ H0, const floa
         float4 h2 = __ldg(&H2[q]);
         if (NEAR) {
             nh.a = f4fma(w, h0, nh.a);
-            nh.bn += w * h2.x; nh.m1 += w * h2.z; nh.m2 += w * h2.w;
+            nh.bn += w * h2.x;
+            nh.m1 += w * h2.z;
+            nh.wv[nh.n] = w; nh.x[nh.n] = h2.z; nh.v[nh.n] = h2.w; nh.n++;
         } else {
             fh.a = f4fma(w, h1, fh.a);
             fh.bf += w * h2.y;
@@ -55,6 +61,12 @@ __device__ __forceinline__ float fetch(const float4 *__restrict__ H0, const floa
     return wsum;
 }
 
+// The luminance moments are kept as (mean, variance) rather than (mean, mean of
+// squares): with weights a_k summing to one (a_k = alpha w_k for the history taps,
+// 1 - alpha W for the current value), the new variance is
+//     sum a_k v_k + sum a_k (x_k - mean')^2,
+// which equals mean-of-squares' - mean'^2 exactly but without its cancellation (the
+// ray count of Eq. 4 multiplies the variance by 1e5).
 __global__ void __launch_bounds__(256) k_accumulate(DevCam cam, DevParams p, const float *__restrict__ z_h,
                                                     const float4 *__restrict__ rt, const int32_t *__restrict__ nrays,
                                                     const float4 *__restrict__ hin, int has_hist, float4 *hout,
@@ -73,7 +85,9 @@ __global__ void __launch_bounds__(256) k_accumulate(DevCam cam, DevParams p, con
     float h = rA.w, g = 1.f - h;
     float L = lum709(rA.x + rB.x, rA.y + rB.y, rA.z + rB.z);
     float3 dp = pixel_dir(cam, 2.f * i + 1.f, 2.f * j + 1.f);
-    float3 Xn = cam.O + (__ldg(&z_h[q]) / dot(dp, cam.F)) * dp;
+    const float3 dO = cam.O - cam.pO;
+    // near field: the G-buffer surface, relative to the previous lens centre
+    float3 relN = dO + (__ldg(&z_h[q]) / dot(dp, cam.F)) * dp;
     float3 Xf;
     if (rC.z > 0.f) {
         float4 d = __ldg(&rt[3 * N + q]);
@@ -92,18 +106,21 @@ __global__ void __launch_bounds__(256) k_accumulate(DevCam cam, DevParams p, con
                     cnt++;
                 }
             }
-        Xf = cnt ? (1.f / (float)cnt) * acc : Xn;
+        Xf = cnt ? (1.f / (float)cnt) * acc : cam.O + (__ldg(&z_h[q]) / dot(dp, cam.F)) * dp;
     }
-    NearH nh;
+    NearH nh, ndummy;
     FarH fh, fdummy;
-    NearH ndummy;
-    float Wn = 0.f, Wf = 0.f, xh, yh;
-    nh.a = make_float4(0.f, 0.f, 0.f, 0.f); nh.bn = nh.m1 = nh.m2 = 0.f;
+    nh.a = make_float4(0.f, 0.f, 0.f, 0.f); nh.bn = nh.m1 = 0.f; nh.n = 0;
+    ndummy = nh;
     fh.a = nh.a; fh.bf = 0.f;
+    fdummy = fh;
+    float Wn = 0.f, Wf = 0.f, xh, yh;
     if (has_hist) {
         const float4 *H0 = hin, *H1 = hin + N, *H2p = hin + 2 * N;
-        if (project_prev(cam, Xn, xh, yh)) Wn = fetch<true>(H0, H1, H2p, W2, H2, xh, yh, nh, fdummy);
-        if (project_prev(cam, Xf, xh, yh)) Wf = fetch<false>(H0, H1, H2p, W2, H2, xh, yh, ndummy, fh);
+        // a static camera maps the G-buffer surface exactly onto its own pixel
+        bool okn = cam.moved ? project_prev(cam, relN, xh, yh) : (xh = (float)i, yh = (float)j, true);
+        if (okn) Wn = fetch<true>(H0, H1, H2p, W2, H2, xh, yh, nh, fdummy);
+        if (project_prev(cam, Xf - cam.pO, xh, yh)) Wf = fetch<false>(H0, H1, H2p, W2, H2, xh, yh, ndummy, fh);
     }
     const float a = cam.moved ? p.alpha_motion : p.alpha;
     const float kn = 1.f - a * Wn, kf = 1.f - a * Wf;
@@ -112,11 +129,17 @@ __global__ void __launch_bounds__(256) k_accumulate(DevCam cam, DevParams p, con
     float4 Af = make_float4(a * fh.a.x + kf * rB.x, a * fh.a.y + kf * rB.y, a * fh.a.z + kf * rB.z,
                             a * fh.a.w + kf * g);
     float Bn = a * nh.bn + kn * rC.x, Bf = a * fh.bf + kf * rC.y;
-    float m1 = a * nh.m1 + kn * L, m2 = a * nh.m2 + kn * L * L;
+    float m1 = a * nh.m1 + kn * L;
+    float dl = L - m1;
+    float v = kn * dl * dl;
+    for (int t = 0; t < nh.n; t++) {
+        float dx = nh.x[t] - m1;
+        v += a * nh.wv[t] * (nh.v[t] + dx * dx);
+    }
     hout[q] = An;
     hout[N + q] = Af;
-    hout[2 * N + q] = make_float4(Bn, Bf, m1, m2);
-    var[q] = fmaxf(0.f, m2 - m1 * m1);
+    hout[2 * N + q] = make_float4(Bn, Bf, m1, v);
+    var[q] = v;
     if (!cam.moved) {
         float r = 1.f / (An.w + Af.w);
         crt[q] = make_float4((An.x + Af.x) * r, (An.y + Af.y) * r, (An.z + Af.z) * r, An.w * r);

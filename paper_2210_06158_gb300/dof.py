@@ -98,6 +98,7 @@ _SIGS = {
     "dof_frame_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofFrameStats)]),
     "dof_debug_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
     "dof_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
+    "dof_debug_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
 }
 
 
@@ -257,16 +258,10 @@ class History:
 
     def read(self, name: str, dtype=np.float32, shape=None):
         """Copy an intermediate buffer to a numpy array (synchronous)."""
-        import torch
         p, n = self.buffer(name)
-        out = torch.empty(n, dtype=torch.uint8)
-        if n:
-            torch.cuda.synchronize()
-            cudart = torch.cuda.cudart()
-            rc = cudart.cudaMemcpy(out.data_ptr(), p, n, 2)   # device -> host
-            if int(rc) != 0:
-                raise RuntimeError(f"cudaMemcpy failed ({rc})")
-        a = out.numpy().view(dtype)
+        out = np.empty(n, dtype=np.uint8)
+        _check(lib().dof_debug_read(self.ptr, BUF[name], out.ctypes.data_as(C.c_void_p), n))
+        a = out.view(dtype)
         return a.reshape(shape) if shape is not None else a
 
     def close(self):

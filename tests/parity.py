@@ -99,6 +99,8 @@ class GpuRunner:
         hist[..., 6] = hh[0, ..., 3]
         hist[..., 7] = hh[1, ..., 3]
         hist[..., 8:12] = hh[2]
+        # the device keeps (mean, variance) of the luminance; the oracle (mean, mean of squares)
+        hist[..., 11] = hh[2, ..., 3] + hh[2, ..., 2].astype(np.float64) ** 2
         r["hist"] = hist
         return r
 
@@ -141,6 +143,12 @@ def threshold_ties(ref, params, cam, w):
         k = np.arange(c.shape[2])[None, None, :] < ref["nrays"][..., None]
         near = k & (np.abs(c + SQRT2) <= 1e-5 * SQRT2)
         out |= near.any(-1)
+    if int(params["ray_mode"]) == 1:
+        # adaptive count clamp(ceil(x_f), 1, m) jumps only where x_f crosses 1..m-1
+        xf = ref["xf"]
+        k = np.round(xf)
+        jump = (k >= 1) & (k <= float(params["m"]) - 1)
+        out |= jump & (np.abs(xf - k) <= 1e-3 * max(1.0, float(params["m"]))) & (ref["nrays"] > 0)
     T = int(params["tile"])
     thr = float(np.float32(params["mask_near_hpx"]))
     tie_t = np.abs(ref["tile_dil"][..., 0] - thr) <= 1e-5 * max(thr, 1e-3)

@@ -51,9 +51,12 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
         assert e_pre < 1e-4 and e_main < 5e-4 and e_med < 5e-4, (e_pre, e_main, e_med)
         # ---- mask: exact outside threshold ties
         ties = threshold_ties(ref, params, cam, w)
-        assert np.array_equal(got["nrays"][~ties], ref["nrays"][~ties])
         if int(params["ray_mode"]) == 1:
-            assert max_abs(got["xn"], ref["xn"]) < 1e-4
+            # x_f reads the previous frame's variance: compare it outside the taint so far
+            e_xn, e_xf = max_abs(got["xn"], ref["xn"]), max_abs(got["xf"][~taint_h], ref["xf"][~taint_h])
+            assert e_xn < 1e-4 and e_xf < 2e-4 * float(params["m"]), (e_xn, e_xf)
+        bad_n = got["nrays"][~ties] != ref["nrays"][~ties]
+        assert not bad_n.any(), (int(bad_n.sum()), int(ties.sum()))
         st = got["stats"]
         assert st.device_status == 0
         assert st.rays == int(got["nrays"].sum())
@@ -65,19 +68,28 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
         taint_h = dilate(dilate(taint_h, 2) | seed, rt_r)
         ok = ~taint_h
         m = (ref["nrays"] > 0) & ok
-        e_rt = max_abs(got["rt"][..., 1:10][m], ref["rt"][..., 1:10][m]) if m.any() else 0.0
+        # h and the field colours absolute, the field CoC radii (up to rmax) relative
+        e_rt = max_abs(got["rt"][..., 1:8][m], ref["rt"][..., 1:8][m]) if m.any() else 0.0
+        e_rb = (max_abs(got["rt"][..., 8:10][m], ref["rt"][..., 8:10][m]) /
+                max(1.0, float(np.abs(ref["rt"][..., 8:10]).max()))) if m.any() else 0.0
         both_far = m & (got["rt"][..., 13] > 0) & (ref["rt"][..., 13] > 0)
         e_pf = (max_abs(got["rt"][..., 10:13][both_far], ref["rt"][..., 10:13][both_far]) /
                 max(1.0, float(np.abs(ref["rt"][..., 10:13][both_far]).max()))) if both_far.any() else 0.0
-        assert e_rt < 1e-4 and e_pf < 1e-4, (e_rt, e_pf)
+        assert e_rt < 1e-4 and e_rb < 1e-4 and e_pf < 1e-4, (e_rt, e_rb, e_pf)
         e_crt = max_abs(got["crt"][ok], ref["crt"][ok])
         e_ct = max_abs(got["ct"][ok], ref["ct"][ok])
         e_hist = max_abs(got["hist"][ok], ref["hist"][ok])
         e_var = max_abs(got["var_blur"][ok], ref["var_blur"][ok])
         e_rtm = max_abs(got["rt_med"][ok], ref["rt_med"][ok])
         e_rec = max_abs(got["recon"][ok], ref["recon"][ok])
+        e_hist = max_abs(got["hist"][..., [0, 1, 2, 3, 4, 5, 6, 7, 10, 11]][ok],
+                         ref["hist"][..., [0, 1, 2, 3, 4, 5, 6, 7, 10, 11]][ok])
+        rmax = 0.5 * float(params["max_coc_px"])
+        e_ct = max(e_ct, max_abs(got["hist"][..., 8:10][ok], ref["hist"][..., 8:10][ok])) / max(1.0, rmax)
         assert e_crt < 5e-4 and e_hist < 5e-4 and e_rtm < 5e-4 and e_rec < 1e-3, (e_crt, e_hist, e_rtm, e_rec)
-        assert e_ct < 1e-3 and e_var < 1e-5, (e_ct, e_var)
+        # FP32 reprojection of a moving camera is accurate to ~1e-5 px, which mixes that
+        # share of a (noisy) neighbour's history in; a static camera is exact
+        assert e_ct < 1e-4 and e_var < (2e-5 if cam_moved(cam) else 1e-6), (e_ct, e_var)
         # ---- final image (linear RGB)
         taint_f = full_res(taint_h, w.W, w.H)
         e_out = max_abs(got["out"][..., :3][~taint_f], ref["out"][..., :3][~taint_f])
@@ -90,6 +102,11 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
         if report is not None:
             report.append(s)
     return stats
+
+
+def cam_moved(cam):
+    return any(not np.array_equal(np.asarray(getattr(cam, a), np.float32), np.asarray(getattr(cam, "prev_" + a), np.float32))
+               for a in ("pos", "right", "up", "fwd"))
 
 
 def _print(stats, name):
