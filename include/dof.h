@@ -232,6 +232,31 @@ int dof_debug_buffer(DofHistory *hist, int which, void **dev_ptr, size_t *bytes)
  * `bytes` bytes (must equal the buffer's size); waits for all work on the device. */
 int dof_debug_read(DofHistory *hist, int which, void *host_dst, size_t bytes);
 
+/* ---- allocation-free tile map ------------------------------------------------ */
+
+/* No counterpart in the paper: a convenience for hosts that cannot allocate device
+ * memory when they need the tile map -- e.g. an engine whose allocator reserved all
+ * device memory up front, or a frame loop where cudaMalloc/cudaFree would implicitly
+ * synchronise the device.  Computes the same dilated tile map as dof_frame's tile
+ * stage (DOF_BUF_TILES_DIL: per 8x8 half-resolution tile the max near CoC radius and
+ * max |rho|, dilated over the tile neighbourhood) from a full-resolution depth map,
+ * and allocates nothing: its one intermediate (the undilated tiles) lives in a
+ * built-in device array of DOF_NOALLOC_MAX_TILES tiles (512 KB, held by every GPU
+ * that loads the library until the process exits).
+ *   depth      device, width*height floats (8-byte aligned), read only
+ *   tiles_dil  device, ceil(width/16)*ceil(height/16) float2 (8-byte aligned), written
+ *   cam, p     only the lens (f, N, focus, sensor width), tile, max_coc_px and z_far_m
+ *              are used
+ * Sizes whose tile count exceeds DOF_NOALLOC_MAX_TILES return DOF_ERR_INVALID_ARG.
+ * The first call on a device looks up that device's address of the array (with the
+ * device current); make that first call before any stream capture.  Every call shares
+ * the array and it keeps the previous call's contents (each call overwrites what it
+ * reads); calls that overlap on the GPU race on it and must be serialised by the
+ * caller.  Enqueued on `stream`; returns without synchronising. */
+#define DOF_NOALLOC_MAX_TILES 65536
+int dof_coc_tiles_noalloc(const float *depth, uint32_t width, uint32_t height, const DofCamera *cam,
+                          const DofParams *p, float *tiles_dil, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,8 @@ _SIGS = {
     "dof_debug_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
     "dof_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
     "dof_debug_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
+    "dof_coc_tiles_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.POINTER(DofCamera),
+                                        C.POINTER(DofParams), C.c_void_p, C.c_void_p]),
 }
 
 
@@ -315,4 +317,18 @@ def frame(ctx: Context, scene: Scene, gbuf: dict, cam, params, hist: History, ou
     p = params_s if params_s is not None else params_struct(params)
     _check(lib().dof_frame(ctx.ptr, scene.ptr, C.byref(g), C.byref(c), C.byref(p), hist.ptr, _ptr(out),
                            _stream_ptr(stream)))
+    return out
+
+
+def coc_tiles_noalloc(depth, cam, params, out=None, stream=None):
+    """Dilated tile map (near CoC radius, |rho|) per 8x8 half-resolution tile from a
+    full-resolution depth tensor, through the allocation-free entry point (the library
+    allocates nothing; `out` is created here by torch if not given)."""
+    import torch
+    H, W = depth.shape
+    TW, TH = -(-(W // 2) // 8), -(-(H // 2) // 8)
+    if out is None:
+        out = torch.empty((TH, TW, 2), dtype=torch.float32, device=depth.device)
+    c, p = camera_struct(cam), params_struct(params)
+    _check(lib().dof_coc_tiles_noalloc(_ptr(depth), W, H, C.byref(c), C.byref(p), _ptr(out), _stream_ptr(stream)))
     return out
