@@ -34,15 +34,25 @@ sys.path.insert(0, ROOT)
 METRIC = "hybrid-DoF frames/s at 1080p/4K, %HBM roofline; served p50/p99 frame latency"
 CYCLE = 16
 
+# FP32 operations of the traversal (FMA = 2): a node visit tests two child boxes
+# (per box 6 (sub, mul) slab products = 12, 10 min/max, 1 compare -> 23, x2 = 46) and
+# orders them (1); a watertight triangle test (Woop et al. 2013) is 9 subtractions,
+# 6 shears (sub, mul) = 12, 3 edge functions (2 mul + sub) = 9, 6 sign tests,
+# det (2), T (3 mul + 3 FMA = 9), 1 division -> 48.
+FLOP_PER_NODE = 47.0
+FLOP_PER_TRI = 48.0
+FP32_LANES_PER_SM = 128
+
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
-# half-resolution pixel N, per masked pixel M, per full-resolution pixel P.
+# half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
 BYTES = {
     "k_downscale_tiles": ("N", 100.0),   # 4 x (colour 16 + depth 4) read, pp_in 16 + z 4 written
     "k_prefilter": ("N", 32.0),
     "k_main_filter": ("N", 36.0),        # pre 16 + z 4 read, 16 written (neighbour taps from cache)
     "k_median_pp": ("N", 32.0),
     "k_mask_compact": ("N", 8.0),
-    "k_trace": ("M", 72.0),              # queue + count read, 4 x float4 written (BVH reads hit L2)
+    "k_trace": ("R", 12.0),              # per ray: ray list 4 read, hit 8 written (BVH reads hit L2)
+    "k_shade": ("M", 76.0),              # queue, count, first ray read, 4 x float4 written (+ hits, per ray)
     "k_accumulate": ("N", 192.0),        # rt 64 + z 4 + nrays 4 + history 48 read; history 48 + 24 written
     "k_var_blur": ("N", 8.0),
     "k_median_rt": ("N", 36.0),
@@ -236,7 +246,7 @@ def run_ours(args, rank, world):
     htime.kernel_times()
     ktot = {k: 0.0 for k in dof.KERNELS}
     nk = 0
-    rays = masked = 0
+    rays = masked = visits = tests = 0
     s = args.warmup
     while s < args.warmup + args.steps:
         for _ in range(min(32, args.warmup + args.steps - s)):
@@ -249,6 +259,8 @@ def run_ours(args, rank, world):
         fs = htime.stats()
         rays += fs.rays
         masked += fs.masked_pixels
+        visits += fs.node_visits
+        tests += fs.tri_tests
     kavg = {k: v / nk for k, v in ktot.items()}
     n_samples = math.ceil(args.steps / 32)
     rays_per_frame = rays / n_samples
@@ -298,7 +310,7 @@ def run_ours(args, rank, world):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     N = (w.W // 2) * (w.H // 2)
-    units = {"N": N, "M": masked_per_frame, "P": w.W * w.H}
+    units = {"N": N, "M": masked_per_frame, "R": rays_per_frame, "P": w.W * w.H}
     dom = max(kavg, key=lambda k: kavg[k])
     kern = {}
     for k, v in kavg.items():
@@ -309,7 +321,19 @@ def run_ours(args, rank, world):
             u, b = BYTES[k]
             e["gbs"] = round(units[u] * b / (v * 1e-3) / 1e9, 1)
         kern[k] = e
-    if dom in BYTES:
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6 / 1e12      # TFLOP/s, FMA = 2
+    trace_flop = (visits * FLOP_PER_NODE + tests * FLOP_PER_TRI) / n_samples
+    if dom == "k_trace" and kavg[dom] > 0:
+        achieved = trace_flop / (kavg[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                "peak_source": f"derived: 2 x {FP32_LANES_PER_SM} FP32 lanes x {n_sm} SMs x {sm_mhz:.0f} MHz",
+                "algorithmic_flop": int(trace_flop), "node_visits_per_ray": round(visits / max(1, rays), 2),
+                "tri_tests_per_ray": round(tests / max(1, rays), 2)}
+    elif dom in BYTES:
         u, b = BYTES[dom]
         algo = units[u] * b
         achieved = algo / (kavg[dom] * 1e-3) / 1e9
@@ -334,10 +358,10 @@ def run_ours(args, rank, world):
                            parallelism="replicas" if world > 1 else "single-gpu",
                            l2="inputs larger than L2: 16 distinct G-buffers cycled (16 x 41 MB)"),
                roofline=roof, e2e=e2e,
-               # per frame: 5 post-process, mask, trace, 2 temporal, RT median, 4 mip, recon, composite
-               # (+ 2 edge kernels in adaptive mode)
-               gpu_launches=(16 + (2 if int(prm["ray_mode"]) == 1 else 0)) * args.steps,
-               clocks=clk.summary(), kernel_ms=kern,
+               # per frame: 5 post-process, mask, trace, shade, 2 temporal, RT median, 4 mip, recon,
+               # composite (+ 2 edge kernels in adaptive mode)
+               gpu_launches=(17 + (2 if int(prm["ray_mode"]) == 1 else 0)) * args.steps,
+               clocks=clocks, kernel_ms=kern,
                image_passes={"ms": round(img_ms, 4), "gbs": round(img_bytes / (img_ms * 1e-3) / 1e9, 1),
                              "frac_of_hbm": round(img_bytes / (img_ms * 1e-3) / 1e9 / hbm_peak, 4)},
                mrays_per_s=round(rays_per_frame / (kavg.get("k_trace", 0) * 1e-3) / 1e6, 1)

@@ -110,7 +110,9 @@ typedef struct DofHistory DofHistory;
 typedef struct {
     uint32_t n_tris, n_nodes, depth, stack_limit;
     uint64_t device_bytes;
-    float bounds_lo[3], bounds_hi[3];
+    float bounds_lo[3], bounds_hi[3];   /* bounds of the triangles in the tree */
+    uint32_t n_large;                   /* large triangles kept out of the tree */
+    uint32_t pad;
 } DofSceneInfo;
 
 typedef struct {
@@ -119,6 +121,8 @@ typedef struct {
     uint32_t rays;             /* last frame: rays traced */
     int32_t device_status;     /* DOF_OK or the first device-side error */
     uint32_t pad;
+    uint64_t node_visits;      /* last frame: BVH nodes visited by the thin-lens rays */
+    uint64_t tri_tests;        /* last frame: ray/triangle tests of the thin-lens rays */
 } DofFrameStats;
 
 /* ---- context ----------------------------------------------------------------- */
@@ -141,7 +145,9 @@ const char *dof_last_error(void);
 /* ---- scene (Section 4.2: the acceleration structure) ------------------------- */
 
 /* Upload a triangle scene and build its BVH on the device: an LBVH (Karras 2012) over
- * 30-bit Morton codes of the triangle centroids, two child boxes per node.
+ * 63-bit Morton codes of the triangle centroids, two child boxes per node.  Up to 64
+ * "large" triangles (box extent above 1/16 of the scene's centroid extent, e.g. a
+ * ground plane) are kept out of the tree and tested directly by every ray.
  *   xyz      host, n_verts * 3 floats
  *   tri_idx  host, n_tris * 3 vertex indices (< n_verts, checked)
  *   tri_mat  host, n_tris material ids (0 diffuse with hash albedo, 1 emitter), or NULL
@@ -197,8 +203,8 @@ int dof_frame_stats(DofHistory *hist, void *stream, DofFrameStats *out);
 /* Kernels of one frame, in launch order (DOF_HIST_TIMING brackets each with events). */
 enum {
     DOF_K_DOWNSCALE = 0, DOF_K_DILATE, DOF_K_PREFILTER, DOF_K_MAIN, DOF_K_MEDIAN_PP, DOF_K_EDGES,
-    DOF_K_MASK, DOF_K_TRACE, DOF_K_ACCUM, DOF_K_VAR_BLUR, DOF_K_MEDIAN_RT, DOF_K_MIPS, DOF_K_RECON,
-    DOF_K_COMPOSITE, DOF_K_COUNT
+    DOF_K_MASK, DOF_K_TRACE, DOF_K_SHADE, DOF_K_ACCUM, DOF_K_VAR_BLUR, DOF_K_MEDIAN_RT, DOF_K_MIPS,
+    DOF_K_RECON, DOF_K_COMPOSITE, DOF_K_COUNT
 };
 /* For a history created with DOF_HIST_TIMING: synchronise `stream`, add the device
  * time (ms) each kernel took, summed over the frames recorded since the previous call

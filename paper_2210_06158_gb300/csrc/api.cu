@@ -253,8 +253,9 @@ extern "C" int dof_scene_info(const DofScene *s, DofSceneInfo *info) {
     if (!s || !info) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_scene_info: null argument");
     info->n_tris = s->n_tris;
     info->n_nodes = s->n_nodes;
+    info->n_large = s->n_large;
     info->depth = s->depth;
-    info->stack_limit = 64;
+    info->stack_limit = kTraversalStack;
     info->device_bytes = s->bytes;
     for (int k = 0; k < 3; k++) { info->bounds_lo[k] = s->lo[k]; info->bounds_hi[k] = s->hi[k]; }
     return DOF_OK;
@@ -264,7 +265,8 @@ static SceneDev scene_dev(const DofScene *s) {
     SceneDev d;
     d.nodes = s->nodes;
     d.tris = s->tris;
-    d.n_tris = (int)s->n_tris;
+    d.n_tris = (int)s->n_tree;
+    d.n_large = (int)s->n_large;
     return d;
 }
 
@@ -305,7 +307,9 @@ static void history_free(DofHistory *h) {
     dof_free(c, h->pp_med, 16 * N); dof_free(c, h->n_h, 16 * N);
     dof_free(c, h->z_h, 4 * N); dof_free(c, h->xn, 4 * N); dof_free(c, h->xf, 4 * N);
     dof_free(c, h->tiles, 8 * T); dof_free(c, h->tiles_dil, 8 * T);
-    dof_free(c, h->nrays, 4 * N); dof_free(c, h->queue, 4 * N); dof_free(c, h->counters, 16);
+    dof_free(c, h->nrays, 4 * N); dof_free(c, h->queue, 4 * N); dof_free(c, h->counters, 32);
+    dof_free(c, h->first_ray, 4 * N); dof_free(c, h->ray_pix, 4 * N * h->max_rays);
+    dof_free(c, h->hits, 8 * N * h->max_rays);
     dof_free(c, h->ray_prim, 4 * N * h->max_rays);
     dof_free(c, h->rt, 64 * N); dof_free(c, h->crt, 16 * N); dof_free(c, h->rt_med, 16 * N);
     dof_free(c, h->recon, 16 * N); dof_free(c, h->ct, 4 * N); dof_free(c, h->var, 4 * N);
@@ -352,7 +356,9 @@ extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, 
     A((void **)&h->pp_med, 16 * N); A((void **)&h->n_h, 16 * N);
     A((void **)&h->z_h, 4 * N); A((void **)&h->xn, 4 * N); A((void **)&h->xf, 4 * N);
     A((void **)&h->tiles, 8 * T); A((void **)&h->tiles_dil, 8 * T);
-    A((void **)&h->nrays, 4 * N); A((void **)&h->queue, 4 * N); A((void **)&h->counters, 16);
+    A((void **)&h->nrays, 4 * N); A((void **)&h->queue, 4 * N); A((void **)&h->counters, 32);
+    A((void **)&h->first_ray, 4 * N); A((void **)&h->ray_pix, 4 * N * max_rays);
+    A((void **)&h->hits, 8 * N * max_rays);
     if (flags & DOF_HIST_RECORD_RAYS) A((void **)&h->ray_prim, 4 * N * max_rays);
     A((void **)&h->rt, 64 * N); A((void **)&h->crt, 16 * N); A((void **)&h->rt_med, 16 * N);
     A((void **)&h->recon, 16 * N); A((void **)&h->ct, 4 * N); A((void **)&h->var, 4 * N);
@@ -372,7 +378,7 @@ extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, 
             if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->var_blur[k], 0, 4 * N), "history clear");
         }
         if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->xf, 0, 4 * N), "history clear");
-        if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->counters, 0, 16), "history clear");
+        if (rc == DOF_OK) rc = dof_cuda_check(cudaMemset(h->counters, 0, 32), "history clear");
         if (rc == DOF_OK && h->ray_prim) rc = dof_cuda_check(cudaMemset(h->ray_prim, 0xFF, 4 * N * max_rays), "clear");
     }
     if (rc == DOF_OK && (flags & DOF_HIST_TIMING)) {
@@ -428,6 +434,7 @@ extern "C" int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *g
     cudaStream_t st = (cudaStream_t)stream;
     cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
     rc = dof_cuda_check(cudaMemsetAsync(h->counters, 0, 3 * sizeof(uint32_t), st), "dof_frame counters");
+    if (rc == DOF_OK) rc = dof_cuda_check(cudaMemsetAsync(h->counters + 4, 0, 4 * sizeof(uint32_t), st), "dof_frame counters");
     if (rc) return rc;
     if (h->ev && h->ev_used < kTimingSlots) {
         // a kernel that is not launched this frame gets an event right after its predecessor's
@@ -476,7 +483,7 @@ extern "C" int dof_kernel_times(DofHistory *h, void *stream, float *ms, uint32_t
 extern "C" int dof_frame_stats(DofHistory *h, void *stream, DofFrameStats *out) {
     if (!h || !out) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame_stats: null argument");
     DeviceGuard g(h->ctx->device);
-    uint32_t c[4];
+    uint32_t c[8];
     int rc = dof_cuda_check(cudaMemcpyAsync(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost, (cudaStream_t)stream),
                             "dof_frame_stats");
     if (rc == DOF_OK) rc = dof_cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "dof_frame_stats sync");
@@ -486,6 +493,8 @@ extern "C" int dof_frame_stats(DofHistory *h, void *stream, DofFrameStats *out) 
     out->rays = c[1];
     out->device_status = c[3] ? DOF_ERR_DEVICE_CHECK : DOF_OK;
     out->pad = 0;
+    out->node_visits = (uint64_t)c[4] | ((uint64_t)c[5] << 32);
+    out->tri_tests = (uint64_t)c[6] | ((uint64_t)c[7] << 32);
     return DOF_OK;
 }
 

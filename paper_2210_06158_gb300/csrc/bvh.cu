@@ -2,9 +2,10 @@
 // counts in its ray-trace time, Section 4.2).
 //
 // LBVH after Karras, "Maximizing Parallelism in the Construction of BVHs, Octrees,
-// and k-d Trees" (HPG 2012): 30-bit Morton codes of triangle centroids, a radix sort,
-// one thread per internal node to find its key range and split (ties between equal
-// codes broken by the sorted index, so the tree depth is at most 62), then a
+// and k-d Trees" (HPG 2012): 63-bit Morton codes of triangle centroids (21 bits per
+// axis: scenes with a ground plane hundreds of metres wide still resolve centimetre
+// detail), a radix sort, one thread per internal node to find its key range and
+// split (ties between equal codes broken by the sorted index), then a
 // bottom-up box refit in which the second thread to reach a node merges its two
 // children (atomic arrival counter, no waiting).  Nodes hold both child boxes so that
 // traversal fetches one node per step.
@@ -40,7 +41,7 @@ __global__ void k_centroids(const float *xyz, uint32_t n_verts, const uint32_t *
         float3 lo = make_float3(fminf(a.x, fminf(b.x, d.x)), fminf(a.y, fminf(b.y, d.y)), fminf(a.z, fminf(b.z, d.z)));
         float3 hi = make_float3(fmaxf(a.x, fmaxf(b.x, d.x)), fmaxf(a.y, fmaxf(b.y, d.y)), fmaxf(a.z, fmaxf(b.z, d.z)));
         c = make_float3(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z));
-        cen[t] = make_float4(c.x, c.y, c.z, 0.f);
+        cen[t] = make_float4(c.x, c.y, c.z, fmaxf(hi.x - lo.x, fmaxf(hi.y - lo.y, hi.z - lo.z)));
     }
     // block reduction of min/max through warp shuffles
     float v[6] = {c.x, c.y, c.z, c.x, c.y, c.z};
@@ -56,17 +57,59 @@ __global__ void k_centroids(const float *xyz, uint32_t n_verts, const uint32_t *
     }
 }
 
-__device__ __forceinline__ uint32_t expand10(uint32_t v) {
-    v = (v * 0x00010001u) & 0xFF0000FFu;
-    v = (v * 0x00000101u) & 0x0F00F00Fu;
-    v = (v * 0x00000011u) & 0xC30C30C3u;
-    v = (v * 0x00000005u) & 0x49249249u;
-    return v;
+// threshold of a "large" triangle: its largest box extent above 1/16 of the largest
+// centroid extent of the scene (a ground plane, a wall spanning the scene)
+__device__ __forceinline__ float big_threshold(const int *bounds) {
+    float e = 0.f;
+    for (int k = 0; k < 3; k++) e = fmaxf(e, float_of(bounds[3 + k]) - float_of(bounds[k]));
+    return e * (1.f / 16.f);
 }
 
-__global__ void k_morton(const float4 *cen, uint32_t n, const int *bounds, uint32_t *keys, uint32_t *vals) {
+// count the large triangles and the centroid bounds of the others
+__global__ void k_classify(const float4 *cen, uint32_t n, const int *bounds, int *n_big, int *small_bounds) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    float thr = big_threshold(bounds);
+    bool ok = t < n;
+    float4 c = ok ? cen[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    bool big = ok && c.w > thr;
+    bool small = ok && !big;
+    unsigned nb = __popc(__ballot_sync(0xffffffffu, big));
+    float v[6] = {c.x, c.y, c.z, c.x, c.y, c.z};
+    if (!small) { v[0] = v[1] = v[2] = INFINITY; v[3] = v[4] = v[5] = -INFINITY; }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 6; k++) {
+            float w = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = k < 3 ? fminf(v[k], w) : fmaxf(v[k], w);
+        }
+    if ((threadIdx.x & 31) == 0) {
+        if (nb) atomicAdd(n_big, (int)nb);
+        for (int k = 0; k < 3; k++) atomicMin(&small_bounds[k], ord_of(v[k]));
+        for (int k = 3; k < 6; k++) atomicMax(&small_bounds[k], ord_of(v[k]));
+    }
+}
+
+// spread the low 21 bits of v to every third bit
+__device__ __forceinline__ unsigned long long expand21(uint32_t v) {
+    unsigned long long x = v & 0x1fffffull;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+// Morton keys over the centroid bounds `bounds`; with separate_big, large triangles
+// (classified against `all_bounds`) get the key ~0 and sort after every other one
+__global__ void k_morton(const float4 *cen, uint32_t n, const int *bounds, const int *all_bounds, int separate_big,
+                         unsigned long long *keys, uint32_t *vals) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    vals[t] = t;
+    if (separate_big && cen[t].w > big_threshold(all_bounds)) {
+        keys[t] = ~0ull;
+        return;
+    }
     float lo[3], ext[3];
     for (int k = 0; k < 3; k++) {
         lo[k] = float_of(bounds[k]);
@@ -77,10 +120,9 @@ __global__ void k_morton(const float4 *cen, uint32_t n, const int *bounds, uint3
     uint32_t q[3];
     for (int k = 0; k < 3; k++) {
         float u = ext[k] > 0.f ? (p[k] - lo[k]) / ext[k] : 0.f;
-        q[k] = (uint32_t)fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
+        q[k] = (uint32_t)fminf(fmaxf(u * 2097152.f, 0.f), 2097151.f);
     }
-    keys[t] = (expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]);
-    vals[t] = t;
+    keys[t] = (expand21(q[0]) << 2) | (expand21(q[1]) << 1) | expand21(q[2]);
 }
 
 // sorted triangles: v0 (w = original id), v1, v2 (w = material)
@@ -98,16 +140,16 @@ __global__ void k_sorted_tris(const float *xyz, const uint32_t *idx, const uint3
 }
 
 // common-prefix length of sorted keys i and j, ties broken by index (Karras 2012)
-__device__ __forceinline__ int delta(const uint32_t *keys, int n, int i, int j) {
+__device__ __forceinline__ int delta(const unsigned long long *keys, int n, int i, int j) {
     if (j < 0 || j >= n) return -1;
-    uint32_t a = keys[i], b = keys[j];
-    if (a != b) return __clz(a ^ b);
-    return 32 + __clz(i ^ j);
+    unsigned long long a = keys[i], b = keys[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz(i ^ j);
 }
 
 // one thread per internal node: its range, split and children; parent links.
 // child refs: >= 0 internal, < 0 leaf ~k
-__global__ void k_karras(const uint32_t *keys, int n, int4 *child, int *parent_node, int *parent_leaf, int *bad) {
+__global__ void k_karras(const unsigned long long *keys, int n, int4 *child, int *parent_node, int *parent_leaf, int *bad) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -160,7 +202,7 @@ __global__ void k_refit(const float4 *tris, int n, const int4 *child, const int 
     __threadfence();
     int p = parent_leaf[k];
     for (int level = 0; p >= 0; level++) {
-        if (p >= n - 1 || level > 128) { atomicExch(bad, 3); return; }
+        if (p >= n - 1 || level > 160) { atomicExch(bad, 3); return; }
         if (atomicAdd(&arrivals[p], 1) == 0) return;   // the sibling finishes this node
         __threadfence();
         int4 ch = child[p];
@@ -205,19 +247,21 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
     int rc = DOF_OK;
     float4 *cen = nullptr;
     int *ibuf = nullptr;                    // bounds[6], bad, depth
-    uint32_t *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr;
+    unsigned long long *keys = nullptr, *keys2 = nullptr;
+    uint32_t *vals = nullptr, *vals2 = nullptr;
     int4 *child = nullptr;
     int *pnode = nullptr, *pleaf = nullptr, *arr = nullptr;
     float4 *blo = nullptr, *bhi = nullptr;
     void *tmp = nullptr;
     size_t tmp_bytes = 0;
-    int hbuf[8];
+    int hbuf[16];
+    int n_small = n, n_big = 0;
     auto ck = [&](cudaError_t e, const char *w) { if (rc == DOF_OK && e != cudaSuccess) rc = dof_cuda_check(e, w); };
     ck(cudaMalloc(&cen, sizeof(float4) * n), "bvh centroids");
-    ck(cudaMalloc(&ibuf, sizeof(int) * 8), "bvh scalars");
-    ck(cudaMalloc(&keys, sizeof(uint32_t) * n), "bvh keys");
+    ck(cudaMalloc(&ibuf, sizeof(int) * 16), "bvh scalars");
+    ck(cudaMalloc(&keys, sizeof(unsigned long long) * n), "bvh keys");
     ck(cudaMalloc(&vals, sizeof(uint32_t) * n), "bvh vals");
-    ck(cudaMalloc(&keys2, sizeof(uint32_t) * n), "bvh keys2");
+    ck(cudaMalloc(&keys2, sizeof(unsigned long long) * n), "bvh keys2");
     ck(cudaMalloc(&vals2, sizeof(uint32_t) * n), "bvh vals2");
     ck(cudaMalloc(&child, sizeof(int4) * (n > 1 ? n - 1 : 1)), "bvh children");
     ck(cudaMalloc(&pnode, sizeof(int) * (n > 1 ? n - 1 : 1)), "bvh parents");
@@ -227,23 +271,36 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
     ck(cudaMalloc(&bhi, sizeof(float4) * (2 * n)), "bvh boxes");
     if (rc != DOF_OK) goto done;
     {
-        int init[8] = {0x7FFFFFFF, 0x7FFFFFFF, 0x7FFFFFFF, (int)0x80000000, (int)0x80000000, (int)0x80000000, 0, 0};
+        // ibuf: [0..5] centroid bounds, [6] bad, [7] depth, [8] large count, [9..14] small bounds
+        const int lo_i = 0x7FFFFFFF, hi_i = (int)0x80000000;
+        int init[16] = {lo_i, lo_i, lo_i, hi_i, hi_i, hi_i, 0, 0, 0, lo_i, lo_i, lo_i, hi_i, hi_i, hi_i, 0};
         ck(cudaMemcpyAsync(ibuf, init, sizeof(init), cudaMemcpyHostToDevice, st), "bvh init");
         k_centroids<<<blocks_for(n, B), B, 0, st>>>(d_xyz, n_verts, d_idx, (uint32_t)n, cen, ibuf, ibuf + 6);
-        k_morton<<<blocks_for(n, B), B, 0, st>>>(cen, (uint32_t)n, ibuf, keys, vals);
-        ck(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, vals, vals2, n, 0, 30, st), "sort size");
+        k_classify<<<blocks_for(n, B), B, 0, st>>>(cen, (uint32_t)n, ibuf, ibuf + 8, ibuf + 9);
+        ck(cudaMemcpyAsync(hbuf, ibuf, sizeof(hbuf), cudaMemcpyDeviceToHost, st), "bvh readback");
+        ck(cudaStreamSynchronize(st), "bvh classify");
+        if (rc != DOF_OK) goto done;
+        // large triangles stay out of the tree (tested directly by every ray) when there
+        // are few of them and at least one other triangle
+        int separate = hbuf[8] > 0 && hbuf[8] <= kMaxLargeTris && hbuf[8] < n;
+        n_big = separate ? hbuf[8] : 0;
+        n_small = n - n_big;
+        k_morton<<<blocks_for(n, B), B, 0, st>>>(cen, (uint32_t)n, separate ? ibuf + 9 : ibuf, ibuf, separate, keys,
+                                                 vals);
+        ck(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, vals, vals2, n, 0, 64, st), "sort size");
         ck(cudaMalloc(&tmp, tmp_bytes ? tmp_bytes : 16), "sort temp");
         if (rc != DOF_OK) goto done;
-        ck(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys2, vals, vals2, n, 0, 30, st), "sort");
+        ck(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys2, vals, vals2, n, 0, 64, st), "sort");
         k_sorted_tris<<<blocks_for(n, B), B, 0, st>>>(d_xyz, d_idx, d_mat, (uint32_t)n, n_verts, vals2, s->tris);
-        if (n >= 2) {
-            ck(cudaMemsetAsync(pleaf, 0xFF, sizeof(int) * n, st), "memset");
-            ck(cudaMemsetAsync(arr, 0, sizeof(int) * (n - 1), st), "memset");
-            ck(cudaMemsetAsync(s->nodes, 0xFF, sizeof(BvhNode) * (n - 1), st), "memset");
-            k_karras<<<blocks_for(n - 1, B), B, 0, st>>>(keys2, n, child, pnode, pleaf, ibuf + 5 + 1);
-            k_refit<<<blocks_for(n, B), B, 0, st>>>(s->tris, n, child, pnode, pleaf, blo, bhi, arr, s->nodes,
+        const int m = n_small;
+        if (m >= 2) {
+            ck(cudaMemsetAsync(pleaf, 0xFF, sizeof(int) * m, st), "memset");
+            ck(cudaMemsetAsync(arr, 0, sizeof(int) * (m - 1), st), "memset");
+            ck(cudaMemsetAsync(s->nodes, 0xFF, sizeof(BvhNode) * (m - 1), st), "memset");
+            k_karras<<<blocks_for(m - 1, B), B, 0, st>>>(keys2, m, child, pnode, pleaf, ibuf + 6);
+            k_refit<<<blocks_for(m, B), B, 0, st>>>(s->tris, m, child, pnode, pleaf, blo, bhi, arr, s->nodes,
                                                     ibuf + 6);
-            k_depth<<<blocks_for(n, B), B, 0, st>>>(n, pnode, pleaf, ibuf + 7);
+            k_depth<<<blocks_for(m, B), B, 0, st>>>(m, pnode, pleaf, ibuf + 7);
         }
         ck(cudaGetLastError(), "bvh kernels");
         ck(cudaMemcpyAsync(hbuf, ibuf, sizeof(hbuf), cudaMemcpyDeviceToHost, st), "bvh readback");
@@ -251,10 +308,16 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
         if (rc != DOF_OK) goto done;
         if (hbuf[6] == 1) { rc = dof_set_error(DOF_ERR_INVALID_ARG, "dof_scene_upload: vertex index out of range"); goto done; }
         if (hbuf[6]) { rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "dof_scene_upload: BVH hierarchy check failed (%d)", hbuf[6]); goto done; }
-        s->depth = n >= 2 ? (uint32_t)hbuf[7] : 1;
-        if (s->depth > 64) { rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "BVH depth %u exceeds the traversal stack", s->depth); goto done; }
-        // scene bounds from the triangle boxes (root box)
-        if (n >= 2) {
+        s->depth = m >= 2 ? (uint32_t)hbuf[7] : 1;
+        s->n_tree = (uint32_t)m;
+        s->n_large = (uint32_t)n_big;
+        s->n_nodes = m >= 2 ? (uint32_t)(m - 1) : 0;
+        if (s->depth > kTraversalStack) {
+            rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "BVH depth %u exceeds the traversal stack", s->depth);
+            goto done;
+        }
+        // bounds of the tree's triangles (root box)
+        if (m >= 2) {
             float4 lo, hi;
             ck(cudaMemcpy(&lo, blo, sizeof(float4), cudaMemcpyDeviceToHost), "bounds");
             ck(cudaMemcpy(&hi, bhi, sizeof(float4), cudaMemcpyDeviceToHost), "bounds");

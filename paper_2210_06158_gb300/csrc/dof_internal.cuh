@@ -56,8 +56,12 @@ struct __align__(16) BvhNode {
 struct SceneDev {
     const BvhNode *nodes;        // n_tris - 1 internal nodes (root = 0) when n_tris >= 2
     const float4 *tris;          // 3 float4 per sorted triangle: v0 (w = prim id bits), v1, v2 (w = material bits)
-    int n_tris;
+    int n_tris;                  // triangles in the tree (sorted indices 0 .. n_tris-1)
+    int n_large;                 // large triangles after them, tested directly by every ray
 };
+
+// at most this many large triangles are kept out of the tree (see bvh.cu)
+constexpr int kMaxLargeTris = 64;
 
 // ---------------------------------------------------------------------------
 // host objects
@@ -73,6 +77,7 @@ struct DofCtx {
 struct DofScene {
     DofCtx *ctx;
     uint32_t n_tris, n_nodes, depth;
+    uint32_t n_tree, n_large;      // triangles in the tree / tested directly
     BvhNode *nodes;
     float4 *tris;
     size_t bytes;
@@ -92,7 +97,11 @@ struct DofHistory {
     float2 *tiles, *tiles_dil;
     int32_t *nrays;
     uint32_t *queue;               // masked pixel indices
-    uint32_t *counters;            // [0] queue length, [1] rays, [2] work cursor, [3] device status
+    uint32_t *first_ray;           // per pixel: index of its first ray in the ray list
+    uint32_t *ray_pix;             // ray list: pixel of each ray (N * max_rays)
+    int2 *hits;                    // per ray: (sorted triangle index or -1, t bits)
+    uint32_t *counters;            // [0] queue length, [1] rays, [2] work cursor, [3] device status,
+                                   // [4..5] node visits (u64), [6..7] triangle tests (u64)
     int32_t *ray_prim;
     float4 *rt;                    // 4 planes of N
     float4 *crt, *rt_med, *recon;
@@ -110,6 +119,9 @@ struct DofHistory {
 };
 
 constexpr int kTimingSlots = 64;
+// traversal stack entries; the LBVH over 63-bit keys with index tie-breaks is at most
+// 63 + 32 levels deep, and uploads whose tree is deeper than this are rejected
+constexpr int kTraversalStack = 96;
 
 // record the event that closes kernel `k` of the current frame (no-op without timing)
 inline void tmark(DofHistory *h, int k, cudaStream_t st) {

@@ -59,6 +59,20 @@ __device__ __forceinline__ void bilinear4z(const float4 *__restrict__ img, const
     zo = w00 * __ldg(&z[qa + xa]) + w10 * __ldg(&z[qa + xb]) + w01 * __ldg(&z[qb + xa]) + w11 * __ldg(&z[qb + xb]);
 }
 
+// Bilinear fetch of (rgb, rho) and z without clamping: the caller guarantees that
+// floor(x), floor(y) and their +1 neighbours lie inside the image.
+__device__ __forceinline__ void bilinear4z_interior(const float4 *__restrict__ img, const float *__restrict__ z, int w,
+                                                    float x, float y, float4 &out, float &zo) {
+    float xf = floorf(x), yf = floorf(y);
+    float fx = x - xf, fy = y - yf;
+    int q = __float2int_rz(yf) * w + __float2int_rz(xf);
+    const float4 *p = img + q;
+    const float *pz = z + q;
+    float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+    out = f4fma(w11, __ldg(p + w + 1), f4fma(w01, __ldg(p + w), f4fma(w10, __ldg(p + 1), f4scale(w00, __ldg(p)))));
+    zo = w00 * __ldg(pz) + w10 * __ldg(pz + 1) + w01 * __ldg(pz + w) + w11 * __ldg(pz + w + 1);
+}
+
 __device__ __forceinline__ void cx4(float4 &a, float4 &b) {
     float4 lo = make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
     float4 hi = make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));

@@ -87,18 +87,13 @@ __global__ void k_prefilter(int W2, int H2, DevParams p, const float4 *__restric
 
 // A4: 81-tap main filter (Eq. 1).  Rings k = 1..4 of 8k taps at radius kR/4 of the
 // dilated max CoC R; foreground/background weights with the coverage ramp D and
-// sampleAlpha; normalised weighted sum plus the share of bright samples.
-__global__ void __launch_bounds__(256) k_main_filter(int W2, int H2, DevParams p, const float4 *__restrict__ pre,
-                                                     const float *__restrict__ z_h, const float2 *__restrict__ dil,
-                                                     float4 *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= W2 || j >= H2) return;
-    size_t q = (size_t)j * W2 + i;
-    float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
-    float z0 = __ldg(&z_h[q]);
-    float r0 = fabsf(__ldg(&pre[q]).w);
+// sampleAlpha; normalised weighted sum plus the share of bright samples.  Blocks whose
+// whole footprint (+-rmax + 1) lies inside the image take taps without index clamping.
+template <bool CLAMP>
+__device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const DevParams &p, const float4 *__restrict__ pre,
+                                          const float *__restrict__ z_h, float R, float z0, float r0, float &ax,
+                                          float &ay, float &az, float &bright, float &wsum) {
     const float kInvSqrtPi = 0.56418958354775628f, kInvPi = 0.31830988618379067f;
-    float ax = 0.f, ay = 0.f, az = 0.f, bright = 0.f, wsum = 0.f;
 #pragma unroll 3
     for (int t = 0; t < 81; t++) {
         float3 u = c_ring81[t];
@@ -106,11 +101,12 @@ __global__ void __launch_bounds__(256) k_main_filter(int W2, int H2, DevParams p
         float x = i + dist * u.x, y = j + dist * u.y;
         float4 s;
         float zi;
-        bilinear4z(pre, z_h, W2, H2, x, y, s, zi);
+        if (CLAMP) bilinear4z(pre, z_h, W2, H2, x, y, s, zi);
+        else bilinear4z_interior(pre, z_h, W2, x, y, s, zi);
         float ri = fabsf(s.w);
         float wf = sat((z0 - zi) * p.inv_depth_range);
         float rr = fmaxf(ri, kInvSqrtPi);
-        float a = kInvPi / (rr * rr);
+        float a = __fdividef(kInvPi, rr * rr);
         float Df = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
         float Db = sat((fminf(ri, r0) - dist) * p.inv_cover_ramp + 0.5f);
         float W = (wf * Df + (1.f - wf) * Db) * a;
@@ -118,6 +114,24 @@ __global__ void __launch_bounds__(256) k_main_filter(int W2, int H2, DevParams p
         bright += W * sat((lum709(s.x, s.y, s.z) - p.bright_lum) * p.inv_bright_ramp);
         wsum += W;
     }
+}
+
+__global__ void __launch_bounds__(256) k_main_filter(int W2, int H2, DevParams p, const float4 *__restrict__ pre,
+                                                     const float *__restrict__ z_h, const float2 *__restrict__ dil,
+                                                     float4 *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int reach = (int)ceilf(p.rmax_hpx) + 2;
+    const int bx = blockIdx.x * blockDim.x, by = blockIdx.y * blockDim.y;
+    const bool interior = bx - reach >= 0 && by - reach >= 0 && bx + (int)blockDim.x + reach < W2 &&
+                          by + (int)blockDim.y + reach < H2;
+    if (i >= W2 || j >= H2) return;
+    size_t q = (size_t)j * W2 + i;
+    float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
+    float z0 = __ldg(&z_h[q]);
+    float r0 = fabsf(__ldg(&pre[q]).w);
+    float ax = 0.f, ay = 0.f, az = 0.f, bright = 0.f, wsum = 0.f;
+    if (interior) main_taps<false>(i, j, W2, H2, p, pre, z_h, R, z0, r0, ax, ay, az, bright, wsum);
+    else main_taps<true>(i, j, W2, H2, p, pre, z_h, R, z0, r0, ax, ay, az, bright, wsum);
     float r = 1.f / wsum;
     out[q] = make_float4(ax * r, ay * r, az * r, bright * r);
 }

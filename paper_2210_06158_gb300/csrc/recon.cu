@@ -79,6 +79,7 @@ struct Mips {
     int w[4], h[4], L;
 };
 
+template <bool CLAMP>
 __device__ __forceinline__ void bilin_mip(const Mips &M, int l, float x, float y, float4 &a, float2 &b) {
     float s = 1.f / (float)(1 << l);
     float xl = (x + 0.5f) * s - 0.5f, yl = (y + 0.5f) * s - 0.5f;
@@ -86,23 +87,57 @@ __device__ __forceinline__ void bilin_mip(const Mips &M, int l, float x, float y
     float xf = floorf(xl), yf = floorf(yl);
     float fx = xl - xf, fy = yl - yf;
     int x0 = (int)xf, y0 = (int)yf;
-    int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
-    int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
     float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
-    size_t qa = (size_t)ya * w, qb = (size_t)yb * w;
-    a = f4fma(w11, __ldg(&M.m0[l][qb + xb]), f4fma(w01, __ldg(&M.m0[l][qb + xa]),
-              f4fma(w10, __ldg(&M.m0[l][qa + xb]), f4scale(w00, __ldg(&M.m0[l][qa + xa])))));
-    float2 c00 = __ldg(&M.m1[l][qa + xa]), c10 = __ldg(&M.m1[l][qa + xb]);
-    float2 c01 = __ldg(&M.m1[l][qb + xa]), c11 = __ldg(&M.m1[l][qb + xb]);
+    const float4 *m0 = M.m0[l];
+    const float2 *m1 = M.m1[l];
+    int qa, qb, xa, xb;
+    if (CLAMP) {
+        xa = min(max(x0, 0), w - 1); xb = min(max(x0 + 1, 0), w - 1);
+        int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
+        qa = ya * w; qb = yb * w;
+    } else {
+        xa = x0; xb = x0 + 1;
+        qa = y0 * w; qb = qa + w;
+    }
+    a = f4fma(w11, __ldg(&m0[qb + xb]), f4fma(w01, __ldg(&m0[qb + xa]),
+              f4fma(w10, __ldg(&m0[qa + xb]), f4scale(w00, __ldg(&m0[qa + xa])))));
+    float2 c00 = __ldg(&m1[qa + xa]), c10 = __ldg(&m1[qa + xb]);
+    float2 c01 = __ldg(&m1[qb + xa]), c11 = __ldg(&m1[qb + xb]);
     b = make_float2(w00 * c00.x + w10 * c10.x + w01 * c01.x + w11 * c11.x,
                     w00 * c00.y + w10 * c10.y + w01 * c01.y + w11 * c11.y);
 }
 
-// A11: reconstruction
+template <bool CLAMP>
+__device__ __forceinline__ void recon_taps(const Mips &M, int i, int j, float R, int l0, int l1, float t,
+                                           float inv_ramp, float4 &num, float &den) {
+#pragma unroll 3
+    for (int k = 0; k < 81; k++) {
+        float3 u = c_ring81[k];
+        float dist = u.z * R;
+        float x = i + dist * u.x, y = j + dist * u.y;
+        float4 a0, a1;
+        float2 b0, b1;
+        bilin_mip<CLAMP>(M, l0, x, y, a0, b0);
+        bilin_mip<CLAMP>(M, l1, x, y, a1, b1);
+        float4 S = f4fma(t, a1, f4scale(1.f - t, a0));
+        float Sc = (1.f - t) * b0.x + t * b1.x, Sv = (1.f - t) * b0.y + t * b1.y;
+        float ri = Sv > 0.f ? __fdividef(Sc, Sv) : 0.f;
+        float D = sat((ri - dist) * inv_ramp + 0.5f);
+        num = f4fma(D, S, num);
+        den += D * Sv;
+    }
+}
+
+// A11: reconstruction.  Blocks whose footprint (+-rmax + 2, at every level) lies
+// inside the image take taps without index clamping.
 __global__ void __launch_bounds__(256) k_recon(int W2, int H2, DevParams p, Mips M, const float4 *__restrict__ med,
                                                const float *__restrict__ ct, const float *__restrict__ var_blur,
                                                const int32_t *__restrict__ nrays, float4 *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int reach = (int)ceilf(p.rmax_hpx) + (2 << (M.L - 1)) + 2;
+    const int bx = blockIdx.x * blockDim.x, by = blockIdx.y * blockDim.y;
+    const bool interior = bx - reach >= 0 && by - reach >= 0 && bx + (int)blockDim.x + reach < W2 &&
+                          by + (int)blockDim.y + reach < H2;
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
     if (__ldg(&nrays[q]) <= 0) { out[q] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
@@ -114,22 +149,8 @@ __global__ void __launch_bounds__(256) k_recon(int W2, int H2, DevParams p, Mips
     int l1 = min(l0 + 1, M.L - 1);
     float4 num = make_float4(0.f, 0.f, 0.f, 0.f);
     float den = 0.f;
-#pragma unroll 3
-    for (int k = 0; k < 81; k++) {
-        float3 u = c_ring81[k];
-        float dist = u.z * R;
-        float x = i + dist * u.x, y = j + dist * u.y;
-        float4 a0, a1;
-        float2 b0, b1;
-        bilin_mip(M, l0, x, y, a0, b0);
-        bilin_mip(M, l1, x, y, a1, b1);
-        float4 S = f4fma(t, a1, f4scale(1.f - t, a0));
-        float Sc = (1.f - t) * b0.x + t * b1.x, Sv = (1.f - t) * b0.y + t * b1.y;
-        float ri = Sv > 0.f ? Sc / Sv : 0.f;
-        float D = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
-        num = f4fma(D, S, num);
-        den += D * Sv;
-    }
+    if (interior) recon_taps<false>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
+    else recon_taps<true>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
     float4 o = __ldg(&med[q]);
     float b = fminf(fmaxf(__ldg(&var_blur[q]) * p.var_w_recon, 0.f), p.b_max);
     float4 f = den > 0.f ? f4scale(1.f / den, num) : o;

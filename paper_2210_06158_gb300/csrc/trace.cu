@@ -6,7 +6,7 @@
 
 namespace {
 
-constexpr int kStack = 64;   // >= the LBVH depth bound (checked at upload)
+constexpr int kStack = kTraversalStack;   // >= the tree depth (checked at upload)
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC 2011); only the first two output words are used
@@ -108,8 +108,20 @@ struct HitRec {
 // closest hit = lexicographic min of (t, prim id); boxes with entry == best are kept.
 // A reference outside the tree, a full stack or more steps than a valid tree can take
 // set the status word and end the query (no fault, no endless loop).
-__device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status) {
+__device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status, uint32_t &n_visit,
+                              uint32_t &n_tests) {
     HitRec h{INFINITY, -1, -1};
+    // large triangles first: their hits bound the tree traversal
+    for (int k = sc.n_tris; k < sc.n_tris + sc.n_large; k++) {
+        n_tests++;
+        const float4 *tp = sc.tris + 3 * (size_t)k;
+        float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+        float t = tri_hit(r, v0, v1, v2);
+        if (t > 0.f) {
+            int prim = __float_as_int(v0.w);
+            if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
+        }
+    }
     if (sc.n_tris <= 0) return h;
     int stack[kStack];
     int sp = 0;
@@ -122,6 +134,7 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
             break;
         }
         if (node >= 0) {
+            n_visit++;
             const float4 *np = reinterpret_cast<const float4 *>(sc.nodes + node);
             float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
             int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
@@ -138,6 +151,7 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
             if (h0) { node = ref.x; continue; }
             if (h1) { node = ref.y; continue; }
         } else {
+            n_tests++;
             int k = ~node;
             const float4 *tp = sc.tris + 3 * (size_t)k;
             float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
@@ -190,7 +204,8 @@ __global__ void k_primary(DevCam cam, DevParams p, SceneDev sc, float4 *color, f
     size_t q = (size_t)j * cam.W + i;
     float3 d = pixel_dir(cam, i + 0.5f, j + 0.5f);
     Ray r = make_ray(cam.O, d);
-    HitRec h = closest_hit(sc, r, status);
+    uint32_t nv = 0, nt = 0;
+    HitRec h = closest_hit(sc, r, status, nv, nt);
     if (prim) prim[q] = h.prim;
     if (h.prim < 0) {
         color[q] = make_float4(p.sky.x, p.sky.y, p.sky.z, 1.f);
@@ -257,15 +272,19 @@ __global__ void k_edges(int W2, int H2, const float4 *zn, const float *var_prev,
 }
 
 // ---------------------------------------------------------------------------
-// A6: mask, ray count, warp-aggregated compaction of masked pixels
+// A6: mask, ray count, and compaction into a pixel queue and a flat ray list
 // ---------------------------------------------------------------------------
-__global__ void k_mask_compact(int W2, int H2, DevParams p, const float2 *tiles_dil, const float *xf,
-                               int32_t *nrays, uint32_t *queue, uint32_t *counters) {
+// Per block (32 x 8 pixels, one warp per row) one atomic reserves room for the
+// block's masked pixels (queue) and their rays (ray list); inside the block the
+// order is raster order, so neighbouring rays stay neighbours in the list.
+__global__ void __launch_bounds__(256) k_mask_compact(int W2, int H2, DevParams p, const float2 *tiles_dil,
+                                                      const float *xf, int32_t *nrays, uint32_t *queue,
+                                                      uint32_t *first_ray, uint32_t *ray_pix, uint32_t *counters) {
     int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    bool inside = i < W2 && j < H2;
+    const unsigned lane = threadIdx.x, warp = threadIdx.y;
     int n = 0;
     uint32_t q = 0;
-    if (inside) {
+    if (i < W2 && j < H2) {
         q = (uint32_t)j * W2 + i;
         float near_max = __ldg(&tiles_dil[(j >> 3) * p.tiles_w + (i >> 3)]).x;
         if (near_max >= p.mask_near_hpx) {
@@ -274,89 +293,230 @@ __global__ void k_mask_compact(int W2, int H2, DevParams p, const float2 *tiles_
         }
         nrays[q] = n;
     }
-    unsigned lane = threadIdx.x + threadIdx.y * blockDim.x;
-    lane &= 31;
-    unsigned ball = __ballot_sync(0xffffffffu, n > 0);
-    int rays = n;
-    for (int o = 16; o > 0; o >>= 1) rays += __shfl_xor_sync(0xffffffffu, rays, o);
-    uint32_t base = 0;
-    if (lane == 0 && ball) {
-        base = atomicAdd(&counters[0], (uint32_t)__popc(ball));
-        atomicAdd(&counters[1], (uint32_t)rays);
+    // warp: inclusive prefix of the ray counts, ballot of the masked pixels
+    int incl = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += v;
     }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (n > 0) queue[base + __popc(ball & ((1u << lane) - 1u))] = q;
+    unsigned ball = __ballot_sync(0xffffffffu, n > 0);
+    __shared__ uint32_t w_pix[8], w_ray[8], b_pix, b_ray;
+    if (lane == 31) { w_pix[warp] = __popc(ball); w_ray[warp] = (uint32_t)incl; }
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        uint32_t tp = 0, tr = 0;
+        for (int w = 0; w < 8; w++) {
+            uint32_t a = w_pix[w], b = w_ray[w];
+            w_pix[w] = tp; w_ray[w] = tr;
+            tp += a; tr += b;
+        }
+        // queue length and ray count share one 64-bit word (rays < 2^32 by the size limits)
+        unsigned long long old = 0;
+        if (tp) old = atomicAdd(reinterpret_cast<unsigned long long *>(counters),
+                                ((unsigned long long)tr << 32) | tp);
+        b_pix = (uint32_t)old;
+        b_ray = (uint32_t)(old >> 32);
+    }
+    __syncthreads();
+    if (n > 0) {
+        queue[b_pix + w_pix[warp] + __popc(ball & ((1u << lane) - 1u))] = q;
+        uint32_t f = b_ray + w_ray[warp] + (uint32_t)(incl - n);
+        first_ray[q] = f;
+        for (int s = 0; s < n; s++) ray_pix[f + s] = q;
+    }
 }
 
 // ---------------------------------------------------------------------------
-// A8: persistent thin-lens ray kernel (one lane per masked pixel, its rays in
-// sample order; warps fetch 32 queue entries at a time)
+// A8: thin-lens rays (Section 3.2.2)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_trace(DevCam cam, DevParams p, SceneDev sc, const uint32_t *queue,
-                                               const int32_t *nrays, uint32_t *counters, float4 *rt,
-                                               int32_t *ray_prim, int max_rays) {
-    const unsigned lane = threadIdx.x & 31;
-    const uint32_t count = *((volatile uint32_t *)&counters[0]);
-    const size_t N = (size_t)cam.W2 * cam.H2;
-    const float inv_sqrt2 = 0.70710678118654752f;
+// The ray of half-resolution pixel q and lens sample s: direction through the pixel
+// and the lens centre meets the focus plane at Pf; Philox(counter = (q, s, frame, 0),
+// key = (seed, session)) gives the lens point.  Not inlined, so that the tracer and the
+// shader compute bit-identical rays.
+__device__ __noinline__ void lens_ray(const DevCam &cam, const DevParams &p, uint32_t q, int s, float3 &L,
+                                      float3 &dir) {
+    int i = (int)(q % (uint32_t)cam.W2), j = (int)(q / (uint32_t)cam.W2);
+    float3 dp = pixel_dir(cam, 2.f * i + 1.f, 2.f * j + 1.f);
+    float tf = cam.d / dot(dp, cam.F);
+    float3 Pf = cam.O + tf * dp;
+    unsigned long long x0, x1;
+    philox2(q, (unsigned long long)s, cam.frame, 0ull, p.seed, p.session, x0, x1);
+    float u1 = (float)(x0 >> 40) * 5.9604644775390625e-8f;
+    float u2 = (float)(x1 >> 40) * 5.9604644775390625e-8f;
+    float rr = cam.lens_r * sqrtf(u1), sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    float lx = rr * cs, ly = rr * sn;
+    L = cam.O + lx * cam.R + ly * cam.U;
+    dir = normalize(Pf - L);
+}
+
+constexpr int kRefillIdle = 8;    // refill a warp's idle lanes once this many are idle
+constexpr int kStepsPerRound = 16;
+
+// Persistent tracer, one ray per lane (Aila and Laine 2009, persistent threads with
+// dynamic fetch): lanes whose ray has finished take new rays from the ray list when
+// enough of the warp is idle, so divergent rays do not hold the warp.  Writes the
+// closest hit of each ray: (sorted triangle index or -1, t).
+__global__ void __launch_bounds__(128) k_trace_rays(DevCam cam, DevParams p, SceneDev sc, const uint32_t *ray_pix,
+                                                    const uint32_t *first_ray, uint32_t *counters, int2 *hits) {
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    const uint32_t total = *((volatile uint32_t *)&counters[1]);
+    const int n_nodes = sc.n_tris - 1;
+    const long long max_steps = 4ll * sc.n_tris + 64;
+    uint32_t *status = &counters[3];
+    uint32_t n_visit = 0, n_tests = 0;
+    bool have = false, exhausted = false;
+    uint32_t r = 0;
+    Ray ray;
+    HitRec h{INFINITY, -1, -1};
+    int node = 0, sp = 0;
+    long long steps = 0;
+    int stack[kStack];
     while (true) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&counters[2], 32u);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= count) break;
-        uint32_t e = base + lane;
-        if (e >= count) continue;   // base < count is warp-uniform: every lane reaches the next fetch
-        uint32_t q = queue[e];
-        int n = nrays[q];
-        int i = (int)(q % (uint32_t)cam.W2), j = (int)(q / (uint32_t)cam.W2);
-        float3 dp = pixel_dir(cam, 2.f * i + 1.f, 2.f * j + 1.f);
-        float tf = cam.d / dot(dp, cam.F);
-        float3 Pf = cam.O + tf * dp;
-        float Sw = 0.f, Bn = 0.f, Bf = 0.f, Fw = 0.f;
-        float3 An = make_float3(0.f, 0.f, 0.f), Af = An, Pfar = An;
-        for (int s = 0; s < n; s++) {
-            unsigned long long x0, x1;
-            philox2(q, (unsigned long long)s, cam.frame, 0ull, p.seed, p.session, x0, x1);
-            float u1 = (float)(x0 >> 40) * 5.9604644775390625e-8f;
-            float u2 = (float)(x1 >> 40) * 5.9604644775390625e-8f;
-            float rr = cam.lens_r * sqrtf(u1), sn, cs;
-            sincospif(2.f * u2, &sn, &cs);
-            float lx = rr * cs, ly = rr * sn;
-            float3 L = cam.O + lx * cam.R + ly * cam.U;
-            float3 dir = normalize(Pf - L);
-            Ray r = make_ray(L, dir);
-            HitRec h = closest_hit(sc, r, &counters[3]);
-            float3 col;
-            float z;
-            if (h.prim >= 0) {
-                float3 nrm;
-                col = shade(p, sc, h, dir, nrm);
-                z = fminf(h.t * dot(dir, cam.F), p.z_far);
-            } else {
-                col = p.sky;
-                z = p.z_far;
+        unsigned idle = __ballot_sync(0xffffffffu, !have);
+        if (idle == 0xffffffffu || (!exhausted && __popc(idle) >= kRefillIdle)) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&counters[2], (uint32_t)__popc(idle));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= total) exhausted = true;
+            if (!have) {
+                uint32_t mine = base + __popc(idle & lt);
+                if (mine < total) {
+                    r = mine;
+                    uint32_t q = __ldg(&ray_pix[r]);
+                    int s = (int)(r - __ldg(&first_ray[q]));
+                    float3 L, dir;
+                    lens_ray(cam, p, q, s, L, dir);
+                    ray = make_ray(L, dir);
+                    h = HitRec{INFINITY, -1, -1};
+                    for (int k = sc.n_tris; k < sc.n_tris + sc.n_large; k++) {
+                        n_tests++;
+                        const float4 *tp = sc.tris + 3 * (size_t)k;
+                        float t = tri_hit(ray, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
+                        if (t > 0.f) {
+                            int prim = __float_as_int(__ldg(tp).w);
+                            if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
+                        }
+                    }
+                    node = sc.n_tris >= 2 ? 0 : ~0;
+                    sp = 0;
+                    steps = 0;
+                    have = sc.n_tris > 0;
+                    if (!have) hits[r] = make_int2(h.k, __float_as_int(h.t));
+                }
             }
-            float c = coc_of(cam, z);
-            float rho = fabsf(fminf(fmaxf(0.25f * c, -p.rmax_hpx), p.rmax_hpx));
-            float w = sat(-c * inv_sqrt2);
-            if (ray_prim && s < max_rays) ray_prim[(size_t)q * max_rays + s] = h.prim;
-            Sw += w;
-            An = An + w * col;
-            Af = Af + (1.f - w) * col;
-            Bn += w * rho;
-            Bf += (1.f - w) * rho;
-            if (h.prim >= 0) {
-                Pfar = Pfar + (1.f - w) * (L + h.t * dir);
-                Fw += 1.f - w;
+            if (__ballot_sync(0xffffffffu, have) == 0 && exhausted) break;
+        }
+        if (!have) continue;
+        for (int it = 0; it < kStepsPerRound; it++) {
+            bool done = false;
+            if (++steps > max_steps || node >= n_nodes || (node < 0 && ~node >= sc.n_tris)) {
+                atomicOr(status, 2u);
+                done = true;
+            } else if (node >= 0) {
+                n_visit++;
+                const float4 *np = reinterpret_cast<const float4 *>(sc.nodes + node);
+                float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+                int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
+                float t0, t1;
+                bool h0 = box_hit(ray, make_float3(a.x, a.y, a.z), make_float3(a.w, b.x, b.y), h.t, t0);
+                bool h1 = box_hit(ray, make_float3(b.z, b.w, c.x), make_float3(c.y, c.z, c.w), h.t, t1);
+                if (h0 && h1) {
+                    int nearc = t0 <= t1 ? ref.x : ref.y, farc = t0 <= t1 ? ref.y : ref.x;
+                    if (sp < kStack) stack[sp++] = farc;
+                    else atomicOr(status, 1u);
+                    node = nearc;
+                    continue;
+                }
+                if (h0) { node = ref.x; continue; }
+                if (h1) { node = ref.y; continue; }
+                if (sp == 0) done = true;
+                else node = stack[--sp];
+            } else {
+                n_tests++;
+                int k = ~node;
+                const float4 *tp = sc.tris + 3 * (size_t)k;
+                float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+                float t = tri_hit(ray, v0, v1, v2);
+                if (t > 0.f) {
+                    int prim = __float_as_int(v0.w);
+                    if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
+                }
+                if (sp == 0) done = true;
+                else node = stack[--sp];
+            }
+            if (done) {
+                hits[r] = make_int2(h.k, __float_as_int(h.t));
+                have = false;
+                break;
             }
         }
-        float inv_n = 1.f / (float)n;
-        float invF = Fw > 0.f ? 1.f / Fw : 0.f;
-        rt[q] = make_float4(An.x * inv_n, An.y * inv_n, An.z * inv_n, Sw * inv_n);
-        rt[N + q] = make_float4(Af.x * inv_n, Af.y * inv_n, Af.z * inv_n, (float)n);
-        rt[2 * N + q] = make_float4(Bn * inv_n, Bf * inv_n, Fw, 0.f);
-        rt[3 * N + q] = make_float4(Pfar.x * invF, Pfar.y * invF, Pfar.z * invF, 0.f);
     }
+    // traversal work of the frame (node visits, triangle tests), one atomic per warp
+    unsigned long long a = n_visit, b = n_tests;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&counters[4]), a);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&counters[6]), b);
+    }
+}
+
+// Shading and the per-pixel near/far split of the masked pixel queue[e]: its rays
+// are regenerated (bit-identical to the tracer's), shaded at their recorded hits and
+// reduced in sample order.
+__global__ void __launch_bounds__(128) k_shade(DevCam cam, DevParams p, SceneDev sc, const uint32_t *queue,
+                                               const int32_t *nrays, const uint32_t *first_ray,
+                                               const uint32_t *counters, const int2 *hits, float4 *rt,
+                                               int32_t *ray_prim, int max_rays) {
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t count = *((volatile const uint32_t *)&counters[0]);
+    if (e >= count) return;
+    const size_t N = (size_t)cam.W2 * cam.H2;
+    const float inv_sqrt2 = 0.70710678118654752f;
+    uint32_t q = queue[e];
+    int n = nrays[q];
+    uint32_t f = first_ray[q];
+    float Sw = 0.f, Bn = 0.f, Bf = 0.f, Fw = 0.f;
+    float3 An = make_float3(0.f, 0.f, 0.f), Af = An, Pfar = An;
+    for (int s = 0; s < n; s++) {
+        float3 L, dir;
+        lens_ray(cam, p, q, s, L, dir);
+        int2 hh = __ldg(&hits[f + s]);
+        HitRec h{__int_as_float(hh.y), -1, hh.x};
+        float3 col;
+        float z;
+        if (h.k >= 0) {
+            h.prim = __float_as_int(__ldg(&sc.tris[3 * (size_t)h.k]).w);
+            float3 nrm;
+            col = shade(p, sc, h, dir, nrm);
+            z = fminf(h.t * dot(dir, cam.F), p.z_far);
+        } else {
+            col = p.sky;
+            z = p.z_far;
+        }
+        float c = coc_of(cam, z);
+        float rho = fabsf(fminf(fmaxf(0.25f * c, -p.rmax_hpx), p.rmax_hpx));
+        float w = sat(-c * inv_sqrt2);
+        if (ray_prim && s < max_rays) ray_prim[(size_t)q * max_rays + s] = h.prim;
+        Sw += w;
+        An = An + w * col;
+        Af = Af + (1.f - w) * col;
+        Bn += w * rho;
+        Bf += (1.f - w) * rho;
+        if (h.k >= 0) {
+            Pfar = Pfar + (1.f - w) * (L + h.t * dir);
+            Fw += 1.f - w;
+        }
+    }
+    float inv_n = 1.f / (float)n;
+    float invF = Fw > 0.f ? 1.f / Fw : 0.f;
+    rt[q] = make_float4(An.x * inv_n, An.y * inv_n, An.z * inv_n, Sw * inv_n);
+    rt[N + q] = make_float4(Af.x * inv_n, Af.y * inv_n, Af.z * inv_n, (float)n);
+    rt[2 * N + q] = make_float4(Bn * inv_n, Bf * inv_n, Fw, 0.f);
+    rt[3 * N + q] = make_float4(Pfar.x * invF, Pfar.y * invF, Pfar.z * invF, 0.f);
 }
 
 }  // namespace
@@ -376,14 +536,18 @@ void launch_mask(const DevCam &cam, const DevParams &p, const DofGBuffer *g, Dof
         k_edges<<<gr, b, 0, st>>>(h->W2, h->H2, zn, h->var_blur[h->cur], h->valid, p, h->xn, h->xf);
     }
     tmark(h, DOF_K_EDGES, st);
-    k_mask_compact<<<gr, b, 0, st>>>(h->W2, h->H2, p, h->tiles_dil, h->xf, h->nrays, h->queue, h->counters);
+    k_mask_compact<<<gr, b, 0, st>>>(h->W2, h->H2, p, h->tiles_dil, h->xf, h->nrays, h->queue, h->first_ray,
+                                     h->ray_pix, h->counters);
     tmark(h, DOF_K_MASK, st);
 }
 
 void launch_trace(const DevCam &cam, const DevParams &p, SceneDev sc, DofHistory *h, int sm_count,
                   cudaStream_t st) {
     int blocks = sm_count * 8;
-    k_trace<<<blocks, 128, 0, st>>>(cam, p, sc, h->queue, h->nrays, h->counters, h->rt,
-                                    (h->flags & DOF_HIST_RECORD_RAYS) ? h->ray_prim : nullptr, (int)h->max_rays);
+    k_trace_rays<<<blocks, 128, 0, st>>>(cam, p, sc, h->ray_pix, h->first_ray, h->counters, h->hits);
     tmark(h, DOF_K_TRACE, st);
+    k_shade<<<(unsigned)((h->N + 127) / 128), 128, 0, st>>>(
+        cam, p, sc, h->queue, h->nrays, h->first_ray, h->counters, h->hits, h->rt,
+        (h->flags & DOF_HIST_RECORD_RAYS) ? h->ray_prim : nullptr, (int)h->max_rays);
+    tmark(h, DOF_K_SHADE, st);
 }

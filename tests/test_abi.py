@@ -51,7 +51,7 @@ def test_struct_layouts_match_header():
 int main(void) {
   S(DofCamera) S(DofParams) S(DofGBuffer) S(DofSceneInfo) S(DofFrameStats)
   O(DofParams, seed) O(DofParams, light_dir) O(DofParams, emit) O(DofParams, tile)
-  O(DofCamera, frame_index) O(DofGBuffer, width) O(DofSceneInfo, device_bytes) O(DofFrameStats, device_status)
+  O(DofCamera, frame_index) O(DofGBuffer, width) O(DofSceneInfo, device_bytes) O(DofFrameStats, device_status) O(DofFrameStats, tri_tests)
   return 0; }
 '''
     with tempfile.TemporaryDirectory() as d:
