@@ -136,6 +136,12 @@ void dof_ctx_destroy(DofCtx *ctx);
 /* bytes currently held by the context's scenes and histories */
 size_t dof_ctx_bytes_in_use(const DofCtx *ctx);
 
+/* Context options (dof_ctx_set_option). */
+#define DOF_OPT_BVH_BUILDER 1
+#define DOF_BVH_PLOC 0   /* default: PLOC clustering over the Morton order (higher tree quality) */
+#define DOF_BVH_LBVH 1   /* Karras 2012 radix tree (faster build) */
+int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value);
+
 /* Fill `p` with the defaults above (1 spp fixed mode, 16 px radius clamp). */
 void dof_params_default(DofParams *p);
 
@@ -144,8 +150,10 @@ const char *dof_last_error(void);
 
 /* ---- scene (Section 4.2: the acceleration structure) ------------------------- */
 
-/* Upload a triangle scene and build its BVH on the device: an LBVH (Karras 2012) over
- * 63-bit Morton codes of the triangle centroids, two child boxes per node.  Up to 64
+/* Upload a triangle scene and build its BVH on the device from 63-bit Morton codes of
+ * the triangle centroids: PLOC agglomerative clustering (Meister and Bittner 2018)
+ * by default, or the LBVH radix tree of Karras 2012 (DOF_OPT_BVH_BUILDER); two child
+ * boxes per node.  Up to 64
  * "large" triangles (box extent above 1/16 of the scene's centroid extent, e.g. a
  * ground plane) are kept out of the tree and tested directly by every ray.
  *   xyz      host, n_verts * 3 floats

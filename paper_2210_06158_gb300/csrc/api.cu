@@ -175,6 +175,7 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->device = device;
     c->budget = mem_budget_bytes;
     c->in_use = 0;
+    c->bvh_builder = DOF_BVH_PLOC;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
@@ -189,6 +190,19 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     }
     *out = c;
     return DOF_OK;
+}
+
+extern "C" int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value) {
+    if (!ctx) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_ctx_set_option: null context");
+    switch (option) {
+        case DOF_OPT_BVH_BUILDER:
+            if (value != DOF_BVH_PLOC && value != DOF_BVH_LBVH)
+                return dof_set_error(DOF_ERR_INVALID_ARG, "dof_ctx_set_option: unknown BVH builder %lld", (long long)value);
+            ctx->bvh_builder = (int)value;
+            return DOF_OK;
+        default:
+            return dof_set_error(DOF_ERR_INVALID_ARG, "dof_ctx_set_option: unknown option %d", option);
+    }
 }
 
 extern "C" void dof_ctx_destroy(DofCtx *ctx) {
@@ -229,7 +243,7 @@ extern "C" int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts,
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_xyz, xyz, sizeof(float) * 3 * (size_t)n_verts, cudaMemcpyHostToDevice, st), "upload");
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_idx, tri_idx, sizeof(uint32_t) * 3 * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
     if (rc == DOF_OK && tri_mat) rc = dof_cuda_check(cudaMemcpyAsync(d_mat, tri_mat, sizeof(uint32_t) * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
-    if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, st);
+    if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, ctx->bvh_builder, st);
     cudaFree(d_xyz); cudaFree(d_idx); cudaFree(d_mat);
     if (rc != DOF_OK) {
         dof_free(ctx, s->tris, sizeof(float4) * 3 * (size_t)n_tris);
@@ -267,6 +281,7 @@ static SceneDev scene_dev(const DofScene *s) {
     d.tris = s->tris;
     d.n_tris = (int)s->n_tree;
     d.n_large = (int)s->n_large;
+    d.root = s->root;
     return d;
 }
 

@@ -236,12 +236,150 @@ __global__ void k_depth(int n, const int *parent_node, const int *parent_leaf, i
     atomicMax(depth, d);
 }
 
+
+// ---------------------------------------------------------------------------
+// PLOC (Meister and Bittner, "Parallel Locally-Ordered Clustering for Bounding
+// Volume Hierarchy Construction", TVCG 2018): clusters start as the Morton-sorted
+// leaves; each finds its nearest neighbour within +-kPlocRadius positions by the
+// surface area of the merged box; mutual nearest neighbours merge into a new node;
+// the cluster array is compacted (order preserved) and the steps repeat.
+// ---------------------------------------------------------------------------
+constexpr int kPlocRadius = 24;
+
+__device__ __forceinline__ float half_area(float4 lo, float4 hi) {
+    float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_ploc_init(const float4 *tris, int m, int *cid, float4 *clo, float4 *chi) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    float3 lo, hi;
+    tri_box(tris, k, lo, hi);
+    cid[k] = ~k;
+    clo[k] = make_float4(lo.x, lo.y, lo.z, 0.f);
+    chi[k] = make_float4(hi.x, hi.y, hi.z, 0.f);
+}
+
+// nearest neighbour by merged area; ties to the smaller index (symmetric cost, so the
+// globally cheapest pair is always mutual and every round merges at least once)
+__global__ void k_ploc_nn(int count, const float4 *clo, const float4 *chi, int *nn) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float4 lo = clo[i], hi = chi[i];
+    float best = INFINITY;
+    int bj = -1;
+    int j0 = max(0, i - kPlocRadius), j1 = min(count - 1, i + kPlocRadius);
+    for (int j = j0; j <= j1; j++) {
+        if (j == i) continue;
+        float4 l2 = clo[j], h2 = chi[j];
+        float a = half_area(make_float4(fminf(lo.x, l2.x), fminf(lo.y, l2.y), fminf(lo.z, l2.z), 0.f),
+                            make_float4(fmaxf(hi.x, h2.x), fmaxf(hi.y, h2.y), fmaxf(hi.z, h2.z), 0.f));
+        if (a < best) { best = a; bj = j; }
+    }
+    nn[i] = bj;
+}
+
+// mutual pairs merge: the lower position creates the node and keeps the merged
+// cluster, the higher one drops out
+__global__ void k_ploc_merge(int count, int *cid, float4 *clo, float4 *chi, const int *nn, int *keep,
+                             int *node_count, BvhNode *nodes, int *parent_node, int *parent_leaf, int n_nodes,
+                             int *bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int j = nn[i];
+    bool mutual = j >= 0 && nn[j] == i;
+    if (!mutual) { keep[i] = 1; return; }
+    if (i > j) { keep[i] = 0; return; }
+    int id = atomicAdd(node_count, 1);
+    if (id >= n_nodes) { atomicExch(bad, 4); keep[i] = 1; return; }
+    int a = cid[i], b = cid[j];
+    float4 l0 = clo[i], h0 = chi[i], l1 = clo[j], h1 = chi[j];
+    BvhNode nd;
+    nd.a = make_float4(l0.x, l0.y, l0.z, h0.x);
+    nd.b = make_float4(h0.y, h0.z, l1.x, l1.y);
+    nd.c = make_float4(l1.z, h1.x, h1.y, h1.z);
+    nd.r = make_int4(a, b, 0, 0);
+    nodes[id] = nd;
+    if (a < 0) parent_leaf[~a] = id; else parent_node[a] = id;
+    if (b < 0) parent_leaf[~b] = id; else parent_node[b] = id;
+    cid[i] = id;
+    clo[i] = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f);
+    chi[i] = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f);
+    keep[i] = 1;
+}
+
+__global__ void k_ploc_scatter(int count, const int *keep, const int *pos, const int *cid, const float4 *clo,
+                               const float4 *chi, int *cid2, float4 *clo2, float4 *chi2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count || !keep[i]) return;
+    int o = pos[i];
+    cid2[o] = cid[i];
+    clo2[o] = clo[i];
+    chi2[o] = chi[i];
+}
+
 }  // namespace
 
 static inline unsigned blocks_for(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// PLOC hierarchy over the m sorted tree triangles; writes nodes, parents, *root
+static int ploc_build(DofScene *s, int m, int *pnode, int *pleaf, int *ibuf, int *root, cudaStream_t st) {
+    const int B = 256;
+    int rc = DOF_OK;
+    int *cid[2] = {nullptr, nullptr}, *nn = nullptr, *keep = nullptr, *pos = nullptr, *cnt = nullptr;
+    float4 *clo[2] = {nullptr, nullptr}, *chi[2] = {nullptr, nullptr};
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    auto ck = [&](cudaError_t e, const char *w) { if (rc == DOF_OK && e != cudaSuccess) rc = dof_cuda_check(e, w); };
+    for (int k = 0; k < 2; k++) {
+        ck(cudaMalloc(&cid[k], sizeof(int) * m), "ploc");
+        ck(cudaMalloc(&clo[k], sizeof(float4) * m), "ploc");
+        ck(cudaMalloc(&chi[k], sizeof(float4) * m), "ploc");
+    }
+    ck(cudaMalloc(&nn, sizeof(int) * m), "ploc");
+    ck(cudaMalloc(&keep, sizeof(int) * m), "ploc");
+    ck(cudaMalloc(&pos, sizeof(int) * m), "ploc");
+    ck(cudaMalloc(&cnt, sizeof(int)), "ploc");
+    ck(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, keep, pos, m, st), "ploc scan size");
+    ck(cudaMalloc(&tmp, tmp_bytes ? tmp_bytes : 16), "ploc scan temp");
+    if (rc == DOF_OK) {
+        ck(cudaMemsetAsync(cnt, 0, sizeof(int), st), "ploc");
+        k_ploc_init<<<blocks_for(m, B), B, 0, st>>>(s->tris, m, cid[0], clo[0], chi[0]);
+        int count = m, cur = 0;
+        for (int round = 0; count > 1 && rc == DOF_OK; round++) {
+            if (round > 100000) { rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "PLOC made no progress"); break; }
+            k_ploc_nn<<<blocks_for(count, B), B, 0, st>>>(count, clo[cur], chi[cur], nn);
+            k_ploc_merge<<<blocks_for(count, B), B, 0, st>>>(count, cid[cur], clo[cur], chi[cur], nn, keep, cnt,
+                                                            s->nodes, pnode, pleaf, m - 1, ibuf + 6);
+            ck(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, keep, pos, count, st), "ploc scan");
+            k_ploc_scatter<<<blocks_for(count, B), B, 0, st>>>(count, keep, pos, cid[cur], clo[cur], chi[cur],
+                                                              cid[cur ^ 1], clo[cur ^ 1], chi[cur ^ 1]);
+            int last[2];
+            ck(cudaMemcpyAsync(&last[0], pos + count - 1, sizeof(int), cudaMemcpyDeviceToHost, st), "ploc count");
+            ck(cudaMemcpyAsync(&last[1], keep + count - 1, sizeof(int), cudaMemcpyDeviceToHost, st), "ploc count");
+            ck(cudaStreamSynchronize(st), "ploc round");
+            int next = last[0] + last[1];
+            if (rc == DOF_OK && next >= count) { rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "PLOC round merged nothing"); break; }
+            count = next;
+            cur ^= 1;
+        }
+        if (rc == DOF_OK) {
+            ck(cudaMemcpyAsync(root, cid[cur], sizeof(int), cudaMemcpyDeviceToHost, st), "ploc root");
+            ck(cudaStreamSynchronize(st), "ploc root");
+            if (rc == DOF_OK && *root >= 0) {
+                int minus1 = -1;
+                ck(cudaMemcpy(pnode + *root, &minus1, sizeof(int), cudaMemcpyHostToDevice), "ploc root parent");
+            }
+        }
+    }
+    for (int k = 0; k < 2; k++) { cudaFree(cid[k]); cudaFree(clo[k]); cudaFree(chi[k]); }
+    cudaFree(nn); cudaFree(keep); cudaFree(pos); cudaFree(cnt); cudaFree(tmp);
+    return rc;
+}
+
 int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const uint32_t *d_idx,
-                     const uint32_t *d_mat, cudaStream_t st) {
+                     const uint32_t *d_mat, int builder, cudaStream_t st) {
     const int n = (int)s->n_tris;
     const int B = 256;
     int rc = DOF_OK;
@@ -293,15 +431,22 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
         ck(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys2, vals, vals2, n, 0, 64, st), "sort");
         k_sorted_tris<<<blocks_for(n, B), B, 0, st>>>(d_xyz, d_idx, d_mat, (uint32_t)n, n_verts, vals2, s->tris);
         const int m = n_small;
+        int root = m >= 2 ? 0 : ~0;
         if (m >= 2) {
             ck(cudaMemsetAsync(pleaf, 0xFF, sizeof(int) * m, st), "memset");
             ck(cudaMemsetAsync(arr, 0, sizeof(int) * (m - 1), st), "memset");
             ck(cudaMemsetAsync(s->nodes, 0xFF, sizeof(BvhNode) * (m - 1), st), "memset");
-            k_karras<<<blocks_for(m - 1, B), B, 0, st>>>(keys2, m, child, pnode, pleaf, ibuf + 6);
-            k_refit<<<blocks_for(m, B), B, 0, st>>>(s->tris, m, child, pnode, pleaf, blo, bhi, arr, s->nodes,
-                                                    ibuf + 6);
+            if (builder == DOF_BVH_PLOC) {
+                if (rc == DOF_OK) rc = ploc_build(s, m, pnode, pleaf, ibuf, &root, st);
+                if (rc != DOF_OK) goto done;
+            } else {
+                k_karras<<<blocks_for(m - 1, B), B, 0, st>>>(keys2, m, child, pnode, pleaf, ibuf + 6);
+                k_refit<<<blocks_for(m, B), B, 0, st>>>(s->tris, m, child, pnode, pleaf, blo, bhi, arr, s->nodes,
+                                                        ibuf + 6);
+            }
             k_depth<<<blocks_for(m, B), B, 0, st>>>(m, pnode, pleaf, ibuf + 7);
         }
+        s->root = root;
         ck(cudaGetLastError(), "bvh kernels");
         ck(cudaMemcpyAsync(hbuf, ibuf, sizeof(hbuf), cudaMemcpyDeviceToHost, st), "bvh readback");
         ck(cudaStreamSynchronize(st), "bvh build");
@@ -316,13 +461,12 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
             rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "BVH depth %u exceeds the traversal stack", s->depth);
             goto done;
         }
-        // bounds of the tree's triangles (root box)
-        if (m >= 2) {
-            float4 lo, hi;
-            ck(cudaMemcpy(&lo, blo, sizeof(float4), cudaMemcpyDeviceToHost), "bounds");
-            ck(cudaMemcpy(&hi, bhi, sizeof(float4), cudaMemcpyDeviceToHost), "bounds");
-            s->lo[0] = lo.x; s->lo[1] = lo.y; s->lo[2] = lo.z;
-            s->hi[0] = hi.x; s->hi[1] = hi.y; s->hi[2] = hi.z;
+        // bounds of the tree's triangles: union of the root's child boxes
+        if (m >= 2 && root >= 0) {
+            BvhNode nd;
+            ck(cudaMemcpy(&nd, s->nodes + root, sizeof(BvhNode), cudaMemcpyDeviceToHost), "bounds");
+            s->lo[0] = fminf(nd.a.x, nd.b.z); s->lo[1] = fminf(nd.a.y, nd.b.w); s->lo[2] = fminf(nd.a.z, nd.c.x);
+            s->hi[0] = fmaxf(nd.a.w, nd.c.y); s->hi[1] = fmaxf(nd.b.x, nd.c.z); s->hi[2] = fmaxf(nd.b.y, nd.c.w);
         }
     }
 done:

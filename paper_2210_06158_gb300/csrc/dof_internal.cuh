@@ -58,6 +58,7 @@ struct SceneDev {
     const float4 *tris;          // 3 float4 per sorted triangle: v0 (w = prim id bits), v1, v2 (w = material bits)
     int n_tris;                  // triangles in the tree (sorted indices 0 .. n_tris-1)
     int n_large;                 // large triangles after them, tested directly by every ray
+    int root;                    // root reference (internal node, or ~0 for a one-leaf tree)
 };
 
 // at most this many large triangles are kept out of the tree (see bvh.cu)
@@ -71,6 +72,7 @@ struct DofCtx {
     int device;
     size_t budget, in_use;
     int sm_count;
+    int bvh_builder;               // DOF_BVH_PLOC or DOF_BVH_LBVH
     uint32_t *d_status;            // device status word of context-level launches
 };
 
@@ -78,6 +80,7 @@ struct DofScene {
     DofCtx *ctx;
     uint32_t n_tris, n_nodes, depth;
     uint32_t n_tree, n_large;      // triangles in the tree / tested directly
+    int root;
     BvhNode *nodes;
     float4 *tris;
     size_t bytes;
@@ -139,7 +142,7 @@ void dof_free(DofCtx *ctx, void *ptr, size_t bytes);
 
 // launch wrappers (one per kernel group, defined in the .cu files)
 int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const uint32_t *d_idx,
-                     const uint32_t *d_mat, cudaStream_t st);
+                     const uint32_t *d_mat, int builder, cudaStream_t st);
 void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *color, float *depth,
                     float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st);
 void launch_post(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h,

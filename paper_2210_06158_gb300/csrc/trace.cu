@@ -125,7 +125,7 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
     if (sc.n_tris <= 0) return h;
     int stack[kStack];
     int sp = 0;
-    int node = sc.n_tris >= 2 ? 0 : ~0;
+    int node = sc.root;
     const int n_nodes = sc.n_tris - 1;
     const long long max_steps = 4ll * sc.n_tris + 64;
     for (long long steps = 0;; steps++) {
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(128) k_trace_rays(DevCam cam, DevParams p, Sce
                             if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
                         }
                     }
-                    node = sc.n_tris >= 2 ? 0 : ~0;
+                    node = sc.root;
                     sp = 0;
                     steps = 0;
                     have = sc.n_tris > 0;

@@ -82,6 +82,7 @@ _SIGS = {
     "dof_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
     "dof_ctx_destroy": (None, [C.c_void_p]),
     "dof_ctx_bytes_in_use": (C.c_size_t, [C.c_void_p]),
+    "dof_ctx_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     "dof_params_default": (None, [C.POINTER(DofParams)]),
     "dof_last_error": (C.c_char_p, []),
     "dof_scene_upload": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint32,
@@ -193,6 +194,10 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_bvh_builder(self, name: str):
+        """'ploc' (default) or 'lbvh' for scenes uploaded afterwards."""
+        _check(lib().dof_ctx_set_option(self.ptr, 1, {"ploc": 0, "lbvh": 1}[name]))
 
     @property
     def bytes_in_use(self) -> int:
