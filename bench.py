@@ -43,6 +43,12 @@ FLOP_PER_NODE = 47.0
 FLOP_PER_TRI = 48.0
 FP32_LANES_PER_SM = 128
 
+# DRAM bytes (read + write) per launch from the last ncu capture of each kernel on the
+# 1080p workload (profiles/top_kernels_c2_1080p.md); a kernel changed since then has no
+# entry.
+PROFILED_TRAFFIC = {"c2": {"k_trace_rays": 10.32e6, "k_recon": 30.23e6, "k_main_filter": 10.45e6,
+                           "k_accumulate": 61.69e6, "k_composite": 65.88e6, "k_downscale_tiles": 41.53e6}}
+
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
 BYTES = {
@@ -51,7 +57,7 @@ BYTES = {
     "k_main_filter": ("N", 36.0),        # pre 16 + z 4 read, 16 written (neighbour taps from cache)
     "k_median_pp": ("N", 32.0),
     "k_mask_compact": ("N", 8.0),
-    "k_trace": ("R", 12.0),              # per ray: ray list 4 read, hit 8 written (BVH reads hit L2)
+    "k_trace_rays": ("R", 12.0),              # per ray: ray list 4 read, hit 8 written (BVH reads hit L2)
     "k_shade": ("M", 76.0),              # queue, count, first ray read, 4 x float4 written (+ hits, per ray)
     "k_accumulate": ("N", 192.0),        # rt 64 + z 4 + nrays 4 + history 48 read; history 48 + 24 written
     "k_var_blur": ("N", 8.0),
@@ -326,10 +332,11 @@ def run_ours(args, rank, world):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6 / 1e12      # TFLOP/s, FMA = 2
     trace_flop = (visits * FLOP_PER_NODE + tests * FLOP_PER_TRI) / n_samples
-    if dom == "k_trace" and kavg[dom] > 0:
+    traffic = PROFILED_TRAFFIC.get(args.config, {}).get(dom)
+    if dom == "k_trace_rays" and kavg[dom] > 0:
         achieved = trace_flop / (kavg[dom] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": traffic,
                 "peak_source": f"derived: 2 x {FP32_LANES_PER_SM} FP32 lanes x {n_sm} SMs x {sm_mhz:.0f} MHz",
                 "algorithmic_flop": int(trace_flop), "node_visits_per_ray": round(visits / max(1, rays), 2),
                 "tri_tests_per_ray": round(tests / max(1, rays), 2)}
@@ -338,13 +345,13 @@ def run_ours(args, rank, world):
         algo = units[u] * b
         achieved = algo / (kavg[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_source": peak_src,
+                "frac": round(achieved / hbm_peak, 4), "traffic": traffic, "peak_source": peak_src,
                 "algorithmic_bytes": int(algo)}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
     # image passes together (streaming kernels only) vs HBM
-    img = [k for k in BYTES if k != "k_trace" and kavg.get(k, 0) > 0]
+    img = [k for k in BYTES if k not in ("k_trace_rays", "k_shade") and kavg.get(k, 0) > 0]
     img_bytes = sum(units[BYTES[k][0]] * BYTES[k][1] for k in img)
     img_ms = sum(kavg[k] for k in img)
     res = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=world, steps=args.steps,
@@ -364,8 +371,8 @@ def run_ours(args, rank, world):
                clocks=clocks, kernel_ms=kern,
                image_passes={"ms": round(img_ms, 4), "gbs": round(img_bytes / (img_ms * 1e-3) / 1e9, 1),
                              "frac_of_hbm": round(img_bytes / (img_ms * 1e-3) / 1e9 / hbm_peak, 4)},
-               mrays_per_s=round(rays_per_frame / (kavg.get("k_trace", 0) * 1e-3) / 1e6, 1)
-               if kavg.get("k_trace", 0) > 0 else None,
+               mrays_per_s=round(rays_per_frame / (kavg.get("k_trace_rays", 0) * 1e-3) / 1e6, 1)
+               if kavg.get("k_trace_rays", 0) > 0 else None,
                rays_per_frame=int(rays_per_frame), mask_fraction=round(masked_per_frame / N, 4),
                bvh_build_ms=round(bvh_ms, 2), gbuffer_ms=round(gbuf_ms, 3),
                device_status=int(st.device_status))

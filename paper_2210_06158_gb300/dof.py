@@ -25,7 +25,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "BUDGET", -4: "CUDA", -5: "TIMEOUT",
 DOF_HIST_RECORD_RAYS = 1
 DOF_HIST_TIMING = 2
 KERNELS = ["k_downscale_tiles", "k_tile_dilate", "k_prefilter", "k_main_filter", "k_median_pp", "k_edges",
-           "k_mask_compact", "k_trace", "k_shade", "k_accumulate", "k_var_blur", "k_median_rt", "k_mips", "k_recon",
+           "k_mask_compact", "k_trace_rays", "k_shade", "k_accumulate", "k_var_blur", "k_median_rt", "k_mips", "k_recon",
            "k_composite"]
 BUF = dict(PP_IN=0, Z_H=1, TILES=2, TILES_DIL=3, PRE=4, MAIN=5, PP_MED=6, XN=7, XF=8,
            NRAYS=9, RAY_PRIM=10, RT=11, CRT=12, CT=13, VAR=14, VAR_BLUR=15, RT_MED=16,
