@@ -192,6 +192,17 @@ void dof_history_destroy(DofHistory *hist);
 /* forget the accumulated history (the next frame restarts accumulation) */
 int dof_history_reset(DofHistory *hist);
 
+/* Checkpoint / resume of a session (the paper has none; the FP32 history is the whole
+ * state a frame carries to the next, and the lens samples are counter-based, so a
+ * session resumed from a checkpoint continues bit-identically).
+ * export: with host_buf NULL, *bytes receives the size needed; otherwise *bytes must
+ *   be at least that size, the history is copied into caller-owned host memory after
+ *   synchronising `stream`, and *bytes is set to the size written.
+ * import: the buffer must come from an export of a history of the same width, height
+ *   and max_rays (DOF_ERR_MISMATCH otherwise); synchronises `stream`. */
+int dof_history_export(DofHistory *hist, void *host_buf, size_t *bytes, void *stream);
+int dof_history_import(DofHistory *hist, const void *host_buf, size_t bytes, void *stream);
+
 /* ---- one frame ----------------------------------------------------------------- */
 
 /* Run the hybrid depth-of-field pass for one frame on `stream`:
@@ -204,6 +215,27 @@ int dof_history_reset(DofHistory *hist);
  * Host-side validation errors return before anything is enqueued. */
 int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *gbuf, const DofCamera *cam,
               const DofParams *p, DofHistory *hist, float *out, void *stream);
+
+/* One session's frame of a batch. */
+typedef struct {
+    const DofScene *scene;
+    const DofGBuffer *gbuf;
+    const DofCamera *cam;
+    const DofParams *params;
+    DofHistory *hist;
+    float *out;
+} DofFrameReq;
+
+#define DOF_MAX_BATCH 32
+
+/* Frames of up to DOF_MAX_BATCH sessions (different sizes, scenes and parameters
+ * allowed; each history at most once) in one launch per pass on `stream`: every
+ * kernel covers the blocks of all the sessions, and the thin-lens rays of all the
+ * sessions share one persistent tracer launch.  Each result is the one dof_frame
+ * gives for that session alone (bit-identical).  Validation as dof_frame; nothing is
+ * enqueued if any request is invalid.  Traversal counters of the batch are reported
+ * by dof_frame_stats of the first request's history. */
+int dof_batch_frame(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, void *stream);
 
 /* Synchronise `stream` and report the last frame's counters and the device status. */
 int dof_frame_stats(DofHistory *hist, void *stream, DofFrameStats *out);

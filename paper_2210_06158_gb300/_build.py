@@ -13,6 +13,7 @@ CSRC = PKG / "csrc"
 LIB_DIR = PKG / "_lib"
 LIB = LIB_DIR / "libdof.so"
 SOURCES = ["api.cu", "bvh.cu", "trace.cu", "post.cu", "temporal.cu", "recon.cu", "noalloc.cu"]
+HEADERS_EXTRA = ["batch.cuh"]
 HEADERS = ["dof_internal.cuh", "filters.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,7 +34,7 @@ def _stale() -> bool:
     if not LIB.exists():
         return True
     t = LIB.stat().st_mtime
-    deps = [CSRC / s for s in SOURCES + HEADERS] + [PKG.parent / "include" / "dof.h", Path(__file__)]
+    deps = [CSRC / s for s in SOURCES + HEADERS + HEADERS_EXTRA] + [PKG.parent / "include" / "dof.h", Path(__file__)]
     return any(d.stat().st_mtime > t for d in deps)
 
 

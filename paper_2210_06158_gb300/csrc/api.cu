@@ -2,10 +2,11 @@
 // orchestration of the pass on one CUDA stream.
 #include <math.h>
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
-#include "dof_internal.cuh"
+#include "batch.cuh"
 
 int post_init_tables();
 int recon_init_tables();
@@ -36,7 +37,7 @@ int dof_alloc(DofCtx *ctx, size_t bytes, void **ptr, size_t *acc) {
     if (bytes == 0) return DOF_OK;
     if (ctx->budget && ctx->in_use + bytes > ctx->budget)
         return dof_set_error(DOF_ERR_BUDGET, "allocation of %zu bytes exceeds the budget (%zu of %zu in use)", bytes,
-                             ctx->in_use, ctx->budget);
+                             (size_t)ctx->in_use, ctx->budget);
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
@@ -55,12 +56,21 @@ void dof_free(DofCtx *ctx, void *ptr, size_t bytes) {
 
 namespace {
 
-// makes `dev` current for the duration of an API call and restores the caller's device
+// makes `dev` current for the duration of an API call and restores the caller's device;
+// also drops a stale error that another library left on this thread, so that the
+// call reports only its own errors
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
+        cudaGetLastError();
         if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
+        if (prev != dev) {
+            cudaError_t e = cudaSetDevice(dev);
+            if (e != cudaSuccess) {
+                if (getenv("DOF_DEBUG")) fprintf(stderr, "libdof: cudaSetDevice(%d) failed: %s\n", dev, cudaGetErrorString(e));
+                cudaGetLastError();
+            }
+        }
     }
     ~DeviceGuard() {
         int cur;
@@ -175,6 +185,7 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->device = device;
     c->budget = mem_budget_bytes;
     c->in_use = 0;
+    c->refs = 1;
     c->bvh_builder = DOF_BVH_PLOC;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
@@ -205,14 +216,23 @@ extern "C" int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value) {
     }
 }
 
-extern "C" void dof_ctx_destroy(DofCtx *ctx) {
-    if (!ctx) return;
-    DeviceGuard g(ctx->device);
-    cudaFree(ctx->d_status);
-    delete ctx;
+void ctx_retain(DofCtx *ctx) { ctx->refs++; }
+
+void ctx_release(DofCtx *ctx) {
+    if (--ctx->refs == 0) {
+        DeviceGuard g(ctx->device);
+        cudaFree(ctx->d_status);
+        delete ctx;
+    }
 }
 
-extern "C" size_t dof_ctx_bytes_in_use(const DofCtx *ctx) { return ctx ? ctx->in_use : 0; }
+// The context lives on until its last scene and history are destroyed, so handles may
+// be released in any order.
+extern "C" void dof_ctx_destroy(DofCtx *ctx) {
+    if (ctx) ctx_release(ctx);
+}
+
+extern "C" size_t dof_ctx_bytes_in_use(const DofCtx *ctx) { return ctx ? (size_t)ctx->in_use : 0; }
 
 // ---------------------------------------------------------------------------
 // scene
@@ -234,9 +254,11 @@ extern "C" int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts,
     int rc = DOF_OK;
     float *d_xyz = nullptr;
     uint32_t *d_idx = nullptr, *d_mat = nullptr;
-    if (n_tris == 0) { s->depth = 0; *out = s; return DOF_OK; }
-    rc = dof_alloc(ctx, sizeof(float4) * 3 * (size_t)n_tris, (void **)&s->tris, &s->bytes);
-    if (rc == DOF_OK && s->n_nodes) rc = dof_alloc(ctx, sizeof(BvhNode) * (size_t)s->n_nodes, (void **)&s->nodes, &s->bytes);
+    if (n_tris == 0) { s->depth = 0; s->root = ~0; ctx_retain(ctx); *out = s; return DOF_OK; }
+    s->tris_bytes = sizeof(float4) * 3 * (size_t)n_tris;
+    s->nodes_bytes = sizeof(BvhNode) * (size_t)s->n_nodes;
+    rc = dof_alloc(ctx, s->tris_bytes, (void **)&s->tris, &s->bytes);
+    if (rc == DOF_OK && s->n_nodes) rc = dof_alloc(ctx, s->nodes_bytes, (void **)&s->nodes, &s->bytes);
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMalloc(&d_xyz, sizeof(float) * 3 * (size_t)n_verts), "scene vertices");
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMalloc(&d_idx, sizeof(uint32_t) * 3 * (size_t)n_tris), "scene indices");
     if (rc == DOF_OK && tri_mat) rc = dof_cuda_check(cudaMalloc(&d_mat, sizeof(uint32_t) * (size_t)n_tris), "scene materials");
@@ -246,21 +268,26 @@ extern "C" int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts,
     if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, ctx->bvh_builder, st);
     cudaFree(d_xyz); cudaFree(d_idx); cudaFree(d_mat);
     if (rc != DOF_OK) {
-        dof_free(ctx, s->tris, sizeof(float4) * 3 * (size_t)n_tris);
-        dof_free(ctx, s->nodes, sizeof(BvhNode) * (size_t)s->n_nodes);
+        dof_free(ctx, s->tris, s->tris_bytes);
+        dof_free(ctx, s->nodes, s->nodes_bytes);
         delete s;
         return rc;
     }
+    ctx_retain(ctx);
     *out = s;
     return DOF_OK;
 }
 
 extern "C" void dof_scene_destroy(DofScene *s) {
     if (!s) return;
-    DeviceGuard g(s->ctx->device);
-    dof_free(s->ctx, s->tris, sizeof(float4) * 3 * (size_t)s->n_tris);
-    dof_free(s->ctx, s->nodes, sizeof(BvhNode) * (size_t)s->n_nodes);
+    DofCtx *ctx = s->ctx;
+    {
+        DeviceGuard g(ctx->device);
+        dof_free(ctx, s->tris, s->tris_bytes);
+        dof_free(ctx, s->nodes, s->nodes_bytes);
+    }
     delete s;
+    ctx_release(ctx);
 }
 
 extern "C" int dof_scene_info(const DofScene *s, DofSceneInfo *info) {
@@ -406,15 +433,20 @@ extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, 
         delete h;
         return rc;
     }
+    ctx_retain(ctx);
     *out = h;
     return DOF_OK;
 }
 
 extern "C" void dof_history_destroy(DofHistory *h) {
     if (!h) return;
-    DeviceGuard g(h->ctx->device);
-    history_free(h);
+    DofCtx *ctx = h->ctx;
+    {
+        DeviceGuard g(ctx->device);
+        history_free(h);
+    }
     delete h;
+    ctx_release(ctx);
 }
 
 extern "C" int dof_history_reset(DofHistory *h) {
@@ -427,49 +459,139 @@ extern "C" int dof_history_reset(DofHistory *h) {
 // frame
 // ---------------------------------------------------------------------------
 
-extern "C" int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *gb, const DofCamera *cam,
-                         const DofParams *p, DofHistory *h, float *out, void *stream) {
-    if (!ctx || !scene || !gb || !cam || !p || !h || !out)
+// ---------------------------------------------------------------------------
+// frames: one launch per pass over the sessions of a batch
+// ---------------------------------------------------------------------------
+
+static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
+    const DofScene *scene = r.scene;
+    const DofGBuffer *gb = r.gbuf;
+    DofHistory *h = r.hist;
+    if (!scene || !gb || !r.cam || !r.params || !h || !r.out)
         return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: null argument");
     if (h->ctx != ctx || scene->ctx != ctx) return dof_set_error(DOF_ERR_MISMATCH, "dof_frame: objects of another context");
     if (gb->width != h->W || gb->height != h->H)
         return dof_set_error(DOF_ERR_MISMATCH, "dof_frame: G-buffer %ux%u, history %ux%u", gb->width, gb->height, h->W, h->H);
     if (gb->fmt != DOF_FMT_F32) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: unsupported G-buffer format");
-    if (!gb->color || !gb->depth || (p->ray_mode == 1 && !gb->normal))
+    if (!gb->color || !gb->depth || (r.params->ray_mode == 1 && !gb->normal))
         return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: G-buffer plane is NULL");
-    if (!aligned(gb->color, 16) || !aligned(gb->depth, 8) || (gb->normal && !aligned(gb->normal, 16)) || !aligned(out, 16))
+    if (!aligned(gb->color, 16) || !aligned(gb->depth, 8) || (gb->normal && !aligned(gb->normal, 16)) || !aligned(r.out, 16))
         return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: misaligned buffer");
-    DevCam dc;
-    DevParams dp;
-    int rc = make_cam(cam, h->W, h->H, dc);
+    memset(&d, 0, sizeof(d));
+    int rc = make_cam(r.cam, h->W, h->H, d.cam);
     if (rc) return rc;
-    rc = make_params(p, h->W, h->H, h->max_rays, dp);
+    rc = make_params(r.params, h->W, h->H, h->max_rays, d.p);
     if (rc) return rc;
-    DeviceGuard g(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
-    rc = dof_cuda_check(cudaMemsetAsync(h->counters, 0, 3 * sizeof(uint32_t), st), "dof_frame counters");
-    if (rc == DOF_OK) rc = dof_cuda_check(cudaMemsetAsync(h->counters + 4, 0, 4 * sizeof(uint32_t), st), "dof_frame counters");
-    if (rc) return rc;
-    if (h->ev && h->ev_used < kTimingSlots) {
-        // a kernel that is not launched this frame gets an event right after its predecessor's
-        for (int k = 0; k <= DOF_K_COUNT; k++) cudaEventRecord(h->ev[h->ev_slot * (DOF_K_COUNT + 1) + k], st);
+    d.sc = scene_dev(scene);
+    d.N = (int)h->N;
+    d.max_rays = (int)h->max_rays;
+    d.valid = h->valid;
+    d.record_rays = (h->flags & DOF_HIST_RECORD_RAYS) && h->ray_prim;
+    d.color = reinterpret_cast<const float4 *>(gb->color);
+    d.depth = gb->depth;
+    d.normal = reinterpret_cast<const float4 *>(gb->normal);
+    d.out = reinterpret_cast<float4 *>(r.out);
+    d.pp_in = h->pp_in; d.pre = h->pre; d.main_ = h->main_; d.pp_med = h->pp_med; d.n_h = h->n_h;
+    d.zn = h->crt;   // adaptive-mode scratch: crt is only written later, by the accumulation
+    d.crt = h->crt; d.rt_med = h->rt_med; d.recon = h->recon; d.rt = h->rt;
+    d.z_h = h->z_h; d.xn = h->xn; d.xf = h->xf; d.ct = h->ct; d.var = h->var;
+    d.tiles = h->tiles; d.tiles_dil = h->tiles_dil;
+    d.nrays = h->nrays; d.ray_prim = h->ray_prim;
+    d.queue = h->queue; d.first_ray = h->first_ray; d.ray_pix = h->ray_pix; d.counters = h->counters;
+    d.hits = h->hits;
+    int L = (int)ceilf(r.params->lod_max) + 1;
+    d.mip_L = L < 1 ? 1 : (L > 4 ? 4 : L);
+    for (int l = 0; l < 4; l++) {
+        d.mip0[l] = h->mip0[l]; d.mip1[l] = h->mip1[l]; d.mip_w[l] = h->mip_w[l]; d.mip_h[l] = h->mip_h[l];
     }
-    launch_post(dc, dp, gb, h, st);
-    launch_mask(dc, dp, gb, h, st);
-    launch_trace(dc, dp, scene_dev(scene), h, ctx->sm_count, st);
-    launch_temporal(dc, dp, h, st);
-    launch_recon(dc, dp, gb, h, reinterpret_cast<float4 *>(out), st);
-    rc = dof_cuda_check(cudaGetLastError(), "dof_frame launch");
+    d.hist_in = h->hist[h->cur];
+    d.hist_out = h->hist[h->cur ^ 1];
+    d.var_in = h->var_blur[h->cur];
+    d.var_out = h->var_blur[h->cur ^ 1];
+    return DOF_OK;
+}
+
+static void shape_grid(const SessDesc &d, const DofHistory *h, int shape, int &gx, int &gy) {
+    switch (shape) {
+        case SH_TILE8: gx = (int)h->TW; gy = (int)h->TH; break;
+        case SH_TILEDIL: gx = ((int)h->TW + 15) / 16; gy = ((int)h->TH + 15) / 16; break;
+        case SH_HPX: gx = ((int)h->W2 + 31) / 32; gy = ((int)h->H2 + 7) / 8; break;
+        case SH_MIP1: case SH_MIP2: case SH_MIP3: {
+            int l = shape - SH_MIP1 + 1;
+            gx = (d.mip_w[l] + 31) / 32; gy = (d.mip_h[l] + 7) / 8;
+            break;
+        }
+        case SH_FPX: gx = ((int)h->W + 31) / 32; gy = ((int)h->H + 7) / 8; break;
+        default: gx = ((int)h->N + 127) / 128; gy = 1; break;   // SH_SHADE
+    }
+}
+
+static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStream_t st) {
+    if (n == 0) return DOF_OK;
+    if (n > (uint32_t)kMaxBatch) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_batch_frame: %u > %d sessions", n, kMaxBatch);
+    static thread_local BatchArgs A;   // ~22 KB: kept off the stack
+    memset(&A, 0, sizeof(A));
+    A.ns = (int)n;
+    bool adaptive = false;
+    for (uint32_t s = 0; s < n; s++) {
+        for (uint32_t t = 0; t < s; t++)
+            if (reqs[t].hist == reqs[s].hist)
+                return dof_set_error(DOF_ERR_INVALID_ARG, "dof_batch_frame: history %u appears twice", s);
+        int rc = make_desc(ctx, reqs[s], A.s[s]);
+        if (rc) return rc;
+        adaptive |= A.s[s].p.ray_mode == 1;
+        for (int sh = 0; sh < SH_COUNT; sh++) {
+            int gx, gy;
+            shape_grid(A.s[s], reqs[s].hist, sh, gx, gy);
+            A.s[s].gx[sh] = gx;
+            long long next = (long long)A.start[sh][s] + (long long)gx * gy;
+            if (next > 0x7FFFFFFFll) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_batch_frame: batch too large");
+            A.start[sh][s + 1] = (int)next;
+        }
+    }
+    A.cursor = &reqs[0].hist->counters[2];
+    DofHistory *tm = reqs[0].hist;
+    cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
+    if (tm->ev && tm->ev_used < kTimingSlots) {
+        // a kernel that is not launched this frame gets an event right after its predecessor's
+        for (int k = 0; k <= DOF_K_COUNT; k++) cudaEventRecord(tm->ev[tm->ev_slot * (DOF_K_COUNT + 1) + k], st);
+    } else {
+        tm = nullptr;
+    }
+    launch_reset_b(A, st);
+    launch_post_b(A, st, tm);
+    launch_mask_b(A, adaptive, st, tm);
+    launch_trace_b(A, ctx->sm_count, st, tm);
+    launch_temporal_b(A, st, tm);
+    launch_recon_b(A, st, tm);
+    int rc = dof_cuda_check(cudaGetLastError(), "dof_frame launch");
     if (rc) return rc;
-    h->cur ^= 1;
-    h->valid = 1;
-    h->frames++;
-    if (h->ev && h->ev_used < kTimingSlots) {
-        h->ev_slot = (h->ev_slot + 1) % kTimingSlots;
-        h->ev_used++;
+    for (uint32_t s = 0; s < n; s++) {
+        DofHistory *h = reqs[s].hist;
+        h->cur ^= 1;
+        h->valid = 1;
+        h->frames++;
+    }
+    if (tm) {
+        tm->ev_slot = (tm->ev_slot + 1) % kTimingSlots;
+        tm->ev_used++;
     }
     return DOF_OK;
+}
+
+extern "C" int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *gb, const DofCamera *cam,
+                         const DofParams *p, DofHistory *h, float *out, void *stream) {
+    if (!ctx || !scene || !gb || !cam || !p || !h || !out)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: null argument");
+    DofFrameReq r{scene, gb, cam, p, h, out};
+    DeviceGuard g(ctx->device);
+    return run_frames(ctx, &r, 1, (cudaStream_t)stream);
+}
+
+extern "C" int dof_batch_frame(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, void *stream) {
+    if (!ctx || (n && !reqs)) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_batch_frame: null argument");
+    DeviceGuard g(ctx->device);
+    return run_frames(ctx, reqs, n, (cudaStream_t)stream);
 }
 
 extern "C" int dof_kernel_times(DofHistory *h, void *stream, float *ms, uint32_t *frames) {
@@ -554,4 +676,64 @@ extern "C" int dof_debug_read(DofHistory *h, int which, void *dst, size_t bytes)
     rc = dof_cuda_check(cudaDeviceSynchronize(), "dof_debug_read sync");
     if (rc) return rc;
     return dof_cuda_check(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost), "dof_debug_read");
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint
+// ---------------------------------------------------------------------------
+
+namespace {
+struct HistHeader {
+    uint32_t magic, version, width, height, max_rays, valid;
+    uint64_t frames, n;
+};
+constexpr uint32_t kHistMagic = 0x48464F44u;   // "DOFH"
+}
+
+extern "C" int dof_history_export(DofHistory *h, void *buf, size_t *bytes, void *stream) {
+    if (!h || !bytes) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_export: null argument");
+    size_t N = h->N, need = sizeof(HistHeader) + 48 * N + 4 * N;
+    if (!buf) { *bytes = need; return DOF_OK; }
+    if (*bytes < need) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_export: buffer of %zu bytes, need %zu", *bytes, need);
+    DeviceGuard g(h->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = dof_cuda_check(cudaStreamSynchronize(st), "dof_history_export sync");
+    if (rc) return rc;
+    HistHeader hd{kHistMagic, 1u, h->W, h->H, h->max_rays, (uint32_t)h->valid, h->frames, N};
+    char *p = static_cast<char *>(buf);
+    memcpy(p, &hd, sizeof(hd));
+    rc = dof_cuda_check(cudaMemcpy(p + sizeof(hd), h->hist[h->cur], 48 * N, cudaMemcpyDeviceToHost), "export history");
+    if (rc == DOF_OK)
+        rc = dof_cuda_check(cudaMemcpy(p + sizeof(hd) + 48 * N, h->var_blur[h->cur], 4 * N, cudaMemcpyDeviceToHost),
+                            "export variance");
+    if (rc == DOF_OK) *bytes = need;
+    return rc;
+}
+
+extern "C" int dof_history_import(DofHistory *h, const void *buf, size_t bytes, void *stream) {
+    if (!h || !buf) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_import: null argument");
+    size_t N = h->N, need = sizeof(HistHeader) + 48 * N + 4 * N;
+    HistHeader hd;
+    if (bytes < sizeof(hd)) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_import: truncated buffer");
+    memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kHistMagic || hd.version != 1u)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_import: not a history checkpoint");
+    if (hd.width != h->W || hd.height != h->H || hd.max_rays != h->max_rays || hd.n != N)
+        return dof_set_error(DOF_ERR_MISMATCH, "dof_history_import: checkpoint of %ux%u (max_rays %u), history %ux%u (%u)",
+                             hd.width, hd.height, hd.max_rays, h->W, h->H, h->max_rays);
+    if (bytes < need) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_import: truncated buffer");
+    DeviceGuard g(h->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = dof_cuda_check(cudaStreamSynchronize(st), "dof_history_import sync");
+    if (rc) return rc;
+    const char *p = static_cast<const char *>(buf);
+    rc = dof_cuda_check(cudaMemcpy(h->hist[h->cur], p + sizeof(hd), 48 * N, cudaMemcpyHostToDevice), "import history");
+    if (rc == DOF_OK)
+        rc = dof_cuda_check(cudaMemcpy(h->var_blur[h->cur], p + sizeof(hd) + 48 * N, 4 * N, cudaMemcpyHostToDevice),
+                            "import variance");
+    if (rc == DOF_OK) {
+        h->valid = (int)hd.valid;
+        h->frames = hd.frames;
+    }
+    return rc;
 }

@@ -1,0 +1,91 @@
+// Batched launches of libdof: every pass of a frame runs as ONE launch over the
+// frames of all sessions of a batch.  A session descriptor holds the session's
+// camera, parameters, scene and buffers; the launch argument (a __grid_constant__
+// kernel parameter, no copy to device memory) holds up to kMaxBatch descriptors and,
+// per launch shape, the prefix of the sessions' block counts, so a block finds its
+// session by binary search and its position in that session's grid.
+#pragma once
+
+#include "dof_internal.cuh"
+
+enum LaunchShape {
+    SH_TILE8 = 0,   // one 8x8 block per max-CoC tile
+    SH_TILEDIL,     // 16x16 tiles per block
+    SH_HPX,         // 32x8 half-resolution pixels per block
+    SH_MIP1,        // 32x8 texels of mip level 1
+    SH_MIP2,
+    SH_MIP3,
+    SH_FPX,         // 32x8 full-resolution pixels per block
+    SH_SHADE,       // 128 queue entries per block
+    SH_COUNT
+};
+
+constexpr int kMaxBatch = DOF_MAX_BATCH;
+
+struct SessDesc {
+    DevCam cam;
+    DevParams p;
+    SceneDev sc;
+    int gx[SH_COUNT];              // blocks per row of each shape
+    int N, max_rays, valid, record_rays;
+    // frame inputs and output (caller-owned)
+    const float4 *color;
+    const float *depth;
+    const float4 *normal;
+    float4 *out;
+    // work buffers of the session (history-owned)
+    float4 *pp_in, *pre, *main_, *pp_med, *n_h, *zn, *crt, *rt_med, *recon, *rt;
+    float *z_h, *xn, *xf, *ct, *var;
+    float2 *tiles, *tiles_dil;
+    int32_t *nrays, *ray_prim;
+    uint32_t *queue, *first_ray, *ray_pix, *counters;
+    int2 *hits;
+    float4 *mip0[4];
+    float2 *mip1[4];
+    int mip_w[4], mip_h[4], mip_L;
+    // history ping-pong
+    const float4 *hist_in;
+    float4 *hist_out;
+    const float *var_in;           // blurred variance of the previous frame
+    float *var_out;
+};
+
+struct BatchArgs {
+    int ns;
+    int start[SH_COUNT][kMaxBatch + 1];
+    uint32_t *cursor;              // device word: ray cursor of the persistent tracer
+    SessDesc s[kMaxBatch];
+};
+
+#ifdef __CUDACC__
+// session of a flat block index for `shape`; *local = the block's index in that session
+__device__ __forceinline__ int find_session(const BatchArgs &A, int shape, int block, int &local) {
+    int lo = 0, hi = A.ns;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (A.start[shape][mid] <= block) lo = mid;
+        else hi = mid;
+    }
+    local = block - A.start[shape][lo];
+    return lo;
+}
+
+// 2D position of the calling thread for a 2D shape with blocks of blockDim
+__device__ __forceinline__ const SessDesc &block_session(const BatchArgs &A, int shape, int &i, int &j) {
+    int lb;
+    int s = find_session(A, shape, blockIdx.x, lb);
+    const SessDesc &S = A.s[s];
+    int gx = S.gx[shape];
+    i = (lb % gx) * blockDim.x + threadIdx.x;
+    j = (lb / gx) * blockDim.y + threadIdx.y;
+    return S;
+}
+#endif
+
+// host: launch wrappers per kernel group (post.cu, trace.cu, temporal.cu, recon.cu)
+void launch_post_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
+void launch_mask_b(const BatchArgs &A, bool any_adaptive, cudaStream_t st, DofHistory *timing);
+void launch_trace_b(const BatchArgs &A, int sm_count, cudaStream_t st, DofHistory *timing);
+void launch_temporal_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
+void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
+void launch_reset_b(const BatchArgs &A, cudaStream_t st);

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <atomic>
 #include <string>
 
 #include "../../include/dof.h"
@@ -70,7 +71,9 @@ constexpr int kMaxLargeTris = 64;
 
 struct DofCtx {
     int device;
-    size_t budget, in_use;
+    std::atomic<int> refs;         // 1 for the caller's handle + 1 per live scene / history
+    std::atomic<size_t> in_use;
+    size_t budget;
     int sm_count;
     int bvh_builder;               // DOF_BVH_PLOC or DOF_BVH_LBVH
     uint32_t *d_status;            // device status word of context-level launches
@@ -81,6 +84,7 @@ struct DofScene {
     uint32_t n_tris, n_nodes, depth;
     uint32_t n_tree, n_large;      // triangles in the tree / tested directly
     int root;
+    size_t tris_bytes, nodes_bytes;  // allocation sizes (for the context's budget)
     BvhNode *nodes;
     float4 *tris;
     size_t bytes;
@@ -128,7 +132,7 @@ constexpr int kTraversalStack = 96;
 
 // record the event that closes kernel `k` of the current frame (no-op without timing)
 inline void tmark(DofHistory *h, int k, cudaStream_t st) {
-    if (h->ev && h->ev_used < kTimingSlots) cudaEventRecord(h->ev[h->ev_slot * (DOF_K_COUNT + 1) + k + 1], st);
+    if (h && h->ev && h->ev_used < kTimingSlots) cudaEventRecord(h->ev[h->ev_slot * (DOF_K_COUNT + 1) + k + 1], st);
 }
 
 // ---------------------------------------------------------------------------
@@ -138,6 +142,8 @@ inline void tmark(DofHistory *h, int k, cudaStream_t st) {
 int dof_set_error(int code, const char *fmt, ...);
 int dof_cuda_check(cudaError_t e, const char *what);
 int dof_alloc(DofCtx *ctx, size_t bytes, void **ptr, size_t *acc);
+void ctx_retain(DofCtx *ctx);
+void ctx_release(DofCtx *ctx);   // frees the context with its last reference
 void dof_free(DofCtx *ctx, void *ptr, size_t bytes);
 
 // launch wrappers (one per kernel group, defined in the .cu files)
@@ -145,16 +151,6 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
                      const uint32_t *d_mat, int builder, cudaStream_t st);
 void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *color, float *depth,
                     float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st);
-void launch_post(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h,
-                 cudaStream_t st);
-void launch_mask(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h,
-                 cudaStream_t st);
-void launch_trace(const DevCam &cam, const DevParams &p, SceneDev sc, DofHistory *h, int sm_count,
-                  cudaStream_t st);
-void launch_temporal(const DevCam &cam, const DevParams &p, DofHistory *h, cudaStream_t st);
-void launch_recon(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h,
-                  float4 *out, cudaStream_t st);
-
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------

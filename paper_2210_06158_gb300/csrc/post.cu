@@ -1,7 +1,7 @@
 // Post-process stage of libdof (Section 3.1): CoC + 2x2 downscale + tile max,
 // tile dilation, 9-tap bilateral prefilter, 81-tap main gather filter (Eq. 1), and the
 // 3x3 median postfilter (a 19-exchange min/max network, Section 3.1.3).
-#include "dof_internal.cuh"
+#include "batch.cuh"
 #include "filters.cuh"
 
 namespace {
@@ -9,11 +9,16 @@ namespace {
 // A1: one 8x8 block per tile of half-resolution pixels.  Colour = mean of the 2x2
 // full-resolution block, depth = the nearest of the four (clamped to z_far), CoC
 // radius rho = clamp(c(z)/4) and normal of that sample; tile max of near and |rho|.
-__global__ void __launch_bounds__(64) k_downscale_tiles(DevCam cam, DevParams p, const float4 *__restrict__ color,
-                                                        const float *__restrict__ depth,
-                                                        const float4 *__restrict__ normal, float4 *pp_in,
-                                                        float *z_h, float4 *n_h, float2 *tiles) {
-    int i = blockIdx.x * 8 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+__global__ void __launch_bounds__(64) k_downscale_tiles(const __grid_constant__ BatchArgs A) {
+    int lb;
+    const SessDesc &S = A.s[find_session(A, SH_TILE8, blockIdx.x, lb)];
+    const DevCam &cam = S.cam;
+    const DevParams &p = S.p;
+    const int tx = lb % S.gx[SH_TILE8], ty = lb / S.gx[SH_TILE8];
+    const float4 *__restrict__ color = S.color;
+    const float *__restrict__ depth = S.depth;
+    const float4 *__restrict__ normal = S.normal;
+    int i = tx * 8 + threadIdx.x, j = ty * 8 + threadIdx.y;
     float nm = 0.f, am = 0.f;
     if (i < cam.W2 && j < cam.H2) {
         size_t f0 = (size_t)(2 * j) * cam.W + 2 * i, f1 = f0 + cam.W;
@@ -28,12 +33,12 @@ __global__ void __launch_bounds__(64) k_downscale_tiles(DevCam cam, DevParams p,
         float zm = z[k];
         float rho = fminf(fmaxf(0.25f * coc_of(cam, zm), -p.rmax_hpx), p.rmax_hpx);
         size_t q = (size_t)j * cam.W2 + i;
-        pp_in[q] = make_float4(0.25f * (c0.x + c1.x + c2.x + c3.x), 0.25f * (c0.y + c1.y + c2.y + c3.y),
+        S.pp_in[q] = make_float4(0.25f * (c0.x + c1.x + c2.x + c3.x), 0.25f * (c0.y + c1.y + c2.y + c3.y),
                                0.25f * (c0.z + c1.z + c2.z + c3.z), rho);
-        z_h[q] = zm;
+        S.z_h[q] = zm;
         if (p.ray_mode == 1) {
             size_t fk = (k < 2 ? f0 : f1) + (k & 1);
-            n_h[q] = __ldg(&normal[fk]);
+            S.n_h[q] = __ldg(&normal[fk]);
         }
         nm = fmaxf(0.f, -rho);
         am = fabsf(rho);
@@ -46,12 +51,16 @@ __global__ void __launch_bounds__(64) k_downscale_tiles(DevCam cam, DevParams p,
     int t = threadIdx.y * 8 + threadIdx.x;
     if ((t & 31) == 0) red[t >> 5] = make_float2(nm, am);
     __syncthreads();
-    if (t == 0) tiles[blockIdx.y * p.tiles_w + blockIdx.x] = make_float2(fmaxf(red[0].x, red[1].x), fmaxf(red[0].y, red[1].y));
+    if (t == 0) S.tiles[ty * p.tiles_w + tx] = make_float2(fmaxf(red[0].x, red[1].x), fmaxf(red[0].y, red[1].y));
 }
 
 // A2: max over the (2K+1)^2 tile neighbourhood
-__global__ void k_tile_dilate(DevParams p, const float2 *tiles, float2 *dil) {
-    int tx = blockIdx.x * blockDim.x + threadIdx.x, ty = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void k_tile_dilate(const __grid_constant__ BatchArgs A) {
+    int tx, ty;
+    const SessDesc &S = block_session(A, SH_TILEDIL, tx, ty);
+    const DevParams &p = S.p;
+    const float2 *tiles = S.tiles;
+    float2 *dil = S.tiles_dil;
     if (tx >= p.tiles_w || ty >= p.tiles_h) return;
     float nm = 0.f, am = 0.f;
     for (int y = max(ty - p.dil_k, 0); y <= min(ty + p.dil_k, p.tiles_h - 1); y++)
@@ -64,9 +73,14 @@ __global__ void k_tile_dilate(DevParams p, const float2 *tiles, float2 *dil) {
 }
 
 // A3: 9-tap bilateral prefilter, radius max(R/8, sqrt(2)/2), taps at angles k pi/4
-__global__ void k_prefilter(int W2, int H2, DevParams p, const float4 *__restrict__ pp_in,
-                            const float2 *__restrict__ dil, float4 *pre) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void k_prefilter(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const DevParams &p = S.p;
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float4 *__restrict__ pp_in = S.pp_in;
+    const float2 *__restrict__ dil = S.tiles_dil;
+    float4 *pre = S.pre;
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
     float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
@@ -116,12 +130,17 @@ __device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const De
     }
 }
 
-__global__ void __launch_bounds__(256) k_main_filter(int W2, int H2, DevParams p, const float4 *__restrict__ pre,
-                                                     const float *__restrict__ z_h, const float2 *__restrict__ dil,
-                                                     float4 *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void __launch_bounds__(256) k_main_filter(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const DevParams &p = S.p;
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float4 *__restrict__ pre = S.pre;
+    const float *__restrict__ z_h = S.z_h;
+    const float2 *__restrict__ dil = S.tiles_dil;
+    float4 *out = S.main_;
     const int reach = (int)ceilf(p.rmax_hpx) + 2;
-    const int bx = blockIdx.x * blockDim.x, by = blockIdx.y * blockDim.y;
+    const int bx = i - (int)threadIdx.x, by = j - (int)threadIdx.y;
     const bool interior = bx - reach >= 0 && by - reach >= 0 && bx + (int)blockDim.x + reach < W2 &&
                           by + (int)blockDim.y + reach < H2;
     if (i >= W2 || j >= H2) return;
@@ -137,8 +156,12 @@ __global__ void __launch_bounds__(256) k_main_filter(int W2, int H2, DevParams p
 }
 
 // A5: per-channel 3x3 median (clamp-to-edge)
-__global__ void k_median_pp(int W2, int H2, const float4 *__restrict__ src, float4 *dst) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void k_median_pp(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float4 *__restrict__ src = S.main_;
+    float4 *dst = S.pp_med;
     if (i >= W2 || j >= H2) return;
     float4 v[9];
     int n = 0;
@@ -158,20 +181,16 @@ __global__ void k_median_pp(int W2, int H2, const float4 *__restrict__ src, floa
 
 int post_init_tables() { return upload_filter_tables(); }
 
-void launch_post(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h, cudaStream_t st) {
-    dim3 b8(8, 8), gt(h->TW, h->TH);
-    k_downscale_tiles<<<gt, b8, 0, st>>>(cam, p, reinterpret_cast<const float4 *>(g->color), g->depth,
-                                         reinterpret_cast<const float4 *>(g->normal), h->pp_in, h->z_h, h->n_h,
-                                         h->tiles);
-    tmark(h, DOF_K_DOWNSCALE, st);
-    dim3 bt(16, 16), gtd((h->TW + 15) / 16, (h->TH + 15) / 16);
-    k_tile_dilate<<<gtd, bt, 0, st>>>(p, h->tiles, h->tiles_dil);
-    tmark(h, DOF_K_DILATE, st);
-    dim3 b(32, 8), gh((h->W2 + 31) / 32, (h->H2 + 7) / 8);
-    k_prefilter<<<gh, b, 0, st>>>(h->W2, h->H2, p, h->pp_in, h->tiles_dil, h->pre);
-    tmark(h, DOF_K_PREFILTER, st);
-    k_main_filter<<<gh, b, 0, st>>>(h->W2, h->H2, p, h->pre, h->z_h, h->tiles_dil, h->main_);
-    tmark(h, DOF_K_MAIN, st);
-    k_median_pp<<<gh, b, 0, st>>>(h->W2, h->H2, h->main_, h->pp_med);
-    tmark(h, DOF_K_MEDIAN_PP, st);
+void launch_post_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+    const int n = A.ns;
+    k_downscale_tiles<<<A.start[SH_TILE8][n], dim3(8, 8), 0, st>>>(A);
+    tmark(tm, DOF_K_DOWNSCALE, st);
+    k_tile_dilate<<<A.start[SH_TILEDIL][n], dim3(16, 16), 0, st>>>(A);
+    tmark(tm, DOF_K_DILATE, st);
+    k_prefilter<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    tmark(tm, DOF_K_PREFILTER, st);
+    k_main_filter<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    tmark(tm, DOF_K_MAIN, st);
+    k_median_pp<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    tmark(tm, DOF_K_MEDIAN_PP, st);
 }

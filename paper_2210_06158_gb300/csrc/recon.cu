@@ -3,16 +3,20 @@
 // reconstruction at LOD clamp(0.05 c_t, 0, 3) blended by b = clamp(2000 sigma^2, 0,
 // 0.9) (Section 3.2.4, Eq. 5, Eq. 8), and the per-pixel composite of sharp,
 // post-processed and ray-traced colour (Section 3.3, Eq. 6, Eq. 7).
-#include "dof_internal.cuh"
+#include "batch.cuh"
 #include "filters.cuh"
 
 namespace {
 
 // A10: lower median over the valid 3x3 neighbours: invalid slots are padded with
 // -inf / +inf so the median-of-9 network selects index (k-1)/2 of the k valid values
-__global__ void k_median_rt(int W2, int H2, const float4 *__restrict__ crt, const int32_t *__restrict__ nrays,
-                            float4 *dst) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void k_median_rt(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float4 *__restrict__ crt = S.crt;
+    const int32_t *__restrict__ nrays = S.nrays;
+    float4 *dst = S.rt_med;
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
     if (__ldg(&nrays[q]) <= 0) { dst[q] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
@@ -44,9 +48,15 @@ __global__ void k_median_rt(int W2, int H2, const float4 *__restrict__ crt, cons
 }
 
 // A11: mip level 0 = (rgb, h) * v and (c_t, 1) * v
-__global__ void k_mip0(int W2, int H2, const float4 *__restrict__ med, const float *__restrict__ ct,
-                       const int32_t *__restrict__ nrays, float4 *m0, float2 *m1) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void k_mip0(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float4 *__restrict__ med = S.rt_med;
+    const float *__restrict__ ct = S.ct;
+    const int32_t *__restrict__ nrays = S.nrays;
+    float4 *m0 = S.mip0[0];
+    float2 *m1 = S.mip1[0];
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
     float v = __ldg(&nrays[q]) > 0 ? 1.f : 0.f;
@@ -55,10 +65,16 @@ __global__ void k_mip0(int W2, int H2, const float4 *__restrict__ med, const flo
 }
 
 // 2x2 box average (clamp-to-edge for odd sizes)
-__global__ void k_mip_down(int w, int h, const float4 *__restrict__ s0, const float2 *__restrict__ s1, int wn,
-                           int hn, float4 *d0, float2 *d1) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= wn || j >= hn) return;
+template <int LEVEL>
+__global__ void k_mip_down(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_MIP1 + LEVEL - 1, i, j);
+    const int w = S.mip_w[LEVEL - 1], h = S.mip_h[LEVEL - 1], wn = S.mip_w[LEVEL], hn = S.mip_h[LEVEL];
+    const float4 *__restrict__ s0 = S.mip0[LEVEL - 1];
+    const float2 *__restrict__ s1 = S.mip1[LEVEL - 1];
+    float4 *d0 = S.mip0[LEVEL];
+    float2 *d1 = S.mip1[LEVEL];
+    if (LEVEL >= S.mip_L || i >= wn || j >= hn) return;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 b = make_float2(0.f, 0.f);
 #pragma unroll
@@ -130,12 +146,23 @@ __device__ __forceinline__ void recon_taps(const Mips &M, int i, int j, float R,
 
 // A11: reconstruction.  Blocks whose footprint (+-rmax + 2, at every level) lies
 // inside the image take taps without index clamping.
-__global__ void __launch_bounds__(256) k_recon(int W2, int H2, DevParams p, Mips M, const float4 *__restrict__ med,
-                                               const float *__restrict__ ct, const float *__restrict__ var_blur,
-                                               const int32_t *__restrict__ nrays, float4 *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void __launch_bounds__(256) k_recon(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const DevParams &p = S.p;
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    Mips M;
+    M.L = S.mip_L;
+    for (int l = 0; l < 4; l++) {
+        M.m0[l] = S.mip0[l]; M.m1[l] = S.mip1[l]; M.w[l] = S.mip_w[l]; M.h[l] = S.mip_h[l];
+    }
+    const float4 *__restrict__ med = S.rt_med;
+    const float *__restrict__ ct = S.ct;
+    const float *__restrict__ var_blur = S.var_out;
+    const int32_t *__restrict__ nrays = S.nrays;
+    float4 *out = S.recon;
     const int reach = (int)ceilf(p.rmax_hpx) + (2 << (M.L - 1)) + 2;
-    const int bx = blockIdx.x * blockDim.x, by = blockIdx.y * blockDim.y;
+    const int bx = i - (int)threadIdx.x, by = j - (int)threadIdx.y;
     const bool interior = bx - reach >= 0 && by - reach >= 0 && bx + (int)blockDim.x + reach < W2 &&
                           by + (int)blockDim.y + reach < H2;
     if (i >= W2 || j >= H2) return;
@@ -158,11 +185,17 @@ __global__ void __launch_bounds__(256) k_recon(int W2, int H2, DevParams p, Mips
 }
 
 // A12: composite per full-resolution pixel
-__global__ void __launch_bounds__(256) k_composite(DevCam cam, DevParams p, const float4 *__restrict__ color,
-                                                   const float *__restrict__ depth, const float4 *__restrict__ pp_med,
-                                                   const float4 *__restrict__ recon, const int32_t *__restrict__ nrays,
-                                                   float4 *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void __launch_bounds__(256) k_composite(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_FPX, i, j);
+    const DevCam &cam = S.cam;
+    const DevParams &p = S.p;
+    const float4 *__restrict__ color = S.color;
+    const float *__restrict__ depth = S.depth;
+    const float4 *__restrict__ pp_med = S.pp_med;
+    const float4 *__restrict__ recon = S.recon;
+    const int32_t *__restrict__ nrays = S.nrays;
+    float4 *out = S.out;
     if (i >= cam.W || j >= cam.H) return;
     size_t f = (size_t)j * cam.W + i;
     float z = fminf(__ldg(&depth[f]), p.z_far);
@@ -209,29 +242,18 @@ __global__ void __launch_bounds__(256) k_composite(DevCam cam, DevParams p, cons
 
 int recon_init_tables() { return upload_filter_tables(); }
 
-void launch_recon(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h, float4 *out,
-                  cudaStream_t st) {
-    dim3 b(32, 8), gh((h->W2 + 31) / 32, (h->H2 + 7) / 8);
-    k_median_rt<<<gh, b, 0, st>>>(h->W2, h->H2, h->crt, h->nrays, h->rt_med);
-    tmark(h, DOF_K_MEDIAN_RT, st);
-    k_mip0<<<gh, b, 0, st>>>(h->W2, h->H2, h->rt_med, h->ct, h->nrays, h->mip0[0], h->mip1[0]);
-    Mips M;
-    M.L = (int)ceilf(p.lod_max) + 1;
-    if (M.L > 4) M.L = 4;
-    if (M.L < 1) M.L = 1;
-    for (int l = 0; l < 4; l++) {
-        M.m0[l] = h->mip0[l]; M.m1[l] = h->mip1[l]; M.w[l] = h->mip_w[l]; M.h[l] = h->mip_h[l];
-    }
-    for (int l = 1; l < M.L; l++) {
-        dim3 gl((h->mip_w[l] + 31) / 32, (h->mip_h[l] + 7) / 8);
-        k_mip_down<<<gl, b, 0, st>>>(h->mip_w[l - 1], h->mip_h[l - 1], h->mip0[l - 1], h->mip1[l - 1], h->mip_w[l],
-                                     h->mip_h[l], h->mip0[l], h->mip1[l]);
-    }
-    tmark(h, DOF_K_MIPS, st);
-    k_recon<<<gh, b, 0, st>>>(h->W2, h->H2, p, M, h->rt_med, h->ct, h->var_blur[h->cur ^ 1], h->nrays, h->recon);
-    tmark(h, DOF_K_RECON, st);
-    dim3 gf((h->W + 31) / 32, (h->H + 7) / 8);
-    k_composite<<<gf, b, 0, st>>>(cam, p, reinterpret_cast<const float4 *>(g->color), g->depth, h->pp_med, h->recon,
-                                  h->nrays, out);
-    tmark(h, DOF_K_COMPOSITE, st);
+void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+    const int n = A.ns;
+    dim3 b(32, 8);
+    k_median_rt<<<A.start[SH_HPX][n], b, 0, st>>>(A);
+    tmark(tm, DOF_K_MEDIAN_RT, st);
+    k_mip0<<<A.start[SH_HPX][n], b, 0, st>>>(A);
+    k_mip_down<1><<<A.start[SH_MIP1][n], b, 0, st>>>(A);
+    k_mip_down<2><<<A.start[SH_MIP2][n], b, 0, st>>>(A);
+    k_mip_down<3><<<A.start[SH_MIP3][n], b, 0, st>>>(A);
+    tmark(tm, DOF_K_MIPS, st);
+    k_recon<<<A.start[SH_HPX][n], b, 0, st>>>(A);
+    tmark(tm, DOF_K_RECON, st);
+    k_composite<<<A.start[SH_FPX][n], b, 0, st>>>(A);
+    tmark(tm, DOF_K_COMPOSITE, st);
 }

@@ -3,7 +3,7 @@
 // position (3x3 neighbour fallback), an exponential moving average whose history
 // weight is the covered share of the bilinear footprint, merge on the hit ratio,
 // luminance moments and variance; then the 5x5 binomial blur of the variance.
-#include "dof_internal.cuh"
+#include "batch.cuh"
 
 namespace {
 
@@ -67,11 +67,18 @@ __device__ __forceinline__ float fetch(const float4 *__restrict__ H0, const floa
 //     sum a_k v_k + sum a_k (x_k - mean')^2,
 // which equals mean-of-squares' - mean'^2 exactly but without its cancellation (the
 // ray count of Eq. 4 multiplies the variance by 1e5).
-__global__ void __launch_bounds__(256) k_accumulate(DevCam cam, DevParams p, const float *__restrict__ z_h,
-                                                    const float4 *__restrict__ rt, const int32_t *__restrict__ nrays,
-                                                    const float4 *__restrict__ hin, int has_hist, float4 *hout,
-                                                    float4 *crt, float *ct, float *var) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const DevCam &cam = S.cam;
+    const DevParams &p = S.p;
+    const float *__restrict__ z_h = S.z_h;
+    const float4 *__restrict__ rt = S.rt;
+    const int32_t *__restrict__ nrays = S.nrays;
+    const float4 *__restrict__ hin = S.hist_in;
+    const int has_hist = S.valid;
+    float4 *hout = S.hist_out, *crt = S.crt;
+    float *ct = S.ct, *var = S.var;
     const int W2 = cam.W2, H2 = cam.H2;
     if (i >= W2 || j >= H2) return;
     const size_t N = (size_t)W2 * H2, q = (size_t)j * W2 + i;
@@ -153,8 +160,12 @@ __global__ void __launch_bounds__(256) k_accumulate(DevCam cam, DevParams p, con
 }
 
 // 5x5 binomial blur of the variance, clamp-to-edge
-__global__ void k_var_blur(int W2, int H2, const float *__restrict__ v, float *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void k_var_blur(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float *__restrict__ v = S.var;
+    float *out = S.var_out;
     if (i >= W2 || j >= H2) return;
     const float b[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
     float acc = 0.f;
@@ -171,12 +182,23 @@ __global__ void k_var_blur(int W2, int H2, const float *__restrict__ v, float *o
 
 }  // namespace
 
-void launch_temporal(const DevCam &cam, const DevParams &p, DofHistory *h, cudaStream_t st) {
-    dim3 b(32, 8), g((h->W2 + 31) / 32, (h->H2 + 7) / 8);
-    int nxt = h->cur ^ 1;
-    k_accumulate<<<g, b, 0, st>>>(cam, p, h->z_h, h->rt, h->nrays, h->hist[h->cur], h->valid, h->hist[nxt], h->crt,
-                                  h->ct, h->var);
-    tmark(h, DOF_K_ACCUM, st);
-    k_var_blur<<<g, b, 0, st>>>(h->W2, h->H2, h->var, h->var_blur[nxt]);
-    tmark(h, DOF_K_VAR_BLUR, st);
+void launch_temporal_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+    const int n = A.ns;
+    k_accumulate<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    tmark(tm, DOF_K_ACCUM, st);
+    k_var_blur<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    tmark(tm, DOF_K_VAR_BLUR, st);
 }
+
+// zero the per-frame counters of every session and the batch's ray cursor
+__global__ void k_reset(const __grid_constant__ BatchArgs A) {
+    int s = threadIdx.x;
+    if (s == 0) *A.cursor = 0u;
+    if (s < A.ns) {
+        uint32_t *c = A.s[s].counters;
+        c[0] = c[1] = c[2] = 0u;
+        c[4] = c[5] = c[6] = c[7] = 0u;
+    }
+}
+
+void launch_reset_b(const BatchArgs &A, cudaStream_t st) { k_reset<<<1, kMaxBatch, 0, st>>>(A); }

@@ -2,7 +2,7 @@
 // warp-aggregated compaction into a ray queue (Section 3.2.1, Eq. 2-4), and the
 // persistent thin-lens ray kernel (Section 3.2.2): Philox lens samples, closest hit
 // through the LBVH, Lambert shading and the per-pixel near/far split.
-#include "dof_internal.cuh"
+#include "batch.cuh"
 
 namespace {
 
@@ -224,9 +224,14 @@ __global__ void k_primary(DevCam cam, DevParams p, SceneDev sc, float4 *color, f
 // A6: edge measure for the adaptive ray count (Eq. 2, Eq. 3)
 // ---------------------------------------------------------------------------
 // 5x5 binomial blur of (z, n.xyz) packed as float4, clamp-to-edge
-__global__ void k_blur_zn(int W2, int H2, const float *z_h, const float4 *n_h, float4 *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= W2 || j >= H2) return;
+__global__ void k_blur_zn(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float *z_h = S.z_h;
+    const float4 *n_h = S.n_h;
+    float4 *out = S.zn;
+    if (S.p.ray_mode != 1 || i >= W2 || j >= H2) return;
     const float b[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int dy = -2; dy <= 2; dy++) {
@@ -243,10 +248,16 @@ __global__ void k_blur_zn(int W2, int H2, const float *z_h, const float4 *n_h, f
 }
 
 // 5x5 Sobel ([-1 -2 0 2 1] x [1 4 6 4 1] / 128) -> x_n (Eq. 2, 3) and x_f (Eq. 4)
-__global__ void k_edges(int W2, int H2, const float4 *zn, const float *var_prev, int has_prev, DevParams p,
-                        float *xn, float *xf) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= W2 || j >= H2) return;
+__global__ void k_edges(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const DevParams &p = S.p;
+    const float4 *zn = S.zn;
+    const float *var_prev = S.var_in;
+    const int has_prev = S.valid;
+    float *xn = S.xn, *xf = S.xf;
+    if (p.ray_mode != 1 || i >= W2 || j >= H2) return;
     const float sm[5] = {1.f, 4.f, 6.f, 4.f, 1.f}, dv[5] = {-1.f, -2.f, 0.f, 2.f, 1.f};
     float4 gx = make_float4(0.f, 0.f, 0.f, 0.f), gy = gx;
     for (int dy = -2; dy <= 2; dy++) {
@@ -277,10 +288,15 @@ __global__ void k_edges(int W2, int H2, const float4 *zn, const float *var_prev,
 // Per block (32 x 8 pixels, one warp per row) one atomic reserves room for the
 // block's masked pixels (queue) and their rays (ray list); inside the block the
 // order is raster order, so neighbouring rays stay neighbours in the list.
-__global__ void __launch_bounds__(256) k_mask_compact(int W2, int H2, DevParams p, const float2 *tiles_dil,
-                                                      const float *xf, int32_t *nrays, uint32_t *queue,
-                                                      uint32_t *first_ray, uint32_t *ray_pix, uint32_t *counters) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ BatchArgs A) {
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const DevParams &p = S.p;
+    const float2 *tiles_dil = S.tiles_dil;
+    const float *xf = S.xf;
+    int32_t *nrays = S.nrays;
+    uint32_t *queue = S.queue, *first_ray = S.first_ray, *ray_pix = S.ray_pix, *counters = S.counters;
     const unsigned lane = threadIdx.x, warp = threadIdx.y;
     int n = 0;
     uint32_t q = 0;
@@ -357,52 +373,76 @@ constexpr int kStepsPerRound = 16;
 // dynamic fetch): lanes whose ray has finished take new rays from the ray list when
 // enough of the warp is idle, so divergent rays do not hold the warp.  Writes the
 // closest hit of each ray: (sorted triangle index or -1, t).
-__global__ void __launch_bounds__(128) k_trace_rays(DevCam cam, DevParams p, SceneDev sc, const uint32_t *ray_pix,
-                                                    const uint32_t *first_ray, uint32_t *counters, int2 *hits) {
+__global__ void __launch_bounds__(128) k_trace_rays(const __grid_constant__ BatchArgs A) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-    const uint32_t total = *((volatile uint32_t *)&counters[1]);
-    const int n_nodes = sc.n_tris - 1;
-    const long long max_steps = 4ll * sc.n_tris + 64;
-    uint32_t *status = &counters[3];
+    // inclusive prefix of the sessions' ray counts (the batch's concatenated ray list)
+    __shared__ uint32_t pre[kMaxBatch];
+    if (threadIdx.x < 32) {
+        uint32_t c = lane < (unsigned)A.ns ? *((volatile uint32_t *)&A.s[lane].counters[1]) : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, c, o);
+            if ((int)lane >= o) c += v;
+        }
+        pre[lane] = c;
+    }
+    __syncthreads();
+    const uint32_t total = pre[A.ns - 1];
     uint32_t n_visit = 0, n_tests = 0;
     bool have = false, exhausted = false;
     uint32_t r = 0;
+    int si = 0;
     Ray ray;
     HitRec h{INFINITY, -1, -1};
-    int node = 0, sp = 0;
-    long long steps = 0;
+    int node = 0, sp = 0, n_tree = 0, n_nodes = 0;
+    const BvhNode *nodes = nullptr;
+    const float4 *tris = nullptr;
+    long long steps = 0, max_steps = 0;
     int stack[kStack];
     while (true) {
         unsigned idle = __ballot_sync(0xffffffffu, !have);
         if (idle == 0xffffffffu || (!exhausted && __popc(idle) >= kRefillIdle)) {
             uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&counters[2], (uint32_t)__popc(idle));
+            if (lane == 0) base = atomicAdd(A.cursor, (uint32_t)__popc(idle));
             base = __shfl_sync(0xffffffffu, base, 0);
             if (base >= total) exhausted = true;
             if (!have) {
-                uint32_t mine = base + __popc(idle & lt);
-                if (mine < total) {
-                    r = mine;
-                    uint32_t q = __ldg(&ray_pix[r]);
-                    int s = (int)(r - __ldg(&first_ray[q]));
+                uint32_t g = base + __popc(idle & lt);
+                if (g < total) {
+                    // session of global ray g: the first s with pre[s] > g
+                    int lo = 0, hi = A.ns - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi) >> 1;
+                        if (pre[mid] > g) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    si = lo;
+                    const SessDesc &S = A.s[si];
+                    r = g - (si > 0 ? pre[si - 1] : 0u);
+                    uint32_t q = __ldg(&S.ray_pix[r]);
+                    int sm = (int)(r - __ldg(&S.first_ray[q]));
                     float3 L, dir;
-                    lens_ray(cam, p, q, s, L, dir);
+                    lens_ray(S.cam, S.p, q, sm, L, dir);
                     ray = make_ray(L, dir);
+                    nodes = S.sc.nodes;
+                    tris = S.sc.tris;
+                    n_tree = S.sc.n_tris;
+                    n_nodes = n_tree - 1;
                     h = HitRec{INFINITY, -1, -1};
-                    for (int k = sc.n_tris; k < sc.n_tris + sc.n_large; k++) {
+                    for (int k = n_tree; k < n_tree + S.sc.n_large; k++) {
                         n_tests++;
-                        const float4 *tp = sc.tris + 3 * (size_t)k;
+                        const float4 *tp = tris + 3 * (size_t)k;
                         float t = tri_hit(ray, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
                         if (t > 0.f) {
                             int prim = __float_as_int(__ldg(tp).w);
                             if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
                         }
                     }
-                    node = sc.root;
+                    node = S.sc.root;
                     sp = 0;
                     steps = 0;
-                    have = sc.n_tris > 0;
-                    if (!have) hits[r] = make_int2(h.k, __float_as_int(h.t));
+                    max_steps = 4ll * n_tree + 64;
+                    have = n_tree > 0;
+                    if (!have) S.hits[r] = make_int2(h.k, __float_as_int(h.t));
                 }
             }
             if (__ballot_sync(0xffffffffu, have) == 0 && exhausted) break;
@@ -410,12 +450,12 @@ __global__ void __launch_bounds__(128) k_trace_rays(DevCam cam, DevParams p, Sce
         if (!have) continue;
         for (int it = 0; it < kStepsPerRound; it++) {
             bool done = false;
-            if (++steps > max_steps || node >= n_nodes || (node < 0 && ~node >= sc.n_tris)) {
-                atomicOr(status, 2u);
+            if (++steps > max_steps || node >= n_nodes || (node < 0 && ~node >= n_tree)) {
+                atomicOr(&A.s[si].counters[3], 2u);
                 done = true;
             } else if (node >= 0) {
                 n_visit++;
-                const float4 *np = reinterpret_cast<const float4 *>(sc.nodes + node);
+                const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
                 float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
                 int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
                 float t0, t1;
@@ -424,7 +464,7 @@ __global__ void __launch_bounds__(128) k_trace_rays(DevCam cam, DevParams p, Sce
                 if (h0 && h1) {
                     int nearc = t0 <= t1 ? ref.x : ref.y, farc = t0 <= t1 ? ref.y : ref.x;
                     if (sp < kStack) stack[sp++] = farc;
-                    else atomicOr(status, 1u);
+                    else atomicOr(&A.s[si].counters[3], 1u);
                     node = nearc;
                     continue;
                 }
@@ -435,7 +475,7 @@ __global__ void __launch_bounds__(128) k_trace_rays(DevCam cam, DevParams p, Sce
             } else {
                 n_tests++;
                 int k = ~node;
-                const float4 *tp = sc.tris + 3 * (size_t)k;
+                const float4 *tp = tris + 3 * (size_t)k;
                 float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
                 float t = tri_hit(ray, v0, v1, v2);
                 if (t > 0.f) {
@@ -446,33 +486,42 @@ __global__ void __launch_bounds__(128) k_trace_rays(DevCam cam, DevParams p, Sce
                 else node = stack[--sp];
             }
             if (done) {
-                hits[r] = make_int2(h.k, __float_as_int(h.t));
+                A.s[si].hits[r] = make_int2(h.k, __float_as_int(h.t));
                 have = false;
                 break;
             }
         }
     }
-    // traversal work of the frame (node visits, triangle tests), one atomic per warp
+    // traversal work (node visits, triangle tests), one atomic per warp, booked on the
+    // first session of the batch
     unsigned long long a = n_visit, b = n_tests;
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
     }
     if (lane == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&counters[4]), a);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&counters[6]), b);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.s[0].counters[4]), a);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.s[0].counters[6]), b);
     }
 }
 
 // Shading and the per-pixel near/far split of the masked pixel queue[e]: its rays
 // are regenerated (bit-identical to the tracer's), shaded at their recorded hits and
 // reduced in sample order.
-__global__ void __launch_bounds__(128) k_shade(DevCam cam, DevParams p, SceneDev sc, const uint32_t *queue,
-                                               const int32_t *nrays, const uint32_t *first_ray,
-                                               const uint32_t *counters, const int2 *hits, float4 *rt,
-                                               int32_t *ray_prim, int max_rays) {
-    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t count = *((volatile const uint32_t *)&counters[0]);
+__global__ void __launch_bounds__(128) k_shade(const __grid_constant__ BatchArgs A) {
+    int lb;
+    const SessDesc &S = A.s[find_session(A, SH_SHADE, blockIdx.x, lb)];
+    const DevCam &cam = S.cam;
+    const DevParams &p = S.p;
+    const SceneDev &sc = S.sc;
+    const uint32_t *queue = S.queue, *first_ray = S.first_ray;
+    const int32_t *nrays = S.nrays;
+    const int2 *hits = S.hits;
+    float4 *rt = S.rt;
+    int32_t *ray_prim = S.record_rays ? S.ray_prim : nullptr;
+    const int max_rays = S.max_rays;
+    const uint32_t e = lb * blockDim.x + threadIdx.x;
+    const uint32_t count = *((volatile const uint32_t *)&S.counters[0]);
     if (e >= count) return;
     const size_t N = (size_t)cam.W2 * cam.H2;
     const float inv_sqrt2 = 0.70710678118654752f;
@@ -527,27 +576,20 @@ void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *
     k_primary<<<g, b, 0, st>>>(cam, p, sc, color, depth, normal, prim, status);
 }
 
-void launch_mask(const DevCam &cam, const DevParams &p, const DofGBuffer *g, DofHistory *h, cudaStream_t st) {
-    (void)g;
-    dim3 b(32, 8), gr((h->W2 + 31) / 32, (h->H2 + 7) / 8);
-    if (p.ray_mode == 1) {
-        float4 *zn = h->crt;   // scratch: crt is only written later, by the accumulation
-        k_blur_zn<<<gr, b, 0, st>>>(h->W2, h->H2, h->z_h, h->n_h, zn);
-        k_edges<<<gr, b, 0, st>>>(h->W2, h->H2, zn, h->var_blur[h->cur], h->valid, p, h->xn, h->xf);
+void launch_mask_b(const BatchArgs &A, bool any_adaptive, cudaStream_t st, DofHistory *tm) {
+    const int n = A.ns;
+    if (any_adaptive) {
+        k_blur_zn<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+        k_edges<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
     }
-    tmark(h, DOF_K_EDGES, st);
-    k_mask_compact<<<gr, b, 0, st>>>(h->W2, h->H2, p, h->tiles_dil, h->xf, h->nrays, h->queue, h->first_ray,
-                                     h->ray_pix, h->counters);
-    tmark(h, DOF_K_MASK, st);
+    tmark(tm, DOF_K_EDGES, st);
+    k_mask_compact<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    tmark(tm, DOF_K_MASK, st);
 }
 
-void launch_trace(const DevCam &cam, const DevParams &p, SceneDev sc, DofHistory *h, int sm_count,
-                  cudaStream_t st) {
-    int blocks = sm_count * 8;
-    k_trace_rays<<<blocks, 128, 0, st>>>(cam, p, sc, h->ray_pix, h->first_ray, h->counters, h->hits);
-    tmark(h, DOF_K_TRACE, st);
-    k_shade<<<(unsigned)((h->N + 127) / 128), 128, 0, st>>>(
-        cam, p, sc, h->queue, h->nrays, h->first_ray, h->counters, h->hits, h->rt,
-        (h->flags & DOF_HIST_RECORD_RAYS) ? h->ray_prim : nullptr, (int)h->max_rays);
-    tmark(h, DOF_K_SHADE, st);
+void launch_trace_b(const BatchArgs &A, int sm_count, cudaStream_t st, DofHistory *tm) {
+    k_trace_rays<<<sm_count * 8, 128, 0, st>>>(A);
+    tmark(tm, DOF_K_TRACE, st);
+    k_shade<<<A.start[SH_SHADE][A.ns], 128, 0, st>>>(A);
+    tmark(tm, DOF_K_SHADE, st);
 }

@@ -65,6 +65,14 @@ class DofGBuffer(C.Structure):
                 ("width", C.c_uint32), ("height", C.c_uint32), ("fmt", C.c_uint32)]
 
 
+class DofFrameReq(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("gbuf", C.POINTER(DofGBuffer)), ("cam", C.POINTER(DofCamera)),
+                ("params", C.POINTER(DofParams)), ("hist", C.c_void_p), ("out", C.c_void_p)]
+
+
+MAX_BATCH = 32
+
+
 class DofSceneInfo(C.Structure):
     _fields_ = [("n_tris", C.c_uint32), ("n_nodes", C.c_uint32), ("depth", C.c_uint32),
                 ("stack_limit", C.c_uint32), ("device_bytes", C.c_uint64),
@@ -95,9 +103,12 @@ _SIGS = {
                                      C.POINTER(C.c_void_p)]),
     "dof_history_destroy": (None, [C.c_void_p]),
     "dof_history_reset": (C.c_int, [C.c_void_p]),
+    "dof_history_export": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t), C.c_void_p]),
+    "dof_history_import": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dof_frame": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofGBuffer), C.POINTER(DofCamera),
                             C.POINTER(DofParams), C.c_void_p, C.c_void_p, C.c_void_p]),
     "dof_frame_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofFrameStats)]),
+    "dof_batch_frame": (C.c_int, [C.c_void_p, C.POINTER(DofFrameReq), C.c_uint32, C.c_void_p]),
     "dof_debug_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
     "dof_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
     "dof_debug_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
@@ -246,6 +257,19 @@ class History:
     def reset(self):
         _check(lib().dof_history_reset(self.ptr))
 
+    def export(self, stream=None) -> bytes:
+        """Checkpoint of the session (host bytes)."""
+        n = C.c_size_t()
+        _check(lib().dof_history_export(self.ptr, None, C.byref(n), _stream_ptr(stream)))
+        buf = (C.c_char * n.value)()
+        _check(lib().dof_history_export(self.ptr, buf, C.byref(n), _stream_ptr(stream)))
+        return bytes(buf[:n.value])
+
+    def load(self, data: bytes, stream=None):
+        """Resume from a checkpoint made by export()."""
+        buf = C.create_string_buffer(data, len(data))
+        _check(lib().dof_history_import(self.ptr, buf, len(data), _stream_ptr(stream)))
+
     def stats(self, stream=None) -> DofFrameStats:
         s = DofFrameStats()
         _check(lib().dof_frame_stats(self.ptr, _stream_ptr(stream), C.byref(s)))
@@ -338,3 +362,34 @@ def coc_tiles_noalloc(depth, cam, params, out=None, stream=None):
     c, p = camera_struct(cam), params_struct(params)
     _check(lib().dof_coc_tiles_noalloc(_ptr(depth), W, H, C.byref(c), C.byref(p), _ptr(out), _stream_ptr(stream)))
     return out
+
+
+def batch_frame(ctx: Context, items, stream=None):
+    """Frames of several sessions in one launch per pass.  items: list of dicts with
+    keys scene (Scene), gbuf (dict of device tensors), cam (synth.Camera or a
+    DofCamera), params (dict or DofParams), hist (History), out (tensor, optional).
+    Returns the output tensors."""
+    import torch
+    n = len(items)
+    reqs = (DofFrameReq * max(1, n))()
+    keep = []
+    outs = []
+    for k, it in enumerate(items):
+        gb = it["gbuf"]
+        H, W = gb["depth"].shape
+        out = it.get("out")
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.float32, device=gb["depth"].device)
+        g = gbuffer_struct(gb["color"], gb["depth"], gb.get("normal"))
+        c = it["cam"] if isinstance(it["cam"], DofCamera) else camera_struct(it["cam"])
+        p = it["params"] if isinstance(it["params"], DofParams) else params_struct(it["params"])
+        keep += [g, c, p]
+        reqs[k].scene = it["scene"].ptr
+        reqs[k].gbuf = C.pointer(g)
+        reqs[k].cam = C.pointer(c)
+        reqs[k].params = C.pointer(p)
+        reqs[k].hist = it["hist"].ptr
+        reqs[k].out = out.data_ptr()
+        outs.append(out)
+    _check(lib().dof_batch_frame(ctx.ptr, reqs, n, _stream_ptr(stream)))
+    return outs

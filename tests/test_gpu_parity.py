@@ -236,6 +236,65 @@ def test_max_spp_and_history_reset():
     assert np.array_equal(a, b)
 
 
+def test_checkpoint_resume_bit_identical():
+    """export after frame 1, import into a fresh history: frame 2 is bit-identical to the
+    uninterrupted session (history + counter-based lens samples are the whole state)."""
+    from paper_2210_06158_gb300 import dof
+    w = make_workload("c2", W=320, H=180, n_frames=3)
+    osc = oracle.Scene(w.scene)
+    gbs = [oracle.gbuffer_f32(oracle.gbuffer(osc, w.camera(k), w.params, w.W, w.H)) for k in range(3)]
+    a = GpuRunner(w, w.params)
+    for k in range(2):
+        a.frame(w.camera(k), gbs[k], read=False)
+    ck = a.hist.export()
+    b = GpuRunner(w, w.params, ctx=a.ctx)
+    b.hist.load(ck)
+    out_a = a.frame(w.camera(2), gbs[2])
+    out_b = b.frame(w.camera(2), gbs[2])
+    assert np.array_equal(out_a["out"], out_b["out"])
+    assert np.array_equal(out_a["hist"], out_b["hist"])
+    other = dof.History(a.ctx, 322, 180)
+    with pytest.raises(dof.DofError) as e:
+        other.load(ck)
+    assert e.value.code == -7
+
+
+def test_batch_equals_alone():
+    """dof_batch_frame over sessions of different sizes, scenes, lenses and ray modes
+    gives, for every session, exactly what dof_frame gives for it alone."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    dev = torch.device("cuda", 0)
+    specs = [("c1", 256, 144, {}), ("c2", 322, 182, {}), ("c3", 192, 108, {}), ("c1", 130, 74, dict(ray_mode=1, m=4))]
+    ctx = dof.Context(0)
+    sess = []
+    for k, (name, W, H, over) in enumerate(specs):
+        w = make_workload(name, W=W, H=H, n_frames=2, session=k)
+        if w.n_frames < 2:
+            w.poses = [w.poses[0]] * 2            # a static camera for the one-pose workload
+        prm = dict(w.params, **over)
+        osc = oracle.Scene(w.scene)
+        gbs = []
+        for f in range(2):
+            gb = oracle.gbuffer_f32(oracle.gbuffer(osc, w.camera(f), prm, W, H))
+            gbs.append({kk: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for kk, v in gb.items()})
+        sc = dof.Scene(ctx, w.scene)
+        mr = oracle.max_rays(prm)
+        sess.append(dict(w=w, prm=prm, gbs=gbs, sc=sc, alone=dof.History(ctx, W, H, mr),
+                         mixed=dof.History(ctx, W, H, mr)))
+    for f in range(2):
+        alone = [dof.frame(ctx, s["sc"], s["gbs"][f], s["w"].camera(f), s["prm"], s["alone"]).clone() for s in sess]
+        mixed = dof.batch_frame(ctx, [dict(scene=s["sc"], gbuf=s["gbs"][f], cam=s["w"].camera(f), params=s["prm"],
+                                           hist=s["mixed"]) for s in sess])
+        torch.cuda.synchronize()
+        for k in range(len(sess)):
+            assert torch.equal(alone[k], mixed[k]), (f, k)
+    with pytest.raises(dof.DofError):
+        s = sess[0]
+        dof.batch_frame(ctx, [dict(scene=s["sc"], gbuf=s["gbs"][0], cam=s["w"].camera(0), params=s["prm"],
+                                   hist=s["mixed"])] * 2)
+
+
 def test_determinism_bit_identical():
     w = make_workload("c2", W=320, H=180, n_frames=2)
     osc = oracle.Scene(w.scene)
@@ -277,6 +336,15 @@ def test_host_validation_errors():
     with pytest.raises(dof.DofError) as e:
         dof.History(ctx, 63, 36)
     assert e.value.code == -1
+    # handles may be released in any order (the context outlives its scene and history)
+    c2 = dof.Context(0)
+    sc2 = dof.Scene(c2, w.scene)
+    h2 = dof.History(c2, 64, 36)
+    used = c2.bytes_in_use
+    assert used > 0
+    c2.close()
+    h2.close()
+    sc2.close()
     small = dof.Context(0, mem_budget_bytes=1 << 16)
     with pytest.raises(dof.DofError) as e:
         dof.History(small, 640, 360)
