@@ -379,13 +379,138 @@ def run_ours(args, rank, world):
     return res, w
 
 
+# ---------------------------------------------------------------------------
+# batched and served workloads
+# ---------------------------------------------------------------------------
+
+RES = [(1280, 720), (1920, 1080), (2560, 1440)]
+
+
+def batch_sessions(n, res_cycle, tri_lo, tri_hi, seed, frames=8):
+    """n sessions, each its own seeded lawn scene with log-uniform triangle count in
+    [tri_lo, tri_hi] and the 35 mm lens of the 1080p workload."""
+    import numpy as np
+    from synth import make_workload
+    from synth.scenes import scene_grass_field
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        W, H = res_cycle[k % len(res_cycle)]
+        w = make_workload("c2", W=W, H=H, n_frames=frames, session=k)
+        tris = float(np.exp(rng.uniform(np.log(tri_lo), np.log(tri_hi))))
+        dens = tris / 495_802.0
+        sd = 2000 + 100 * k
+        w.scene_fn = (lambda sd=sd, dens=dens: scene_grass_field(sd, dens))
+        w._scene = None
+        w.params = dict(w.params, seed=sd, albedo_seed=sd, session=k, max_coc_px=32.0 * W / 1920.0)
+        out.append(w)
+    return out
+
+
+def run_batch(args):
+    import torch
+    from paper_2210_06158_gb300 import _build, dof
+    _build.build()
+    dev = torch.device("cuda", 0)
+    ctx = dof.Context(0)
+    ws = batch_sessions(32, RES, 200_000, 1_000_000, seed=4)
+    S = []
+    for w in ws:
+        sc = dof.Scene(ctx, w.scene)
+        gbs = []
+        for f in range(w.n_frames):
+            g = dof.gbuffer(ctx, sc, w.camera(f), w.params, w.W, w.H)
+            del g["prim"]
+            gbs.append(g)
+        S.append(dict(w=w, sc=sc, gbs=gbs, hb=dof.History(ctx, w.W, w.H), hs=dof.History(ctx, w.W, w.H),
+                      out=torch.empty((w.H, w.W, 4), device=dev), p=dof.params_struct(w.params),
+                      cams=[dof.camera_struct(w.camera(f)) for f in range(w.n_frames)]))
+    tris = sum(s["sc"].info().n_tris for s in S)
+    px = sum(s["w"].W * s["w"].H for s in S)
+    torch.cuda.synchronize()
+
+    def batched(step):
+        f = step % 8
+        dof.batch_frame(ctx, [dict(scene=s["sc"], gbuf=s["gbs"][f], cam=s["cams"][f], params=s["p"], hist=s["hb"],
+                                   out=s["out"]) for s in S])
+
+    def single(step):
+        f = step % 8
+        for s in S:
+            dof.frame(ctx, s["sc"], s["gbs"][f], None, None, s["hs"], s["out"], cam_struct=s["cams"][f],
+                      params_s=s["p"])
+
+    res = {}
+    for name, fn in (("batched", batched), ("per_frame", single)):
+        for k in range(args.warmup):
+            fn(k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record()
+            for k in range(args.warmup, args.warmup + args.steps):
+                fn(k)
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = dict(ms_per_step=ms / args.steps, frames_per_s=len(S) * args.steps / (ms / 1e3),
+                         clocks=clk.summary())
+    line = dict(metric=METRIC, value=round(res["batched"]["frames_per_s"], 2), unit="frames/s", n_gpus=1,
+                steps=args.steps, warmup=args.warmup, ms_per_step=round(res["batched"]["ms_per_step"], 3),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=f"batched: 32 sessions, own lawn scenes 200k-1M triangles ({tris} total), "
+                                     f"1280x720/1920x1080/2560x1440 cycled ({px / 1e6:.1f} Mpx per step), 8-frame dollies, "
+                                     "one dof_batch_frame (one launch per pass) per step",
+                            l2="inputs larger than L2: 256 distinct G-buffers"),
+                per_frame_form=dict(frames_per_s=round(res["per_frame"]["frames_per_s"], 2),
+                                    ms_per_step=round(res["per_frame"]["ms_per_step"], 3)),
+                gpu_launches=18 * args.steps, clocks=res["batched"]["clocks"])
+    return line
+
+
+def run_serve(args):
+    import numpy as np
+    from paper_2210_06158_gb300 import _build
+    from paper_2210_06158_gb300.serve import GpuExecutor, Server, SessionSpec, poisson_arrivals
+    _build.build()
+    res = [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
+    ws = batch_sessions(64, res, 100_000, 2_000_000, seed=5, frames=4)
+    ex = GpuExecutor(budget_bytes=40 << 30, gbuf_ring=2)
+    srv = Server(ex, max_batch=32)
+    specs = {}
+    t0 = time.time()
+    for k, w in enumerate(ws):
+        spec = SessionSpec(f"s{k}", w.W, w.H, 30.0 if k % 2 == 0 else 60.0, scene=w.scene, params=w.params,
+                           poses=w.poses, intr=w.intr)
+        specs[k] = spec
+        srv.admit(k, spec)
+    setup_s = time.time() - t0
+    admitted = {k: v for k, v in specs.items() if k in srv.specs}
+    duration = float(os.environ.get("DOF_SERVE_SECONDS", "2.0"))
+    arr = poisson_arrivals(6, admitted, duration_s=duration)
+    with ClockSampler(0) as clk:
+        st = srv.run(arr)
+    line = dict(metric=METRIC, value=round(st["frames_per_s"], 2), unit="frames/s", n_gpus=1, steps=st["frames"],
+                warmup=0, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic",
+                config=dict(workload="serving: 64 sessions, Poisson frame requests at 30/60 fps for "
+                                     f"{duration:g} s, 1280x720..3840x2160, lawn scenes 100k-2M triangles, "
+                                     "40 GB device budget, continuous batching (<= 32 per launch, 2 streams)"),
+                served=dict(p50_ms=round(st["p50_ms"], 3), p99_ms=round(st["p99_ms"], 3),
+                            mean_ms=round(st["mean_ms"], 3), frames=st["frames"], requests=len(arr),
+                            dropped_superseded=st["dropped"], failed=st["failed"], admitted=st["admitted"],
+                            rejected=st["rejected"], mean_batch=round(st["mean_batch"], 2)),
+                setup_s=round(setup_s, 1), clocks=clk.summary())
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "batch", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -411,6 +536,11 @@ def main():
         print(json.dumps(line), flush=True)
         return 0
 
+    if args.config in ("batch", "serve"):
+        if rank == 0:
+            line = run_batch(args) if args.config == "batch" else run_serve(args)
+            print(json.dumps(line), flush=True)
+        return 0
     if world > 1:
         import torch.distributed as tdist
         tdist.init_process_group("gloo")

@@ -1,0 +1,318 @@
+"""Serving loop for many render sessions: admission by a device-memory budget and
+continuous batching of frame requests over dof_batch_frame.
+
+Requests (a session wants its next frame) arrive at any time.  Each tick the server
+  * retires finished batches (latency = completion - arrival),
+  * starts a new batch from the pending requests as soon as fewer than `max_inflight`
+    batches are on the GPU: at most one request per session (its history is
+    sequential) and at most `max_batch` requests, oldest first,
+so requests that arrive while others are on the GPU join the next batch and their
+work overlaps the running one (two streams).  A session whose newer request arrives
+before the older one started keeps only the newest (a real-time renderer shows the
+latest camera); the superseded request is counted as dropped.
+
+The executor does the work; GpuExecutor drives the CUDA library, FakeExecutor models
+the cost on a virtual clock (host-only tests of the scheduling logic).
+"""
+
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+
+
+@dataclass
+class SessionSpec:
+    name: str
+    width: int
+    height: int
+    fps: float                     # arrival rate of frame requests
+    scene: object = None           # synth.Scene
+    params: dict = field(default_factory=dict)
+    poses: list = field(default_factory=list)   # camera poses cycled by frame index
+    intr: dict = field(default_factory=dict)
+
+
+@dataclass
+class Request:
+    session: int
+    arrival: float
+    frame: int
+    start: float = -1.0
+    done: float = -1.0
+
+
+def percentile(xs, q):
+    if not xs:
+        return float("nan")
+    s = sorted(xs)
+    k = min(len(s) - 1, max(0, int(math.ceil(q / 100.0 * len(s))) - 1))
+    return s[k]
+
+
+# ---------------------------------------------------------------------------
+# executors
+# ---------------------------------------------------------------------------
+
+class FakeExecutor:
+    """Virtual-clock executor: a batch takes fixed_ms + sum of per-pixel costs."""
+
+    def __init__(self, budget_bytes, ms_per_mpix=0.5, fixed_ms=0.05, bytes_per_px=400, fail_on=None):
+        self.budget = budget_bytes
+        self.used = 0
+        self.ms_per_mpix, self.fixed_ms, self.bytes_per_px = ms_per_mpix, fixed_ms, bytes_per_px
+        self.now = 0.0
+        self.gpu_free_at = [0.0, 0.0]
+        self.sessions = {}
+        self.fail_on = fail_on or set()
+        self._next = 0
+
+    def clock(self):
+        return self.now
+
+    def advance(self, t):
+        self.now = max(self.now, t)
+
+    def estimate_bytes(self, spec):
+        return spec.width * spec.height * self.bytes_per_px
+
+    def open(self, sid, spec):
+        b = self.estimate_bytes(spec)
+        if self.used + b > self.budget:
+            raise MemoryError("budget")
+        self.used += b
+        self.sessions[sid] = (spec, b)
+
+    def close(self, sid):
+        spec, b = self.sessions.pop(sid)
+        self.used -= b
+
+    def submit(self, reqs, stream):
+        if any(r.session in self.fail_on for r in reqs):
+            raise RuntimeError("executor failure")
+        cost = self.fixed_ms + sum(self.sessions[r.session][0].width * self.sessions[r.session][0].height
+                                   for r in reqs) / 1e6 * self.ms_per_mpix
+        start = max(self.now, self.gpu_free_at[stream])
+        end = start + cost / 1e3
+        self.gpu_free_at[stream] = end
+        self._next += 1
+        return (self._next, end)
+
+    def done(self, token):
+        return self.now >= token[1]
+
+    def finish_time(self, token):
+        return token[1]
+
+    def next_event(self):
+        return min(self.gpu_free_at)
+
+
+class GpuExecutor:
+    """Drives libdof: per admitted session a device scene (BVH), a history and a small
+    ring of device G-buffers rendered by the G-buffer producer; batches go through
+    dof_batch_frame on one of two streams, completion is an event."""
+
+    def __init__(self, budget_bytes, device=0, gbuf_ring=2):
+        import torch
+        from . import dof
+        self.torch, self.dof = torch, dof
+        self.ctx = dof.Context(device, mem_budget_bytes=budget_bytes)
+        self.device = torch.device("cuda", device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(2)]
+        self.sessions = {}
+        self.ring = gbuf_ring
+        self.t0 = time.perf_counter()
+
+    def clock(self):
+        return time.perf_counter() - self.t0
+
+    def advance(self, t):
+        dt = t - self.clock()
+        if dt > 0:
+            time.sleep(min(dt, 0.0005))
+
+    def estimate_bytes(self, spec):
+        hpx = (spec.width // 2) * (spec.height // 2)
+        mr = int(spec.params.get("spp", 1)) if int(spec.params.get("ray_mode", 0)) == 0 else int(spec.params.get("m", 1))
+        return int(hpx * (400 + 12 * mr) + spec.scene.n_tris * 112)
+
+    def open(self, sid, spec):
+        from synth.scenes import Camera
+        dof, torch = self.dof, self.torch
+        try:
+            scene = dof.Scene(self.ctx, spec.scene)
+            mr = int(spec.params.get("spp", 1)) if int(spec.params.get("ray_mode", 0)) == 0 else int(spec.params.get("m", 1))
+            hist = dof.History(self.ctx, spec.width, spec.height, max_rays=mr)
+        except dof.DofError as e:
+            if e.code in (-2, -3):
+                raise MemoryError(str(e))
+            raise
+        gbs = []
+        for k in range(self.ring):
+            cam = Camera.from_poses(spec.intr, spec.poses[k % len(spec.poses)])
+            g = dof.gbuffer(self.ctx, scene, cam, spec.params, spec.width, spec.height)
+            del g["prim"]
+            gbs.append(g)
+        out = torch.empty((spec.height, spec.width, 4), dtype=torch.float32, device=self.device)
+        self.sessions[sid] = dict(spec=spec, scene=scene, hist=hist, gbs=gbs, out=out,
+                                  pstruct=dof.params_struct(spec.params))
+        torch.cuda.synchronize()
+
+    def close(self, sid):
+        s = self.sessions.pop(sid)
+        s["hist"].close()
+        s["scene"].close()
+
+    def camera(self, s, frame):
+        """Camera of frame `frame`: the pose of its G-buffer (the ring cycles the first
+        `gbuf_ring` poses) and the previous frame's pose."""
+        from synth.scenes import Camera
+        spec = s["spec"]
+        n = min(self.ring, len(spec.poses))
+        cam = Camera.from_poses(spec.intr, spec.poses[frame % n], spec.poses[(frame - 1) % n] if frame else None,
+                                frame_index=frame)
+        return self.dof.camera_struct(cam)
+
+    def submit(self, reqs, stream):
+        items = []
+        for r in reqs:
+            s = self.sessions[r.session]
+            items.append(dict(scene=s["scene"], gbuf=s["gbs"][r.frame % self.ring], cam=self.camera(s, r.frame),
+                              params=s["pstruct"], hist=s["hist"], out=s["out"]))
+        st = self.streams[stream]
+        self.dof.batch_frame(self.ctx, items, stream=st)
+        ev = self.torch.cuda.Event()
+        ev.record(st)
+        return ev
+
+    def done(self, token):
+        return token.query()
+
+    def finish_time(self, token):
+        return self.clock()
+
+    def next_event(self):
+        return self.clock() + 0.0002
+
+
+# ---------------------------------------------------------------------------
+# server
+# ---------------------------------------------------------------------------
+
+class Server:
+    def __init__(self, executor, max_batch=32, max_inflight=2):
+        self.ex = executor
+        self.max_batch = max_batch
+        self.max_inflight = max_inflight
+        self.specs = {}
+        self.rejected = []
+
+    def admit(self, sid, spec) -> bool:
+        """Admit a session if its scene, history and buffers fit the budget."""
+        try:
+            self.ex.open(sid, spec)
+        except MemoryError:
+            self.rejected.append(sid)
+            return False
+        self.specs[sid] = spec
+        return True
+
+    def release(self, sid):
+        self.ex.close(sid)
+        self.specs.pop(sid, None)
+
+    def run(self, arrivals):
+        """Serve `arrivals` (list of (time_s, session id), sorted by time, times relative
+        to the start of the run) to completion.  Returns the statistics: frames, dropped,
+        failed, p50/p99 latency (ms), frames/s, and per-session completed frame numbers."""
+        base = self.ex.clock()
+        arrivals = collections.deque((t + base, sid) for t, sid in arrivals if sid in self.specs)
+        pending = collections.OrderedDict()     # session -> Request (newest only)
+        busy = set()                            # sessions with a frame on the GPU
+        inflight = []                           # (token, [requests], stream)
+        frame_no = collections.Counter()
+        done, dropped, failed = [], 0, []
+        batches = []
+        stream_busy = [False] * self.max_inflight
+        t_first = arrivals[0][0] if arrivals else base
+        while arrivals or pending or inflight:
+            now = self.ex.clock()
+            while arrivals and arrivals[0][0] <= now:
+                t, sid = arrivals.popleft()
+                if sid not in self.specs:
+                    continue                    # evicted
+                if sid in pending:
+                    dropped += 1
+                    pending.pop(sid)
+                pending[sid] = Request(sid, t, frame_no[sid])
+                frame_no[sid] += 1
+            still = []
+            for tok, reqs, st in inflight:
+                if self.ex.done(tok):
+                    tf = self.ex.finish_time(tok)
+                    for r in reqs:
+                        r.done = tf
+                        busy.discard(r.session)
+                        done.append(r)
+                    stream_busy[st] = False
+                else:
+                    still.append((tok, reqs, st))
+            inflight = still
+            launched = False
+            if pending and len(inflight) < self.max_inflight:
+                batch = [r for sid, r in pending.items() if sid not in busy][: self.max_batch]
+                if batch:
+                    st = stream_busy.index(False)
+                    for r in batch:
+                        pending.pop(r.session)
+                        r.start = now
+                    try:
+                        tok = self.ex.submit(batch, st)
+                    except Exception:
+                        # the batch failed as a whole: its sessions are evicted, the others go on
+                        for r in batch:
+                            failed.append(r)
+                            if r.session in self.specs:
+                                self.release(r.session)
+                        continue
+                    for r in batch:
+                        busy.add(r.session)
+                    stream_busy[st] = True
+                    inflight.append((tok, batch, st))
+                    batches.append(len(batch))
+                    launched = True
+            if not launched:
+                nxt = [arrivals[0][0]] if arrivals else []
+                if inflight:
+                    nxt.append(min(self.ex.finish_time(t) if isinstance(self.ex, FakeExecutor) else now + 2e-4
+                                   for t, _, _ in inflight))
+                if nxt:
+                    self.ex.advance(min(nxt))
+        lat = [(r.done - r.arrival) * 1e3 for r in done]
+        t_last = max((r.done for r in done), default=t_first)
+        span = max(t_last - t_first, 1e-9)
+        per_session = collections.defaultdict(list)
+        for r in sorted(done, key=lambda r: r.done):
+            per_session[r.session].append(r.frame)
+        return dict(frames=len(done), dropped=dropped, failed=len(failed), p50_ms=percentile(lat, 50),
+                    p99_ms=percentile(lat, 99), mean_ms=sum(lat) / len(lat) if lat else float("nan"),
+                    frames_per_s=len(done) / span, admitted=len(self.specs), rejected=len(self.rejected),
+                    mean_batch=sum(batches) / len(batches) if batches else 0.0, max_batch=max(batches, default=0),
+                    per_session=dict(per_session))
+
+
+def poisson_arrivals(rng_seed, sessions, duration_s):
+    """Seeded Poisson arrivals: per session exponential gaps at its fps."""
+    import numpy as np
+    rng = np.random.default_rng(rng_seed)
+    out = []
+    for sid, spec in sessions.items():
+        t = float(rng.exponential(1.0 / spec.fps))
+        while t < duration_s:
+            out.append((t, sid))
+            t += float(rng.exponential(1.0 / spec.fps))
+    out.sort()
+    return out
