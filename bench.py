@@ -72,6 +72,22 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def max_over_ranks(x: float) -> float:
+    """Largest value over the ranks of the default process group (identity alone)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps: int, ms: float, world: int) -> float:
+    """Whole-job frames/s: every rank renders `steps` frames; time = max over ranks."""
+    return world * steps / (ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -236,14 +252,10 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
     if dist:
         tdist.barrier()
-    ms = e_start.elapsed_time(e_end)
+    ms = max_over_ranks(e_start.elapsed_time(e_end))
     st = hist.stats()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = job_value(args.steps, ms, world)
 
     # ---- instrumented pass: per-kernel device times over the same kind of steps
     htime = dof.History(ctx, w.W, w.H, max_rays=spp, timing=True)
@@ -298,12 +310,8 @@ def run_ours(args, rank, world):
         e2e_step(s)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_e2e], dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": world * args.steps / (ms_e2e / 1e3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+    e2e = {"value": job_value(args.steps, ms_e2e, world), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h)}
 
     # ---- roofline of the dominant kernel
