@@ -91,7 +91,13 @@ typedef struct {
     float k_a, k_d;         /* ambient and Lambert coefficients */
     float sky[3];           /* radiance of rays that hit nothing */
     float emit;             /* radiance scale of material 1 (emitters) */
+    uint32_t image_storage; /* DOF_STORAGE_F32, or DOF_STORAGE_F16: colour image buffers of the
+                               pass in FP16 (arithmetic stays FP32; depth, CoC and history FP32) */
+    uint32_t pad0;
 } DofParams;
+
+#define DOF_STORAGE_F32 0
+#define DOF_STORAGE_F16 1
 
 #define DOF_MAX_RAYS 64
 

@@ -142,6 +142,8 @@ int make_params(const DofParams *p, uint32_t W, uint32_t H, uint32_t max_rays, D
     o.k_a = p->k_a; o.k_d = p->k_d; o.emit = p->emit;
     o.sky = make_float3(p->sky[0], p->sky[1], p->sky[2]);
     uint32_t W2 = W / 2, H2 = H / 2;
+    if (p->image_storage > 1) return dof_set_error(DOF_ERR_INVALID_ARG, "params: image_storage must be 0 or 1");
+    o.f16 = p->image_storage == DOF_STORAGE_F16;
     o.tiles_w = (int)((W2 + 7) / 8);
     o.tiles_h = (int)((H2 + 7) / 8);
     o.dil_k = (int)ceil(0.5 * (double)p->max_coc_px / 8.0);

@@ -2,6 +2,7 @@
 // small FP32 helpers shared by the kernels, and the host objects behind the C ABI.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <atomic>
@@ -39,6 +40,7 @@ struct DevParams {
     float k_a, k_d, emit;
     float3 sky;
     int tiles_w, tiles_h, dil_k;
+    int f16;                    // colour image buffers stored as FP16
 };
 
 // ---------------------------------------------------------------------------
@@ -167,6 +169,28 @@ __device__ __forceinline__ float3 normalize(float3 v) { return rsqrtf(dot(v, v))
 __device__ __forceinline__ float sat(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return a + t * (b - a); }
 __device__ __forceinline__ float lum709(float r, float g, float b) { return 0.2126f * r + 0.7152f * g + 0.0722f * b; }
+
+// colour image buffers: float4, or 4 x FP16 (8 bytes) when `h` (FP32 arithmetic either way)
+__device__ __forceinline__ float4 ld_img(const float4 *base, size_t i, bool h) {
+    if (h) {
+        uint2 u = __ldg(reinterpret_cast<const uint2 *>(base) + i);
+        __half2 a = *reinterpret_cast<__half2 *>(&u.x), b = *reinterpret_cast<__half2 *>(&u.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    return __ldg(base + i);
+}
+__device__ __forceinline__ void st_img(float4 *base, size_t i, float4 v, bool h) {
+    if (h) {
+        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t *>(&a);
+        u.y = *reinterpret_cast<uint32_t *>(&b);
+        reinterpret_cast<uint2 *>(base)[i] = u;
+    } else {
+        base[i] = v;
+    }
+}
 
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 __device__ __forceinline__ float4 f4scale(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }

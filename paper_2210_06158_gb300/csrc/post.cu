@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_main_filter(const __grid_constant__ Bat
     if (interior) main_taps<false>(i, j, W2, H2, p, pre, z_h, R, z0, r0, ax, ay, az, bright, wsum);
     else main_taps<true>(i, j, W2, H2, p, pre, z_h, R, z0, r0, ax, ay, az, bright, wsum);
     float r = 1.f / wsum;
-    out[q] = make_float4(ax * r, ay * r, az * r, bright * r);
+    st_img(out, q, make_float4(ax * r, ay * r, az * r, bright * r), p.f16);
 }
 
 // A5: per-channel 3x3 median (clamp-to-edge)
@@ -162,6 +162,7 @@ __global__ void k_median_pp(const __grid_constant__ BatchArgs A) {
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const float4 *__restrict__ src = S.main_;
     float4 *dst = S.pp_med;
+    const bool h = S.p.f16;
     if (i >= W2 || j >= H2) return;
     float4 v[9];
     int n = 0;
@@ -171,10 +172,10 @@ __global__ void k_median_pp(const __grid_constant__ BatchArgs A) {
 #pragma unroll
         for (int dx = -1; dx <= 1; dx++) {
             int x = min(max(i + dx, 0), W2 - 1);
-            v[n++] = __ldg(&src[(size_t)y * W2 + x]);
+            v[n++] = ld_img(src, (size_t)y * W2 + x, h);
         }
     }
-    dst[(size_t)j * W2 + i] = median9(v);
+    st_img(dst, (size_t)j * W2 + i, median9(v), h);
 }
 
 }  // namespace

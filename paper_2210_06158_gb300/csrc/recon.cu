@@ -17,9 +17,10 @@ __global__ void k_median_rt(const __grid_constant__ BatchArgs A) {
     const float4 *__restrict__ crt = S.crt;
     const int32_t *__restrict__ nrays = S.nrays;
     float4 *dst = S.rt_med;
+    const bool hs = S.p.f16;
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
-    if (__ldg(&nrays[q]) <= 0) { dst[q] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+    if (__ldg(&nrays[q]) <= 0) { st_img(dst, q, make_float4(0.f, 0.f, 0.f, 0.f), hs); return; }
     float4 v[9];
     bool ok[9];
     int k = 0, n = 0;
@@ -31,7 +32,7 @@ __global__ void k_median_rt(const __grid_constant__ BatchArgs A) {
             bool in = x >= 0 && y >= 0 && x < W2 && y < H2;
             size_t qn = in ? (size_t)y * W2 + x : q;
             ok[n] = in && __ldg(&nrays[qn]) > 0;
-            v[n] = __ldg(&crt[qn]);
+            v[n] = ld_img(crt, qn, hs);
             k += ok[n];
             n++;
         }
@@ -44,7 +45,7 @@ __global__ void k_median_rt(const __grid_constant__ BatchArgs A) {
             v[m] = make_float4(pad, pad, pad, pad);
         }
     float4 med = median9(v);
-    dst[q] = make_float4(med.x, med.y, med.z, __ldg(&crt[q]).w);
+    st_img(dst, q, make_float4(med.x, med.y, med.z, ld_img(crt, q, hs).w), hs);
 }
 
 // A11: mip level 0 = (rgb, h) * v and (c_t, 1) * v
@@ -59,8 +60,9 @@ __global__ void k_mip0(const __grid_constant__ BatchArgs A) {
     float2 *m1 = S.mip1[0];
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
+    const bool hs = S.p.f16;
     float v = __ldg(&nrays[q]) > 0 ? 1.f : 0.f;
-    m0[q] = f4scale(v, __ldg(&med[q]));
+    st_img(m0, q, f4scale(v, ld_img(med, q, hs)), hs);
     m1[q] = make_float2(v * __ldg(&ct[q]), v);
 }
 
@@ -81,11 +83,11 @@ __global__ void k_mip_down(const __grid_constant__ BatchArgs A) {
     for (int t = 0; t < 4; t++) {
         int x = min(2 * i + (t & 1), w - 1), y = min(2 * j + (t >> 1), h - 1);
         size_t q = (size_t)y * w + x;
-        a = f4add(a, __ldg(&s0[q]));
+        a = f4add(a, ld_img(s0, q, S.p.f16));
         float2 c = __ldg(&s1[q]);
         b.x += c.x; b.y += c.y;
     }
-    d0[(size_t)j * wn + i] = f4scale(0.25f, a);
+    st_img(d0, (size_t)j * wn + i, f4scale(0.25f, a), S.p.f16);
     d1[(size_t)j * wn + i] = make_float2(0.25f * b.x, 0.25f * b.y);
 }
 
@@ -95,7 +97,7 @@ struct Mips {
     int w[4], h[4], L;
 };
 
-template <bool CLAMP>
+template <bool CLAMP, bool H>
 __device__ __forceinline__ void bilin_mip(const Mips &M, int l, float x, float y, float4 &a, float2 &b) {
     float s = 1.f / (float)(1 << l);
     float xl = (x + 0.5f) * s - 0.5f, yl = (y + 0.5f) * s - 0.5f;
@@ -115,15 +117,15 @@ __device__ __forceinline__ void bilin_mip(const Mips &M, int l, float x, float y
         xa = x0; xb = x0 + 1;
         qa = y0 * w; qb = qa + w;
     }
-    a = f4fma(w11, __ldg(&m0[qb + xb]), f4fma(w01, __ldg(&m0[qb + xa]),
-              f4fma(w10, __ldg(&m0[qa + xb]), f4scale(w00, __ldg(&m0[qa + xa])))));
+    a = f4fma(w11, ld_img(m0, qb + xb, H), f4fma(w01, ld_img(m0, qb + xa, H),
+              f4fma(w10, ld_img(m0, qa + xb, H), f4scale(w00, ld_img(m0, qa + xa, H)))));
     float2 c00 = __ldg(&m1[qa + xa]), c10 = __ldg(&m1[qa + xb]);
     float2 c01 = __ldg(&m1[qb + xa]), c11 = __ldg(&m1[qb + xb]);
     b = make_float2(w00 * c00.x + w10 * c10.x + w01 * c01.x + w11 * c11.x,
                     w00 * c00.y + w10 * c10.y + w01 * c01.y + w11 * c11.y);
 }
 
-template <bool CLAMP>
+template <bool CLAMP, bool H>
 __device__ __forceinline__ void recon_taps(const Mips &M, int i, int j, float R, int l0, int l1, float t,
                                            float inv_ramp, float4 &num, float &den) {
 #pragma unroll 3
@@ -133,8 +135,8 @@ __device__ __forceinline__ void recon_taps(const Mips &M, int i, int j, float R,
         float x = i + dist * u.x, y = j + dist * u.y;
         float4 a0, a1;
         float2 b0, b1;
-        bilin_mip<CLAMP>(M, l0, x, y, a0, b0);
-        bilin_mip<CLAMP>(M, l1, x, y, a1, b1);
+        bilin_mip<CLAMP, H>(M, l0, x, y, a0, b0);
+        bilin_mip<CLAMP, H>(M, l1, x, y, a1, b1);
         float4 S = f4fma(t, a1, f4scale(1.f - t, a0));
         float Sc = (1.f - t) * b0.x + t * b1.x, Sv = (1.f - t) * b0.y + t * b1.y;
         float ri = Sv > 0.f ? __fdividef(Sc, Sv) : 0.f;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ BatchArgs
                           by + (int)blockDim.y + reach < H2;
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
-    if (__ldg(&nrays[q]) <= 0) { out[q] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+    if (__ldg(&nrays[q]) <= 0) { st_img(out, q, make_float4(0.f, 0.f, 0.f, 0.f), p.f16); return; }
     float R = __ldg(&ct[q]);
     float lod = fminf(fmaxf(R * p.lod_scale, 0.f), p.lod_max);
     int l0 = (int)floorf(lod);
@@ -176,12 +178,17 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ BatchArgs
     int l1 = min(l0 + 1, M.L - 1);
     float4 num = make_float4(0.f, 0.f, 0.f, 0.f);
     float den = 0.f;
-    if (interior) recon_taps<false>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
-    else recon_taps<true>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
-    float4 o = __ldg(&med[q]);
+    if (p.f16) {
+        if (interior) recon_taps<false, true>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
+        else recon_taps<true, true>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
+    } else {
+        if (interior) recon_taps<false, false>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
+        else recon_taps<true, false>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
+    }
+    float4 o = ld_img(med, q, p.f16);
     float b = fminf(fmaxf(__ldg(&var_blur[q]) * p.var_w_recon, 0.f), p.b_max);
     float4 f = den > 0.f ? f4scale(1.f / den, num) : o;
-    out[q] = make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b));
+    st_img(out, q, make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b)), p.f16);
 }
 
 // A12: composite per full-resolution pixel
@@ -203,20 +210,21 @@ __global__ void __launch_bounds__(256) k_composite(const __grid_constant__ Batch
     float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
     float xh = 0.5f * (i + 0.5f) - 0.5f, yh = 0.5f * (j + 0.5f) - 0.5f;
     const int W2 = cam.W2, H2 = cam.H2;
-    float4 pp = bilinear4(pp_med, W2, H2, xh, yh);
+    const bool hs = p.f16;
     float xf = floorf(xh), yf = floorf(yh);
     float fx = xh - xf, fy = yh - yf;
     int x0 = (int)xf, y0 = (int)yf;
-    float4 rt = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 rt = make_float4(0.f, 0.f, 0.f, 0.f), pp = rt;
     float cov = 0.f;
 #pragma unroll
     for (int t = 0; t < 4; t++) {
         int dx = t & 1, dy = t >> 1;
         int x = min(max(x0 + dx, 0), W2 - 1), y = min(max(y0 + dy, 0), H2 - 1);
         size_t q = (size_t)y * W2 + x;
-        if (__ldg(&nrays[q]) <= 0) continue;
         float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
-        rt = f4fma(w, __ldg(&recon[q]), rt);
+        pp = f4fma(w, ld_img(pp_med, q, hs), pp);
+        if (__ldg(&nrays[q]) <= 0) continue;
+        rt = f4fma(w, ld_img(recon, q, hs), rt);
         cov += w;
     }
     float4 s = __ldg(&color[f]);

@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ Batc
     if (__ldg(&nrays[q]) <= 0) {
         float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         hout[q] = zero; hout[N + q] = zero; hout[2 * N + q] = zero;
-        crt[q] = zero; ct[q] = 0.f; var[q] = 0.f;
+        st_img(crt, q, zero, p.f16);
+        ct[q] = 0.f; var[q] = 0.f;
         return;
     }
     float4 rA = __ldg(&rt[q]), rB = __ldg(&rt[N + q]), rC = __ldg(&rt[2 * N + q]);
@@ -149,12 +150,12 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ Batc
     var[q] = v;
     if (!cam.moved) {
         float r = 1.f / (An.w + Af.w);
-        crt[q] = make_float4((An.x + Af.x) * r, (An.y + Af.y) * r, (An.z + Af.z) * r, An.w * r);
+        st_img(crt, q, make_float4((An.x + Af.x) * r, (An.y + Af.y) * r, (An.z + Af.z) * r, An.w * r), p.f16);
         ct[q] = (Bn + Bf) * r;
     } else {
         float rn = An.w > 0.f ? 1.f / An.w : 0.f, rf = Af.w > 0.f ? 1.f / Af.w : 0.f;
-        crt[q] = make_float4(h * An.x * rn + (1.f - h) * Af.x * rf, h * An.y * rn + (1.f - h) * Af.y * rf,
-                             h * An.z * rn + (1.f - h) * Af.z * rf, h);
+        st_img(crt, q, make_float4(h * An.x * rn + (1.f - h) * Af.x * rf, h * An.y * rn + (1.f - h) * Af.y * rf,
+                                   h * An.z * rn + (1.f - h) * Af.z * rf, h), p.f16);
         ct[q] = h * Bn * rn + (1.f - h) * Bf * rf;
     }
 }

@@ -295,6 +295,34 @@ def test_batch_equals_alone():
                                    hist=s["mixed"])] * 2)
 
 
+@pytest.mark.parametrize("name,W,H,nf", [("c3", 384, 216, 2), ("c2", 322, 182, 3)])
+def test_fp16_storage_error_vs_oracle(name, W, H, nf):
+    """FP16 storage of the colour image buffers (FP32 arithmetic, FP32 depth, CoC and
+    history): the final image meets the FP32 tolerances against the FP64 oracle."""
+    w = make_workload(name, W=W, H=H, n_frames=nf)
+    prm32 = dict(w.params)
+    prm16 = dict(prm32, image_storage=1)
+    osc = oracle.Scene(w.scene)
+    g32, g16 = GpuRunner(w, prm32), GpuRunner(w, prm16)
+    ohist = oracle.History(w.W, w.H)
+    taint = np.zeros((H // 2, W // 2), bool)
+    for k in range(nf):
+        cam = w.camera(k)
+        gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, prm32, W, H))
+        ref = oracle.frame(osc, cam, prm32, W, H, gb, ohist)
+        a = g32.frame(cam, gb)
+        b = g16.frame(cam, gb, read=False)
+        _, _, n_bad, mism = classify_hits(osc, w, prm32, cam, a, ref)
+        assert n_bad == 0
+        taint = dilate(dilate(taint, 2) | mism | threshold_ties(ref, prm32, cam, w), taint_radius(prm32))
+        tf = full_res(taint, W, H)
+        e32 = max_abs(a["out"][..., :3][~tf], ref["out"][..., :3][~tf])
+        e16 = max_abs(b["out"][..., :3][~tf], ref["out"][..., :3][~tf])
+        p16 = psnr(b["out"][..., :3], ref["out"][..., :3])
+        print(f"[fp16 {name}] frame={k} max_fp32={e32:.3g} max_fp16={e16:.3g} psnr_fp16={p16:.1f} tainted={tf.mean():.3g}")
+        assert e16 <= 2e-3 and p16 >= 50.0, (e16, p16)
+
+
 def test_determinism_bit_identical():
     w = make_workload("c2", W=320, H=180, n_frames=2)
     osc = oracle.Scene(w.scene)
