@@ -257,6 +257,23 @@ def run_ours(args, rank, world):
     ms_per_step = ms / args.steps
     value = job_value(args.steps, ms, world)
 
+    # ---- the FP16-storage variant over the same steps (another session history)
+    p16 = dof.params_struct(dict(prm, image_storage=1))
+    h16 = dof.History(ctx, w.W, w.H, max_rays=spp)
+    for s in range(args.warmup):
+        dof.frame(ctx, scene, gbs[s % CYCLE], None, None, h16, out, cam_struct=cams[s], params_s=p16)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for s in range(args.warmup, args.warmup + args.steps):
+        dof.frame(ctx, scene, gbs[s % CYCLE], None, None, h16, out, cam_struct=cams[s], params_s=p16)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms16 = max_over_ranks(f0.elapsed_time(f1))
+    fp16 = {"ms_per_step": round(ms16 / args.steps, 4), "value": round(job_value(args.steps, ms16, world), 2),
+            "unit": "frames/s", "storage": "colour image buffers FP16, FP32 arithmetic/depth/CoC/history"}
+    del h16
+
     # ---- instrumented pass: per-kernel device times over the same kind of steps
     htime = dof.History(ctx, w.W, w.H, max_rays=spp, timing=True)
     for s in range(args.warmup):
@@ -372,7 +389,7 @@ def run_ours(args, rank, world):
                            resolution=[w.W, w.H], triangles=info.n_tris, spp=spp, bvh_depth=info.depth,
                            parallelism="replicas" if world > 1 else "single-gpu",
                            l2="inputs larger than L2: 16 distinct G-buffers cycled (16 x 41 MB)"),
-               roofline=roof, e2e=e2e,
+               roofline=roof, e2e=e2e, fp16_storage=fp16,
                # per frame: 5 post-process, mask, trace, shade, 2 temporal, RT median, 4 mip, recon,
                # composite (+ 2 edge kernels in adaptive mode)
                gpu_launches=(17 + (2 if int(prm["ray_mode"]) == 1 else 0)) * args.steps,

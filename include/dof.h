@@ -118,6 +118,8 @@ typedef struct {
     uint64_t device_bytes;
     float bounds_lo[3], bounds_hi[3];   /* bounds of the triangles in the tree */
     uint32_t n_large;                   /* large triangles kept out of the tree */
+    uint32_t n_nodes4;                  /* nodes of the 4-wide tree (0 when the tree is one leaf) */
+    uint32_t depth4;                    /* levels of the 4-wide tree */
     uint32_t pad;
 } DofSceneInfo;
 
@@ -146,6 +148,13 @@ size_t dof_ctx_bytes_in_use(const DofCtx *ctx);
 #define DOF_OPT_BVH_BUILDER 1
 #define DOF_BVH_PLOC 0   /* default: PLOC clustering over the Morton order (higher tree quality) */
 #define DOF_BVH_LBVH 1   /* Karras 2012 radix tree (faster build) */
+/* launch shape and scheduling of the persistent ray tracer (results do not depend on them) */
+#define DOF_OPT_TRACE_BLOCKS_PER_SM 2   /* 128-thread blocks per SM, 1..32 (default 8) */
+#define DOF_OPT_TRACE_REFILL_IDLE   3   /* refill a warp when this many lanes are idle, 1..32 (default 16) */
+#define DOF_OPT_TRACE_STEPS         4   /* traversal steps between refill checks, 1..256 (default 64) */
+#define DOF_OPT_PLOC_RADIUS         5   /* PLOC nearest-neighbour search radius, 1..256 (default 24) */
+#define DOF_OPT_BVH_WIDTH           6   /* tree the rays traverse: 4 (default) = the binary tree collapsed
+                                         * to 4-wide nodes, 2 = the binary tree; same hits either way */
 int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value);
 
 /* Fill `p` with the defaults above (1 spp fixed mode, 16 px radius clamp). */
@@ -159,7 +168,8 @@ const char *dof_last_error(void);
 /* Upload a triangle scene and build its BVH on the device from 63-bit Morton codes of
  * the triangle centroids: PLOC agglomerative clustering (Meister and Bittner 2018)
  * by default, or the LBVH radix tree of Karras 2012 (DOF_OPT_BVH_BUILDER); two child
- * boxes per node.  Up to 64
+ * boxes per node.  The binary tree is then collapsed top-down into nodes of four child
+ * boxes (the largest-area child is opened until four remain).  Up to 64
  * "large" triangles (box extent above 1/16 of the scene's centroid extent, e.g. a
  * ground plane) are kept out of the tree and tested directly by every ray.
  *   xyz      host, n_verts * 3 floats

@@ -189,6 +189,11 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->in_use = 0;
     c->refs = 1;
     c->bvh_builder = DOF_BVH_PLOC;
+    c->trace_blocks_per_sm = 8;
+    c->trace_refill_idle = 16;
+    c->trace_steps = 64;
+    c->ploc_radius = 24;
+    c->bvh_width = 4;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
@@ -212,6 +217,26 @@ extern "C" int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value) {
             if (value != DOF_BVH_PLOC && value != DOF_BVH_LBVH)
                 return dof_set_error(DOF_ERR_INVALID_ARG, "dof_ctx_set_option: unknown BVH builder %lld", (long long)value);
             ctx->bvh_builder = (int)value;
+            return DOF_OK;
+        case DOF_OPT_TRACE_BLOCKS_PER_SM:
+            if (value < 1 || value > 32) return dof_set_error(DOF_ERR_INVALID_ARG, "trace blocks per SM must be 1..32");
+            ctx->trace_blocks_per_sm = (int)value;
+            return DOF_OK;
+        case DOF_OPT_TRACE_REFILL_IDLE:
+            if (value < 1 || value > 32) return dof_set_error(DOF_ERR_INVALID_ARG, "refill threshold must be 1..32");
+            ctx->trace_refill_idle = (int)value;
+            return DOF_OK;
+        case DOF_OPT_PLOC_RADIUS:
+            if (value < 1 || value > 256) return dof_set_error(DOF_ERR_INVALID_ARG, "PLOC radius must be 1..256");
+            ctx->ploc_radius = (int)value;
+            return DOF_OK;
+        case DOF_OPT_BVH_WIDTH:
+            if (value != 2 && value != 4) return dof_set_error(DOF_ERR_INVALID_ARG, "BVH width must be 2 or 4");
+            ctx->bvh_width = (int)value;
+            return DOF_OK;
+        case DOF_OPT_TRACE_STEPS:
+            if (value < 1 || value > 256) return dof_set_error(DOF_ERR_INVALID_ARG, "steps per round must be 1..256");
+            ctx->trace_steps = (int)value;
             return DOF_OK;
         default:
             return dof_set_error(DOF_ERR_INVALID_ARG, "dof_ctx_set_option: unknown option %d", option);
@@ -267,11 +292,12 @@ extern "C" int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts,
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_xyz, xyz, sizeof(float) * 3 * (size_t)n_verts, cudaMemcpyHostToDevice, st), "upload");
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_idx, tri_idx, sizeof(uint32_t) * 3 * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
     if (rc == DOF_OK && tri_mat) rc = dof_cuda_check(cudaMemcpyAsync(d_mat, tri_mat, sizeof(uint32_t) * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
-    if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, ctx->bvh_builder, st);
+    if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, ctx->bvh_builder, ctx->ploc_radius, st);
     cudaFree(d_xyz); cudaFree(d_idx); cudaFree(d_mat);
     if (rc != DOF_OK) {
         dof_free(ctx, s->tris, s->tris_bytes);
         dof_free(ctx, s->nodes, s->nodes_bytes);
+        dof_free(ctx, s->nodes4, s->nodes4_bytes);
         delete s;
         return rc;
     }
@@ -287,6 +313,7 @@ extern "C" void dof_scene_destroy(DofScene *s) {
         DeviceGuard g(ctx->device);
         dof_free(ctx, s->tris, s->tris_bytes);
         dof_free(ctx, s->nodes, s->nodes_bytes);
+        dof_free(ctx, s->nodes4, s->nodes4_bytes);
     }
     delete s;
     ctx_release(ctx);
@@ -297,6 +324,8 @@ extern "C" int dof_scene_info(const DofScene *s, DofSceneInfo *info) {
     info->n_tris = s->n_tris;
     info->n_nodes = s->n_nodes;
     info->n_large = s->n_large;
+    info->n_nodes4 = (uint32_t)s->n_nodes4;
+    info->depth4 = (uint32_t)s->depth4;
     info->depth = s->depth;
     info->stack_limit = kTraversalStack;
     info->device_bytes = s->bytes;
@@ -304,13 +333,22 @@ extern "C" int dof_scene_info(const DofScene *s, DofSceneInfo *info) {
     return DOF_OK;
 }
 
-static SceneDev scene_dev(const DofScene *s) {
+// `cam`: the rays' origins are within its lens (the 4-wide tree needs them within
+// kWideOriginMax of 0 on every axis)
+static SceneDev scene_dev(const DofScene *s, const DevCam &cam) {
     SceneDev d;
     d.nodes = s->nodes;
     d.tris = s->tris;
     d.n_tris = (int)s->n_tree;
     d.n_large = (int)s->n_large;
     d.root = s->root;
+    // the 4-wide tree, when its traversal stack bound (3 per level) fits
+    float om = fmaxf(fmaxf(fabsf(cam.O.x), fabsf(cam.O.y)), fabsf(cam.O.z)) + cam.lens_r;
+    bool wide = s->nodes4 && s->ctx->bvh_width == 4 && 3 * s->depth4 + 3 <= kTraversalStack &&
+                om <= 0.5f * kWideOriginMax;
+    d.nodes4 = wide ? s->nodes4 : nullptr;
+    d.root4 = s->root4;
+    d.n_nodes4 = s->n_nodes4;
     return d;
 }
 
@@ -335,7 +373,7 @@ extern "C" int dof_gbuffer(DofCtx *ctx, const DofScene *scene, const DofCamera *
     rc = make_params(p, width, height, DOF_MAX_RAYS, dp);
     if (rc) return rc;
     cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
-    launch_primary(dc, dp, scene_dev(scene), reinterpret_cast<float4 *>(color), depth,
+    launch_primary(dc, dp, scene_dev(scene, dc), reinterpret_cast<float4 *>(color), depth,
                    reinterpret_cast<float4 *>(normal), prim, ctx->d_status, (cudaStream_t)stream);
     return dof_cuda_check(cudaGetLastError(), "dof_gbuffer launch");
 }
@@ -484,7 +522,7 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
     if (rc) return rc;
     rc = make_params(r.params, h->W, h->H, h->max_rays, d.p);
     if (rc) return rc;
-    d.sc = scene_dev(scene);
+    d.sc = scene_dev(scene, d.cam);
     d.N = (int)h->N;
     d.max_rays = (int)h->max_rays;
     d.valid = h->valid;
@@ -552,6 +590,8 @@ static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStre
         }
     }
     A.cursor = &reqs[0].hist->counters[2];
+    A.refill_idle = ctx->trace_refill_idle;
+    A.steps_per_round = ctx->trace_steps;
     DofHistory *tm = reqs[0].hist;
     cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
     if (tm->ev && tm->ev_used < kTimingSlots) {
@@ -563,7 +603,7 @@ static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStre
     launch_reset_b(A, st);
     launch_post_b(A, st, tm);
     launch_mask_b(A, adaptive, st, tm);
-    launch_trace_b(A, ctx->sm_count, st, tm);
+    launch_trace_b(A, ctx->sm_count * ctx->trace_blocks_per_sm, st, tm);
     launch_temporal_b(A, st, tm);
     launch_recon_b(A, st, tm);
     int rc = dof_cuda_check(cudaGetLastError(), "dof_frame launch");

@@ -52,6 +52,7 @@ struct SessDesc {
 
 struct BatchArgs {
     int ns;
+    int refill_idle, steps_per_round;   // tracer scheduling
     int start[SH_COUNT][kMaxBatch + 1];
     uint32_t *cursor;              // device word: ray cursor of the persistent tracer
     SessDesc s[kMaxBatch];
@@ -85,7 +86,7 @@ __device__ __forceinline__ const SessDesc &block_session(const BatchArgs &A, int
 // host: launch wrappers per kernel group (post.cu, trace.cu, temporal.cu, recon.cu)
 void launch_post_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
 void launch_mask_b(const BatchArgs &A, bool any_adaptive, cudaStream_t st, DofHistory *timing);
-void launch_trace_b(const BatchArgs &A, int sm_count, cudaStream_t st, DofHistory *timing);
+void launch_trace_b(const BatchArgs &A, int blocks, cudaStream_t st, DofHistory *timing);
 void launch_temporal_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
 void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
 void launch_reset_b(const BatchArgs &A, cudaStream_t st);

@@ -244,7 +244,6 @@ __global__ void k_depth(int n, const int *parent_node, const int *parent_leaf, i
 // surface area of the merged box; mutual nearest neighbours merge into a new node;
 // the cluster array is compacted (order preserved) and the steps repeat.
 // ---------------------------------------------------------------------------
-constexpr int kPlocRadius = 24;
 
 __device__ __forceinline__ float half_area(float4 lo, float4 hi) {
     float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
@@ -263,13 +262,13 @@ __global__ void k_ploc_init(const float4 *tris, int m, int *cid, float4 *clo, fl
 
 // nearest neighbour by merged area; ties to the smaller index (symmetric cost, so the
 // globally cheapest pair is always mutual and every round merges at least once)
-__global__ void k_ploc_nn(int count, const float4 *clo, const float4 *chi, int *nn) {
+__global__ void k_ploc_nn(int count, int radius, const float4 *clo, const float4 *chi, int *nn) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     float4 lo = clo[i], hi = chi[i];
     float best = INFINITY;
     int bj = -1;
-    int j0 = max(0, i - kPlocRadius), j1 = min(count - 1, i + kPlocRadius);
+    int j0 = max(0, i - radius), j1 = min(count - 1, i + radius);
     for (int j = j0; j <= j1; j++) {
         if (j == i) continue;
         float4 l2 = clo[j], h2 = chi[j];
@@ -319,12 +318,96 @@ __global__ void k_ploc_scatter(int count, const int *keep, const int *pos, const
     chi2[o] = chi[i];
 }
 
+
+// ---------------------------------------------------------------------------
+// Collapse of the binary tree into 4-wide nodes, top-down one level per launch:
+// a 4-wide node starts from the two children of its binary node and opens its
+// largest-area internal child until it holds four children (or only leaves).  The
+// stored child boxes are widened by kWideBoxPad for the fused slab test.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bin_child(const BvhNode &nd, int c, float3 &lo, float3 &hi, int &ref) {
+    if (c == 0) {
+        lo = make_float3(nd.a.x, nd.a.y, nd.a.z); hi = make_float3(nd.a.w, nd.b.x, nd.b.y); ref = nd.r.x;
+    } else {
+        lo = make_float3(nd.b.z, nd.b.w, nd.c.x); hi = make_float3(nd.c.y, nd.c.z, nd.c.w); ref = nd.r.y;
+    }
+}
+
+__global__ void k_collapse(const BvhNode *nodes, int n_bin, const int2 *fin, int n_in, Bvh4Node *out4, int max4,
+                           int *n4, int2 *fout, int *n_out, int *bad) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_in) return;
+    int w4 = fin[t].x, b = fin[t].y;
+    if (b < 0 || b >= n_bin || w4 < 0 || w4 >= max4) { atomicExch(bad, 5); return; }
+    float3 lo[4], hi[4];
+    int ref[4], cnt = 2;
+    BvhNode nd = nodes[b];
+    bin_child(nd, 0, lo[0], hi[0], ref[0]);
+    bin_child(nd, 1, lo[1], hi[1], ref[1]);
+    while (cnt < 4) {
+        int best = -1;
+        float ba = -1.f;
+        for (int e = 0; e < cnt; e++) {
+            if (ref[e] < 0) continue;
+            float dx = hi[e].x - lo[e].x, dy = hi[e].y - lo[e].y, dz = hi[e].z - lo[e].z;
+            float a = dx * dy + dy * dz + dz * dx;
+            if (a > ba) { ba = a; best = e; }
+        }
+        if (best < 0) break;
+        if (ref[best] >= n_bin) { atomicExch(bad, 5); return; }
+        BvhNode c = nodes[ref[best]];
+        bin_child(c, 0, lo[best], hi[best], ref[best]);
+        bin_child(c, 1, lo[cnt], hi[cnt], ref[cnt]);
+        cnt++;
+    }
+    int nint = 0;
+    for (int e = 0; e < cnt; e++) nint += ref[e] >= 0;
+    int base = nint ? atomicAdd(n4, nint) : 0;
+    if (base + nint > max4) { atomicExch(bad, 6); return; }
+    int fo = nint ? atomicAdd(n_out, nint) : 0;
+    if (fo + nint > max4) { atomicExch(bad, 6); return; }
+    float L[3][4], Hh[3][4];
+    int R[4];
+    int k = 0;
+    for (int e = 0; e < 4; e++) {
+        if (e < cnt) {
+            L[0][e] = __fsub_rd(lo[e].x, kWideBoxPad);
+            L[1][e] = __fsub_rd(lo[e].y, kWideBoxPad);
+            L[2][e] = __fsub_rd(lo[e].z, kWideBoxPad);
+            Hh[0][e] = __fadd_ru(hi[e].x, kWideBoxPad);
+            Hh[1][e] = __fadd_ru(hi[e].y, kWideBoxPad);
+            Hh[2][e] = __fadd_ru(hi[e].z, kWideBoxPad);
+            if (ref[e] >= 0) {
+                R[e] = base + k;
+                fout[fo + k] = make_int2(base + k, ref[e]);
+                k++;
+            } else {
+                R[e] = ref[e];
+            }
+        } else {
+            L[0][e] = L[1][e] = L[2][e] = 0.f;
+            Hh[0][e] = Hh[1][e] = Hh[2][e] = 0.f;
+            R[e] = kEmptyChild;
+        }
+    }
+    Bvh4Node o;
+    o.lox = make_float4(L[0][0], L[0][1], L[0][2], L[0][3]);
+    o.hix = make_float4(Hh[0][0], Hh[0][1], Hh[0][2], Hh[0][3]);
+    o.loy = make_float4(L[1][0], L[1][1], L[1][2], L[1][3]);
+    o.hiy = make_float4(Hh[1][0], Hh[1][1], Hh[1][2], Hh[1][3]);
+    o.loz = make_float4(L[2][0], L[2][1], L[2][2], L[2][3]);
+    o.hiz = make_float4(Hh[2][0], Hh[2][1], Hh[2][2], Hh[2][3]);
+    o.ref = make_int4(R[0], R[1], R[2], R[3]);
+    o.pad = make_int4(0, 0, 0, 0);
+    out4[w4] = o;
+}
+
 }  // namespace
 
 static inline unsigned blocks_for(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // PLOC hierarchy over the m sorted tree triangles; writes nodes, parents, *root
-static int ploc_build(DofScene *s, int m, int *pnode, int *pleaf, int *ibuf, int *root, cudaStream_t st) {
+static int ploc_build(DofScene *s, int m, int radius, int *pnode, int *pleaf, int *ibuf, int *root, cudaStream_t st) {
     const int B = 256;
     int rc = DOF_OK;
     int *cid[2] = {nullptr, nullptr}, *nn = nullptr, *keep = nullptr, *pos = nullptr, *cnt = nullptr;
@@ -349,7 +432,7 @@ static int ploc_build(DofScene *s, int m, int *pnode, int *pleaf, int *ibuf, int
         int count = m, cur = 0;
         for (int round = 0; count > 1 && rc == DOF_OK; round++) {
             if (round > 100000) { rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "PLOC made no progress"); break; }
-            k_ploc_nn<<<blocks_for(count, B), B, 0, st>>>(count, clo[cur], chi[cur], nn);
+            k_ploc_nn<<<blocks_for(count, B), B, 0, st>>>(count, radius, clo[cur], chi[cur], nn);
             k_ploc_merge<<<blocks_for(count, B), B, 0, st>>>(count, cid[cur], clo[cur], chi[cur], nn, keep, cnt,
                                                             s->nodes, pnode, pleaf, m - 1, ibuf + 6);
             ck(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, keep, pos, count, st), "ploc scan");
@@ -378,8 +461,56 @@ static int ploc_build(DofScene *s, int m, int *pnode, int *pleaf, int *ibuf, int
     return rc;
 }
 
+// 4-wide tree from the binary one (root `root`, n_bin internal nodes); sets
+// s->nodes4 / root4 / n_nodes4 / depth4 (nodes4 stays null for a one-leaf tree)
+static int collapse4(DofScene *s, int root, int n_bin, int *ibuf, cudaStream_t st) {
+    const int B = 256;
+    int rc = DOF_OK;
+    s->root4 = root;
+    s->n_nodes4 = 0;
+    s->depth4 = 0;
+    if (root < 0 || n_bin < 1) return DOF_OK;
+    Bvh4Node *big = nullptr;
+    int2 *fr[2] = {nullptr, nullptr};
+    int *cnt = nullptr;
+    auto ck = [&](cudaError_t e, const char *w) { if (rc == DOF_OK && e != cudaSuccess) rc = dof_cuda_check(e, w); };
+    ck(cudaMalloc(&big, sizeof(Bvh4Node) * n_bin), "collapse");
+    ck(cudaMalloc(&fr[0], sizeof(int2) * n_bin), "collapse");
+    ck(cudaMalloc(&fr[1], sizeof(int2) * n_bin), "collapse");
+    ck(cudaMalloc(&cnt, sizeof(int) * 2), "collapse");
+    if (rc == DOF_OK) {
+        int2 first = make_int2(0, root);
+        int init[2] = {1, 0};   // [0] 4-wide nodes allocated (the root), [1] next frontier size
+        ck(cudaMemcpy(fr[0], &first, sizeof(int2), cudaMemcpyHostToDevice), "collapse");
+        ck(cudaMemcpy(cnt, init, sizeof(init), cudaMemcpyHostToDevice), "collapse");
+        int n_in = 1, cur = 0, level = 0;
+        while (n_in > 0 && rc == DOF_OK) {
+            if (++level > 200) { rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "BVH collapse did not terminate"); break; }
+            ck(cudaMemsetAsync(cnt + 1, 0, sizeof(int), st), "collapse");
+            k_collapse<<<blocks_for(n_in, B), B, 0, st>>>(s->nodes, n_bin, fr[cur], n_in, big, n_bin, cnt, fr[cur ^ 1],
+                                                         cnt + 1, ibuf + 6);
+            int h[2];
+            ck(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st), "collapse");
+            ck(cudaStreamSynchronize(st), "collapse");
+            n_in = h[1];
+            s->n_nodes4 = h[0];
+            cur ^= 1;
+        }
+        s->depth4 = level;
+    }
+    if (rc == DOF_OK) {
+        s->nodes4_bytes = sizeof(Bvh4Node) * (size_t)s->n_nodes4;
+        rc = dof_alloc(s->ctx, s->nodes4_bytes, (void **)&s->nodes4, &s->bytes);
+        if (rc == DOF_OK)
+            ck(cudaMemcpy(s->nodes4, big, s->nodes4_bytes, cudaMemcpyDeviceToDevice), "collapse copy");
+        s->root4 = 0;
+    }
+    cudaFree(big); cudaFree(fr[0]); cudaFree(fr[1]); cudaFree(cnt);
+    return rc;
+}
+
 int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const uint32_t *d_idx,
-                     const uint32_t *d_mat, int builder, cudaStream_t st) {
+                     const uint32_t *d_mat, int builder, int ploc_radius, cudaStream_t st) {
     const int n = (int)s->n_tris;
     const int B = 256;
     int rc = DOF_OK;
@@ -437,7 +568,7 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
             ck(cudaMemsetAsync(arr, 0, sizeof(int) * (m - 1), st), "memset");
             ck(cudaMemsetAsync(s->nodes, 0xFF, sizeof(BvhNode) * (m - 1), st), "memset");
             if (builder == DOF_BVH_PLOC) {
-                if (rc == DOF_OK) rc = ploc_build(s, m, pnode, pleaf, ibuf, &root, st);
+                if (rc == DOF_OK) rc = ploc_build(s, m, ploc_radius, pnode, pleaf, ibuf, &root, st);
                 if (rc != DOF_OK) goto done;
             } else {
                 k_karras<<<blocks_for(m - 1, B), B, 0, st>>>(keys2, m, child, pnode, pleaf, ibuf + 6);
@@ -460,6 +591,14 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
         if (s->depth > kTraversalStack) {
             rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "BVH depth %u exceeds the traversal stack", s->depth);
             goto done;
+        }
+        if (m >= 2) {
+            rc = collapse4(s, root, m - 1, ibuf, st);
+            if (rc != DOF_OK) goto done;
+            ck(cudaMemcpyAsync(hbuf, ibuf, sizeof(hbuf), cudaMemcpyDeviceToHost, st), "bvh readback");
+            ck(cudaStreamSynchronize(st), "bvh collapse");
+            if (rc != DOF_OK) goto done;
+            if (hbuf[6]) { rc = dof_set_error(DOF_ERR_DEVICE_CHECK, "dof_scene_upload: BVH collapse check failed (%d)", hbuf[6]); goto done; }
         }
         // bounds of the tree's triangles: union of the root's child boxes
         if (m >= 2 && root >= 0) {

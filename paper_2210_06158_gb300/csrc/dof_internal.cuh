@@ -56,12 +56,31 @@ struct __align__(16) BvhNode {
     int4 r;     // child0 ref, child1 ref, unused, unused
 };
 
+// 4-wide node: the boxes of up to four children (structure of arrays) and their
+// references (>= 0 node, < 0 leaf ~k, kEmptyChild for an unused slot)
+struct __align__(16) Bvh4Node {
+    float4 lox, hix, loy, hiy, loz, hiz;
+    int4 ref;
+    int4 pad;
+};
+constexpr int kEmptyChild = (int)0x80000000;
+// The 4-wide boxes are widened by kWideBoxPad (outward rounding), so that the slab
+// test may take the ray origin in the fused form lo * inv - o * inv: that equals the
+// exact slab of a ray whose origin moved by at most |o| 2^-24 per axis, which the pad
+// covers for origins within kWideOriginMax of 0 on every axis (2^10 * 2^-22 = 2^-12,
+// twice the bound).  Rays starting farther out traverse the binary tree.
+constexpr float kWideOriginMax = 1024.f;
+constexpr float kWideBoxPad = 2.44140625e-4f;
+
 struct SceneDev {
     const BvhNode *nodes;        // n_tris - 1 internal nodes (root = 0) when n_tris >= 2
     const float4 *tris;          // 3 float4 per sorted triangle: v0 (w = prim id bits), v1, v2 (w = material bits)
     int n_tris;                  // triangles in the tree (sorted indices 0 .. n_tris-1)
     int n_large;                 // large triangles after them, tested directly by every ray
     int root;                    // root reference (internal node, or ~0 for a one-leaf tree)
+    const Bvh4Node *nodes4;      // the tree collapsed to 4-wide nodes (traversed when non-null)
+    int root4;                   // its root reference
+    int n_nodes4;
 };
 
 // at most this many large triangles are kept out of the tree (see bvh.cu)
@@ -78,6 +97,9 @@ struct DofCtx {
     size_t budget;
     int sm_count;
     int bvh_builder;               // DOF_BVH_PLOC or DOF_BVH_LBVH
+    int trace_blocks_per_sm, trace_refill_idle, trace_steps;
+    int ploc_radius;
+    int bvh_width;                 // 4: traverse the collapsed 4-wide tree, 2: the binary tree
     uint32_t *d_status;            // device status word of context-level launches
 };
 
@@ -87,6 +109,9 @@ struct DofScene {
     uint32_t n_tree, n_large;      // triangles in the tree / tested directly
     int root;
     size_t tris_bytes, nodes_bytes;  // allocation sizes (for the context's budget)
+    Bvh4Node *nodes4;
+    size_t nodes4_bytes;
+    int root4, n_nodes4, depth4;
     BvhNode *nodes;
     float4 *tris;
     size_t bytes;
@@ -150,7 +175,7 @@ void dof_free(DofCtx *ctx, void *ptr, size_t bytes);
 
 // launch wrappers (one per kernel group, defined in the .cu files)
 int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const uint32_t *d_idx,
-                     const uint32_t *d_mat, int builder, cudaStream_t st);
+                     const uint32_t *d_mat, int builder, int ploc_radius, cudaStream_t st);
 void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *color, float *depth,
                     float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st);
 // ---------------------------------------------------------------------------

@@ -33,6 +33,7 @@ __device__ __forceinline__ void philox2(unsigned long long c0, unsigned long lon
 // ---------------------------------------------------------------------------
 struct Ray {
     float3 o, d, inv;
+    float3 oinv;        // o * inv (the fused slab test of the 4-wide tree)
     int kx, ky, kz;
     float Sx, Sy, Sz;
 };
@@ -44,6 +45,7 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     r.o = o; r.d = d;
     auto safe = [](float x) { return fabsf(x) < 1e-30f ? copysignf(1e-30f, x) : x; };
     r.inv = make_float3(1.f / safe(d.x), 1.f / safe(d.y), 1.f / safe(d.z));
+    r.oinv = make_float3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
     float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -62,6 +64,18 @@ __device__ __forceinline__ bool box_hit(const Ray &r, float3 lo, float3 hi, floa
     float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
     float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
     float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tbest));
+    tent = tmin;
+    return tmin <= tmax * 1.0000005f;
+}
+
+// slab test on a widened 4-wide box: one fused multiply-add per plane
+__device__ __forceinline__ bool box_hit_w(const Ray &r, float lx, float ly, float lz, float hx, float hy, float hz,
+                                          float tbest, float &tent) {
+    float tx0 = fmaf(lx, r.inv.x, -r.oinv.x), tx1 = fmaf(hx, r.inv.x, -r.oinv.x);
+    float ty0 = fmaf(ly, r.inv.y, -r.oinv.y), ty1 = fmaf(hy, r.inv.y, -r.oinv.y);
+    float tz0 = fmaf(lz, r.inv.z, -r.oinv.z), tz1 = fmaf(hz, r.inv.z, -r.oinv.z);
     float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
     float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tbest));
     tent = tmin;
@@ -105,6 +119,91 @@ struct HitRec {
     int k;      // sorted index
 };
 
+// ---------------------------------------------------------------------------
+// 4-wide traversal step: the four child boxes of a node are tested at once and the
+// children that are hit, internal nodes and leaves alike, are ordered by entry
+// distance; the nearest is taken next and the others are pushed, farthest first.  A
+// leaf reference taken from the stack is intersected.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cx_hit(float &ta, int &ra, float &tb, int &rb) {
+    if (tb < ta) {
+        float t = ta; ta = tb; tb = t;
+        int r = ra; ra = rb; rb = r;
+    }
+}
+
+__device__ __forceinline__ void tri_update(const Ray &ray, const float4 *__restrict__ tris, int k, HitRec &h) {
+    const float4 *tp = tris + 3 * (size_t)k;
+    float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+    float t = tri_hit(ray, v0, v1, v2);
+    if (t > 0.f) {
+        int prim = __float_as_int(v0.w);
+        if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
+    }
+}
+
+// Returns true when the query has ended (stack empty or a guard tripped).
+__device__ __forceinline__ bool step4(const Ray &ray, const Bvh4Node *__restrict__ nodes4, int n4,
+                                      const float4 *__restrict__ tris, int n_tree, int &node, int *stack, int &sp,
+                                      HitRec &h, uint32_t &n_visit, uint32_t &n_tests, uint32_t *status) {
+    if (node < 0) {
+        const int k = ~node;
+        if (k >= n_tree) {
+            atomicOr(status, 2u);
+            return true;
+        }
+        n_tests++;
+        tri_update(ray, tris, k, h);
+    } else {
+        if (node >= n4) {
+            atomicOr(status, 2u);
+            return true;
+        }
+        n_visit++;
+        const float4 *np = reinterpret_cast<const float4 *>(nodes4 + node);
+        const float4 lx = __ldg(np), hx = __ldg(np + 1), ly = __ldg(np + 2), hy = __ldg(np + 3);
+        const float4 lz = __ldg(np + 4), hz = __ldg(np + 5);
+        const int4 rf = __ldg(reinterpret_cast<const int4 *>(np + 6));
+        float t[4];
+        int c[4] = {rf.x, rf.y, rf.z, rf.w};
+        if (!box_hit_w(ray, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, h.t, t[0]) || c[0] == kEmptyChild) {
+            c[0] = kEmptyChild; t[0] = INFINITY;
+        }
+        if (!box_hit_w(ray, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, h.t, t[1]) || c[1] == kEmptyChild) {
+            c[1] = kEmptyChild; t[1] = INFINITY;
+        }
+        if (!box_hit_w(ray, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, h.t, t[2]) || c[2] == kEmptyChild) {
+            c[2] = kEmptyChild; t[2] = INFINITY;
+        }
+        if (!box_hit_w(ray, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, h.t, t[3]) || c[3] == kEmptyChild) {
+            c[3] = kEmptyChild; t[3] = INFINITY;
+        }
+        // an entry distance that overflowed to +inf still sorts before the misses
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            if (c[e] != kEmptyChild) t[e] = fminf(t[e], 3.4e38f);
+        cx_hit(t[0], c[0], t[1], c[1]);
+        cx_hit(t[2], c[2], t[3], c[3]);
+        cx_hit(t[0], c[0], t[2], c[2]);
+        cx_hit(t[1], c[1], t[3], c[3]);
+        cx_hit(t[1], c[1], t[2], c[2]);
+#pragma unroll
+        for (int e = 3; e >= 1; e--) {
+            if (c[e] != kEmptyChild) {
+                if (sp < kStack) stack[sp++] = c[e];
+                else atomicOr(status, 1u);
+            }
+        }
+        if (c[0] != kEmptyChild) {
+            node = c[0];
+            return false;
+        }
+    }
+    if (sp == 0) return true;
+    node = stack[--sp];
+    return false;
+}
+
 // closest hit = lexicographic min of (t, prim id); boxes with entry == best are kept.
 // A reference outside the tree, a full stack or more steps than a valid tree can take
 // set the status word and end the query (no fault, no endless loop).
@@ -125,6 +224,19 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
     if (sc.n_tris <= 0) return h;
     int stack[kStack];
     int sp = 0;
+    if (sc.nodes4) {
+        int node4 = sc.root4;
+        const long long max4 = 4ll * sc.n_tris + 64;
+        for (long long steps = 0;; steps++) {
+            if (steps > max4) {
+                atomicOr(status, 2u);
+                break;
+            }
+            if (step4(r, sc.nodes4, sc.n_nodes4, sc.tris, sc.n_tris, node4, stack, sp, h, n_visit, n_tests, status))
+                break;
+        }
+        return h;
+    }
     int node = sc.root;
     const int n_nodes = sc.n_tris - 1;
     const long long max_steps = 4ll * sc.n_tris + 64;
@@ -366,14 +478,12 @@ __device__ __noinline__ void lens_ray(const DevCam &cam, const DevParams &p, uin
     dir = normalize(Pf - L);
 }
 
-constexpr int kRefillIdle = 8;    // refill a warp's idle lanes once this many are idle
-constexpr int kStepsPerRound = 16;
 
 // Persistent tracer, one ray per lane (Aila and Laine 2009, persistent threads with
 // dynamic fetch): lanes whose ray has finished take new rays from the ray list when
 // enough of the warp is idle, so divergent rays do not hold the warp.  Writes the
 // closest hit of each ray: (sorted triangle index or -1, t).
-__global__ void __launch_bounds__(128) k_trace_rays(const __grid_constant__ BatchArgs A) {
+__global__ void __launch_bounds__(128, 8) k_trace_rays(const __grid_constant__ BatchArgs A) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     // inclusive prefix of the sessions' ray counts (the batch's concatenated ray list)
     __shared__ uint32_t pre[kMaxBatch];
@@ -387,20 +497,22 @@ __global__ void __launch_bounds__(128) k_trace_rays(const __grid_constant__ Batc
     }
     __syncthreads();
     const uint32_t total = pre[A.ns - 1];
+    const int refill_idle = A.refill_idle, steps_per_round = A.steps_per_round;
     uint32_t n_visit = 0, n_tests = 0;
     bool have = false, exhausted = false;
     uint32_t r = 0;
     int si = 0;
     Ray ray;
     HitRec h{INFINITY, -1, -1};
-    int node = 0, sp = 0, n_tree = 0, n_nodes = 0;
+    int node = 0, sp = 0, n_tree = 0, n_nodes = 0, n4 = 0;
     const BvhNode *nodes = nullptr;
+    const Bvh4Node *nodes4 = nullptr;
     const float4 *tris = nullptr;
     long long steps = 0, max_steps = 0;
     int stack[kStack];
     while (true) {
         unsigned idle = __ballot_sync(0xffffffffu, !have);
-        if (idle == 0xffffffffu || (!exhausted && __popc(idle) >= kRefillIdle)) {
+        if (idle == 0xffffffffu || (!exhausted && __popc(idle) >= refill_idle)) {
             uint32_t base = 0;
             if (lane == 0) base = atomicAdd(A.cursor, (uint32_t)__popc(idle));
             base = __shfl_sync(0xffffffffu, base, 0);
@@ -424,6 +536,8 @@ __global__ void __launch_bounds__(128) k_trace_rays(const __grid_constant__ Batc
                     lens_ray(S.cam, S.p, q, sm, L, dir);
                     ray = make_ray(L, dir);
                     nodes = S.sc.nodes;
+                    nodes4 = S.sc.nodes4;
+                    n4 = S.sc.n_nodes4;
                     tris = S.sc.tris;
                     n_tree = S.sc.n_tris;
                     n_nodes = n_tree - 1;
@@ -437,7 +551,7 @@ __global__ void __launch_bounds__(128) k_trace_rays(const __grid_constant__ Batc
                             if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
                         }
                     }
-                    node = S.sc.root;
+                    node = nodes4 ? S.sc.root4 : S.sc.root;
                     sp = 0;
                     steps = 0;
                     max_steps = 4ll * n_tree + 64;
@@ -448,9 +562,17 @@ __global__ void __launch_bounds__(128) k_trace_rays(const __grid_constant__ Batc
             if (__ballot_sync(0xffffffffu, have) == 0 && exhausted) break;
         }
         if (!have) continue;
-        for (int it = 0; it < kStepsPerRound; it++) {
+        for (int it = 0; it < steps_per_round; it++) {
             bool done = false;
-            if (++steps > max_steps || node >= n_nodes || (node < 0 && ~node >= n_tree)) {
+            if (nodes4) {
+                if (++steps > max_steps) {
+                    atomicOr(&A.s[si].counters[3], 2u);
+                    done = true;
+                } else {
+                    done = step4(ray, nodes4, n4, tris, n_tree, node, stack, sp, h, n_visit, n_tests,
+                                 &A.s[si].counters[3]);
+                }
+            } else if (++steps > max_steps || node >= n_nodes || (node < 0 && ~node >= n_tree)) {
                 atomicOr(&A.s[si].counters[3], 2u);
                 done = true;
             } else if (node >= 0) {
@@ -587,8 +709,8 @@ void launch_mask_b(const BatchArgs &A, bool any_adaptive, cudaStream_t st, DofHi
     tmark(tm, DOF_K_MASK, st);
 }
 
-void launch_trace_b(const BatchArgs &A, int sm_count, cudaStream_t st, DofHistory *tm) {
-    k_trace_rays<<<sm_count * 8, 128, 0, st>>>(A);
+void launch_trace_b(const BatchArgs &A, int blocks, cudaStream_t st, DofHistory *tm) {
+    k_trace_rays<<<blocks, 128, 0, st>>>(A);
     tmark(tm, DOF_K_TRACE, st);
     k_shade<<<A.start[SH_SHADE][A.ns], 128, 0, st>>>(A);
     tmark(tm, DOF_K_SHADE, st);

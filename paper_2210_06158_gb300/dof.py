@@ -77,7 +77,8 @@ MAX_BATCH = 32
 class DofSceneInfo(C.Structure):
     _fields_ = [("n_tris", C.c_uint32), ("n_nodes", C.c_uint32), ("depth", C.c_uint32),
                 ("stack_limit", C.c_uint32), ("device_bytes", C.c_uint64),
-                ("bounds_lo", _f3), ("bounds_hi", _f3), ("n_large", C.c_uint32), ("pad", C.c_uint32)]
+                ("bounds_lo", _f3), ("bounds_hi", _f3), ("n_large", C.c_uint32), ("n_nodes4", C.c_uint32), ("depth4", C.c_uint32),
+                ("pad", C.c_uint32)]
 
 
 class DofFrameStats(C.Structure):
@@ -210,6 +211,20 @@ class Context:
     def set_bvh_builder(self, name: str):
         """'ploc' (default) or 'lbvh' for scenes uploaded afterwards."""
         _check(lib().dof_ctx_set_option(self.ptr, 1, {"ploc": 0, "lbvh": 1}[name]))
+
+    def set_ploc_radius(self, r: int):
+        """PLOC search radius for scenes uploaded afterwards (tree quality vs build time)."""
+        _check(lib().dof_ctx_set_option(self.ptr, 5, int(r)))
+
+    def set_bvh_width(self, width: int):
+        """Tree the rays traverse: 4 (collapsed 4-wide nodes, default) or 2 (binary)."""
+        _check(lib().dof_ctx_set_option(self.ptr, 6, int(width)))
+
+    def set_trace(self, blocks_per_sm=None, refill_idle=None, steps=None):
+        """Launch shape / scheduling of the persistent tracer (no effect on results)."""
+        for opt, v in ((2, blocks_per_sm), (3, refill_idle), (4, steps)):
+            if v is not None:
+                _check(lib().dof_ctx_set_option(self.ptr, opt, int(v)))
 
     @property
     def bytes_in_use(self) -> int:

@@ -1,0 +1,59 @@
+"""Autotuner of the persistent ray tracer's launch shape and scheduling.
+
+The knobs (128-thread blocks per SM, idle lanes that trigger a refill, traversal
+steps between refill checks) change only the speed of dof_frame, never its result.
+`tune_trace` times a few frames of the caller's own session for each candidate
+(coordinate descent from the defaults, CUDA events on the session's stream) and
+leaves the fastest setting on the context.
+"""
+
+from __future__ import annotations
+
+SPACE = {
+    "blocks_per_sm": [4, 6, 8, 12, 16],
+    "refill_idle": [4, 8, 12, 16, 24],
+    "steps": [8, 16, 32, 64],
+}
+DEFAULT = {"blocks_per_sm": 8, "refill_idle": 16, "steps": 64}
+
+
+def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None):
+    """run_frame(k) enqueues frame k of a representative session on `stream` (or the
+    current stream).  Returns (best settings, {settings tuple: ms per frame})."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    best = dict(DEFAULT)
+    seen = {}
+    k = 0
+
+    def measure(cfg):
+        nonlocal k
+        key = tuple(sorted(cfg.items()))
+        if key in seen:
+            return seen[key]
+        ctx.set_trace(**cfg)
+        run_frame(k)                               # warm-up with this setting
+        k += 1
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(frames):
+            run_frame(k)
+            k += 1
+        e1.record(st)
+        e1.synchronize()
+        seen[key] = e0.elapsed_time(e1) / frames
+        return seen[key]
+
+    best_ms = measure(best)
+    for _ in range(rounds):
+        improved = False
+        for name, values in SPACE.items():
+            for v in values:
+                cand = dict(best, **{name: v})
+                ms = measure(cand)
+                if ms < best_ms * 0.99:
+                    best, best_ms, improved = cand, ms, True
+        if not improved:
+            break
+    ctx.set_trace(**best)
+    return best, seen

@@ -263,13 +263,16 @@ def scene_grass_field(seed: int, density: float = 1.0, f_m=0.035, sensor_w_m=0.0
                       near=(1.3, 4.8), far=(8.0, 60.0)) -> Scene:
     """Lawn field: thin blade quads and fence bars in the near field (the dolly
     start is 0.8 m behind `near[0]`, so distances during a 16-frame dolly span
-    0.5-4.8 m), a box field and level-3 icospheres in the far field.
-    density 1 gives ~500k triangles, density 4 ~2M."""
+    0.5-4.8 m), a sparse box field and icospheres (level 4, level 5 from density 2) in the far field (8-60 m,
+    sparse enough that sight lines reach the focus distance and beyond).
+    density 1 gives ~500k triangles, density 4 ~2M: the blade count scales with it,
+    the far field keeps its boxes per square metre and takes the rest of the
+    triangle budget as spheres."""
     rng = SplitMix64(seed)
     b = _Builder(seed)
     b.add("ground", *ground())
     tanhx = sensor_w_m / (2 * f_m)
-    nbl = int(165_000 * density)
+    nbl = int(180_000 * density)
     z = rng.uniform(nbl, *near)
     x = _frustum_x(rng, z, tanhx)
     b.add("blades", *blades(np.stack([x, z], -1), rng.uniform(nbl, 0.01, 0.03),
@@ -279,18 +282,25 @@ def scene_grass_field(seed: int, density: float = 1.0, f_m=0.035, sensor_w_m=0.0
     x = _frustum_x(rng, z, tanhx)
     size = np.stack([np.full(nfb, 0.03), rng.uniform(nfb, 0.4, 0.8), np.full(nfb, 0.03)], -1)
     b.add("fence", *boxes(np.stack([x, z], -1), np.zeros(nfb), size, rng.uniform(nfb, 0, np.pi)))
-    nbx = int(3000 * density)
+    # far field: object sizes follow the frustum width (relative to a 35 mm lens on
+    # a 36 mm sensor), box count per ground area keeps the mean free path of a
+    # ground-level sight line (~11 m, so the focus distance is seen)
+    area = 1.15 * tanhx * (far[1] ** 2 - far[0] ** 2)
+    sc = tanhx / (0.036 / (2 * 0.035))
+    nbx = max(1, int(0.05 * area / sc))
     z = rng.uniform(nbx, *far)
     x = _frustum_x(rng, z, tanhx)
-    size = np.stack([rng.uniform(nbx, 0.5, 3.0), rng.uniform(nbx, 0.5, 3.0),
-                     rng.uniform(nbx, 0.5, 3.0)], -1)
+    size = sc * np.stack([rng.uniform(nbx, 0.5, 3.0), rng.uniform(nbx, 0.5, 3.0),
+                          rng.uniform(nbx, 0.5, 3.0)], -1)
     b.add("boxes", *boxes(np.stack([x, z], -1), np.zeros(nbx), size, rng.uniform(nbx, 0, np.pi)))
-    nsp = int(100 * density)
+    level = 4 if density < 2 else 5    # finer spheres rather than more of them
+    per_sphere = 20 * 4 ** level
+    nsp = max(1, int((500_000 * density - 2 * nbl - 12 * (nfb + nbx)) // per_sphere))
     z = rng.uniform(nsp, *far)
     x = _frustum_x(rng, z, tanhx)
-    r = rng.uniform(nsp, 0.3, 1.5)
-    y = r + rng.uniform(nsp, 0.0, 2.0)
-    b.add("spheres", *spheres(np.stack([x, y, z], -1), r, 3))
+    r = sc * rng.uniform(nsp, 0.3, 1.5)
+    y = r + sc * rng.uniform(nsp, 0.0, 2.0)
+    b.add("spheres", *spheres(np.stack([x, y, z], -1), r, level))
     return b.build()
 
 
@@ -407,7 +417,7 @@ def make_workload(name: str, W: int | None = None, H: int | None = None,
             W, H = W or 3840, H or 2160
             params = default_params(spp=4, max_coc_px=64.0, seed=seed, session=session, albedo_seed=seed)
             dens = 4.0
-        height, pitch = (1.0, 8.0) if cfg == 2 else (0.7, 4.0)
+        height, pitch = (1.0, 8.0) if cfg == 2 else (1.0, 4.0)
         poses = dolly_path(seed, (0.0, height, 0.0), n_frames or 16, pitch_deg=pitch)
         f_m = intr["f_m"]
         fn = lambda: scene_grass_field(seed, dens, f_m=f_m)

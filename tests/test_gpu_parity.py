@@ -145,12 +145,16 @@ def test_gbuffer_matches_oracle():
         assert max_abs(got["normal"].cpu().numpy()[..., :3][ok], ref["normal"][ok]) < 1e-5
 
 
-def test_gpu_hits_equal_brute_force_on_tiny_scenes():
+@pytest.mark.parametrize("builder,width", [("ploc", 4), ("ploc", 2), ("lbvh", 4)])
+def test_gpu_hits_equal_brute_force_on_tiny_scenes(builder, width):
     """G-buffer ids against the oracle's all-triangle loop (no BVH on either side
-    decides the answer), incl. shared-edge and coplanar ties; 0, 1 and 2 triangles."""
+    decides the answer), incl. shared-edge and coplanar ties; 0, 1 and 2 triangles;
+    every tree builder and traversal width."""
     from paper_2210_06158_gb300 import dof
     import torch
     ctx = dof.Context(0)
+    ctx.set_bvh_builder(builder)
+    ctx.set_bvh_width(width)
     pose = camera_pose((0.0, 0.0, 0.0), pitch_deg=0.0)
     cam = Camera.from_poses(dict(f_m=0.05, f_number=2.0, focus_m=3.0, sensor_w_m=0.036), pose)
     W, H = 96, 64
@@ -257,6 +261,48 @@ def test_checkpoint_resume_bit_identical():
     with pytest.raises(dof.DofError) as e:
         other.load(ck)
     assert e.value.code == -7
+
+
+def test_tree_shape_does_not_change_hits():
+    """The closest hit is a property of the triangles, not of the tree: PLOC or LBVH,
+    binary or 4-wide traversal give bit-identical hit ids and images."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    dev = torch.device("cuda", 0)
+    w = make_workload("c2", W=322, H=182, n_frames=2, session=3)
+    prm = dict(w.params)
+    osc = oracle.Scene(w.scene)
+    gbs = []
+    for f in range(2):
+        gb = oracle.gbuffer_f32(oracle.gbuffer(osc, w.camera(f), prm, w.W, w.H))
+        gbs.append({k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in gb.items()})
+    results = []
+    for builder in ("ploc", "lbvh"):
+        ctx = dof.Context(0)
+        ctx.set_bvh_builder(builder)
+        sc = dof.Scene(ctx, w.scene)
+        info = sc.info()
+        assert info.n_nodes4 > 0 and 0 < info.depth4 <= info.depth
+        assert info.n_nodes4 <= info.n_nodes
+        for width in (2, 4):
+            ctx.set_bvh_width(width)
+            h = dof.History(ctx, w.W, w.H, max_rays=oracle.max_rays(prm), record_rays=True)
+            outs = []
+            for f in range(2):
+                outs.append(dof.frame(ctx, sc, gbs[f], w.camera(f), prm, h).cpu().numpy())
+            torch.cuda.synchronize()
+            assert h.stats().device_status == 0
+            results.append((builder, width, outs, h.read("RAY_PRIM", np.int32), h.stats().node_visits))
+            h.close()
+        sc.close()
+    b0 = results[0]
+    for b in results[1:]:
+        for f in range(2):
+            assert np.array_equal(b0[2][f], b[2][f]), (b[0], b[1], f)
+        assert np.array_equal(b0[3], b[3]), (b[0], b[1])
+    # the 4-wide tree visits fewer nodes than the binary one
+    assert results[0][1] == 2 and results[1][1] == 4
+    assert results[1][4] < results[0][4]
 
 
 def test_batch_equals_alone():
