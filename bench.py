@@ -34,20 +34,20 @@ sys.path.insert(0, ROOT)
 METRIC = "hybrid-DoF frames/s at 1080p/4K, %HBM roofline; served p50/p99 frame latency"
 CYCLE = 16
 
-# FP32 operations of the traversal (FMA = 2): a node visit tests two child boxes
-# (per box 6 (sub, mul) slab products = 12, 10 min/max, 1 compare -> 23, x2 = 46) and
-# orders them (1); a watertight triangle test (Woop et al. 2013) is 9 subtractions,
-# 6 shears (sub, mul) = 12, 3 edge functions (2 mul + sub) = 9, 6 sign tests,
-# det (2), T (3 mul + 3 FMA = 9), 1 division -> 48.
-FLOP_PER_NODE = 47.0
+# FP32 operations of the traversal (FMA = 2): a binary node visit tests two child
+# boxes (per box 6 (sub, mul) slab products = 12, 10 min/max, 1 compare -> 23, x2 = 46)
+# and orders them (1); a 4-wide node visit tests four boxes (6 FMA slab products = 12,
+# 10 min/max, 1 compare -> 23, x4 = 92) and sorts them (5 compares); a watertight
+# triangle test (Woop et al. 2013) is 9 subtractions, 6 shears (sub, mul) = 12,
+# 3 edge functions (2 mul + sub) = 9, 6 sign tests, det (2), T (3 mul + 3 FMA = 9),
+# 1 division -> 48.
+FLOP_PER_NODE = {2: 47.0, 4: 97.0}
 FLOP_PER_TRI = 48.0
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes (read + write) per launch from the last ncu capture of each kernel on the
-# 1080p workload (profiles/top_kernels_c2_1080p.md); a kernel changed since then has no
-# entry.
-PROFILED_TRAFFIC = {"c2": {"k_trace_rays": 10.32e6, "k_recon": 30.23e6, "k_main_filter": 10.45e6,
-                           "k_accumulate": 61.69e6, "k_composite": 65.88e6, "k_downscale_tiles": 41.53e6}}
+# workload (profiles/); a kernel or workload changed since then has no entry.
+PROFILED_TRAFFIC = {}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
@@ -189,7 +189,7 @@ def oracle_sample(w, budget_s=15.0, steps=None):
 def run_ours(args, rank, world):
     import numpy as np
     import torch
-    from paper_2210_06158_gb300 import _build, dof
+    from paper_2210_06158_gb300 import _build, dof, tune
     from synth import make_workload
 
     _build.build()
@@ -232,6 +232,12 @@ def run_ours(args, rank, world):
     def step(s, h, g=None):
         gb = g if g is not None else gbs[s % CYCLE]
         dof.frame(ctx, scene, gb, None, None, h, out, cam_struct=cams[s], params_s=pstruct)
+
+    # session start: the autotuner picks the tracer's tree and launch shape (untimed)
+    t0 = time.perf_counter()
+    tuned, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4)
+    tune_s = time.perf_counter() - t0
+    hist.reset()
 
     dist = world > 1
     if dist:
@@ -356,7 +362,7 @@ def run_ours(args, rank, world):
     sm_mhz = clocks.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6 / 1e12      # TFLOP/s, FMA = 2
-    trace_flop = (visits * FLOP_PER_NODE + tests * FLOP_PER_TRI) / n_samples
+    trace_flop = (visits * FLOP_PER_NODE[tuned["bvh_width"]] + tests * FLOP_PER_TRI) / n_samples
     traffic = PROFILED_TRAFFIC.get(args.config, {}).get(dom)
     if dom == "k_trace_rays" and kavg[dom] > 0:
         achieved = trace_flop / (kavg[dom] * 1e-3) / 1e12
@@ -387,12 +393,13 @@ def run_ours(args, rank, world):
                                     f"{w.intr['focus_m']:g} m, CoC radius <= {prm['max_coc_px']:g} px, {spp} spp, "
                                     f"16-frame dolly",
                            resolution=[w.W, w.H], triangles=info.n_tris, spp=spp, bvh_depth=info.depth,
+                           tracer=dict(tuned, tune_s=round(tune_s, 2)),
                            parallelism="replicas" if world > 1 else "single-gpu",
                            l2="inputs larger than L2: 16 distinct G-buffers cycled (16 x 41 MB)"),
                roofline=roof, e2e=e2e, fp16_storage=fp16,
-               # per frame: 5 post-process, mask, trace, shade, 2 temporal, RT median, 4 mip, recon,
-               # composite (+ 2 edge kernels in adaptive mode)
-               gpu_launches=(17 + (2 if int(prm["ray_mode"]) == 1 else 0)) * args.steps,
+               # per frame: reset, 5 post-process, mask, trace, shade, 2 temporal, RT median, 4 mip,
+               # recon, composite (+ 2 edge kernels in adaptive mode)
+               gpu_launches=(18 + (2 if int(prm["ray_mode"]) == 1 else 0)) * args.steps,
                clocks=clocks, kernel_ms=kern,
                image_passes={"ms": round(img_ms, 4), "gbs": round(img_bytes / (img_ms * 1e-3) / 1e9, 1),
                              "frac_of_hbm": round(img_bytes / (img_ms * 1e-3) / 1e9 / hbm_peak, 4)},
@@ -434,7 +441,7 @@ def batch_sessions(n, res_cycle, tri_lo, tri_hi, seed, frames=8):
 
 def run_batch(args):
     import torch
-    from paper_2210_06158_gb300 import _build, dof
+    from paper_2210_06158_gb300 import _build, dof, tune
     _build.build()
     dev = torch.device("cuda", 0)
     ctx = dof.Context(0)
@@ -448,7 +455,8 @@ def run_batch(args):
             del g["prim"]
             gbs.append(g)
         S.append(dict(w=w, sc=sc, gbs=gbs, hb=dof.History(ctx, w.W, w.H), hs=dof.History(ctx, w.W, w.H),
-                      out=torch.empty((w.H, w.W, 4), device=dev), p=dof.params_struct(w.params),
+                      h16=dof.History(ctx, w.W, w.H), out=torch.empty((w.H, w.W, 4), device=dev),
+                      p=dof.params_struct(w.params), p16=dof.params_struct(dict(w.params, image_storage=1)),
                       cams=[dof.camera_struct(w.camera(f)) for f in range(w.n_frames)]))
     tris = sum(s["sc"].info().n_tris for s in S)
     px = sum(s["w"].W * s["w"].H for s in S)
@@ -459,14 +467,25 @@ def run_batch(args):
         dof.batch_frame(ctx, [dict(scene=s["sc"], gbuf=s["gbs"][f], cam=s["cams"][f], params=s["p"], hist=s["hb"],
                                    out=s["out"]) for s in S])
 
+    def batched16(step):
+        f = step % 8
+        dof.batch_frame(ctx, [dict(scene=s["sc"], gbuf=s["gbs"][f], cam=s["cams"][f], params=s["p16"],
+                                   hist=s["h16"], out=s["out"]) for s in S])
+
     def single(step):
         f = step % 8
         for s in S:
             dof.frame(ctx, s["sc"], s["gbs"][f], None, None, s["hs"], s["out"], cam_struct=s["cams"][f],
                       params_s=s["p"])
 
+    # the autotuner picks the tracer's tree and launch shape on the batch (untimed)
+    t0 = time.perf_counter()
+    tuned, _ = tune.tune_trace(ctx, batched, frames=2)
+    tune_s = time.perf_counter() - t0
+    for s in S:
+        s["hb"].reset()
     res = {}
-    for name, fn in (("batched", batched), ("per_frame", single)):
+    for name, fn in (("batched", batched), ("batched_fp16", batched16), ("per_frame", single)):
         for k in range(args.warmup):
             fn(k)
         torch.cuda.synchronize()
@@ -486,9 +505,14 @@ def run_batch(args):
                 config=dict(workload=f"batched: 32 sessions, own lawn scenes 200k-1M triangles ({tris} total), "
                                      f"1280x720/1920x1080/2560x1440 cycled ({px / 1e6:.1f} Mpx per step), 8-frame dollies, "
                                      "one dof_batch_frame (one launch per pass) per step",
-                            l2="inputs larger than L2: 256 distinct G-buffers"),
+                            l2="inputs larger than L2: 256 distinct G-buffers",
+                            tracer=dict(tuned, tune_s=round(tune_s, 2))),
                 per_frame_form=dict(frames_per_s=round(res["per_frame"]["frames_per_s"], 2),
-                                    ms_per_step=round(res["per_frame"]["ms_per_step"], 3)),
+                                    ms_per_step=round(res["per_frame"]["ms_per_step"], 3),
+                                    note="plain FP32, one dof_frame per session"),
+                batched_fp16_form=dict(frames_per_s=round(res["batched_fp16"]["frames_per_s"], 2),
+                                       ms_per_step=round(res["batched_fp16"]["ms_per_step"], 3),
+                                       note="FP16 storage of the colour image buffers, FP32 arithmetic"),
                 gpu_launches=18 * args.steps, clocks=res["batched"]["clocks"])
     return line
 

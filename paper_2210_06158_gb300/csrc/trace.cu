@@ -204,6 +204,42 @@ __device__ __forceinline__ bool step4(const Ray &ray, const Bvh4Node *__restrict
     return false;
 }
 
+// One step of the binary traversal: an internal node tests its two child boxes and
+// descends into the nearer hit child (the farther one is pushed); a leaf is
+// intersected.  Returns true when the query has ended (stack empty or a guard tripped).
+__device__ __forceinline__ bool step2(const Ray &ray, const BvhNode *__restrict__ nodes, int n_nodes,
+                                      const float4 *__restrict__ tris, int n_tree, int &node, int *stack, int &sp,
+                                      HitRec &h, uint32_t &n_visit, uint32_t &n_tests, uint32_t *status) {
+    if (node >= n_nodes || (node < 0 && ~node >= n_tree)) {
+        atomicOr(status, 2u);
+        return true;
+    }
+    if (node >= 0) {
+        n_visit++;
+        const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
+        float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+        int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
+        float t0, t1;
+        bool h0 = box_hit(ray, make_float3(a.x, a.y, a.z), make_float3(a.w, b.x, b.y), h.t, t0);
+        bool h1 = box_hit(ray, make_float3(b.z, b.w, c.x), make_float3(c.y, c.z, c.w), h.t, t1);
+        if (h0 && h1) {
+            int nearc = t0 <= t1 ? ref.x : ref.y, farc = t0 <= t1 ? ref.y : ref.x;
+            if (sp < kStack) stack[sp++] = farc;
+            else atomicOr(status, 1u);
+            node = nearc;
+            return false;
+        }
+        if (h0) { node = ref.x; return false; }
+        if (h1) { node = ref.y; return false; }
+    } else {
+        n_tests++;
+        tri_update(ray, tris, ~node, h);
+    }
+    if (sp == 0) return true;
+    node = stack[--sp];
+    return false;
+}
+
 // closest hit = lexicographic min of (t, prim id); boxes with entry == best are kept.
 // A reference outside the tree, a full stack or more steps than a valid tree can take
 // set the status word and end the query (no fault, no endless loop).
@@ -238,43 +274,13 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
         return h;
     }
     int node = sc.root;
-    const int n_nodes = sc.n_tris - 1;
     const long long max_steps = 4ll * sc.n_tris + 64;
     for (long long steps = 0;; steps++) {
-        if (steps > max_steps || node >= n_nodes || (node < 0 && ~node >= sc.n_tris)) {
+        if (steps > max_steps) {
             atomicOr(status, 2u);
             break;
         }
-        if (node >= 0) {
-            n_visit++;
-            const float4 *np = reinterpret_cast<const float4 *>(sc.nodes + node);
-            float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
-            int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
-            float t0, t1;
-            bool h0 = box_hit(r, make_float3(a.x, a.y, a.z), make_float3(a.w, b.x, b.y), h.t, t0);
-            bool h1 = box_hit(r, make_float3(b.z, b.w, c.x), make_float3(c.y, c.z, c.w), h.t, t1);
-            if (h0 && h1) {
-                int nearc = t0 <= t1 ? ref.x : ref.y, farc = t0 <= t1 ? ref.y : ref.x;
-                if (sp < kStack) stack[sp++] = farc;
-                else atomicOr(status, 1u);
-                node = nearc;
-                continue;
-            }
-            if (h0) { node = ref.x; continue; }
-            if (h1) { node = ref.y; continue; }
-        } else {
-            n_tests++;
-            int k = ~node;
-            const float4 *tp = sc.tris + 3 * (size_t)k;
-            float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-            float t = tri_hit(r, v0, v1, v2);
-            if (t > 0.f) {
-                int prim = __float_as_int(v0.w);
-                if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
-            }
-        }
-        if (sp == 0) break;
-        node = stack[--sp];
+        if (step2(r, sc.nodes, sc.n_tris - 1, sc.tris, sc.n_tris, node, stack, sp, h, n_visit, n_tests, status)) break;
     }
     return h;
 }
@@ -482,8 +488,10 @@ __device__ __noinline__ void lens_ray(const DevCam &cam, const DevParams &p, uin
 // Persistent tracer, one ray per lane (Aila and Laine 2009, persistent threads with
 // dynamic fetch): lanes whose ray has finished take new rays from the ray list when
 // enough of the warp is idle, so divergent rays do not hold the warp.  Writes the
-// closest hit of each ray: (sorted triangle index or -1, t).
-__global__ void __launch_bounds__(128, 8) k_trace_rays(const __grid_constant__ BatchArgs A) {
+// closest hit of each ray: (sorted triangle index or -1, t).  kWide: every session of
+// the batch traverses its 4-wide tree, else every session its binary tree.
+template <bool kWide>
+__global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ BatchArgs A) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     // inclusive prefix of the sessions' ray counts (the batch's concatenated ray list)
     __shared__ uint32_t pre[kMaxBatch];
@@ -504,7 +512,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_rays(const __grid_constant__ B
     int si = 0;
     Ray ray;
     HitRec h{INFINITY, -1, -1};
-    int node = 0, sp = 0, n_tree = 0, n_nodes = 0, n4 = 0;
+    int node = 0, sp = 0, n_tree = 0, n_nodes = 0;
     const BvhNode *nodes = nullptr;
     const Bvh4Node *nodes4 = nullptr;
     const float4 *tris = nullptr;
@@ -535,12 +543,15 @@ __global__ void __launch_bounds__(128, 8) k_trace_rays(const __grid_constant__ B
                     float3 L, dir;
                     lens_ray(S.cam, S.p, q, sm, L, dir);
                     ray = make_ray(L, dir);
-                    nodes = S.sc.nodes;
-                    nodes4 = S.sc.nodes4;
-                    n4 = S.sc.n_nodes4;
+                    if (kWide) {
+                        nodes4 = S.sc.nodes4;
+                        n_nodes = S.sc.n_nodes4;
+                    } else {
+                        nodes = S.sc.nodes;
+                        n_nodes = S.sc.n_tris - 1;
+                    }
                     tris = S.sc.tris;
                     n_tree = S.sc.n_tris;
-                    n_nodes = n_tree - 1;
                     h = HitRec{INFINITY, -1, -1};
                     for (int k = n_tree; k < n_tree + S.sc.n_large; k++) {
                         n_tests++;
@@ -551,7 +562,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_rays(const __grid_constant__ B
                             if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
                         }
                     }
-                    node = nodes4 ? S.sc.root4 : S.sc.root;
+                    node = kWide ? S.sc.root4 : S.sc.root;
                     sp = 0;
                     steps = 0;
                     max_steps = 4ll * n_tree + 64;
@@ -563,49 +574,16 @@ __global__ void __launch_bounds__(128, 8) k_trace_rays(const __grid_constant__ B
         }
         if (!have) continue;
         for (int it = 0; it < steps_per_round; it++) {
-            bool done = false;
-            if (nodes4) {
-                if (++steps > max_steps) {
-                    atomicOr(&A.s[si].counters[3], 2u);
-                    done = true;
-                } else {
-                    done = step4(ray, nodes4, n4, tris, n_tree, node, stack, sp, h, n_visit, n_tests,
-                                 &A.s[si].counters[3]);
-                }
-            } else if (++steps > max_steps || node >= n_nodes || (node < 0 && ~node >= n_tree)) {
+            bool done;
+            if (++steps > max_steps) {
                 atomicOr(&A.s[si].counters[3], 2u);
                 done = true;
-            } else if (node >= 0) {
-                n_visit++;
-                const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
-                float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
-                int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
-                float t0, t1;
-                bool h0 = box_hit(ray, make_float3(a.x, a.y, a.z), make_float3(a.w, b.x, b.y), h.t, t0);
-                bool h1 = box_hit(ray, make_float3(b.z, b.w, c.x), make_float3(c.y, c.z, c.w), h.t, t1);
-                if (h0 && h1) {
-                    int nearc = t0 <= t1 ? ref.x : ref.y, farc = t0 <= t1 ? ref.y : ref.x;
-                    if (sp < kStack) stack[sp++] = farc;
-                    else atomicOr(&A.s[si].counters[3], 1u);
-                    node = nearc;
-                    continue;
-                }
-                if (h0) { node = ref.x; continue; }
-                if (h1) { node = ref.y; continue; }
-                if (sp == 0) done = true;
-                else node = stack[--sp];
+            } else if (kWide) {
+                done = step4(ray, nodes4, n_nodes, tris, n_tree, node, stack, sp, h, n_visit, n_tests,
+                             &A.s[si].counters[3]);
             } else {
-                n_tests++;
-                int k = ~node;
-                const float4 *tp = tris + 3 * (size_t)k;
-                float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-                float t = tri_hit(ray, v0, v1, v2);
-                if (t > 0.f) {
-                    int prim = __float_as_int(v0.w);
-                    if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
-                }
-                if (sp == 0) done = true;
-                else node = stack[--sp];
+                done = step2(ray, nodes, n_nodes, tris, n_tree, node, stack, sp, h, n_visit, n_tests,
+                             &A.s[si].counters[3]);
             }
             if (done) {
                 A.s[si].hits[r] = make_int2(h.k, __float_as_int(h.t));
@@ -710,7 +688,11 @@ void launch_mask_b(const BatchArgs &A, bool any_adaptive, cudaStream_t st, DofHi
 }
 
 void launch_trace_b(const BatchArgs &A, int blocks, cudaStream_t st, DofHistory *tm) {
-    k_trace_rays<<<blocks, 128, 0, st>>>(A);
+    // the 4-wide kernel when every session of the batch has its 4-wide tree in use
+    bool wide = A.ns > 0;
+    for (int i = 0; i < A.ns; i++) wide = wide && A.s[i].sc.nodes4 != nullptr;
+    if (wide) k_trace_rays<true><<<blocks, 128, 0, st>>>(A);
+    else k_trace_rays<false><<<blocks, 128, 0, st>>>(A);
     tmark(tm, DOF_K_TRACE, st);
     k_shade<<<A.start[SH_SHADE][A.ns], 128, 0, st>>>(A);
     tmark(tm, DOF_K_SHADE, st);

@@ -220,9 +220,10 @@ class Context:
         """Tree the rays traverse: 4 (collapsed 4-wide nodes, default) or 2 (binary)."""
         _check(lib().dof_ctx_set_option(self.ptr, 6, int(width)))
 
-    def set_trace(self, blocks_per_sm=None, refill_idle=None, steps=None):
-        """Launch shape / scheduling of the persistent tracer (no effect on results)."""
-        for opt, v in ((2, blocks_per_sm), (3, refill_idle), (4, steps)):
+    def set_trace(self, blocks_per_sm=None, refill_idle=None, steps=None, bvh_width=None):
+        """Launch shape / scheduling of the persistent tracer and the tree it traverses
+        (no effect on results)."""
+        for opt, v in ((2, blocks_per_sm), (3, refill_idle), (4, steps), (6, bvh_width)):
             if v is not None:
                 _check(lib().dof_ctx_set_option(self.ptr, opt, int(v)))
 

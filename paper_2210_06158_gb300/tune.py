@@ -1,7 +1,9 @@
 """Autotuner of the persistent ray tracer's launch shape and scheduling.
 
-The knobs (128-thread blocks per SM, idle lanes that trigger a refill, traversal
-steps between refill checks) change only the speed of dof_frame, never its result.
+The knobs (the tree the rays traverse: binary or 4-wide; 128-thread blocks per SM,
+idle lanes that trigger a refill, traversal steps between refill checks) change only
+the speed of dof_frame, never its result (the closest hit does not depend on the
+tree's shape).
 `tune_trace` times a few frames of the caller's own session for each candidate
 (coordinate descent from the defaults, CUDA events on the session's stream) and
 leaves the fastest setting on the context.
@@ -10,11 +12,12 @@ leaves the fastest setting on the context.
 from __future__ import annotations
 
 SPACE = {
+    "bvh_width": [4, 2],
     "blocks_per_sm": [4, 6, 8, 12, 16],
     "refill_idle": [4, 8, 12, 16, 24],
     "steps": [8, 16, 32, 64],
 }
-DEFAULT = {"blocks_per_sm": 8, "refill_idle": 16, "steps": 64}
+DEFAULT = {"bvh_width": 4, "blocks_per_sm": 8, "refill_idle": 16, "steps": 64}
 
 
 def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None):
