@@ -152,7 +152,7 @@ size_t dof_ctx_bytes_in_use(const DofCtx *ctx);
 #define DOF_OPT_TRACE_BLOCKS_PER_SM 2   /* 128-thread blocks per SM, 1..32 (default 8) */
 #define DOF_OPT_TRACE_REFILL_IDLE   3   /* refill a warp when this many lanes are idle, 1..32 (default 16) */
 #define DOF_OPT_TRACE_STEPS         4   /* traversal steps between refill checks, 1..256 (default 64) */
-#define DOF_OPT_PLOC_RADIUS         5   /* PLOC nearest-neighbour search radius, 1..256 (default 24) */
+#define DOF_OPT_PLOC_RADIUS         5   /* PLOC nearest-neighbour search radius, 1..256 (default 48) */
 #define DOF_OPT_BVH_WIDTH           6   /* tree the rays traverse: 4 (default) = the binary tree collapsed
                                          * to 4-wide nodes, 2 = the binary tree; same hits either way */
 int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value);

@@ -192,7 +192,7 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->trace_blocks_per_sm = 8;
     c->trace_refill_idle = 16;
     c->trace_steps = 64;
-    c->ploc_radius = 24;
+    c->ploc_radius = 48;
     c->bvh_width = 4;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
@@ -200,6 +200,18 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
         cudaGetLastError();
         delete c;
         return dof_set_error(DOF_ERR_OOM, "dof_ctx_create: status word");
+    }
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (cudaStreamCreateWithPriority(&c->ray_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->ray_stream) cudaStreamDestroy(c->ray_stream);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        cudaFree(c->d_status);
+        delete c;
+        return dof_set_error(DOF_ERR_CUDA, "dof_ctx_create: stream or events");
     }
     if (post_init_tables() != 0 || recon_init_tables() != 0) {
         cudaFree(c->d_status);
@@ -248,6 +260,10 @@ void ctx_retain(DofCtx *ctx) { ctx->refs++; }
 void ctx_release(DofCtx *ctx) {
     if (--ctx->refs == 0) {
         DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->ray_stream);
+        cudaStreamDestroy(ctx->ray_stream);
+        cudaEventDestroy(ctx->ev_fork);
+        cudaEventDestroy(ctx->ev_join);
         cudaFree(ctx->d_status);
         delete ctx;
     }
@@ -600,12 +616,34 @@ static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStre
     } else {
         tm = nullptr;
     }
+    const int trace_blocks = ctx->sm_count * ctx->trace_blocks_per_sm;
     launch_reset_b(A, st);
-    launch_post_b(A, st, tm);
-    launch_mask_b(A, adaptive, st, tm);
-    launch_trace_b(A, ctx->sm_count * ctx->trace_blocks_per_sm, st, tm);
-    launch_temporal_b(A, st, tm);
-    launch_recon_b(A, st, tm);
+    launch_tiles_b(A, st, tm);
+    if (tm) {
+        // per-kernel timing: every kernel in sequence on the caller's stream
+        launch_pp_b(A, st, tm);
+        launch_mask_b(A, adaptive, st, tm);
+        launch_trace_b(A, trace_blocks, st, tm);
+        launch_temporal_b(A, st, tm);
+        launch_recon_b(A, st, tm);
+        launch_composite_b(A, st, tm);
+    } else {
+        // the ray path (A6 - A11) on the high-priority stream, the post-process filters
+        // (A3 - A5, which only the composite reads) beside it on the caller's stream: the
+        // filters fill the SMs that the tracer's tail leaves idle
+        std::lock_guard<std::mutex> lock(ctx->launch_mu);
+        cudaStream_t rs = ctx->ray_stream;
+        cudaEventRecord(ctx->ev_fork, st);
+        cudaStreamWaitEvent(rs, ctx->ev_fork, 0);
+        launch_mask_b(A, adaptive, rs, nullptr);
+        launch_trace_b(A, trace_blocks, rs, nullptr);
+        launch_temporal_b(A, rs, nullptr);
+        launch_recon_b(A, rs, nullptr);
+        cudaEventRecord(ctx->ev_join, rs);
+        launch_pp_b(A, st, nullptr);
+        cudaStreamWaitEvent(st, ctx->ev_join, 0);
+        launch_composite_b(A, st, nullptr);
+    }
     int rc = dof_cuda_check(cudaGetLastError(), "dof_frame launch");
     if (rc) return rc;
     for (uint32_t s = 0; s < n; s++) {

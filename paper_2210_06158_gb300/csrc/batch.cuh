@@ -84,9 +84,11 @@ __device__ __forceinline__ const SessDesc &block_session(const BatchArgs &A, int
 #endif
 
 // host: launch wrappers per kernel group (post.cu, trace.cu, temporal.cu, recon.cu)
-void launch_post_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
+void launch_tiles_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);    // A1, A2
+void launch_pp_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);       // A3 - A5
 void launch_mask_b(const BatchArgs &A, bool any_adaptive, cudaStream_t st, DofHistory *timing);
 void launch_trace_b(const BatchArgs &A, int blocks, cudaStream_t st, DofHistory *timing);
 void launch_temporal_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
-void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
+void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);    // A10, A11
+void launch_composite_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing); // A12
 void launch_reset_b(const BatchArgs &A, cudaStream_t st);

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "../../include/dof.h"
@@ -101,6 +102,12 @@ struct DofCtx {
     int ploc_radius;
     int bvh_width;                 // 4: traverse the collapsed 4-wide tree, 2: the binary tree
     uint32_t *d_status;            // device status word of context-level launches
+    // A frame's ray path (mask .. reconstruction) runs on ray_stream (highest priority)
+    // while its post-process filters run on the caller's stream; ev_fork / ev_join order
+    // them around the shared inputs (tiles) and the composite.
+    cudaStream_t ray_stream;
+    cudaEvent_t ev_fork, ev_join;
+    std::mutex launch_mu;          // one frame's enqueue at a time on ray_stream
 };
 
 struct DofScene {

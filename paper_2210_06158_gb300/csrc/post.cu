@@ -182,12 +182,16 @@ __global__ void k_median_pp(const __grid_constant__ BatchArgs A) {
 
 int post_init_tables() { return upload_filter_tables(); }
 
-void launch_post_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+void launch_tiles_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     k_downscale_tiles<<<A.start[SH_TILE8][n], dim3(8, 8), 0, st>>>(A);
     tmark(tm, DOF_K_DOWNSCALE, st);
     k_tile_dilate<<<A.start[SH_TILEDIL][n], dim3(16, 16), 0, st>>>(A);
     tmark(tm, DOF_K_DILATE, st);
+}
+
+void launch_pp_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+    const int n = A.ns;
     k_prefilter<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
     tmark(tm, DOF_K_PREFILTER, st);
     k_main_filter<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);

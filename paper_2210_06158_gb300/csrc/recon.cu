@@ -262,6 +262,11 @@ void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
     tmark(tm, DOF_K_MIPS, st);
     k_recon<<<A.start[SH_HPX][n], b, 0, st>>>(A);
     tmark(tm, DOF_K_RECON, st);
+}
+
+void launch_composite_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+    const int n = A.ns;
+    dim3 b(32, 8);
     k_composite<<<A.start[SH_FPX][n], b, 0, st>>>(A);
     tmark(tm, DOF_K_COMPOSITE, st);
 }

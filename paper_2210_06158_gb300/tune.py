@@ -1,4 +1,5 @@
-"""Autotuner of the persistent ray tracer's launch shape and scheduling.
+"""Autotuners of the ray tracer: the BVH build (PLOC search radius) and the persistent
+tracer's tree width, launch shape and scheduling.
 
 The knobs (the tree the rays traverse: binary or 4-wide; 128-thread blocks per SM,
 idle lanes that trigger a refill, traversal steps between refill checks) change only
@@ -60,3 +61,47 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None):
             break
     ctx.set_trace(**best)
     return best, seen
+
+
+SCENE_RADII = [16, 24, 48, 96]
+
+
+def tune_scene(ctx, host_scene, run_frame, radii=None, widths=(4, 2), frames=4, stream=None):
+    """Build the scene's BVH with each PLOC search radius and time `frames` frames with
+    each tree width; keep the fastest.  run_frame(scene, k) enqueues frame k of a
+    representative session with the given device scene (the hits, hence the images,
+    do not depend on the tree).  Returns (device scene, {"ploc_radius", "bvh_width"},
+    {(radius, width): ms per frame}); the context keeps the chosen width."""
+    import torch
+    from . import dof
+    st = stream if stream is not None else torch.cuda.current_stream()
+    best, best_ms, best_scene = None, float("inf"), None
+    seen = {}
+    k = 0
+    for r in (radii or SCENE_RADII):
+        ctx.set_ploc_radius(r)
+        sc = dof.Scene(ctx, host_scene)
+        for wdt in widths:
+            ctx.set_bvh_width(wdt)
+            run_frame(sc, k)
+            k += 1
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(frames):
+                run_frame(sc, k)
+                k += 1
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / frames
+            seen[(r, wdt)] = ms
+            if ms < best_ms:
+                best_ms, best = ms, {"ploc_radius": r, "bvh_width": wdt}
+        if best_scene is None or best["ploc_radius"] == r:
+            if best_scene is not None and best_scene is not sc:
+                best_scene.close()
+            best_scene = sc
+        else:
+            sc.close()
+    ctx.set_ploc_radius(best["ploc_radius"])
+    ctx.set_bvh_width(best["bvh_width"])
+    return best_scene, best, seen
