@@ -95,7 +95,7 @@ class OrFrame(C.Structure):
                [("nrays", _pi), ("ray_prim", _pi), ("ray_c", _pd)] + \
                [(n, _pd) for n in ("rt", "crt", "ct", "var", "rt_med", "recon", "out",
                                    "hist_in", "hist_out", "var_in", "var_out")] + \
-               [("has_history", C.c_int32), ("max_rays", C.c_int32)]
+               [("has_history", C.c_int32), ("max_rays", C.c_int32), ("nrays_force", _pi)]
 
 
 def _declare(L):
@@ -285,14 +285,21 @@ class History:
         self.var = np.zeros(n)
         self.valid = False
 
+    def copy(self) -> "History":
+        h = History.__new__(History)
+        h.hist, h.var, h.valid = self.hist.copy(), self.var.copy(), self.valid
+        return h
+
 
 def max_rays(prm) -> int:
     return int(prm["spp"]) if int(prm["ray_mode"]) == 0 else int(prm["m"])
 
 
 def frame(scene: Scene, cam, prm, W, H, gb32: dict, hist: History | None = None,
-          keep_rays: bool = True) -> dict:
-    """Run one frame; returns every intermediate (numpy, float64) and updates `hist`."""
+          keep_rays: bool = True, nrays_force=None) -> dict:
+    """Run one frame; returns every intermediate (numpy, float64) and updates `hist`.
+    nrays_force (tests): int32 (H/2, W/2), a ray count to take instead of the mask's
+    where >= 0 (the count decision's ties, where either count is valid)."""
     W2, H2 = W // 2, H // 2
     N = W2 * H2
     T = int(prm["tile"])
@@ -320,6 +327,10 @@ def frame(scene: Scene, cam, prm, W, H, gb32: dict, hist: History | None = None,
     fr.var_in = hist.var.ctypes.data_as(_pd)
     fr.has_history = 1 if hist.valid else 0
     fr.max_rays = mr
+    if nrays_force is not None:
+        force = np.ascontiguousarray(nrays_force, dtype=np.int32).reshape(-1)
+        assert force.size == N
+        fr.nrays_force = force.ctypes.data_as(_pi)
     col = np.ascontiguousarray(gb32["color"], dtype=np.float32)
     dep = np.ascontiguousarray(gb32["depth"], dtype=np.float32)
     nrm = np.ascontiguousarray(gb32["normal"], dtype=np.float32)

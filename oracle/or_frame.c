@@ -43,6 +43,11 @@ int or_frame(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int 
     /* ray mask (Section 3.2.1) */
     or_mask(p, W2, H2, fr->z_h, fr->n_h, fr->tile_dil, fr->has_history ? fr->var_in : NULL,
             fr->xn, fr->xf, fr->nrays);
+    if (fr->nrays_force) {
+        int cap = p->ray_mode == 0 ? p->spp : (int)p->m;
+        for (size_t q = 0; q < (size_t)W2 * H2; q++)
+            if (fr->nrays_force[q] >= 0) fr->nrays[q] = fr->nrays_force[q] < cap ? fr->nrays_force[q] : cap;
+    }
     /* ray tracing (Section 3.2.2) */
     or_trace(s, c, p, W, H, fr->nrays, fr->rt, fr->ray_prim, fr->ray_c, fr->max_rays);
     /* accumulation, reprojection and variance (Section 3.2.3) */

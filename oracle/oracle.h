@@ -108,6 +108,12 @@ typedef struct {
     double *var_out;        /* blurred variance of this frame                  */
     int32_t has_history;
     int32_t max_rays;       /* stride of ray_prim / ray_c                       */
+    /* optional (tests): per hpx, a ray count to use instead of the mask's where >= 0.
+     * Where x_f (Eq. 4) lies on an integer, or a tile's dilated near radius on the
+     * mask threshold, the count is decided by rounding and either neighbour is a valid
+     * result; a test passes the other side's count there so the rest of the frame can
+     * be compared.  NULL: the mask's counts. */
+    const int32_t *nrays_force;
 } OrFrame;
 
 int or_frame(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int H,

@@ -133,16 +133,12 @@ def classify_hits(osc, w, params, cam, gpu, ref):
     return n_rays, n_mis, n_bad, mism
 
 
-def threshold_ties(ref, params, cam, w):
-    """hpx whose rays' CoC lies within 1e-5 of the far-weight boundary c = -sqrt2, and
-    tiles whose dilated near radius is within 1e-5 of the mask threshold."""
+def count_ties(ref, params):
+    """hpx whose ray count is decided on a rounding tie: x_f (Eq. 4) within 1e-3 m of
+    an integer the count can jump at, or a tile whose dilated near radius lies within
+    1e-5 of the mask threshold.  Either count is a valid result there."""
     H2, W2 = ref["nrays"].shape
     out = np.zeros((H2, W2), bool)
-    if "ray_c" in ref:
-        c = ref["ray_c"]
-        k = np.arange(c.shape[2])[None, None, :] < ref["nrays"][..., None]
-        near = k & (np.abs(c + SQRT2) <= 1e-5 * SQRT2)
-        out |= near.any(-1)
     if int(params["ray_mode"]) == 1:
         # adaptive count clamp(ceil(x_f), 1, m) jumps only where x_f crosses 1..m-1
         xf = ref["xf"]
@@ -154,6 +150,23 @@ def threshold_ties(ref, params, cam, w):
     tie_t = np.abs(ref["tile_dil"][..., 0] - thr) <= 1e-5 * max(thr, 1e-3)
     out |= np.repeat(np.repeat(tie_t, T, 0), T, 1)[:H2, :W2]
     return out
+
+
+def weight_ties(ref):
+    """hpx with a ray whose hit CoC lies within 1e-5 of the far-weight boundary
+    c = -sqrt2."""
+    H2, W2 = ref["nrays"].shape
+    out = np.zeros((H2, W2), bool)
+    if "ray_c" in ref:
+        c = ref["ray_c"]
+        k = np.arange(c.shape[2])[None, None, :] < ref["nrays"][..., None]
+        near = k & (np.abs(c + SQRT2) <= 1e-5 * SQRT2)
+        out |= near.any(-1)
+    return out
+
+
+def threshold_ties(ref, params, cam, w):
+    return count_ties(ref, params) | weight_ties(ref)
 
 
 def taint_radius(params):

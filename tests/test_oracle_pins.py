@@ -581,3 +581,29 @@ def test_default_params_are_the_papers():
     for k in ("s", "var_w_mask", "alpha", "var_w_recon", "b_max", "h_edge", "lod_scale",
               "lod_max", "depth_range_m"):
         assert p[k] == g[k]["value"], k
+
+
+def test_forced_ray_counts_are_taken_and_neutral():
+    """The test hook for count ties: forcing the mask's own counts reproduces the frame
+    bit for bit; a forced count is the one traced."""
+    import oracle
+    from synth import make_workload
+    w = make_workload("c1", W=64, H=36)
+    prm = dict(w.params)
+    osc = oracle.Scene(w.scene)
+    cam = w.camera(0)
+    gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, prm, w.W, w.H))
+    a = oracle.frame(osc, cam, prm, w.W, w.H, gb, oracle.History(w.W, w.H))
+    b = oracle.frame(osc, cam, prm, w.W, w.H, gb, oracle.History(w.W, w.H), nrays_force=a["nrays"])
+    for k in ("nrays", "rt", "out", "hist_out"):
+        assert np.array_equal(a[k], b[k]), k
+    force = np.full(a["nrays"].shape, -1, np.int32)
+    masked = np.argwhere(a["nrays"] > 0)
+    assert len(masked) > 0
+    j, i = masked[0]
+    force[j, i] = 0
+    c = oracle.frame(osc, cam, prm, w.W, w.H, gb, oracle.History(w.W, w.H), nrays_force=force)
+    assert c["nrays"][j, i] == 0 and c["rt"][j, i, 0] == 0.0
+    other = np.ones(a["nrays"].shape, bool)
+    other[j, i] = False
+    assert np.array_equal(c["nrays"][other], a["nrays"][other])
