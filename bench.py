@@ -47,8 +47,13 @@ FLOP_PER_TRI = 48.0
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes (read + write) per launch from the last ncu capture of each kernel on the
-# workload (profiles/); a kernel or workload changed since then has no entry.
-PROFILED_TRAFFIC = {}
+# workload (profiles/top_kernels_*.md); a kernel or workload changed since then has no
+# entry.  The 4K tracer was captured at 1920x1080 (same scene, lens, 4 spp) and is
+# scaled by the rays of a full launch (6.73M / 1.68M).
+PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": 8.9e6, "k_trace_rays<0>": None, "k_recon": 27.1e6,
+                           "k_main_filter": 10.4e6, "k_accumulate": 55.9e6, "k_composite": 65.8e6,
+                           "k_downscale_tiles": 41.6e6},
+                    "c3": {"k_trace_rays<0>": 21.9e6 * 4.0}}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
@@ -376,10 +381,11 @@ def run_ours(args, rank, world):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6 / 1e12      # TFLOP/s, FMA = 2
     trace_flop = (visits * FLOP_PER_NODE[tuned["bvh_width"]] + tests * FLOP_PER_TRI) / n_samples
-    traffic = PROFILED_TRAFFIC.get(args.config, {}).get(dom)
+    dom_key = f"{dom}<{1 if tuned['bvh_width'] == 4 else 0}>" if dom == "k_trace_rays" else dom
+    traffic = PROFILED_TRAFFIC.get(args.config, {}).get(dom_key) if not args.size else None
     if dom == "k_trace_rays" and kavg[dom] > 0:
         achieved = trace_flop / (kavg[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
+        roof = {"kernel": dom_key, "bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": traffic,
                 "peak_source": f"derived: 2 x {FP32_LANES_PER_SM} FP32 lanes x {n_sm} SMs x {sm_mhz:.0f} MHz",
                 "algorithmic_flop": int(trace_flop), "node_visits_per_ray": round(visits / max(1, rays), 2),
