@@ -133,10 +133,11 @@ def classify_hits(osc, w, params, cam, gpu, ref):
     return n_rays, n_mis, n_bad, mism
 
 
-def count_ties(ref, params):
-    """hpx whose ray count is decided on a rounding tie: x_f (Eq. 4) within 1e-3 m of
-    an integer the count can jump at, or a tile whose dilated near radius lies within
-    1e-5 of the mask threshold.  Either count is a valid result there."""
+def count_ties(ref, params, band=None):
+    """hpx whose ray count is decided on a rounding tie: x_f (Eq. 4) within `band`
+    (default 1e-3 m) of an integer the count can jump at, or a tile whose dilated near
+    radius lies within 1e-5 of the mask threshold.  Either count is a valid result
+    there."""
     H2, W2 = ref["nrays"].shape
     out = np.zeros((H2, W2), bool)
     if int(params["ray_mode"]) == 1:
@@ -144,7 +145,8 @@ def count_ties(ref, params):
         xf = ref["xf"]
         k = np.round(xf)
         jump = (k >= 1) & (k <= float(params["m"]) - 1)
-        out |= jump & (np.abs(xf - k) <= 1e-3 * max(1.0, float(params["m"]))) & (ref["nrays"] > 0)
+        b = 1e-3 * max(1.0, float(params["m"])) if band is None else band
+        out |= jump & (np.abs(xf - k) <= b) & (ref["nrays"] > 0)
     T = int(params["tile"])
     thr = float(np.float32(params["mask_near_hpx"]))
     tie_t = np.abs(ref["tile_dil"][..., 0] - thr) <= 1e-5 * max(thr, 1e-3)

@@ -34,6 +34,7 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
     rt_r = taint_radius(params)
     taint_h = np.zeros((H2, W2), bool)
     stats = []
+    e_var_prev = 0.0     # blurred-variance error of the previous frame (what Eq. 4 reads)
     for k in range(n_frames):
         cam = w.camera(k)
         gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, params, w.W, w.H))
@@ -43,7 +44,11 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
         # ray counts: equal except where the count is decided on a rounding tie (either
         # count is valid there); the oracle then reruns the frame with the kernel's
         # counts at those pixels, so everything downstream is compared in full
-        cties = count_ties(ref, params)
+        # Eq. 4 reads the previous frame's variance times var_w_mask (1e5) times m: its
+        # FP32 error moves x_f by up to m * var_w_mask * e_var_prev
+        m_rays = float(params["m"])
+        xf_tol = m_rays * (1e-4 + float(params["var_w_mask"]) * e_var_prev) + 1e-6
+        cties = count_ties(ref, params, band=max(1e-3 * max(1.0, m_rays), xf_tol))
         bad_n = got["nrays"][~cties] != ref["nrays"][~cties]
         assert not bad_n.any(), (int(bad_n.sum()), int(cties.sum()))
         n_forced = int((got["nrays"] != ref["nrays"]).sum())
@@ -69,7 +74,7 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
             e_xn, e_xf = max_abs(got["xn"], ref["xn"]), max_abs(got["xf"][~taint_h], ref["xf"][~taint_h])
             # Eq. 4 scales the variance by 1e5 m: FP32 variance rounding shows up at ~1e-4 m;
             # the tie band of the count is 1e-3 m
-            assert e_xn < 1e-4 and e_xf < 1e-3 * float(params["m"]), (e_xn, e_xf)
+            assert e_xn < 1e-4 and e_xf <= xf_tol, (e_xn, e_xf, xf_tol)
         st = got["stats"]
         assert st.device_status == 0
         assert st.rays == int(got["nrays"].sum())
@@ -104,6 +109,7 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
         # FP32 reprojection of a moving camera is accurate to ~1e-5 px, which mixes that
         # share of a (noisy) neighbour's history in; a static camera is exact
         assert e_ct < 1e-4 and e_var < (2e-5 if cam_moved(cam) else 1e-6), (e_ct, e_var)
+        e_var_prev = e_var
         # ---- final image (linear RGB)
         taint_f = full_res(taint_h, w.W, w.H)
         e_out = max_abs(got["out"][..., :3][~taint_f], ref["out"][..., :3][~taint_f])
