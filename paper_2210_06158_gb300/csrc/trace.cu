@@ -403,9 +403,9 @@ __global__ void k_edges(const __grid_constant__ BatchArgs A) {
 // ---------------------------------------------------------------------------
 // A6: mask, ray count, and compaction into a pixel queue and a flat ray list
 // ---------------------------------------------------------------------------
-// Per block (32 x 8 pixels, one warp per row) one atomic reserves room for the
-// block's masked pixels (queue) and their rays (ray list); inside the block the
-// order is raster order, so neighbouring rays stay neighbours in the list.
+// Per block (32 x 8 pixels, one warp per 8 x 4 tile) one atomic reserves room for the
+// block's masked pixels (queue) and their rays (ray list); inside the block the order
+// is tile by tile, Morton order inside a tile, so neighbouring rays stay neighbours.
 __global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ BatchArgs A) {
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
@@ -416,6 +416,10 @@ __global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ Ba
     int32_t *nrays = S.nrays;
     uint32_t *queue = S.queue, *first_ray = S.first_ray, *ray_pix = S.ray_pix, *counters = S.counters;
     const unsigned lane = threadIdx.x, warp = threadIdx.y;
+    // each warp takes an 8x4 tile of the block's 32x8 pixels, lanes in Morton order, so
+    // that the 32 consecutive rays a tracer warp takes come from a compact patch
+    i = i - (int)threadIdx.x + (int)((warp & 3u) * 8u + (lane & 1u) + ((lane >> 1) & 2u) + ((lane >> 2) & 4u));
+    j = j - (int)threadIdx.y + (int)((warp >> 2) * 4u + ((lane >> 1) & 1u) + ((lane >> 2) & 2u));
     int n = 0;
     uint32_t q = 0;
     if (i < W2 && j < H2) {
