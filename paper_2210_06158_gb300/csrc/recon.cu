@@ -191,10 +191,13 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ BatchArgs
     st_img(out, q, make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b)), p.f16);
 }
 
-// A12: composite per full-resolution pixel
-__global__ void __launch_bounds__(256) k_composite(const __grid_constant__ BatchArgs A) {
+// A12: composite.  One thread per half-resolution pixel (i, j) writes its 2x2
+// full-resolution pixels: their bilinear taps into the half-resolution layers (texel
+// centres at 0.5 (x + 0.5) - 0.5, i.e. i -/+ 1/4) all lie in the clamped 3x3
+// neighbourhood of (i, j), which is loaded once; weights 1/4 and 3/4 are exact.
+__global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ BatchArgs A) {
     int i, j;
-    const SessDesc &S = block_session(A, SH_FPX, i, j);
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevCam &cam = S.cam;
     const DevParams &p = S.p;
     const float4 *__restrict__ color = S.color;
@@ -203,47 +206,75 @@ __global__ void __launch_bounds__(256) k_composite(const __grid_constant__ Batch
     const float4 *__restrict__ recon = S.recon;
     const int32_t *__restrict__ nrays = S.nrays;
     float4 *out = S.out;
-    if (i >= cam.W || j >= cam.H) return;
-    size_t f = (size_t)j * cam.W + i;
-    float z = fminf(__ldg(&depth[f]), p.z_far);
-    float c = coc_of(cam, z);
-    float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
-    float xh = 0.5f * (i + 0.5f) - 0.5f, yh = 0.5f * (j + 0.5f) - 0.5f;
     const int W2 = cam.W2, H2 = cam.H2;
+    if (i >= W2 || j >= H2) return;
     const bool hs = p.f16;
-    float xf = floorf(xh), yf = floorf(yh);
-    float fx = xh - xf, fy = yh - yf;
-    int x0 = (int)xf, y0 = (int)yf;
-    float4 rt = make_float4(0.f, 0.f, 0.f, 0.f), pp = rt;
-    float cov = 0.f;
+    // accumulators of the 2x2 full-resolution pixels (a, b) -> index 2 b + a; the
+    // neighbourhood is visited in raster order, so each pixel sums its four taps in
+    // the order (x0, y0), (x0 + 1, y0), (x0, y0 + 1), (x0 + 1, y0 + 1)
+    float4 pp[4], rt[4];
+    float cov[4];
 #pragma unroll
-    for (int t = 0; t < 4; t++) {
-        int dx = t & 1, dy = t >> 1;
-        int x = min(max(x0 + dx, 0), W2 - 1), y = min(max(y0 + dy, 0), H2 - 1);
-        size_t q = (size_t)y * W2 + x;
-        float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
-        pp = f4fma(w, ld_img(pp_med, q, hs), pp);
-        if (__ldg(&nrays[q]) <= 0) continue;
-        rt = f4fma(w, ld_img(recon, q, hs), rt);
-        cov += w;
+    for (int k = 0; k < 4; k++) {
+        pp[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rt[k] = pp[k];
+        cov[k] = 0.f;
     }
-    float4 s = __ldg(&color[f]);
-    float bx = pp.x, by = pp.y, bz = pp.z;
-    if (cov > 0.f) {
-        float ic = 1.f / cov;
-        float rx = rt.x * ic, ry = rt.y * ic, rz = rt.z * ic, hh = rt.w * ic;
-        float tb;
-        if (c < 0.f) {
-            tb = pp.w;
-        } else {
-            float u = sat(hh / p.h_edge);
-            tb = u * u * (3.f - 2.f * u);
+#pragma unroll
+    for (int ny = 0; ny < 3; ny++)
+#pragma unroll
+        for (int nx = 0; nx < 3; nx++) {
+            int x = min(max(i + nx - 1, 0), W2 - 1), y = min(max(j + ny - 1, 0), H2 - 1);
+            size_t q = (size_t)y * W2 + x;
+            const float4 P = ld_img(pp_med, q, hs);
+            const bool V = __ldg(&nrays[q]) > 0;
+            const float4 R = V ? ld_img(recon, q, hs) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int a = 0; a < 2; a++) {
+                    const int dx = nx - a, dy = ny - b;
+                    if (dx < 0 || dx > 1 || dy < 0 || dy > 1) continue;
+                    // fx = 3/4 for a = 0 (taps i - 1, i), 1/4 for a = 1 (taps i, i + 1)
+                    const float fx = a ? 0.25f : 0.75f, fy = b ? 0.25f : 0.75f;
+                    const float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
+                    const int k = 2 * b + a;
+                    pp[k] = f4fma(w, P, pp[k]);
+                    if (V) {
+                        rt[k] = f4fma(w, R, rt[k]);
+                        cov[k] += w;
+                    }
+                }
         }
-        bx = lerpf(pp.x, lerpf(rx, pp.x, tb), cov);
-        by = lerpf(pp.y, lerpf(ry, pp.y, tb), cov);
-        bz = lerpf(pp.z, lerpf(rz, pp.z, tb), cov);
-    }
-    out[f] = make_float4(lerpf(bx, s.x, ws), lerpf(by, s.y, ws), lerpf(bz, s.z, ws), 1.f);
+#pragma unroll
+    for (int b = 0; b < 2; b++)
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            const int k = 2 * b + a;
+            const size_t f = (size_t)(2 * j + b) * cam.W + (2 * i + a);
+            float z = fminf(__ldg(&depth[f]), p.z_far);
+            float c = coc_of(cam, z);
+            float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
+            const float4 pk = pp[k], rk = rt[k];
+            const float cv = cov[k];
+            float4 s = __ldg(&color[f]);
+            float bx = pk.x, by = pk.y, bz = pk.z;
+            if (cv > 0.f) {
+                float ic = 1.f / cv;
+                float rx = rk.x * ic, ry = rk.y * ic, rz = rk.z * ic, hh = rk.w * ic;
+                float tb;
+                if (c < 0.f) {
+                    tb = pk.w;
+                } else {
+                    float u = sat(hh / p.h_edge);
+                    tb = u * u * (3.f - 2.f * u);
+                }
+                bx = lerpf(pk.x, lerpf(rx, pk.x, tb), cv);
+                by = lerpf(pk.y, lerpf(ry, pk.y, tb), cv);
+                bz = lerpf(pk.z, lerpf(rz, pk.z, tb), cv);
+            }
+            out[f] = make_float4(lerpf(bx, s.x, ws), lerpf(by, s.y, ws), lerpf(bz, s.z, ws), 1.f);
+        }
 }
 
 }  // namespace
@@ -267,6 +298,6 @@ void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
 void launch_composite_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     dim3 b(32, 8);
-    k_composite<<<A.start[SH_FPX][n], b, 0, st>>>(A);
+    k_composite<<<A.start[SH_HPX][n], b, 0, st>>>(A);
     tmark(tm, DOF_K_COMPOSITE, st);
 }
