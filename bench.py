@@ -491,7 +491,8 @@ def run_batch(args):
             del g["prim"]
             gbs.append(g)
         S.append(dict(w=w, sc=sc, gbs=gbs, hb=dof.History(ctx, w.W, w.H), hs=dof.History(ctx, w.W, w.H),
-                      h16=dof.History(ctx, w.W, w.H), out=torch.empty((w.H, w.W, 4), device=dev),
+                      h16=dof.History(ctx, w.W, w.H), hgr=dof.History(ctx, w.W, w.H),
+                      out=torch.empty((w.H, w.W, 4), device=dev),
                       p=dof.params_struct(w.params), p16=dof.params_struct(dict(w.params, image_storage=1)),
                       cams=[dof.camera_struct(w.camera(f)) for f in range(w.n_frames)]))
     tris = sum(s["sc"].info().n_tris for s in S)
@@ -520,8 +521,20 @@ def run_batch(args):
     tune_s = time.perf_counter() - t0
     for s in S:
         s["hb"].reset()
+
+    def graph_items(step):
+        f = step % 8
+        return [dict(scene=s["sc"], gbuf=s["gbs"][f], cam=s["cams"][f], params=s["p"], hist=s["hgr"], out=s["out"])
+                for s in S]
+
+    graph = dof.Graph(ctx, graph_items(0))     # captured once, after tuning
+
+    def batched_graph(step):
+        graph.launch(graph_items(step))
+
     res = {}
-    for name, fn in (("batched", batched), ("batched_fp16", batched16), ("per_frame", single)):
+    for name, fn in (("batched", batched), ("batched_graph", batched_graph), ("batched_fp16", batched16),
+                     ("per_frame", single)):
         for k in range(args.warmup):
             fn(k)
         torch.cuda.synchronize()
@@ -546,6 +559,9 @@ def run_batch(args):
                 per_frame_form=dict(frames_per_s=round(res["per_frame"]["frames_per_s"], 2),
                                     ms_per_step=round(res["per_frame"]["ms_per_step"], 3),
                                     note="plain FP32, one dof_frame per session"),
+                batched_graph_form=dict(frames_per_s=round(res["batched_graph"]["frames_per_s"], 2),
+                                        ms_per_step=round(res["batched_graph"]["ms_per_step"], 3),
+                                        note="the same step captured once as a CUDA graph and replayed"),
                 batched_fp16_form=dict(frames_per_s=round(res["batched_fp16"]["frames_per_s"], 2),
                                        ms_per_step=round(res["batched_fp16"]["ms_per_step"], 3),
                                        note="FP16 storage of the colour image buffers, FP32 arithmetic"),

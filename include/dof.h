@@ -253,6 +253,26 @@ typedef struct {
  * by dof_frame_stats of the first request's history. */
 int dof_batch_frame(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, void *stream);
 
+/* ---- captured steps (CUDA graphs; no counterpart in the paper) --------------------
+ * A step of dof_batch_frame over a fixed set of sessions, captured once as a CUDA graph
+ * and replayed per frame: one graph launch instead of the step's ~20 kernel launches.
+ * The kernels of the graph read the batch descriptor from device memory, which a copy
+ * node refreshes from a pinned staging buffer at the start of every replay, so cameras,
+ * parameters, G-buffer and output pointers may change between launches.
+ *   dof_graph_create: validates `reqs` as dof_batch_frame and captures (nothing runs,
+ *     the histories do not advance).  The graph keeps the histories and their order,
+ *     the launch shapes (sizes, ray modes, spp / m, tree kinds) and the context's tracer
+ *     options of that moment.
+ *   dof_graph_launch: one step, results identical to dof_batch_frame on the same
+ *     requests.  DOF_ERR_MISMATCH if the requests need other launch shapes or other
+ *     histories than the capture.  Launches of one graph on different streams are
+ *     ordered by the library (one graph runs one step at a time).
+ *   dof_graph_destroy: waits for the graph's last launch and frees it. */
+typedef struct DofGraph DofGraph;
+int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, DofGraph **out);
+int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n, void *stream);
+void dof_graph_destroy(DofGraph *g);
+
 /* Synchronise `stream` and report the last frame's counters and the device status. */
 int dof_frame_stats(DofHistory *hist, void *stream, DofFrameStats *out);
 

@@ -582,13 +582,12 @@ static void shape_grid(const SessDesc &d, const DofHistory *h, int shape, int &g
     }
 }
 
-static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStream_t st) {
-    if (n == 0) return DOF_OK;
+// The batch descriptor of one step of `reqs` (validated); *adaptive: a session uses Eq. 4.
+static int build_batch(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, BatchArgs &A, bool &adaptive) {
     if (n > (uint32_t)kMaxBatch) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_batch_frame: %u > %d sessions", n, kMaxBatch);
-    static thread_local BatchArgs A;   // ~22 KB: kept off the stack
     memset(&A, 0, sizeof(A));
     A.ns = (int)n;
-    bool adaptive = false;
+    adaptive = false;
     for (uint32_t s = 0; s < n; s++) {
         for (uint32_t t = 0; t < s; t++)
             if (reqs[t].hist == reqs[s].hist)
@@ -608,25 +607,23 @@ static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStre
     A.cursor = &reqs[0].hist->counters[2];
     A.refill_idle = ctx->trace_refill_idle;
     A.steps_per_round = ctx->trace_steps;
-    DofHistory *tm = reqs[0].hist;
-    cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
-    if (tm->ev && tm->ev_used < kTimingSlots) {
-        // a kernel that is not launched this frame gets an event right after its predecessor's
-        for (int k = 0; k <= DOF_K_COUNT; k++) cudaEventRecord(tm->ev[tm->ev_slot * (DOF_K_COUNT + 1) + k], st);
-    } else {
-        tm = nullptr;
-    }
+    return DOF_OK;
+}
+
+// Every launch of one step.  `A` gives the launch shapes; the kernels receive `as`.
+template <class AS>
+static void enqueue_step(DofCtx *ctx, const BatchArgs &A, const AS &as, bool adaptive, cudaStream_t st, DofHistory *tm) {
     const int trace_blocks = ctx->sm_count * ctx->trace_blocks_per_sm;
-    launch_reset_b(A, st);
-    launch_tiles_b(A, st, tm);
+    launch_reset_b(A, as, st);
+    launch_tiles_b(A, as, st, tm);
     if (tm) {
         // per-kernel timing: every kernel in sequence on the caller's stream
-        launch_pp_b(A, st, tm);
-        launch_mask_b(A, adaptive, st, tm);
-        launch_trace_b(A, trace_blocks, st, tm);
-        launch_temporal_b(A, st, tm);
-        launch_recon_b(A, st, tm);
-        launch_composite_b(A, st, tm);
+        launch_pp_b(A, as, st, tm);
+        launch_mask_b(A, as, adaptive, st, tm);
+        launch_trace_b(A, as, trace_blocks, st, tm);
+        launch_temporal_b(A, as, st, tm);
+        launch_recon_b(A, as, st, tm);
+        launch_composite_b(A, as, st, tm);
     } else {
         // the ray path (A6 - A11) on the high-priority stream, the post-process filters
         // (A3 - A5, which only the composite reads) beside it on the caller's stream: the
@@ -635,28 +632,182 @@ static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStre
         cudaStream_t rs = ctx->ray_stream;
         cudaEventRecord(ctx->ev_fork, st);
         cudaStreamWaitEvent(rs, ctx->ev_fork, 0);
-        launch_mask_b(A, adaptive, rs, nullptr);
-        launch_trace_b(A, trace_blocks, rs, nullptr);
-        launch_temporal_b(A, rs, nullptr);
-        launch_recon_b(A, rs, nullptr);
+        launch_mask_b(A, as, adaptive, rs, nullptr);
+        launch_trace_b(A, as, trace_blocks, rs, nullptr);
+        launch_temporal_b(A, as, rs, nullptr);
+        launch_recon_b(A, as, rs, nullptr);
         cudaEventRecord(ctx->ev_join, rs);
-        launch_pp_b(A, st, nullptr);
+        launch_pp_b(A, as, st, nullptr);
         cudaStreamWaitEvent(st, ctx->ev_join, 0);
-        launch_composite_b(A, st, nullptr);
+        launch_composite_b(A, as, st, nullptr);
     }
-    int rc = dof_cuda_check(cudaGetLastError(), "dof_frame launch");
-    if (rc) return rc;
+}
+
+// host side of a step that was enqueued: the histories' ping-pong advances
+static void finish_step(const DofFrameReq *reqs, uint32_t n) {
     for (uint32_t s = 0; s < n; s++) {
         DofHistory *h = reqs[s].hist;
         h->cur ^= 1;
         h->valid = 1;
         h->frames++;
     }
+}
+
+static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStream_t st) {
+    if (n == 0) return DOF_OK;
+    static thread_local BatchArgs A;   // ~22 KB: kept off the stack
+    bool adaptive = false;
+    int rc = build_batch(ctx, reqs, n, A, adaptive);
+    if (rc) return rc;
+    DofHistory *tm = reqs[0].hist;
+    cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
+    if (tm->ev && tm->ev_used < kTimingSlots) {
+        // a kernel that is not launched this frame gets an event right after its predecessor's
+        for (int k = 0; k <= DOF_K_COUNT; k++) cudaEventRecord(tm->ev[tm->ev_slot * (DOF_K_COUNT + 1) + k], st);
+    } else {
+        tm = nullptr;
+    }
+    enqueue_step(ctx, A, A, adaptive, st, tm);
+    rc = dof_cuda_check(cudaGetLastError(), "dof_frame launch");
+    if (rc) return rc;
+    finish_step(reqs, n);
     if (tm) {
         tm->ev_slot = (tm->ev_slot + 1) % kTimingSlots;
         tm->ev_used++;
     }
     return DOF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// captured steps (CUDA graphs)
+// ---------------------------------------------------------------------------
+
+struct DofGraph {
+    DofCtx *ctx;
+    uint32_t n;
+    DofHistory *hist[kMaxBatch];
+    int start[SH_COUNT][kMaxBatch + 1];
+    bool adaptive, wide;
+    int trace_blocks, refill_idle, steps_per_round;
+    BatchArgs *d_args;            // read by the captured kernels
+    BatchArgs *h_stage;           // pinned source of the captured copy
+    cudaEvent_t staged;           // recorded after the copy: the staging buffer may be rewritten
+    cudaEvent_t done;             // end of the last launch (orders launches on different streams)
+    cudaStream_t last;
+    bool launched;
+    cudaGraphExec_t exec;
+};
+
+static bool all_wide(const BatchArgs &A) {
+    bool w = A.ns > 0;
+    for (int i = 0; i < A.ns; i++) w = w && A.s[i].sc.nodes4 != nullptr;
+    return w;
+}
+
+static void graph_free(DofGraph *g) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->staged) cudaEventDestroy(g->staged);
+    if (g->done) cudaEventDestroy(g->done);
+    if (g->h_stage) cudaFreeHost(g->h_stage);
+    if (g->d_args) cudaFree(g->d_args);
+}
+
+extern "C" int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, DofGraph **out) {
+    if (!ctx || !reqs || !out || n == 0) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_graph_create: null argument");
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    static thread_local BatchArgs A;
+    bool adaptive = false;
+    int rc = build_batch(ctx, reqs, n, A, adaptive);
+    if (rc) return rc;
+    DofGraph *g = new DofGraph();
+    memset(g, 0, sizeof(*g));
+    g->ctx = ctx;
+    g->n = n;
+    for (uint32_t s = 0; s < n; s++) g->hist[s] = reqs[s].hist;
+    memcpy(g->start, A.start, sizeof(A.start));
+    g->adaptive = adaptive;
+    g->wide = all_wide(A);
+    g->trace_blocks = ctx->sm_count * ctx->trace_blocks_per_sm;
+    g->refill_idle = A.refill_idle;
+    g->steps_per_round = A.steps_per_round;
+    cudaGetLastError();
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    auto ck = [&](cudaError_t e, const char *w) { if (rc == DOF_OK && e != cudaSuccess) rc = dof_cuda_check(e, w); };
+    ck(cudaMalloc(&g->d_args, sizeof(BatchArgs)), "dof_graph_create: device arguments");
+    ck(cudaHostAlloc(&g->h_stage, sizeof(BatchArgs), cudaHostAllocDefault), "dof_graph_create: staging");
+    ck(cudaEventCreateWithFlags(&g->staged, cudaEventDisableTiming), "dof_graph_create: event");
+    ck(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming), "dof_graph_create: event");
+    ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "dof_graph_create: stream");
+    if (rc == DOF_OK) {
+        const BatchArgs *dp = g->d_args;
+        ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "dof_graph_create: begin capture");
+        if (rc == DOF_OK) {
+            cudaMemcpyAsync(g->d_args, g->h_stage, sizeof(BatchArgs), cudaMemcpyHostToDevice, cs);
+            cudaEventRecordWithFlags(g->staged, cs, cudaEventRecordExternal);
+            enqueue_step(ctx, A, dp, adaptive, cs, nullptr);
+            cudaError_t e = cudaStreamEndCapture(cs, &graph);
+            ck(e, "dof_graph_create: capture");
+        }
+    }
+    if (rc == DOF_OK) ck(cudaGraphInstantiate(&g->exec, graph, 0), "dof_graph_create: instantiate");
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (rc != DOF_OK) {
+        graph_free(g);
+        delete g;
+        return rc;
+    }
+    ctx_retain(ctx);
+    *out = g;
+    return DOF_OK;
+}
+
+extern "C" int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n, void *stream) {
+    if (!g || !reqs) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_graph_launch: null argument");
+    if (n != g->n) return dof_set_error(DOF_ERR_MISMATCH, "dof_graph_launch: %u sessions, captured %u", n, g->n);
+    for (uint32_t s = 0; s < n; s++)
+        if (reqs[s].hist != g->hist[s])
+            return dof_set_error(DOF_ERR_MISMATCH, "dof_graph_launch: session %u is not the captured history", s);
+    DofCtx *ctx = g->ctx;
+    DeviceGuard dg(ctx->device);
+    static thread_local BatchArgs A;
+    bool adaptive = false;
+    int rc = build_batch(ctx, reqs, n, A, adaptive);
+    if (rc) return rc;
+    if (memcmp(A.start, g->start, sizeof(A.start)) != 0 || adaptive != g->adaptive || all_wide(A) != g->wide ||
+        ctx->sm_count * ctx->trace_blocks_per_sm != g->trace_blocks)
+        return dof_set_error(DOF_ERR_MISMATCH, "dof_graph_launch: launch shapes differ from the captured step");
+    // the kernels' scheduling knobs come from the staged copy; keep the captured ones
+    A.refill_idle = g->refill_idle;
+    A.steps_per_round = g->steps_per_round;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaGetLastError();
+    // the previous launch's copy has consumed the staging buffer
+    rc = dof_cuda_check(cudaEventSynchronize(g->staged), "dof_graph_launch: staging");
+    if (rc) return rc;
+    memcpy(g->h_stage, &A, sizeof(BatchArgs));
+    if (g->launched && st != g->last) cudaStreamWaitEvent(st, g->done, 0);
+    rc = dof_cuda_check(cudaGraphLaunch(g->exec, st), "dof_graph_launch");
+    if (rc) return rc;
+    cudaEventRecord(g->done, st);
+    g->last = st;
+    g->launched = true;
+    finish_step(reqs, n);
+    return DOF_OK;
+}
+
+extern "C" void dof_graph_destroy(DofGraph *g) {
+    if (!g) return;
+    DofCtx *ctx = g->ctx;
+    {
+        DeviceGuard dg(ctx->device);
+        if (g->launched) cudaEventSynchronize(g->done);
+        graph_free(g);
+    }
+    delete g;
+    ctx_release(ctx);
 }
 
 extern "C" int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *gb, const DofCamera *cam,

@@ -83,12 +83,22 @@ __device__ __forceinline__ const SessDesc &block_session(const BatchArgs &A, int
 }
 #endif
 
-// host: launch wrappers per kernel group (post.cu, trace.cu, temporal.cu, recon.cu)
-void launch_tiles_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);    // A1, A2
-void launch_pp_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);       // A3 - A5
-void launch_mask_b(const BatchArgs &A, bool any_adaptive, cudaStream_t st, DofHistory *timing);
-void launch_trace_b(const BatchArgs &A, int blocks, cudaStream_t st, DofHistory *timing);
-void launch_temporal_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);
-void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing);    // A10, A11
-void launch_composite_b(const BatchArgs &A, cudaStream_t st, DofHistory *timing); // A12
-void launch_reset_b(const BatchArgs &A, cudaStream_t st);
+// device: the batch descriptor, passed by value (a __grid_constant__ kernel parameter)
+// or, for captured graphs, as a pointer to device memory that a copy refreshes per step
+#ifdef __CUDACC__
+__device__ __forceinline__ const BatchArgs &batch_args(const BatchArgs &a) { return a; }
+__device__ __forceinline__ const BatchArgs &batch_args(const BatchArgs *a) { return *a; }
+#endif
+
+// host: launch wrappers per kernel group (post.cu, trace.cu, temporal.cu, recon.cu); `A`
+// gives the launch shapes, `as` is what the kernels receive (A itself, or a device
+// pointer to a copy of it)
+template <class AS> void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A1, A2
+template <class AS> void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);     // A3 - A5
+template <class AS>
+void launch_mask_b(const BatchArgs &A, const AS &as, bool any_adaptive, cudaStream_t st, DofHistory *timing);
+template <class AS> void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t st, DofHistory *timing);
+template <class AS> void launch_temporal_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);
+template <class AS> void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A10, A11
+template <class AS> void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A12
+template <class AS> void launch_reset_b(const BatchArgs &A, const AS &as, cudaStream_t st);

@@ -9,7 +9,9 @@ namespace {
 // A1: one 8x8 block per tile of half-resolution pixels.  Colour = mean of the 2x2
 // full-resolution block, depth = the nearest of the four (clamped to z_far), CoC
 // radius rho = clamp(c(z)/4) and normal of that sample; tile max of near and |rho|.
-__global__ void __launch_bounds__(64) k_downscale_tiles(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void __launch_bounds__(64) k_downscale_tiles(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int lb;
     const SessDesc &S = A.s[find_session(A, SH_TILE8, blockIdx.x, lb)];
     const DevCam &cam = S.cam;
@@ -55,7 +57,9 @@ __global__ void __launch_bounds__(64) k_downscale_tiles(const __grid_constant__ 
 }
 
 // A2: max over the (2K+1)^2 tile neighbourhood
-__global__ void k_tile_dilate(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_tile_dilate(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int tx, ty;
     const SessDesc &S = block_session(A, SH_TILEDIL, tx, ty);
     const DevParams &p = S.p;
@@ -73,7 +77,9 @@ __global__ void k_tile_dilate(const __grid_constant__ BatchArgs A) {
 }
 
 // A3: 9-tap bilateral prefilter, radius max(R/8, sqrt(2)/2), taps at angles k pi/4
-__global__ void k_prefilter(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_prefilter(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevParams &p = S.p;
@@ -130,7 +136,9 @@ __device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const De
     }
 }
 
-__global__ void __launch_bounds__(256) k_main_filter(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void __launch_bounds__(256) k_main_filter(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevParams &p = S.p;
@@ -156,7 +164,9 @@ __global__ void __launch_bounds__(256) k_main_filter(const __grid_constant__ Bat
 }
 
 // A5: per-channel 3x3 median (clamp-to-edge)
-__global__ void k_median_pp(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_median_pp(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
@@ -182,20 +192,28 @@ __global__ void k_median_pp(const __grid_constant__ BatchArgs A) {
 
 int post_init_tables() { return upload_filter_tables(); }
 
-void launch_tiles_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+template <class AS>
+void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
-    k_downscale_tiles<<<A.start[SH_TILE8][n], dim3(8, 8), 0, st>>>(A);
+    k_downscale_tiles<AS><<<A.start[SH_TILE8][n], dim3(8, 8), 0, st>>>(as);
     tmark(tm, DOF_K_DOWNSCALE, st);
-    k_tile_dilate<<<A.start[SH_TILEDIL][n], dim3(16, 16), 0, st>>>(A);
+    k_tile_dilate<AS><<<A.start[SH_TILEDIL][n], dim3(16, 16), 0, st>>>(as);
     tmark(tm, DOF_K_DILATE, st);
 }
 
-void launch_pp_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+template <class AS>
+void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
-    k_prefilter<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    k_prefilter<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_PREFILTER, st);
-    k_main_filter<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    k_main_filter<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_MAIN, st);
-    k_median_pp<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    k_median_pp<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_MEDIAN_PP, st);
 }
+
+// the two argument forms: by value (a kernel parameter) and from device memory (graphs)
+template void launch_tiles_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t, DofHistory *);
+template void launch_tiles_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, cudaStream_t, DofHistory *);
+template void launch_pp_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t, DofHistory *);
+template void launch_pp_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, cudaStream_t, DofHistory *);

@@ -10,7 +10,9 @@ namespace {
 
 // A10: lower median over the valid 3x3 neighbours: invalid slots are padded with
 // -inf / +inf so the median-of-9 network selects index (k-1)/2 of the k valid values
-__global__ void k_median_rt(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_median_rt(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
@@ -49,7 +51,9 @@ __global__ void k_median_rt(const __grid_constant__ BatchArgs A) {
 }
 
 // A11: mip level 0 = (rgb, h) * v and (c_t, 1) * v
-__global__ void k_mip0(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_mip0(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
@@ -67,8 +71,9 @@ __global__ void k_mip0(const __grid_constant__ BatchArgs A) {
 }
 
 // 2x2 box average (clamp-to-edge for odd sizes)
-template <int LEVEL>
-__global__ void k_mip_down(const __grid_constant__ BatchArgs A) {
+template <int LEVEL, class AS>
+__global__ void k_mip_down(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_MIP1 + LEVEL - 1, i, j);
     const int w = S.mip_w[LEVEL - 1], h = S.mip_h[LEVEL - 1], wn = S.mip_w[LEVEL], hn = S.mip_h[LEVEL];
@@ -148,7 +153,9 @@ __device__ __forceinline__ void recon_taps(const Mips &M, int i, int j, float R,
 
 // A11: reconstruction.  Blocks whose footprint (+-rmax + 2, at every level) lies
 // inside the image take taps without index clamping.
-__global__ void __launch_bounds__(256) k_recon(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void __launch_bounds__(256) k_recon(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevParams &p = S.p;
@@ -195,7 +202,9 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ BatchArgs
 // full-resolution pixels: their bilinear taps into the half-resolution layers (texel
 // centres at 0.5 (x + 0.5) - 0.5, i.e. i -/+ 1/4) all lie in the clamped 3x3
 // neighbourhood of (i, j), which is loaded once; weights 1/4 and 3/4 are exact.
-__global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevCam &cam = S.cam;
@@ -281,23 +290,31 @@ __global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ Ba
 
 int recon_init_tables() { return upload_filter_tables(); }
 
-void launch_recon_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+template <class AS>
+void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     dim3 b(32, 8);
-    k_median_rt<<<A.start[SH_HPX][n], b, 0, st>>>(A);
+    k_median_rt<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MEDIAN_RT, st);
-    k_mip0<<<A.start[SH_HPX][n], b, 0, st>>>(A);
-    k_mip_down<1><<<A.start[SH_MIP1][n], b, 0, st>>>(A);
-    k_mip_down<2><<<A.start[SH_MIP2][n], b, 0, st>>>(A);
-    k_mip_down<3><<<A.start[SH_MIP3][n], b, 0, st>>>(A);
+    k_mip0<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
+    k_mip_down<1, AS><<<A.start[SH_MIP1][n], b, 0, st>>>(as);
+    k_mip_down<2, AS><<<A.start[SH_MIP2][n], b, 0, st>>>(as);
+    k_mip_down<3, AS><<<A.start[SH_MIP3][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MIPS, st);
-    k_recon<<<A.start[SH_HPX][n], b, 0, st>>>(A);
+    k_recon<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_RECON, st);
 }
 
-void launch_composite_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+template <class AS>
+void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     dim3 b(32, 8);
-    k_composite<<<A.start[SH_HPX][n], b, 0, st>>>(A);
+    k_composite<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_COMPOSITE, st);
 }
+
+// the two argument forms: by value (a kernel parameter) and from device memory (graphs)
+template void launch_recon_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t, DofHistory *);
+template void launch_recon_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, cudaStream_t, DofHistory *);
+template void launch_composite_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t, DofHistory *);
+template void launch_composite_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, cudaStream_t, DofHistory *);

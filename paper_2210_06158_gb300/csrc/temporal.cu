@@ -67,7 +67,9 @@ __device__ __forceinline__ float fetch(const float4 *__restrict__ H0, const floa
 //     sum a_k v_k + sum a_k (x_k - mean')^2,
 // which equals mean-of-squares' - mean'^2 exactly but without its cancellation (the
 // ray count of Eq. 4 multiplies the variance by 1e5).
-__global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevCam &cam = S.cam;
@@ -161,7 +163,9 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ Batc
 }
 
 // 5x5 binomial blur of the variance, clamp-to-edge
-__global__ void k_var_blur(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_var_blur(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
@@ -183,16 +187,19 @@ __global__ void k_var_blur(const __grid_constant__ BatchArgs A) {
 
 }  // namespace
 
-void launch_temporal_b(const BatchArgs &A, cudaStream_t st, DofHistory *tm) {
+template <class AS>
+void launch_temporal_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
-    k_accumulate<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    k_accumulate<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_ACCUM, st);
-    k_var_blur<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    k_var_blur<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_VAR_BLUR, st);
 }
 
 // zero the per-frame counters of every session and the batch's ray cursor
-__global__ void k_reset(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_reset(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int s = threadIdx.x;
     if (s == 0) *A.cursor = 0u;
     if (s < A.ns) {
@@ -202,4 +209,11 @@ __global__ void k_reset(const __grid_constant__ BatchArgs A) {
     }
 }
 
-void launch_reset_b(const BatchArgs &A, cudaStream_t st) { k_reset<<<1, kMaxBatch, 0, st>>>(A); }
+template <class AS>
+void launch_reset_b(const BatchArgs &A, const AS &as, cudaStream_t st) { k_reset<AS><<<1, kMaxBatch, 0, st>>>(as); }
+
+// the two argument forms: by value (a kernel parameter) and from device memory (graphs)
+template void launch_temporal_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t, DofHistory *);
+template void launch_temporal_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, cudaStream_t, DofHistory *);
+template void launch_reset_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t);
+template void launch_reset_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, cudaStream_t);

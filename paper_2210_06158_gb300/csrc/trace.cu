@@ -342,7 +342,9 @@ __global__ void k_primary(DevCam cam, DevParams p, SceneDev sc, float4 *color, f
 // A6: edge measure for the adaptive ray count (Eq. 2, Eq. 3)
 // ---------------------------------------------------------------------------
 // 5x5 binomial blur of (z, n.xyz) packed as float4, clamp-to-edge
-__global__ void k_blur_zn(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_blur_zn(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
@@ -366,7 +368,9 @@ __global__ void k_blur_zn(const __grid_constant__ BatchArgs A) {
 }
 
 // 5x5 Sobel ([-1 -2 0 2 1] x [1 4 6 4 1] / 128) -> x_n (Eq. 2, 3) and x_f (Eq. 4)
-__global__ void k_edges(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void k_edges(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
@@ -406,7 +410,9 @@ __global__ void k_edges(const __grid_constant__ BatchArgs A) {
 // Per block (32 x 8 pixels, one warp per 8 x 4 tile) one atomic reserves room for the
 // block's masked pixels (queue) and their rays (ray list); inside the block the order
 // is tile by tile, Morton order inside a tile, so neighbouring rays stay neighbours.
-__global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
@@ -494,8 +500,9 @@ __device__ __noinline__ void lens_ray(const DevCam &cam, const DevParams &p, uin
 // enough of the warp is idle, so divergent rays do not hold the warp.  Writes the
 // closest hit of each ray: (sorted triangle index or -1, t).  kWide: every session of
 // the batch traverses its 4-wide tree, else every session its binary tree.
-template <bool kWide>
-__global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ BatchArgs A) {
+template <bool kWide, class AS>
+__global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     // inclusive prefix of the sessions' ray counts (the batch's concatenated ray list)
     __shared__ uint32_t pre[kMaxBatch];
@@ -612,7 +619,9 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ B
 // Shading and the per-pixel near/far split of the masked pixel queue[e]: its rays
 // are regenerated (bit-identical to the tracer's), shaded at their recorded hits and
 // reduced in sample order.
-__global__ void __launch_bounds__(128) k_shade(const __grid_constant__ BatchArgs A) {
+template <class AS>
+__global__ void __launch_bounds__(128) k_shade(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
     int lb;
     const SessDesc &S = A.s[find_session(A, SH_SHADE, blockIdx.x, lb)];
     const DevCam &cam = S.cam;
@@ -680,24 +689,32 @@ void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *
     k_primary<<<g, b, 0, st>>>(cam, p, sc, color, depth, normal, prim, status);
 }
 
-void launch_mask_b(const BatchArgs &A, bool any_adaptive, cudaStream_t st, DofHistory *tm) {
+template <class AS>
+void launch_mask_b(const BatchArgs &A, const AS &as, bool any_adaptive, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     if (any_adaptive) {
-        k_blur_zn<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
-        k_edges<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+        k_blur_zn<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+        k_edges<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     }
     tmark(tm, DOF_K_EDGES, st);
-    k_mask_compact<<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(A);
+    k_mask_compact<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_MASK, st);
 }
 
-void launch_trace_b(const BatchArgs &A, int blocks, cudaStream_t st, DofHistory *tm) {
+template <class AS>
+void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t st, DofHistory *tm) {
     // the 4-wide kernel when every session of the batch has its 4-wide tree in use
     bool wide = A.ns > 0;
     for (int i = 0; i < A.ns; i++) wide = wide && A.s[i].sc.nodes4 != nullptr;
-    if (wide) k_trace_rays<true><<<blocks, 128, 0, st>>>(A);
-    else k_trace_rays<false><<<blocks, 128, 0, st>>>(A);
+    if (wide) k_trace_rays<true, AS><<<blocks, 128, 0, st>>>(as);
+    else k_trace_rays<false, AS><<<blocks, 128, 0, st>>>(as);
     tmark(tm, DOF_K_TRACE, st);
-    k_shade<<<A.start[SH_SHADE][A.ns], 128, 0, st>>>(A);
+    k_shade<AS><<<A.start[SH_SHADE][A.ns], 128, 0, st>>>(as);
     tmark(tm, DOF_K_SHADE, st);
 }
+
+// the two argument forms: by value (a kernel parameter) and from device memory (graphs)
+template void launch_mask_b<BatchArgs>(const BatchArgs &, const BatchArgs &, bool, cudaStream_t, DofHistory *);
+template void launch_mask_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, bool, cudaStream_t, DofHistory *);
+template void launch_trace_b<BatchArgs>(const BatchArgs &, const BatchArgs &, int, cudaStream_t, DofHistory *);
+template void launch_trace_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, int, cudaStream_t, DofHistory *);

@@ -111,6 +111,9 @@ _SIGS = {
                             C.POINTER(DofParams), C.c_void_p, C.c_void_p, C.c_void_p]),
     "dof_frame_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofFrameStats)]),
     "dof_batch_frame": (C.c_int, [C.c_void_p, C.POINTER(DofFrameReq), C.c_uint32, C.c_void_p]),
+    "dof_graph_create": (C.c_int, [C.c_void_p, C.POINTER(DofFrameReq), C.c_uint32, C.POINTER(C.c_void_p)]),
+    "dof_graph_launch": (C.c_int, [C.c_void_p, C.POINTER(DofFrameReq), C.c_uint32, C.c_void_p]),
+    "dof_graph_destroy": (None, [C.c_void_p]),
     "dof_debug_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
     "dof_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
     "dof_debug_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
@@ -381,11 +384,7 @@ def coc_tiles_noalloc(depth, cam, params, out=None, stream=None):
     return out
 
 
-def batch_frame(ctx: Context, items, stream=None):
-    """Frames of several sessions in one launch per pass.  items: list of dicts with
-    keys scene (Scene), gbuf (dict of device tensors), cam (synth.Camera or a
-    DofCamera), params (dict or DofParams), hist (History), out (tensor, optional).
-    Returns the output tensors."""
+def _requests(items):
     import torch
     n = len(items)
     reqs = (DofFrameReq * max(1, n))()
@@ -408,5 +407,42 @@ def batch_frame(ctx: Context, items, stream=None):
         reqs[k].hist = it["hist"].ptr
         reqs[k].out = out.data_ptr()
         outs.append(out)
-    _check(lib().dof_batch_frame(ctx.ptr, reqs, n, _stream_ptr(stream)))
+    return reqs, keep, outs
+
+
+def batch_frame(ctx: Context, items, stream=None):
+    """Frames of several sessions in one launch per pass.  items: list of dicts with
+    keys scene (Scene), gbuf (dict of device tensors), cam (synth.Camera or a
+    DofCamera), params (dict or DofParams), hist (History), out (tensor, optional).
+    Returns the output tensors."""
+    reqs, keep, outs = _requests(items)
+    _check(lib().dof_batch_frame(ctx.ptr, reqs, len(items), _stream_ptr(stream)))
     return outs
+
+
+class Graph:
+    """A captured step of batch_frame over fixed histories (CUDA graph).  Create it from
+    the items of one step; launch(items) runs a step with new cameras, parameters,
+    G-buffers or outputs (same sessions and launch shapes)."""
+
+    def __init__(self, ctx: Context, items):
+        self.ctx = ctx
+        reqs, keep, _ = _requests(items)
+        self.ptr = C.c_void_p()
+        _check(lib().dof_graph_create(ctx.ptr, reqs, len(items), C.byref(self.ptr)))
+
+    def launch(self, items, stream=None):
+        reqs, keep, outs = _requests(items)
+        _check(lib().dof_graph_launch(self.ptr, reqs, len(items), _stream_ptr(stream)))
+        return outs
+
+    def close(self):
+        if self.ptr:
+            lib().dof_graph_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -359,6 +359,49 @@ def test_batch_equals_alone():
                                    hist=s["mixed"])] * 2)
 
 
+def test_graph_equals_batch():
+    """A captured step (CUDA graph) replayed with new cameras and G-buffers gives, frame
+    after frame, exactly what dof_batch_frame gives; launches that need other histories
+    or launch shapes are refused."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    dev = torch.device("cuda", 0)
+    specs = [("c1", 256, 144, {}), ("c2", 322, 182, {}), ("c1", 130, 74, dict(ray_mode=1, m=4))]
+    ctx = dof.Context(0)
+    sess = []
+    nf = 3
+    for k, (name, W, H, over) in enumerate(specs):
+        w = make_workload(name, W=W, H=H, n_frames=nf, session=k)
+        if w.n_frames < nf:
+            w.poses = [w.poses[0]] * nf
+        prm = dict(w.params, **over)
+        osc = oracle.Scene(w.scene)
+        gbs = []
+        for f in range(nf):
+            gb = oracle.gbuffer_f32(oracle.gbuffer(osc, w.camera(f), prm, W, H))
+            gbs.append({kk: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for kk, v in gb.items()})
+        sc = dof.Scene(ctx, w.scene)
+        mr = oracle.max_rays(prm)
+        sess.append(dict(w=w, prm=prm, gbs=gbs, sc=sc, hb=dof.History(ctx, W, H, mr), hg=dof.History(ctx, W, H, mr)))
+
+    def items(f, key):
+        return [dict(scene=s["sc"], gbuf=s["gbs"][f], cam=s["w"].camera(f), params=s["prm"], hist=s[key]) for s in sess]
+
+    graph = dof.Graph(ctx, items(0, "hg"))
+    for f in range(nf):
+        a = [t.clone() for t in dof.batch_frame(ctx, items(f, "hb"))]
+        b = graph.launch(items(f, "hg"))
+        torch.cuda.synchronize()
+        for k in range(len(sess)):
+            assert torch.equal(a[k], b[k]), (f, k)
+    assert sess[0]["hg"].stats().device_status == 0
+    with pytest.raises(dof.DofError):
+        graph.launch(items(0, "hb"))                    # not the captured histories
+    with pytest.raises(dof.DofError):
+        graph.launch(items(0, "hg")[:2])                # fewer sessions
+    graph.close()
+
+
 @pytest.mark.parametrize("name,W,H,nf", [("c3", 384, 216, 2), ("c2", 322, 182, 3)])
 def test_fp16_storage_error_vs_oracle(name, W, H, nf):
     """FP16 storage of the colour image buffers (FP32 arithmetic, FP32 depth, CoC and
