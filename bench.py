@@ -569,6 +569,71 @@ def run_batch(args):
     return line
 
 
+def run_budget(args):
+    """Adaptive ray count (Eq. 4) on the 1080p workload with the ray cap m swept over
+    1, 10, 30, 50 (the paper varies m the same way): rays, tracer and frame time per m
+    and the least-squares slope of frame time over m."""
+    import numpy as np
+    import torch
+    from paper_2210_06158_gb300 import _build, dof
+    from synth import make_workload
+    _build.build()
+    dev = torch.device("cuda", 0)
+    w = make_workload("c2")
+    ctx = dof.Context(0)
+    scene = dof.Scene(ctx, w.scene)
+    gbs = []
+    for k in range(CYCLE):
+        g = dof.gbuffer(ctx, scene, w.camera(k % w.n_frames), w.params, w.W, w.H)
+        del g["prim"]
+        gbs.append(g)
+    out = torch.empty((w.H, w.W, 4), dtype=torch.float32, device=dev)
+    rows = []
+    clk_all = None
+    for m in (1, 10, 30, 50):
+        prm = dict(w.params, ray_mode=1, m=m)
+        ps = dof.params_struct(prm)
+        cams = [dof.camera_struct(w.camera(s % CYCLE % w.n_frames)) for s in range(args.warmup + args.steps)]
+        h = dof.History(ctx, w.W, w.H, max_rays=m)
+        ht = dof.History(ctx, w.W, w.H, max_rays=m, timing=True)
+        for s in range(args.warmup):
+            dof.frame(ctx, scene, gbs[s % CYCLE], None, None, h, out, cam_struct=cams[s], params_s=ps)
+            dof.frame(ctx, scene, gbs[s % CYCLE], None, None, ht, out, cam_struct=cams[s], params_s=ps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record()
+            for s in range(args.warmup, args.warmup + args.steps):
+                dof.frame(ctx, scene, gbs[s % CYCLE], None, None, h, out, cam_struct=cams[s], params_s=ps)
+            e1.record()
+            torch.cuda.synchronize()
+        clk_all = clk.summary()
+        ms = e0.elapsed_time(e1) / args.steps
+        ht.kernel_times()
+        rays = 0
+        for s in range(args.warmup, args.warmup + args.steps):
+            dof.frame(ctx, scene, gbs[s % CYCLE], None, None, ht, out, cam_struct=cams[s], params_s=ps)
+            rays += ht.stats().rays
+        km, n = ht.kernel_times()
+        rows.append(dict(m=m, frame_ms=round(ms, 4), trace_ms=round(km["k_trace_rays"] / n, 4),
+                         shade_ms=round(km["k_shade"] / n, 4), rays_per_frame=int(rays / args.steps),
+                         rays_per_masked_pixel=round(rays / args.steps / max(1, ht.stats().masked_pixels), 3),
+                         status=int(ht.stats().device_status)))
+        del h, ht
+    mm = np.array([r["m"] for r in rows], float)
+    fm = np.array([r["frame_ms"] for r in rows], float)
+    slope = float(np.polyfit(mm, fm, 1)[0])
+    r10 = next(r for r in rows if r["m"] == 10)
+    return dict(metric=METRIC, value=round(1e3 / r10["frame_ms"], 2), unit="frames/s", n_gpus=1, steps=args.steps,
+                warmup=args.warmup, ms_per_step=r10["frame_ms"], higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload="budget: the 1080p lawn workload in adaptive mode (Eq. 4), ray cap m in "
+                                     "{1, 10, 30, 50}; value = frames/s at m = 10",
+                            l2=f"inputs larger than L2: {CYCLE} distinct G-buffers cycled"),
+                budget=rows, slope_ms_per_m=round(slope, 5), clocks=clk_all,
+                paper_context="0.04-0.07 ms per unit m for the ray-trace pass on an RTX 2080 Ti (Table 2)")
+
+
 def run_serve(args):
     import numpy as np
     from paper_2210_06158_gb300 import _build
@@ -611,7 +676,7 @@ def main():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "batch", "serve"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "batch", "serve", "budget"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", default=None,
                     help="WxH: the workload's scene, lens and camera path at another resolution (profiler captures)")
@@ -624,7 +689,8 @@ def main():
         if rank != 0:
             return 0
         from synth import make_workload
-        w = make_workload(args.config)
+        # the batched, served and budget modes run the 1080p workload's frames
+        w = make_workload(args.config if args.config in ("c1", "c2", "c3") else "c2")
         fps, desc, threads, times, frac = oracle_sample(w, steps=args.warmup + args.steps if args.steps <= 16 else None)
         timed = times[min(len(times) - 1, args.warmup):] or times
         ms = statistics.median(timed) / frac * 1e3
@@ -639,9 +705,9 @@ def main():
         print(json.dumps(line), flush=True)
         return 0
 
-    if args.config in ("batch", "serve"):
+    if args.config in ("batch", "serve", "budget"):
         if rank == 0:
-            line = run_batch(args) if args.config == "batch" else run_serve(args)
+            line = {"batch": run_batch, "serve": run_serve, "budget": run_budget}[args.config](args)
             print(json.dumps(line), flush=True)
         return 0
     if world > 1:

@@ -95,7 +95,8 @@ class OrFrame(C.Structure):
                [("nrays", _pi), ("ray_prim", _pi), ("ray_c", _pd)] + \
                [(n, _pd) for n in ("rt", "crt", "ct", "var", "rt_med", "recon", "out",
                                    "hist_in", "hist_out", "var_in", "var_out")] + \
-               [("has_history", C.c_int32), ("max_rays", C.c_int32), ("nrays_force", _pi)]
+               [("has_history", C.c_int32), ("max_rays", C.c_int32), ("nrays_force", _pi),
+                ("ray_hit_force", _pi)]
 
 
 def _declare(L):
@@ -296,10 +297,12 @@ def max_rays(prm) -> int:
 
 
 def frame(scene: Scene, cam, prm, W, H, gb32: dict, hist: History | None = None,
-          keep_rays: bool = True, nrays_force=None) -> dict:
+          keep_rays: bool = True, nrays_force=None, hit_force=None) -> dict:
     """Run one frame; returns every intermediate (numpy, float64) and updates `hist`.
     nrays_force (tests): int32 (H/2, W/2), a ray count to take instead of the mask's
-    where >= 0 (the count decision's ties, where either count is valid)."""
+    where >= 0 (the count decision's ties, where either count is valid).
+    hit_force (tests): int32 (H/2, W/2, max_rays), a triangle id (-1 = miss) to take as
+    the ray's hit where >= -1 (near ties, where either hit is valid)."""
     W2, H2 = W // 2, H // 2
     N = W2 * H2
     T = int(prm["tile"])
@@ -331,6 +334,12 @@ def frame(scene: Scene, cam, prm, W, H, gb32: dict, hist: History | None = None,
         force = np.ascontiguousarray(nrays_force, dtype=np.int32).reshape(-1)
         assert force.size == N
         fr.nrays_force = force.ctypes.data_as(_pi)
+    if hit_force is not None:
+        hforce = np.full((H2, W2, mr), -2, dtype=np.int32)
+        k = min(mr, hit_force.shape[2])
+        hforce[..., :k] = hit_force[..., :k]
+        hforce = np.ascontiguousarray(hforce).reshape(-1)
+        fr.ray_hit_force = hforce.ctypes.data_as(_pi)
     col = np.ascontiguousarray(gb32["color"], dtype=np.float32)
     dep = np.ascontiguousarray(gb32["depth"], dtype=np.float32)
     nrm = np.ascontiguousarray(gb32["normal"], dtype=np.float32)

@@ -17,7 +17,8 @@ void or_median3x3(int W2, int H2, const double *src, double *dst);
 void or_mask(const OrParams *p, int W2, int H2, const double *z_h, const double *n_h,
              const double *dil, const double *var_prev, double *xn, double *xf, int32_t *nrays);
 void or_trace(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int H,
-              const int32_t *nrays, double *rt, int32_t *ray_prim, double *ray_c, int max_rays);
+              const int32_t *nrays, double *rt, int32_t *ray_prim, double *ray_c, int max_rays,
+              const int32_t *hit_force);
 void or_accumulate(const OrCamera *c, const OrParams *p, int W, int H, const double *z_h,
                    const double *rt, const int32_t *nrays, const double *hist_in, int has_history,
                    double *hist_out, double *crt, double *ct, double *var);
@@ -49,7 +50,7 @@ int or_frame(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int 
             if (fr->nrays_force[q] >= 0) fr->nrays[q] = fr->nrays_force[q] < cap ? fr->nrays_force[q] : cap;
     }
     /* ray tracing (Section 3.2.2) */
-    or_trace(s, c, p, W, H, fr->nrays, fr->rt, fr->ray_prim, fr->ray_c, fr->max_rays);
+    or_trace(s, c, p, W, H, fr->nrays, fr->rt, fr->ray_prim, fr->ray_c, fr->max_rays, fr->ray_hit_force);
     /* accumulation, reprojection and variance (Section 3.2.3) */
     or_accumulate(c, p, W, H, fr->z_h, fr->rt, fr->nrays, fr->hist_in, fr->has_history,
                   fr->hist_out, fr->crt, fr->ct, fr->var);

@@ -69,7 +69,8 @@ void or_mask(const OrParams *p, int W2, int H2, const double *z_h, const double 
  *   Pfar = sum_hits (1-w) P / Fw, Fw = sum_hits (1-w)  (mean far hit position)
  * Layout of rt per pixel: n, h, An(3), Af(3), Bn, Bf, Pfar(3), Fw. */
 void or_trace(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int H,
-              const int32_t *nrays, double *rt, int32_t *ray_prim, double *ray_c, int max_rays) {
+              const int32_t *nrays, double *rt, int32_t *ray_prim, double *ray_c, int max_rays,
+              const int32_t *hit_force) {
     int W2 = W / 2, H2 = H / 2;
     double rmax = 0.5 * p->max_coc_px;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -85,7 +86,14 @@ void or_trace(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int
             for (int smp = 0; smp < n; smp++) {
                 double ro[3], rd[3], col[3], nrm[3], t = 0.0, z;
                 or_lens_ray(c, p, W, H, i, j, smp, ro, rd);
-                int hit = or_closest(s, ro, rd, &t);
+                int forced = hit_force && smp < max_rays ? hit_force[q * max_rays + smp] : -2;
+                int hit;
+                if (forced >= -1 && forced < or_scene_ntris(s)) {
+                    hit = forced;
+                    if (hit >= 0) t = or_plane_t(s, hit, ro, rd);
+                } else {
+                    hit = or_closest(s, ro, rd, &t);
+                }
                 if (hit >= 0) {
                     or_shade(s, p, hit, ro, rd, t, col, nrm);
                     z = fmin(t * dot3(rd, c->F), p->z_far);

@@ -115,6 +115,7 @@ void or_scene_destroy(OrScene *s) {
 }
 
 int or_scene_depth(const OrScene *s) { return s->depth; }
+int or_scene_ntris(const OrScene *s) { return s->n; }
 
 /* Moller-Trumbore ray/triangle test in double precision; edges count as inside.
  * Returns 1 and the distance t > 0 on a hit. */
@@ -227,6 +228,18 @@ static int graze(const OrScene *s, int prim, const double o[3], const double d[3
     }
     *inside = (n_in == 3) && t > 0.0;
     return near_edge;
+}
+
+double or_plane_t(const OrScene *s, int prim, const double o[3], const double d[3]) {
+    const double *v = s->v + 9 * (size_t)prim;
+    double e1[3], e2[3], n[3], tv[3];
+    sub3(v + 3, v, e1);
+    sub3(v + 6, v, e2);
+    cross3(e1, e2, n);
+    double dn = dot3(d, n);
+    if (dn == 0.0) return INFINITY;
+    sub3(v, o, tv);
+    return dot3(tv, n) / dn;
 }
 
 int or_near_tie(const OrScene *s, const double o[3], const double d[3], int prim_a, int prim_b,

@@ -56,6 +56,7 @@ OrScene *or_scene_create(const float *xyz, int n_verts, const uint32_t *idx,
                          const uint32_t *mat, int n_tris);
 void or_scene_destroy(OrScene *s);
 int or_scene_depth(const OrScene *s);
+int or_scene_ntris(const OrScene *s);
 /* closest hit through the oracle's BVH; returns prim or -1; *t set on hit */
 int or_closest(const OrScene *s, const double o[3], const double d[3], double *t);
 /* closest hit by testing every triangle (no acceleration structure) */
@@ -63,6 +64,8 @@ int or_closest_brute(const OrScene *s, const double o[3], const double d[3], dou
 /* FP-near-tie test of two disagreeing answers (prim or -1) for the ray (o, d) */
 int or_near_tie(const OrScene *s, const double o[3], const double d[3], int prim_a, int prim_b,
                 double rel_tol);
+/* distance along (o, d) to the plane of triangle `prim` (+inf if parallel) */
+double or_plane_t(const OrScene *s, int prim, const double o[3], const double d[3]);
 void or_shade(const OrScene *s, const OrParams *p, int prim, const double o[3],
               const double d[3], double t, double col[3], double nrm[3]);
 void or_albedo(uint32_t seed, int prim, double col[3]);
@@ -114,6 +117,12 @@ typedef struct {
      * result; a test passes the other side's count there so the rest of the frame can
      * be compared.  NULL: the mask's counts. */
     const int32_t *nrays_force;
+    /* optional (tests): per ray (W2*H2*max_rays), the triangle id to take as the ray's
+     * hit where >= -1 (-1 = a miss), at the distance to its plane.  Where a ray passes
+     * within rounding of a shared edge, or two triangles at equal depth, either answer
+     * is a valid closest hit; a test passes the other side's answer there.  NULL: the
+     * closest hit. */
+    const int32_t *ray_hit_force;
 } OrFrame;
 
 int or_frame(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int H,

@@ -52,11 +52,26 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
         bad_n = got["nrays"][~cties] != ref["nrays"][~cties]
         assert not bad_n.any(), (int(bad_n.sum()), int(cties.sum()))
         n_forced = int((got["nrays"] != ref["nrays"]).sum())
+        force = None
         if n_forced:
             force = np.where(got["nrays"] != ref["nrays"], got["nrays"], -1).astype(np.int32)
-            ohist = hist0
+            ohist = hist0.copy()
             ref = oracle.frame(osc, cam, params, w.W, w.H, gb, ohist, nrays_force=force)
             assert np.array_equal(got["nrays"], ref["nrays"])
+        # hit ids: equal except FP near ties (a ray within rounding of a shared edge or of
+        # two triangles at equal depth), where either hit is valid; the oracle then reruns
+        # the frame with the kernel's hits for those rays
+        n_rays, n_mis, n_bad, mism = classify_hits(osc, w, params, cam, got, ref)
+        assert n_bad == 0, f"{n_bad} hit-id mismatches are not FP near ties"
+        if n_mis:
+            mr_o = ref["ray_prim"].shape[2]
+            valid = np.arange(mr_o)[None, None, :] < ref["nrays"][..., None]
+            gp = got["ray_prim"][..., :mr_o]
+            hforce = np.where(valid & (gp != ref["ray_prim"]), gp, -2).astype(np.int32)
+            ohist = hist0.copy()
+            ref = oracle.frame(osc, cam, params, w.W, w.H, gb, ohist, nrays_force=force, hit_force=hforce)
+            valid_g = np.arange(gp.shape[2])[None, None, :] < ref["nrays"][..., None]
+            assert np.array_equal(np.where(valid_g, gp, 0), np.where(valid_g, ref["ray_prim"], 0))
         # ---- post-process: same FP32 inputs on both sides
         assert np.array_equal(got["z_h"], ref["z_h"].astype(np.float32))
         assert max_abs(got["pp_in"][..., :3], ref["pp_in"][..., :3]) < 1e-6
@@ -78,15 +93,12 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
         st = got["stats"]
         assert st.device_status == 0
         assert st.rays == int(got["nrays"].sum())
-        # ---- hit ids
-        n_rays, n_mis, n_bad, mism = classify_hits(osc, w, params, cam, got, ref)
-        assert n_bad == 0, f"{n_bad} hit-id mismatches are not FP near ties"
-        # ---- taint cone, carried through the history
-        seed = mism | ties
+        # ---- taint cone of the far-weight ties, carried through the history
+        seed = ties
         taint_h = dilate(dilate(taint_h, 2) | seed, rt_r)
         ok = ~taint_h
         # a pixel's ray sums depend on its own rays only
-        m = (ref["nrays"] > 0) & ~(mism | ties)
+        m = (ref["nrays"] > 0) & ~ties
         # h and the field colours absolute, the field CoC radii (up to rmax) relative
         e_rt = max_abs(got["rt"][..., 1:8][m], ref["rt"][..., 1:8][m]) if m.any() else 0.0
         e_rb = (max_abs(got["rt"][..., 8:10][m], ref["rt"][..., 8:10][m]) /
@@ -221,13 +233,16 @@ def test_frame_parity_4spp_c3_lens():
     _print(stats, "c3-384x216")
 
 
-def test_frame_parity_adaptive_ray_count():
-    """Eq. 4 adaptive mode: Sobel edge measure and the previous frame's variance."""
-    w = make_workload("c1", W=192, H=108)
-    w.poses = [w.poses[0]] * 3
-    prm = dict(w.params, ray_mode=1, m=6)
+@pytest.mark.parametrize("m,name,W,H,moving", [(6, "c1", 192, 108, False), (30, "c2", 256, 144, True)])
+def test_frame_parity_adaptive_ray_count(m, name, W, H, moving):
+    """Eq. 4 adaptive mode: Sobel edge measure and the previous frame's variance; a
+    static camera and a moving one, small and large ray caps m."""
+    w = make_workload(name, W=W, H=H, n_frames=3)
+    if not moving or w.n_frames < 3:
+        w.poses = [w.poses[0]] * 3
+    prm = dict(w.params, ray_mode=1, m=m)
     stats = run_sequence(w, 3, prm)
-    _print(stats, "c1-adaptive")
+    _print(stats, f"{name}-adaptive-m{m}")
 
 
 def test_edge_cases_tiny_empty_single():

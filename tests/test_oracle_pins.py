@@ -607,3 +607,30 @@ def test_forced_ray_counts_are_taken_and_neutral():
     other = np.ones(a["nrays"].shape, bool)
     other[j, i] = False
     assert np.array_equal(c["nrays"][other], a["nrays"][other])
+
+
+def test_forced_hits_are_taken():
+    """The test hook for near-tie hits: forcing the closest hits reproduces the frame
+    (the forced hit's distance is its plane's, equal to the hit distance up to
+    rounding); a forced miss makes that ray see the sky and changes only its pixel."""
+    import oracle
+    from synth import make_workload
+    w = make_workload("c1", W=64, H=36)
+    prm = dict(w.params)
+    osc = oracle.Scene(w.scene)
+    cam = w.camera(0)
+    gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, prm, w.W, w.H))
+    a = oracle.frame(osc, cam, prm, w.W, w.H, gb, oracle.History(w.W, w.H))
+    b = oracle.frame(osc, cam, prm, w.W, w.H, gb, oracle.History(w.W, w.H), hit_force=a["ray_prim"])
+    assert np.array_equal(a["ray_prim"], b["ray_prim"])
+    assert np.allclose(a["rt"], b["rt"], rtol=1e-10, atol=1e-10)
+    hits = np.argwhere((a["ray_prim"][..., 0] >= 0) & (a["nrays"] > 0))
+    j, i = hits[0]
+    force = np.full(a["ray_prim"].shape, -2, np.int32)
+    force[j, i, 0] = -1
+    c = oracle.frame(osc, cam, prm, w.W, w.H, gb, oracle.History(w.W, w.H), hit_force=force)
+    assert c["ray_prim"][j, i, 0] == -1
+    other = np.ones(a["nrays"].shape, bool)
+    other[j, i] = False
+    assert np.array_equal(c["rt"][other], a["rt"][other])
+    assert not np.array_equal(c["rt"][j, i], a["rt"][j, i])
