@@ -215,6 +215,9 @@ def run_ours(args, rank, world):
     else:
         w = make_workload(args.config, session=rank)
     prm = dict(w.params)
+    if args.taa:
+        w.jitter = True
+        prm["taa_alpha"] = 0.1
     spp = int(prm["spp"])
     ctx = dof.Context(local)
     stream = torch.cuda.current_stream()
@@ -244,7 +247,7 @@ def run_ours(args, rank, world):
 
     cams = [cam_for(s) for s in range(args.warmup + args.steps)]
     out = torch.empty((w.H, w.W, 4), dtype=torch.float32, device=dev)
-    hist = dof.History(ctx, w.W, w.H, max_rays=spp)
+    hist = dof.History(ctx, w.W, w.H, max_rays=spp, taa=args.taa)
 
     def step(s, h, g=None):
         gb = g if g is not None else gbs[s % CYCLE]
@@ -290,7 +293,7 @@ def run_ours(args, rank, world):
 
     # ---- the FP16-storage variant over the same steps (another session history)
     p16 = dof.params_struct(dict(prm, image_storage=1))
-    h16 = dof.History(ctx, w.W, w.H, max_rays=spp)
+    h16 = dof.History(ctx, w.W, w.H, max_rays=spp, taa=args.taa)
     for s in range(args.warmup):
         dof.frame(ctx, scene, gbs[s % CYCLE], None, None, h16, out, cam_struct=cams[s], params_s=p16)
     torch.cuda.synchronize()
@@ -306,7 +309,7 @@ def run_ours(args, rank, world):
     del h16
 
     # ---- instrumented pass: per-kernel device times over the same kind of steps
-    htime = dof.History(ctx, w.W, w.H, max_rays=spp, timing=True)
+    htime = dof.History(ctx, w.W, w.H, max_rays=spp, timing=True, taa=args.taa)
     for s in range(args.warmup):
         step(s, htime)
     htime.kernel_times()
@@ -338,7 +341,7 @@ def run_ours(args, rank, world):
         pin.append(dict(color=g["color"].cpu().pin_memory(), depth=g["depth"].cpu().pin_memory()))
     hout = torch.empty((w.H, w.W, 4), dtype=torch.float32).pin_memory()
     stage = dict(color=torch.empty_like(gbs[0]["color"]), depth=torch.empty_like(gbs[0]["depth"]))
-    he = dof.History(ctx, w.W, w.H, max_rays=spp)
+    he = dof.History(ctx, w.W, w.H, max_rays=spp, taa=args.taa)
     h2d = pin[0]["color"].numel() * 4 + pin[0]["depth"].numel() * 4
     d2h = hout.numel() * 4
 
@@ -422,7 +425,7 @@ def run_ours(args, rank, world):
                config=dict(workload=f"{w.name}: {w.W}x{w.H}, {info.n_tris} triangles (lawn + box field), "
                                     f"{w.intr['f_m'] * 1000:.0f} mm f/{w.intr['f_number']:g} focus "
                                     f"{w.intr['focus_m']:g} m, CoC radius <= {prm['max_coc_px']:g} px, {spp} spp, "
-                                    f"16-frame dolly",
+                                    f"16-frame dolly" + (", camera jitter + final TAA (blend 0.1)" if args.taa else ""),
                            resolution=[w.W, w.H], triangles=info.n_tris, spp=spp, bvh_depth=info.depth,
                            tracer=dict(tuned, tune_s=round(tune_s, 2)),
                            parallelism="replicas" if world > 1 else "single-gpu",
@@ -431,7 +434,7 @@ def run_ours(args, rank, world):
                roofline=roof, e2e=e2e, fp16_storage=fp16,
                # per frame: reset, 5 post-process, mask, trace, shade, 2 temporal, RT median, 4 mip,
                # recon, composite (+ 2 edge kernels in adaptive mode)
-               gpu_launches=(18 + (2 if int(prm["ray_mode"]) == 1 else 0)) * args.steps,
+               gpu_launches=(18 + (2 if int(prm["ray_mode"]) == 1 else 0) + (1 if args.taa else 0)) * args.steps,
                clocks=clocks, kernel_ms=kern,
                image_passes={"streaming": {"kernels": STREAMING, "ms": round(img_ms, 4),
                                            "gbs": round(img_bytes / (img_ms * 1e-3) / 1e9, 1),
@@ -678,6 +681,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "batch", "serve", "budget"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--taa", action="store_true",
+                    help="camera jitter (Halton 2, 3) and the final TAA pass with blend 0.1")
     ap.add_argument("--size", default=None,
                     help="WxH: the workload's scene, lens and camera path at another resolution (profiler captures)")
     args = ap.parse_args()

@@ -51,12 +51,18 @@ extern "C" {
 /* Thin-lens camera (Section 3.3 below Eq. 6: focal length f, aperture a = f/N, focus
  * distance d, sensor width w_s) and the pose of this and of the previous frame.  The
  * pose is an orthonormal basis: `fwd` the optical axis, `right`/`up` the image x / -y
- * axes.  The focal length in pixels is F = W v / w_s with v = f d / (d - f). */
+ * axes.  The focal length in pixels is F = W v / w_s with v = f d / (d - f).
+ * jitter: the frame's sub-pixel camera jitter against aliasing (Section 3.1.2), in
+ * full-resolution pixels, |.| <= 1: every pixel samples the sensor at its position plus
+ * the jitter (G-buffer producer and thin-lens rays alike), and reprojection into the
+ * previous frame subtracts prev_jitter.  Zero: no jitter. */
 typedef struct {
     float f_m, f_number, focus_m, sensor_w_m;
     float pos[3], right[3], up[3], fwd[3];
     float prev_pos[3], prev_right[3], prev_up[3], prev_fwd[3];
     uint32_t frame_index;          /* Philox counter word (lens samples differ per frame) */
+    float jitter[2];               /* this frame's sampling offset (x, y), full-res px */
+    float prev_jitter[2];          /* the previous frame's */
 } DofCamera;
 
 /* Method constants.  Defaults (dof_params_default) are the paper's values where it
@@ -93,7 +99,8 @@ typedef struct {
     float emit;             /* radiance scale of material 1 (emitters) */
     uint32_t image_storage; /* DOF_STORAGE_F32, or DOF_STORAGE_F16: colour image buffers of the
                                pass in FP16 (arithmetic stays FP32; depth, CoC and history FP32) */
-    uint32_t pad0;
+    float taa_alpha;        /* final TAA (Section 3.4) blend of the current frame, 0 < a <= 1;
+                               0 = no TAA (the history needs DOF_HIST_TAA otherwise) */
 } DofParams;
 
 #define DOF_STORAGE_F32 0
@@ -198,6 +205,7 @@ int dof_gbuffer(DofCtx *ctx, const DofScene *scene, const DofCamera *cam, const 
 
 #define DOF_HIST_RECORD_RAYS 1u   /* also keep each ray's hit triangle id (tests) */
 #define DOF_HIST_TIMING      2u   /* record a CUDA event after every kernel of a frame */
+#define DOF_HIST_TAA         4u   /* keep the final TAA's image history (3 x 16 B per pixel) */
 
 /* Session state for width x height frames: accumulated ray-traced layer (FP32),
  * blurred variance, and the per-frame work buffers of the pass.  max_rays (1..64)
@@ -280,7 +288,7 @@ int dof_frame_stats(DofHistory *hist, void *stream, DofFrameStats *out);
 enum {
     DOF_K_DOWNSCALE = 0, DOF_K_DILATE, DOF_K_PREFILTER, DOF_K_MAIN, DOF_K_MEDIAN_PP, DOF_K_EDGES,
     DOF_K_MASK, DOF_K_TRACE, DOF_K_SHADE, DOF_K_ACCUM, DOF_K_VAR_BLUR, DOF_K_MEDIAN_RT, DOF_K_MIPS,
-    DOF_K_RECON, DOF_K_COMPOSITE, DOF_K_COUNT
+    DOF_K_RECON, DOF_K_COMPOSITE, DOF_K_TAA, DOF_K_COUNT
 };
 /* For a history created with DOF_HIST_TIMING: synchronise `stream`, add the device
  * time (ms) each kernel took, summed over the frames recorded since the previous call
@@ -307,7 +315,7 @@ enum {
     DOF_BUF_PP_IN = 0, DOF_BUF_Z_H, DOF_BUF_TILES, DOF_BUF_TILES_DIL, DOF_BUF_PRE,
     DOF_BUF_MAIN, DOF_BUF_PP_MED, DOF_BUF_XN, DOF_BUF_XF, DOF_BUF_NRAYS, DOF_BUF_RAY_PRIM,
     DOF_BUF_RT, DOF_BUF_CRT, DOF_BUF_CT, DOF_BUF_VAR, DOF_BUF_VAR_BLUR, DOF_BUF_RT_MED,
-    DOF_BUF_RECON, DOF_BUF_HIST, DOF_BUF_COUNT
+    DOF_BUF_RECON, DOF_BUF_HIST, DOF_BUF_COMPOSITE, DOF_BUF_COUNT
 };
 int dof_debug_buffer(DofHistory *hist, int which, void **dev_ptr, size_t *bytes);
 /* Synchronous copy of intermediate buffer `which` into caller-owned host memory of

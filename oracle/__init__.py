@@ -23,7 +23,7 @@ _HERE = Path(__file__).resolve().parent
 _BUILD = _HERE / "_build"
 _LIB_PATH = _BUILD / "liboracle.so"
 _SOURCES = ["or_camera.c", "or_scene.c", "or_gbuffer.c", "or_post.c", "or_rays.c",
-            "or_temporal.c", "or_recon.c", "or_frame.c"]
+            "or_temporal.c", "or_recon.c", "or_taa.c", "or_frame.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -67,7 +67,8 @@ class OrCamera(C.Structure):
     _fields_ = [("f", C.c_double), ("N", C.c_double), ("d", C.c_double), ("ws", C.c_double),
                 ("O", _d3), ("R", _d3), ("U", _d3), ("F", _d3),
                 ("pO", _d3), ("pR", _d3), ("pU", _d3), ("pF", _d3),
-                ("frame", C.c_int64)]
+                ("frame", C.c_int64), ("jx", C.c_double), ("jy", C.c_double),
+                ("pjx", C.c_double), ("pjy", C.c_double)]
 
 
 class OrParams(C.Structure):
@@ -82,7 +83,8 @@ class OrParams(C.Structure):
                 ("tile", C.c_int32), ("pad0", C.c_int32),
                 ("seed", C.c_uint64), ("session", C.c_uint64),
                 ("light", _d3), ("k_a", C.c_double), ("k_d", C.c_double), ("sky", _d3),
-                ("emit", C.c_double), ("albedo_seed", C.c_uint32), ("pad1", C.c_int32)]
+                ("emit", C.c_double), ("albedo_seed", C.c_uint32), ("pad1", C.c_int32),
+                ("taa_alpha", C.c_double)]
 
 
 _pd = C.POINTER(C.c_double)
@@ -96,7 +98,8 @@ class OrFrame(C.Structure):
                [(n, _pd) for n in ("rt", "crt", "ct", "var", "rt_med", "recon", "out",
                                    "hist_in", "hist_out", "var_in", "var_out")] + \
                [("has_history", C.c_int32), ("max_rays", C.c_int32), ("nrays_force", _pi),
-                ("ray_hit_force", _pi)]
+                ("ray_hit_force", _pi), ("taa_in", _pd), ("taa_out", _pd), ("has_taa_history", C.c_int32),
+                ("pad_taa", C.c_int32)]
 
 
 def _declare(L):
@@ -139,6 +142,7 @@ def _declare(L):
     L.or_mask.argtypes = [C.POINTER(OrParams), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp]
     L.or_composite.argtypes = [C.POINTER(OrCamera), C.POINTER(OrParams), C.c_int, C.c_int,
                                vp, vp, vp, vp, vp, vp]
+    L.or_taa.argtypes = [C.POINTER(OrCamera), C.POINTER(OrParams), C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
 
 
 def _p(a):
@@ -159,6 +163,9 @@ def camera(cam) -> OrCamera:
                       ("pF", cam.prev_fwd)):
         setattr(c, name, _d3(*[float(np.float32(x)) for x in src]))
     c.frame = int(cam.frame_index)
+    jx, jy = getattr(cam, "jitter", (0.0, 0.0))
+    pjx, pjy = getattr(cam, "prev_jitter", (0.0, 0.0))
+    c.jx, c.jy, c.pjx, c.pjy = (float(np.float32(v)) for v in (jx, jy, pjx, pjy))
     return c
 
 
@@ -182,6 +189,7 @@ def params(p: dict) -> OrParams:
     o.sky = _d3(*[f(x) for x in p["sky"]])
     o.emit = f(p["emit"])
     o.albedo_seed = int(p["albedo_seed"]) & 0xFFFFFFFF
+    o.taa_alpha = f(p.get("taa_alpha", 0.0))
     return o
 
 
@@ -285,11 +293,27 @@ class History:
         self.hist = np.zeros(12 * n)
         self.var = np.zeros(n)
         self.valid = False
+        self.taa = np.zeros(W * H * 4)      # previous resolved (TAA) image
+        self.taa_valid = False
 
     def copy(self) -> "History":
         h = History.__new__(History)
         h.hist, h.var, h.valid = self.hist.copy(), self.var.copy(), self.valid
+        h.taa, h.taa_valid = self.taa.copy(), self.taa_valid
         return h
+
+
+def taa(cam, prm, W, H, depth, cur, hist=None):
+    """Final TAA of one image (Section 3.4): depth (H, W) float32, cur and hist (H, W, 4)
+    float64; hist None = no previous frame."""
+    d = np.ascontiguousarray(depth, dtype=np.float32)
+    c0 = np.ascontiguousarray(cur, dtype=np.float64)
+    h0 = np.ascontiguousarray(hist if hist is not None else np.zeros_like(c0), dtype=np.float64)
+    out = np.zeros((H, W, 4))
+    c, p = camera(cam), params(prm)
+    lib().or_taa(C.byref(c), C.byref(p), int(W), int(H), _p(d), _p(c0), _p(h0), 1 if hist is not None else 0,
+                 _p(out))
+    return out
 
 
 def max_rays(prm) -> int:
@@ -316,6 +340,9 @@ def frame(scene: Scene, cam, prm, W, H, gb32: dict, hist: History | None = None,
                rt=z(H2, W2, 14), crt=z(H2, W2, 4), ct=z(H2, W2), var=z(H2, W2),
                rt_med=z(H2, W2, 4), recon=z(H2, W2, 4), out=z(H, W, 4),
                hist_out=z(12 * N), var_out=z(N))
+    taa = float(prm.get("taa_alpha", 0.0)) > 0.0
+    if taa:
+        out["out_taa"] = z(H, W, 4)
     if keep_rays:
         out["ray_prim"] = np.full((H2, W2, mr), -2, dtype=np.int32)
         out["ray_c"] = z(H2, W2, mr)
@@ -330,6 +357,14 @@ def frame(scene: Scene, cam, prm, W, H, gb32: dict, hist: History | None = None,
     fr.var_in = hist.var.ctypes.data_as(_pd)
     fr.has_history = 1 if hist.valid else 0
     fr.max_rays = mr
+    if taa:
+        if hist.taa.size != W * H * 4:
+            hist.taa = np.zeros(W * H * 4)
+            hist.taa_valid = False
+        taa_in = np.ascontiguousarray(hist.taa)
+        fr.taa_in = taa_in.ctypes.data_as(_pd)
+        fr.taa_out = out["out_taa"].ctypes.data_as(_pd)
+        fr.has_taa_history = 1 if hist.taa_valid else 0
     if nrays_force is not None:
         force = np.ascontiguousarray(nrays_force, dtype=np.int32).reshape(-1)
         assert force.size == N
@@ -351,6 +386,9 @@ def frame(scene: Scene, cam, prm, W, H, gb32: dict, hist: History | None = None,
     hist.hist = out["hist_out"].copy()
     hist.var = out["var_out"].copy()
     hist.valid = True
+    if taa:
+        hist.taa = out["out_taa"].reshape(-1).copy()
+        hist.taa_valid = True
     out["hist"] = out["hist_out"].reshape(H2, W2, 12)
     out["var_blur"] = out["var_out"].reshape(H2, W2)
     return out

@@ -34,10 +34,12 @@ static double focal_px(const OrCamera *c, int W) {
 }
 
 /* Direction through the sensor point (x, y) (full-resolution pixel units, y down)
- * and the lens centre. */
+ * and the lens centre; the frame's camera jitter (jx, jy) shifts every sampling
+ * position by a sub-pixel offset (Section 3.1.2: the camera is jittered against
+ * aliasing). */
 void or_pixel_dir(const OrCamera *c, int W, int H, double x, double y, double dir[3]) {
     double F = focal_px(c, W);
-    double sx = (x - 0.5 * W) / F, sy = (y - 0.5 * H) / F;
+    double sx = (x + c->jx - 0.5 * W) / F, sy = (y + c->jy - 0.5 * H) / F;
     for (int k = 0; k < 3; k++) dir[k] = c->F[k] + sx * c->R[k] - sy * c->U[k];
     normalize3(dir);
 }

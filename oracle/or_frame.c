@@ -60,5 +60,8 @@ int or_frame(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int 
     or_recon(p, W2, H2, fr->rt_med, fr->ct, fr->var_out, fr->nrays, fr->recon);
     /* composite (Section 3.3) */
     or_composite(c, p, W, H, color4, depth, fr->pp_med, fr->recon, fr->nrays, fr->out);
+    /* final TAA (Section 3.4) */
+    if (p->taa_alpha > 0.0 && fr->taa_out)
+        or_taa(c, p, W, H, depth, fr->out, fr->taa_in, fr->has_taa_history && fr->taa_in, fr->taa_out);
     return 0;
 }

@@ -8,7 +8,8 @@ static double focal_px(const OrCamera *c, int W) {
 }
 
 /* Position of the world point X in the previous frame, in half-resolution pixel
- * coordinates (texel centres at integers).  0 when X is not in front of the
+ * coordinates (texel centres at integers; the previous frame's pixels sampled the
+ * sensor at their position plus its jitter).  0 when X is not in front of the
  * previous camera. */
 static int project_prev(const OrCamera *c, int W, int H, const double X[3], double *xh,
                         double *yh) {
@@ -17,8 +18,8 @@ static int project_prev(const OrCamera *c, int W, int H, const double X[3], doub
     double zc = dot3(rel, c->pF);
     if (!(zc > 0.0)) return 0;
     double F = focal_px(c, W);
-    double x = 0.5 * W + F * dot3(rel, c->pR) / zc;
-    double y = 0.5 * H - F * dot3(rel, c->pU) / zc;
+    double x = 0.5 * W + F * dot3(rel, c->pR) / zc - c->pjx;
+    double y = 0.5 * H - F * dot3(rel, c->pU) / zc - c->pjy;
     *xh = 0.5 * x - 0.5;
     *yh = 0.5 * y - 0.5;
     return fabs(*xh) < 1e7 && fabs(*yh) < 1e7;

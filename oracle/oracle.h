@@ -26,6 +26,8 @@ typedef struct {
     double O[3], R[3], U[3], F[3];        /* current lens centre and basis (right, up, forward) */
     double pO[3], pR[3], pU[3], pF[3];    /* previous frame's pose */
     int64_t frame;
+    double jx, jy;                        /* this frame's sub-pixel jitter (full-res px) */
+    double pjx, pjy;                      /* the previous frame's */
 } OrCamera;
 
 typedef struct {
@@ -47,6 +49,7 @@ typedef struct {
     double light[3], k_a, k_d, sky[3], emit;
     uint32_t albedo_seed;
     int32_t pad1;
+    double taa_alpha;                     /* final TAA blend of the current frame (0 = no TAA) */
 } OrParams;
 
 typedef struct OrScene OrScene;
@@ -123,10 +126,20 @@ typedef struct {
      * is a valid closest hit; a test passes the other side's answer there.  NULL: the
      * closest hit. */
     const int32_t *ray_hit_force;
+    /* final TAA (Section 3.4), when taa_alpha > 0: W*H*4 resolved image of the previous
+     * frame (history) and of this one */
+    const double *taa_in;
+    double *taa_out;
+    int32_t has_taa_history;
+    int32_t pad_taa;
 } OrFrame;
 
 int or_frame(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int H,
              const float *color4, const float *depth, const float *normal4, OrFrame *fr);
+
+/* Final TAA of the composited image (Section 3.4; Karis 2014) */
+void or_taa(const OrCamera *c, const OrParams *p, int W, int H, const float *depth, const double *cur,
+            const double *hist_in, int has_history, double *out);
 
 /* individual steps, exposed for the pins */
 void or_median9(const double v[9], int k, double *out);

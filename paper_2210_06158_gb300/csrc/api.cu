@@ -103,6 +103,12 @@ int make_cam(const DofCamera *c, uint32_t W, uint32_t H, DevCam &o) {
     o.frame = c->frame_index;
     o.moved = memcmp(c->pos, c->prev_pos, 12) || memcmp(c->right, c->prev_right, 12) ||
               memcmp(c->up, c->prev_up, 12) || memcmp(c->fwd, c->prev_fwd, 12);
+    for (int k = 0; k < 2; k++)
+        if (!(fabsf(c->jitter[k]) <= 1.f) || !(fabsf(c->prev_jitter[k]) <= 1.f))
+            return dof_set_error(DOF_ERR_INVALID_ARG, "camera: jitter outside [-1, 1] px");
+    o.jx = c->jitter[0]; o.jy = c->jitter[1];
+    o.pjx = c->prev_jitter[0]; o.pjy = c->prev_jitter[1];
+    o.exact = !o.moved && memcmp(c->jitter, c->prev_jitter, 8) == 0;
     return DOF_OK;
 }
 
@@ -144,6 +150,9 @@ int make_params(const DofParams *p, uint32_t W, uint32_t H, uint32_t max_rays, D
     uint32_t W2 = W / 2, H2 = H / 2;
     if (p->image_storage > 1) return dof_set_error(DOF_ERR_INVALID_ARG, "params: image_storage must be 0 or 1");
     o.f16 = p->image_storage == DOF_STORAGE_F16;
+    if (!(p->taa_alpha >= 0.f && p->taa_alpha <= 1.f))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "params: taa_alpha must be in [0, 1]");
+    o.taa_alpha = p->taa_alpha;
     o.tiles_w = (int)((W2 + 7) / 8);
     o.tiles_h = (int)((H2 + 7) / 8);
     o.dil_k = (int)ceil(0.5 * (double)p->max_coc_px / 8.0);
@@ -420,6 +429,10 @@ static void history_free(DofHistory *h) {
         dof_free(c, h->hist[k], 48 * N);
         dof_free(c, h->var_blur[k], 4 * N);
     }
+    size_t P = (size_t)h->W * h->H;
+    dof_free(c, h->comp, 16 * P);
+    dof_free(c, h->taa[0], 16 * P);
+    dof_free(c, h->taa[1], 16 * P);
     if (h->ev) {
         for (int k = 0; k < kTimingSlots * (DOF_K_COUNT + 1); k++)
             if (h->ev[k]) cudaEventDestroy(h->ev[k]);
@@ -469,6 +482,12 @@ extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, 
         A((void **)&h->hist[k], 48 * N);
         A((void **)&h->var_blur[k], 4 * N);
     }
+    if (flags & DOF_HIST_TAA) {
+        size_t P = (size_t)h->W * h->H;
+        A((void **)&h->comp, 16 * P);
+        A((void **)&h->taa[0], 16 * P);
+        A((void **)&h->taa[1], 16 * P);
+    }
     if (rc == DOF_OK) {
         // history starts empty; the remaining buffers are defined before use each frame
         for (int k = 0; k < 2 && rc == DOF_OK; k++) {
@@ -508,6 +527,7 @@ extern "C" void dof_history_destroy(DofHistory *h) {
 extern "C" int dof_history_reset(DofHistory *h) {
     if (!h) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_history_reset: null history");
     h->valid = 0;
+    h->taa_valid = 0;
     return DOF_OK;
 }
 
@@ -564,6 +584,15 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
     d.hist_out = h->hist[h->cur ^ 1];
     d.var_in = h->var_blur[h->cur];
     d.var_out = h->var_blur[h->cur ^ 1];
+    d.comp_out = d.out;
+    if (d.p.taa_alpha > 0.f) {
+        if (!h->comp) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: taa_alpha > 0 needs a history with DOF_HIST_TAA");
+        d.taa = 1;
+        d.taa_valid = h->taa_valid;
+        d.comp_out = h->comp;
+        d.taa_in = h->taa[h->taa_cur];
+        d.taa_out = h->taa[h->taa_cur ^ 1];
+    }
     return DOF_OK;
 }
 
@@ -650,6 +679,10 @@ static void finish_step(const DofFrameReq *reqs, uint32_t n) {
         h->cur ^= 1;
         h->valid = 1;
         h->frames++;
+        if (reqs[s].params->taa_alpha > 0.f) {
+            h->taa_cur ^= 1;
+            h->taa_valid = 1;
+        }
     }
 }
 
@@ -890,6 +923,7 @@ extern "C" int dof_debug_buffer(DofHistory *h, int which, void **ptr, size_t *by
         case DOF_BUF_RT_MED: *ptr = h->rt_med; *bytes = 16 * N; break;
         case DOF_BUF_RECON: *ptr = h->recon; *bytes = 16 * N; break;
         case DOF_BUF_HIST: *ptr = h->hist[last]; *bytes = 48 * N; break;
+        case DOF_BUF_COMPOSITE: *ptr = h->comp; *bytes = h->comp ? 16 * (size_t)h->W * h->H : 0; break;
         default: return dof_set_error(DOF_ERR_INVALID_ARG, "dof_debug_buffer: unknown buffer %d", which);
     }
     return DOF_OK;
@@ -964,6 +998,7 @@ extern "C" int dof_history_import(DofHistory *h, const void *buf, size_t bytes, 
                             "import variance");
     if (rc == DOF_OK) {
         h->valid = (int)hd.valid;
+        h->taa_valid = 0;   // the TAA image history is not part of a checkpoint
         h->frames = hd.frames;
     }
     return rc;

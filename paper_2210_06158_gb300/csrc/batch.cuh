@@ -33,6 +33,10 @@ struct SessDesc {
     const float *depth;
     const float4 *normal;
     float4 *out;
+    float4 *comp_out;              // composite target: out, or the history's image for the TAA
+    const float4 *taa_in;          // previous resolved image (TAA)
+    float4 *taa_out;
+    int taa, taa_valid;
     // work buffers of the session (history-owned)
     float4 *pp_in, *pre, *main_, *pp_med, *n_h, *zn, *crt, *rt_med, *recon, *rt;
     float *z_h, *xn, *xf, *ct, *var;

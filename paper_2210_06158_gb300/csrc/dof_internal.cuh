@@ -26,7 +26,9 @@ struct DevCam {
     float halfW, halfH;         // W / 2, H / 2
     int W, H, W2, H2;
     uint32_t frame;
-    int moved;
+    int moved;                  // the pose changed (jitter aside)
+    float jx, jy, pjx, pjy;     // sampling jitter of this and of the previous frame (full-res px)
+    int exact;                  // pose and jitter unchanged: reprojection is the identity
 };
 
 struct DevParams {
@@ -42,6 +44,7 @@ struct DevParams {
     float3 sky;
     int tiles_w, tiles_h, dil_k;
     int f16;                    // colour image buffers stored as FP16
+    float taa_alpha;            // final TAA blend (0 = off)
 };
 
 // ---------------------------------------------------------------------------
@@ -150,6 +153,9 @@ struct DofHistory {
     float4 *mip0[4];               // (rgb, h) * valid per level
     float2 *mip1[4];               // (c_t, 1) * valid per level
     int mip_w[4], mip_h[4];
+    // final TAA (DOF_HIST_TAA): composited image of the frame, resolved images (ping-pong)
+    float4 *comp, *taa[2];
+    int taa_cur, taa_valid;
     // persistent state (ping-pong)
     float4 *hist[2];               // 3 planes of N each
     float *var_blur[2];
@@ -234,8 +240,9 @@ __device__ __forceinline__ float4 f4fma(float s, float4 a, float4 acc) {
 __device__ __forceinline__ float coc_of(const DevCam &c, float z) { return c.cocK * (z - c.d) / z; }
 
 // direction through sensor point (x, y) (full-resolution px) and the lens centre
+// direction through the sensor point (x, y) + jitter and the lens centre
 __device__ __forceinline__ float3 pixel_dir(const DevCam &c, float x, float y) {
-    float sx = (x - c.halfW) * c.invF, sy = (y - c.halfH) * c.invF;
+    float sx = (x + c.jx - c.halfW) * c.invF, sy = (y + c.jy - c.halfH) * c.invF;
     return normalize(make_float3(c.F.x + sx * c.R.x - sy * c.U.x, c.F.y + sx * c.R.y - sy * c.U.y,
                                  c.F.z + sx * c.R.z - sy * c.U.z));
 }

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS
     const float4 *__restrict__ pp_med = S.pp_med;
     const float4 *__restrict__ recon = S.recon;
     const int32_t *__restrict__ nrays = S.nrays;
-    float4 *out = S.out;
+    float4 *out = S.comp_out;
     const int W2 = cam.W2, H2 = cam.H2;
     if (i >= W2 || j >= H2) return;
     const bool hs = p.f16;
@@ -286,6 +286,71 @@ __global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS
         }
 }
 
+
+// A13: final TAA (Section 3.4, after Karis 2014), per full-resolution pixel of the
+// sessions that ask for it: the surface the pixel shows (depth along its jittered ray)
+// projected into the previous frame (minus that frame's jitter) samples the previous
+// resolved image bilinearly (clamp to edge, also for points outside the previous image);
+// clamped per channel to the min / max of the current 3x3 neighbourhood;
+// out = h + taa_alpha (cur - h).  No previous frame or a point behind the previous
+// camera: out = cur.
+template <class AS>
+__global__ void __launch_bounds__(256) k_taa(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
+    int x, y;
+    const SessDesc &S = block_session(A, SH_FPX, x, y);
+    const DevCam &cam = S.cam;
+    const DevParams &p = S.p;
+    const int W = cam.W, H = cam.H;
+    if (!S.taa || x >= W || y >= H) return;
+    const float4 *__restrict__ cur = S.comp_out;
+    const size_t q = (size_t)y * W + x;
+    const float4 c = __ldg(&cur[q]);
+    float3 lo = make_float3(c.x, c.y, c.z), hi = lo;
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+        for (int dx = -1; dx <= 1; dx++) {
+            int xx = min(max(x + dx, 0), W - 1), yy = min(max(y + dy, 0), H - 1);
+            float4 n = __ldg(&cur[(size_t)yy * W + xx]);
+            lo = make_float3(fminf(lo.x, n.x), fminf(lo.y, n.y), fminf(lo.z, n.z));
+            hi = make_float3(fmaxf(hi.x, n.x), fmaxf(hi.y, n.y), fmaxf(hi.z, n.z));
+        }
+    float4 o = make_float4(c.x, c.y, c.z, 1.f);
+    if (S.taa_valid) {
+        float z = fminf(__ldg(&S.depth[q]), p.z_far);
+        float3 dir = pixel_dir(cam, x + 0.5f, y + 0.5f);
+        float3 rel = (cam.O + (z / dot(dir, cam.F)) * dir) - cam.pO;
+        float zc = dot(rel, cam.pF);
+        if (zc > 0.f) {
+            float iz = cam.Fpx / zc;
+            float u = cam.halfW + dot(rel, cam.pR) * iz - cam.pjx;
+            float v = cam.halfH - dot(rel, cam.pU) * iz - cam.pjy;
+            {
+                float tx = u - 0.5f, ty = v - 0.5f;
+                float xf = floorf(tx), yf = floorf(ty);
+                float fx = tx - xf, fy = ty - yf;
+                int x0 = (int)xf, y0 = (int)yf;
+                float3 hsum = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    int ddx = t & 1, ddy = t >> 1;
+                    int xi = min(max(x0 + ddx, 0), W - 1), yi = min(max(y0 + ddy, 0), H - 1);
+                    float w = (ddx ? fx : 1.f - fx) * (ddy ? fy : 1.f - fy);
+                    float4 hv = __ldg(&S.taa_in[(size_t)yi * W + xi]);
+                    hsum = hsum + w * make_float3(hv.x, hv.y, hv.z);
+                }
+                float hx = fminf(fmaxf(hsum.x, lo.x), hi.x), hy = fminf(fmaxf(hsum.y, lo.y), hi.y);
+                float hz = fminf(fmaxf(hsum.z, lo.z), hi.z);
+                o = make_float4(hx + p.taa_alpha * (c.x - hx), hy + p.taa_alpha * (c.y - hy),
+                                hz + p.taa_alpha * (c.z - hz), 1.f);
+            }
+        }
+    }
+    S.out[q] = o;
+    S.taa_out[q] = o;
+}
+
 }  // namespace
 
 int recon_init_tables() { return upload_filter_tables(); }
@@ -311,6 +376,10 @@ void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHi
     dim3 b(32, 8);
     k_composite<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_COMPOSITE, st);
+    bool any_taa = false;
+    for (int i = 0; i < n; i++) any_taa |= A.s[i].taa != 0;
+    if (any_taa) k_taa<AS><<<A.start[SH_FPX][n], b, 0, st>>>(as);
+    tmark(tm, DOF_K_TAA, st);
 }
 
 // the two argument forms: by value (a kernel parameter) and from device memory (graphs)

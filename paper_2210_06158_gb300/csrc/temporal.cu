@@ -7,13 +7,14 @@
 
 namespace {
 
-// rel = the point relative to the previous lens centre
+// rel = the point relative to the previous lens centre; the previous frame's pixels
+// sampled the sensor at their position plus its jitter
 __device__ __forceinline__ bool project_prev(const DevCam &c, float3 rel, float &xh, float &yh) {
     float zc = dot(rel, c.pF);
     if (!(zc > 0.f)) return false;
     float iz = c.Fpx / zc;
-    float x = c.halfW + dot(rel, c.pR) * iz;
-    float y = c.halfH - dot(rel, c.pU) * iz;
+    float x = c.halfW + dot(rel, c.pR) * iz - c.pjx;
+    float y = c.halfH - dot(rel, c.pU) * iz - c.pjy;
     xh = 0.5f * x - 0.5f;
     yh = 0.5f * y - 0.5f;
     return fabsf(xh) < 1e7f && fabsf(yh) < 1e7f;
@@ -127,8 +128,9 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AS a
     float Wn = 0.f, Wf = 0.f, xh, yh;
     if (has_hist) {
         const float4 *H0 = hin, *H1 = hin + N, *H2p = hin + 2 * N;
-        // a static camera maps the G-buffer surface exactly onto its own pixel
-        bool okn = cam.moved ? project_prev(cam, relN, xh, yh) : (xh = (float)i, yh = (float)j, true);
+        // an unchanged camera (pose and jitter) maps the G-buffer surface exactly onto its
+        // own pixel
+        bool okn = !cam.exact ? project_prev(cam, relN, xh, yh) : (xh = (float)i, yh = (float)j, true);
         if (okn) Wn = fetch<true>(H0, H1, H2p, W2, H2, xh, yh, nh, fdummy);
         if (project_prev(cam, Xf - cam.pO, xh, yh)) Wf = fetch<false>(H0, H1, H2p, W2, H2, xh, yh, ndummy, fh);
     }

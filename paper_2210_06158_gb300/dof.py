@@ -24,12 +24,13 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "BUDGET", -4: "CUDA", -5: "TIMEOUT",
           -6: "DEVICE_CHECK", -7: "MISMATCH"}
 DOF_HIST_RECORD_RAYS = 1
 DOF_HIST_TIMING = 2
+DOF_HIST_TAA = 4
 KERNELS = ["k_downscale_tiles", "k_tile_dilate", "k_prefilter", "k_main_filter", "k_median_pp", "k_edges",
            "k_mask_compact", "k_trace_rays", "k_shade", "k_accumulate", "k_var_blur", "k_median_rt", "k_mips", "k_recon",
-           "k_composite"]
+           "k_composite", "k_taa"]
 BUF = dict(PP_IN=0, Z_H=1, TILES=2, TILES_DIL=3, PRE=4, MAIN=5, PP_MED=6, XN=7, XF=8,
            NRAYS=9, RAY_PRIM=10, RT=11, CRT=12, CT=13, VAR=14, VAR_BLUR=15, RT_MED=16,
-           RECON=17, HIST=18)
+           RECON=17, HIST=18, COMPOSITE=19)
 
 
 class DofError(RuntimeError):
@@ -45,7 +46,7 @@ class DofCamera(C.Structure):
     _fields_ = [("f_m", C.c_float), ("f_number", C.c_float), ("focus_m", C.c_float),
                 ("sensor_w_m", C.c_float), ("pos", _f3), ("right", _f3), ("up", _f3), ("fwd", _f3),
                 ("prev_pos", _f3), ("prev_right", _f3), ("prev_up", _f3), ("prev_fwd", _f3),
-                ("frame_index", C.c_uint32)]
+                ("frame_index", C.c_uint32), ("jitter", C.c_float * 2), ("prev_jitter", C.c_float * 2)]
 
 
 class DofParams(C.Structure):
@@ -58,7 +59,7 @@ class DofParams(C.Structure):
                 ("z_far_m", C.c_float), ("tile", C.c_uint32), ("albedo_seed", C.c_uint32),
                 ("seed", C.c_uint64), ("session", C.c_uint64), ("light_dir", _f3), ("k_a", C.c_float),
                 ("k_d", C.c_float), ("sky", _f3), ("emit", C.c_float), ("image_storage", C.c_uint32),
-                ("pad0", C.c_uint32)]
+                ("taa_alpha", C.c_float)]
 
 
 class DofGBuffer(C.Structure):
@@ -167,6 +168,10 @@ def camera_struct(cam) -> DofCamera:
     for name in ("pos", "right", "up", "fwd", "prev_pos", "prev_right", "prev_up", "prev_fwd"):
         setattr(c, name, _f3(*[float(x) for x in np.asarray(getattr(cam, name), dtype=np.float32)]))
     c.frame_index = int(cam.frame_index)
+    jx, jy = getattr(cam, "jitter", (0.0, 0.0))
+    pjx, pjy = getattr(cam, "prev_jitter", (0.0, 0.0))
+    c.jitter[0], c.jitter[1] = float(jx), float(jy)
+    c.prev_jitter[0], c.prev_jitter[1] = float(pjx), float(pjy)
     return c
 
 
@@ -175,7 +180,7 @@ def params_struct(p: dict) -> DofParams:
     lib().dof_params_default(C.byref(o))
     for k in ("s", "var_w_mask", "depth_range_m", "alpha", "alpha_motion", "var_w_recon", "b_max", "h_edge",
               "lod_scale", "lod_max", "max_coc_px", "zof_ramp_px", "cover_ramp_px", "bright_lum",
-              "bright_ramp", "mask_near_hpx", "z_far_m", "k_a", "k_d", "emit"):
+              "bright_ramp", "mask_near_hpx", "z_far_m", "k_a", "k_d", "emit", "taa_alpha"):
         if k in p:
             setattr(o, k, float(p[k]))
     for k in ("m", "spp", "ray_mode", "tile", "seed", "session", "image_storage"):
@@ -267,11 +272,12 @@ class Scene:
 
 class History:
     def __init__(self, ctx: Context, width: int, height: int, max_rays: int = 1, record_rays: bool = False,
-                 timing: bool = False):
+                 timing: bool = False, taa: bool = False):
         self.ctx = ctx
         self.width, self.height, self.max_rays = width, height, max_rays
         self.ptr = C.c_void_p()
-        flags = (DOF_HIST_RECORD_RAYS if record_rays else 0) | (DOF_HIST_TIMING if timing else 0)
+        flags = (DOF_HIST_RECORD_RAYS if record_rays else 0) | (DOF_HIST_TIMING if timing else 0) | \
+            (DOF_HIST_TAA if taa else 0)
         _check(lib().dof_history_create(ctx.ptr, width, height, max_rays, flags, C.byref(self.ptr)))
 
     def reset(self):

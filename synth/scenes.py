@@ -200,6 +200,8 @@ class Camera:
     prev_up: np.ndarray
     prev_fwd: np.ndarray
     frame_index: int = 0
+    jitter: tuple = (0.0, 0.0)          # sub-pixel sampling offset of this frame (full-res px)
+    prev_jitter: tuple = (0.0, 0.0)     # the previous frame's
 
     @staticmethod
     def from_poses(intr: dict, pose: dict, prev: dict | None = None, frame_index: int = 0):
@@ -209,6 +211,23 @@ class Camera:
                       pos=pose["pos"], right=pose["right"], up=pose["up"], fwd=pose["fwd"],
                       prev_pos=prev["pos"], prev_right=prev["right"], prev_up=prev["up"],
                       prev_fwd=prev["fwd"], frame_index=frame_index)
+
+
+def halton(i: int, base: int) -> float:
+    """Radical inverse of i in `base` (the Halton sequence)."""
+    f, r = 1.0, 0.0
+    while i > 0:
+        f /= base
+        r += f * (i % base)
+        i //= base
+    return r
+
+
+def taa_jitter(k: int) -> tuple:
+    """Camera jitter of frame k for temporal anti-aliasing: the 8-point Halton (2, 3)
+    sequence, centred on the pixel (offsets in (-1/2, 1/2) full-resolution pixels)."""
+    i = k % 8 + 1
+    return (halton(i, 2) - 0.5, halton(i, 3) - 0.5)
 
 
 def dolly_path(seed, start, n_frames, step_z=0.05, sway_sigma=0.01, pitch_deg=2.0):
@@ -356,7 +375,7 @@ def default_params(**over) -> dict:
              alpha=0.95, alpha_motion=0.8, var_w_recon=2000.0, b_max=0.9, h_edge=0.3,
              lod_scale=0.05, lod_max=3.0, max_coc_px=16.0, zof_ramp_px=0.25,
              cover_ramp_px=1.0, bright_lum=4.0, bright_ramp=1.0, mask_near_hpx=0.5,
-             z_far_m=1.0e5, tile=8, seed=1, session=0,
+             z_far_m=1.0e5, tile=8, seed=1, session=0, taa_alpha=0.0,
              light_dir=(0.3, -1.0, 0.5), k_a=0.1, k_d=1.0, sky=(0.5, 0.6, 0.8),
              emit=8.0, albedo_seed=1)
     p.update(over)
@@ -386,7 +405,11 @@ class Workload:
 
     def camera(self, k: int) -> Camera:
         prev = self.poses[k - 1] if k > 0 else self.poses[k]
-        return Camera.from_poses(self.intr, self.poses[k], prev, frame_index=k)
+        cam = Camera.from_poses(self.intr, self.poses[k], prev, frame_index=k)
+        if getattr(self, "jitter", False):
+            cam.jitter = taa_jitter(k)
+            cam.prev_jitter = taa_jitter(k - 1) if k > 0 else cam.jitter
+        return cam
 
 
 def make_workload(name: str, W: int | None = None, H: int | None = None,

@@ -41,7 +41,8 @@ class GpuRunner:
         mr = max_rays or oracle.max_rays(self.params)
         self.ctx = ctx or dof.Context(0)
         self.scene = dof.Scene(self.ctx, workload.scene)
-        self.hist = dof.History(self.ctx, workload.W, workload.H, max_rays=mr, record_rays=record_rays)
+        self.taa = float(self.params.get("taa_alpha", 0.0)) > 0.0
+        self.hist = dof.History(self.ctx, workload.W, workload.H, max_rays=mr, record_rays=record_rays, taa=self.taa)
         self.max_rays = mr
         self.dev = torch.device("cuda", 0)
 
@@ -53,6 +54,8 @@ class GpuRunner:
         res = dict(out=out.cpu().numpy())
         if read:
             res.update(self.read_all())
+            if self.taa:
+                res["composite"] = self.hist.read("COMPOSITE", shape=(self.w.H, self.w.W, 4))
         res["stats"] = self.hist.stats()
         return res
 

@@ -124,8 +124,17 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
         e_var_prev = e_var
         # ---- final image (linear RGB)
         taint_f = full_res(taint_h, w.W, w.H)
-        e_out = max_abs(got["out"][..., :3][~taint_f], ref["out"][..., :3][~taint_f])
-        p = psnr(got["out"][..., :3], ref["out"][..., :3])
+        if "out_taa" in ref:
+            # composite before the final TAA, then the resolved image (its history carries
+            # the taint of earlier frames, dilated by the 3x3 clamp and the reprojection)
+            e_comp = max_abs(got["composite"][..., :3][~taint_f], ref["out"][..., :3][~taint_f])
+            assert e_comp <= tol_img, e_comp
+            taint_taa = taint_f if k == 0 else dilate(taint_taa | taint_f, 3)
+            e_out = max_abs(got["out"][..., :3][~taint_taa], ref["out_taa"][..., :3][~taint_taa])
+            p = psnr(got["out"][..., :3], ref["out_taa"][..., :3])
+        else:
+            e_out = max_abs(got["out"][..., :3][~taint_f], ref["out"][..., :3][~taint_f])
+            p = psnr(got["out"][..., :3], ref["out"][..., :3])
         assert e_out <= tol_img, e_out
         assert p >= 50.0, p
         s = dict(frame=k, rays=n_rays, mismatches=n_mis, forced=n_forced, tainted=float(taint_f.mean()), max_out=e_out, psnr=p,
@@ -217,6 +226,20 @@ def test_frame_parity_ragged_dolly_with_history():
     w = make_workload("c2", W=250, H=142, n_frames=4)
     stats = run_sequence(w, 4)
     _print(stats, "c2-250x142")
+
+
+@pytest.mark.parametrize("moving", [True, False])
+def test_frame_parity_jitter_and_taa(moving):
+    """Camera jitter (Section 3.1.2) and the final TAA (Section 3.4): jittered pixel rays
+    and G-buffer, reprojection minus the previous jitter, TAA history clamped to the
+    current neighbourhood; a moving dolly and a static pose with only the jitter moving."""
+    w = make_workload("c2", W=256, H=144, n_frames=4)
+    if not moving:
+        w.poses = [w.poses[0]] * 4
+    w.jitter = True
+    prm = dict(w.params, taa_alpha=0.1)
+    stats = run_sequence(w, 4, prm)
+    _print(stats, "c2-taa" + ("" if moving else "-static"))
 
 
 def test_frame_parity_static_accumulation():

@@ -634,3 +634,65 @@ def test_forced_hits_are_taken():
     other[j, i] = False
     assert np.array_equal(c["rt"][other], a["rt"][other])
     assert not np.array_equal(c["rt"][j, i], a["rt"][j, i])
+
+
+def _taa_cam(pos=(0.0, 1.0, 0.0), prev=None, jitter=(0.0, 0.0), prev_jitter=(0.0, 0.0)):
+    intr = dict(f_m=0.035, f_number=2.0, focus_m=20.0, sensor_w_m=0.036)
+    cam = Camera.from_poses(intr, camera_pose(pos, pitch_deg=0.0), camera_pose(prev or pos, pitch_deg=0.0))
+    cam.jitter, cam.prev_jitter = jitter, prev_jitter
+    return cam
+
+
+def _bilinear_clamped(img, u, v):
+    """img (H, W, C) sampled at texel coordinates (u, v) (centres at integers), clamp to edge."""
+    H, W = img.shape[:2]
+    x0, y0 = np.floor(u).astype(int), np.floor(v).astype(int)
+    fx, fy = u - x0, v - y0
+    out = np.zeros(u.shape + img.shape[2:])
+    for dy in (0, 1):
+        for dx in (0, 1):
+            xi, yi = np.clip(x0 + dx, 0, W - 1), np.clip(y0 + dy, 0, H - 1)
+            w = (fx if dx else 1 - fx) * (fy if dy else 1 - fy)
+            out += w[..., None] * img[yi, xi]
+    return out
+
+
+def _taa_expected(cur, hist_sampled, alpha):
+    lo = ndi.minimum_filter(cur[..., :3], size=(3, 3, 1), mode="nearest")
+    hi = ndi.maximum_filter(cur[..., :3], size=(3, 3, 1), mode="nearest")
+    hc = np.minimum(np.maximum(hist_sampled[..., :3], lo), hi)
+    return hc + alpha * (cur[..., :3] - hc)
+
+
+@pytest.mark.parametrize("case", ["static", "jitter", "pan"])
+def test_taa_matches_reprojection_closed_forms(case):
+    """Final TAA (Section 3.4, Karis 2014): history reprojected onto the newest frame,
+    clamped to the current 3x3 neighbourhood, blended with alpha.  On a fronto-parallel
+    wall at distance Z: a static camera reprojects every pixel to itself; jitter alone
+    shifts the history by (j - j_prev); a sideways move by dx shifts it by F dx / Z
+    (F the focal length in pixels) -- checked against numpy shifts with bilinear taps."""
+    W, H, Z, alpha = 48, 32, 7.0, 0.1
+    rng = np.random.default_rng(3)
+    cur = rng.uniform(0, 1, (H, W, 4))
+    hist = rng.uniform(0, 1, (H, W, 4))
+    depth = np.full((H, W), Z, np.float32)
+    F = W * (0.035 * 20.0 / (20.0 - 0.035)) / 0.036
+    ys, xs = np.mgrid[0:H, 0:W].astype(float)
+    if case == "static":
+        cam, su, sv = _taa_cam(), xs, ys
+    elif case == "jitter":
+        j, pj = (0.25, -0.125), (-0.375, 0.0625)
+        cam = _taa_cam(jitter=j, prev_jitter=pj)
+        su, sv = xs + j[0] - pj[0], ys + j[1] - pj[1]
+    else:
+        dx = 0.02
+        cam = _taa_cam(pos=(dx, 1.0, 0.0), prev=(0.0, 1.0, 0.0))
+        su, sv = xs + F * dx / Z, ys
+    prm = default_params(taa_alpha=alpha)
+    got = oracle.taa(cam, prm, W, H, depth, cur, hist)
+    want = _taa_expected(cur, _bilinear_clamped(hist, su, sv), alpha)
+    assert np.allclose(got[..., :3], want, atol=1e-9), np.abs(got[..., :3] - want).max()
+    assert np.all(got[..., 3] == 1.0)
+    # no previous frame: the current image
+    first = oracle.taa(cam, prm, W, H, depth, cur, None)
+    assert np.array_equal(first[..., :3], cur[..., :3])
