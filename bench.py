@@ -72,12 +72,13 @@ BYTES = {
     "k_recon": ("N", 44.0),
     "k_composite": ("P", 45.0),          # colour 16 + depth 4 read, 16 written, + hpx inputs / 4
                                          # (one thread per hpx writes its 2x2 fpx)
+    "k_taa": ("P", 68.0),                # composite 16 + depth 4 + history 16 read, out 16 + history 16 written
 }
 
 
 # HBM-bound streaming passes and the gather passes of a frame
 STREAMING = ["k_downscale_tiles", "k_median_pp", "k_mask_compact", "k_accumulate", "k_var_blur", "k_median_rt",
-             "k_mips", "k_composite"]
+             "k_mips", "k_composite", "k_taa"]
 GATHERS = ["k_prefilter", "k_main_filter", "k_recon"]
 
 
@@ -331,6 +332,10 @@ def run_ours(args, rank, world):
         visits += fs.node_visits
         tests += fs.tri_tests
     kavg = {k: v / nk for k, v in ktot.items()}
+    if not args.taa:
+        kavg["k_taa"] = 0.0             # no TAA launch: its timing slot only brackets nothing
+    if int(prm["ray_mode"]) != 1:
+        kavg["k_edges"] = 0.0
     n_samples = math.ceil(args.steps / 32)
     rays_per_frame = rays / n_samples
     masked_per_frame = masked / n_samples
