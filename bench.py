@@ -66,9 +66,10 @@ BYTES = {
     "k_trace_rays": ("R", 12.0),              # per ray: ray list 4 read, hit 8 written (BVH reads hit L2)
     "k_shade": ("M", 76.0),              # queue, count, first ray read, 4 x float4 written (+ hits, per ray)
     "k_accumulate": ("N", 192.0),        # rt 64 + z 4 + nrays 4 + history 48 read; history 48 + 24 written
-    "k_var_blur": ("N", 8.0),
-    "k_median_rt": ("N", 36.0),
-    "k_mips": ("N", 64.0),
+    "k_median_rt": ("N", 72.0),          # fused: variance blur (var 4 read, 4 written), RT median
+                                         # (crt 16 + nrays 4 read, 16 written), mip 0 (ct 4 read,
+                                         # 24 written)
+    "k_mips": ("N", 40.0),               # mip levels 1-3: level reads 24 (1 + 1/4 + 1/16), writes 24 / 3
     "k_recon": ("N", 44.0),
     "k_composite": ("P", 45.0),          # colour 16 + depth 4 read, 16 written, + hpx inputs / 4
                                          # (one thread per hpx writes its 2x2 fpx)
@@ -77,8 +78,8 @@ BYTES = {
 
 
 # HBM-bound streaming passes and the gather passes of a frame
-STREAMING = ["k_downscale_tiles", "k_median_pp", "k_mask_compact", "k_accumulate", "k_var_blur", "k_median_rt",
-             "k_mips", "k_composite", "k_taa"]
+STREAMING = ["k_downscale_tiles", "k_median_pp", "k_mask_compact", "k_accumulate", "k_median_rt", "k_mips",
+             "k_composite", "k_taa"]
 GATHERS = ["k_prefilter", "k_main_filter", "k_recon"]
 
 
@@ -336,6 +337,7 @@ def run_ours(args, rank, world):
         kavg["k_taa"] = 0.0             # no TAA launch: its timing slot only brackets nothing
     if int(prm["ray_mode"]) != 1:
         kavg["k_edges"] = 0.0
+    kavg["k_var_blur"] = 0.0             # fused into k_median_rt: its slot brackets nothing
     n_samples = math.ceil(args.steps / 32)
     rays_per_frame = rays / n_samples
     masked_per_frame = masked / n_samples

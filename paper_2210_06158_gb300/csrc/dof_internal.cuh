@@ -218,6 +218,12 @@ __device__ __forceinline__ float4 ld_img(const float4 *base, size_t i, bool h) {
     }
     return __ldg(base + i);
 }
+// the value st_img stores (FP16 storage rounds each channel to half)
+__device__ __forceinline__ float4 round_img(float4 v, bool h) {
+    if (!h) return v;
+    float2 a = __half22float2(__floats2half2_rn(v.x, v.y)), b = __half22float2(__floats2half2_rn(v.z, v.w));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
 __device__ __forceinline__ void st_img(float4 *base, size_t i, float4 v, bool h) {
     if (h) {
         __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);

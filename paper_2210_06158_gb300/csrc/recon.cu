@@ -8,66 +8,71 @@
 
 namespace {
 
-// A10: lower median over the valid 3x3 neighbours: invalid slots are padded with
-// -inf / +inf so the median-of-9 network selects index (k-1)/2 of the k valid values
+// A9 / A10 / A11, fused per half-resolution pixel: the 5x5 binomial blur of the
+// luminance variance (Section 3.2.3), the lower median of the ray-traced colour over the
+// valid 3x3 neighbours (invalid slots padded with -inf / +inf so the median-of-9 network
+// selects index (k-1)/2 of the k valid values), and mip level 0 of the reconstruction,
+// (rgb, h) * v and (c_t, 1) * v.
 template <class AS>
-__global__ void k_median_rt(const __grid_constant__ AS as_) {
+__global__ void k_resolve_rt(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
+    if (i >= W2 || j >= H2) return;
+    const size_t q = (size_t)j * W2 + i;
+    // variance blur
+    {
+        const float *__restrict__ v = S.var;
+        const float b[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
+        float acc = 0.f;
+#pragma unroll
+        for (int dy = -2; dy <= 2; dy++) {
+            int y = min(max(j + dy, 0), H2 - 1);
+            float row = 0.f;
+#pragma unroll
+            for (int dx = -2; dx <= 2; dx++) row += b[dx + 2] * __ldg(&v[(size_t)y * W2 + min(max(i + dx, 0), W2 - 1)]);
+            acc += b[dy + 2] * row;
+        }
+        S.var_out[q] = acc * (1.f / 256.f);
+    }
     const float4 *__restrict__ crt = S.crt;
     const int32_t *__restrict__ nrays = S.nrays;
-    float4 *dst = S.rt_med;
     const bool hs = S.p.f16;
-    if (i >= W2 || j >= H2) return;
-    size_t q = (size_t)j * W2 + i;
-    if (__ldg(&nrays[q]) <= 0) { st_img(dst, q, make_float4(0.f, 0.f, 0.f, 0.f), hs); return; }
-    float4 v[9];
-    bool ok[9];
-    int k = 0, n = 0;
+    float4 med = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool valid = __ldg(&nrays[q]) > 0;
+    if (valid) {
+        float4 v[9];
+        bool ok[9];
+        int k = 0, n = 0;
 #pragma unroll
-    for (int dy = -1; dy <= 1; dy++)
+        for (int dy = -1; dy <= 1; dy++)
 #pragma unroll
-        for (int dx = -1; dx <= 1; dx++) {
-            int x = i + dx, y = j + dy;
-            bool in = x >= 0 && y >= 0 && x < W2 && y < H2;
-            size_t qn = in ? (size_t)y * W2 + x : q;
-            ok[n] = in && __ldg(&nrays[qn]) > 0;
-            v[n] = ld_img(crt, qn, hs);
-            k += ok[n];
-            n++;
-        }
-    int lows = 4 - (k - 1) / 2;   // -inf pads; the rest of the invalid slots get +inf
+            for (int dx = -1; dx <= 1; dx++) {
+                int x = i + dx, y = j + dy;
+                bool in = x >= 0 && y >= 0 && x < W2 && y < H2;
+                size_t qn = in ? (size_t)y * W2 + x : q;
+                ok[n] = in && __ldg(&nrays[qn]) > 0;
+                v[n] = ld_img(crt, qn, hs);
+                k += ok[n];
+                n++;
+            }
+        int lows = 4 - (k - 1) / 2;   // -inf pads; the rest of the invalid slots get +inf
 #pragma unroll
-    for (int m = 0; m < 9; m++)
-        if (!ok[m]) {
-            float pad = lows > 0 ? -INFINITY : INFINITY;
-            lows--;
-            v[m] = make_float4(pad, pad, pad, pad);
-        }
-    float4 med = median9(v);
-    st_img(dst, q, make_float4(med.x, med.y, med.z, ld_img(crt, q, hs).w), hs);
-}
-
-// A11: mip level 0 = (rgb, h) * v and (c_t, 1) * v
-template <class AS>
-__global__ void k_mip0(const __grid_constant__ AS as_) {
-    const BatchArgs &A = batch_args(as_);
-    int i, j;
-    const SessDesc &S = block_session(A, SH_HPX, i, j);
-    const int W2 = S.cam.W2, H2 = S.cam.H2;
-    const float4 *__restrict__ med = S.rt_med;
-    const float *__restrict__ ct = S.ct;
-    const int32_t *__restrict__ nrays = S.nrays;
-    float4 *m0 = S.mip0[0];
-    float2 *m1 = S.mip1[0];
-    if (i >= W2 || j >= H2) return;
-    size_t q = (size_t)j * W2 + i;
-    const bool hs = S.p.f16;
-    float v = __ldg(&nrays[q]) > 0 ? 1.f : 0.f;
-    st_img(m0, q, f4scale(v, ld_img(med, q, hs)), hs);
-    m1[q] = make_float2(v * __ldg(&ct[q]), v);
+        for (int m = 0; m < 9; m++)
+            if (!ok[m]) {
+                float pad = lows > 0 ? -INFINITY : INFINITY;
+                lows--;
+                v[m] = make_float4(pad, pad, pad, pad);
+            }
+        float4 m9 = median9(v);
+        med = make_float4(m9.x, m9.y, m9.z, ld_img(crt, q, hs).w);
+    }
+    st_img(S.rt_med, q, med, hs);
+    // mip level 0 from the median as stored (FP16 storage rounds it)
+    const float vv = valid ? 1.f : 0.f;
+    st_img(S.mip0[0], q, f4scale(vv, round_img(med, hs)), hs);
+    S.mip1[0][q] = make_float2(vv * __ldg(&S.ct[q]), vv);
 }
 
 // 2x2 box average (clamp-to-edge for odd sizes)
@@ -359,9 +364,8 @@ template <class AS>
 void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     dim3 b(32, 8);
-    k_median_rt<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
+    k_resolve_rt<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MEDIAN_RT, st);
-    k_mip0<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     k_mip_down<1, AS><<<A.start[SH_MIP1][n], b, 0, st>>>(as);
     k_mip_down<2, AS><<<A.start[SH_MIP2][n], b, 0, st>>>(as);
     k_mip_down<3, AS><<<A.start[SH_MIP3][n], b, 0, st>>>(as);

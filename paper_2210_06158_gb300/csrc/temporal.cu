@@ -164,29 +164,6 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AS a
     }
 }
 
-// 5x5 binomial blur of the variance, clamp-to-edge
-template <class AS>
-__global__ void k_var_blur(const __grid_constant__ AS as_) {
-    const BatchArgs &A = batch_args(as_);
-    int i, j;
-    const SessDesc &S = block_session(A, SH_HPX, i, j);
-    const int W2 = S.cam.W2, H2 = S.cam.H2;
-    const float *__restrict__ v = S.var;
-    float *out = S.var_out;
-    if (i >= W2 || j >= H2) return;
-    const float b[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
-    float acc = 0.f;
-#pragma unroll
-    for (int dy = -2; dy <= 2; dy++) {
-        int y = min(max(j + dy, 0), H2 - 1);
-        float row = 0.f;
-#pragma unroll
-        for (int dx = -2; dx <= 2; dx++) row += b[dx + 2] * __ldg(&v[(size_t)y * W2 + min(max(i + dx, 0), W2 - 1)]);
-        acc += b[dy + 2] * row;
-    }
-    out[(size_t)j * W2 + i] = acc * (1.f / 256.f);
-}
-
 }  // namespace
 
 template <class AS>
@@ -194,7 +171,7 @@ void launch_temporal_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHis
     const int n = A.ns;
     k_accumulate<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_ACCUM, st);
-    k_var_blur<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+    // the variance blur runs fused with the RT median and mip level 0 (recon.cu)
     tmark(tm, DOF_K_VAR_BLUR, st);
 }
 
