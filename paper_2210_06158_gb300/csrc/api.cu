@@ -695,8 +695,9 @@ static int run_frames(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, cudaStre
     DofHistory *tm = reqs[0].hist;
     cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
     if (tm->ev && tm->ev_used < kTimingSlots) {
-        // a kernel that is not launched this frame gets an event right after its predecessor's
-        for (int k = 0; k <= DOF_K_COUNT; k++) cudaEventRecord(tm->ev[tm->ev_slot * (DOF_K_COUNT + 1) + k], st);
+        // the frame's start; every kernel slot is marked in launch order after it (a kernel
+        // that is not launched this frame is marked right after its predecessor)
+        cudaEventRecord(tm->ev[tm->ev_slot * (DOF_K_COUNT + 1)], st);
     } else {
         tm = nullptr;
     }
