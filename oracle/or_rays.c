@@ -66,7 +66,8 @@ void or_mask(const OrParams *p, int W2, int H2, const double *z_h, const double 
  *   h  = sum w / n                                  (hit ratio)
  *   An = sum w col / n,  Af = sum (1-w) col / n     (premultiplied field colours)
  *   Bn = sum w |rho| / n, Bf = sum (1-w) |rho| / n  (premultiplied field CoCs)
- *   Pfar = sum_hits (1-w) P / Fw, Fw = sum_hits (1-w)  (mean far hit position)
+ *   Pfar = sum (1-w) P / Fw, Fw = sum (1-w)  (mean far position: the hit point, or
+ *   for a ray that hits nothing its point at depth z_far)
  * Layout of rt per pixel: n, h, An(3), Af(3), Bn, Bf, Pfar(3), Fw. */
 void or_trace(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int H,
               const int32_t *nrays, double *rt, int32_t *ray_prim, double *ray_c, int max_rays,
@@ -113,10 +114,11 @@ void or_trace(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int
                 }
                 Bn += w * rho;
                 Bf += (1.0 - w) * rho;
-                if (hit >= 0) {
-                    for (int k = 0; k < 3; k++) Pf[k] += (1.0 - w) * (ro[k] + t * rd[k]);
-                    Fw += 1.0 - w;
-                }
+                /* far position: the hit, or for a ray that escapes, its point at depth z_far
+                 * (the sky is a finite depth, so its reprojection follows the ray) */
+                double tf = hit >= 0 ? t : p->z_far / dot3(rd, c->F);
+                for (int k = 0; k < 3; k++) Pf[k] += (1.0 - w) * (ro[k] + tf * rd[k]);
+                Fw += 1.0 - w;
             }
             o[0] = n;
             o[1] = Sw / n;

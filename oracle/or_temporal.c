@@ -76,6 +76,7 @@ void or_accumulate(const OrCamera *c, const OrParams *p, int W, int H, const dou
                    double *hist_out, double *crt, double *ct, double *var) {
     int W2 = W / 2, H2 = H / 2;
     int moved = camera_moved(c);
+    int unchanged = !moved && c->jx == c->pjx && c->jy == c->pjy;
     double alpha = moved ? p->alpha_motion : p->alpha;
     static const int near_ch[7] = {0, 1, 2, 6, 8, 10, 11};
     static const int far_ch[5] = {3, 4, 5, 7, 9};
@@ -120,7 +121,14 @@ void or_accumulate(const OrCamera *c, const OrParams *p, int W, int H, const dou
             double Hn[7] = {0}, Hf[5] = {0}, Wn = 0.0, Wf = 0.0, xh, yh;
             if (has_history) {
                 if (project_prev(c, W, H, Xn, &xh, &yh)) Wn = fetch(hist_in, W2, H2, xh, yh, near_ch, 7, Hn);
-                if (project_prev(c, W, H, Xf, &xh, &yh)) Wf = fetch(hist_in, W2, H2, xh, yh, far_ch, 5, Hf);
+                /* an unchanged camera (pose and jitter) maps every static point onto its own
+                 * pixel: the far field keeps its pixel (the mean far position would move it by
+                 * a fraction of a pixel every frame and smear the history) */
+                if (unchanged) {
+                    Wf = fetch(hist_in, W2, H2, (double)i, (double)j, far_ch, 5, Hf);
+                } else if (project_prev(c, W, H, Xf, &xh, &yh)) {
+                    Wf = fetch(hist_in, W2, H2, xh, yh, far_ch, 5, Hf);
+                }
             }
             double kn = 1.0 - alpha * Wn, kf = 1.0 - alpha * Wf;
             double An[3], Af[3];

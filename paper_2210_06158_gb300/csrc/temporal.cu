@@ -132,7 +132,10 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AS a
         // own pixel
         bool okn = !cam.exact ? project_prev(cam, relN, xh, yh) : (xh = (float)i, yh = (float)j, true);
         if (okn) Wn = fetch<true>(H0, H1, H2p, W2, H2, xh, yh, nh, fdummy);
-        if (project_prev(cam, Xf - cam.pO, xh, yh)) Wf = fetch<false>(H0, H1, H2p, W2, H2, xh, yh, ndummy, fh);
+        // the far field keeps its pixel under an unchanged camera, too (the mean far
+        // position would move it by a fraction of a pixel every frame)
+        bool okf = !cam.exact ? project_prev(cam, Xf - cam.pO, xh, yh) : (xh = (float)i, yh = (float)j, true);
+        if (okf) Wf = fetch<false>(H0, H1, H2p, W2, H2, xh, yh, ndummy, fh);
     }
     const float a = cam.moved ? p.alpha_motion : p.alpha;
     const float kn = 1.f - a * Wn, kf = 1.f - a * Wf;

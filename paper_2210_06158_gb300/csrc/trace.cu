@@ -668,10 +668,11 @@ __global__ void __launch_bounds__(128) k_shade(const __grid_constant__ AS as_) {
         Af = Af + (1.f - w) * col;
         Bn += w * rho;
         Bf += (1.f - w) * rho;
-        if (h.k >= 0) {
-            Pfar = Pfar + (1.f - w) * (L + h.t * dir);
-            Fw += 1.f - w;
-        }
+        // far position: the hit, or for a ray that escapes, its point at depth z_far
+        // (the sky is a finite depth, so its reprojection follows the ray's direction)
+        const float tf = h.k >= 0 ? h.t : p.z_far / dot(dir, cam.F);
+        Pfar = Pfar + (1.f - w) * (L + tf * dir);
+        Fw += 1.f - w;
     }
     float inv_n = 1.f / (float)n;
     float invF = Fw > 0.f ? 1.f / Fw : 0.f;
