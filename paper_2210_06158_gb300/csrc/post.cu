@@ -6,21 +6,21 @@
 
 namespace {
 
-// A1: one 8x8 block per tile of half-resolution pixels.  Colour = mean of the 2x2
-// full-resolution block, depth = the nearest of the four (clamped to z_far), CoC
-// radius rho = clamp(c(z)/4) and normal of that sample; tile max of near and |rho|.
+// A1: one thread per half-resolution pixel, blocks of 32x8 pixels = four 8x8 max-CoC
+// tiles.  Colour = mean of the 2x2 full-resolution block, depth = the nearest of the
+// four (clamped to z_far), CoC radius rho = clamp(c(z)/4) and normal of that sample;
+// tile max of near and |rho| (lanes of a tile row by shuffles, rows through shared
+// memory).
 template <class AS>
-__global__ void __launch_bounds__(64) k_downscale_tiles(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(256) k_downscale_tiles(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
-    int lb;
-    const SessDesc &S = A.s[find_session(A, SH_TILE8, blockIdx.x, lb)];
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevCam &cam = S.cam;
     const DevParams &p = S.p;
-    const int tx = lb % S.gx[SH_TILE8], ty = lb / S.gx[SH_TILE8];
     const float4 *__restrict__ color = S.color;
     const float *__restrict__ depth = S.depth;
     const float4 *__restrict__ normal = S.normal;
-    int i = tx * 8 + threadIdx.x, j = ty * 8 + threadIdx.y;
     float nm = 0.f, am = 0.f;
     if (i < cam.W2 && j < cam.H2) {
         size_t f0 = (size_t)(2 * j) * cam.W + 2 * i, f1 = f0 + cam.W;
@@ -45,15 +45,23 @@ __global__ void __launch_bounds__(64) k_downscale_tiles(const __grid_constant__ 
         nm = fmaxf(0.f, -rho);
         am = fabsf(rho);
     }
-    for (int o = 16; o > 0; o >>= 1) {
+    // max over the 8 lanes of each tile in this row
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
         nm = fmaxf(nm, __shfl_xor_sync(0xffffffffu, nm, o));
         am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
     }
-    __shared__ float2 red[2];
-    int t = threadIdx.y * 8 + threadIdx.x;
-    if ((t & 31) == 0) red[t >> 5] = make_float2(nm, am);
+    __shared__ float2 red[8][4];
+    const int lane = threadIdx.x, row = threadIdx.y;
+    if ((lane & 7) == 0) red[row][lane >> 3] = make_float2(nm, am);
     __syncthreads();
-    if (t == 0) S.tiles[ty * p.tiles_w + tx] = make_float2(fmaxf(red[0].x, red[1].x), fmaxf(red[0].y, red[1].y));
+    if (row == 0 && lane < 4) {
+        float2 m = red[0][lane];
+#pragma unroll
+        for (int r = 1; r < 8; r++) m = make_float2(fmaxf(m.x, red[r][lane].x), fmaxf(m.y, red[r][lane].y));
+        const int tx = (i - lane) / 8 + lane, ty = j / 8;
+        if (tx < p.tiles_w && ty < p.tiles_h) S.tiles[ty * p.tiles_w + tx] = m;
+    }
 }
 
 // A2: max over the (2K+1)^2 tile neighbourhood
@@ -195,7 +203,7 @@ int post_init_tables() { return upload_filter_tables(); }
 template <class AS>
 void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
-    k_downscale_tiles<AS><<<A.start[SH_TILE8][n], dim3(8, 8), 0, st>>>(as);
+    k_downscale_tiles<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_DOWNSCALE, st);
     k_tile_dilate<AS><<<A.start[SH_TILEDIL][n], dim3(16, 16), 0, st>>>(as);
     tmark(tm, DOF_K_DILATE, st);
