@@ -201,6 +201,29 @@ def oracle_sample(w, budget_s=15.0, steps=None):
 # our arm
 # ---------------------------------------------------------------------------
 
+def gbuffer_producers(dof, ctx, scene, w, prm, reps=10):
+    """Device time of the two G-buffer producers on the workload's first camera (outputs
+    preallocated, 3 warm-up calls each), and whether their outputs agree bit for bit."""
+    import torch
+    cam = w.camera(0)
+    outs, ms = {}, {}
+    for raster in (False, True):
+        o = dof.gbuffer(ctx, scene, cam, prm, w.W, w.H, raster=raster)
+        for _ in range(2):
+            dof.gbuffer(ctx, scene, cam, prm, w.W, w.H, out=o, raster=raster)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            dof.gbuffer(ctx, scene, cam, prm, w.W, w.H, out=o, raster=raster)
+        e1.record()
+        torch.cuda.synchronize()
+        ms["raster" if raster else "ray_cast"] = round(e0.elapsed_time(e1) / reps, 4)
+        outs[raster] = o
+    same = all(torch.equal(outs[False][k].view(torch.int32), outs[True][k].view(torch.int32))
+               for k in ("color", "depth", "normal", "prim"))
+    return dict(ms=ms, bitwise_equal=bool(same))
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -238,6 +261,7 @@ def run_ours(args, rank, world):
     ev1.record()
     torch.cuda.synchronize()
     gbuf_ms = ev0.elapsed_time(ev1) / CYCLE
+    gbuf_cmp = gbuffer_producers(dof, ctx, scene, w, prm)
     for g in gbs:
         del g["prim"]
     pstruct = dof.params_struct(prm)
@@ -452,7 +476,7 @@ def run_ours(args, rank, world):
                mrays_per_s=round(rays_per_frame / (kavg.get("k_trace_rays", 0) * 1e-3) / 1e6, 1)
                if kavg.get("k_trace_rays", 0) > 0 else None,
                rays_per_frame=int(rays_per_frame), mask_fraction=round(masked_per_frame / N, 4),
-               bvh_build_ms=round(bvh_ms, 2), gbuffer_ms=round(gbuf_ms, 3),
+               bvh_build_ms=round(bvh_ms, 2), gbuffer_ms=round(gbuf_ms, 3), gbuffer_producers=gbuf_cmp,
                device_status=int(st.device_status))
     return res, w
 

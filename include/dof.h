@@ -201,6 +201,17 @@ int dof_gbuffer(DofCtx *ctx, const DofScene *scene, const DofCamera *cam, const 
                 uint32_t width, uint32_t height, float *color, float *depth, float *normal,
                 int32_t *prim, void *stream);
 
+/* Same outputs as dof_gbuffer, bit for bit, produced object-order: every triangle is
+ * set up once (the three planes through the lens centre and its edges bound the pixel
+ * centres that can see it), the pixels of that conservative region run the same
+ * watertight ray/triangle test, and the closest hit per pixel is kept by a 64-bit
+ * atomic minimum of (distance bits, triangle id), then shaded.  Scratch (8 bytes per
+ * pixel plus 68 bytes per triangle) comes from a stream-ordered pool that the context
+ * keeps until it is destroyed; the call does not synchronise `stream`. */
+int dof_gbuffer_raster(DofCtx *ctx, const DofScene *scene, const DofCamera *cam, const DofParams *p,
+                       uint32_t width, uint32_t height, float *color, float *depth, float *normal,
+                       int32_t *prim, void *stream);
+
 /* ---- per-session history (Section 3.2.3) ------------------------------------- */
 
 #define DOF_HIST_RECORD_RAYS 1u   /* also keep each ray's hit triangle id (tests) */

@@ -12,8 +12,8 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 LIB_DIR = PKG / "_lib"
 LIB = LIB_DIR / "libdof.so"
-SOURCES = ["api.cu", "bvh.cu", "trace.cu", "post.cu", "temporal.cu", "recon.cu", "noalloc.cu"]
-HEADERS_EXTRA = ["batch.cuh"]
+SOURCES = ["api.cu", "bvh.cu", "trace.cu", "post.cu", "temporal.cu", "recon.cu", "noalloc.cu", "raster.cu"]
+HEADERS_EXTRA = ["batch.cuh", "geometry.cuh"]
 HEADERS = ["dof_internal.cuh", "filters.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

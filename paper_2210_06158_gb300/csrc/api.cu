@@ -222,6 +222,20 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
         delete c;
         return dof_set_error(DOF_ERR_CUDA, "dof_ctx_create: stream or events");
     }
+    {
+        // scratch of dof_gbuffer_raster: kept in the pool between calls
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {
+            cudaGetLastError();
+            c->pool = nullptr;
+        }
+    }
     if (post_init_tables() != 0 || recon_init_tables() != 0) {
         cudaFree(c->d_status);
         delete c;
@@ -273,6 +287,7 @@ void ctx_release(DofCtx *ctx) {
         cudaStreamDestroy(ctx->ray_stream);
         cudaEventDestroy(ctx->ev_fork);
         cudaEventDestroy(ctx->ev_join);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         cudaFree(ctx->d_status);
         delete ctx;
     }
@@ -310,6 +325,7 @@ extern "C" int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts,
     s->tris_bytes = sizeof(float4) * 3 * (size_t)n_tris;
     s->nodes_bytes = sizeof(BvhNode) * (size_t)s->n_nodes;
     rc = dof_alloc(ctx, s->tris_bytes, (void **)&s->tris, &s->bytes);
+    if (rc == DOF_OK) rc = dof_alloc(ctx, 4 * (size_t)n_tris, (void **)&s->prim_k, &s->bytes);
     if (rc == DOF_OK && s->n_nodes) rc = dof_alloc(ctx, s->nodes_bytes, (void **)&s->nodes, &s->bytes);
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMalloc(&d_xyz, sizeof(float) * 3 * (size_t)n_verts), "scene vertices");
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMalloc(&d_idx, sizeof(uint32_t) * 3 * (size_t)n_tris), "scene indices");
@@ -318,9 +334,14 @@ extern "C" int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts,
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_idx, tri_idx, sizeof(uint32_t) * 3 * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
     if (rc == DOF_OK && tri_mat) rc = dof_cuda_check(cudaMemcpyAsync(d_mat, tri_mat, sizeof(uint32_t) * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
     if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, ctx->bvh_builder, ctx->ploc_radius, st);
+    if (rc == DOF_OK) {
+        launch_prim_index(s->tris, (int)n_tris, s->prim_k, st);
+        rc = dof_cuda_check(cudaStreamSynchronize(st), "scene triangle index");
+    }
     cudaFree(d_xyz); cudaFree(d_idx); cudaFree(d_mat);
     if (rc != DOF_OK) {
         dof_free(ctx, s->tris, s->tris_bytes);
+        dof_free(ctx, s->prim_k, 4 * (size_t)n_tris);
         dof_free(ctx, s->nodes, s->nodes_bytes);
         dof_free(ctx, s->nodes4, s->nodes4_bytes);
         delete s;
@@ -337,6 +358,7 @@ extern "C" void dof_scene_destroy(DofScene *s) {
     {
         DeviceGuard g(ctx->device);
         dof_free(ctx, s->tris, s->tris_bytes);
+        dof_free(ctx, s->prim_k, 4 * (size_t)s->n_tris);
         dof_free(ctx, s->nodes, s->nodes_bytes);
         dof_free(ctx, s->nodes4, s->nodes4_bytes);
     }
@@ -401,6 +423,38 @@ extern "C" int dof_gbuffer(DofCtx *ctx, const DofScene *scene, const DofCamera *
     launch_primary(dc, dp, scene_dev(scene, dc), reinterpret_cast<float4 *>(color), depth,
                    reinterpret_cast<float4 *>(normal), prim, ctx->d_status, (cudaStream_t)stream);
     return dof_cuda_check(cudaGetLastError(), "dof_gbuffer launch");
+}
+
+extern "C" int dof_gbuffer_raster(DofCtx *ctx, const DofScene *scene, const DofCamera *cam, const DofParams *p,
+                                  uint32_t width, uint32_t height, float *color, float *depth, float *normal,
+                                  int32_t *prim, void *stream) {
+    if (!ctx || !scene || !cam || !p || !color || !depth || !normal)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_gbuffer_raster: null argument");
+    if (width < 2 || height < 2 || (width & 1) || (height & 1))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_gbuffer_raster: size must be even and >= 2");
+    if (!aligned(color, 16) || !aligned(normal, 16) || !aligned(depth, 8))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_gbuffer_raster: misaligned output");
+    if (!ctx->pool) return dof_set_error(DOF_ERR_CUDA, "dof_gbuffer_raster: no memory pool on this device");
+    DeviceGuard g(ctx->device);
+    DevCam dc;
+    DevParams dp;
+    int rc = make_cam(cam, width, height, dc);
+    if (rc) return rc;
+    rc = make_params(p, width, height, DOF_MAX_RAYS, dp);
+    if (rc) return rc;
+    cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    const SceneDev sd = scene_dev(scene, dc);
+    const size_t bytes = raster_scratch_bytes((int)width, (int)height, (int)scene->n_tris);
+    void *scratch = nullptr;
+    rc = dof_cuda_check(cudaMallocFromPoolAsync(&scratch, bytes, ctx->pool, st), "dof_gbuffer_raster scratch");
+    if (rc) return rc;
+    cudaError_t e = launch_raster(dc, dp, sd, scene->prim_k, scratch, ctx->sm_count, reinterpret_cast<float4 *>(color),
+                                  depth, reinterpret_cast<float4 *>(normal), prim, st);
+    cudaError_t f = cudaFreeAsync(scratch, st);
+    rc = dof_cuda_check(e, "dof_gbuffer_raster launch");
+    if (rc) return rc;
+    return dof_cuda_check(f, "dof_gbuffer_raster scratch release");
 }
 
 // ---------------------------------------------------------------------------

@@ -111,6 +111,7 @@ struct DofCtx {
     cudaStream_t ray_stream;
     cudaEvent_t ev_fork, ev_join;
     std::mutex launch_mu;          // one frame's enqueue at a time on ray_stream
+    cudaMemPool_t pool;            // stream-ordered scratch of the rasterising G-buffer producer
 };
 
 struct DofScene {
@@ -124,6 +125,7 @@ struct DofScene {
     int root4, n_nodes4, depth4;
     BvhNode *nodes;
     float4 *tris;
+    int32_t *prim_k;               // triangle id -> sorted index (n_tris)
     size_t bytes;
     float lo[3], hi[3];
 };
@@ -191,6 +193,12 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
                      const uint32_t *d_mat, int builder, int ploc_radius, cudaStream_t st);
 void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *color, float *depth,
                     float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st);
+// rasterising G-buffer producer (raster.cu)
+void launch_prim_index(const float4 *tris, int n, int32_t *prim_k, cudaStream_t st);
+size_t raster_scratch_bytes(int W, int H, int n_tot);
+cudaError_t launch_raster(const DevCam &cam, const DevParams &p, const SceneDev &sc, const int32_t *prim_k,
+                          void *scratch, int sm_count, float4 *color, float *depth, float4 *normal, int32_t *prim,
+                          cudaStream_t st);
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------

@@ -3,6 +3,7 @@
 // persistent thin-lens ray kernel (Section 3.2.2): Philox lens samples, closest hit
 // through the LBVH, Lambert shading and the per-pixel near/far split.
 #include "batch.cuh"
+#include "geometry.cuh"
 
 namespace {
 
@@ -28,37 +29,6 @@ __device__ __forceinline__ void philox2(unsigned long long c0, unsigned long lon
     o0 = c0; o1 = c1;
 }
 
-// ---------------------------------------------------------------------------
-// ray / box / triangle
-// ---------------------------------------------------------------------------
-struct Ray {
-    float3 o, d, inv;
-    float3 oinv;        // o * inv (the fused slab test of the 4-wide tree)
-    int kx, ky, kz;
-    float Sx, Sy, Sz;
-};
-
-__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
-
-__device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
-    Ray r;
-    r.o = o; r.d = d;
-    auto safe = [](float x) { return fabsf(x) < 1e-30f ? copysignf(1e-30f, x) : x; };
-    r.inv = make_float3(1.f / safe(d.x), 1.f / safe(d.y), 1.f / safe(d.z));
-    r.oinv = make_float3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
-    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
-    int kx = kz == 2 ? 0 : kz + 1;
-    int ky = kx == 2 ? 0 : kx + 1;
-    if (comp(d, kz) < 0.f) { int t = kx; kx = ky; ky = t; }
-    r.kx = kx; r.ky = ky; r.kz = kz;
-    float dz = comp(d, kz);
-    r.Sx = comp(d, kx) / dz;
-    r.Sy = comp(d, ky) / dz;
-    r.Sz = 1.f / dz;
-    return r;
-}
-
 // slab test, conservative by a few ulps so rounding never culls a hit on the surface
 __device__ __forceinline__ bool box_hit(const Ray &r, float3 lo, float3 hi, float tbest, float &tent) {
     float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
@@ -82,42 +52,7 @@ __device__ __forceinline__ bool box_hit_w(const Ray &r, float lx, float ly, floa
     return tmin <= tmax * 1.0000005f;
 }
 
-// Watertight ray/triangle test (Woop, Benthin and Wald, JCGT 2013): shear the
-// vertices into ray space, evaluate the three edge functions (without FMA
-// contraction, so a shared edge evaluates to exact negatives), double precision only
-// when an edge function is exactly zero.  Returns t > 0 or -1.
-__device__ __forceinline__ float tri_hit(const Ray &r, float4 v0, float4 v1, float4 v2) {
-    float3 A = make_float3(v0.x - r.o.x, v0.y - r.o.y, v0.z - r.o.z);
-    float3 B = make_float3(v1.x - r.o.x, v1.y - r.o.y, v1.z - r.o.z);
-    float3 C = make_float3(v2.x - r.o.x, v2.y - r.o.y, v2.z - r.o.z);
-    float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
-    float Ax = __fsub_rn(comp(A, r.kx), __fmul_rn(r.Sx, Akz));
-    float Ay = __fsub_rn(comp(A, r.ky), __fmul_rn(r.Sy, Akz));
-    float Bx = __fsub_rn(comp(B, r.kx), __fmul_rn(r.Sx, Bkz));
-    float By = __fsub_rn(comp(B, r.ky), __fmul_rn(r.Sy, Bkz));
-    float Cx = __fsub_rn(comp(C, r.kx), __fmul_rn(r.Sx, Ckz));
-    float Cy = __fsub_rn(comp(C, r.ky), __fmul_rn(r.Sy, Ckz));
-    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-    if (U == 0.f || V == 0.f || W == 0.f) {
-        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
-        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
-        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
-    }
-    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return -1.f;
-    float det = U + V + W;
-    if (det == 0.f) return -1.f;
-    float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
-    float t = T / det;
-    return t > 0.f ? t : -1.f;
-}
 
-struct HitRec {
-    float t;
-    int prim;   // original triangle id, -1 = miss
-    int k;      // sorted index
-};
 
 // ---------------------------------------------------------------------------
 // 4-wide traversal step: the four child boxes of a node are tested at once and the
@@ -283,33 +218,6 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
         if (step2(r, sc.nodes, sc.n_tris - 1, sc.tris, sc.n_tris, node, stack, sp, h, n_visit, n_tests, status)) break;
     }
     return h;
-}
-
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
-    return h;
-}
-
-// colour of a hit: per-triangle hash albedo, Lambert + ambient under one directional
-// light (material 1: emitter); also the face normal turned towards the ray
-__device__ __forceinline__ float3 shade(const DevParams &p, const SceneDev &sc, const HitRec &h, float3 dir,
-                                        float3 &n) {
-    const float4 *tp = sc.tris + 3 * (size_t)h.k;
-    float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-    n = normalize(cross(make_float3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z),
-                        make_float3(v2.x - v0.x, v2.y - v0.y, v2.z - v0.z)));
-    if (dot(n, dir) > 0.f) n = -1.f * n;
-    uint32_t base = fmix32(p.albedo_seed);
-    float alb[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        uint32_t hh = fmix32(base ^ (uint32_t)(3 * h.prim + c));
-        alb[c] = 0.1f + 0.8f * ((float)(hh >> 8) * 5.9604644775390625e-8f);
-    }
-    if (__float_as_int(v2.w) == 1) return make_float3(p.emit * alb[0], p.emit * alb[1], p.emit * alb[2]);
-    float lam = fmaxf(0.f, -dot(n, p.light));
-    float k = p.k_a + p.k_d * lam;
-    return make_float3(alb[0] * k, alb[1] * k, alb[2] * k);
 }
 
 // ---------------------------------------------------------------------------

@@ -102,6 +102,9 @@ _SIGS = {
     "dof_scene_info": (C.c_int, [C.c_void_p, C.POINTER(DofSceneInfo)]),
     "dof_gbuffer": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofCamera), C.POINTER(DofParams), C.c_uint32,
                               C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dof_gbuffer_raster": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofCamera), C.POINTER(DofParams),
+                                     C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
     "dof_history_create": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                      C.POINTER(C.c_void_p)]),
     "dof_history_destroy": (None, [C.c_void_p]),
@@ -334,9 +337,11 @@ class History:
             pass
 
 
-def gbuffer(ctx: Context, scene: Scene, cam, params: dict, width: int, height: int, out=None, stream=None):
+def gbuffer(ctx: Context, scene: Scene, cam, params: dict, width: int, height: int, out=None, stream=None,
+            raster: bool = False):
     """G-buffer producer on the device; returns dict of torch tensors (color, depth,
-    normal, prim)."""
+    normal, prim).  raster=True produces the same bits object-order
+    (dof_gbuffer_raster) instead of by one primary ray per pixel (dof_gbuffer)."""
     import torch
     dev = torch.device("cuda", ctx.device)
     if out is None:
@@ -345,8 +350,9 @@ def gbuffer(ctx: Context, scene: Scene, cam, params: dict, width: int, height: i
                    normal=torch.empty((height, width, 4), dtype=torch.float32, device=dev),
                    prim=torch.empty((height, width), dtype=torch.int32, device=dev))
     c, p = camera_struct(cam), params_struct(params)
-    _check(lib().dof_gbuffer(ctx.ptr, scene.ptr, C.byref(c), C.byref(p), width, height, _ptr(out["color"]),
-                             _ptr(out["depth"]), _ptr(out["normal"]), _ptr(out.get("prim")), _stream_ptr(stream)))
+    fn = lib().dof_gbuffer_raster if raster else lib().dof_gbuffer
+    _check(fn(ctx.ptr, scene.ptr, C.byref(c), C.byref(p), width, height, _ptr(out["color"]), _ptr(out["depth"]),
+              _ptr(out["normal"]), _ptr(out.get("prim")), _stream_ptr(stream)))
     return out
 
 

@@ -29,6 +29,7 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("dof_ctx_create", "dof_scene_upload", "dof_frame", "dof_history_create", "dof_gbuffer",
+                 "dof_gbuffer_raster",
                  "dof_last_error", "dof_frame_stats", "dof_debug_buffer"):
         assert must in names
 
