@@ -49,11 +49,11 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch from the last ncu capture of each kernel on the
 # workload (profiles/top_kernels_*.md); a kernel or workload changed since then has no
 # entry.  The 4K tracer was captured at 1920x1080 (same scene, lens, 4 spp) and is
-# scaled by the rays of a full launch (6.73M / 1.68M).
+# scaled by the rays of a full launch (6.73M / 1.78M).
 PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": 9.0e6, "k_trace_rays<0>": None, "k_recon": 27.1e6,
                            "k_main_filter": 10.4e6, "k_accumulate": 55.7e6, "k_composite": 63.3e6,
                            "k_downscale_tiles": 41.5e6},
-                    "c3": {"k_trace_rays<0>": None}}
+                    "c3": {"k_trace_rays<0>": 21.7e6 * 6.73 / 1.78}}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
@@ -370,26 +370,28 @@ def run_ours(args, rank, world):
     pin = []
     for g in gbs:
         pin.append(dict(color=g["color"].cpu().pin_memory(), depth=g["depth"].cpu().pin_memory()))
+        if int(prm["ray_mode"]) == 1:
+            pin[-1]["normal"] = g["normal"].cpu().pin_memory()
     hout = torch.empty((w.H, w.W, 4), dtype=torch.float32).pin_memory()
-    stage = dict(color=torch.empty_like(gbs[0]["color"]), depth=torch.empty_like(gbs[0]["depth"]))
     he = dof.History(ctx, w.W, w.H, max_rays=spp, taa=args.taa)
-    h2d = pin[0]["color"].numel() * 4 + pin[0]["depth"].numel() * 4
+    h2d = sum(t.numel() * 4 for t in pin[0].values())
     d2h = hout.numel() * 4
 
+    # through dof_frame_host: each frame's G-buffer is copied in from pinned host memory
+    # and its image copied out to pinned host memory, on the library's copy streams, so
+    # the copies of one frame overlap the passes of its neighbours
     def e2e_step(s):
-        p = pin[s % CYCLE]
-        stage["color"].copy_(p["color"], non_blocking=True)
-        stage["depth"].copy_(p["depth"], non_blocking=True)
-        step(s, he, stage)
-        hout.copy_(out, non_blocking=True)
+        dof.frame_host(ctx, scene, pin[s % CYCLE], None, None, he, hout, cam_struct=cams[s], params_s=pstruct)
 
     for s in range(args.warmup):
         e2e_step(s)
+    dof.frame_host_join(he)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for s in range(args.warmup, args.warmup + args.steps):
         e2e_step(s)
+    dof.frame_host_join(he, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1))

@@ -251,6 +251,23 @@ int dof_history_import(DofHistory *hist, const void *host_buf, size_t bytes, voi
 int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *gbuf, const DofCamera *cam,
               const DofParams *p, DofHistory *hist, float *out, void *stream);
 
+/* One frame from and to host memory.  color (W*H float4), depth (W*H float) and, in
+ * the adaptive ray mode, normal (W*H float4; else may be NULL) are host buffers in the
+ * layout of DofGBuffer; out (W*H float4) receives the composited image, as dof_frame
+ * writes it; W, H are the history's.  The history keeps two device slots used in
+ * turn and one copy stream per direction: the inputs are copied in once the frame two
+ * calls back is done with the slot, the pass runs on `stream` after its inputs, and
+ * the image is copied out once the pass is done, so the copies of one frame overlap
+ * the passes of its neighbours.  The call returns once all of it is enqueued (with
+ * pageable host memory the driver may copy synchronously; pinned memory overlaps).
+ * The caller keeps the inputs unchanged and leaves `out` unread until the frame's
+ * copy-out has completed: dof_frame_host_join(hist, s) makes stream `s` wait for the
+ * copy-outs enqueued so far.  The slots (52 B per pixel) are allocated on first use. */
+int dof_frame_host(DofCtx *ctx, const DofScene *scene, const float *color, const float *depth,
+                   const float *normal, const DofCamera *cam, const DofParams *p, DofHistory *hist,
+                   float *out, void *stream);
+int dof_frame_host_join(DofHistory *hist, void *stream);
+
 /* One session's frame of a batch. */
 typedef struct {
     const DofScene *scene;

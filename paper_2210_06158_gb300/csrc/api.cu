@@ -493,6 +493,19 @@ static void history_free(DofHistory *h) {
         delete[] h->ev;
         h->ev = nullptr;
     }
+    if (h->hio_h2d) cudaStreamSynchronize(h->hio_h2d);
+    if (h->hio_d2h) cudaStreamSynchronize(h->hio_d2h);
+    for (int k = 0; k < 2; k++) {
+        dof_free(c, h->hio_color[k], 16 * P);
+        dof_free(c, h->hio_depth[k], 4 * P);
+        dof_free(c, h->hio_normal[k], 16 * P);
+        dof_free(c, h->hio_out[k], 16 * P);
+        if (h->hio_in[k]) cudaEventDestroy(h->hio_in[k]);
+        if (h->hio_used[k]) cudaEventDestroy(h->hio_used[k]);
+        if (h->hio_done[k]) cudaEventDestroy(h->hio_done[k]);
+    }
+    if (h->hio_h2d) cudaStreamDestroy(h->hio_h2d);
+    if (h->hio_d2h) cudaStreamDestroy(h->hio_d2h);
 }
 
 extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, uint32_t max_rays, uint32_t flags,
@@ -905,6 +918,95 @@ extern "C" int dof_frame(DofCtx *ctx, const DofScene *scene, const DofGBuffer *g
     DofFrameReq r{scene, gb, cam, p, h, out};
     DeviceGuard g(ctx->device);
     return run_frames(ctx, &r, 1, (cudaStream_t)stream);
+}
+
+// the slots of dof_frame_host, made on first use (the normal planes when first needed)
+static int host_io_init(DofHistory *h, bool normals) {
+    DofCtx *c = h->ctx;
+    const size_t P = (size_t)h->W * h->H;
+    int rc = DOF_OK;
+    if (!h->hio_ready) {
+        for (int k = 0; k < 2 && rc == DOF_OK; k++) {
+            rc = dof_alloc(c, 16 * P, (void **)&h->hio_color[k], &h->bytes);
+            if (rc == DOF_OK) rc = dof_alloc(c, 4 * P, (void **)&h->hio_depth[k], &h->bytes);
+            if (rc == DOF_OK) rc = dof_alloc(c, 16 * P, (void **)&h->hio_out[k], &h->bytes);
+            if (rc == DOF_OK &&
+                (cudaEventCreateWithFlags(&h->hio_in[k], cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&h->hio_used[k], cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&h->hio_done[k], cudaEventDisableTiming) != cudaSuccess))
+                rc = dof_set_error(DOF_ERR_CUDA, "dof_frame_host: events");
+        }
+        if (rc == DOF_OK && (cudaStreamCreateWithFlags(&h->hio_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+                             cudaStreamCreateWithFlags(&h->hio_d2h, cudaStreamNonBlocking) != cudaSuccess))
+            rc = dof_set_error(DOF_ERR_CUDA, "dof_frame_host: copy streams");
+        if (rc != DOF_OK) {
+            cudaGetLastError();
+            return rc;      // what was made is released with the history
+        }
+        h->hio_ready = 1;
+    }
+    if (normals && !h->hio_normals) {
+        for (int k = 0; k < 2 && rc == DOF_OK; k++)
+            rc = dof_alloc(c, 16 * P, (void **)&h->hio_normal[k], &h->bytes);
+        if (rc != DOF_OK) return rc;
+        h->hio_normals = 1;
+    }
+    return DOF_OK;
+}
+
+extern "C" int dof_frame_host(DofCtx *ctx, const DofScene *scene, const float *color, const float *depth,
+                              const float *normal, const DofCamera *cam, const DofParams *p, DofHistory *h,
+                              float *out, void *stream) {
+    if (!ctx || !scene || !color || !depth || !cam || !p || !h || !out)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame_host: null argument");
+    if (h->ctx != ctx) return dof_set_error(DOF_ERR_MISMATCH, "dof_frame_host: history of another context");
+    DeviceGuard g(ctx->device);
+    int rc = host_io_init(h, normal != nullptr);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int k = (int)(h->hio_frames & 1);
+    const size_t P = (size_t)h->W * h->H;
+    DofGBuffer gb{};
+    gb.color = reinterpret_cast<const float *>(h->hio_color[k]);
+    gb.depth = h->hio_depth[k];
+    gb.normal = normal ? reinterpret_cast<const float *>(h->hio_normal[k]) : nullptr;
+    gb.width = h->W;
+    gb.height = h->H;
+    gb.fmt = DOF_FMT_F32;
+    cudaGetLastError();
+    // inputs: once the frame two calls back is done with this slot
+    cudaError_t e = cudaStreamWaitEvent(h->hio_h2d, h->hio_used[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hio_color[k], color, 16 * P, cudaMemcpyHostToDevice, h->hio_h2d);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hio_depth[k], depth, 4 * P, cudaMemcpyHostToDevice, h->hio_h2d);
+    if (e == cudaSuccess && normal)
+        e = cudaMemcpyAsync(h->hio_normal[k], normal, 16 * P, cudaMemcpyHostToDevice, h->hio_h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(h->hio_in[k], h->hio_h2d);
+    // the frame: after its inputs, and once the image of two calls back has been copied out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->hio_in[k], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->hio_done[k], 0);
+    rc = dof_cuda_check(e, "dof_frame_host input copy");
+    if (rc) return rc;
+    DofFrameReq r{scene, &gb, cam, p, h, reinterpret_cast<float *>(h->hio_out[k])};
+    rc = run_frames(ctx, &r, 1, st);
+    if (rc) return rc;
+    // the image: copied out once the frame is done
+    e = cudaEventRecord(h->hio_used[k], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->hio_d2h, h->hio_used[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->hio_out[k], 16 * P, cudaMemcpyDeviceToHost, h->hio_d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(h->hio_done[k], h->hio_d2h);
+    rc = dof_cuda_check(e, "dof_frame_host output copy");
+    if (rc) return rc;
+    h->hio_frames++;
+    return DOF_OK;
+}
+
+extern "C" int dof_frame_host_join(DofHistory *h, void *stream) {
+    if (!h) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame_host_join: null history");
+    if (!h->hio_ready) return DOF_OK;
+    DeviceGuard g(h->ctx->device);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaStreamWaitEvent((cudaStream_t)stream, h->hio_done[k], 0);
+    return dof_cuda_check(e, "dof_frame_host_join");
 }
 
 extern "C" int dof_batch_frame(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, void *stream) {

@@ -165,6 +165,15 @@ struct DofHistory {
     // per-kernel timing ring (DOF_HIST_TIMING)
     cudaEvent_t *ev;               // kTimingSlots x (DOF_K_COUNT + 1)
     int ev_slot, ev_used;
+    // frames from and to host memory (dof_frame_host): two device slots (G-buffer in,
+    // image out) used in turn, a copy stream per direction, and per slot the events
+    // "inputs copied", "frame done with the slot", "image copied out"
+    float4 *hio_color[2], *hio_normal[2], *hio_out[2];
+    float *hio_depth[2];
+    cudaEvent_t hio_in[2], hio_used[2], hio_done[2];
+    cudaStream_t hio_h2d, hio_d2h;
+    int hio_ready, hio_normals;
+    uint64_t hio_frames;
 };
 
 constexpr int kTimingSlots = 64;

@@ -105,6 +105,9 @@ _SIGS = {
     "dof_gbuffer_raster": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(DofCamera), C.POINTER(DofParams),
                                      C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "dof_frame_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(DofCamera), C.POINTER(DofParams), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dof_frame_host_join": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dof_history_create": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                      C.POINTER(C.c_void_p)]),
     "dof_history_destroy": (None, [C.c_void_p]),
@@ -380,6 +383,31 @@ def frame(ctx: Context, scene: Scene, gbuf: dict, cam, params, hist: History, ou
     _check(lib().dof_frame(ctx.ptr, scene.ptr, C.byref(g), C.byref(c), C.byref(p), hist.ptr, _ptr(out),
                            _stream_ptr(stream)))
     return out
+
+
+def frame_host(ctx: Context, scene: Scene, gbuf: dict, cam, params, hist: History, out, stream=None,
+               cam_struct: DofCamera | None = None, params_s: DofParams | None = None):
+    """One frame from and to host memory (dof_frame_host): gbuf holds host tensors
+    (color HxWx4, depth HxW, normal HxWx4 or absent), out a host HxWx4 float32 tensor;
+    pinned tensors let the copies overlap the neighbouring frames' passes.  Returns
+    before the copies end: call frame_host_join (then synchronise) before reading out."""
+    c = cam_struct if cam_struct is not None else camera_struct(cam)
+    p = params_s if params_s is not None else params_struct(params)
+    for k in ("color", "depth", "normal"):
+        t = gbuf.get(k)
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
+            raise ValueError(f"frame_host: {k} must be a contiguous host tensor")
+    if out.is_cuda or not out.is_contiguous():
+        raise ValueError("frame_host: out must be a contiguous host tensor")
+    _check(lib().dof_frame_host(ctx.ptr, scene.ptr, _ptr(gbuf["color"]), _ptr(gbuf["depth"]),
+                                _ptr(gbuf.get("normal")), C.byref(c), C.byref(p), hist.ptr, _ptr(out),
+                                _stream_ptr(stream)))
+    return out
+
+
+def frame_host_join(hist: History, stream=None):
+    """Make `stream` wait for the copy-outs of the host frames enqueued so far."""
+    _check(lib().dof_frame_host_join(hist.ptr, _stream_ptr(stream)))
 
 
 def coc_tiles_noalloc(depth, cam, params, out=None, stream=None):

@@ -535,3 +535,33 @@ def test_full_size_c2_two_frames():
     tot = sum(s["rays"] for s in stats)
     mis = sum(s["mismatches"] for s in stats)
     assert mis <= max(2, 1e-4 * tot), (mis, tot)
+
+
+def test_host_frames_equal_device_frames():
+    """dof_frame_host (G-buffer in and image out through host memory, two device slots,
+    copies on the library's own streams, three frames in flight before the join) gives
+    the images dof_frame gives from device buffers, bit for bit; in the adaptive mode the
+    normal plane travels too."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    for mode in (0, 1):
+        w = make_workload("c1", n_frames=5)
+        prm = dict(w.params, ray_mode=mode, m=6)
+        ctx = dof.Context(0)
+        sc = dof.Scene(ctx, w.scene)
+        gbs = [dof.gbuffer(ctx, sc, w.camera(k), prm, w.W, w.H) for k in range(w.n_frames)]
+        mr = oracle.max_rays(prm)
+        ha = dof.History(ctx, w.W, w.H, max_rays=mr)
+        hb = dof.History(ctx, w.W, w.H, max_rays=mr)
+        want = []
+        for k in range(w.n_frames):
+            want.append(dof.frame(ctx, sc, gbs[k], w.camera(k), prm, ha).cpu())
+        keys = ("color", "depth", "normal") if mode == 1 else ("color", "depth")
+        hosts = [{key: gbs[k][key].cpu().pin_memory() for key in keys} for k in range(w.n_frames)]
+        outs = [torch.empty((w.H, w.W, 4), dtype=torch.float32).pin_memory() for _ in range(w.n_frames)]
+        for k in range(w.n_frames):
+            dof.frame_host(ctx, sc, hosts[k], w.camera(k), prm, hb, outs[k])
+        dof.frame_host_join(hb)
+        torch.cuda.synchronize()
+        for k in range(w.n_frames):
+            assert torch.equal(outs[k].view(torch.int32), want[k].view(torch.int32)), (mode, k)

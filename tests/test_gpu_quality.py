@@ -1,7 +1,8 @@
 """Quality against a converged ray-traced reference (the analogue of the paper's
 image comparisons, Section 4): the hybrid image, after temporal accumulation on a static
 camera, against the thin-lens integral rendered by the oracle with 256 rays per pixel,
-for 1, 4 and 16 rays per masked pixel, and the post-process alone (no rays) beside it.
+for 1, 4 and 16 rays per masked pixel, for the adaptive ray budget (Eq. 4) at m = 6 and
+m = 30, and the post-process alone (no rays) beside it.
 
 The reference is the oracle's ray-traced layer of a frame at twice the resolution:
 its half-resolution pixels are the full-resolution pixels of the image under test
@@ -55,8 +56,9 @@ def test_hybrid_approaches_the_ray_traced_reference(name):
     results = {}
     masked = None
     for label, over in (("post-process only", dict(mask_near_hpx=1e9)), ("1 ray", dict(spp=1)),
-                        ("4 rays", dict(spp=4)), ("16 rays", dict(spp=16))):
-        prm = dict(w.params, ray_mode=0, **over)
+                        ("4 rays", dict(spp=4)), ("16 rays", dict(spp=16)),
+                        ("adaptive m=6", dict(ray_mode=1, m=6)), ("adaptive m=30", dict(ray_mode=1, m=30))):
+        prm = dict(w.params, **dict(dict(ray_mode=0), **over))
         g = GpuRunner(w, prm, record_rays=False)
         for k in range(8):
             res = g.frame(w.camera(k), gb, read=(k == 7))
@@ -75,3 +77,5 @@ def test_hybrid_approaches_the_ray_traced_reference(name):
     # more rays do not make it worse
     assert table["16 rays"][1] >= table["post-process only"][1] + 0.3, table
     assert table["16 rays"][1] >= table["4 rays"][1] - 0.2 and table["4 rays"][1] >= table["1 ray"][1] - 0.2, table
+    # the adaptive budget (Eq. 4): a larger m spends more rays where the variance is high
+    assert table["adaptive m=30"][1] >= table["adaptive m=6"][1] - 0.2, table
