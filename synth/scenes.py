@@ -278,6 +278,38 @@ def scene_c1(seed: int, cam_pos=(0.0, 1.2, 0.0), pitch_deg=5.0, f_m=0.05, sensor
     return b.build()
 
 
+def scene_bokeh(seed: int, cam_pos=(0.0, 1.2, 0.0), pitch_deg=3.0, f_m=0.085, sensor_w_m=0.036,
+                aspect=144.0 / 256.0) -> Scene:
+    """Bright bokeh: emissive icospheres (material 1) out of focus in front of and far
+    behind a focus distance of a few metres, diffuse boxes around it, on the ground."""
+    rng = SplitMix64(seed)
+    b = _Builder(seed)
+    b.add("ground", *ground())
+    tanhx = sensor_w_m / (2 * f_m)
+    tanhy = tanhx * aspect
+    pose = camera_pose(cam_pos, pitch_deg)
+
+    def in_view(n, z0, z1, r0, r1):
+        z = rng.uniform(n, z0, z1)
+        sx = rng.uniform(n, -0.85, 0.85)
+        sy = rng.uniform(n, -0.7, 0.7)
+        r = rng.uniform(n, r0, r1)
+        dirs = (pose["fwd"][None].astype(np.float64) + sx[:, None] * tanhx * pose["right"][None]
+                + sy[:, None] * tanhy * pose["up"][None])
+        return np.asarray(cam_pos)[None] + z[:, None] * dirs, r
+
+    c, r = in_view(6, 0.8, 2.5, 0.02, 0.06)
+    b.add("near_lights", *spheres(c, r, 1), mat=1)
+    c, r = in_view(24, 25.0, 60.0, 0.1, 0.3)
+    b.add("far_lights", *spheres(c, r, 1), mat=1)
+    nb = 12
+    zb = rng.uniform(nb, 4.0, 30.0)
+    xb = _frustum_x(rng, zb, tanhx, 0.9)
+    size = np.stack([rng.uniform(nb, 0.3, 1.5), rng.uniform(nb, 0.3, 1.5), rng.uniform(nb, 0.3, 1.5)], -1)
+    b.add("boxes", *boxes(np.stack([xb, zb], -1), np.zeros(nb), size, rng.uniform(nb, 0, np.pi)))
+    return b.build()
+
+
 def scene_grass_field(seed: int, density: float = 1.0, f_m=0.035, sensor_w_m=0.036,
                       near=(1.3, 4.8), far=(8.0, 60.0)) -> Scene:
     """Lawn field: thin blade quads and fence bars in the near field (the dolly
@@ -419,6 +451,7 @@ def make_workload(name: str, W: int | None = None, H: int | None = None,
     c1  256x144, ~2.8k tris, 50 mm f/1.4 focus 15 m, 1 frame, 1 spp
     c2  1920x1080, ~500k tris, 35 mm f/2 focus 20 m, 16-frame dolly, 1 spp, CoC radius <= 32 px
     c3  3840x2160, ~2M tris, 85 mm f/1.2 focus 20 m, 16-frame dolly, 4 spp, CoC radius <= 64 px
+    bokeh  256x144, emissive spheres near and far, 85 mm f/1.2 focus 5 m, 4 frames, 4 spp
     W/H override the resolution (for oracle-sized crops of the same scene and lens)."""
     if name == "c1":
         seed = 1001 + 100 * session
@@ -444,6 +477,14 @@ def make_workload(name: str, W: int | None = None, H: int | None = None,
         poses = dolly_path(seed, (0.0, height, 0.0), n_frames or 16, pitch_deg=pitch)
         f_m = intr["f_m"]
         fn = lambda: scene_grass_field(seed, dens, f_m=f_m)
+    elif name == "bokeh":
+        # bright bokeh (not a benchmark configuration): 85 mm f/1.2 focused at 5 m
+        seed = 1004 + 100 * session
+        intr = dict(f_m=0.085, f_number=1.2, focus_m=5.0, sensor_w_m=0.036)
+        W, H = W or 256, H or 144
+        poses = dolly_path(seed, (0.0, 1.2, 0.0), n_frames or 4, pitch_deg=3.0)
+        params = default_params(spp=4, max_coc_px=16.0, seed=seed, session=session, albedo_seed=seed)
+        fn = lambda: scene_bokeh(seed)
     else:
         raise ValueError(f"unknown workload {name!r}")
     if n_frames is not None:

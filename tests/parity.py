@@ -29,6 +29,26 @@ def psnr(a, b):
     return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
 
 
+def ssim(a, b, mask=None):
+    """Mean structural similarity (Wang, Bovik, Sheikh and Simoncelli 2004) of two linear
+    RGB images with peak 1: Gaussian window sigma 1.5 (truncated at 3.5 sigma, 11 taps),
+    C1 = (0.01)^2, C2 = (0.03)^2, per channel, averaged over the channels and over the
+    pixels of `mask` (all pixels if None)."""
+    from scipy.ndimage import gaussian_filter
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    g = lambda x: gaussian_filter(x, 1.5, mode="reflect", truncate=3.5)
+    vals = []
+    for c in range(a.shape[-1]):
+        x, y = a[..., c], b[..., c]
+        mx, my = g(x), g(y)
+        sxx, syy, sxy = g(x * x) - mx * mx, g(y * y) - my * my, g(x * y) - mx * my
+        m = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+        vals.append(m if mask is None else m[mask])
+    return float(np.mean(vals))
+
+
 class GpuRunner:
     """One session on the CUDA path: scene + history, frames through dof_frame."""
 
@@ -189,6 +209,16 @@ def dilate(mask, r):
 def full_res(mask_h, W, H):
     m = np.repeat(np.repeat(mask_h, 2, 0), 2, 1)[:H, :W]
     return dilate(m, 2)
+
+
+def max_hdr(a, b):
+    """Largest error of a against b, absolute where |b| <= 1 and relative above: the
+    image bounds are stated for display-range linear RGB (peak 1); HDR values (emitters)
+    carry FP32 rounding in proportion to their magnitude."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    d = np.abs(a - b) / np.maximum(1.0, np.abs(b))
+    return float(d.max()) if d.size else 0.0
 
 
 def max_abs(a, b, mask=None):

@@ -14,7 +14,7 @@ import pytest
 import oracle
 from synth import make_workload
 
-from parity import GpuRunner, psnr
+from parity import GpuRunner, psnr, ssim
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -70,9 +70,10 @@ def test_hybrid_approaches_the_ray_traced_reference(name):
     table = {}
     sel = masked & blurred
     for label, out in results.items():
-        table[label] = (psnr(out, ref), psnr(out[sel], ref[sel]))
+        table[label] = (psnr(out, ref), psnr(out[sel], ref[sel]), ssim(out, ref), ssim(out, ref, sel))
         print(f"[quality {name} 256x144] {label:18s} PSNR all {table[label][0]:6.2f} dB, "
-              f"out-of-focus masked pixels {table[label][1]:6.2f} dB  ({sel.mean():.2f} of the image)")
+              f"out-of-focus masked pixels {table[label][1]:6.2f} dB  ({sel.mean():.2f} of the image); "
+              f"SSIM all {table[label][2]:.4f}, out-of-focus masked {table[label][3]:.4f}")
     # the ray-traced layer brings the out-of-focus foreground closer to the reference, and
     # more rays do not make it worse
     assert table["16 rays"][1] >= table["post-process only"][1] + 0.3, table

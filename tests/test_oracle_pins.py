@@ -344,6 +344,15 @@ def test_uniform_colour_is_fixed_point_of_post_process():
     for k in ("pp_in", "pre", "main_out", "pp_med"):
         assert np.abs(fr[k][..., :3] - want).max() < 1e-12, k
     assert np.abs(fr["main_out"][..., 3]).max() == 0.0         # no bright samples
+    # a uniform emitter colour (luminance 6 > bright_lum + bright_ramp): every tap is
+    # bright, so the bright fraction is 1 and the colour is still a fixed point
+    bright = np.float32([5.0, 6.0, 7.0])
+    g["color"][...] = np.append(bright, np.float32(1.0))
+    assert float(bright.astype(np.float64) @ [0.2126, 0.7152, 0.0722]) > prm["bright_lum"] + prm["bright_ramp"]
+    fr = oracle.frame(sc, cam, prm, w.W, w.H, g)
+    for k in ("pp_in", "pre", "main_out", "pp_med"):
+        assert np.abs(fr[k][..., :3] - bright.astype(np.float64)).max() < 1e-12, k
+    assert np.abs(fr["main_out"][..., 3] - 1.0).max() < 1e-12
 
 
 def test_downscale_and_tiles_by_definition():
