@@ -62,9 +62,11 @@ BYTES = {
     "k_prefilter": ("N", 32.0),
     "k_main_filter": ("N", 36.0),        # pre 16 + z 4 read, 16 written (neighbour taps from cache)
     "k_median_pp": ("N", 32.0),
-    "k_mask_compact": ("N", 8.0),
+    "k_mask_compact": [("N", 4.0), ("M", 8.0), ("R", 4.0)],   # ray count per hpx; queue entry and
+                                         # first-ray index per masked hpx; ray list entry per ray
+                                         # (+ 4 B/N of x_f read in the adaptive mode, not counted)
     "k_trace_rays": ("R", 12.0),              # per ray: ray list 4 read, hit 8 written (BVH reads hit L2)
-    "k_shade": ("M", 76.0),              # queue, count, first ray read, 4 x float4 written (+ hits, per ray)
+    "k_shade": [("M", 76.0), ("R", 8.0)],   # queue, count, first ray read, 4 x float4 written; hits read
     "k_accumulate": ("N", 192.0),        # rt 64 + z 4 + nrays 4 + history 48 read; history 48 + 24 written
     "k_median_rt": ("N", 72.0),          # fused: variance blur (var 4 read, 4 written), RT median
                                          # (crt 16 + nrays 4 read, 16 written), mip 0 (ct 4 read,
@@ -75,6 +77,14 @@ BYTES = {
                                          # (one thread per hpx writes its 2x2 fpx)
     "k_taa": ("P", 68.0),                # composite 16 + depth 4 + history 16 read, out 16 + history 16 written
 }
+
+
+def algo_bytes(kernel, units):
+    """Algorithmic bytes of one launch: the sum over the kernel's (unit, bytes per unit) terms."""
+    terms = BYTES[kernel]
+    if isinstance(terms, tuple):
+        terms = [terms]
+    return sum(units[u] * b for u, b in terms)
 
 
 # HBM-bound streaming passes and the gather passes of a frame
@@ -416,8 +426,7 @@ def run_ours(args, rank, world):
             continue
         e = {"ms": round(v, 5), "share": round(v / sum(kavg.values()), 4)}
         if k in BYTES:
-            u, b = BYTES[k]
-            e["gbs"] = round(units[u] * b / (v * 1e-3) / 1e9, 1)
+            e["gbs"] = round(algo_bytes(k, units) / (v * 1e-3) / 1e9, 1)
         kern[k] = e
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
@@ -434,8 +443,7 @@ def run_ours(args, rank, world):
                 "algorithmic_flop": int(trace_flop), "node_visits_per_ray": round(visits / max(1, rays), 2),
                 "tri_tests_per_ray": round(tests / max(1, rays), 2)}
     elif dom in BYTES:
-        u, b = BYTES[dom]
-        algo = units[u] * b
+        algo = algo_bytes(dom, units)
         achieved = algo / (kavg[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": traffic, "peak_source": peak_src,
@@ -447,7 +455,7 @@ def run_ours(args, rank, world):
     # gather passes (81-tap filters: L1/issue-bound by nature, reported apart)
     def agg(names):
         names = [k for k in names if kavg.get(k, 0) > 0]
-        b = sum(units[BYTES[k][0]] * BYTES[k][1] for k in names)
+        b = sum(algo_bytes(k, units) for k in names)
         t = sum(kavg[k] for k in names)
         return b, t
     img_bytes, img_ms = agg(STREAMING)
