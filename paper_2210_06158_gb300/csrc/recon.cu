@@ -13,7 +13,7 @@ namespace {
 // valid 3x3 neighbours (invalid slots padded with -inf / +inf so the median-of-9 network
 // selects index (k-1)/2 of the k valid values), and mip level 0 of the reconstruction,
 // (rgb, h) * v and (c_t, 1) * v.  Capped at 40 registers (six blocks per SM): the loads
-// of the three stages then overlap better (8% faster at 4K, within noise at 1080p).
+// of the three stages then overlap better at 4K (8% faster; 4% slower at 1080p).
 template <class AS>
 __global__ void __launch_bounds__(256, 6) k_resolve_rt(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
