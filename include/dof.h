@@ -45,6 +45,7 @@ extern "C" {
 
 /* ---- image formats ----------------------------------------------------------- */
 #define DOF_FMT_F32 0              /* colour/normal float4 (rgb/xyz + unused), depth float */
+#define DOF_FMT_F16 1              /* colour/normal half4 (8 bytes per pixel), depth float */
 
 /* ---- parameters -------------------------------------------------------------- */
 
@@ -113,7 +114,7 @@ typedef struct {
     const float *depth;     /* W*H float: depth along the optical axis, +inf = sky */
     const float *normal;    /* W*H float4: surface normal (xyz, unused); read in adaptive mode */
     uint32_t width, height; /* full resolution, both even and >= 2 */
-    uint32_t fmt;           /* DOF_FMT_F32 */
+    uint32_t fmt;           /* DOF_FMT_F32 or DOF_FMT_F16; rows tightly packed */
 } DofGBuffer;
 
 typedef struct DofCtx DofCtx;

@@ -615,10 +615,12 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
     if (h->ctx != ctx || scene->ctx != ctx) return dof_set_error(DOF_ERR_MISMATCH, "dof_frame: objects of another context");
     if (gb->width != h->W || gb->height != h->H)
         return dof_set_error(DOF_ERR_MISMATCH, "dof_frame: G-buffer %ux%u, history %ux%u", gb->width, gb->height, h->W, h->H);
-    if (gb->fmt != DOF_FMT_F32) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: unsupported G-buffer format");
+    if (gb->fmt != DOF_FMT_F32 && gb->fmt != DOF_FMT_F16)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: unsupported G-buffer format %u", gb->fmt);
     if (!gb->color || !gb->depth || (r.params->ray_mode == 1 && !gb->normal))
         return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: G-buffer plane is NULL");
-    if (!aligned(gb->color, 16) || !aligned(gb->depth, 8) || (gb->normal && !aligned(gb->normal, 16)) || !aligned(r.out, 16))
+    const size_t ga = gb->fmt == DOF_FMT_F16 ? 8 : 16;
+    if (!aligned(gb->color, ga) || !aligned(gb->depth, 8) || (gb->normal && !aligned(gb->normal, ga)) || !aligned(r.out, 16))
         return dof_set_error(DOF_ERR_INVALID_ARG, "dof_frame: misaligned buffer");
     memset(&d, 0, sizeof(d));
     int rc = make_cam(r.cam, h->W, h->H, d.cam);
@@ -633,6 +635,7 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
     d.color = reinterpret_cast<const float4 *>(gb->color);
     d.depth = gb->depth;
     d.normal = reinterpret_cast<const float4 *>(gb->normal);
+    d.gf16 = gb->fmt == DOF_FMT_F16;
     d.out = reinterpret_cast<float4 *>(r.out);
     d.pp_in = h->pp_in; d.pre = h->pre; d.main_ = h->main_; d.pp_med = h->pp_med; d.n_h = h->n_h;
     d.zn = h->crt;   // adaptive-mode scratch: crt is only written later, by the accumulation

@@ -32,6 +32,7 @@ struct SessDesc {
     const float4 *color;
     const float *depth;
     const float4 *normal;
+    int gf16;                      // colour and normal planes in half4 (DOF_FMT_F16)
     float4 *out;
     float4 *comp_out;              // composite target: out, or the history's image for the TAA
     const float4 *taa_in;          // previous resolved image (TAA)

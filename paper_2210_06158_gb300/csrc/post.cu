@@ -24,7 +24,9 @@ __global__ void __launch_bounds__(256) k_downscale_tiles(const __grid_constant__
     float nm = 0.f, am = 0.f;
     if (i < cam.W2 && j < cam.H2) {
         size_t f0 = (size_t)(2 * j) * cam.W + 2 * i, f1 = f0 + cam.W;
-        float4 c0 = __ldg(&color[f0]), c1 = __ldg(&color[f0 + 1]), c2 = __ldg(&color[f1]), c3 = __ldg(&color[f1 + 1]);
+        const bool gh = S.gf16;
+        float4 c0 = ld_img(color, f0, gh), c1 = ld_img(color, f0 + 1, gh), c2 = ld_img(color, f1, gh),
+               c3 = ld_img(color, f1 + 1, gh);
         float2 d01 = __ldg(reinterpret_cast<const float2 *>(&depth[f0]));
         float2 d23 = __ldg(reinterpret_cast<const float2 *>(&depth[f1]));
         float z[4] = {fminf(d01.x, p.z_far), fminf(d01.y, p.z_far), fminf(d23.x, p.z_far), fminf(d23.y, p.z_far)};
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(256) k_downscale_tiles(const __grid_constant__
         S.z_h[q] = zm;
         if (p.ray_mode == 1) {
             size_t fk = (k < 2 ? f0 : f1) + (k & 1);
-            S.n_h[q] = __ldg(&normal[fk]);
+            S.n_h[q] = ld_img(normal, fk, gh);
         }
         nm = fmaxf(0.f, -rho);
         am = fabsf(rho);

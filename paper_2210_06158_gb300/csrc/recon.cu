@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS
             float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
             const float4 pk = pp[k], rk = rt[k];
             const float cv = cov[k];
-            float4 s = __ldg(&color[f]);
+            float4 s = ld_img(color, f, S.gf16);
             float bx = pk.x, by = pk.y, bz = pk.z;
             if (cv > 0.f) {
                 float ic = 1.f / cv;

@@ -365,7 +365,11 @@ def gbuffer_struct(color, depth, normal=None) -> DofGBuffer:
     g.depth = depth.data_ptr()
     g.normal = normal.data_ptr() if normal is not None else None
     g.height, g.width = int(depth.shape[0]), int(depth.shape[1])
-    g.fmt = 0
+    # half colour / normal planes: DOF_FMT_F16 (both planes in one format)
+    half = str(color.dtype) == "torch.float16"
+    if normal is not None and (str(normal.dtype) == "torch.float16") != half:
+        raise ValueError("gbuffer: colour and normal planes must share one precision")
+    g.fmt = 1 if half else 0
     return g
 
 

@@ -23,8 +23,10 @@ def _built():
     oracle.build()
 
 
-def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
-    """Frames 0..n-1 of workload w on both sides; asserts parity frame by frame."""
+def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3, gbuf_f16=False):
+    """Frames 0..n-1 of workload w on both sides; asserts parity frame by frame.
+    gbuf_f16: the kernels take colour and normal as half planes (DOF_FMT_F16) and the
+    oracle the same values widened to float."""
     params = dict(params or w.params)
     w.params = params
     osc = oracle.Scene(w.scene)
@@ -38,9 +40,13 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3):
     for k in range(n_frames):
         cam = w.camera(k)
         gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, params, w.W, w.H))
+        gb_dev = gb
+        if gbuf_f16:
+            gb_dev = dict(gb, color=gb["color"].astype(np.float16), normal=gb["normal"].astype(np.float16))
+            gb = dict(gb, color=gb_dev["color"].astype(np.float32), normal=gb_dev["normal"].astype(np.float32))
         hist0 = ohist.copy()
         ref = oracle.frame(osc, cam, params, w.W, w.H, gb, ohist)
-        got = gpu.frame(cam, gb)
+        got = gpu.frame(cam, gb_dev)
         # ray counts: equal except where the count is decided on a rounding tie (either
         # count is valid there); the oracle then reruns the frame with the kernel's
         # counts at those pixels, so everything downstream is compared in full
@@ -234,6 +240,15 @@ def test_frame_parity_bright_bokeh():
     assert fr["main_out"][..., 3].max() > 0.5          # bright taps reach the gather
     stats = run_sequence(w, 3)
     _print(stats, "bokeh")
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_frame_parity_half_gbuffer(mode):
+    """A G-buffer whose colour and normal planes are half precision (DOF_FMT_F16), in the
+    fixed and the adaptive ray mode (which reads the normals), 3 frames of the dolly."""
+    w = make_workload("c2", W=256, H=144, n_frames=3)
+    stats = run_sequence(w, 3, dict(w.params, ray_mode=mode, m=6), gbuf_f16=True)
+    _print(stats, f"c2-f16-gbuffer-mode{mode}")
 
 
 def test_frame_parity_ragged_dolly_with_history():
