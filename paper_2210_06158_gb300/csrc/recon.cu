@@ -201,6 +201,14 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ AS as_) {
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
     if (__ldg(&nrays[q]) <= 0) { st_img(out, q, make_float4(0.f, 0.f, 0.f, 0.f), p.f16); return; }
+    const float4 o = ld_img(med, q, p.f16);
+    const float b = fminf(fmaxf(__ldg(&var_blur[q]) * p.var_w_recon, 0.f), p.b_max);
+    // Eq. 5 blends by b: below 2^-24 the filtered term changes the result by less than
+    // the rounding of the 81-tap sum itself, so the taps are not taken
+    if (!(b >= 5.9604645e-8f)) {
+        st_img(out, q, make_float4(o.x + 0.f, o.y + 0.f, o.z + 0.f, o.w + 0.f), p.f16);
+        return;
+    }
     float R = __ldg(&ct[q]);
     float lod = fminf(fmaxf(R * p.lod_scale, 0.f), p.lod_max);
     int l0 = (int)floorf(lod);
@@ -216,8 +224,6 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ AS as_) {
         if (interior) recon_taps<false, false>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
         else recon_taps<true, false>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
     }
-    float4 o = ld_img(med, q, p.f16);
-    float b = fminf(fmaxf(__ldg(&var_blur[q]) * p.var_w_recon, 0.f), p.b_max);
     float4 f = den > 0.f ? f4scale(1.f / den, num) : o;
     st_img(out, q, make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b)), p.f16);
 }
