@@ -173,6 +173,77 @@ __global__ void __launch_bounds__(256) k_main_filter(const __grid_constant__ AS 
     st_img(out, q, make_float4(ax * r, ay * r, az * r, bright * r), p.f16);
 }
 
+// A4 with the block's neighbourhood staged in shared memory: the block's 32x8 pixels
+// plus a halo of h = ceil(rmax) + 2 on every side, of the prefiltered colour and of z,
+// loaded once with indices clamped to the image.  Every tap then reads the tile, which
+// holds exactly the clamped values the other form reads through L1, in the same order,
+// so the two forms give the same bits.
+constexpr int kMainTileMaxBytes = 64 * 1024;
+
+__host__ __device__ inline int main_tile_halo(float rmax_hpx) { return (int)ceilf(rmax_hpx) + 2; }
+__host__ __device__ inline int main_tile_bytes(float rmax_hpx) {
+    const int h = main_tile_halo(rmax_hpx);
+    return (32 + 2 * h) * (8 + 2 * h) * (int)(sizeof(float4) + sizeof(float));
+}
+
+template <class AS>
+__global__ void __launch_bounds__(256) k_main_filter_tiled(const __grid_constant__ AS as_) {
+    extern __shared__ float4 sm_pre[];
+    const BatchArgs &A = batch_args(as_);
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const DevParams &p = S.p;
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float4 *__restrict__ pre = S.pre;
+    const float *__restrict__ z_h = S.z_h;
+    const float2 *__restrict__ dil = S.tiles_dil;
+    float4 *out = S.main_;
+    const int h = main_tile_halo(p.rmax_hpx);
+    const int tw = 32 + 2 * h, th = 8 + 2 * h;
+    float *sm_z = reinterpret_cast<float *>(sm_pre + tw * th);
+    const int ox = i - (int)threadIdx.x - h, oy = j - (int)threadIdx.y - h;
+    for (int e = threadIdx.y * 32 + threadIdx.x; e < tw * th; e += 256) {
+        const int ty = e / tw, tx = e - ty * tw;
+        const int x = min(max(ox + tx, 0), W2 - 1), y = min(max(oy + ty, 0), H2 - 1);
+        const size_t g = (size_t)y * W2 + x;
+        sm_pre[e] = __ldg(&pre[g]);
+        sm_z[e] = __ldg(&z_h[g]);
+    }
+    __syncthreads();
+    if (i >= W2 || j >= H2) return;
+    const size_t q = (size_t)j * W2 + i;
+    const float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
+    const float z0 = __ldg(&z_h[q]);
+    const float r0 = fabsf(__ldg(&pre[q]).w);
+    const float kInvSqrtPi = 0.56418958354775628f, kInvPi = 0.31830988618379067f;
+    float ax = 0.f, ay = 0.f, az = 0.f, bright = 0.f, wsum = 0.f;
+#pragma unroll 3
+    for (int t = 0; t < 81; t++) {
+        const float3 u = c_ring81[t];
+        const float dist = u.z * R;
+        const float x = i + dist * u.x, y = j + dist * u.y;
+        const float xf = floorf(x), yf = floorf(y);
+        const float fx = x - xf, fy = y - yf;
+        const int b = ((int)yf - oy) * tw + ((int)xf - ox);
+        const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+        const float4 s = f4fma(w11, sm_pre[b + tw + 1], f4fma(w01, sm_pre[b + tw], f4fma(w10, sm_pre[b + 1],
+                               f4scale(w00, sm_pre[b]))));
+        const float zi = w00 * sm_z[b] + w10 * sm_z[b + 1] + w01 * sm_z[b + tw] + w11 * sm_z[b + tw + 1];
+        const float ri = fabsf(s.w);
+        const float wf = sat((z0 - zi) * p.inv_depth_range);
+        const float rr = fmaxf(ri, kInvSqrtPi);
+        const float a = __fdividef(kInvPi, rr * rr);
+        const float Df = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
+        const float Db = sat((fminf(ri, r0) - dist) * p.inv_cover_ramp + 0.5f);
+        const float W = (wf * Df + (1.f - wf) * Db) * a;
+        ax += W * s.x; ay += W * s.y; az += W * s.z;
+        bright += W * sat((lum709(s.x, s.y, s.z) - p.bright_lum) * p.inv_bright_ramp);
+        wsum += W;
+    }
+    const float r = 1.f / wsum;
+    st_img(out, q, make_float4(ax * r, ay * r, az * r, bright * r), p.f16);
+}
+
 // A5: per-channel 3x3 median (clamp-to-edge)
 template <class AS>
 __global__ void k_median_pp(const __grid_constant__ AS as_) {
@@ -216,7 +287,19 @@ void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *
     const int n = A.ns;
     k_prefilter<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_PREFILTER, st);
-    k_main_filter<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+    // the shared-memory form when every session's halo tile fits
+    int tile_bytes = 0;
+    for (int s = 0; s < n; s++) tile_bytes = max(tile_bytes, main_tile_bytes(A.s[s].p.rmax_hpx));
+    if (tile_bytes <= kMainTileMaxBytes) {
+        static bool attr_set = false;    // per argument form (one instantiation each)
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_main_filter_tiled<AS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMainTileMaxBytes);
+            attr_set = true;
+        }
+        k_main_filter_tiled<AS><<<A.start[SH_HPX][n], dim3(32, 8), tile_bytes, st>>>(as);
+    } else {
+        k_main_filter<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+    }
     tmark(tm, DOF_K_MAIN, st);
     k_median_pp<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_MEDIAN_PP, st);
