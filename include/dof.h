@@ -298,8 +298,9 @@ int dof_batch_frame(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, void *stre
  * parameters, G-buffer and output pointers may change between launches.
  *   dof_graph_create: validates `reqs` as dof_batch_frame and captures (nothing runs,
  *     the histories do not advance).  The graph keeps the histories and their order,
- *     the launch shapes (sizes, ray modes, spp / m, tree kinds) and the context's tracer
- *     options of that moment.
+ *     the launch shapes (sizes, ray modes, spp / m, tree kinds, the main filter's
+ *     shared-memory tile, which follows max_coc_px) and the context's tracer options of
+ *     that moment.
  *   dof_graph_launch: one step, results identical to dof_batch_frame on the same
  *     requests.  DOF_ERR_MISMATCH if the requests need other launch shapes or other
  *     histories than the capture.  Launches of one graph on different streams are

@@ -793,6 +793,7 @@ struct DofGraph {
     int start[SH_COUNT][kMaxBatch + 1];
     bool adaptive, wide;
     int trace_blocks, refill_idle, steps_per_round;
+    int main_tile;                // the main filter's shared-memory bytes (0: through L1)
     BatchArgs *d_args;            // read by the captured kernels
     BatchArgs *h_stage;           // pinned source of the captured copy
     cudaEvent_t staged;           // recorded after the copy: the staging buffer may be rewritten
@@ -833,6 +834,7 @@ extern "C" int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n
     g->adaptive = adaptive;
     g->wide = all_wide(A);
     g->trace_blocks = ctx->sm_count * ctx->trace_blocks_per_sm;
+    g->main_tile = main_filter_tile_bytes(A);
     g->refill_idle = A.refill_idle;
     g->steps_per_round = A.steps_per_round;
     cudaGetLastError();
@@ -881,7 +883,7 @@ extern "C" int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n
     int rc = build_batch(ctx, reqs, n, A, adaptive);
     if (rc) return rc;
     if (memcmp(A.start, g->start, sizeof(A.start)) != 0 || adaptive != g->adaptive || all_wide(A) != g->wide ||
-        ctx->sm_count * ctx->trace_blocks_per_sm != g->trace_blocks)
+        ctx->sm_count * ctx->trace_blocks_per_sm != g->trace_blocks || main_filter_tile_bytes(A) != g->main_tile)
         return dof_set_error(DOF_ERR_MISMATCH, "dof_graph_launch: launch shapes differ from the captured step");
     // the kernels' scheduling knobs come from the staged copy; keep the captured ones
     A.refill_idle = g->refill_idle;

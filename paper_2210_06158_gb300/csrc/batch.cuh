@@ -100,6 +100,7 @@ __device__ __forceinline__ const BatchArgs &batch_args(const BatchArgs *a) { ret
 // pointer to a copy of it)
 template <class AS> void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A1, A2
 template <class AS> void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);     // A3 - A5
+int main_filter_tile_bytes(const BatchArgs &A);   // the main filter's launch form (post.cu)
 template <class AS>
 void launch_mask_b(const BatchArgs &A, const AS &as, bool any_adaptive, cudaStream_t st, DofHistory *timing);
 template <class AS> void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t st, DofHistory *timing);

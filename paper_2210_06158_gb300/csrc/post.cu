@@ -282,15 +282,22 @@ void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistor
     tmark(tm, DOF_K_DILATE, st);
 }
 
+// Dynamic shared memory of the main filter's staged form for this batch, or 0 when a
+// session's halo tile does not fit (the form through L1 runs then).
+int main_filter_tile_bytes(const BatchArgs &A) {
+    int bytes = 0;
+    for (int s = 0; s < A.ns; s++) bytes = max(bytes, main_tile_bytes(A.s[s].p.rmax_hpx));
+    return bytes <= kMainTileMaxBytes ? bytes : 0;
+}
+
 template <class AS>
 void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     k_prefilter<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_PREFILTER, st);
     // the shared-memory form when every session's halo tile fits
-    int tile_bytes = 0;
-    for (int s = 0; s < n; s++) tile_bytes = max(tile_bytes, main_tile_bytes(A.s[s].p.rmax_hpx));
-    if (tile_bytes <= kMainTileMaxBytes) {
+    const int tile_bytes = main_filter_tile_bytes(A);
+    if (tile_bytes > 0) {
         static bool attr_set = false;    // per argument form (one instantiation each)
         if (!attr_set) {
             cudaFuncSetAttribute(k_main_filter_tiled<AS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMainTileMaxBytes);

@@ -468,6 +468,11 @@ def test_graph_equals_batch():
         graph.launch(items(0, "hb"))                    # not the captured histories
     with pytest.raises(dof.DofError):
         graph.launch(items(0, "hg")[:2])                # fewer sessions
+    wider = items(0, "hg")
+    for it in wider:
+        it["params"] = dict(it["params"], max_coc_px=2.0 * float(it["params"]["max_coc_px"]))
+    with pytest.raises(dof.DofError):
+        graph.launch(wider)                             # another main-filter tile (halo follows max_coc_px)
     graph.close()
 
 
