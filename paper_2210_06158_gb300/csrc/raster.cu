@@ -15,6 +15,8 @@
 // cut into chunks of kChunkPx pixels that persistent blocks claim from a counter.
 #include "geometry.cuh"
 
+#include <algorithm>
+
 namespace {
 
 constexpr int kSmallPx = 4096;       // candidate pixels above which a triangle is queued
@@ -201,13 +203,18 @@ struct SmallSlot {               // one triangle of a warp's list (112 bytes)
 };
 
 // Setup of every triangle; the small ones are rasterised here, the others queued.
-__global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDev sc, int n_tot,
+// `split` warps serve each group of 32 triangles (each sets the group up and takes every
+// split-th stretch of 32 of its candidate pixels), so that scenes with few triangles
+// still occupy the GPU.
+__global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDev sc, int n_tot, int split,
                                                               unsigned long long *keys, BigTri *big,
                                                               uint32_t *n_big) {
     __shared__ SmallSlot slot[kRastThreads];
     __shared__ int excl[kRastThreads];
     const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-    const int k = blockIdx.x * kRastThreads + threadIdx.x;
+    const int gw = blockIdx.x * (kRastThreads / 32) + (threadIdx.x >> 5);
+    const int part = gw % split;
+    const int k = (gw / split) * 32 + lane;
     int npx = 0;
     if (k < n_tot) {
         const float4 *tp = sc.tris + 3 * (size_t)k;
@@ -217,15 +224,17 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDe
             const int bw = S.i1 - S.i0 + 1, bh = S.j1 - S.j0 + 1;
             const long long n = (long long)bw * bh;
             if (n > kSmallPx) {
-                const uint32_t b = atomicAdd(n_big, 1u);
-                BigTri B;
-                B.e0 = make_float4(S.e[0], S.e[1], S.e[2], 0.f);
-                B.e1 = make_float4(S.e[3], S.e[4], S.e[5], 0.f);
-                B.e2 = make_float4(S.e[6], S.e[7], S.e[8], 0.f);
-                B.box = make_int4(S.i0, S.j0, bw, (int)n);
-                B.k = k;
-                B.pad[0] = B.pad[1] = B.pad[2] = 0;
-                big[b] = B;
+                if (part == 0) {                     // the group's first warp queues it
+                    const uint32_t b = atomicAdd(n_big, 1u);
+                    BigTri B;
+                    B.e0 = make_float4(S.e[0], S.e[1], S.e[2], 0.f);
+                    B.e1 = make_float4(S.e[3], S.e[4], S.e[5], 0.f);
+                    B.e2 = make_float4(S.e[6], S.e[7], S.e[8], 0.f);
+                    B.box = make_int4(S.i0, S.j0, bw, (int)n);
+                    B.k = k;
+                    B.pad[0] = B.pad[1] = B.pad[2] = 0;
+                    big[b] = B;
+                }
             } else {
                 npx = (int)n;
                 SmallSlot &o = slot[threadIdx.x];
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDe
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     excl[threadIdx.x] = incl - npx;
     __syncwarp();
-    for (int w = lane; w < total; w += 32) {
+    for (int w = lane + 32 * part; w < total; w += 32 * split) {
         // owner: the last triangle whose list starts at or before w (it has pixels)
         int l = 0;
 #pragma unroll
@@ -415,8 +424,12 @@ cudaError_t launch_raster(const DevCam &cam, const DevParams &p, const SceneDev 
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 16, st);
     if (e != cudaSuccess) return e;
     if (n_tot > 0) {
-        k_rast_small<<<(n_tot + kRastThreads - 1) / kRastThreads, kRastThreads, 0, st>>>(cam, sc, n_tot, keys, big,
-                                                                                        counters);
+        // at least 32 warps per SM: groups of 32 triangles are split over several warps
+        const int groups = (n_tot + 31) / 32;
+        const int split = std::min(16, std::max(1, (32 * sm_count + groups - 1) / groups));
+        const int warps = groups * split;
+        k_rast_small<<<(warps + kRastThreads / 32 - 1) / (kRastThreads / 32), kRastThreads, 0, st>>>(
+            cam, sc, n_tot, split, keys, big, counters);
         k_big_chunks<<<1, 1024, 0, st>>>(big, counters, chunk_start, counters + 1);
         k_rast_big<<<4 * sm_count, kRastThreads, 0, st>>>(cam, sc, keys, big, counters, chunk_start, counters + 1,
                                                          counters + 2);
