@@ -473,9 +473,10 @@ def run_ours(args, rank, world):
                            l2=f"inputs larger than L2: {CYCLE} distinct G-buffers cycled "
                               f"({CYCLE} x {w.W * w.H * 20 / 1e6:.0f} MB)"),
                roofline=roof, e2e=e2e, fp16_storage=fp16,
-               # per frame: reset, 5 post-process, mask, trace, shade, 2 temporal, RT median, 4 mip,
-               # recon, composite (+ 2 edge kernels in adaptive mode)
-               gpu_launches=(18 + (2 if int(prm["ray_mode"]) == 1 else 0) + (1 if args.taa else 0)) * args.steps,
+               # per frame: reset, 5 post-process, mask, trace, shade, accumulation, the fused RT
+               # resolve (variance blur, RT median, mip level 0), 3 mip levels, recon, composite
+               # (+ 2 edge kernels in adaptive mode, + the final TAA)
+               gpu_launches=(16 + (2 if int(prm["ray_mode"]) == 1 else 0) + (1 if args.taa else 0)) * args.steps,
                clocks=clocks, kernel_ms=kern,
                image_passes={"streaming": {"kernels": STREAMING, "ms": round(img_ms, 4),
                                            "gbs": round(img_bytes / (img_ms * 1e-3) / 1e9, 1),
@@ -609,7 +610,7 @@ def run_batch(args):
                 batched_fp16_form=dict(frames_per_s=round(res["batched_fp16"]["frames_per_s"], 2),
                                        ms_per_step=round(res["batched_fp16"]["ms_per_step"], 3),
                                        note="FP16 storage of the colour image buffers, FP32 arithmetic"),
-                gpu_launches=18 * args.steps, clocks=res["batched"]["clocks"])
+                gpu_launches=16 * args.steps, clocks=res["batched"]["clocks"])
     return line
 
 
