@@ -314,10 +314,12 @@ def run_ours(args, rank, world):
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")      # profilers select the timed frames by this range
+        launches0 = dof.launch_count()           # the library's own tally of enqueued kernels
         e_start.record(stream)
         for s in range(args.warmup, args.warmup + args.steps):
             step(s, hist)
         e_end.record(stream)
+        launches = dof.launch_count() - launches0
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     if dist:
@@ -473,10 +475,10 @@ def run_ours(args, rank, world):
                            l2=f"inputs larger than L2: {CYCLE} distinct G-buffers cycled "
                               f"({CYCLE} x {w.W * w.H * 20 / 1e6:.0f} MB)"),
                roofline=roof, e2e=e2e, fp16_storage=fp16,
-               # per frame: reset, 5 post-process, mask, trace, shade, accumulation, the fused RT
-               # resolve (variance blur, RT median, mip level 0), 3 mip levels, recon, composite
-               # (+ 2 edge kernels in adaptive mode, + the final TAA)
-               gpu_launches=(16 + (2 if int(prm["ray_mode"]) == 1 else 0) + (1 if args.taa else 0)) * args.steps,
+               # counted by the library over the timed steps: per frame reset, 5 post-process,
+               # mask, trace, shade, accumulation, the fused RT resolve, 3 mip levels, recon,
+               # composite (+ 2 edge kernels in adaptive mode, + the final TAA)
+               gpu_launches=int(launches),
                clocks=clocks, kernel_ms=kern,
                image_passes={"streaming": {"kernels": STREAMING, "ms": round(img_ms, 4),
                                            "gbs": round(img_bytes / (img_ms * 1e-3) / 1e9, 1),
@@ -585,14 +587,16 @@ def run_batch(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(0) as clk:
+            l0 = dof.launch_count()
             e0.record()
             for k in range(args.warmup, args.warmup + args.steps):
                 fn(k)
             e1.record()
             torch.cuda.synchronize()
+            nl = dof.launch_count() - l0
         ms = e0.elapsed_time(e1)
         res[name] = dict(ms_per_step=ms / args.steps, frames_per_s=len(S) * args.steps / (ms / 1e3),
-                         clocks=clk.summary())
+                         clocks=clk.summary(), launches=int(nl))
     line = dict(metric=METRIC, value=round(res["batched"]["frames_per_s"], 2), unit="frames/s", n_gpus=1,
                 steps=args.steps, warmup=args.warmup, ms_per_step=round(res["batched"]["ms_per_step"], 3),
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
@@ -610,7 +614,7 @@ def run_batch(args):
                 batched_fp16_form=dict(frames_per_s=round(res["batched_fp16"]["frames_per_s"], 2),
                                        ms_per_step=round(res["batched_fp16"]["ms_per_step"], 3),
                                        note="FP16 storage of the colour image buffers, FP32 arithmetic"),
-                gpu_launches=16 * args.steps, clocks=res["batched"]["clocks"])
+                gpu_launches=res["batched"]["launches"], clocks=res["batched"]["clocks"])
     return line
 
 

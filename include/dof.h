@@ -311,6 +311,11 @@ int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, DofGraph 
 int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n, void *stream);
 void dof_graph_destroy(DofGraph *g);
 
+/* Kernel launches this library has enqueued in this process so far (frame passes, the
+ * G-buffer producers and the allocation-free tile map; a replayed graph counts the
+ * kernels it holds; scene builds are not counted).  Host-side tally, no synchronisation. */
+unsigned long long dof_launch_count(void);
+
 /* Synchronise `stream` and report the last frame's counters and the device status. */
 int dof_frame_stats(DofHistory *hist, void *stream, DofFrameStats *out);
 

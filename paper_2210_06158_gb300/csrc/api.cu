@@ -17,6 +17,10 @@ int recon_init_tables();
 
 static thread_local char g_err[512] = "";
 
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches += n; }
+extern "C" unsigned long long dof_launch_count(void) { return (unsigned long long)g_launches.load(); }
+
 int dof_set_error(int code, const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -794,6 +798,7 @@ struct DofGraph {
     bool adaptive, wide;
     int trace_blocks, refill_idle, steps_per_round;
     int main_tile;                // the main filter's shared-memory bytes (0: through L1)
+    long long kernels;            // kernel launches in one replay
     BatchArgs *d_args;            // read by the captured kernels
     BatchArgs *h_stage;           // pinned source of the captured copy
     cudaEvent_t staged;           // recorded after the copy: the staging buffer may be rewritten
@@ -852,7 +857,11 @@ extern "C" int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n
         if (rc == DOF_OK) {
             cudaMemcpyAsync(g->d_args, g->h_stage, sizeof(BatchArgs), cudaMemcpyHostToDevice, cs);
             cudaEventRecordWithFlags(g->staged, cs, cudaEventRecordExternal);
+            // captured kernels run at each replay, not now: they are counted per launch
+            const long long before = g_launches.load();
             enqueue_step(ctx, A, dp, adaptive, cs, nullptr);
+            g->kernels = g_launches.load() - before;
+            g_launches -= g->kernels;
             cudaError_t e = cudaStreamEndCapture(cs, &graph);
             ck(e, "dof_graph_create: capture");
         }
@@ -897,6 +906,7 @@ extern "C" int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n
     if (g->launched && st != g->last) cudaStreamWaitEvent(st, g->done, 0);
     rc = dof_cuda_check(cudaGraphLaunch(g->exec, st), "dof_graph_launch");
     if (rc) return rc;
+    count_launches(g->kernels);
     cudaEventRecord(g->done, st);
     g->last = st;
     g->launched = true;

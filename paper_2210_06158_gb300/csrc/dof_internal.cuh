@@ -202,6 +202,10 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
                      const uint32_t *d_mat, int builder, int ploc_radius, cudaStream_t st);
 void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *color, float *depth,
                     float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st);
+// host-side tally of this library's kernel launches (dof_launch_count); each launch
+// wrapper adds the launches it enqueued
+void count_launches(long long n);
+
 // rasterising G-buffer producer (raster.cu)
 void launch_prim_index(const float4 *tris, int n, int32_t *prim_k, cudaStream_t st);
 size_t raster_scratch_bytes(int W, int H, int n_tot);

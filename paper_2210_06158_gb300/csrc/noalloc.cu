@@ -133,5 +133,6 @@ extern "C" int dof_coc_tiles_noalloc(const float *depth, uint32_t width, uint32_
     k_tiles_scratch<<<dim3(a.TW, a.TH), dim3(8, 8), 0, st>>>(a, depth, scratch);
     k_dilate_scratch<<<dim3((a.TW + 15) / 16, (a.TH + 15) / 16), dim3(16, 16), 0, st>>>(
         a, scratch, reinterpret_cast<float2 *>(tiles_dil));
+    count_launches(2);
     return dof_cuda_check(cudaGetLastError(), "dof_coc_tiles_noalloc launch");
 }

@@ -279,6 +279,7 @@ void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistor
     k_downscale_tiles<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
     tmark(tm, DOF_K_DOWNSCALE, st);
     k_tile_dilate<AS><<<A.start[SH_TILEDIL][n], dim3(16, 16), 0, st>>>(as);
+    count_launches(2);
     tmark(tm, DOF_K_DILATE, st);
 }
 
@@ -309,6 +310,7 @@ void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *
     }
     tmark(tm, DOF_K_MAIN, st);
     k_median_pp<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+    count_launches(3);
     tmark(tm, DOF_K_MEDIAN_PP, st);
 }
 

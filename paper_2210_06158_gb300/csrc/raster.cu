@@ -398,7 +398,10 @@ __global__ void k_prim_index(const float4 *tris, int n, int32_t *prim_k) {
 }  // namespace
 
 void launch_prim_index(const float4 *tris, int n, int32_t *prim_k, cudaStream_t st) {
-    if (n > 0) k_prim_index<<<(n + 255) / 256, 256, 0, st>>>(tris, n, prim_k);
+    if (n > 0) {
+        k_prim_index<<<(n + 255) / 256, 256, 0, st>>>(tris, n, prim_k);
+        count_launches(1);
+    }
 }
 
 // Scratch of one call, from the context's stream-ordered pool.
@@ -436,5 +439,6 @@ cudaError_t launch_raster(const DevCam &cam, const DevParams &p, const SceneDev 
     }
     dim3 b(32, 8), g((cam.W + 31) / 32, (cam.H + 7) / 8);
     k_rast_resolve<<<g, b, 0, st>>>(cam, p, sc, keys, prim_k, color, depth, normal, prim);
+    count_launches(n_tot > 0 ? 4 : 1);
     return cudaGetLastError();
 }

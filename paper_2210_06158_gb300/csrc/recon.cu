@@ -396,6 +396,7 @@ void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistor
     k_mip_down<3, AS><<<A.start[SH_MIP3][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MIPS, st);
     k_recon<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
+    count_launches(5);
     tmark(tm, DOF_K_RECON, st);
 }
 
@@ -408,6 +409,7 @@ void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHi
     bool any_taa = false;
     for (int i = 0; i < n; i++) any_taa |= A.s[i].taa != 0;
     if (any_taa) k_taa<AS><<<A.start[SH_FPX][n], b, 0, st>>>(as);
+    count_launches(any_taa ? 2 : 1);
     tmark(tm, DOF_K_TAA, st);
 }
 

@@ -173,6 +173,7 @@ template <class AS>
 void launch_temporal_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     k_accumulate<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+    count_launches(1);
     tmark(tm, DOF_K_ACCUM, st);
     // the variance blur runs fused with the RT median and mip level 0 (recon.cu)
     tmark(tm, DOF_K_VAR_BLUR, st);
@@ -192,7 +193,10 @@ __global__ void k_reset(const __grid_constant__ AS as_) {
 }
 
 template <class AS>
-void launch_reset_b(const BatchArgs &A, const AS &as, cudaStream_t st) { k_reset<AS><<<1, kMaxBatch, 0, st>>>(as); }
+void launch_reset_b(const BatchArgs &A, const AS &as, cudaStream_t st) {
+    k_reset<AS><<<1, kMaxBatch, 0, st>>>(as);
+    count_launches(1);
+}
 
 // the two argument forms: by value (a kernel parameter) and from device memory (graphs)
 template void launch_temporal_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t, DofHistory *);

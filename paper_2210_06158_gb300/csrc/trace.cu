@@ -596,6 +596,7 @@ void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *
                     float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st) {
     dim3 b(16, 8), g((cam.W + 15) / 16, (cam.H + 7) / 8);
     k_primary<<<g, b, 0, st>>>(cam, p, sc, color, depth, normal, prim, status);
+    count_launches(1);
 }
 
 template <class AS>
@@ -607,6 +608,7 @@ void launch_mask_b(const BatchArgs &A, const AS &as, bool any_adaptive, cudaStre
     }
     tmark(tm, DOF_K_EDGES, st);
     k_mask_compact<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+    count_launches(any_adaptive ? 3 : 1);
     tmark(tm, DOF_K_MASK, st);
 }
 
@@ -619,6 +621,7 @@ void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t s
     else k_trace_rays<false, AS><<<blocks, 128, 0, st>>>(as);
     tmark(tm, DOF_K_TRACE, st);
     k_shade<AS><<<A.start[SH_SHADE][A.ns], 128, 0, st>>>(as);
+    count_launches(2);
     tmark(tm, DOF_K_SHADE, st);
 }
 

@@ -108,6 +108,7 @@ _SIGS = {
     "dof_frame_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.POINTER(DofCamera), C.POINTER(DofParams), C.c_void_p, C.c_void_p, C.c_void_p]),
     "dof_frame_host_join": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dof_launch_count": (C.c_ulonglong, []),
     "dof_history_create": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                      C.POINTER(C.c_void_p)]),
     "dof_history_destroy": (None, [C.c_void_p]),
@@ -407,6 +408,11 @@ def frame_host(ctx: Context, scene: Scene, gbuf: dict, cam, params, hist: Histor
                                 _ptr(gbuf.get("normal")), C.byref(c), C.byref(p), hist.ptr, _ptr(out),
                                 _stream_ptr(stream)))
     return out
+
+
+def launch_count() -> int:
+    """Kernel launches the library has enqueued in this process (dof_launch_count)."""
+    return int(lib().dof_launch_count())
 
 
 def frame_host_join(hist: History, stream=None):

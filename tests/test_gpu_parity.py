@@ -601,3 +601,34 @@ def test_host_frames_equal_device_frames():
         torch.cuda.synchronize()
         for k in range(w.n_frames):
             assert torch.equal(outs[k].view(torch.int32), want[k].view(torch.int32)), (mode, k)
+
+
+def test_launch_count_per_frame():
+    """The library's own launch tally (dof_launch_count): 16 kernels per frame, +2 for the
+    edge measure in the adaptive mode, +1 for the final TAA; a replayed graph counts the
+    kernels it holds."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    w = make_workload("c1", W=128, H=72)
+    ctx = dof.Context(0)
+    sc = dof.Scene(ctx, w.scene)
+    g = dof.gbuffer(ctx, sc, w.camera(0), w.params, w.W, w.H)
+    for over, taa, want in ((dict(ray_mode=0), False, 16), (dict(ray_mode=1, m=4), False, 18),
+                            (dict(ray_mode=0, taa_alpha=0.1), True, 17)):
+        prm = dict(w.params, **over)
+        h = dof.History(ctx, w.W, w.H, max_rays=oracle.max_rays(prm), taa=taa)
+        dof.frame(ctx, sc, g, w.camera(0), prm, h)
+        n0 = dof.launch_count()
+        for _ in range(3):
+            dof.frame(ctx, sc, g, w.camera(0), prm, h)
+        assert dof.launch_count() - n0 == 3 * want, (over, dof.launch_count() - n0)
+    h = dof.History(ctx, w.W, w.H, max_rays=1)
+    items = [dict(scene=sc, gbuf=g, cam=w.camera(0), params=w.params, hist=h)]
+    n0 = dof.launch_count()
+    graph = dof.Graph(ctx, items)
+    assert dof.launch_count() == n0                 # capturing runs nothing
+    graph.launch(items)
+    graph.launch(items)
+    torch.cuda.synchronize()
+    assert dof.launch_count() - n0 == 2 * 16
+    graph.close()
