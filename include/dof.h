@@ -10,8 +10,9 @@
  * reconstruction of the ray-traced layer, and the CoC-driven composite.
  *
  * Conventions
- *  - All image pointers are DEVICE pointers owned by the caller, row-major and
- *    densely packed (row pitch = width * element size) unless a pitch is given.
+ *  - Image pointers are DEVICE pointers owned by the caller (dof_frame_host: HOST
+ *    pointers), row-major and densely packed (row pitch = width * element size; no
+ *    other pitch is supported).
  *  - Scene geometry passed to dof_scene_upload is in HOST memory and is copied.
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *    Calls enqueue work on it and return without synchronising, except where stated.
