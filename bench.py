@@ -476,7 +476,7 @@ def run_ours(args, rank, world):
                               f"({CYCLE} x {w.W * w.H * 20 / 1e6:.0f} MB)"),
                roofline=roof, e2e=e2e, fp16_storage=fp16,
                # counted by the library over the timed steps: per frame reset, 5 post-process,
-               # mask, trace, shade, accumulation, the fused RT resolve, 3 mip levels, recon,
+               # mask, trace, shade, accumulation, the fused RT resolve, mip levels 1-3, recon,
                # composite (+ 2 edge kernels in adaptive mode, + the final TAA)
                gpu_launches=int(launches),
                clocks=clocks, kernel_ms=kern,

@@ -94,30 +94,81 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
     S.mip1[0][q] = make_float2(vv * __ldg(&S.ct[q]), vv);
 }
 
-// 2x2 box average (clamp-to-edge for odd sizes)
-template <int LEVEL, class AS>
-__global__ void k_mip_down(const __grid_constant__ AS as_) {
+// Mip levels 1-3 in one pass: a block computes 32x8 texels of level 1 from level 0,
+// then the 16x4 of level 2 and the 8x2 of level 3 they cover, from the values it keeps
+// in shared memory exactly as they are stored (FP16 storage rounds them), with the
+// same sums in the same order as one 2x2 box average per level.
+template <class AS>
+__global__ void __launch_bounds__(256) k_mips(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
-    const SessDesc &S = block_session(A, SH_MIP1 + LEVEL - 1, i, j);
-    const int w = S.mip_w[LEVEL - 1], h = S.mip_h[LEVEL - 1], wn = S.mip_w[LEVEL], hn = S.mip_h[LEVEL];
-    const float4 *__restrict__ s0 = S.mip0[LEVEL - 1];
-    const float2 *__restrict__ s1 = S.mip1[LEVEL - 1];
-    float4 *d0 = S.mip0[LEVEL];
-    float2 *d1 = S.mip1[LEVEL];
-    if (LEVEL >= S.mip_L || i >= wn || j >= hn) return;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 b = make_float2(0.f, 0.f);
+    const SessDesc &S = block_session(A, SH_MIP1, i, j);
+    const bool hs = S.p.f16;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int bx = i - tx, by = j - ty;            // block origin at level 1
+    __shared__ float4 l1a[8][32], l2a[4][16];
+    __shared__ float2 l1b[8][32], l2b[4][16];
+    // level 1 from level 0 (global)
+    if (1 < S.mip_L && i < S.mip_w[1] && j < S.mip_h[1]) {
+        const int w = S.mip_w[0], h = S.mip_h[0];
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 b = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int t = 0; t < 4; t++) {
-        int x = min(2 * i + (t & 1), w - 1), y = min(2 * j + (t >> 1), h - 1);
-        size_t q = (size_t)y * w + x;
-        a = f4add(a, ld_img(s0, q, S.p.f16));
-        float2 c = __ldg(&s1[q]);
-        b.x += c.x; b.y += c.y;
+        for (int t = 0; t < 4; t++) {
+            const int x = min(2 * i + (t & 1), w - 1), y = min(2 * j + (t >> 1), h - 1);
+            const size_t q = (size_t)y * w + x;
+            a = f4add(a, ld_img(S.mip0[0], q, hs));
+            const float2 c = __ldg(&S.mip1[0][q]);
+            b.x += c.x; b.y += c.y;
+        }
+        const float4 v = f4scale(0.25f, a);
+        const float2 u = make_float2(0.25f * b.x, 0.25f * b.y);
+        const size_t o = (size_t)j * S.mip_w[1] + i;
+        st_img(S.mip0[1], o, v, hs);
+        S.mip1[1][o] = u;
+        l1a[ty][tx] = round_img(v, hs);
+        l1b[ty][tx] = u;
     }
-    st_img(d0, (size_t)j * wn + i, f4scale(0.25f, a), S.p.f16);
-    d1[(size_t)j * wn + i] = make_float2(0.25f * b.x, 0.25f * b.y);
+    __syncthreads();
+    // level 2 from the block's level-1 texels
+    const int i2 = bx / 2 + tx, j2 = by / 2 + ty;
+    if (tx < 16 && ty < 4 && 2 < S.mip_L && i2 < S.mip_w[2] && j2 < S.mip_h[2]) {
+        const int w = S.mip_w[1], h = S.mip_h[1];
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 b = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int x = min(2 * i2 + (t & 1), w - 1) - bx, y = min(2 * j2 + (t >> 1), h - 1) - by;
+            a = f4add(a, l1a[y][x]);
+            const float2 c = l1b[y][x];
+            b.x += c.x; b.y += c.y;
+        }
+        const float4 v = f4scale(0.25f, a);
+        const float2 u = make_float2(0.25f * b.x, 0.25f * b.y);
+        const size_t o = (size_t)j2 * S.mip_w[2] + i2;
+        st_img(S.mip0[2], o, v, hs);
+        S.mip1[2][o] = u;
+        l2a[ty][tx] = round_img(v, hs);
+        l2b[ty][tx] = u;
+    }
+    __syncthreads();
+    // level 3 from the block's level-2 texels
+    const int i3 = bx / 4 + tx, j3 = by / 4 + ty;
+    if (tx < 8 && ty < 2 && 3 < S.mip_L && i3 < S.mip_w[3] && j3 < S.mip_h[3]) {
+        const int w = S.mip_w[2], h = S.mip_h[2];
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 b = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int x = min(2 * i3 + (t & 1), w - 1) - bx / 2, y = min(2 * j3 + (t >> 1), h - 1) - by / 2;
+            a = f4add(a, l2a[y][x]);
+            const float2 c = l2b[y][x];
+            b.x += c.x; b.y += c.y;
+        }
+        const size_t o = (size_t)j3 * S.mip_w[3] + i3;
+        st_img(S.mip0[3], o, f4scale(0.25f, a), hs);
+        S.mip1[3][o] = make_float2(0.25f * b.x, 0.25f * b.y);
+    }
 }
 
 struct Mips {
@@ -391,12 +442,10 @@ void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistor
     dim3 b(32, 8);
     k_resolve_rt<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MEDIAN_RT, st);
-    k_mip_down<1, AS><<<A.start[SH_MIP1][n], b, 0, st>>>(as);
-    k_mip_down<2, AS><<<A.start[SH_MIP2][n], b, 0, st>>>(as);
-    k_mip_down<3, AS><<<A.start[SH_MIP3][n], b, 0, st>>>(as);
+    k_mips<AS><<<A.start[SH_MIP1][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MIPS, st);
     k_recon<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
-    count_launches(5);
+    count_launches(3);
     tmark(tm, DOF_K_RECON, st);
 }
 

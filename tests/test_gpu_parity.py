@@ -604,7 +604,7 @@ def test_host_frames_equal_device_frames():
 
 
 def test_launch_count_per_frame():
-    """The library's own launch tally (dof_launch_count): 16 kernels per frame, +2 for the
+    """The library's own launch tally (dof_launch_count): 14 kernels per frame, +2 for the
     edge measure in the adaptive mode, +1 for the final TAA; a replayed graph counts the
     kernels it holds."""
     from paper_2210_06158_gb300 import dof
@@ -613,8 +613,8 @@ def test_launch_count_per_frame():
     ctx = dof.Context(0)
     sc = dof.Scene(ctx, w.scene)
     g = dof.gbuffer(ctx, sc, w.camera(0), w.params, w.W, w.H)
-    for over, taa, want in ((dict(ray_mode=0), False, 16), (dict(ray_mode=1, m=4), False, 18),
-                            (dict(ray_mode=0, taa_alpha=0.1), True, 17)):
+    for over, taa, want in ((dict(ray_mode=0), False, 14), (dict(ray_mode=1, m=4), False, 16),
+                            (dict(ray_mode=0, taa_alpha=0.1), True, 15)):
         prm = dict(w.params, **over)
         h = dof.History(ctx, w.W, w.H, max_rays=oracle.max_rays(prm), taa=taa)
         dof.frame(ctx, sc, g, w.camera(0), prm, h)
@@ -630,5 +630,5 @@ def test_launch_count_per_frame():
     graph.launch(items)
     graph.launch(items)
     torch.cuda.synchronize()
-    assert dof.launch_count() - n0 == 2 * 16
+    assert dof.launch_count() - n0 == 2 * 14
     graph.close()
