@@ -14,7 +14,8 @@ namespace {
 struct Ray {
     float3 o, d, inv;
     float3 oinv;        // o * inv (the fused slab test of the 4-wide tree)
-    int kx, ky, kz;
+    float3 off0, off1;  // o * inv moved outward per axis (the fused slab test of the binary tree)
+    int perm;           // 2 kz + (kx, ky swapped): the axis order of the watertight test
     float Sx, Sy, Sz;
 };
 
@@ -26,12 +27,25 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     auto safe = [](float x) { return fabsf(x) < 1e-30f ? copysignf(1e-30f, x) : x; };
     r.inv = make_float3(1.f / safe(d.x), 1.f / safe(d.y), 1.f / safe(d.z));
     r.oinv = make_float3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    // fma(lo, inv, -o inv) differs from (lo - o) inv by at most 2^-24 |o inv| from the
+    // rounding of o inv (the rest is relative to t); the offsets move each slab plane
+    // outward by 2^-22 |o inv|, which covers that and the rounding of the offset itself.
+    // The lo plane is the near one where inv >= 0, the far one where inv < 0.
+    auto out = [](float oi, float inv, float &o0, float &o1) {
+        const float e = fabsf(oi) * 2.38418579e-7f;
+        o0 = inv >= 0.f ? oi + e : oi - e;
+        o1 = inv >= 0.f ? oi - e : oi + e;
+    };
+    out(r.oinv.x, r.inv.x, r.off0.x, r.off1.x);
+    out(r.oinv.y, r.inv.y, r.off0.y, r.off1.y);
+    out(r.oinv.z, r.inv.z, r.off0.z, r.off1.z);
     float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
     int ky = kx == 2 ? 0 : kx + 1;
-    if (comp(d, kz) < 0.f) { int t = kx; kx = ky; ky = t; }
-    r.kx = kx; r.ky = ky; r.kz = kz;
+    const bool sw = comp(d, kz) < 0.f;
+    if (sw) { int t = kx; kx = ky; ky = t; }
+    r.perm = 2 * kz + (sw ? 1 : 0);
     float dz = comp(d, kz);
     r.Sx = comp(d, kx) / dz;
     r.Sy = comp(d, ky) / dz;
@@ -39,21 +53,32 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     return r;
 }
 
+template <int K> __device__ __forceinline__ float cmp3(float3 v) { return K == 0 ? v.x : (K == 1 ? v.y : v.z); }
+
 // Watertight ray/triangle test (Woop, Benthin and Wald, JCGT 2013): shear the
 // vertices into ray space, evaluate the three edge functions (without FMA
 // contraction, so a shared edge evaluates to exact negatives), double precision only
-// when an edge function is exactly zero.  Returns t > 0 or -1.
-__device__ __forceinline__ float tri_hit(const Ray &r, float4 v0, float4 v1, float4 v2) {
-    float3 A = make_float3(v0.x - r.o.x, v0.y - r.o.y, v0.z - r.o.z);
-    float3 B = make_float3(v1.x - r.o.x, v1.y - r.o.y, v1.z - r.o.z);
-    float3 C = make_float3(v2.x - r.o.x, v2.y - r.o.y, v2.z - r.o.z);
-    float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
-    float Ax = __fsub_rn(comp(A, r.kx), __fmul_rn(r.Sx, Akz));
-    float Ay = __fsub_rn(comp(A, r.ky), __fmul_rn(r.Sy, Akz));
-    float Bx = __fsub_rn(comp(B, r.kx), __fmul_rn(r.Sx, Bkz));
-    float By = __fsub_rn(comp(B, r.ky), __fmul_rn(r.Sy, Bkz));
-    float Cx = __fsub_rn(comp(C, r.kx), __fmul_rn(r.Sx, Ckz));
-    float Cy = __fsub_rn(comp(C, r.ky), __fmul_rn(r.Sy, Ckz));
+// when an edge function is exactly zero.  Returns t > 0 or -1.  The axis order is a
+// template argument (one instance per permutation), so no component is selected at
+// run time.  t = T / det is divided out only when it is positive and not certainly
+// beyond `tmax`: |T| > |det| tmax (1 + 2^-20), evaluated in FP32, implies
+// T / det > tmax (1 + 2^-21), which rounds above tmax, so a skipped triangle is one
+// that the caller's t <= tmax comparison would reject anyway.
+template <int KZ, bool SW>
+__device__ __forceinline__ float tri_hit_k(const Ray &r, float4 v0, float4 v1, float4 v2, float tmax) {
+    constexpr int KX0 = KZ == 2 ? 0 : KZ + 1;
+    constexpr int KY0 = KX0 == 2 ? 0 : KX0 + 1;
+    constexpr int KX = SW ? KY0 : KX0, KY = SW ? KX0 : KY0;
+    const float3 A = make_float3(v0.x - r.o.x, v0.y - r.o.y, v0.z - r.o.z);
+    const float3 B = make_float3(v1.x - r.o.x, v1.y - r.o.y, v1.z - r.o.z);
+    const float3 C = make_float3(v2.x - r.o.x, v2.y - r.o.y, v2.z - r.o.z);
+    const float Akz = cmp3<KZ>(A), Bkz = cmp3<KZ>(B), Ckz = cmp3<KZ>(C);
+    const float Ax = __fsub_rn(cmp3<KX>(A), __fmul_rn(r.Sx, Akz));
+    const float Ay = __fsub_rn(cmp3<KY>(A), __fmul_rn(r.Sy, Akz));
+    const float Bx = __fsub_rn(cmp3<KX>(B), __fmul_rn(r.Sx, Bkz));
+    const float By = __fsub_rn(cmp3<KY>(B), __fmul_rn(r.Sy, Bkz));
+    const float Cx = __fsub_rn(cmp3<KX>(C), __fmul_rn(r.Sx, Ckz));
+    const float Cy = __fsub_rn(cmp3<KY>(C), __fmul_rn(r.Sy, Ckz));
     float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
     float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
     float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -63,11 +88,24 @@ __device__ __forceinline__ float tri_hit(const Ray &r, float4 v0, float4 v1, flo
         W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
     }
     if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return -1.f;
-    float det = U + V + W;
+    const float det = U + V + W;
     if (det == 0.f) return -1.f;
-    float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
-    float t = T / det;
+    const float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+    if (det > 0.f ? T <= 0.f : T >= 0.f) return -1.f;           // t <= 0
+    if (fabsf(T) > fabsf(det) * tmax * 1.00000095f) return -1.f;  // t > tmax
+    const float t = T / det;
     return t > 0.f ? t : -1.f;
+}
+
+__device__ __forceinline__ float tri_hit(const Ray &r, float4 v0, float4 v1, float4 v2, float tmax = INFINITY) {
+    switch (r.perm) {
+    case 0: return tri_hit_k<0, false>(r, v0, v1, v2, tmax);
+    case 1: return tri_hit_k<0, true>(r, v0, v1, v2, tmax);
+    case 2: return tri_hit_k<1, false>(r, v0, v1, v2, tmax);
+    case 3: return tri_hit_k<1, true>(r, v0, v1, v2, tmax);
+    case 4: return tri_hit_k<2, false>(r, v0, v1, v2, tmax);
+    default: return tri_hit_k<2, true>(r, v0, v1, v2, tmax);
+    }
 }
 
 struct HitRec {

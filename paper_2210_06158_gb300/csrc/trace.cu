@@ -29,11 +29,13 @@ __device__ __forceinline__ void philox2(unsigned long long c0, unsigned long lon
     o0 = c0; o1 = c1;
 }
 
-// slab test, conservative by a few ulps so rounding never culls a hit on the surface
+// slab test, one fused multiply-add per plane: the ray's outward-moved offsets cover
+// the rounding of o * inv, and the relative slack on tmax the rest, so rounding never
+// culls a hit on the surface
 __device__ __forceinline__ bool box_hit(const Ray &r, float3 lo, float3 hi, float tbest, float &tent) {
-    float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
-    float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
-    float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
+    float tx0 = fmaf(lo.x, r.inv.x, -r.off0.x), tx1 = fmaf(hi.x, r.inv.x, -r.off1.x);
+    float ty0 = fmaf(lo.y, r.inv.y, -r.off0.y), ty1 = fmaf(hi.y, r.inv.y, -r.off1.y);
+    float tz0 = fmaf(lo.z, r.inv.z, -r.off0.z), tz1 = fmaf(hi.z, r.inv.z, -r.off1.z);
     float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
     float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tbest));
     tent = tmin;
@@ -70,7 +72,7 @@ __device__ __forceinline__ void cx_hit(float &ta, int &ra, float &tb, int &rb) {
 __device__ __forceinline__ void tri_update(const Ray &ray, const float4 *__restrict__ tris, int k, HitRec &h) {
     const float4 *tp = tris + 3 * (size_t)k;
     float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-    float t = tri_hit(ray, v0, v1, v2);
+    float t = tri_hit(ray, v0, v1, v2, h.t);
     if (t > 0.f) {
         int prim = __float_as_int(v0.w);
         if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
@@ -186,7 +188,7 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
         n_tests++;
         const float4 *tp = sc.tris + 3 * (size_t)k;
         float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-        float t = tri_hit(r, v0, v1, v2);
+        float t = tri_hit(r, v0, v1, v2, h.t);
         if (t > 0.f) {
             int prim = __float_as_int(v0.w);
             if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
     const BvhNode *nodes = nullptr;
     const Bvh4Node *nodes4 = nullptr;
     const float4 *tris = nullptr;
-    long long steps = 0, max_steps = 0;
+    uint32_t steps = 0, max_steps = 0;
     int stack[kStack];
     while (true) {
         unsigned idle = __ballot_sync(0xffffffffu, !have);
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
                     for (int k = n_tree; k < n_tree + S.sc.n_large; k++) {
                         n_tests++;
                         const float4 *tp = tris + 3 * (size_t)k;
-                        float t = tri_hit(ray, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
+                        float t = tri_hit(ray, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), h.t);
                         if (t > 0.f) {
                             int prim = __float_as_int(__ldg(tp).w);
                             if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
                     node = kWide ? S.sc.root4 : S.sc.root;
                     sp = 0;
                     steps = 0;
-                    max_steps = 4ll * n_tree + 64;
+                    max_steps = (uint32_t)min(4ll * n_tree + 64, 4294967295ll);
                     have = n_tree > 0;
                     if (!have) S.hits[r] = make_int2(h.k, __float_as_int(h.t));
                 }
