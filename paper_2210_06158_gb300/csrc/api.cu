@@ -384,9 +384,7 @@ extern "C" int dof_scene_info(const DofScene *s, DofSceneInfo *info) {
     return DOF_OK;
 }
 
-// `cam`: the rays' origins are within its lens (the 4-wide tree needs them within
-// kWideOriginMax of 0 on every axis)
-static SceneDev scene_dev(const DofScene *s, const DevCam &cam) {
+static SceneDev scene_dev(const DofScene *s) {
     SceneDev d;
     d.nodes = s->nodes;
     d.tris = s->tris;
@@ -394,9 +392,7 @@ static SceneDev scene_dev(const DofScene *s, const DevCam &cam) {
     d.n_large = (int)s->n_large;
     d.root = s->root;
     // the 4-wide tree, when its traversal stack bound (3 per level) fits
-    float om = fmaxf(fmaxf(fabsf(cam.O.x), fabsf(cam.O.y)), fabsf(cam.O.z)) + cam.lens_r;
-    bool wide = s->nodes4 && s->ctx->bvh_width == 4 && 3 * s->depth4 + 3 <= kTraversalStack &&
-                om <= 0.5f * kWideOriginMax;
+    bool wide = s->nodes4 && s->ctx->bvh_width == 4 && 3 * s->depth4 + 3 <= kTraversalStack;
     d.nodes4 = wide ? s->nodes4 : nullptr;
     d.root4 = s->root4;
     d.n_nodes4 = s->n_nodes4;
@@ -424,7 +420,7 @@ extern "C" int dof_gbuffer(DofCtx *ctx, const DofScene *scene, const DofCamera *
     rc = make_params(p, width, height, DOF_MAX_RAYS, dp);
     if (rc) return rc;
     cudaGetLastError();   // drop a stale error of an earlier call of another library on this thread
-    launch_primary(dc, dp, scene_dev(scene, dc), reinterpret_cast<float4 *>(color), depth,
+    launch_primary(dc, dp, scene_dev(scene), reinterpret_cast<float4 *>(color), depth,
                    reinterpret_cast<float4 *>(normal), prim, ctx->d_status, (cudaStream_t)stream);
     return dof_cuda_check(cudaGetLastError(), "dof_gbuffer launch");
 }
@@ -448,7 +444,7 @@ extern "C" int dof_gbuffer_raster(DofCtx *ctx, const DofScene *scene, const DofC
     if (rc) return rc;
     cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
-    const SceneDev sd = scene_dev(scene, dc);
+    const SceneDev sd = scene_dev(scene);
     const size_t bytes = raster_scratch_bytes((int)width, (int)height, (int)scene->n_tris);
     void *scratch = nullptr;
     rc = dof_cuda_check(cudaMallocFromPoolAsync(&scratch, bytes, ctx->pool, st), "dof_gbuffer_raster scratch");
@@ -631,7 +627,7 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
     if (rc) return rc;
     rc = make_params(r.params, h->W, h->H, h->max_rays, d.p);
     if (rc) return rc;
-    d.sc = scene_dev(scene, d.cam);
+    d.sc = scene_dev(scene);
     d.N = (int)h->N;
     d.max_rays = (int)h->max_rays;
     d.valid = h->valid;

@@ -323,7 +323,7 @@ __global__ void k_ploc_scatter(int count, const int *keep, const int *pos, const
 // Collapse of the binary tree into 4-wide nodes, top-down one level per launch:
 // a 4-wide node starts from the two children of its binary node and opens its
 // largest-area internal child until it holds four children (or only leaves).  The
-// stored child boxes are widened by kWideBoxPad for the fused slab test.
+// child boxes are stored as the binary tree holds them.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void bin_child(const BvhNode &nd, int c, float3 &lo, float3 &hi, int &ref) {
     if (c == 0) {
@@ -371,12 +371,12 @@ __global__ void k_collapse(const BvhNode *nodes, int n_bin, const int2 *fin, int
     int k = 0;
     for (int e = 0; e < 4; e++) {
         if (e < cnt) {
-            L[0][e] = __fsub_rd(lo[e].x, kWideBoxPad);
-            L[1][e] = __fsub_rd(lo[e].y, kWideBoxPad);
-            L[2][e] = __fsub_rd(lo[e].z, kWideBoxPad);
-            Hh[0][e] = __fadd_ru(hi[e].x, kWideBoxPad);
-            Hh[1][e] = __fadd_ru(hi[e].y, kWideBoxPad);
-            Hh[2][e] = __fadd_ru(hi[e].z, kWideBoxPad);
+            L[0][e] = lo[e].x;
+            L[1][e] = lo[e].y;
+            L[2][e] = lo[e].z;
+            Hh[0][e] = hi[e].x;
+            Hh[1][e] = hi[e].y;
+            Hh[2][e] = hi[e].z;
             if (ref[e] >= 0) {
                 R[e] = base + k;
                 fout[fo + k] = make_int2(base + k, ref[e]);

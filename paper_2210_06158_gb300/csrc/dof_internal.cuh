@@ -68,13 +68,6 @@ struct __align__(16) Bvh4Node {
     int4 pad;
 };
 constexpr int kEmptyChild = (int)0x80000000;
-// The 4-wide boxes are widened by kWideBoxPad (outward rounding), so that the slab
-// test may take the ray origin in the fused form lo * inv - o * inv: that equals the
-// exact slab of a ray whose origin moved by at most |o| 2^-24 per axis, which the pad
-// covers for origins within kWideOriginMax of 0 on every axis (2^10 * 2^-22 = 2^-12,
-// twice the bound).  Rays starting farther out traverse the binary tree.
-constexpr float kWideOriginMax = 1024.f;
-constexpr float kWideBoxPad = 2.44140625e-4f;
 
 struct SceneDev {
     const BvhNode *nodes;        // n_tris - 1 internal nodes (root = 0) when n_tris >= 2

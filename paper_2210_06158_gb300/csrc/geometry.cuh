@@ -13,8 +13,7 @@ namespace {
 // ---------------------------------------------------------------------------
 struct Ray {
     float3 o, d, inv;
-    float3 oinv;        // o * inv (the fused slab test of the 4-wide tree)
-    float3 off0, off1;  // o * inv moved outward per axis (the fused slab test of the binary tree)
+    float3 off0, off1;  // o * inv moved outward per axis (the fused slab test)
     int perm;           // 2 kz + (kx, ky swapped): the axis order of the watertight test
     float Sx, Sy, Sz;
 };
@@ -26,7 +25,6 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     r.o = o; r.d = d;
     auto safe = [](float x) { return fabsf(x) < 1e-30f ? copysignf(1e-30f, x) : x; };
     r.inv = make_float3(1.f / safe(d.x), 1.f / safe(d.y), 1.f / safe(d.z));
-    r.oinv = make_float3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
     // fma(lo, inv, -o inv) differs from (lo - o) inv by at most 2^-24 |o inv| from the
     // rounding of o inv (the rest is relative to t); the offsets move each slab plane
     // outward by 2^-22 |o inv|, which covers that and the rounding of the offset itself.
@@ -36,9 +34,9 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
         o0 = inv >= 0.f ? oi + e : oi - e;
         o1 = inv >= 0.f ? oi - e : oi + e;
     };
-    out(r.oinv.x, r.inv.x, r.off0.x, r.off1.x);
-    out(r.oinv.y, r.inv.y, r.off0.y, r.off1.y);
-    out(r.oinv.z, r.inv.z, r.off0.z, r.off1.z);
+    out(o.x * r.inv.x, r.inv.x, r.off0.x, r.off1.x);
+    out(o.y * r.inv.y, r.inv.y, r.off0.y, r.off1.y);
+    out(o.z * r.inv.z, r.inv.z, r.off0.z, r.off1.z);
     float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;

@@ -42,16 +42,10 @@ __device__ __forceinline__ bool box_hit(const Ray &r, float3 lo, float3 hi, floa
     return tmin <= tmax * 1.0000005f;
 }
 
-// slab test on a widened 4-wide box: one fused multiply-add per plane
+// the same slab test on one box of a 4-wide node (boxes stored per axis)
 __device__ __forceinline__ bool box_hit_w(const Ray &r, float lx, float ly, float lz, float hx, float hy, float hz,
                                           float tbest, float &tent) {
-    float tx0 = fmaf(lx, r.inv.x, -r.oinv.x), tx1 = fmaf(hx, r.inv.x, -r.oinv.x);
-    float ty0 = fmaf(ly, r.inv.y, -r.oinv.y), ty1 = fmaf(hy, r.inv.y, -r.oinv.y);
-    float tz0 = fmaf(lz, r.inv.z, -r.oinv.z), tz1 = fmaf(hz, r.inv.z, -r.oinv.z);
-    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
-    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tbest));
-    tent = tmin;
-    return tmin <= tmax * 1.0000005f;
+    return box_hit(r, make_float3(lx, ly, lz), make_float3(hx, hy, hz), tbest, tent);
 }
 
 
