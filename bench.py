@@ -50,10 +50,10 @@ FP32_LANES_PER_SM = 128
 # workload (profiles/top_kernels_*.md); a kernel or workload changed since then has no
 # entry.  The 4K tracer was captured at 1920x1080 (same scene, lens, 4 spp) and is
 # scaled by the rays of a full launch (6.73M / 1.78M).
-PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": 9.0e6, "k_trace_rays<0>": None, "k_recon": 25.4e6,
+PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_recon": 25.4e6,
                            "k_main_filter": 10.4e6, "k_accumulate": 55.8e6, "k_composite": 63.3e6,
                            "k_downscale_tiles": 41.6e6},
-                    "c3": {"k_trace_rays<0>": 21.7e6 * 6.73 / 1.78}}
+                    "c3": {"k_trace_rays<0>": None}}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
