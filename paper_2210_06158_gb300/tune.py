@@ -7,7 +7,11 @@ the speed of dof_frame, never its result (the closest hit does not depend on the
 tree's shape).
 `tune_trace` times a few frames of the caller's own session for each candidate
 (coordinate descent from the defaults, CUDA events on the session's stream) and
-leaves the fastest setting on the context.
+leaves the fastest setting on the context.  Every candidate is timed on the same
+frames (run_frame(0) .. run_frame(frames - 1), after one warm-up run_frame(0)), so a
+moving camera does not favour the settings that happened to get the cheaper frames;
+a candidate that beats the incumbent by more than 1% replaces it only if a second
+timing of both confirms it.
 """
 
 from __future__ import annotations
@@ -21,6 +25,19 @@ SPACE = {
 DEFAULT = {"bvh_width": 4, "blocks_per_sm": 8, "refill_idle": 16, "steps": 64}
 
 
+def _time_frames(run_frame, frames, st):
+    """Warm-up frame 0, then the CUDA-event time of frames 0 .. frames - 1 (ms per frame)."""
+    import torch
+    run_frame(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for f in range(frames):
+        run_frame(f)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / frames
+
+
 def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None):
     """run_frame(k) enqueues frame k of a representative session on `stream` (or the
     current stream).  Returns (best settings, {settings tuple: ms per frame})."""
@@ -28,24 +45,13 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream()
     best = dict(DEFAULT)
     seen = {}
-    k = 0
 
-    def measure(cfg):
-        nonlocal k
+    def measure(cfg, fresh=False):
         key = tuple(sorted(cfg.items()))
-        if key in seen:
+        if key in seen and not fresh:
             return seen[key]
         ctx.set_trace(**cfg)
-        run_frame(k)                               # warm-up with this setting
-        k += 1
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(frames):
-            run_frame(k)
-            k += 1
-        e1.record(st)
-        e1.synchronize()
-        seen[key] = e0.elapsed_time(e1) / frames
+        seen[key] = _time_frames(run_frame, frames, st)
         return seen[key]
 
     best_ms = measure(best)
@@ -56,7 +62,11 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None):
                 cand = dict(best, **{name: v})
                 ms = measure(cand)
                 if ms < best_ms * 0.99:
-                    best, best_ms, improved = cand, ms, True
+                    ms2, inc2 = measure(cand, fresh=True), measure(best, fresh=True)
+                    if ms2 < inc2 * 0.99:
+                        best, best_ms, improved = cand, ms2, True
+                    else:
+                        best_ms = inc2
         if not improved:
             break
     ctx.set_trace(**best)
@@ -77,22 +87,12 @@ def tune_scene(ctx, host_scene, run_frame, radii=None, widths=(4, 2), frames=4, 
     st = stream if stream is not None else torch.cuda.current_stream()
     best, best_ms, best_scene = None, float("inf"), None
     seen = {}
-    k = 0
     for r in (radii or SCENE_RADII):
         ctx.set_ploc_radius(r)
         sc = dof.Scene(ctx, host_scene)
         for wdt in widths:
             ctx.set_bvh_width(wdt)
-            run_frame(sc, k)
-            k += 1
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            for _ in range(frames):
-                run_frame(sc, k)
-                k += 1
-            e1.record(st)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1) / frames
+            ms = _time_frames(lambda f: run_frame(sc, f), frames, st)
             seen[(r, wdt)] = ms
             if ms < best_ms:
                 best_ms, best = ms, {"ploc_radius": r, "bvh_width": wdt}

@@ -114,3 +114,40 @@ def test_tune_scene_keeps_the_fastest_tree_and_closes_the_others(monkeypatch):
     assert len(made) == len(tune.SCENE_RADII) and len(closed) == len(made) - 1
     assert (ctx.radius, ctx.width) == (24, 2)
     assert set(seen) == {(r, w) for r in tune.SCENE_RADII for w in (4, 2)}
+
+
+def test_tune_trace_times_every_candidate_on_the_same_frames(monkeypatch):
+    """Frames of a moving camera differ in cost; each candidate must see the same ones."""
+    clock = _Clock()
+    _fake_cuda(monkeypatch, clock)
+    ctx = _Ctx()
+    calls = []
+
+    def run_frame(k):
+        calls.append(k)
+        clock.t += 1.0 + 0.1 * k       # later frames cost more
+
+    tune.tune_trace(ctx, run_frame, frames=3, stream=types.SimpleNamespace())
+    assert len(calls) % 4 == 0
+    for m in range(len(calls) // 4):
+        assert calls[4 * m:4 * m + 4] == [0, 0, 1, 2]   # warm-up, then frames 0 .. 2
+
+
+def test_tune_trace_rejects_a_win_that_a_second_timing_does_not_confirm(monkeypatch):
+    """A candidate that looks 5% faster once (noise) but not when timed again is not taken."""
+    clock = _Clock()
+    _fake_cuda(monkeypatch, clock)
+    ctx = _Ctx()
+    timed = {}
+
+    def run_frame(k):
+        key = tuple(sorted(ctx.cfg.items()))
+        if k == 0 and key not in timed:
+            timed[key] = 0
+        if k == 0:
+            timed[key] += 1
+        lucky = ctx.cfg["blocks_per_sm"] == 12 and timed[key] <= 2   # fast only on its first timing
+        clock.t += 0.95 if lucky else 1.0
+
+    best, _ = tune.tune_trace(ctx, run_frame, frames=2, stream=types.SimpleNamespace())
+    assert best == tune.DEFAULT
