@@ -171,58 +171,74 @@ __global__ void __launch_bounds__(256) k_mips(const __grid_constant__ AS as_) {
     }
 }
 
-struct Mips {
-    const float4 *m0[4];
-    const float2 *m1[4];
-    int w[4], h[4], L;
+// One level of the pyramid as a tap reads it: texel centres of level l sit at
+// 2^l (x + 0.5) - 0.5 in half-resolution pixels, so a half-resolution position x maps
+// to x 2^-l + (2^-l - 1) / 2 in level texels.
+struct MipLevel {
+    const float4 *m0;
+    const float2 *m1;
+    int w, h;
+    float s, c;
 };
 
+__device__ __forceinline__ MipLevel mip_level(const SessDesc &S, int l) {
+    MipLevel L;
+    L.m0 = S.mip0[l]; L.m1 = S.mip1[l]; L.w = S.mip_w[l]; L.h = S.mip_h[l];
+    L.s = 1.f / (float)(1 << l);
+    L.c = 0.5f * L.s - 0.5f;
+    return L;
+}
+
+// Bilinear sample of one level at (x, y), scaled by the level's trilinear weight wl and
+// added to (a, b): the trilinear blend of Eq. 8 is folded into the bilinear weights.
 template <bool CLAMP, bool H>
-__device__ __forceinline__ void bilin_mip(const Mips &M, int l, float x, float y, float4 &a, float2 &b) {
-    float s = 1.f / (float)(1 << l);
-    float xl = (x + 0.5f) * s - 0.5f, yl = (y + 0.5f) * s - 0.5f;
-    int w = M.w[l], h = M.h[l];
-    float xf = floorf(xl), yf = floorf(yl);
-    float fx = xl - xf, fy = yl - yf;
-    int x0 = (int)xf, y0 = (int)yf;
-    float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
-    const float4 *m0 = M.m0[l];
-    const float2 *m1 = M.m1[l];
+__device__ __forceinline__ void bilin_acc(const MipLevel &L, float x, float y, float wl, float4 &a, float2 &b) {
+    const float xl = fmaf(x, L.s, L.c), yl = fmaf(y, L.s, L.c);
+    const float xf = floorf(xl), yf = floorf(yl);
+    const float fx = xl - xf, fy = yl - yf;
+    const int x0 = (int)xf, y0 = (int)yf;
+    const float gx = 1.f - fx, gy0 = (1.f - fy) * wl, gy1 = fy * wl;
+    const float w00 = gx * gy0, w10 = fx * gy0, w01 = gx * gy1, w11 = fx * gy1;
+    const int w = L.w;
     int qa, qb, xa, xb;
     if (CLAMP) {
         xa = min(max(x0, 0), w - 1); xb = min(max(x0 + 1, 0), w - 1);
-        int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
+        const int ya = min(max(y0, 0), L.h - 1), yb = min(max(y0 + 1, 0), L.h - 1);
         qa = ya * w; qb = yb * w;
     } else {
         xa = x0; xb = x0 + 1;
         qa = y0 * w; qb = qa + w;
     }
-    a = f4fma(w11, ld_img(m0, qb + xb, H), f4fma(w01, ld_img(m0, qb + xa, H),
-              f4fma(w10, ld_img(m0, qa + xb, H), f4scale(w00, ld_img(m0, qa + xa, H)))));
-    float2 c00 = __ldg(&m1[qa + xa]), c10 = __ldg(&m1[qa + xb]);
-    float2 c01 = __ldg(&m1[qb + xa]), c11 = __ldg(&m1[qb + xb]);
-    b = make_float2(w00 * c00.x + w10 * c10.x + w01 * c01.x + w11 * c11.x,
-                    w00 * c00.y + w10 * c10.y + w01 * c01.y + w11 * c11.y);
+    a = f4fma(w00, ld_img(L.m0, qa + xa, H), a);
+    a = f4fma(w10, ld_img(L.m0, qa + xb, H), a);
+    a = f4fma(w01, ld_img(L.m0, qb + xa, H), a);
+    a = f4fma(w11, ld_img(L.m0, qb + xb, H), a);
+    const float2 c00 = __ldg(&L.m1[qa + xa]), c10 = __ldg(&L.m1[qa + xb]);
+    const float2 c01 = __ldg(&L.m1[qb + xa]), c11 = __ldg(&L.m1[qb + xb]);
+    b.x = fmaf(w11, c11.x, fmaf(w01, c01.x, fmaf(w10, c10.x, fmaf(w00, c00.x, b.x))));
+    b.y = fmaf(w11, c11.y, fmaf(w01, c01.y, fmaf(w10, c10.y, fmaf(w00, c00.y, b.y))));
 }
 
 template <bool CLAMP, bool H>
-__device__ __forceinline__ void recon_taps(const Mips &M, int i, int j, float R, int l0, int l1, float t,
+__device__ __forceinline__ void recon_taps(const MipLevel &L0, const MipLevel &L1, int i, int j, float R, float t,
                                            float inv_ramp, float4 &num, float &den) {
+    const float fi = (float)i, fj = (float)j, t0 = 1.f - t;
 #pragma unroll 3
     for (int k = 0; k < 81; k++) {
-        float3 u = c_ring81[k];
-        float dist = u.z * R;
-        float x = i + dist * u.x, y = j + dist * u.y;
-        float4 a0, a1;
-        float2 b0, b1;
-        bilin_mip<CLAMP, H>(M, l0, x, y, a0, b0);
-        bilin_mip<CLAMP, H>(M, l1, x, y, a1, b1);
-        float4 S = f4fma(t, a1, f4scale(1.f - t, a0));
-        float Sc = (1.f - t) * b0.x + t * b1.x, Sv = (1.f - t) * b0.y + t * b1.y;
-        float ri = Sv > 0.f ? __fdividef(Sc, Sv) : 0.f;
-        float D = sat((ri - dist) * inv_ramp + 0.5f);
+        const float3 u = c_ring81[k];
+        // dist and the cover weight D are rounded explicitly (no contraction left to the
+        // compiler), so that every instance of this kernel computes the same bits
+        const float dist = __fmul_rn(u.z, R);
+        const float x = fmaf(dist, u.x, fi), y = fmaf(dist, u.y, fj);
+        float4 S = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 Sb = make_float2(0.f, 0.f);
+        bilin_acc<CLAMP, H>(L0, x, y, t0, S, Sb);
+        bilin_acc<CLAMP, H>(L1, x, y, t, S, Sb);
+        const float Sc = Sb.x, Sv = Sb.y;
+        const float ri = Sv > 0.f ? __fdividef(Sc, Sv) : 0.f;
+        const float D = sat(__fmaf_rn(__fsub_rn(ri, dist), inv_ramp, 0.5f));
         num = f4fma(D, S, num);
-        den += D * Sv;
+        den = fmaf(D, Sv, den);
     }
 }
 
@@ -235,17 +251,13 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ AS as_) {
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevParams &p = S.p;
     const int W2 = S.cam.W2, H2 = S.cam.H2;
-    Mips M;
-    M.L = S.mip_L;
-    for (int l = 0; l < 4; l++) {
-        M.m0[l] = S.mip0[l]; M.m1[l] = S.mip1[l]; M.w[l] = S.mip_w[l]; M.h[l] = S.mip_h[l];
-    }
+    const int mL = S.mip_L;
     const float4 *__restrict__ med = S.rt_med;
     const float *__restrict__ ct = S.ct;
     const float *__restrict__ var_blur = S.var_out;
     const int32_t *__restrict__ nrays = S.nrays;
     float4 *out = S.recon;
-    const int reach = (int)ceilf(p.rmax_hpx) + (2 << (M.L - 1)) + 2;
+    const int reach = (int)ceilf(p.rmax_hpx) + (2 << (mL - 1)) + 2;
     const int bx = i - (int)threadIdx.x, by = j - (int)threadIdx.y;
     const bool interior = bx - reach >= 0 && by - reach >= 0 && bx + (int)blockDim.x + reach < W2 &&
                           by + (int)blockDim.y + reach < H2;
@@ -264,30 +276,36 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ AS as_) {
     float lod = fminf(fmaxf(R * p.lod_scale, 0.f), p.lod_max);
     int l0 = (int)floorf(lod);
     float t = lod - (float)l0;
-    if (l0 >= M.L - 1) { l0 = M.L - 1; t = 0.f; }
-    int l1 = min(l0 + 1, M.L - 1);
+    if (l0 >= mL - 1) { l0 = mL - 1; t = 0.f; }
+    const int l1 = min(l0 + 1, mL - 1);
+    const MipLevel L0 = mip_level(S, l0), L1 = mip_level(S, l1);
     float4 num = make_float4(0.f, 0.f, 0.f, 0.f);
     float den = 0.f;
     if (p.f16) {
-        if (interior) recon_taps<false, true>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
-        else recon_taps<true, true>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
+        if (interior) recon_taps<false, true>(L0, L1, i, j, R, t, p.inv_cover_ramp, num, den);
+        else recon_taps<true, true>(L0, L1, i, j, R, t, p.inv_cover_ramp, num, den);
     } else {
-        if (interior) recon_taps<false, false>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
-        else recon_taps<true, false>(M, i, j, R, l0, l1, t, p.inv_cover_ramp, num, den);
+        if (interior) recon_taps<false, false>(L0, L1, i, j, R, t, p.inv_cover_ramp, num, den);
+        else recon_taps<true, false>(L0, L1, i, j, R, t, p.inv_cover_ramp, num, den);
     }
     float4 f = den > 0.f ? f4scale(1.f / den, num) : o;
     st_img(out, q, make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b)), p.f16);
 }
 
-// A12: composite.  One thread per half-resolution pixel (i, j) writes its 2x2
-// full-resolution pixels: their bilinear taps into the half-resolution layers (texel
-// centres at 0.5 (x + 0.5) - 0.5, i.e. i -/+ 1/4) all lie in the clamped 3x3
-// neighbourhood of (i, j), which is loaded once; weights 1/4 and 3/4 are exact.
+// A12: composite.  Two threads per half-resolution pixel (i, j), one per row b of its
+// 2x2 full-resolution pixels; each writes the two pixels (2i, 2j + b), (2i + 1, 2j + b).
+// Their bilinear taps into the half-resolution layers (texel centres at
+// 0.5 (x + 0.5) - 0.5, i.e. i -/+ 1/4) lie in the clamped neighbourhood rows j + b - 1,
+// j + b and columns i - 1 .. i + 1; weights 1/4 and 3/4 are exact.  A block of 32 x 16
+// threads covers the 32 x 8 half-resolution pixels of one SH_HPX block.
 template <class AS>
-__global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(512, 2) k_composite(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
-    int i, j;
-    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    int lb;
+    const SessDesc &S = A.s[find_session(A, SH_HPX, blockIdx.x, lb)];
+    const int gx = S.gx[SH_HPX];
+    const int i = (lb % gx) * 32 + (int)threadIdx.x, j = (lb / gx) * 8 + (int)(threadIdx.y >> 1);
+    const int b = (int)(threadIdx.y & 1u);
     const DevCam &cam = S.cam;
     const DevParams &p = S.p;
     const float4 *__restrict__ color = S.color;
@@ -299,72 +317,68 @@ __global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS
     const int W2 = cam.W2, H2 = cam.H2;
     if (i >= W2 || j >= H2) return;
     const bool hs = p.f16;
-    // accumulators of the 2x2 full-resolution pixels (a, b) -> index 2 b + a; the
-    // neighbourhood is visited in raster order, so each pixel sums its four taps in
-    // the order (x0, y0), (x0 + 1, y0), (x0, y0 + 1), (x0 + 1, y0 + 1)
-    float4 pp[4], rt[4];
-    float cov[4];
+    // accumulators of the pixels a = 0, 1 of row b; the neighbourhood is visited in
+    // raster order, so each pixel sums its four taps in the order (x0, y0), (x0 + 1, y0),
+    // (x0, y0 + 1), (x0 + 1, y0 + 1)
+    float4 pp[2], rt[2];
+    float cov[2];
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < 2; k++) {
         pp[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         rt[k] = pp[k];
         cov[k] = 0.f;
     }
+    // fy = 3/4 for b = 0 (taps rows j - 1, j), 1/4 for b = 1 (taps rows j, j + 1)
+    const float fy = b ? 0.25f : 0.75f;
 #pragma unroll
-    for (int ny = 0; ny < 3; ny++)
+    for (int dy = 0; dy < 2; dy++)
 #pragma unroll
         for (int nx = 0; nx < 3; nx++) {
-            int x = min(max(i + nx - 1, 0), W2 - 1), y = min(max(j + ny - 1, 0), H2 - 1);
-            size_t q = (size_t)y * W2 + x;
+            const int x = min(max(i + nx - 1, 0), W2 - 1), y = min(max(j + b + dy - 1, 0), H2 - 1);
+            const size_t q = (size_t)y * W2 + x;
             const float4 P = ld_img(pp_med, q, hs);
             const bool V = __ldg(&nrays[q]) > 0;
             const float4 R = V ? ld_img(recon, q, hs) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int b = 0; b < 2; b++)
-#pragma unroll
-                for (int a = 0; a < 2; a++) {
-                    const int dx = nx - a, dy = ny - b;
-                    if (dx < 0 || dx > 1 || dy < 0 || dy > 1) continue;
-                    // fx = 3/4 for a = 0 (taps i - 1, i), 1/4 for a = 1 (taps i, i + 1)
-                    const float fx = a ? 0.25f : 0.75f, fy = b ? 0.25f : 0.75f;
-                    const float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
-                    const int k = 2 * b + a;
-                    pp[k] = f4fma(w, P, pp[k]);
-                    if (V) {
-                        rt[k] = f4fma(w, R, rt[k]);
-                        cov[k] += w;
-                    }
+            for (int a = 0; a < 2; a++) {
+                const int dx = nx - a;
+                if (dx < 0 || dx > 1) continue;
+                // fx = 3/4 for a = 0 (taps i - 1, i), 1/4 for a = 1 (taps i, i + 1)
+                const float fx = a ? 0.25f : 0.75f;
+                const float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
+                pp[a] = f4fma(w, P, pp[a]);
+                if (V) {
+                    rt[a] = f4fma(w, R, rt[a]);
+                    cov[a] += w;
                 }
-        }
-#pragma unroll
-    for (int b = 0; b < 2; b++)
-#pragma unroll
-        for (int a = 0; a < 2; a++) {
-            const int k = 2 * b + a;
-            const size_t f = (size_t)(2 * j + b) * cam.W + (2 * i + a);
-            float z = fminf(__ldg(&depth[f]), p.z_far);
-            float c = coc_of(cam, z);
-            float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
-            const float4 pk = pp[k], rk = rt[k];
-            const float cv = cov[k];
-            float4 s = ld_img(color, f, S.gf16);
-            float bx = pk.x, by = pk.y, bz = pk.z;
-            if (cv > 0.f) {
-                float ic = 1.f / cv;
-                float rx = rk.x * ic, ry = rk.y * ic, rz = rk.z * ic, hh = rk.w * ic;
-                float tb;
-                if (c < 0.f) {
-                    tb = pk.w;
-                } else {
-                    float u = sat(hh / p.h_edge);
-                    tb = u * u * (3.f - 2.f * u);
-                }
-                bx = lerpf(pk.x, lerpf(rx, pk.x, tb), cv);
-                by = lerpf(pk.y, lerpf(ry, pk.y, tb), cv);
-                bz = lerpf(pk.z, lerpf(rz, pk.z, tb), cv);
             }
-            out[f] = make_float4(lerpf(bx, s.x, ws), lerpf(by, s.y, ws), lerpf(bz, s.z, ws), 1.f);
         }
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const size_t f = (size_t)(2 * j + b) * cam.W + (2 * i + a);
+        float z = fminf(__ldg(&depth[f]), p.z_far);
+        float c = coc_of(cam, z);
+        float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
+        const float4 pk = pp[a], rk = rt[a];
+        const float cv = cov[a];
+        float4 s = ld_img(color, f, S.gf16);
+        float bx = pk.x, by = pk.y, bz = pk.z;
+        if (cv > 0.f) {
+            float ic = 1.f / cv;
+            float rx = rk.x * ic, ry = rk.y * ic, rz = rk.z * ic, hh = rk.w * ic;
+            float tb;
+            if (c < 0.f) {
+                tb = pk.w;
+            } else {
+                float u = sat(hh / p.h_edge);
+                tb = u * u * (3.f - 2.f * u);
+            }
+            bx = lerpf(pk.x, lerpf(rx, pk.x, tb), cv);
+            by = lerpf(pk.y, lerpf(ry, pk.y, tb), cv);
+            bz = lerpf(pk.z, lerpf(rz, pk.z, tb), cv);
+        }
+        out[f] = make_float4(lerpf(bx, s.x, ws), lerpf(by, s.y, ws), lerpf(bz, s.z, ws), 1.f);
+    }
 }
 
 
@@ -453,7 +467,7 @@ template <class AS>
 void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     dim3 b(32, 8);
-    k_composite<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
+    k_composite<AS><<<A.start[SH_HPX][n], dim3(32, 16), 0, st>>>(as);
     tmark(tm, DOF_K_COMPOSITE, st);
     bool any_taa = false;
     for (int i = 0; i < n; i++) any_taa |= A.s[i].taa != 0;
