@@ -292,11 +292,13 @@ def run_ours(args, rank, world):
     # session start (untimed): the autotuners pick the BVH build (PLOC radius), the
     # tree the rays traverse and the tracer's launch shape
     t0 = time.perf_counter()
+    widths = (args.bvh_width,) if args.bvh_width else (4, 2)
     scene, tuned_bvh, _ = tune.tune_scene(
         ctx, w.scene, lambda sc, k: dof.frame(ctx, sc, gbs[k % CYCLE], None, None, hist, out,
-                                              cam_struct=cams[k % len(cams)], params_s=pstruct))
+                                              cam_struct=cams[k % len(cams)], params_s=pstruct), widths=widths)
     info = scene.info()
-    tuned, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4)
+    tuned, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4,
+                               widths=(args.bvh_width,) if args.bvh_width else None)
     tuned = dict(tuned, ploc_radius=tuned_bvh["ploc_radius"])
     tune_s = time.perf_counter() - t0
     hist.reset()
@@ -731,6 +733,8 @@ def main():
                     help="camera jitter (Halton 2, 3) and the final TAA pass with blend 0.1")
     ap.add_argument("--size", default=None,
                     help="WxH: the workload's scene, lens and camera path at another resolution (profiler captures)")
+    ap.add_argument("--bvh-width", type=int, default=None, choices=[2, 4],
+                    help="traverse this tree width instead of the autotuner's choice (profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", 1))

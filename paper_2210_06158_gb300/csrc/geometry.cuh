@@ -96,14 +96,11 @@ __device__ __forceinline__ float tri_hit_k(const Ray &r, float4 v0, float4 v1, f
 }
 
 __device__ __forceinline__ float tri_hit(const Ray &r, float4 v0, float4 v1, float4 v2, float tmax = INFINITY) {
-    switch (r.perm) {
-    case 0: return tri_hit_k<0, false>(r, v0, v1, v2, tmax);
-    case 1: return tri_hit_k<0, true>(r, v0, v1, v2, tmax);
-    case 2: return tri_hit_k<1, false>(r, v0, v1, v2, tmax);
-    case 3: return tri_hit_k<1, true>(r, v0, v1, v2, tmax);
-    case 4: return tri_hit_k<2, false>(r, v0, v1, v2, tmax);
-    default: return tri_hit_k<2, true>(r, v0, v1, v2, tmax);
-    }
+    // conditional branches, not a jump table (an indirect branch stalls the warp)
+    const int pm = r.perm;
+    if (pm >= 4) return pm == 4 ? tri_hit_k<2, false>(r, v0, v1, v2, tmax) : tri_hit_k<2, true>(r, v0, v1, v2, tmax);
+    if (pm >= 2) return pm == 2 ? tri_hit_k<1, false>(r, v0, v1, v2, tmax) : tri_hit_k<1, true>(r, v0, v1, v2, tmax);
+    return pm == 0 ? tri_hit_k<0, false>(r, v0, v1, v2, tmax) : tri_hit_k<0, true>(r, v0, v1, v2, tmax);
 }
 
 struct HitRec {

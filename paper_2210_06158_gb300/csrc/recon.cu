@@ -292,20 +292,15 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ AS as_) {
     st_img(out, q, make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b)), p.f16);
 }
 
-// A12: composite.  Two threads per half-resolution pixel (i, j), one per row b of its
-// 2x2 full-resolution pixels; each writes the two pixels (2i, 2j + b), (2i + 1, 2j + b).
-// Their bilinear taps into the half-resolution layers (texel centres at
-// 0.5 (x + 0.5) - 0.5, i.e. i -/+ 1/4) lie in the clamped neighbourhood rows j + b - 1,
-// j + b and columns i - 1 .. i + 1; weights 1/4 and 3/4 are exact.  A block of 32 x 16
-// threads covers the 32 x 8 half-resolution pixels of one SH_HPX block.
+// A12: composite.  One thread per half-resolution pixel (i, j) writes its 2x2
+// full-resolution pixels: their bilinear taps into the half-resolution layers (texel
+// centres at 0.5 (x + 0.5) - 0.5, i.e. i -/+ 1/4) all lie in the clamped 3x3
+// neighbourhood of (i, j), which is loaded once; weights 1/4 and 3/4 are exact.
 template <class AS>
-__global__ void __launch_bounds__(512, 2) k_composite(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
-    int lb;
-    const SessDesc &S = A.s[find_session(A, SH_HPX, blockIdx.x, lb)];
-    const int gx = S.gx[SH_HPX];
-    const int i = (lb % gx) * 32 + (int)threadIdx.x, j = (lb / gx) * 8 + (int)(threadIdx.y >> 1);
-    const int b = (int)(threadIdx.y & 1u);
+    int i, j;
+    const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevCam &cam = S.cam;
     const DevParams &p = S.p;
     const float4 *__restrict__ color = S.color;
@@ -317,68 +312,72 @@ __global__ void __launch_bounds__(512, 2) k_composite(const __grid_constant__ AS
     const int W2 = cam.W2, H2 = cam.H2;
     if (i >= W2 || j >= H2) return;
     const bool hs = p.f16;
-    // accumulators of the pixels a = 0, 1 of row b; the neighbourhood is visited in
-    // raster order, so each pixel sums its four taps in the order (x0, y0), (x0 + 1, y0),
-    // (x0, y0 + 1), (x0 + 1, y0 + 1)
-    float4 pp[2], rt[2];
-    float cov[2];
+    // accumulators of the 2x2 full-resolution pixels (a, b) -> index 2 b + a; the
+    // neighbourhood is visited in raster order, so each pixel sums its four taps in
+    // the order (x0, y0), (x0 + 1, y0), (x0, y0 + 1), (x0 + 1, y0 + 1)
+    float4 pp[4], rt[4];
+    float cov[4];
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < 4; k++) {
         pp[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         rt[k] = pp[k];
         cov[k] = 0.f;
     }
-    // fy = 3/4 for b = 0 (taps rows j - 1, j), 1/4 for b = 1 (taps rows j, j + 1)
-    const float fy = b ? 0.25f : 0.75f;
 #pragma unroll
-    for (int dy = 0; dy < 2; dy++)
+    for (int ny = 0; ny < 3; ny++)
 #pragma unroll
         for (int nx = 0; nx < 3; nx++) {
-            const int x = min(max(i + nx - 1, 0), W2 - 1), y = min(max(j + b + dy - 1, 0), H2 - 1);
-            const size_t q = (size_t)y * W2 + x;
+            int x = min(max(i + nx - 1, 0), W2 - 1), y = min(max(j + ny - 1, 0), H2 - 1);
+            size_t q = (size_t)y * W2 + x;
             const float4 P = ld_img(pp_med, q, hs);
             const bool V = __ldg(&nrays[q]) > 0;
             const float4 R = V ? ld_img(recon, q, hs) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int a = 0; a < 2; a++) {
-                const int dx = nx - a;
-                if (dx < 0 || dx > 1) continue;
-                // fx = 3/4 for a = 0 (taps i - 1, i), 1/4 for a = 1 (taps i, i + 1)
-                const float fx = a ? 0.25f : 0.75f;
-                const float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
-                pp[a] = f4fma(w, P, pp[a]);
-                if (V) {
-                    rt[a] = f4fma(w, R, rt[a]);
-                    cov[a] += w;
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int a = 0; a < 2; a++) {
+                    const int dx = nx - a, dy = ny - b;
+                    if (dx < 0 || dx > 1 || dy < 0 || dy > 1) continue;
+                    // fx = 3/4 for a = 0 (taps i - 1, i), 1/4 for a = 1 (taps i, i + 1)
+                    const float fx = a ? 0.25f : 0.75f, fy = b ? 0.25f : 0.75f;
+                    const float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
+                    const int k = 2 * b + a;
+                    pp[k] = f4fma(w, P, pp[k]);
+                    if (V) {
+                        rt[k] = f4fma(w, R, rt[k]);
+                        cov[k] += w;
+                    }
                 }
-            }
         }
 #pragma unroll
-    for (int a = 0; a < 2; a++) {
-        const size_t f = (size_t)(2 * j + b) * cam.W + (2 * i + a);
-        float z = fminf(__ldg(&depth[f]), p.z_far);
-        float c = coc_of(cam, z);
-        float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
-        const float4 pk = pp[a], rk = rt[a];
-        const float cv = cov[a];
-        float4 s = ld_img(color, f, S.gf16);
-        float bx = pk.x, by = pk.y, bz = pk.z;
-        if (cv > 0.f) {
-            float ic = 1.f / cv;
-            float rx = rk.x * ic, ry = rk.y * ic, rz = rk.z * ic, hh = rk.w * ic;
-            float tb;
-            if (c < 0.f) {
-                tb = pk.w;
-            } else {
-                float u = sat(hh / p.h_edge);
-                tb = u * u * (3.f - 2.f * u);
+    for (int b = 0; b < 2; b++)
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            const int k = 2 * b + a;
+            const size_t f = (size_t)(2 * j + b) * cam.W + (2 * i + a);
+            float z = fminf(__ldg(&depth[f]), p.z_far);
+            float c = coc_of(cam, z);
+            float ws = sat((1.41421356237309505f - fabsf(c) + 0.5f * p.zof_ramp) / p.zof_ramp);
+            const float4 pk = pp[k], rk = rt[k];
+            const float cv = cov[k];
+            float4 s = ld_img(color, f, S.gf16);
+            float bx = pk.x, by = pk.y, bz = pk.z;
+            if (cv > 0.f) {
+                float ic = 1.f / cv;
+                float rx = rk.x * ic, ry = rk.y * ic, rz = rk.z * ic, hh = rk.w * ic;
+                float tb;
+                if (c < 0.f) {
+                    tb = pk.w;
+                } else {
+                    float u = sat(hh / p.h_edge);
+                    tb = u * u * (3.f - 2.f * u);
+                }
+                bx = lerpf(pk.x, lerpf(rx, pk.x, tb), cv);
+                by = lerpf(pk.y, lerpf(ry, pk.y, tb), cv);
+                bz = lerpf(pk.z, lerpf(rz, pk.z, tb), cv);
             }
-            bx = lerpf(pk.x, lerpf(rx, pk.x, tb), cv);
-            by = lerpf(pk.y, lerpf(ry, pk.y, tb), cv);
-            bz = lerpf(pk.z, lerpf(rz, pk.z, tb), cv);
+            out[f] = make_float4(lerpf(bx, s.x, ws), lerpf(by, s.y, ws), lerpf(bz, s.z, ws), 1.f);
         }
-        out[f] = make_float4(lerpf(bx, s.x, ws), lerpf(by, s.y, ws), lerpf(bz, s.z, ws), 1.f);
-    }
 }
 
 
@@ -467,7 +466,7 @@ template <class AS>
 void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     dim3 b(32, 8);
-    k_composite<AS><<<A.start[SH_HPX][n], dim3(32, 16), 0, st>>>(as);
+    k_composite<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_COMPOSITE, st);
     bool any_taa = false;
     for (int i = 0; i < n; i++) any_taa |= A.s[i].taa != 0;

@@ -38,12 +38,14 @@ def _time_frames(run_frame, frames, st):
     return e0.elapsed_time(e1) / frames
 
 
-def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None):
+def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None):
     """run_frame(k) enqueues frame k of a representative session on `stream` (or the
-    current stream).  Returns (best settings, {settings tuple: ms per frame})."""
+    current stream); `widths` restricts the tree widths searched (default: all).
+    Returns (best settings, {settings tuple: ms per frame})."""
     import torch
     st = stream if stream is not None else torch.cuda.current_stream()
-    best = dict(DEFAULT)
+    space = dict(SPACE, bvh_width=list(widths)) if widths else SPACE
+    best = dict(DEFAULT, bvh_width=space["bvh_width"][0])
     seen = {}
 
     def measure(cfg, fresh=False):
@@ -57,7 +59,7 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None):
     best_ms = measure(best)
     for _ in range(rounds):
         improved = False
-        for name, values in SPACE.items():
+        for name, values in space.items():
             for v in values:
                 cand = dict(best, **{name: v})
                 ms = measure(cand)

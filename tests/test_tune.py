@@ -151,3 +151,16 @@ def test_tune_trace_rejects_a_win_that_a_second_timing_does_not_confirm(monkeypa
 
     best, _ = tune.tune_trace(ctx, run_frame, frames=2, stream=types.SimpleNamespace())
     assert best == tune.DEFAULT
+
+
+def test_tune_trace_searches_only_the_widths_given(monkeypatch):
+    clock = _Clock()
+    _fake_cuda(monkeypatch, clock)
+    ctx = _Ctx()
+
+    def run_frame(k):
+        clock.t += _cost(dict(ctx.cfg, bvh_width=2 if ctx.cfg["bvh_width"] == 4 else 4))   # 4 would win
+
+    best, seen = tune.tune_trace(ctx, run_frame, frames=2, stream=types.SimpleNamespace(), widths=(2,))
+    assert best["bvh_width"] == 2
+    assert all(dict(key)["bvh_width"] == 2 for key in seen)
