@@ -36,7 +36,7 @@ METRIC = "hybrid-DoF frames/s at 1080p/4K, %HBM roofline; served p50/p99 frame l
 CYCLE = 16
 
 # FP32 operations of the traversal (FMA = 2): a binary node visit tests two child
-# boxes (per box 6 (sub, mul) slab products = 12, 10 min/max, 1 compare -> 23, x2 = 46)
+# boxes (per box 6 FMA slab products = 12, 10 min/max, 1 compare -> 23, x2 = 46)
 # and orders them (1); a 4-wide node visit tests four boxes (6 FMA slab products = 12,
 # 10 min/max, 1 compare -> 23, x4 = 92) and sorts them (5 compares); a watertight
 # triangle test (Woop et al. 2013) is 9 subtractions, 6 shears (sub, mul) = 12,
@@ -49,11 +49,11 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch from the last ncu capture of each kernel on the
 # workload (profiles/top_kernels_*.md); a kernel or workload changed since then has no
 # entry.  The 4K tracer was captured at 1920x1080 (same scene, lens, 4 spp) and is
-# scaled by the rays of a full launch (6.73M / 1.78M).
-PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_recon": 25.4e6,
-                           "k_main_filter": 10.4e6, "k_accumulate": 55.8e6, "k_composite": 63.3e6,
+# scaled by the rays of a full launch (6.72M / 1.78M).
+PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": 11.3e6, "k_recon": 25.3e6,
+                           "k_main_filter": 10.4e6, "k_accumulate": 55.9e6, "k_composite": 62.8e6,
                            "k_downscale_tiles": 41.6e6},
-                    "c3": {"k_trace_rays<0>": None}}
+                    "c3": {"k_trace_rays<0>": 21.6e6 * 6.72 / 1.78}}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
