@@ -84,7 +84,7 @@ class OrParams(C.Structure):
                 ("seed", C.c_uint64), ("session", C.c_uint64),
                 ("light", _d3), ("k_a", C.c_double), ("k_d", C.c_double), ("sky", _d3),
                 ("emit", C.c_double), ("albedo_seed", C.c_uint32), ("pad1", C.c_int32),
-                ("taa_alpha", C.c_double)]
+                ("taa_alpha", C.c_double), ("blades", C.c_double)]
 
 
 _pd = C.POINTER(C.c_double)
@@ -126,6 +126,12 @@ def _declare(L):
     L.or_frame.argtypes = [vp, C.POINTER(OrCamera), C.POINTER(OrParams), C.c_int, C.c_int,
                            vp, vp, vp, C.POINTER(OrFrame)]
     L.or_median9.argtypes = [vp, C.c_int, vp]
+    L.or_poly_rho.restype = C.c_double
+    L.or_poly_rho.argtypes = [C.c_int, C.c_double]
+    L.or_poly_area.restype = C.c_double
+    L.or_poly_area.argtypes = [C.c_int]
+    L.or_aperture_point.argtypes = [C.c_int, C.c_double, C.c_double, vp]
+    L.or_ring_tap.argtypes = [C.c_int, C.c_int, vp]
     L.or_binomial5.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
     L.or_sobel5.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.or_albedo.argtypes = [C.c_uint32, C.c_int, vp]
@@ -190,6 +196,7 @@ def params(p: dict) -> OrParams:
     o.emit = f(p["emit"])
     o.albedo_seed = int(p["albedo_seed"]) & 0xFFFFFFFF
     o.taa_alpha = f(p.get("taa_alpha", 0.0))
+    o.blades = float(int(p.get("aperture_blades", 0)))
     return o
 
 
@@ -251,6 +258,30 @@ def lens_ray(cam, prm, W, H, i, j, sample):
     o, d = np.zeros(3), np.zeros(3)
     lib().or_lens_ray(C.byref(c), C.byref(p), int(W), int(H), int(i), int(j), int(sample), _p(o), _p(d))
     return o, d
+
+
+def poly_rho(n: int, th: float) -> float:
+    """Boundary radius of the regular n-gon aperture (circumradius 1, a vertex at angle
+    0) in direction th; 1 for the circle (n = 0)."""
+    return lib().or_poly_rho(int(n), float(th))
+
+
+def poly_area(n: int) -> float:
+    return lib().or_poly_area(int(n))
+
+
+def aperture_point(n: int, u1: float, u2: float) -> np.ndarray:
+    """Lens point of the unit-circumradius aperture from two uniforms."""
+    out = np.zeros(2)
+    lib().or_aperture_point(int(n), float(u1), float(u2), _p(out))
+    return out
+
+
+def ring_tap(n: int, t: int) -> np.ndarray:
+    """Tap t of the 81-tap kernel on the aperture's shape: (x, y, ring fraction)."""
+    out = np.zeros(3)
+    lib().or_ring_tap(int(n), int(t), _p(out))
+    return out
 
 
 def pixel_dir(cam, W, H, x, y):

@@ -64,12 +64,42 @@ void or_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+double or_poly_rho(int n, double th) {
+    if (n <= 0) return 1.0;
+    double sector = 2.0 * M_PI / n;
+    double phi = fmod(th, sector);
+    if (phi < 0.0) phi += sector;
+    return cos(M_PI / n) / cos(phi - M_PI / n);
+}
+
+double or_poly_area(int n) {
+    if (n <= 0) return M_PI;
+    return 0.5 * n * sin(2.0 * M_PI / n);
+}
+
+void or_aperture_point(int n, double u1, double u2, double out[2]) {
+    if (n <= 0) {
+        double r = sqrt(u1), phi = 2.0 * M_PI * u2;
+        out[0] = r * cos(phi);
+        out[1] = r * sin(phi);
+        return;
+    }
+    double a = u2 * n;
+    int k = (int)floor(a);
+    if (k > n - 1) k = n - 1;
+    double t = a - k, r = sqrt(u1);
+    double t0 = 2.0 * M_PI * k / n, t1 = 2.0 * M_PI * (k + 1) / n;
+    out[0] = r * ((1.0 - t) * cos(t0) + t * cos(t1));
+    out[1] = r * ((1.0 - t) * sin(t0) + t * sin(t1));
+}
+
 /* Distributed ray of Cook et al. for the half-resolution pixel (i, j) and lens
  * sample `sample` (Section 3.2.2): the pixel's direction through the lens centre
  * meets the focus plane z = d at P_f; a point L on the lens disk (radius a/2) is
  * drawn from Philox keyed on (seed, session) with counter (pixel, sample, frame, 0);
- * the ray runs from L towards P_f.  Lens point: polar map r = (a/2) sqrt(u1),
- * phi = 2 pi u2 of two 24-bit uniforms (the paper only says "within a circle"). */
+ * the ray runs from L towards P_f.  Lens point: (a/2) or_aperture_point of two 24-bit
+ * uniforms, the polar map r = sqrt(u1), phi = 2 pi u2 for the circular aperture (the
+ * paper only says "within a circle"). */
 void or_lens_ray(const OrCamera *c, const OrParams *p, int W, int H, int i, int j, int sample,
                  double o[3], double d[3]) {
     int W2 = W / 2;
@@ -83,9 +113,9 @@ void or_lens_ray(const OrCamera *c, const OrParams *p, int W, int H, int i, int 
     or_philox4x64(ctr, key, x);
     double u1 = (double)(x[0] >> 40) * (1.0 / 16777216.0);
     double u2 = (double)(x[1] >> 40) * (1.0 / 16777216.0);
-    double a = c->f / c->N;
-    double r = 0.5 * a * sqrt(u1), phi = 2.0 * M_PI * u2;
-    double lx = r * cos(phi), ly = r * sin(phi);
+    double a = c->f / c->N, pt[2];
+    or_aperture_point((int)p->blades, u1, u2, pt);
+    double lx = 0.5 * a * pt[0], ly = 0.5 * a * pt[1];
     for (int k = 0; k < 3; k++) o[k] = c->O[k] + lx * c->R[k] + ly * c->U[k];
     sub3(Pf, o, d);
     normalize3(d);

@@ -165,17 +165,19 @@ void or_prefilter(const OrParams *p, int W2, int H2, const double *pp_in, const 
 
 /* ---- A4: 81-tap main filter (Section 3.1.2, Eq. 1) ------------------------- */
 
-/* tap t of the 81-tap kernel: centre (t = 0), then rings k = 1..4 of 8k taps at
- * radius k/4 of the kernel radius, angles 2 pi m / (8k) */
-static void ring_tap(int t, double *fx, double *fy, double *frac) {
-    if (t == 0) { *fx = 0; *fy = 0; *frac = 0; return; }
+/* tap t of the 81-tap kernel (declared in oracle.h): centre (t = 0), then rings
+ * k = 1..4 of 8k taps at angles 2 pi m / (8k), at radius k/4 of the kernel radius on
+ * the circle, or on the n-gon boundary in the same direction */
+void or_ring_tap(int n, int t, double out[3]) {
+    if (t == 0) { out[0] = 0; out[1] = 0; out[2] = 0; return; }
     int k = 1, base = 1;
     while (t >= base + 8 * k) { base += 8 * k; k++; }
     int m = t - base;
     double th = 2.0 * M_PI * m / (8.0 * k);
-    *frac = k / 4.0;
-    *fx = cos(th);
-    *fy = sin(th);
+    double rho = or_poly_rho(n, th);
+    out[0] = rho * cos(th);
+    out[1] = rho * sin(th);
+    out[2] = k / 4.0;
 }
 
 /* Coverage test D of Eq. 1: the paper counts a sample when its CoC radius exceeds
@@ -186,10 +188,12 @@ static double coverage(double dist, double r, double ramp) {
 }
 
 /* sampleAlpha (named but not defined in Section 3.1.2): the share of the sample's
- * blur disk that lands on one pixel, 1 / (pi r^2), at most 1. */
-static double sample_alpha(double r) {
-    double rr = fmax(fabs(r), 1.0 / sqrt(M_PI));
-    return 1.0 / (M_PI * rr * rr);
+ * blur disk that lands on one pixel, 1 / (pi r^2), at most 1; for an n-gon aperture
+ * the share of its n-gon of circumradius r, 1 / (A_n r^2). */
+static double sample_alpha(int n, double r) {
+    double A = or_poly_area(n);
+    double rr = fmax(fabs(r), 1.0 / sqrt(A));
+    return 1.0 / (A * rr * rr);
 }
 
 /* Main filter.  Kernel radius R = the dilated max |rho| of the pixel's tile.  For
@@ -211,8 +215,9 @@ void or_main_filter(const OrParams *p, int W2, int H2, const double *pre, const 
             double z0 = z_h[q], rho0 = pre[4 * q + 3];
             double acc[3] = {0, 0, 0}, bright = 0.0, wsum = 0.0;
             for (int t = 0; t < 81; t++) {
-                double ux, uy, frac;
-                ring_tap(t, &ux, &uy, &frac);
+                double u[3];
+                or_ring_tap((int)p->blades, t, u);
+                double ux = u[0], uy = u[1], frac = u[2];
                 double dist = frac * R;
                 double x = i + dist * ux, y = j + dist * uy;
                 double s[4], zi;
@@ -220,7 +225,7 @@ void or_main_filter(const OrParams *p, int W2, int H2, const double *pre, const 
                 bilinear_clamped(z_h, W2, H2, 1, x, y, &zi);
                 double ri = fabs(s[3]);
                 double wf = saturate((z0 - zi) / p->depth_range);
-                double a = sample_alpha(s[3]);
+                double a = sample_alpha((int)p->blades, s[3]);
                 double Wf = wf * coverage(dist, ri, p->cover_ramp) * a;
                 double Wb = (1.0 - wf) * coverage(dist, fmin(ri, fabs(rho0)), p->cover_ramp) * a;
                 double Wt = Wf + Wb;

@@ -86,17 +86,7 @@ static void trilinear(const Mips *m, double x, double y, double lod, double out[
     for (int c = 0; c < 6; c++) out[c] = (1.0 - t) * a[c] + t * b[c];
 }
 
-static void ring_tap81(int t, double *fx, double *fy, double *frac) {
-    if (t == 0) { *fx = 0; *fy = 0; *frac = 0; return; }
-    int k = 1, base = 1;
-    while (t >= base + 8 * k) { base += 8 * k; k++; }
-    double th = 2.0 * M_PI * (t - base) / (8.0 * k);
-    *frac = k / 4.0;
-    *fx = cos(th);
-    *fy = sin(th);
-}
-
-/* Reconstruction: the 81-tap ring kernel scaled to the accumulated CoC radius
+/* Reconstruction: the 81-tap ring kernel (on the aperture's shape, or_ring_tap) scaled to the accumulated CoC radius
  * c_t, sampled trilinearly at lod = clamp(c_t * 0.05, 0, 3) (Eq. 8).  A sample
  * whose CoC radius is below its distance to the centre is rejected (the coverage
  * ramp D of the main filter, on the sample's own c_t).  The filtered colour and
@@ -120,8 +110,9 @@ void or_recon(const OrParams *p, int W2, int H2, const double *med, const double
             double lod = clampd(R * p->lod_scale, 0.0, p->lod_max);
             double num[4] = {0, 0, 0, 0}, den = 0.0;
             for (int t = 0; t < 81; t++) {
-                double ux, uy, frac, S[6];
-                ring_tap81(t, &ux, &uy, &frac);
+                double u[3], S[6];
+                or_ring_tap((int)p->blades, t, u);
+                double ux = u[0], uy = u[1], frac = u[2];
                 double dist = frac * R;
                 trilinear(&m, i + dist * ux, j + dist * uy, lod, S);
                 double ri = S[5] > 0.0 ? S[4] / S[5] : 0.0;

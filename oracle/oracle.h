@@ -50,9 +50,28 @@ typedef struct {
     uint32_t albedo_seed;
     int32_t pad1;
     double taa_alpha;                     /* final TAA blend of the current frame (0 = no TAA) */
+    double blades;                        /* aperture: 0 = circle, n = 3..8 regular n-gon */
 } OrParams;
 
 typedef struct OrScene OrScene;
+
+/* ---------------- polygonal aperture (or_camera.c) ----------------
+ * Section 1.1: bokeh takes the aperture's shape, a polygon for an n-blade diaphragm;
+ * Section 2.2: the method extends to such shapes by changing the shape of its
+ * sampling kernel.  Reading: a regular n-gon inscribed in the circle the circular
+ * aperture would have (circumradius 1 here, a vertex at angle 0); the lens samples
+ * of the rays and the taps of the 81-tap kernels both take that shape, and
+ * sampleAlpha divides by its area.  n = 0 is the circle. */
+double or_poly_rho(int n, double th);     /* boundary radius in direction th (1 for n = 0) */
+double or_poly_area(int n);               /* area (pi for n = 0) */
+/* uniform point of the unit disk (n = 0: r = sqrt(u1), phi = 2 pi u2) or of the n-gon
+ * (sector k = floor(n u2), position t = n u2 - k along its edge: sqrt(u1) ((1 - t) V_k
+ * + t V_k+1), which is uniform over the triangle (0, V_k, V_k+1)) */
+void or_aperture_point(int n, double u1, double u2, double out[2]);
+/* tap t of the 81-tap kernel (centre, then rings k = 1..4 of 8k taps at angles
+ * 2 pi m / (8k)): unit offset (x, y) on the circle (n = 0) or on the n-gon boundary
+ * in the same direction, and the ring fraction k / 4 (or_post.c) */
+void or_ring_tap(int n, int t, double out[3]);
 
 /* ---------------- scene / rays (or_scene.c) ---------------- */
 OrScene *or_scene_create(const float *xyz, int n_verts, const uint32_t *idx,

@@ -705,3 +705,69 @@ def test_taa_matches_reprojection_closed_forms(case):
     # no previous frame: the current image
     first = oracle.taa(cam, prm, W, H, depth, cur, None)
     assert np.array_equal(first[..., :3], cur[..., :3])
+
+
+# ---- polygonal aperture (Section 1.1: bokeh takes the aperture's shape, polygonal for
+# an n-blade diaphragm; Section 2.2: the kernel's shape can be changed to produce it) ----
+
+def _support_norm(n, x, y):
+    """Polygon norm of (x, y) for the regular n-gon of circumradius 1 with a vertex at
+    angle 0, from its edge normals (angles (2k + 1) pi / n) and apothem cos(pi / n):
+    1 exactly on the boundary.  Independent of the oracle's radial formula."""
+    ang = (2 * np.arange(n) + 1) * np.pi / n
+    return np.max(np.cos(ang) * x + np.sin(ang) * y) / np.cos(np.pi / n)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 7, 8])
+def test_polygon_boundary_and_area_against_geometry(n):
+    """The boundary radius agrees with the support-function norm of the n-gon, its
+    vertices sit on the unit circle, and the area equals the shoelace area."""
+    for th in np.linspace(-3.0, 9.0, 997):
+        r = oracle.poly_rho(n, th)
+        assert _support_norm(n, r * np.cos(th), r * np.sin(th)) == pytest.approx(1.0, abs=1e-12)
+    for k in range(n):
+        assert oracle.poly_rho(n, 2 * np.pi * k / n) == pytest.approx(1.0, abs=1e-12)
+    vx = np.cos(2 * np.pi * np.arange(n) / n)
+    vy = np.sin(2 * np.pi * np.arange(n) / n)
+    shoelace = 0.5 * abs(np.sum(vx * np.roll(vy, -1) - np.roll(vx, -1) * vy))
+    assert oracle.poly_area(n) == pytest.approx(shoelace, rel=1e-13)
+    assert oracle.poly_rho(0, 1.234) == 1.0 and oracle.poly_area(0) == pytest.approx(np.pi, rel=1e-15)
+
+
+@pytest.mark.parametrize("n", [0, 3, 5, 6, 8])
+def test_aperture_point_is_uniform_over_the_aperture(n):
+    """Lens points from a midpoint grid of the two uniforms: all inside the aperture,
+    centred, with the second moment of the uniform n-gon, (2 + cos(2 pi / n)) / 6
+    (1/2 for the disk), and a quarter of them inside the aperture scaled by 1/2."""
+    g = (np.arange(240) + 0.5) / 240
+    pts = np.array([oracle.aperture_point(n, u1, u2) for u1 in g for u2 in g])
+    if n:
+        norms = np.array([_support_norm(n, x, y) for x, y in pts])
+    else:
+        norms = np.hypot(pts[:, 0], pts[:, 1])
+    assert norms.max() <= 1.0 + 1e-12
+    assert np.abs(pts.mean(axis=0)).max() < 1e-3
+    m2 = (pts ** 2).sum(axis=1).mean()
+    want = 0.5 if n == 0 else (2.0 + np.cos(2 * np.pi / n)) / 6.0
+    assert m2 == pytest.approx(want, abs=2e-4)
+    assert (norms <= 0.5).mean() == pytest.approx(0.25, abs=3e-3)
+
+
+@pytest.mark.parametrize("n", [0, 3, 4, 5, 6, 8])
+def test_ring_taps_lie_on_the_aperture_shape(n):
+    """Tap t of the 81-tap kernel: centre, then rings k = 1..4 of 8k taps in the
+    directions 2 pi m / (8k), each on the aperture's boundary scaled by k / 4."""
+    assert np.allclose(oracle.ring_tap(n, 0), [0.0, 0.0, 0.0])
+    t = 1
+    for k in range(1, 5):
+        for m in range(8 * k):
+            x, y, frac = oracle.ring_tap(n, t)
+            assert frac == k / 4.0
+            th = 2 * np.pi * m / (8 * k)
+            # same direction as the circular tap
+            assert x * np.sin(th) - y * np.cos(th) == pytest.approx(0.0, abs=1e-12)
+            assert x * np.cos(th) + y * np.sin(th) > 0.0
+            norm = np.hypot(x, y) if n == 0 else _support_norm(n, x, y)
+            assert norm == pytest.approx(1.0, abs=1e-12)
+            t += 1
+    assert t == 81
