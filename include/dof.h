@@ -103,6 +103,13 @@ typedef struct {
                                pass in FP16 (arithmetic stays FP32; depth, CoC and history FP32) */
     float taa_alpha;        /* final TAA (Section 3.4) blend of the current frame, 0 < a <= 1;
                                0 = no TAA (the history needs DOF_HIST_TAA otherwise) */
+    uint32_t aperture_blades; /* aperture shape (Section 1.1: bokeh takes the shape of an n-blade
+                               diaphragm; Section 2.2: the kernel's shape can be changed to
+                               produce it): 0 = circle; 3..8 = regular n-gon inscribed in the
+                               circle, a vertex along the camera's right axis.  The thin-lens
+                               samples are uniform over it, the 81-tap kernels of the main filter
+                               and the reconstruction lie on it, sampleAlpha divides by its area.
+                               Other values: DOF_ERR_INVALID_ARG. */
 } DofParams;
 
 #define DOF_STORAGE_F32 0

@@ -157,6 +157,16 @@ int make_params(const DofParams *p, uint32_t W, uint32_t H, uint32_t max_rays, D
     if (!(p->taa_alpha >= 0.f && p->taa_alpha <= 1.f))
         return dof_set_error(DOF_ERR_INVALID_ARG, "params: taa_alpha must be in [0, 1]");
     o.taa_alpha = p->taa_alpha;
+    if (p->aperture_blades != 0 && (p->aperture_blades < 3 || p->aperture_blades > 8))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "params: aperture_blades must be 0 or 3..8");
+    o.blades = (int)p->aperture_blades;
+    o.ring = o.blades ? o.blades - 2 : 0;
+    {
+        const double kPi = 3.14159265358979323846;
+        const double A = o.blades ? 0.5 * o.blades * sin(2.0 * kPi / o.blades) : kPi;
+        o.inv_area = (float)(1.0 / A);
+        o.inv_sqrt_area = (float)(1.0 / sqrt(A));
+    }
     o.tiles_w = (int)((W2 + 7) / 8);
     o.tiles_h = (int)((H2 + 7) / 8);
     o.dil_k = (int)ceil(0.5 * (double)p->max_coc_px / 8.0);

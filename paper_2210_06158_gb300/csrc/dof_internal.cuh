@@ -45,6 +45,9 @@ struct DevParams {
     int tiles_w, tiles_h, dil_k;
     int f16;                    // colour image buffers stored as FP16
     float taa_alpha;            // final TAA blend (0 = off)
+    int blades;                 // aperture: 0 circle, 3..8 regular n-gon
+    int ring;                   // row of the 81-tap table: 0 circle, blades - 2 for an n-gon
+    float inv_area, inv_sqrt_area;  // sampleAlpha: 1 / A and 1 / sqrt(A), A = the aperture's area at radius 1
 };
 
 // ---------------------------------------------------------------------------

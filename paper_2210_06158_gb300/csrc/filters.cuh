@@ -10,24 +10,38 @@
 
 // unit offsets (cos, sin) of the 8 prefilter taps (angles k pi / 4)
 static __constant__ float2 c_pre8[8];
-// 81-tap ring kernel: (cos, sin, radius fraction) -- centre, then rings k = 1..4 of
-// 8k taps at angles 2 pi m / (8k) and radius k / 4
-static __constant__ float3 c_ring81[81];
+// 81-tap ring kernels: (x, y, radius fraction) -- centre, then rings k = 1..4 of 8k
+// taps in the directions 2 pi m / (8k) at radius k / 4.  Row 0: the circle, (x, y) =
+// (cos, sin); row n - 2 (n = 3..8): the regular n-gon of circumradius 1 with a vertex
+// at angle 0, (x, y) = its boundary point in the same direction, at distance
+// cos(pi / n) / cos(phi - pi / n), phi = the direction modulo 2 pi / n.  The radius
+// fraction stays the tap's distance in the aperture's own norm.
+constexpr int kRingRows = 7;
+static __constant__ float3 c_rings[kRingRows][81];
 
 // Fill this translation unit's copy of the tables (computed in double, rounded once).
 static inline int upload_filter_tables() {
     float2 pre[8];
     for (int k = 0; k < 8; k++) pre[k] = make_float2((float)cos(k * M_PI / 4.0), (float)sin(k * M_PI / 4.0));
-    float3 ring[81];
-    ring[0] = make_float3(0.f, 0.f, 0.f);
-    int t = 1;
-    for (int k = 1; k <= 4; k++)
-        for (int m = 0; m < 8 * k; m++, t++) {
-            double th = 2.0 * M_PI * m / (8.0 * k);
-            ring[t] = make_float3((float)cos(th), (float)sin(th), (float)(k / 4.0));
-        }
+    static float3 ring[kRingRows][81];
+    for (int row = 0; row < kRingRows; row++) {
+        const int n = row ? row + 2 : 0;
+        ring[row][0] = make_float3(0.f, 0.f, 0.f);
+        int t = 1;
+        for (int k = 1; k <= 4; k++)
+            for (int m = 0; m < 8 * k; m++, t++) {
+                const double th = 2.0 * M_PI * m / (8.0 * k);
+                double rho = 1.0;
+                if (n) {
+                    const double sector = 2.0 * M_PI / n;
+                    const double phi = th - sector * floor(th / sector);
+                    rho = cos(M_PI / n) / cos(phi - M_PI / n);
+                }
+                ring[row][t] = make_float3((float)(rho * cos(th)), (float)(rho * sin(th)), (float)(k / 4.0));
+            }
+    }
     cudaError_t e1 = cudaMemcpyToSymbol(c_pre8, pre, sizeof(pre));
-    cudaError_t e2 = cudaMemcpyToSymbol(c_ring81, ring, sizeof(ring));
+    cudaError_t e2 = cudaMemcpyToSymbol(c_rings, ring, sizeof(ring));
     return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : -1;
 }
 

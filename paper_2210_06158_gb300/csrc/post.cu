@@ -123,10 +123,11 @@ template <bool CLAMP>
 __device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const DevParams &p, const float4 *__restrict__ pre,
                                           const float *__restrict__ z_h, float R, float z0, float r0, float &ax,
                                           float &ay, float &az, float &bright, float &wsum) {
-    const float kInvSqrtPi = 0.56418958354775628f, kInvPi = 0.31830988618379067f;
+    const float kInvSqrtA = p.inv_sqrt_area, kInvA = p.inv_area;
+    const int ring = p.ring;
 #pragma unroll 3
     for (int t = 0; t < 81; t++) {
-        float3 u = c_ring81[t];
+        float3 u = c_rings[ring][t];
         float dist = u.z * R;
         float x = i + dist * u.x, y = j + dist * u.y;
         float4 s;
@@ -135,8 +136,8 @@ __device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const De
         else bilinear4z_interior(pre, z_h, W2, x, y, s, zi);
         float ri = fabsf(s.w);
         float wf = sat((z0 - zi) * p.inv_depth_range);
-        float rr = fmaxf(ri, kInvSqrtPi);
-        float a = __fdividef(kInvPi, rr * rr);
+        float rr = fmaxf(ri, kInvSqrtA);
+        float a = __fdividef(kInvA, rr * rr);
         float Df = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
         float Db = sat((fminf(ri, r0) - dist) * p.inv_cover_ramp + 0.5f);
         float W = (wf * Df + (1.f - wf) * Db) * a;
@@ -215,11 +216,12 @@ __global__ void __launch_bounds__(256) k_main_filter_tiled(const __grid_constant
     const float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
     const float z0 = __ldg(&z_h[q]);
     const float r0 = fabsf(__ldg(&pre[q]).w);
-    const float kInvSqrtPi = 0.56418958354775628f, kInvPi = 0.31830988618379067f;
+    const float kInvSqrtA = p.inv_sqrt_area, kInvA = p.inv_area;
+    const int ring = p.ring;
     float ax = 0.f, ay = 0.f, az = 0.f, bright = 0.f, wsum = 0.f;
 #pragma unroll 3
     for (int t = 0; t < 81; t++) {
-        const float3 u = c_ring81[t];
+        const float3 u = c_rings[ring][t];
         const float dist = u.z * R;
         const float x = i + dist * u.x, y = j + dist * u.y;
         const float xf = floorf(x), yf = floorf(y);
@@ -231,8 +233,8 @@ __global__ void __launch_bounds__(256) k_main_filter_tiled(const __grid_constant
         const float zi = w00 * sm_z[b] + w10 * sm_z[b + 1] + w01 * sm_z[b + tw] + w11 * sm_z[b + tw + 1];
         const float ri = fabsf(s.w);
         const float wf = sat((z0 - zi) * p.inv_depth_range);
-        const float rr = fmaxf(ri, kInvSqrtPi);
-        const float a = __fdividef(kInvPi, rr * rr);
+        const float rr = fmaxf(ri, kInvSqrtA);
+        const float a = __fdividef(kInvA, rr * rr);
         const float Df = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
         const float Db = sat((fminf(ri, r0) - dist) * p.inv_cover_ramp + 0.5f);
         const float W = (wf * Df + (1.f - wf) * Db) * a;

@@ -221,11 +221,11 @@ __device__ __forceinline__ void bilin_acc(const MipLevel &L, float x, float y, f
 
 template <bool CLAMP, bool H>
 __device__ __forceinline__ void recon_taps(const MipLevel &L0, const MipLevel &L1, int i, int j, float R, float t,
-                                           float inv_ramp, float4 &num, float &den) {
+                                           float inv_ramp, int ring, float4 &num, float &den) {
     const float fi = (float)i, fj = (float)j, t0 = 1.f - t;
 #pragma unroll 3
     for (int k = 0; k < 81; k++) {
-        const float3 u = c_ring81[k];
+        const float3 u = c_rings[ring][k];
         // dist and the cover weight D are rounded explicitly (no contraction left to the
         // compiler), so that every instance of this kernel computes the same bits
         const float dist = __fmul_rn(u.z, R);
@@ -282,11 +282,11 @@ __global__ void __launch_bounds__(256) k_recon(const __grid_constant__ AS as_) {
     float4 num = make_float4(0.f, 0.f, 0.f, 0.f);
     float den = 0.f;
     if (p.f16) {
-        if (interior) recon_taps<false, true>(L0, L1, i, j, R, t, p.inv_cover_ramp, num, den);
-        else recon_taps<true, true>(L0, L1, i, j, R, t, p.inv_cover_ramp, num, den);
+        if (interior) recon_taps<false, true>(L0, L1, i, j, R, t, p.inv_cover_ramp, p.ring, num, den);
+        else recon_taps<true, true>(L0, L1, i, j, R, t, p.inv_cover_ramp, p.ring, num, den);
     } else {
-        if (interior) recon_taps<false, false>(L0, L1, i, j, R, t, p.inv_cover_ramp, num, den);
-        else recon_taps<true, false>(L0, L1, i, j, R, t, p.inv_cover_ramp, num, den);
+        if (interior) recon_taps<false, false>(L0, L1, i, j, R, t, p.inv_cover_ramp, p.ring, num, den);
+        else recon_taps<true, false>(L0, L1, i, j, R, t, p.inv_cover_ramp, p.ring, num, den);
     }
     float4 f = den > 0.f ? f4scale(1.f / den, num) : o;
     st_img(out, q, make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b)), p.f16);

@@ -391,9 +391,24 @@ __device__ __noinline__ void lens_ray(const DevCam &cam, const DevParams &p, uin
     philox2(q, (unsigned long long)s, cam.frame, 0ull, p.seed, p.session, x0, x1);
     float u1 = (float)(x0 >> 40) * 5.9604644775390625e-8f;
     float u2 = (float)(x1 >> 40) * 5.9604644775390625e-8f;
-    float rr = cam.lens_r * sqrtf(u1), sn, cs;
-    sincospif(2.f * u2, &sn, &cs);
-    float lx = rr * cs, ly = rr * sn;
+    float rr = cam.lens_r * sqrtf(u1), lx, ly;
+    if (p.blades == 0) {
+        float sn, cs;
+        sincospif(2.f * u2, &sn, &cs);
+        lx = rr * cs; ly = rr * sn;
+    } else {
+        // regular n-gon (vertex k at angle 2 pi k / n): sector k = floor(n u2), position
+        // t = n u2 - k along its edge; sqrt(u1) (lerp of the edge's vertices) is uniform
+        // over the triangle (centre, V_k, V_k+1)
+        const float a = u2 * (float)p.blades;
+        const int k = min((int)a, p.blades - 1);
+        const float t = a - (float)k;
+        float s0, c0, s1, c1;
+        sincospif(2.f * (float)k / (float)p.blades, &s0, &c0);
+        sincospif(2.f * (float)(k + 1) / (float)p.blades, &s1, &c1);
+        lx = rr * ((1.f - t) * c0 + t * c1);
+        ly = rr * ((1.f - t) * s0 + t * s1);
+    }
     L = cam.O + lx * cam.R + ly * cam.U;
     dir = normalize(Pf - L);
 }

@@ -59,7 +59,7 @@ class DofParams(C.Structure):
                 ("z_far_m", C.c_float), ("tile", C.c_uint32), ("albedo_seed", C.c_uint32),
                 ("seed", C.c_uint64), ("session", C.c_uint64), ("light_dir", _f3), ("k_a", C.c_float),
                 ("k_d", C.c_float), ("sky", _f3), ("emit", C.c_float), ("image_storage", C.c_uint32),
-                ("taa_alpha", C.c_float)]
+                ("taa_alpha", C.c_float), ("aperture_blades", C.c_uint32)]
 
 
 class DofGBuffer(C.Structure):
@@ -190,7 +190,7 @@ def params_struct(p: dict) -> DofParams:
               "bright_ramp", "mask_near_hpx", "z_far_m", "k_a", "k_d", "emit", "taa_alpha"):
         if k in p:
             setattr(o, k, float(p[k]))
-    for k in ("m", "spp", "ray_mode", "tile", "seed", "session", "image_storage"):
+    for k in ("m", "spp", "ray_mode", "tile", "seed", "session", "image_storage", "aperture_blades"):
         if k in p:
             setattr(o, k, int(p[k]))
     if "albedo_seed" in p:

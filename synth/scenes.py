@@ -407,7 +407,7 @@ def default_params(**over) -> dict:
              alpha=0.95, alpha_motion=0.8, var_w_recon=2000.0, b_max=0.9, h_edge=0.3,
              lod_scale=0.05, lod_max=3.0, max_coc_px=16.0, zof_ramp_px=0.25,
              cover_ramp_px=1.0, bright_lum=4.0, bright_ramp=1.0, mask_near_hpx=0.5,
-             z_far_m=1.0e5, tile=8, seed=1, session=0, taa_alpha=0.0,
+             z_far_m=1.0e5, tile=8, seed=1, session=0, taa_alpha=0.0, aperture_blades=0,
              light_dir=(0.3, -1.0, 0.5), k_a=0.1, k_d=1.0, sky=(0.5, 0.6, 0.8),
              emit=8.0, albedo_seed=1)
     p.update(over)

@@ -242,6 +242,25 @@ def test_frame_parity_bright_bokeh():
     _print(stats, "bokeh")
 
 
+@pytest.mark.parametrize("blades,name,W,H", [(6, "c3", 384, 216), (5, "bokeh", None, None)])
+def test_frame_parity_polygonal_aperture(blades, name, W, H):
+    """A regular n-gon aperture (a hexagon, and the odd pentagon on the bright-bokeh
+    scene): lens samples uniform over it, the 81-tap kernels of the main filter and the
+    reconstruction on it, sampleAlpha over its area; two frames against the oracle."""
+    w = make_workload(name, n_frames=2) if W is None else make_workload(name, W=W, H=H, n_frames=2)
+    prm = dict(w.params, aperture_blades=blades)
+    # the shape changes what the oracle computes, so the comparison below is not vacuous
+    osc = oracle.Scene(w.scene)
+    cam = w.camera(0)
+    gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, prm, w.W, w.H))
+    circ = oracle.frame(osc, cam, w.params, w.W, w.H, gb)
+    poly = oracle.frame(osc, cam, prm, w.W, w.H, gb)
+    assert np.abs(poly["main_out"] - circ["main_out"]).max() > 1e-2
+    assert np.abs(poly["out"] - circ["out"]).max() > 1e-2
+    stats = run_sequence(w, 2, prm)
+    _print(stats, f"{name}-{blades}-gon")
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_frame_parity_half_gbuffer(mode):
     """A G-buffer whose colour and normal planes are half precision (DOF_FMT_F16), in the
@@ -538,6 +557,10 @@ def test_host_validation_errors():
     with pytest.raises(dof.DofError) as e:
         dof.frame(ctx, sc, gb, bad, w.params, h)
     assert e.value.code == -1
+    for blades in (1, 2, 9):                         # aperture: 0 (circle) or 3..8 blades
+        with pytest.raises(dof.DofError) as e:
+            dof.frame(ctx, sc, gb, cam, dict(w.params, aperture_blades=blades), h)
+        assert e.value.code == -1
     gb2 = dict(color=torch.zeros((38, 64, 4), device=dev), depth=torch.ones((38, 64), device=dev))
     with pytest.raises(dof.DofError) as e:
         dof.frame(ctx, sc, gb2, cam, w.params, h)
