@@ -412,12 +412,13 @@ def test_tree_shape_does_not_change_hits():
 
 
 def test_batch_equals_alone():
-    """dof_batch_frame over sessions of different sizes, scenes, lenses and ray modes
-    gives, for every session, exactly what dof_frame gives for it alone."""
+    """dof_batch_frame over sessions of different sizes, scenes, lenses, ray modes and
+    aperture shapes gives, for every session, exactly what dof_frame gives for it alone."""
     from paper_2210_06158_gb300 import dof
     import torch
     dev = torch.device("cuda", 0)
-    specs = [("c1", 256, 144, {}), ("c2", 322, 182, {}), ("c3", 192, 108, {}), ("c1", 130, 74, dict(ray_mode=1, m=4))]
+    specs = [("c1", 256, 144, {}), ("c2", 322, 182, dict(aperture_blades=6)), ("c3", 192, 108, {}),
+             ("c1", 130, 74, dict(ray_mode=1, m=4, aperture_blades=5))]
     ctx = dof.Context(0)
     sess = []
     for k, (name, W, H, over) in enumerate(specs):
