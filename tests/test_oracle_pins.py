@@ -295,6 +295,56 @@ def test_partial_occlusion_circular_segment():
     assert checked == 48
 
 
+def _polygon_share_right_of(n, tau):
+    """Share of the regular n-gon (circumradius 1, a vertex at angle 0) with x > tau,
+    by clipping its vertex list against the half-plane and the shoelace formula."""
+    ang = 2 * np.pi * np.arange(n) / n
+    pts = list(zip(np.cos(ang), np.sin(ang)))
+    out = []
+    for k in range(n):
+        a, b = pts[k], pts[(k + 1) % n]
+        if a[0] > tau:
+            out.append(a)
+        if (a[0] > tau) != (b[0] > tau):
+            t = (tau - a[0]) / (b[0] - a[0])
+            out.append((tau, a[1] + t * (b[1] - a[1])))
+    if len(out) < 3:
+        return 0.0
+    x, y = np.array(out).T
+    area = 0.5 * abs(np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y))
+    return min(1.0, area / (0.5 * n * np.sin(2 * np.pi / n)))
+
+
+@pytest.mark.parametrize("n", [5, 6])
+def test_partial_occlusion_polygonal_aperture(n):
+    """The partial-occlusion scene above with an n-blade aperture: a ray is blocked iff
+    its lens point has L_x > -P_fx s / (1 - s), so the blocked share is the part of the
+    n-gon right of that line (the pentagon is not symmetric about x = 0, so this also
+    fixes the aperture's orientation along the camera's right axis)."""
+    W, H, spp = 512, 4, 4096
+    sc = oracle.Scene(plane_scene([(1.0, "right", 0.0, 0), (20.0, "full", 0.0, 0)]))
+    cam = axis_camera()
+    prm = default_params(spp=spp, mask_near_hpx=0.0, max_coc_px=64.0, aperture_blades=n)
+    gb = oracle.gbuffer(sc, cam, prm, W, H)
+    fr = oracle.frame(sc, cam, prm, W, H, oracle.gbuffer_f32(gb))
+    g = _lens_geometry(W)
+    s = 1.0 / g["d"]
+    shares = []
+    for i in range(W // 2 // 2 - 12, W // 2 // 2 + 12):
+        Pfx = g["d"] * ((2 * i + 1) - W / 2) / g["F"]
+        tau = (-Pfx * s / (1 - s)) / g["A"]
+        p = _polygon_share_right_of(n, tau)
+        shares.append(p)
+        sig = math.sqrt(p * (1 - p) / spp)
+        for j in range(H // 2):
+            h = fr["rt"][j, i, 1]
+            assert abs(h - p) <= 4.5 * sig + 1e-3, (i, tau, h, p)
+    # the polygon's shares differ from the disk's where the line crosses it
+    disk = [seg_fraction(-Pfx * s / (1 - s) / g["A"]) for Pfx in
+            [g["d"] * ((2 * i + 1) - W / 2) / g["F"] for i in range(W // 4 - 12, W // 4 + 12)]]
+    assert max(abs(a - b) for a, b in zip(shares, disk)) > 0.02
+
+
 def test_thin_lens_step_edge_behind_focus():
     """A coplanar colour step at z = 30 m (behind the 10 m focus plane): the ray
     lands at x = L_x (1 - s) + P_fx s, s = 3, so it lands right of the edge iff
