@@ -481,6 +481,7 @@ static void history_free(DofHistory *h) {
     dof_free(c, h->nrays, 4 * N); dof_free(c, h->queue, 4 * N); dof_free(c, h->counters, 32);
     dof_free(c, h->first_ray, 4 * N); dof_free(c, h->ray_pix, 4 * N * h->max_rays);
     dof_free(c, h->hits, 8 * N * h->max_rays);
+    dof_free(c, h->ray_a, 16 * N * h->max_rays); dof_free(c, h->ray_b, 8 * N * h->max_rays);
     dof_free(c, h->ray_prim, 4 * N * h->max_rays);
     dof_free(c, h->rt, 64 * N); dof_free(c, h->crt, 16 * N); dof_free(c, h->rt_med, 16 * N);
     dof_free(c, h->recon, 16 * N); dof_free(c, h->ct, 4 * N); dof_free(c, h->var, 4 * N);
@@ -547,6 +548,7 @@ extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, 
     A((void **)&h->nrays, 4 * N); A((void **)&h->queue, 4 * N); A((void **)&h->counters, 32);
     A((void **)&h->first_ray, 4 * N); A((void **)&h->ray_pix, 4 * N * max_rays);
     A((void **)&h->hits, 8 * N * max_rays);
+    A((void **)&h->ray_a, 16 * N * max_rays); A((void **)&h->ray_b, 8 * N * max_rays);
     if (flags & DOF_HIST_RECORD_RAYS) A((void **)&h->ray_prim, 4 * N * max_rays);
     A((void **)&h->rt, 64 * N); A((void **)&h->crt, 16 * N); A((void **)&h->rt_med, 16 * N);
     A((void **)&h->recon, 16 * N); A((void **)&h->ct, 4 * N); A((void **)&h->var, 4 * N);
@@ -654,7 +656,7 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
     d.tiles = h->tiles; d.tiles_dil = h->tiles_dil;
     d.nrays = h->nrays; d.ray_prim = h->ray_prim;
     d.queue = h->queue; d.first_ray = h->first_ray; d.ray_pix = h->ray_pix; d.counters = h->counters;
-    d.hits = h->hits;
+    d.hits = h->hits; d.ray_a = h->ray_a; d.ray_b = h->ray_b;
     int L = (int)ceilf(r.params->lod_max) + 1;
     d.mip_L = L < 1 ? 1 : (L > 4 ? 4 : L);
     for (int l = 0; l < 4; l++) {

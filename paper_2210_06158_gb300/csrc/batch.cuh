@@ -45,6 +45,8 @@ struct SessDesc {
     int32_t *nrays, *ray_prim;
     uint32_t *queue, *first_ray, *ray_pix, *counters;
     int2 *hits;
+    float4 *ray_a;
+    float2 *ray_b;
     float4 *mip0[4];
     float2 *mip1[4];
     int mip_w[4], mip_h[4], mip_L;

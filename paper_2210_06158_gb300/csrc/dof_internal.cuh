@@ -142,6 +142,8 @@ struct DofHistory {
     uint32_t *first_ray;           // per pixel: index of its first ray in the ray list
     uint32_t *ray_pix;             // ray list: pixel of each ray (N * max_rays)
     int2 *hits;                    // per ray: (sorted triangle index or -1, t bits)
+    float4 *ray_a;                 // per ray as the tracer made it: (origin, dir.x) ...
+    float2 *ray_b;                 // ... and (dir.y, dir.z); the shader reads them back
     uint32_t *counters;            // [0] queue length, [1] rays, [2] work cursor, [3] device status,
                                    // [4..5] node visits (u64), [6..7] triangle tests (u64)
     int32_t *ray_prim;

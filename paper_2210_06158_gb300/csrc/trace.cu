@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ AS
 // ---------------------------------------------------------------------------
 // The ray of half-resolution pixel q and lens sample s: direction through the pixel
 // and the lens centre meets the focus plane at Pf; Philox(counter = (q, s, frame, 0),
-// key = (seed, session)) gives the lens point.  Not inlined, so that the tracer and the
-// shader compute bit-identical rays.
+// key = (seed, session)) gives the lens point.  The tracer makes each ray once and keeps
+// it (origin, direction) for the shader.
 __device__ __noinline__ void lens_ray(const DevCam &cam, const DevParams &p, uint32_t q, int s, float3 &L,
                                       float3 &dir) {
     int i = (int)(q % (uint32_t)cam.W2), j = (int)(q / (uint32_t)cam.W2);
@@ -472,6 +472,9 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
                     int sm = (int)(r - __ldg(&S.first_ray[q]));
                     float3 L, dir;
                     lens_ray(S.cam, S.p, q, sm, L, dir);
+                    // kept for the shader, which takes the ray as made here
+                    S.ray_a[r] = make_float4(L.x, L.y, L.z, dir.x);
+                    S.ray_b[r] = make_float2(dir.y, dir.z);
                     ray = make_ray(L, dir);
                     if (kWide) {
                         nodes4 = S.sc.nodes4;
@@ -535,9 +538,9 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
     }
 }
 
-// Shading and the per-pixel near/far split of the masked pixel queue[e]: its rays
-// are regenerated (bit-identical to the tracer's), shaded at their recorded hits and
-// reduced in sample order.
+// Shading and the per-pixel near/far split of the masked pixel queue[e]: its rays, as
+// the tracer made and kept them, are shaded at their recorded hits and reduced in
+// sample order.
 template <class AS>
 __global__ void __launch_bounds__(128) k_shade(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
@@ -562,9 +565,13 @@ __global__ void __launch_bounds__(128) k_shade(const __grid_constant__ AS as_) {
     uint32_t f = first_ray[q];
     float Sw = 0.f, Bn = 0.f, Bf = 0.f, Fw = 0.f;
     float3 An = make_float3(0.f, 0.f, 0.f), Af = An, Pfar = An;
+    const float4 *__restrict__ ray_a = S.ray_a;
+    const float2 *__restrict__ ray_b = S.ray_b;
     for (int s = 0; s < n; s++) {
-        float3 L, dir;
-        lens_ray(cam, p, q, s, L, dir);
+        // the ray as the tracer made it (lens_ray): origin on the lens and direction
+        const float4 ra = __ldg(&ray_a[f + s]);
+        const float2 rb = __ldg(&ray_b[f + s]);
+        const float3 L = make_float3(ra.x, ra.y, ra.z), dir = make_float3(ra.w, rb.x, rb.y);
         int2 hh = __ldg(&hits[f + s]);
         HitRec h{__int_as_float(hh.y), -1, hh.x};
         float3 col;
