@@ -65,8 +65,8 @@ BYTES = {
     "k_mask_compact": [("N", 4.0), ("M", 8.0), ("R", 4.0)],   # ray count per hpx; queue entry and
                                          # first-ray index per masked hpx; ray list entry per ray
                                          # (+ 4 B/N of x_f read in the adaptive mode, not counted)
-    "k_trace_rays": ("R", 12.0),              # per ray: ray list 4 read, hit 8 written (BVH reads hit L2)
-    "k_shade": [("M", 76.0), ("R", 8.0)],   # queue, count, first ray read, 4 x float4 written; hits read
+    "k_trace_rays": ("R", 36.0),              # per ray: ray list 4 read, hit 8 + kept ray 24 written (BVH reads hit L2)
+    "k_shade": [("M", 76.0), ("R", 32.0)],  # queue, count, first ray read, 4 x float4 written; hits + kept rays read
     "k_accumulate": ("N", 192.0),        # rt 64 + z 4 + nrays 4 + history 48 read; history 48 + 24 written
     "k_median_rt": ("N", 72.0),          # fused: variance blur (var 4 read, 4 written), RT median
                                          # (crt 16 + nrays 4 read, 16 written), mip 0 (ct 4 read,
