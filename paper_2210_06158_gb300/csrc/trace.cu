@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ AS
 // and the lens centre meets the focus plane at Pf; Philox(counter = (q, s, frame, 0),
 // key = (seed, session)) gives the lens point.  The tracer makes each ray once and keeps
 // it (origin, direction) for the shader.
-__device__ __noinline__ void lens_ray(const DevCam &cam, const DevParams &p, uint32_t q, int s, float3 &L,
+__device__ __forceinline__ void lens_ray(const DevCam &cam, const DevParams &p, uint32_t q, int s, float3 &L,
                                       float3 &dir) {
     int i = (int)(q % (uint32_t)cam.W2), j = (int)(q / (uint32_t)cam.W2);
     float3 dp = pixel_dir(cam, 2.f * i + 1.f, 2.f * j + 1.f);
