@@ -113,12 +113,15 @@ class FakeExecutor:
 class GpuExecutor:
     """Drives libdof: per admitted session a device scene (BVH), a history and a small
     ring of device G-buffers rendered by the G-buffer producer; batches go through
-    dof_batch_frame on one of two streams, completion is an event."""
+    dof_batch_frame on one of two streams, completion is an event.  per_frame: each
+    request of a batch runs as its own dof_frame instead (the plain per-frame form);
+    fp16: the sessions store their colour image buffers in FP16 (FP32 arithmetic)."""
 
-    def __init__(self, budget_bytes, device=0, gbuf_ring=2):
+    def __init__(self, budget_bytes, device=0, gbuf_ring=2, per_frame=False, fp16=False):
         import torch
         from . import dof
         self.torch, self.dof = torch, dof
+        self.per_frame, self.fp16 = per_frame, fp16
         self.ctx = dof.Context(device, mem_budget_bytes=budget_bytes)
         self.device = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(2)]
@@ -157,8 +160,9 @@ class GpuExecutor:
             del g["prim"]
             gbs.append(g)
         out = torch.empty((spec.height, spec.width, 4), dtype=torch.float32, device=self.device)
+        prm = dict(spec.params, image_storage=1) if self.fp16 else spec.params
         self.sessions[sid] = dict(spec=spec, scene=scene, hist=hist, gbs=gbs, out=out,
-                                  pstruct=dof.params_struct(spec.params))
+                                  pstruct=dof.params_struct(prm))
         torch.cuda.synchronize()
 
     def close(self, sid):
@@ -183,7 +187,12 @@ class GpuExecutor:
             items.append(dict(scene=s["scene"], gbuf=s["gbs"][r.frame % self.ring], cam=self.camera(s, r.frame),
                               params=s["pstruct"], hist=s["hist"], out=s["out"]))
         st = self.streams[stream]
-        self.dof.batch_frame(self.ctx, items, stream=st)
+        if self.per_frame:
+            for it in items:
+                self.dof.frame(self.ctx, it["scene"], it["gbuf"], None, None, it["hist"], it["out"], stream=st,
+                               cam_struct=it["cam"], params_s=it["params"])
+        else:
+            self.dof.batch_frame(self.ctx, items, stream=st)
         ev = self.torch.cuda.Event()
         ev.record(st)
         return ev
