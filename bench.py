@@ -47,14 +47,15 @@ FLOP_PER_TRI = 48.0
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes (read + write) per launch from the last ncu capture of each kernel on the
-# workload (profiles/top_kernels_*.md); a kernel or workload changed since then has no
+# workload (profiles/top_kernels_*.md, the tracer: profiles/tracer_traffic_c2_c3.md); a
+# kernel or workload changed since then has no
 # entry.  The 4K tracer was captured at 1920x1080 (same scene, lens, 4 spp) and is
 # scaled by the rays of a full launch (6.72M / 1.78M); its DRAM writes are the rays it
 # keeps for the shader that L2 does not hold, so the scaled figure is an estimate.
 PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": 10.1e6, "k_recon": 25.3e6,
                            "k_main_filter": 10.4e6, "k_accumulate": 56.2e6, "k_composite": 63.4e6,
                            "k_downscale_tiles": 41.7e6},
-                    "c3": {"k_trace_rays<0>": 31.6e6 * 6.72 / 1.78}}
+                    "c3": {"k_trace_rays<0>": 30.7e6 * 6.72 / 1.78}}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.

@@ -15,6 +15,7 @@ struct Ray {
     float3 o, d, inv;
     float3 off0, off1;  // o * inv moved outward per axis (the fused slab test)
     int perm;           // 2 kz + (kx, ky swapped): the axis order of the watertight test
+    int oct;            // direction octant: bit 0/1/2 set where inv.x/y/z < 0
     float Sx, Sy, Sz;
 };
 
@@ -44,6 +45,7 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     const bool sw = comp(d, kz) < 0.f;
     if (sw) { int t = kx; kx = ky; ky = t; }
     r.perm = 2 * kz + (sw ? 1 : 0);
+    r.oct = (r.inv.x < 0.f ? 1 : 0) | (r.inv.y < 0.f ? 2 : 0) | (r.inv.z < 0.f ? 4 : 0);
     float dz = comp(d, kz);
     r.Sx = comp(d, kx) / dz;
     r.Sy = comp(d, ky) / dz;

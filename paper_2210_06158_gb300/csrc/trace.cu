@@ -42,6 +42,46 @@ __device__ __forceinline__ bool box_hit(const Ray &r, float3 lo, float3 hi, floa
     return tmin <= tmax * 1.0000005f;
 }
 
+// The slab test for a ray of known octant: per axis the near plane is lo where inv >= 0
+// and hi where inv < 0, so the near and far distances need no min/max.  With the
+// offsets of make_ray (off0 for lo, off1 for hi) these are exactly the min and max
+// that box_hit takes, so both tests give the same answer.
+template <bool NX, bool NY, bool NZ>
+__device__ __forceinline__ bool box_hit_o(const Ray &r, float3 lo, float3 hi, float tbest, float &tent) {
+    const float nx = NX ? fmaf(hi.x, r.inv.x, -r.off1.x) : fmaf(lo.x, r.inv.x, -r.off0.x);
+    const float fx = NX ? fmaf(lo.x, r.inv.x, -r.off0.x) : fmaf(hi.x, r.inv.x, -r.off1.x);
+    const float ny = NY ? fmaf(hi.y, r.inv.y, -r.off1.y) : fmaf(lo.y, r.inv.y, -r.off0.y);
+    const float fy = NY ? fmaf(lo.y, r.inv.y, -r.off0.y) : fmaf(hi.y, r.inv.y, -r.off1.y);
+    const float nz = NZ ? fmaf(hi.z, r.inv.z, -r.off1.z) : fmaf(lo.z, r.inv.z, -r.off0.z);
+    const float fz = NZ ? fmaf(lo.z, r.inv.z, -r.off0.z) : fmaf(hi.z, r.inv.z, -r.off1.z);
+    const float tmin = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.f));
+    const float tmax = fminf(fminf(fx, fy), fminf(fz, tbest));
+    tent = tmin;
+    return tmin <= tmax * 1.0000005f;
+}
+
+// both child boxes of a binary node, the octant's instance chosen by conditional
+// branches (uniform across a warp whose rays share the octant)
+__device__ __forceinline__ void box_pair(const Ray &r, const float4 &a, const float4 &b, const float4 &c,
+                                         float tbest, bool &h0, float &t0, bool &h1, float &t1) {
+    const float3 lo0 = make_float3(a.x, a.y, a.z), hi0 = make_float3(a.w, b.x, b.y);
+    const float3 lo1 = make_float3(b.z, b.w, c.x), hi1 = make_float3(c.y, c.z, c.w);
+#define DOF_BOX_PAIR(X, Y, Z)                                   \
+    {                                                           \
+        h0 = box_hit_o<X, Y, Z>(r, lo0, hi0, tbest, t0);        \
+        h1 = box_hit_o<X, Y, Z>(r, lo1, hi1, tbest, t1);        \
+    }
+    const int o = r.oct;
+    if (o & 4) {
+        if (o & 2) { if (o & 1) DOF_BOX_PAIR(true, true, true) else DOF_BOX_PAIR(false, true, true) }
+        else { if (o & 1) DOF_BOX_PAIR(true, false, true) else DOF_BOX_PAIR(false, false, true) }
+    } else {
+        if (o & 2) { if (o & 1) DOF_BOX_PAIR(true, true, false) else DOF_BOX_PAIR(false, true, false) }
+        else { if (o & 1) DOF_BOX_PAIR(true, false, false) else DOF_BOX_PAIR(false, false, false) }
+    }
+#undef DOF_BOX_PAIR
+}
+
 // the same slab test on one box of a 4-wide node (boxes stored per axis)
 __device__ __forceinline__ bool box_hit_w(const Ray &r, float lx, float ly, float lz, float hx, float hy, float hz,
                                           float tbest, float &tent) {
@@ -151,8 +191,8 @@ __device__ __forceinline__ bool step2(const Ray &ray, const BvhNode *__restrict_
         float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
         int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
         float t0, t1;
-        bool h0 = box_hit(ray, make_float3(a.x, a.y, a.z), make_float3(a.w, b.x, b.y), h.t, t0);
-        bool h1 = box_hit(ray, make_float3(b.z, b.w, c.x), make_float3(c.y, c.z, c.w), h.t, t1);
+        bool h0, h1;
+        box_pair(ray, a, b, c, h.t, h0, t0, h1, t1);
         if (h0 && h1) {
             int nearc = t0 <= t1 ? ref.x : ref.y, farc = t0 <= t1 ? ref.y : ref.x;
             if (sp < kStack) stack[sp++] = farc;
