@@ -140,7 +140,7 @@ class GpuExecutor:
     def estimate_bytes(self, spec):
         hpx = (spec.width // 2) * (spec.height // 2)
         mr = int(spec.params.get("spp", 1)) if int(spec.params.get("ray_mode", 0)) == 0 else int(spec.params.get("m", 1))
-        return int(hpx * (400 + 12 * mr) + spec.scene.n_tris * 112)
+        return int(hpx * (400 + 36 * mr) + spec.scene.n_tris * 112)
 
     def open(self, sid, spec):
         from synth.scenes import Camera
