@@ -380,9 +380,13 @@ int dof_debug_read(DofHistory *hist, int which, void *host_dst, size_t bytes);
  *   tiles_dil  device, ceil(width/16)*ceil(height/16) float2 (8-byte aligned), written
  *   cam, p     only the lens (f, N, focus, sensor width), tile, max_coc_px and z_far_m
  *              are used
- * Sizes whose tile count exceeds DOF_NOALLOC_MAX_TILES return DOF_ERR_INVALID_ARG.
- * The first call on a device looks up that device's address of the array (with the
- * device current); make that first call before any stream capture.  Every call shares
+ * Sizes whose tile count exceeds DOF_NOALLOC_MAX_TILES, sizes above 16384 and lens
+ * values that are not finite return DOF_ERR_INVALID_ARG.
+ * Every call looks up the array's address in the current device's context with
+ * cudaGetSymbolAddress (nothing is cached, so the call stays valid after a device
+ * reset or from another context); the first call in a context also loads the
+ * library's device code there, so make that first call before any stream capture.
+ * Every call shares
  * the array and it keeps the previous call's contents (each call overwrites what it
  * reads); calls that overlap on the GPU race on it and must be serialised by the
  * caller.  Enqueued on `stream`; returns without synchronising. */

@@ -28,6 +28,12 @@ _lock = threading.Lock()
 _lib = None
 
 
+# Relative tolerance of the hit-id tie classification: a ray within 1e-6 (|o| + s)
+# of a triangle's edge segment, or two hits whose distances agree to that tolerance,
+# may be resolved either way by an FP32 tracer.
+HIT_TIE_REL_TOL = 1e-6
+
+
 def build(force: bool = False) -> Path:
     """Compile the oracle (gcc, -O2, no FP contraction so x86 and Arm agree)."""
     srcs = [_HERE / s for s in _SOURCES]
@@ -111,8 +117,8 @@ def _declare(L):
     for fn in (L.or_closest, L.or_closest_brute):
         fn.restype = C.c_int
         fn.argtypes = [vp, vp, vp, vp]
-    L.or_near_tie.restype = C.c_int
-    L.or_near_tie.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_double]
+    L.or_hit_check.restype = C.c_int
+    L.or_hit_check.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_double]
     L.or_coc.restype = C.c_double
     L.or_coc.argtypes = [C.POINTER(OrCamera), C.c_int, C.c_double]
     L.or_zof_bounds.argtypes = [C.POINTER(OrCamera), C.c_int, vp, vp]
@@ -227,10 +233,22 @@ class Scene:
         prim = fn(self.ptr, _p(o), _p(d), _p(t))
         return prim, (float(t[0]) if prim >= 0 else float("inf"))
 
-    def near_tie(self, o, d, prim_a, prim_b, rel_tol=1e-5) -> bool:
+    def hit_check(self, o, d, prim_kernel, prim_oracle, rel_tol=HIT_TIE_REL_TOL) -> int:
+        """Validity of a closest hit computed in lower precision (prim_kernel, -1 = no
+        hit) for the ray (o, d), against the FP64 answer prim_oracle: 0 = equal ids;
+        1 = depth tie (both clean hits at distances rounding cannot order); 2 = the
+        FP64 hit is grazed (within rel_tol (|o| + s) of an edge segment); 3 = the
+        kernel's triangle is grazed; 4 = no hit reported and every hit is grazed;
+        negative = invalid (-1 the kernel's triangle is not hit within rounding, -2 a
+        clean hit lies certainly in front of it, -3 its clean hit lies certainly in
+        front of the FP64 answer)."""
         o = np.ascontiguousarray(o, dtype=np.float64)
         d = np.ascontiguousarray(d, dtype=np.float64)
-        return bool(lib().or_near_tie(self.ptr, _p(o), _p(d), int(prim_a), int(prim_b), rel_tol))
+        return int(lib().or_hit_check(self.ptr, _p(o), _p(d), int(prim_kernel), int(prim_oracle), rel_tol))
+
+    def near_tie(self, o, d, prim_kernel, prim_oracle, rel_tol=HIT_TIE_REL_TOL) -> bool:
+        """True when prim_kernel is a valid answer (equal, or a rounding tie)."""
+        return self.hit_check(o, d, prim_kernel, prim_oracle, rel_tol) >= 0
 
 
 def coc(cam, W, z) -> float:

@@ -192,44 +192,6 @@ int or_closest(const OrScene *s, const double o[3], const double d[3], double *t
     return best;
 }
 
-/* Is the disagreement "prim_a vs prim_b" for the ray (o, d) a floating-point near
- * tie?  Yes when the ray crosses the plane of either triangle within
- * rel_tol * (t + |o|) of that triangle's boundary (an edge graze, from inside or
- * outside) or runs nearly parallel to it, or when it passes inside both triangles
- * at relatively equal distance (a depth tie).  (The inner side of edge A->B is
- * where (B - A) x (P - A) points along the face normal.) */
-static int graze(const OrScene *s, int prim, const double o[3], const double d[3], double rel_tol,
-                 double *t_out, int *inside) {
-    const double *v = s->v + 9 * (size_t)prim;
-    double e1[3], e2[3], n[3];
-    sub3(v + 3, v, e1);
-    sub3(v + 6, v, e2);
-    cross3(e1, e2, n);
-    normalize3(n);
-    double dn = dot3(d, n);
-    *inside = 0;
-    if (fabs(dn) < 1e-6) { *t_out = INFINITY; return 1; }
-    double tv[3];
-    sub3(v, o, tv);
-    double t = dot3(tv, n) / dn;
-    *t_out = t;
-    double P[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
-    double tol = rel_tol * (fabs(t) + sqrt(dot3(o, o)));
-    int near_edge = 0, n_in = 0;
-    for (int e = 0; e < 3; e++) {
-        const double *A = v + 3 * e, *B = v + 3 * ((e + 1) % 3);
-        double ab[3], ap[3], c[3];
-        sub3(B, A, ab);
-        sub3(P, A, ap);
-        cross3(ab, ap, c);
-        double sd = dot3(c, n) / sqrt(dot3(ab, ab));   /* > 0 on the inner side */
-        if (fabs(sd) <= tol) near_edge = 1;
-        if (sd >= 0.0) n_in++;
-    }
-    *inside = (n_in == 3) && t > 0.0;
-    return near_edge;
-}
-
 double or_plane_t(const OrScene *s, int prim, const double o[3], const double d[3]) {
     const double *v = s->v + 9 * (size_t)prim;
     double e1[3], e2[3], n[3], tv[3];
@@ -242,16 +204,148 @@ double or_plane_t(const OrScene *s, int prim, const double o[3], const double d[
     return dot3(tv, n) / dn;
 }
 
-int or_near_tie(const OrScene *s, const double o[3], const double d[3], int prim_a, int prim_b,
-                double rel_tol) {
-    if (prim_a == prim_b) return 1;
-    double ta = INFINITY, tb = INFINITY;
-    int ia = 0, ib = 0;
-    int ga = prim_a >= 0 ? graze(s, prim_a, o, d, rel_tol, &ta, &ia) : 0;
-    int gb = prim_b >= 0 ? graze(s, prim_b, o, d, rel_tol, &tb, &ib) : 0;
-    if (ga || gb) return 1;
-    if (ia && ib && fabs(ta - tb) <= rel_tol * fmax(fabs(ta), fabs(tb))) return 1;
+/* ---- validity of a closest-hit answer computed in lower precision ------------
+ *
+ * A ray traced in FP32 may disagree with the FP64 closest hit only where rounding
+ * can change the answer: where the ray passes within rounding distance of a
+ * triangle's boundary (it may be counted inside or outside), or where two hits lie
+ * at distances that rounding cannot order.  The rounding of a ray made in FP32 moves
+ * it sideways by a distance proportional to |o| + s at ray parameter s, so "within
+ * rounding" is measured as the distance between the ray and each edge segment of the
+ * triangle, against rel_tol * (|o| + s).  The hit distance of a triangle the ray meets
+ * at incidence cos = |d.n| is uncertain by that sideways tolerance over cos. */
+
+enum { PROBE_MISS = 0, PROBE_GRAZED = 1, PROBE_CLEAN = 2 };
+typedef struct { int state; double t, dt; } TriProbe;
+
+/* Closest approach of the ray o + s d (s >= 0, |d| = 1) to the segment A + u e,
+ * u in [0, 1]: returns the distance and the ray parameter s there. */
+static double ray_segment(const double o[3], const double d[3], const double A[3], const double e[3],
+                          double *s_out) {
+    double w0[3];
+    sub3(o, A, w0);
+    double b = dot3(d, e), c = dot3(e, e), dd = dot3(d, w0), ee = dot3(e, w0);
+    double u, sp;
+    double den = c - b * b;            /* |e|^2 sin^2 of the angle between ray and edge */
+    if (c <= 0.0) {
+        u = 0.0;                        /* the edge is a point */
+    } else if (den > 1e-14 * c) {
+        u = (ee - dd * b) / den;
+    } else {
+        u = ee / c;                     /* parallel: the point of the edge nearest to o */
+    }
+    if (u < 0.0) u = 0.0;
+    if (u > 1.0) u = 1.0;
+    sp = u * b - dd;                    /* the ray's point nearest to A + u e */
+    if (sp < 0.0) {                     /* behind the origin: nearest point of the edge to o */
+        sp = 0.0;
+        u = c > 0.0 ? ee / c : 0.0;     /* (o - A).e / |e|^2 */
+        if (u < 0.0) u = 0.0;
+        if (u > 1.0) u = 1.0;
+    }
+    double r[3];
+    for (int k = 0; k < 3; k++) r[k] = w0[k] + sp * d[k] - u * e[k];
+    *s_out = sp;
+    return sqrt(dot3(r, r));
+}
+
+/* Classifies triangle prim for the ray (o, d), |d| = 1:
+ *   CLEAN   the FP64 test hits it and the ray stays clear of its edges by more than
+ *           the tolerance (a lower-precision test must hit it too);
+ *   GRAZED  the ray passes within the tolerance of an edge segment, in front of the
+ *           origin (a lower-precision test may hit or miss it);
+ *   MISS    neither (no test within rounding hits it).
+ * t is the hit distance (FP64 hit, else the plane's distance, else the ray parameter
+ * of the closest approach to the edge) and dt its uncertainty. */
+static TriProbe probe(const OrScene *s, int prim, const double o[3], const double d[3], double rel_tol) {
+    const double *v = s->v + 9 * (size_t)prim;
+    TriProbe r = {PROBE_MISS, INFINITY, 0.0};
+    double on = sqrt(dot3(o, o));
+    double best_gap = INFINITY, s_best = 0.0;
+    int grazed = 0;
+    for (int e = 0; e < 3; e++) {
+        const double *A = v + 3 * e, *B = v + 3 * ((e + 1) % 3);
+        double ab[3], se;
+        sub3(B, A, ab);
+        double dist = ray_segment(o, d, A, ab, &se);
+        double tol = rel_tol * (on + se);
+        if (dist <= tol) grazed = 1;
+        if (dist - tol < best_gap) { best_gap = dist - tol; s_best = se; }
+    }
+    double e1[3], e2[3], n[3];
+    sub3(v + 3, v, e1);
+    sub3(v + 6, v, e2);
+    cross3(e1, e2, n);
+    double nn = sqrt(dot3(n, n));
+    double cosi = nn > 0.0 ? fabs(dot3(d, n)) / nn : 0.0;
+    double th;
+    int hit = tri_hit(v, o, d, &th);
+    double t;
+    if (hit) t = th;
+    else if (nn > 0.0 && cosi > 1e-9) t = or_plane_t(s, prim, o, d);
+    else t = s_best;
+    double tol_t = rel_tol * (on + fabs(t));
+    double dt = tol_t / fmax(cosi, 1e-12) + tol_t;
+    if (hit && !grazed) { r.state = PROBE_CLEAN; r.t = t; r.dt = dt; return r; }
+    if (grazed && t > -dt) { r.state = PROBE_GRAZED; r.t = t; r.dt = dt; return r; }
+    return r;
+}
+
+/* Is there a CLEAN hit whose whole uncertainty interval lies before t_lim? */
+static int clean_hit_before(const OrScene *s, const double o[3], const double d[3], double t_lim,
+                            double rel_tol) {
+    if (s->n == 0 || !(t_lim > 0.0)) return 0;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const OrNode *nd = &s->nodes[stack[--sp]];
+        if (!box_hit(nd, o, d, t_lim)) continue;
+        if (nd->left < 0) {
+            for (int i = nd->first; i < nd->first + nd->count; i++) {
+                TriProbe p = probe(s, s->order[i], o, d, rel_tol);
+                if (p.state == PROBE_CLEAN && p.t + p.dt < t_lim) return 1;
+            }
+        } else {
+            stack[sp++] = nd->left;
+            stack[sp++] = nd->right;
+        }
+    }
     return 0;
+}
+
+/* Is prim_k (a closest hit computed in lower precision; -1 = no hit) a valid answer
+ * for the ray (o, d), given the FP64 answer prim_o?  The answer is valid when rounding
+ * can explain the difference: the kernel's triangle is hit within rounding (CLEAN or
+ * GRAZED), no CLEAN hit lies certainly in front of it, and, when it is CLEAN, the
+ * FP64 answer does not lie certainly behind it.  Returns
+ *    0  the ids agree
+ *    1  depth tie: both hits clean, at distances rounding cannot order
+ *    2  the FP64 hit is grazed (the kernel may miss it and see what lies behind)
+ *    3  the kernel's triangle is grazed (it may count a hit the FP64 test misses)
+ *    4  the kernel reports no hit and every hit along the ray is grazed
+ *   -1  the kernel's triangle is not hit within rounding
+ *   -2  a clean hit lies certainly in front of the kernel's answer
+ *   -3  the kernel's hit is clean and the FP64 answer lies certainly behind it
+ *       (or is a miss) */
+int or_hit_check(const OrScene *s, const double o_in[3], const double d_in[3], int prim_k, int prim_o,
+                 double rel_tol) {
+    if (prim_k == prim_o) return 0;
+    double o[3] = {o_in[0], o_in[1], o_in[2]}, d[3] = {d_in[0], d_in[1], d_in[2]};
+    normalize3(d);
+    TriProbe K = {PROBE_MISS, INFINITY, 0.0};
+    if (prim_k >= 0) {
+        if (prim_k >= s->n) return -1;
+        K = probe(s, prim_k, o, d, rel_tol);
+        if (K.state == PROBE_MISS) return -1;
+    }
+    double t_lim = prim_k >= 0 ? K.t - K.dt : INFINITY;
+    if (clean_hit_before(s, o, d, t_lim, rel_tol)) return -2;
+    if (prim_k < 0) return 4;
+    if (K.state == PROBE_GRAZED) return 3;
+    if (prim_o < 0 || prim_o >= s->n) return -3;
+    TriProbe O = probe(s, prim_o, o, d, rel_tol);
+    if (O.state == PROBE_MISS || O.t - O.dt > K.t + K.dt) return -3;
+    return O.state == PROBE_CLEAN ? 1 : 2;
 }
 
 /* murmur3's 32-bit finaliser (Appleby) */

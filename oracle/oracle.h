@@ -83,9 +83,11 @@ int or_scene_ntris(const OrScene *s);
 int or_closest(const OrScene *s, const double o[3], const double d[3], double *t);
 /* closest hit by testing every triangle (no acceleration structure) */
 int or_closest_brute(const OrScene *s, const double o[3], const double d[3], double *t);
-/* FP-near-tie test of two disagreeing answers (prim or -1) for the ray (o, d) */
-int or_near_tie(const OrScene *s, const double o[3], const double d[3], int prim_a, int prim_b,
-                double rel_tol);
+/* Validity of a closest hit computed in lower precision (prim_k, -1 = none) against
+ * the FP64 answer prim_o for the ray (o, d): 0 equal, 1..4 a valid rounding tie,
+ * negative an invalid answer (codes in or_scene.c) */
+int or_hit_check(const OrScene *s, const double o[3], const double d[3], int prim_k, int prim_o,
+                 double rel_tol);
 /* distance along (o, d) to the plane of triangle `prim` (+inf if parallel) */
 double or_plane_t(const OrScene *s, int prim, const double o[3], const double d[3]);
 void or_shade(const OrScene *s, const OrParams *p, int prim, const double o[3],

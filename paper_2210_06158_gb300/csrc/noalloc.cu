@@ -15,7 +15,6 @@
 // overlaps on the GPU (different streams, or different host threads without
 // ordering) race on the array and must be serialised by the caller.
 #include <math.h>
-#include <mutex>
 #include <string.h>
 
 #include "dof_internal.cuh"
@@ -26,11 +25,6 @@ constexpr int kMaxTiles = DOF_NOALLOC_MAX_TILES;
 
 // the scratch array: raw (undilated) tile maxima (near radius, |rho|)
 __device__ __align__(256) float2 g_tile_scratch[kMaxTiles];
-
-// host-side device addresses of g_tile_scratch, resolved once per device
-constexpr int kMaxDevices = 64;
-float2 *g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
 
 struct TileArgs {
     float cocK, d, rmax, z_far;
@@ -78,21 +72,17 @@ __global__ void k_dilate_scratch(TileArgs a, const float2 *raw, float2 *dil) {
     dil[ty * a.TW + tx] = make_float2(nm, am);
 }
 
-// Device address of g_tile_scratch on the current device (set-up on first use).
+// Device address of g_tile_scratch in the current device's context.  It is looked up
+// on every call, not cached: after cudaDeviceReset, or from another context on the same
+// device, the library's device code is loaded afresh and the array moves, so an address
+// kept from an earlier call could point at memory that is no longer this array.  The
+// lookup enqueues no work; the first one in a context loads the library's device code
+// there.
 int scratch_for_current_device(float2 **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return dof_cuda_check(e, "dof_coc_tiles_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices)
-        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: device %d beyond %d", dev, kMaxDevices);
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_tile_scratch);
-        if (e != cudaSuccess || !p) return dof_cuda_check(e, "dof_coc_tiles_noalloc: cudaGetSymbolAddress");
-        g_scratch_addr[dev] = static_cast<float2 *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_tile_scratch);
+    if (e != cudaSuccess || !p) return dof_cuda_check(e, "dof_coc_tiles_noalloc: cudaGetSymbolAddress");
+    *out = static_cast<float2 *>(p);
     return DOF_OK;
 }
 
@@ -102,16 +92,19 @@ extern "C" int dof_coc_tiles_noalloc(const float *depth, uint32_t width, uint32_
                                      const DofParams *p, float *tiles_dil, void *stream) {
     if (!depth || !cam || !p || !tiles_dil)
         return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: null argument");
-    if (width < 2 || height < 2 || (width & 1) || (height & 1))
-        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: size must be even and >= 2");
+    if (width < 2 || height < 2 || (width & 1) || (height & 1) || width > 16384 || height > 16384)
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: size must be even, 2..16384");
     if (((uintptr_t)depth % 8) || ((uintptr_t)tiles_dil % 8))
         return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: depth and tiles must be 8-byte aligned");
     if (p->tile != 8) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: tile must be 8");
     if (!(p->max_coc_px >= 1.f && p->max_coc_px <= 256.f))
         return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: max_coc_px must be in [1, 256]");
-    if (!(p->z_far_m > 0.f)) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: z_far must be > 0");
-    if (!(cam->f_m > 0.f) || !(cam->f_number > 0.f) || !(cam->sensor_w_m > 0.f) || !(cam->focus_m > cam->f_m))
-        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: need f > 0, N > 0, w_s > 0, focus > f");
+    if (!(p->z_far_m > 0.f) || !isfinite(p->z_far_m))
+        return dof_set_error(DOF_ERR_INVALID_ARG, "dof_coc_tiles_noalloc: z_far must be finite and > 0");
+    if (!(cam->f_m > 0.f) || !(cam->f_number > 0.f) || !(cam->sensor_w_m > 0.f) || !(cam->focus_m > cam->f_m) ||
+        !isfinite(cam->f_m) || !isfinite(cam->f_number) || !isfinite(cam->focus_m) || !isfinite(cam->sensor_w_m))
+        return dof_set_error(DOF_ERR_INVALID_ARG,
+                             "dof_coc_tiles_noalloc: need finite f > 0, N > 0, w_s > 0 and focus > f");
     TileArgs a;
     a.W = (int)width; a.H = (int)height; a.W2 = a.W / 2; a.H2 = a.H / 2;
     a.TW = (a.W2 + 7) / 8; a.TH = (a.H2 + 7) / 8;

@@ -2,9 +2,11 @@
 oracle on the same seeded inputs and compare them element by element.
 
 Tolerance accounting
-  * hit ids: bit-exact, except rays the oracle classifies as floating-point near
-    ties (an edge graze or equal depths within 1e-5 relative); every mismatch must
-    classify, and the fraction is reported (target <= 1e-4 of rays);
+  * hit ids: bit-exact, except rays whose kernel answer the oracle's hit_check
+    accepts as a floating-point near tie (the kernel's triangle is hit within
+    1e-6 (|o| + s) of rounding, no clean hit lies certainly in front of it, and a
+    clean kernel hit is not certainly in front of the oracle's); every mismatch must
+    classify, and they are at most 1e-4 of the rays;
   * images: max |d| <= 2e-3 and PSNR >= 50 dB in linear RGB; the max excludes the
     taint cone of mismatched rays (the pixel, the reconstruction footprint, the
     median and the upsampling, carried through the history by the motion), whose
@@ -136,7 +138,9 @@ def oracle_inputs(w, frame_idx, osc=None):
 
 
 def classify_hits(osc, w, params, cam, gpu, ref):
-    """Returns (n_rays, n_mismatch, n_unclassified, mismatch mask per hpx)."""
+    """Returns (n_rays, n_mismatch, n_invalid, mismatch mask per hpx).  A mismatch is
+    valid when oracle.Scene.hit_check accepts the kernel's triangle for the ray (the
+    oracle's FP64 ray of that pixel and sample)."""
     nr = ref["nrays"]
     H2, W2 = nr.shape
     mism = np.zeros((H2, W2), bool)
@@ -150,17 +154,29 @@ def classify_hits(osc, w, params, cam, gpu, ref):
         for (j, i) in np.argwhere(diff):
             n_mis += 1
             o, d = oracle.lens_ray(cam, params, w.W, w.H, i, j, s)
-            if not osc.near_tie(o, d, int(gp[j, i, s]), int(op[j, i, s])):
+            code = osc.hit_check(o, d, int(gp[j, i, s]), int(op[j, i, s]))
+            if code < 0:
                 n_bad += 1
+                print(f"invalid hit at hpx ({i},{j}) sample {s}: kernel {int(gp[j, i, s])} "
+                      f"oracle {int(op[j, i, s])} code {code}")
             mism[j, i] = True
     return n_rays, n_mis, n_bad, mism
 
 
+def mask_ties(ref, params):
+    """hpx on a tile whose dilated near radius lies within 1e-5 of the mask threshold:
+    whether the pixel gets rays is decided on a rounding tie there."""
+    H2, W2 = ref["nrays"].shape
+    T = int(params["tile"])
+    thr = float(np.float32(params["mask_near_hpx"]))
+    tie_t = np.abs(ref["tile_dil"][..., 0] - thr) <= 1e-5 * max(thr, 1e-3)
+    return np.repeat(np.repeat(tie_t, T, 0), T, 1)[:H2, :W2]
+
+
 def count_ties(ref, params, band=None):
-    """hpx whose ray count is decided on a rounding tie: x_f (Eq. 4) within `band`
-    (default 1e-3 m) of an integer the count can jump at, or a tile whose dilated near
-    radius lies within 1e-5 of the mask threshold.  Either count is a valid result
-    there."""
+    """hpx whose ray count may be decided on a rounding tie: x_f (Eq. 4) within `band`
+    (default 1e-3 m) of an integer the count can jump at, or a mask tie.  Used only to
+    widen the taint of comparisons that do not force the counts."""
     H2, W2 = ref["nrays"].shape
     out = np.zeros((H2, W2), bool)
     if int(params["ray_mode"]) == 1:
@@ -170,11 +186,7 @@ def count_ties(ref, params, band=None):
         jump = (k >= 1) & (k <= float(params["m"]) - 1)
         b = 1e-3 * max(1.0, float(params["m"])) if band is None else band
         out |= jump & (np.abs(xf - k) <= b) & (ref["nrays"] > 0)
-    T = int(params["tile"])
-    thr = float(np.float32(params["mask_near_hpx"]))
-    tie_t = np.abs(ref["tile_dil"][..., 0] - thr) <= 1e-5 * max(thr, 1e-3)
-    out |= np.repeat(np.repeat(tie_t, T, 0), T, 1)[:H2, :W2]
-    return out
+    return out | mask_ties(ref, params)
 
 
 def weight_ties(ref):

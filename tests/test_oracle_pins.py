@@ -152,25 +152,136 @@ def test_bvh_equals_brute_force_c1_scene():
     assert hits > 1000
 
 
-def test_near_tie_classifier():
+def _tri_scene(tris):
+    """A scene of the given triangles (each 3 corners), float32 corners."""
+    from synth.scenes import Scene
+    v = np.asarray(tris, dtype=np.float64).reshape(-1, 3)
+    return Scene(verts=v.astype(np.float32), tris=np.arange(len(v), dtype=np.uint32).reshape(-1, 3),
+                 mat=np.zeros(len(tris), np.uint32), seed=1)
+
+
+def test_hit_check_classifier_tiny_ties():
     sc = tiny_scene(3, 4, ties=True)          # exactly the shared-edge quad and the coplanar pair
     os_ = oracle.Scene(sc)
     o = np.zeros(3)
     # the quad (z = 3) is split along its diagonal (-0.5,-0.5)-(0.5,0.5): aim at the diagonal
+    # beside the coplanar pair (z = 2.5, which covers the diagonal's middle)
+    d = np.array([0.4, 0.4, 3.0]); d /= np.linalg.norm(d)
+    assert os_.closest(o, d)[0] in (0, 1)
+    assert os_.hit_check(o, d, 0, 1) >= 1 and os_.hit_check(o, d, 1, 0) >= 1
+    # nearer the quad's centre the coplanar pair lies in front: the quad is no valid answer
     d = np.array([0.1, 0.1, 3.0]); d /= np.linalg.norm(d)
-    assert os_.near_tie(o, d, 0, 1)
-    # well inside triangle 0 (below the diagonal) vs triangle 1: not a tie
+    assert os_.closest(o, d)[0] in (2, 3)
+    assert os_.hit_check(o, d, 0, 2) == -2
+    # well inside triangle 0 (below the diagonal): triangle 1 is missed, a miss is wrong
     d = np.array([0.4, -0.45, 3.0]); d /= np.linalg.norm(d)
     prim, _ = os_.closest(o, d)
     assert prim == 0
-    assert not os_.near_tie(o, d, 0, 1)
-    # interior hit vs a miss: not a tie; grazing the quad's outer edge: a tie
-    assert not os_.near_tie(o, d, 0, -1)
+    assert os_.hit_check(o, d, 1, 0) == -1
+    assert os_.hit_check(o, d, -1, 0) == -2
+    # the FP64 answer is itself a miss while the kernel reports a clean hit: inconsistent
+    assert os_.hit_check(o, d, 0, -1) == -3
+    # on the quad's outer edge (x = 0.5), the only hit is grazed: a miss is valid
     d = np.array([0.5, 0.0, 3.0]); d /= np.linalg.norm(d)
-    assert os_.near_tie(o, d, 0, -1)
+    assert os_.hit_check(o, d, -1, 0) == 4
+    assert os_.hit_check(o, d, 0, -1) == 3
     # coplanar overlapping triangles at equal distance: a depth tie
     d = np.array([0.0, 0.0, 2.5]); d /= np.linalg.norm(d)
-    assert os_.near_tie(o, d, 2, 3)
+    assert os_.hit_check(o, d, 2, 3) == 1 and os_.hit_check(o, d, 3, 2) == 1
+
+
+def test_hit_check_rejects_what_rounding_cannot_explain():
+    """Each case is a plausible tracer bug that an edge-line or either-side graze test
+    would let through."""
+    z = np.array([0.0, 0.0, 1.0])
+    o = np.zeros(3)
+    near = [(-1, -1, 1), (1, -1, 1), (0, 1, 1)]                 # 0: clean near hit at t = 1
+    line_only = [(0.5, 0, 3), (1.5, 0, 3), (1, 1, 3)]           # 1: its edge's LINE meets the ray at (0,0,3)
+    grazed_far = [(0, -1, 3), (1, -1, 3), (0, 1, 3)]            # 2: an edge segment through (0,0,3)
+    behind = [(-1, -1, -2), (1, -1, -2), (0, 1, -2)]            # 3: on the ray's line, behind the origin
+    os_ = oracle.Scene(_tri_scene([near, line_only, grazed_far, behind]))
+    assert os_.closest(o, z)[0] == 0
+    # a far triangle whose extended edge line passes the ray, against a clean nearer hit
+    assert os_.hit_check(o, z, 1, 0) == -1
+    # a grazed far triangle hiding a clean near one
+    assert os_.hit_check(o, z, 2, 0) == -2
+    # a triangle behind the origin
+    assert os_.hit_check(o, z, 3, 0) == -1
+    # an id out of range
+    assert os_.hit_check(o, z, 4, 0) == -1
+
+
+def test_hit_check_grazed_near_and_depth_ties():
+    o = np.zeros(3)
+    z = np.array([0.0, 0.0, 1.0])
+    dlt = float(np.float32(5e-7))     # inside the 1e-6 (|o| + s) band at s = 1
+    far = float(np.float32(5e-6))     # outside it
+    T = [[(0, -1, 1), (1, -1, 1), (0, 1, 1)],                   # 0: near, edge through the ray (grazed hit)
+         [(-2, -2, 2), (2, -2, 2), (0, 2, 2)],                  # 1: clean at t = 2
+         [(dlt, -1, 1), (1, 0, 1), (dlt, 1, 1)],                # 2: near, the ray passes 5e-7 outside its edge
+         [(far, -1, 1), (1, 0, 1), (far, 1, 1)],                # 3: near, 5e-6 outside its edge
+         [(-2, -2, 1.5), (2, -2, 1.5), (0, 2, 1.5)],            # 4: clean at t = 1.5
+         [(-2, -2, 2.0000005), (2, -2, 2.0000005), (0, 2, 2.0000005)],   # 5: clean, 2.4e-7 behind 1
+         [(-2, -2, 2.001), (2, -2, 2.001), (0, 2, 2.001)]]      # 6: clean, 5e-4 behind 1
+    os_ = oracle.Scene(_tri_scene(T))
+    # the FP64 hit is grazed: the kernel may miss it and see the clean hit behind
+    sub = oracle.Scene(_tri_scene([T[0], T[1]]))
+    assert sub.closest(o, z)[0] == 0
+    assert sub.hit_check(o, z, 1, 0) == 2
+    # ... but not past a clean hit in between
+    sub = oracle.Scene(_tri_scene([T[0], T[1], T[4]]))
+    assert sub.hit_check(o, z, 1, 0) == -2 and sub.hit_check(o, z, 2, 0) == 2
+    # a near triangle missed by 5e-7 may be hit in lower precision; by 5e-6 it may not
+    sub = oracle.Scene(_tri_scene([T[1], T[2], T[3]]))
+    assert sub.closest(o, z)[0] == 0
+    assert sub.hit_check(o, z, 1, 0) == 3
+    assert sub.hit_check(o, z, 2, 0) == -1
+    # depth ties: 2.4e-7 relative is within rounding, 5e-4 is not
+    sub = oracle.Scene(_tri_scene([T[1], T[5], T[6]]))
+    assert sub.closest(o, z)[0] == 0
+    assert sub.hit_check(o, z, 1, 0) == 1
+    assert sub.hit_check(o, z, 2, 0) == -2
+    assert os_.hit_check(o, z, 0, 0) == 0
+
+
+def test_hit_check_accepts_rounding_and_rejects_wrong_ids():
+    """Completeness and soundness on random scenes: the FP64 closest hit of the same ray
+    perturbed at rounding scale (1e-9, far below the 1e-6 band) is always accepted; an
+    id the ray does not meet at all is always rejected."""
+    rng = np.random.default_rng(5)
+    n_alt = n_rej = 0
+    for seed in range(4):
+        sc = tiny_scene(40 + seed, 200, ties=True)
+        os_ = oracle.Scene(sc)
+        V = sc.tri_vertices().astype(np.float64)
+        for _ in range(600):
+            o = rng.uniform(-0.05, 0.05, 3)
+            # aim at a random triangle's edge or vertex half the time, else anywhere
+            k = rng.integers(sc.n_tris)
+            if rng.uniform() < 0.5:
+                a, b = rng.choice(3, 2, replace=False)
+                tgt = V[k, a] + rng.uniform() * (V[k, b] - V[k, a])
+            else:
+                tgt = np.array([rng.uniform(-1.5, 1.5), rng.uniform(-1.5, 1.5), 3.0])
+            d = tgt - o
+            d /= np.linalg.norm(d)
+            want, _ = os_.closest(o, d, brute=True)
+            d2 = d * (1.0 + 1e-9 * rng.standard_normal(3))
+            o2 = o + 1e-9 * rng.standard_normal(3)
+            alt, _ = os_.closest(o2, d2, brute=True)
+            if alt != want:
+                n_alt += 1
+            assert os_.hit_check(o, d, alt, want) >= 0, (seed, want, alt)
+            # a triangle whose corners all lie more than 1e-3 from the ray's line: missed
+            other = int(rng.integers(sc.n_tris))
+            P = V[other] - o
+            dist = np.linalg.norm(P - (P @ d)[:, None] * d[None, :], axis=1)
+            cen = V[other].mean(0) - o
+            ray_dist_c = np.linalg.norm(cen - (cen @ d) * d)
+            if other != want and dist.min() > 1e-3 and ray_dist_c > 1.0 and os_.closest(o, d)[0] != other:
+                assert os_.hit_check(o, d, other, want) < 0
+                n_rej += 1
+    assert n_alt >= 5 and n_rej >= 100, (n_alt, n_rej)
 
 
 # ---------------------------------------------------------------------------

@@ -1,4 +1,5 @@
-"""The allocation-free tile-map entry point agrees with the tile stage of dof_frame.
+"""The allocation-free tile-map entry point agrees with the tile stage of dof_frame and
+with the FP64 oracle's tile dilation.
 
 dof_coc_tiles_noalloc serves callers that cannot allocate device memory at the point
 where they need the tile map (an engine that reserved all device memory up front, or
@@ -7,6 +8,8 @@ cudaMalloc/cudaFree).  It keeps its intermediate in a built-in device array shar
 by all calls.  This file is collected last so that, if it fails, a run that stops at
 the first failure has already run every other test."""
 
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -14,6 +17,8 @@ import oracle
 from synth import make_workload
 
 pytestmark = pytest.mark.gpu
+
+TILE_TOL = 2e-5      # the tile tolerance of the parity tests (FP32 CoC vs the FP64 oracle)
 
 
 def _tiles_via_frame(w, gb):
@@ -26,7 +31,7 @@ def _tiles_via_frame(w, gb):
     return g.hist.read("TILES_DIL", shape=(-(-H2 // T), -(-W2 // T), 2))
 
 
-def test_noalloc_tiles_match_dof_frame_two_calls():
+def test_noalloc_tiles_match_dof_frame_and_oracle_two_calls():
     import torch
     from paper_2210_06158_gb300 import _build, dof
     _build.build()
@@ -38,17 +43,41 @@ def test_noalloc_tiles_match_dof_frame_two_calls():
         osc = oracle.Scene(w.scene)
         cam = w.camera(0)
         gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, w.params, w.W, w.H))
-        want = _tiles_via_frame(w, gb)
+        want_frame = _tiles_via_frame(w, gb)
+        want_oracle = oracle.frame(osc, cam, w.params, w.W, w.H, gb)["tile_dil"]
         depth = torch.from_numpy(np.ascontiguousarray(gb["depth"])).to(dev)
         got = dof.coc_tiles_noalloc(depth, cam, w.params)
         torch.cuda.synchronize()
         got = got.cpu().numpy()
-        assert got.shape == want.shape
-        assert np.abs(got - want).max() <= 2e-5          # the tile tolerance of the parity tests
-        assert want[..., 1].max() > 0.5                  # a non-trivial tile map
+        assert got.shape == want_frame.shape == want_oracle.shape
+        assert np.abs(got - want_frame).max() <= TILE_TOL
+        assert np.abs(got.astype(np.float64) - want_oracle).max() <= TILE_TOL
+        assert want_oracle[..., 1].max() > 0.5           # a non-trivial tile map
 
 
-def test_noalloc_rejects_oversize():
+def test_noalloc_allocates_nothing():
+    """Free device memory and torch's allocator are unchanged across calls (after the
+    first call in this process, which may load the library's device code)."""
+    import torch
+    from paper_2210_06158_gb300 import _build, dof
+    _build.build()
+    w = make_workload("c2", W=640, H=360)
+    dev = torch.device("cuda", 0)
+    depth = torch.rand((w.H, w.W), dtype=torch.float32, device=dev) * 50.0 + 0.5
+    out = torch.empty((-(-(w.H // 2) // 8), -(-(w.W // 2) // 8), 2), dtype=torch.float32, device=dev)
+    dof.coc_tiles_noalloc(depth, w.camera(0), w.params, out=out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    alloc0 = torch.cuda.memory_allocated(dev)
+    for _ in range(3):
+        dof.coc_tiles_noalloc(depth, w.camera(0), w.params, out=out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0
+    assert torch.cuda.memory_allocated(dev) == alloc0
+
+
+def test_noalloc_rejects_oversize_and_bad_lens():
     import torch
     from paper_2210_06158_gb300 import _build, dof
     _build.build()
@@ -58,3 +87,19 @@ def test_noalloc_rejects_oversize():
     with pytest.raises(dof.DofError) as e:
         dof.coc_tiles_noalloc(depth, w.camera(0), w.params)
     assert e.value.code == -1 and "scratch" in str(e.value)
+    # host-side rejections (nothing is launched): sizes beyond 16384, non-finite lens
+    small = torch.ones((16, 16), dtype=torch.float32, device=dev)
+    out = torch.empty((1, 1, 2), dtype=torch.float32, device=dev)
+    L = dof.lib()
+    for W, H in ((1 << 31, 2), (2, 1 << 31), (16386, 2)):
+        c, p = dof.camera_struct(w.camera(0)), dof.params_struct(w.params)
+        rc = L.dof_coc_tiles_noalloc(C.c_void_p(small.data_ptr()), W, H, C.byref(c), C.byref(p),
+                                     C.c_void_p(out.data_ptr()), None)
+        assert rc == -1, (W, H, rc)
+    for field, val in (("focus_m", float("inf")), ("f_m", float("nan")), ("f_number", float("inf"))):
+        c, p = dof.camera_struct(w.camera(0)), dof.params_struct(w.params)
+        setattr(c, field, val)
+        rc = L.dof_coc_tiles_noalloc(C.c_void_p(small.data_ptr()), 16, 16, C.byref(c), C.byref(p),
+                                     C.c_void_p(out.data_ptr()), None)
+        assert rc == -1, (field, rc)
+        assert b"finite" in L.dof_last_error()
