@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "hybrid-DoF frames/s at 1080p/4K, %HBM roofline; served p50/p99 frame latency"
 CYCLE = 16
+C3_STEPS = 32        # timed 4K frames of the default run's c3 sub-record
 
 # FP32 operations of the traversal (FMA = 2): a binary node visit tests two child
 # boxes (per box 6 FMA slab products = 12, 10 min/max, 1 compare -> 23, x2 = 46)
@@ -209,6 +210,54 @@ def oracle_sample(w, budget_s=15.0, steps=None):
     return 1.0 / per_frame, desc, threads, times, frac
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(w, budget_s=15.0, single_steps=2):
+    """The FP64 oracle on the host cores: all threads (OpenMP over rows), then one
+    thread, on bands of the workload's frame (same output for any thread count)."""
+    import oracle
+    fps, desc, threads, _, _ = oracle_sample(w, budget_s=budget_s)
+    prev = oracle.set_threads(1)
+    try:
+        fps1, desc1, _, _, _ = oracle_sample(w, steps=single_steps)
+    finally:
+        oracle.set_threads(prev)
+    return dict(value=round(fps, 5), unit="frames/s", cores=threads, kind="oracle", sample=desc,
+                cpu_model=cpu_model(), single_thread=dict(value=round(fps1, 5), unit="frames/s", cores=1,
+                                                          sample=desc1))
+
+
+def coc_reach(w, gbs, prm):
+    """Largest CoC radius (full-resolution px) the workload's frames reach: the thin-lens
+    radius at the nearest depth of the G-buffers (Eq. 6 closed form), and the same after
+    the max_coc_px clamp the passes apply."""
+    import torch
+    f, N, d, ws = (w.intr[k] for k in ("f_m", "f_number", "focus_m", "sensor_w_m"))
+    k_coc = (f / N) * f * w.W / (ws * (d - f))
+    zmin = min(float(torch.nan_to_num(g["depth"], posinf=1e30).min()) for g in gbs)
+    r = abs(k_coc * (zmin - d) / zmin) / 2.0
+    return dict(nearest_depth_m=round(zmin, 4), physical=round(r, 2),
+                clamped=round(min(r, float(prm["max_coc_px"])), 2), clamp=float(prm["max_coc_px"]))
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -274,6 +323,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     gbuf_ms = ev0.elapsed_time(ev1) / CYCLE
     gbuf_cmp = gbuffer_producers(dof, ctx, scene, w, prm)
+    reach = coc_reach(w, gbs, prm)
     for g in gbs:
         del g["prim"]
     pstruct = dof.params_struct(prm)
@@ -302,6 +352,10 @@ def run_ours(args, rank, world):
     tuned, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4,
                                widths=(args.bvh_width,) if args.bvh_width else None)
     tuned = dict(tuned, ploc_radius=tuned_bvh["ploc_radius"])
+    # the 81-tap gathers' block shape and the main filter's form
+    gathers, _ = tune.tune_gathers(ctx, lambda k: step(k % len(cams), hist), frames=4)
+    gathers = dict(main_filter_block=list(gathers["gather_block"]), main_filter_form=gathers["main_form"],
+                   recon_block=list(gathers["recon_block"]))
     tune_s = time.perf_counter() - t0
     hist.reset()
 
@@ -474,7 +528,7 @@ def run_ours(args, rank, world):
                                     f"{w.intr['focus_m']:g} m, CoC radius <= {prm['max_coc_px']:g} px, {spp} spp, "
                                     f"16-frame dolly" + (", camera jitter + final TAA (blend 0.1)" if args.taa else ""),
                            resolution=[w.W, w.H], triangles=info.n_tris, spp=spp, bvh_depth=info.depth,
-                           tracer=dict(tuned, tune_s=round(tune_s, 2)),
+                           tracer=dict(tuned, tune_s=round(tune_s, 2)), gathers=gathers,
                            parallelism="replicas" if world > 1 else "single-gpu",
                            l2=f"inputs larger than L2: {CYCLE} distinct G-buffers cycled "
                               f"({CYCLE} x {w.W * w.H * 20 / 1e6:.0f} MB)"),
@@ -494,7 +548,7 @@ def run_ours(args, rank, world):
                if kavg.get("k_trace_rays", 0) > 0 else None,
                rays_per_frame=int(rays_per_frame), mask_fraction=round(masked_per_frame / N, 4),
                bvh_build_ms=round(bvh_ms, 2), gbuffer_ms=round(gbuf_ms, 3), gbuffer_producers=gbuf_cmp,
-               device_status=int(st.device_status))
+               coc_radius_px=reach, device_status=int(st.device_status))
     return res, w
 
 
@@ -519,7 +573,7 @@ def batch_sessions(n, res_cycle, tri_lo, tri_hi, seed, frames=8):
         tris = float(np.exp(rng.uniform(np.log(tri_lo), np.log(tri_hi))))
         dens = tris / 495_802.0
         sd = 2000 + 100 * k
-        w.scene_fn = (lambda sd=sd, dens=dens: scene_grass_field(sd, dens))
+        w.scene_fn = (lambda sd=sd, dens=dens: scene_grass_field(sd, dens, near=(1.2, 4.7)))
         w._scene = None
         w.params = dict(w.params, seed=sd, albedo_seed=sd, session=k, max_coc_px=32.0 * W / 1920.0)
         out.append(w)
@@ -687,59 +741,95 @@ def run_budget(args):
                 paper_context="0.04-0.07 ms per unit m for the ray-trace pass on an RTX 2080 Ti (Table 2)")
 
 
+SERVE_LOADS = (0.25, 0.5, 0.75, 1.0, 1.5)      # offered load as a fraction of the batched FP32 capacity
+
+
 def run_serve(args):
-    import numpy as np
     from paper_2210_06158_gb300 import _build
     from paper_2210_06158_gb300.serve import GpuExecutor, Server, SessionSpec, poisson_arrivals
+    import torch
     _build.build()
     res = [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
     ws = batch_sessions(64, res, 100_000, 2_000_000, seed=5, frames=4)
-    duration = float(os.environ.get("DOF_SERVE_SECONDS", "2.0"))
-
-    def serve(per_frame=False, fp16=False):
-        """One serving run over the same 64 sessions and the same Poisson arrivals."""
-        import torch
-        ex = GpuExecutor(budget_bytes=40 << 30, gbuf_ring=2, per_frame=per_frame, fp16=fp16)
-        srv = Server(ex, max_batch=32)
-        specs = {}
-        t0 = time.time()
-        for k, w in enumerate(ws):
-            spec = SessionSpec(f"s{k}", w.W, w.H, 30.0 if k % 2 == 0 else 60.0, scene=w.scene, params=w.params,
+    duration = float(os.environ.get("DOF_SERVE_SECONDS", "1.5"))
+    ex = GpuExecutor(budget_bytes=40 << 30, gbuf_ring=2)
+    srv = Server(ex, max_batch=32)
+    specs = {}
+    t0 = time.time()
+    for k, w in enumerate(ws):
+        specs[k] = SessionSpec(f"s{k}", w.W, w.H, 30.0 if k % 2 == 0 else 60.0, scene=w.scene, params=w.params,
                                poses=w.poses, intr=w.intr)
-            specs[k] = spec
-            srv.admit(k, spec)
-        setup = time.time() - t0
-        admitted = {k: v for k, v in specs.items() if k in srv.specs}
-        arr = poisson_arrivals(6, admitted, duration_s=duration)
-        with ClockSampler(0) as clk:
-            st = srv.run(arr)
-        for k in list(srv.specs):
-            srv.release(k)
+        srv.admit(k, specs[k])
+    setup_s = time.time() - t0
+    admitted = {k: v for k, v in specs.items() if k in srv.specs}
+    nominal = {k: v.fps for k, v in admitted.items()}
+    offered_nominal = sum(nominal.values())
+
+    def serve_at(scale, seed):
+        """Poisson requests at `scale` x the nominal 30/60 fps of every session."""
+        for k, v in admitted.items():
+            v.fps = nominal[k] * scale
+        arr = poisson_arrivals(seed, admitted, duration_s=duration)
+        st = srv.run(arr)
         torch.cuda.synchronize()
-        return st, arr, setup, clk
+        return st, len(arr)
 
-    def form(st):
-        return dict(frames_per_s=round(st["frames_per_s"], 2), p50_ms=round(st["p50_ms"], 3),
-                    p99_ms=round(st["p99_ms"], 3), frames=st["frames"], mean_batch=round(st["mean_batch"], 2))
+    def point(st, n_req, offered):
+        return dict(offered_frames_per_s=round(offered, 1), frames_per_s=round(st["frames_per_s"], 2),
+                    p50_ms=round(st["p50_ms"], 3), p99_ms=round(st["p99_ms"], 3), frames=st["frames"],
+                    requests=n_req, superseded=round(st["dropped"] / max(1, n_req), 4),
+                    mean_batch=round(st["mean_batch"], 2))
 
-    st, arr, setup_s, clk = serve()
-    # the same load in the batched FP16-storage form and in the plain FP32 per-frame form
-    st16 = serve(fp16=True)[0]
-    st1 = serve(per_frame=True)[0]
-    line = dict(metric=METRIC, value=round(st["frames_per_s"], 2), unit="frames/s", n_gpus=1, steps=st["frames"],
-                warmup=0, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
-                data="synthetic",
-                config=dict(workload="serving: 64 sessions, Poisson frame requests at 30/60 fps for "
-                                     f"{duration:g} s, 1280x720..3840x2160, lawn scenes 100k-2M triangles, "
-                                     "40 GB device budget, continuous batching (<= 32 per launch, 2 streams)"),
-                served=dict(p50_ms=round(st["p50_ms"], 3), p99_ms=round(st["p99_ms"], 3),
-                            mean_ms=round(st["mean_ms"], 3), frames=st["frames"], requests=len(arr),
-                            dropped_superseded=st["dropped"], failed=st["failed"], admitted=st["admitted"],
-                            rejected=st["rejected"], mean_batch=round(st["mean_batch"], 2)),
-                batched_fp16_form=dict(form(st16), note="FP16 storage of the colour image buffers, FP32 arithmetic "
-                                                        "(max |d| <= 4e-4 vs the FP64 oracle in the tests)"),
-                per_frame_fp32_form=dict(form(st1), note="plain FP32, one dof_frame per request"),
-                setup_s=round(setup_s, 1), clocks=clk.summary())
+    forms = [("batched_fp32", False, False), ("batched_fp16", False, True), ("per_frame_fp32", True, False)]
+    out = {}
+    capacity = None
+    with ClockSampler(0) as clk:
+        for name, per_frame, fp16 in forms:
+            ex.set_form(per_frame=per_frame, fp16=fp16)
+            # capacity: the nominal 30/60 fps offer far more frames than one GPU renders
+            st, n_req = serve_at(1.0, 6)
+            cap = st["frames_per_s"]
+            if capacity is None:
+                capacity = cap           # the batched FP32 capacity sets the sweep's offered loads
+            sweep = []
+            for f in SERVE_LOADS:
+                scale = f * capacity / offered_nominal
+                st_f, n_f = serve_at(scale, 7 + int(100 * f))
+                sweep.append(dict(point(st_f, n_f, scale * offered_nominal), load=f))
+            out[name] = dict(capacity_frames_per_s=round(cap, 2), overload=point(st, n_req, offered_nominal),
+                             sweep=sweep)
+    for k in list(srv.specs):
+        srv.release(k)
+    del ex, srv
+    torch.cuda.synchronize()
+    # admission under a budget that binds: 8 GB admits only part of the 64 sessions
+    ex8 = GpuExecutor(budget_bytes=8 << 30, gbuf_ring=2)
+    srv8 = Server(ex8, max_batch=32)
+    specs8 = {k: SessionSpec(f"s{k}", w.W, w.H, 30.0 if k % 2 == 0 else 60.0, scene=w.scene, params=w.params,
+                             poses=w.poses, intr=w.intr) for k, w in enumerate(ws)}
+    for k in specs8:
+        srv8.admit(k, specs8[k])
+    adm8 = {k: v for k, v in specs8.items() if k in srv8.specs}
+    st8 = srv8.run(poisson_arrivals(9, adm8, duration_s=duration))
+    budget8 = dict(budget_gb=8, admitted=len(adm8), rejected=len(srv8.rejected),
+                   bytes_in_use=int(ex8.ctx.bytes_in_use), frames_per_s=round(st8["frames_per_s"], 2),
+                   p50_ms=round(st8["p50_ms"], 3), p99_ms=round(st8["p99_ms"], 3))
+    for k in list(srv8.specs):
+        srv8.release(k)
+    b = out["batched_fp32"]
+    half = next(p for p in b["sweep"] if p["load"] == 0.5)
+    line = dict(metric=METRIC, value=b["capacity_frames_per_s"], unit="frames/s", n_gpus=1,
+                steps=b["overload"]["frames"], warmup=0, ms_per_step=None, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload="serving: 64 sessions, Poisson frame requests (nominal 30/60 fps), "
+                                     f"{duration:g} s per point, 1280x720..3840x2160, lawn scenes 100k-2M "
+                                     "triangles, 40 GB device budget, continuous batching (<= 32 per launch, "
+                                     "2 streams)"),
+                served=dict(p50_ms_at_half_load=half["p50_ms"], p99_ms_at_half_load=half["p99_ms"],
+                            admitted=len(admitted), rejected=len(srv.rejected)),
+                forms=out, budget_8gb=budget8, setup_s=round(setup_s, 1), clocks=clk.summary(),
+                note="value = batched FP32 capacity (served frames/s when every session always has a "
+                     "request); sweep loads are fractions of it, the same offered loads for every form")
     return line
 
 
@@ -751,6 +841,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "batch", "serve", "budget"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the 4K sub-record of the default (c2) run")
     ap.add_argument("--taa", action="store_true",
                     help="camera jitter (Halton 2, 3) and the final TAA pass with blend 0.1")
     ap.add_argument("--size", default=None,
@@ -791,9 +883,21 @@ def main():
         import torch.distributed as tdist
         tdist.init_process_group("gloo")
     res, w = run_ours(args, rank, world)
-    if rank == 0 and not args.no_cpu_baseline:
-        fps, desc, threads, times, frac = oracle_sample(w)
-        res["cpu_baseline"] = dict(value=round(fps, 5), unit="frames/s", cores=threads, kind="oracle", sample=desc)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(w)
+    if args.config == "c2" and not args.size and not args.no_c3:
+        # the 4K workload (3840x2160, 4 spp) with the same timing method: its own frames/s,
+        # kernel times, image-pass rooflines, end-to-end figure and clocks
+        import copy
+        a3 = copy.copy(args)
+        a3.config, a3.steps = "c3", min(args.steps, C3_STEPS)
+        r3, w3 = run_ours(a3, rank, world)
+        keep = ("value", "unit", "steps", "warmup", "ms_per_step", "config", "roofline", "e2e", "fp16_storage",
+                "gpu_launches", "clocks", "kernel_ms", "image_passes", "mrays_per_s", "rays_per_frame",
+                "mask_fraction", "coc_radius_px", "device_status")
+        res["c3"] = {k: r3[k] for k in keep}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            res["c3"]["cpu_baseline"] = cpu_baseline(w3, budget_s=10.0, single_steps=1)
     if world > 1:
         import torch.distributed as tdist
         tdist.barrier()

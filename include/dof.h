@@ -171,6 +171,23 @@ size_t dof_ctx_bytes_in_use(const DofCtx *ctx);
 #define DOF_OPT_PLOC_RADIUS         5   /* PLOC nearest-neighbour search radius, 1..256 (default 48) */
 #define DOF_OPT_BVH_WIDTH           6   /* tree the rays traverse: 4 (default) = the binary tree collapsed
                                          * to 4-wide nodes, 2 = the binary tree; same hits either way */
+#define DOF_OPT_RAY_ORDER_GRID      7   /* order in which the tracer takes a block's rays: grouped by the
+                                         * cell of their lens point on a g x g grid over the aperture,
+                                         * g = 1..16 (default 4), cells in Morton order; 1 = pixel by
+                                         * pixel.  Same hits either way */
+/* block of the main filter's 81-tap gather in half-resolution pixels: value = width |
+ * height << 16, width >= 8, width * height a multiple of 32 in 64..512 (default 32 x 8) */
+#define DOF_OPT_GATHER_BLOCK        8
+/* the main filter's reads: 0 (default) = the block's halo tile staged in shared memory when
+ * it fits in 64 KB, else through L1; 1 = always through L1; 2 = the halo tile whenever it
+ * fits in the SM's opt-in shared memory.  Same results either way */
+#define DOF_OPT_MAIN_FILTER_FORM    9
+/* block of the reconstruction's 81-tap gather, encoded as DOF_OPT_GATHER_BLOCK (default 32 x 8) */
+#define DOF_OPT_RECON_BLOCK         10
+/* entries of the tracer's per-ray traversal stack, 1..96 (default 96); the launch takes the
+ * smallest compiled capacity (32, 64, 96) that holds both this and what the batch's trees
+ * can need, so a small value never overflows.  Same hits either way */
+#define DOF_OPT_TRACE_STACK         11
 int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value);
 
 /* Fill `p` with the defaults above (1 spp fixed mode, 16 px radius clamp). */

@@ -117,6 +117,8 @@ def _declare(L):
     for fn in (L.or_closest, L.or_closest_brute):
         fn.restype = C.c_int
         fn.argtypes = [vp, vp, vp, vp]
+    L.or_set_threads.restype = C.c_int
+    L.or_set_threads.argtypes = [C.c_int]
     L.or_hit_check.restype = C.c_int
     L.or_hit_check.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_double]
     L.or_coc.restype = C.c_double
@@ -249,6 +251,12 @@ class Scene:
     def near_tie(self, o, d, prim_kernel, prim_oracle, rel_tol=HIT_TIE_REL_TOL) -> bool:
         """True when prim_kernel is a valid answer (equal, or a rounding tie)."""
         return self.hit_check(o, d, prim_kernel, prim_oracle, rel_tol) >= 0
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP row loops (results do not depend on it); returns
+    the previous count.  n <= 0 only queries."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def coc(cam, W, z) -> float:

@@ -3,6 +3,7 @@
  * variance blur, median, reconstruction, composite.  Test infrastructure (see
  * oracle.h). */
 #include "or_internal.h"
+#include <omp.h>
 
 void or_downscale(const OrCamera *cam, const OrParams *p, int W, int H, const float *color4,
                   const float *depth, const float *normal4, double *pp_in, double *z_h,
@@ -64,4 +65,12 @@ int or_frame(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int 
     if (p->taa_alpha > 0.0 && fr->taa_out)
         or_taa(c, p, W, H, depth, fr->out, fr->taa_in, fr->has_taa_history && fr->taa_in, fr->taa_out);
     return 0;
+}
+
+/* Threads of the OpenMP loops over image rows (results do not depend on it); returns
+ * the previous count.  n <= 0 only queries. */
+int or_set_threads(int n) {
+    int prev = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return prev;
 }

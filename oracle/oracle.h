@@ -155,6 +155,9 @@ typedef struct {
     int32_t pad_taa;
 } OrFrame;
 
+/* OpenMP threads of the row loops (output independent of it); returns the previous
+ * count, n <= 0 only queries */
+int or_set_threads(int n);
 int or_frame(const OrScene *s, const OrCamera *c, const OrParams *p, int W, int H,
              const float *color4, const float *depth, const float *normal4, OrFrame *fr);
 

@@ -215,6 +215,13 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->trace_blocks_per_sm = 8;
     c->trace_refill_idle = 16;
     c->trace_steps = 64;
+    c->ray_order_grid = 4;
+    c->stack_depth = kTraversalStack;
+    c->gather_w = 32;
+    c->gather_h = 8;
+    c->recon_w = 32;
+    c->recon_h = 8;
+    c->main_form = 0;
     c->ploc_radius = 48;
     c->bvh_width = 4;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -286,6 +293,33 @@ extern "C" int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value) {
         case DOF_OPT_TRACE_STEPS:
             if (value < 1 || value > 256) return dof_set_error(DOF_ERR_INVALID_ARG, "steps per round must be 1..256");
             ctx->trace_steps = (int)value;
+            return DOF_OK;
+        case DOF_OPT_RAY_ORDER_GRID:
+            if (value < 1 || value > 16) return dof_set_error(DOF_ERR_INVALID_ARG, "ray order grid must be 1..16");
+            ctx->ray_order_grid = (int)value;
+            return DOF_OK;
+        case DOF_OPT_GATHER_BLOCK:
+        case DOF_OPT_RECON_BLOCK: {
+            const long long w = value & 0xFFFF, h = (value >> 16) & 0xFFFF;
+            if (value < 0 || (value >> 32) || w < 8 || h < 1 || (w * h) % 32 || w * h < 64 || w * h > 512)
+                return dof_set_error(DOF_ERR_INVALID_ARG, "gather block: width >= 8, whole warps, 64..512 threads");
+            if (option == DOF_OPT_GATHER_BLOCK) {
+                ctx->gather_w = (int)w;
+                ctx->gather_h = (int)h;
+            } else {
+                ctx->recon_w = (int)w;
+                ctx->recon_h = (int)h;
+            }
+            return DOF_OK;
+        }
+        case DOF_OPT_TRACE_STACK:
+            if (value < 1 || value > kTraversalStack)
+                return dof_set_error(DOF_ERR_INVALID_ARG, "trace stack depth must be 1..%d", kTraversalStack);
+            ctx->stack_depth = (int)value;
+            return DOF_OK;
+        case DOF_OPT_MAIN_FILTER_FORM:
+            if (value < 0 || value > 2) return dof_set_error(DOF_ERR_INVALID_ARG, "main filter form must be 0, 1 or 2");
+            ctx->main_form = (int)value;
             return DOF_OK;
         default:
             return dof_set_error(DOF_ERR_INVALID_ARG, "dof_ctx_set_option: unknown option %d", option);
@@ -406,6 +440,8 @@ static SceneDev scene_dev(const DofScene *s) {
     d.nodes4 = wide ? s->nodes4 : nullptr;
     d.root4 = s->root4;
     d.n_nodes4 = s->n_nodes4;
+    // a binary node pushes at most one child per level, a 4-wide node three
+    d.stack_need = wide ? 3 * s->depth4 + 3 : (int)s->depth;
     return d;
 }
 
@@ -678,8 +714,10 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
     return DOF_OK;
 }
 
-static void shape_grid(const SessDesc &d, const DofHistory *h, int shape, int &gx, int &gy) {
+static void shape_grid(const BatchArgs &A, const SessDesc &d, const DofHistory *h, int shape, int &gx, int &gy) {
     switch (shape) {
+        case SH_GATHER: gx = ((int)h->W2 + A.gather_w - 1) / A.gather_w; gy = ((int)h->H2 + A.gather_h - 1) / A.gather_h; break;
+        case SH_RECON: gx = ((int)h->W2 + A.recon_w - 1) / A.recon_w; gy = ((int)h->H2 + A.recon_h - 1) / A.recon_h; break;
         case SH_TILE8: gx = (int)h->TW; gy = (int)h->TH; break;
         case SH_TILEDIL: gx = ((int)h->TW + 15) / 16; gy = ((int)h->TH + 15) / 16; break;
         case SH_HPX: gx = ((int)h->W2 + 31) / 32; gy = ((int)h->H2 + 7) / 8; break;
@@ -698,6 +736,11 @@ static int build_batch(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, BatchAr
     if (n > (uint32_t)kMaxBatch) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_batch_frame: %u > %d sessions", n, kMaxBatch);
     memset(&A, 0, sizeof(A));
     A.ns = (int)n;
+    A.gather_w = ctx->gather_w;
+    A.gather_h = ctx->gather_h;
+    A.recon_w = ctx->recon_w;
+    A.recon_h = ctx->recon_h;
+    A.main_form = ctx->main_form;
     adaptive = false;
     for (uint32_t s = 0; s < n; s++) {
         for (uint32_t t = 0; t < s; t++)
@@ -708,7 +751,7 @@ static int build_batch(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, BatchAr
         adaptive |= A.s[s].p.ray_mode == 1;
         for (int sh = 0; sh < SH_COUNT; sh++) {
             int gx, gy;
-            shape_grid(A.s[s], reqs[s].hist, sh, gx, gy);
+            shape_grid(A, A.s[s], reqs[s].hist, sh, gx, gy);
             A.s[s].gx[sh] = gx;
             long long next = (long long)A.start[sh][s] + (long long)gx * gy;
             if (next > 0x7FFFFFFFll) return dof_set_error(DOF_ERR_INVALID_ARG, "dof_batch_frame: batch too large");
@@ -718,6 +761,8 @@ static int build_batch(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, BatchAr
     A.cursor = &reqs[0].hist->counters[2];
     A.refill_idle = ctx->trace_refill_idle;
     A.steps_per_round = ctx->trace_steps;
+    A.lens_grid = ctx->ray_order_grid;
+    A.stack_depth = ctx->stack_depth;
     return DOF_OK;
 }
 
@@ -804,7 +849,8 @@ struct DofGraph {
     DofHistory *hist[kMaxBatch];
     int start[SH_COUNT][kMaxBatch + 1];
     bool adaptive, wide;
-    int trace_blocks, refill_idle, steps_per_round;
+    int trace_blocks, refill_idle, steps_per_round, lens_grid, stack_depth;
+    int gather_w, gather_h, main_form, recon_w, recon_h;
     int main_tile;                // the main filter's shared-memory bytes (0: through L1)
     long long kernels;            // kernel launches in one replay
     BatchArgs *d_args;            // read by the captured kernels
@@ -850,6 +896,13 @@ extern "C" int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n
     g->main_tile = main_filter_tile_bytes(A);
     g->refill_idle = A.refill_idle;
     g->steps_per_round = A.steps_per_round;
+    g->lens_grid = A.lens_grid;
+    g->stack_depth = A.stack_depth;
+    g->gather_w = A.gather_w;
+    g->gather_h = A.gather_h;
+    g->main_form = A.main_form;
+    g->recon_w = A.recon_w;
+    g->recon_h = A.recon_h;
     cudaGetLastError();
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
@@ -900,11 +953,15 @@ extern "C" int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n
     int rc = build_batch(ctx, reqs, n, A, adaptive);
     if (rc) return rc;
     if (memcmp(A.start, g->start, sizeof(A.start)) != 0 || adaptive != g->adaptive || all_wide(A) != g->wide ||
-        ctx->sm_count * ctx->trace_blocks_per_sm != g->trace_blocks || main_filter_tile_bytes(A) != g->main_tile)
+        ctx->sm_count * ctx->trace_blocks_per_sm != g->trace_blocks || main_filter_tile_bytes(A) != g->main_tile ||
+        A.gather_w != g->gather_w || A.gather_h != g->gather_h || A.main_form != g->main_form ||
+        A.recon_w != g->recon_w || A.recon_h != g->recon_h)
         return dof_set_error(DOF_ERR_MISMATCH, "dof_graph_launch: launch shapes differ from the captured step");
     // the kernels' scheduling knobs come from the staged copy; keep the captured ones
     A.refill_idle = g->refill_idle;
     A.steps_per_round = g->steps_per_round;
+    A.lens_grid = g->lens_grid;
+    A.stack_depth = g->stack_depth;
     cudaStream_t st = (cudaStream_t)stream;
     cudaGetLastError();
     // the previous launch's copy has consumed the staging buffer

@@ -17,6 +17,8 @@ enum LaunchShape {
     SH_MIP3,
     SH_FPX,         // 32x8 full-resolution pixels per block
     SH_SHADE,       // 128 queue entries per block
+    SH_GATHER,      // the main filter's 81-tap gather: gather_w x gather_h hpx
+    SH_RECON,       // the reconstruction's 81-tap gather: recon_w x recon_h hpx
     SH_COUNT
 };
 
@@ -60,6 +62,12 @@ struct SessDesc {
 struct BatchArgs {
     int ns;
     int refill_idle, steps_per_round;   // tracer scheduling
+    int lens_grid;                 // tracer work order: lens-cell grid of the mask kernel (1 = pixel order)
+    int stack_depth;               // requested traversal stack entries (the launch takes an instance >= the need)
+    int gather_w, gather_h;        // block of the main filter (SH_GATHER), <= 512 threads
+    int recon_w, recon_h;          // block of the reconstruction (SH_RECON), <= 512 threads
+    int main_form;                 // main filter: 0 halo tile up to 64 KB, 1 through L1, 2 halo tile up
+                                   // to the SM's opt-in shared memory
     int start[SH_COUNT][kMaxBatch + 1];
     uint32_t *cursor;              // device word: ray cursor of the persistent tracer
     SessDesc s[kMaxBatch];

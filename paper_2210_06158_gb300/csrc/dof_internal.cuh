@@ -81,6 +81,7 @@ struct SceneDev {
     const Bvh4Node *nodes4;      // the tree collapsed to 4-wide nodes (traversed when non-null)
     int root4;                   // its root reference
     int n_nodes4;
+    int stack_need;              // traversal stack entries the traversed tree can need
 };
 
 // at most this many large triangles are kept out of the tree (see bvh.cu)
@@ -97,7 +98,10 @@ struct DofCtx {
     size_t budget;
     int sm_count;
     int bvh_builder;               // DOF_BVH_PLOC or DOF_BVH_LBVH
-    int trace_blocks_per_sm, trace_refill_idle, trace_steps;
+    int trace_blocks_per_sm, trace_refill_idle, trace_steps, ray_order_grid;
+    int gather_w, gather_h, main_form;   // main filter launch shape and form
+    int recon_w, recon_h;                // reconstruction launch shape
+    int stack_depth;                     // requested traversal stack entries (raised to the tree's need)
     int ploc_radius;
     int bvh_width;                 // 4: traverse the collapsed 4-wide tree, 2: the binary tree
     uint32_t *d_status;            // device status word of context-level launches
@@ -139,8 +143,9 @@ struct DofHistory {
     float2 *tiles, *tiles_dil;
     int32_t *nrays;
     uint32_t *queue;               // masked pixel indices
-    uint32_t *first_ray;           // per pixel: index of its first ray in the ray list
-    uint32_t *ray_pix;             // ray list: pixel of each ray (N * max_rays)
+    uint32_t *first_ray;           // per pixel: slot of its first ray (its rays own n slots)
+    uint32_t *ray_pix;             // tracer work order: q << 6 | sample, grouped by lens cell
+                                   // (N * max_rays; q < 2^26 by the 16384 size limit)
     int2 *hits;                    // per ray: (sorted triangle index or -1, t bits)
     float4 *ray_a;                 // per ray as the tracer made it: (origin, dir.x) ...
     float2 *ray_b;                 // ... and (dir.y, dir.z); the shader reads them back

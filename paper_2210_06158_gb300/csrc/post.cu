@@ -148,10 +148,10 @@ __device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const De
 }
 
 template <class AS>
-__global__ void __launch_bounds__(256) k_main_filter(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(512) k_main_filter(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
-    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const SessDesc &S = block_session(A, SH_GATHER, i, j);
     const DevParams &p = S.p;
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const float4 *__restrict__ pre = S.pre;
@@ -174,25 +174,25 @@ __global__ void __launch_bounds__(256) k_main_filter(const __grid_constant__ AS 
     st_img(out, q, make_float4(ax * r, ay * r, az * r, bright * r), p.f16);
 }
 
-// A4 with the block's neighbourhood staged in shared memory: the block's 32x8 pixels
-// plus a halo of h = ceil(rmax) + 2 on every side, of the prefiltered colour and of z,
-// loaded once with indices clamped to the image.  Every tap then reads the tile, which
-// holds exactly the clamped values the other form reads through L1, in the same order,
-// so the two forms give the same bits.
-constexpr int kMainTileMaxBytes = 64 * 1024;
+// A4 with the block's neighbourhood staged in shared memory: the block's pixels (the
+// gather block, SH_GATHER) plus a halo of h = ceil(rmax) + 2 on every side, of the
+// prefiltered colour and of z, loaded once with indices clamped to the image.  Every tap
+// then reads the tile, which holds exactly the clamped values the other form reads
+// through L1, in the same order, so the two forms give the same bits.
+constexpr int kMainTileAutoBytes = 64 * 1024;
 
 __host__ __device__ inline int main_tile_halo(float rmax_hpx) { return (int)ceilf(rmax_hpx) + 2; }
-__host__ __device__ inline int main_tile_bytes(float rmax_hpx) {
+__host__ __device__ inline int main_tile_bytes(float rmax_hpx, int bw, int bh) {
     const int h = main_tile_halo(rmax_hpx);
-    return (32 + 2 * h) * (8 + 2 * h) * (int)(sizeof(float4) + sizeof(float));
+    return (bw + 2 * h) * (bh + 2 * h) * (int)(sizeof(float4) + sizeof(float));
 }
 
 template <class AS>
-__global__ void __launch_bounds__(256) k_main_filter_tiled(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(512) k_main_filter_tiled(const __grid_constant__ AS as_) {
     extern __shared__ float4 sm_pre[];
     const BatchArgs &A = batch_args(as_);
     int i, j;
-    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const SessDesc &S = block_session(A, SH_GATHER, i, j);
     const DevParams &p = S.p;
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const float4 *__restrict__ pre = S.pre;
@@ -200,10 +200,11 @@ __global__ void __launch_bounds__(256) k_main_filter_tiled(const __grid_constant
     const float2 *__restrict__ dil = S.tiles_dil;
     float4 *out = S.main_;
     const int h = main_tile_halo(p.rmax_hpx);
-    const int tw = 32 + 2 * h, th = 8 + 2 * h;
+    const int bw = (int)blockDim.x, bh = (int)blockDim.y;
+    const int tw = bw + 2 * h, th = bh + 2 * h;
     float *sm_z = reinterpret_cast<float *>(sm_pre + tw * th);
     const int ox = i - (int)threadIdx.x - h, oy = j - (int)threadIdx.y - h;
-    for (int e = threadIdx.y * 32 + threadIdx.x; e < tw * th; e += 256) {
+    for (int e = (int)(threadIdx.y * blockDim.x + threadIdx.x); e < tw * th; e += bw * bh) {
         const int ty = e / tw, tx = e - ty * tw;
         const int x = min(max(ox + tx, 0), W2 - 1), y = min(max(oy + ty, 0), H2 - 1);
         const size_t g = (size_t)y * W2 + x;
@@ -285,12 +286,30 @@ void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistor
     tmark(tm, DOF_K_DILATE, st);
 }
 
-// Dynamic shared memory of the main filter's staged form for this batch, or 0 when a
-// session's halo tile does not fit (the form through L1 runs then).
+// The SM's opt-in shared memory per block (queried once).
+static int smem_optin_bytes() {
+    static int bytes = 0;
+    if (!bytes) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0)
+            bytes = v;
+        else
+            bytes = 48 * 1024;
+        cudaGetLastError();
+    }
+    return bytes;
+}
+
+// Dynamic shared memory of the main filter's staged form for this batch, or 0 when the
+// form through L1 runs: always for form 1, else when a session's halo tile exceeds the
+// form's limit (64 KB for form 0, the SM's opt-in shared memory for form 2).
 int main_filter_tile_bytes(const BatchArgs &A) {
+    if (A.main_form == 1) return 0;
     int bytes = 0;
-    for (int s = 0; s < A.ns; s++) bytes = max(bytes, main_tile_bytes(A.s[s].p.rmax_hpx));
-    return bytes <= kMainTileMaxBytes ? bytes : 0;
+    for (int s = 0; s < A.ns; s++) bytes = max(bytes, main_tile_bytes(A.s[s].p.rmax_hpx, A.gather_w, A.gather_h));
+    const int limit = A.main_form == 2 ? smem_optin_bytes() : kMainTileAutoBytes;
+    return bytes <= limit ? bytes : 0;
 }
 
 template <class AS>
@@ -300,15 +319,16 @@ void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *
     tmark(tm, DOF_K_PREFILTER, st);
     // the shared-memory form when every session's halo tile fits
     const int tile_bytes = main_filter_tile_bytes(A);
+    const dim3 gb(A.gather_w, A.gather_h);
     if (tile_bytes > 0) {
         static bool attr_set = false;    // per argument form (one instantiation each)
         if (!attr_set) {
-            cudaFuncSetAttribute(k_main_filter_tiled<AS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMainTileMaxBytes);
+            cudaFuncSetAttribute(k_main_filter_tiled<AS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_bytes());
             attr_set = true;
         }
-        k_main_filter_tiled<AS><<<A.start[SH_HPX][n], dim3(32, 8), tile_bytes, st>>>(as);
+        k_main_filter_tiled<AS><<<A.start[SH_GATHER][n], gb, tile_bytes, st>>>(as);
     } else {
-        k_main_filter<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+        k_main_filter<AS><<<A.start[SH_GATHER][n], gb, 0, st>>>(as);
     }
     tmark(tm, DOF_K_MAIN, st);
     k_median_pp<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);

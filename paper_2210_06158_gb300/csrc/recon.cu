@@ -245,10 +245,10 @@ __device__ __forceinline__ void recon_taps(const MipLevel &L0, const MipLevel &L
 // A11: reconstruction.  Blocks whose footprint (+-rmax + 2, at every level) lies
 // inside the image take taps without index clamping.
 template <class AS>
-__global__ void __launch_bounds__(256) k_recon(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(512) k_recon(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
-    const SessDesc &S = block_session(A, SH_HPX, i, j);
+    const SessDesc &S = block_session(A, SH_RECON, i, j);
     const DevParams &p = S.p;
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const int mL = S.mip_L;
@@ -457,7 +457,7 @@ void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistor
     tmark(tm, DOF_K_MEDIAN_RT, st);
     k_mips<AS><<<A.start[SH_MIP1][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MIPS, st);
-    k_recon<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
+    k_recon<AS><<<A.start[SH_RECON][n], dim3(A.recon_w, A.recon_h), 0, st>>>(as);
     count_launches(3);
     tmark(tm, DOF_K_RECON, st);
 }

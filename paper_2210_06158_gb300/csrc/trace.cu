@@ -114,6 +114,7 @@ __device__ __forceinline__ void tri_update(const Ray &ray, const float4 *__restr
 }
 
 // Returns true when the query has ended (stack empty or a guard tripped).
+template <int kCap>
 __device__ __forceinline__ bool step4(const Ray &ray, const Bvh4Node *__restrict__ nodes4, int n4,
                                       const float4 *__restrict__ tris, int n_tree, int &node, int *stack, int &sp,
                                       HitRec &h, uint32_t &n_visit, uint32_t &n_tests, uint32_t *status) {
@@ -161,7 +162,7 @@ __device__ __forceinline__ bool step4(const Ray &ray, const Bvh4Node *__restrict
 #pragma unroll
         for (int e = 3; e >= 1; e--) {
             if (c[e] != kEmptyChild) {
-                if (sp < kStack) stack[sp++] = c[e];
+                if (sp < kCap) stack[sp++] = c[e];
                 else atomicOr(status, 1u);
             }
         }
@@ -178,6 +179,7 @@ __device__ __forceinline__ bool step4(const Ray &ray, const Bvh4Node *__restrict
 // One step of the binary traversal: an internal node tests its two child boxes and
 // descends into the nearer hit child (the farther one is pushed); a leaf is
 // intersected.  Returns true when the query has ended (stack empty or a guard tripped).
+template <int kCap>
 __device__ __forceinline__ bool step2(const Ray &ray, const BvhNode *__restrict__ nodes, int n_nodes,
                                       const float4 *__restrict__ tris, int n_tree, int &node, int *stack, int &sp,
                                       HitRec &h, uint32_t &n_visit, uint32_t &n_tests, uint32_t *status) {
@@ -195,7 +197,7 @@ __device__ __forceinline__ bool step2(const Ray &ray, const BvhNode *__restrict_
         box_pair(ray, a, b, c, h.t, h0, t0, h1, t1);
         if (h0 && h1) {
             int nearc = t0 <= t1 ? ref.x : ref.y, farc = t0 <= t1 ? ref.y : ref.x;
-            if (sp < kStack) stack[sp++] = farc;
+            if (sp < kCap) stack[sp++] = farc;
             else atomicOr(status, 1u);
             node = nearc;
             return false;
@@ -239,7 +241,8 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
                 atomicOr(status, 2u);
                 break;
             }
-            if (step4(r, sc.nodes4, sc.n_nodes4, sc.tris, sc.n_tris, node4, stack, sp, h, n_visit, n_tests, status))
+            if (step4<kStack>(r, sc.nodes4, sc.n_nodes4, sc.tris, sc.n_tris, node4, stack, sp, h, n_visit, n_tests,
+                              status))
                 break;
         }
         return h;
@@ -251,7 +254,8 @@ __device__ HitRec closest_hit(const SceneDev &sc, const Ray &r, uint32_t *status
             atomicOr(status, 2u);
             break;
         }
-        if (step2(r, sc.nodes, sc.n_tris - 1, sc.tris, sc.n_tris, node, stack, sp, h, n_visit, n_tests, status)) break;
+        if (step2<kStack>(r, sc.nodes, sc.n_tris - 1, sc.tris, sc.n_tris, node, stack, sp, h, n_visit, n_tests, status))
+            break;
     }
     return h;
 }
@@ -352,8 +356,41 @@ __global__ void k_edges(const __grid_constant__ AS as_) {
 // A6: mask, ray count, and compaction into a pixel queue and a flat ray list
 // ---------------------------------------------------------------------------
 // Per block (32 x 8 pixels, one warp per 8 x 4 tile) one atomic reserves room for the
-// block's masked pixels (queue) and their rays (ray list); inside the block the order
-// is tile by tile, Morton order inside a tile, so neighbouring rays stay neighbours.
+// block's masked pixels (queue) and their rays.  A pixel's rays own the consecutive
+// slots first_ray[q] + s (s = sample index): the tracer writes each ray and its hit
+// there and the shader reduces them in sample order.  The order in which the tracer
+// takes the rays is a separate list (ray_pix: work items q << 6 | s over the same
+// range): inside the block the rays are grouped by the cell of their lens point on a
+// g x g grid over the aperture's bounding square (g = BatchArgs::lens_grid; 1 keeps
+// pixel order), cells taken in Morton order, so the 32 rays a tracer warp takes leave
+// nearby lens points for nearby pixels and stay close together through the blurred near
+// field.  The grouping changes no result: every ray is traced independently.
+constexpr int kMaxLensGrid = 16, kMaxLensCells = 256;
+
+__device__ __forceinline__ int morton2(int x, int y) {
+    int m = 0;
+#pragma unroll
+    for (int b = 0; b < 4; b++) m |= (((x >> b) & 1) << (2 * b)) | (((y >> b) & 1) << (2 * b + 1));
+    return m;
+}
+
+// Lens cell of the ray (q, s) on a g x g grid: its lens sample (the same Philox draw as
+// lens_ray) on the unit disk; the cell's Morton index (< 256 for g <= 16).  Only a
+// scheduling key.
+__device__ __forceinline__ int lens_cell(const DevCam &cam, const DevParams &p, uint32_t q, int s, int g) {
+    unsigned long long x0, x1;
+    philox2(q, (unsigned long long)s, cam.frame, 0ull, p.seed, p.session, x0, x1);
+    const float u1 = (float)(x0 >> 40) * 5.9604644775390625e-8f;
+    const float u2 = (float)(x1 >> 40) * 5.9604644775390625e-8f;
+    float sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    const float r = sqrtf(u1), half_g = 0.5f * (float)g;
+    const int cx = min(max((int)((r * cs + 1.f) * half_g), 0), g - 1);
+    const int cy = min(max((int)((r * sn + 1.f) * half_g), 0), g - 1);
+    return morton2(cx, cy);
+}
+static_assert(DOF_MAX_RAYS <= 64, "work items keep the sample index in 6 bits");
+
 template <class AS>
 __global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
@@ -405,12 +442,53 @@ __global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ AS
         b_pix = (uint32_t)old;
         b_ray = (uint32_t)(old >> 32);
     }
+    __syncthreads();     // b_pix, b_ray and the warp offsets are read by every thread below
+    const int grid = A.lens_grid;
+    if (grid <= 1) {
+        // pixel order: the work items follow the pixels' own slots
+        if (n > 0) {
+            queue[b_pix + w_pix[warp] + __popc(ball & ((1u << lane) - 1u))] = q;
+            const uint32_t f = b_ray + w_ray[warp] + (uint32_t)(incl - n);
+            first_ray[q] = f;
+            for (int s = 0; s < n; s++) ray_pix[f + s] = (q << 6) | (uint32_t)s;
+        }
+        return;
+    }
+    // lens cells of the block's rays (Morton indices below the power-of-two square that
+    // holds the g x g grid), and how many rays fall in each
+    __shared__ uint32_t cell_n[kMaxLensCells], cell_at[kMaxLensCells];
+    __shared__ uint8_t cell_of[DOF_MAX_RAYS][256];
+    const int tid = (int)(warp * 32u + lane);
+    cell_n[tid] = 0u;                       // 256 threads, 256 cells
+    __syncthreads();
+    for (int s = 0; s < n; s++) {
+        const int c = lens_cell(S.cam, p, q, s, grid);
+        cell_of[s][tid] = (uint8_t)c;
+        atomicAdd(&cell_n[c], 1u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive prefix over the 256 cells: 8 per lane, then across the warp
+        uint32_t v[8], acc = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) { v[k] = acc; acc += cell_n[lane * 8 + k]; }
+        uint32_t incl_c = acc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl_c, o);
+            if ((int)lane >= o) incl_c += u;
+        }
+        const uint32_t base = incl_c - acc;
+#pragma unroll
+        for (int k = 0; k < 8; k++) cell_at[lane * 8 + k] = base + v[k];
+    }
     __syncthreads();
     if (n > 0) {
         queue[b_pix + w_pix[warp] + __popc(ball & ((1u << lane) - 1u))] = q;
-        uint32_t f = b_ray + w_ray[warp] + (uint32_t)(incl - n);
-        first_ray[q] = f;
-        for (int s = 0; s < n; s++) ray_pix[f + s] = q;
+        first_ray[q] = b_ray + w_ray[warp] + (uint32_t)(incl - n);
+        for (int s = 0; s < n; s++) {
+            const uint32_t at = atomicAdd(&cell_at[cell_of[s][tid]], 1u);
+            ray_pix[b_ray + at] = (q << 6) | (uint32_t)s;
+        }
     }
 }
 
@@ -459,7 +537,7 @@ __device__ __forceinline__ void lens_ray(const DevCam &cam, const DevParams &p, 
 // enough of the warp is idle, so divergent rays do not hold the warp.  Writes the
 // closest hit of each ray: (sorted triangle index or -1, t).  kWide: every session of
 // the batch traverses its 4-wide tree, else every session its binary tree.
-template <bool kWide, class AS>
+template <bool kWide, int kCap, class AS>
 __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
@@ -487,7 +565,7 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
     const Bvh4Node *nodes4 = nullptr;
     const float4 *tris = nullptr;
     uint32_t steps = 0, max_steps = 0;
-    int stack[kStack];
+    int stack[kCap];
     while (true) {
         unsigned idle = __ballot_sync(0xffffffffu, !have);
         if (idle == 0xffffffffu || (!exhausted && __popc(idle) >= refill_idle)) {
@@ -507,40 +585,47 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
                     }
                     si = lo;
                     const SessDesc &S = A.s[si];
-                    r = g - (si > 0 ? pre[si - 1] : 0u);
-                    uint32_t q = __ldg(&S.ray_pix[r]);
-                    int sm = (int)(r - __ldg(&S.first_ray[q]));
-                    float3 L, dir;
-                    lens_ray(S.cam, S.p, q, sm, L, dir);
-                    // kept for the shader, which takes the ray as made here
-                    S.ray_a[r] = make_float4(L.x, L.y, L.z, dir.x);
-                    S.ray_b[r] = make_float2(dir.y, dir.z);
-                    ray = make_ray(L, dir);
-                    if (kWide) {
-                        nodes4 = S.sc.nodes4;
-                        n_nodes = S.sc.n_nodes4;
+                    // work item (pixel q, sample sm) -> the ray's own slot r
+                    const uint32_t wq = __ldg(&S.ray_pix[g - (si > 0 ? pre[si - 1] : 0u)]);
+                    const uint32_t q = wq >> 6;
+                    const int sm = (int)(wq & 63u);
+                    if (q >= (uint32_t)S.N || sm >= S.max_rays) {
+                        // a work item outside the session: flag it, the lane stays idle
+                        atomicOr(&A.s[si].counters[3], 2u);
                     } else {
-                        nodes = S.sc.nodes;
-                        n_nodes = S.sc.n_tris - 1;
-                    }
-                    tris = S.sc.tris;
-                    n_tree = S.sc.n_tris;
-                    h = HitRec{INFINITY, -1, -1};
-                    for (int k = n_tree; k < n_tree + S.sc.n_large; k++) {
-                        n_tests++;
-                        const float4 *tp = tris + 3 * (size_t)k;
-                        float t = tri_hit(ray, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), h.t);
-                        if (t > 0.f) {
-                            int prim = __float_as_int(__ldg(tp).w);
-                            if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
+                        r = __ldg(&S.first_ray[q]) + (uint32_t)sm;
+                        float3 L, dir;
+                        lens_ray(S.cam, S.p, q, sm, L, dir);
+                        // kept for the shader, which takes the ray as made here
+                        S.ray_a[r] = make_float4(L.x, L.y, L.z, dir.x);
+                        S.ray_b[r] = make_float2(dir.y, dir.z);
+                        ray = make_ray(L, dir);
+                        if (kWide) {
+                            nodes4 = S.sc.nodes4;
+                            n_nodes = S.sc.n_nodes4;
+                        } else {
+                            nodes = S.sc.nodes;
+                            n_nodes = S.sc.n_tris - 1;
                         }
+                        tris = S.sc.tris;
+                        n_tree = S.sc.n_tris;
+                        h = HitRec{INFINITY, -1, -1};
+                        for (int k = n_tree; k < n_tree + S.sc.n_large; k++) {
+                            n_tests++;
+                            const float4 *tp = tris + 3 * (size_t)k;
+                            float t = tri_hit(ray, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), h.t);
+                            if (t > 0.f) {
+                                int prim = __float_as_int(__ldg(tp).w);
+                                if (t < h.t || (t == h.t && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; }
+                            }
+                        }
+                        node = kWide ? S.sc.root4 : S.sc.root;
+                        sp = 0;
+                        steps = 0;
+                        max_steps = (uint32_t)min(4ll * n_tree + 64, 4294967295ll);
+                        have = n_tree > 0;
+                        if (!have) S.hits[r] = make_int2(h.k, __float_as_int(h.t));
                     }
-                    node = kWide ? S.sc.root4 : S.sc.root;
-                    sp = 0;
-                    steps = 0;
-                    max_steps = (uint32_t)min(4ll * n_tree + 64, 4294967295ll);
-                    have = n_tree > 0;
-                    if (!have) S.hits[r] = make_int2(h.k, __float_as_int(h.t));
                 }
             }
             if (__ballot_sync(0xffffffffu, have) == 0 && exhausted) break;
@@ -552,10 +637,10 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
                 atomicOr(&A.s[si].counters[3], 2u);
                 done = true;
             } else if (kWide) {
-                done = step4(ray, nodes4, n_nodes, tris, n_tree, node, stack, sp, h, n_visit, n_tests,
+                done = step4<kCap>(ray, nodes4, n_nodes, tris, n_tree, node, stack, sp, h, n_visit, n_tests,
                              &A.s[si].counters[3]);
             } else {
-                done = step2(ray, nodes, n_nodes, tris, n_tree, node, stack, sp, h, n_visit, n_tests,
+                done = step2<kCap>(ray, nodes, n_nodes, tris, n_tree, node, stack, sp, h, n_visit, n_tests,
                              &A.s[si].counters[3]);
             }
             if (done) {
@@ -675,8 +760,19 @@ void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t s
     // the 4-wide kernel when every session of the batch has its 4-wide tree in use
     bool wide = A.ns > 0;
     for (int i = 0; i < A.ns; i++) wide = wide && A.s[i].sc.nodes4 != nullptr;
-    if (wide) k_trace_rays<true, AS><<<blocks, 128, 0, st>>>(as);
-    else k_trace_rays<false, AS><<<blocks, 128, 0, st>>>(as);
+    // the stack capacity: the smallest compiled one that holds the requested depth and
+    // what every session's tree can need
+    int need = A.stack_depth;
+    for (int i = 0; i < A.ns; i++) need = max(need, A.s[i].sc.stack_need);
+    if (wide) {
+        if (need <= 32) k_trace_rays<true, 32, AS><<<blocks, 128, 0, st>>>(as);
+        else if (need <= 64) k_trace_rays<true, 64, AS><<<blocks, 128, 0, st>>>(as);
+        else k_trace_rays<true, kStack, AS><<<blocks, 128, 0, st>>>(as);
+    } else {
+        if (need <= 32) k_trace_rays<false, 32, AS><<<blocks, 128, 0, st>>>(as);
+        else if (need <= 64) k_trace_rays<false, 64, AS><<<blocks, 128, 0, st>>>(as);
+        else k_trace_rays<false, kStack, AS><<<blocks, 128, 0, st>>>(as);
+    }
     tmark(tm, DOF_K_TRACE, st);
     k_shade<AS><<<A.start[SH_SHADE][A.ns], 128, 0, st>>>(as);
     count_launches(2);

@@ -235,12 +235,26 @@ class Context:
         """Tree the rays traverse: 4 (collapsed 4-wide nodes, default) or 2 (binary)."""
         _check(lib().dof_ctx_set_option(self.ptr, 6, int(width)))
 
-    def set_trace(self, blocks_per_sm=None, refill_idle=None, steps=None, bvh_width=None):
-        """Launch shape / scheduling of the persistent tracer and the tree it traverses
-        (no effect on results)."""
-        for opt, v in ((2, blocks_per_sm), (3, refill_idle), (4, steps), (6, bvh_width)):
+    def set_trace(self, blocks_per_sm=None, refill_idle=None, steps=None, bvh_width=None, ray_grid=None, stack=None):
+        """Launch shape / scheduling of the persistent tracer, the tree it traverses, the
+        order it takes the rays in (lens-cell grid; 1 = pixel order) and its traversal
+        stack depth (raised to what the tree needs) -- no effect on results."""
+        for opt, v in ((2, blocks_per_sm), (3, refill_idle), (4, steps), (6, bvh_width), (7, ray_grid), (11, stack)):
             if v is not None:
                 _check(lib().dof_ctx_set_option(self.ptr, opt, int(v)))
+
+    def set_gather(self, block=None, main_form=None, recon_block=None):
+        """Launch shapes of the 81-tap gathers -- block (main filter) and recon_block
+        (reconstruction) = (width, height) in half-resolution pixels (width >= 8, whole
+        warps, 64..512 threads) -- and the main filter's form: 0 = halo tile in shared
+        memory when it fits in 64 KB, 1 = through L1, 2 = halo tile up to the SM's opt-in
+        shared memory (no effect on results)."""
+        for opt, b in ((8, block), (10, recon_block)):
+            if b is not None:
+                w, h = (int(v) for v in b)
+                _check(lib().dof_ctx_set_option(self.ptr, opt, w | (h << 16)))
+        if main_form is not None:
+            _check(lib().dof_ctx_set_option(self.ptr, 9, int(main_form)))
 
     @property
     def bytes_in_use(self) -> int:

@@ -115,13 +115,18 @@ class GpuExecutor:
     ring of device G-buffers rendered by the G-buffer producer; batches go through
     dof_batch_frame on one of two streams, completion is an event.  per_frame: each
     request of a batch runs as its own dof_frame instead (the plain per-frame form);
-    fp16: the sessions store their colour image buffers in FP16 (FP32 arithmetic)."""
+    fp16: the sessions store their colour image buffers in FP16 (FP32 arithmetic).
+    record: every served frame's image is copied (on its stream, after its batch) into
+    `records[(session, frame)]`, so that each can be compared with the same frame
+    rendered alone."""
 
-    def __init__(self, budget_bytes, device=0, gbuf_ring=2, per_frame=False, fp16=False):
+    def __init__(self, budget_bytes, device=0, gbuf_ring=2, per_frame=False, fp16=False, record=False):
         import torch
         from . import dof
         self.torch, self.dof = torch, dof
         self.per_frame, self.fp16 = per_frame, fp16
+        self.record = record
+        self.records = {}
         self.ctx = dof.Context(device, mem_budget_bytes=budget_bytes)
         self.device = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(2)]
@@ -165,6 +170,16 @@ class GpuExecutor:
                                   pstruct=dof.params_struct(prm))
         torch.cuda.synchronize()
 
+    def set_form(self, per_frame=False, fp16=False):
+        """Switch every admitted session to the given form (batched or per-frame, FP16 or
+        FP32 image storage) and start its history afresh."""
+        self.torch.cuda.synchronize()
+        self.per_frame, self.fp16 = per_frame, fp16
+        for s in self.sessions.values():
+            prm = dict(s["spec"].params, image_storage=1) if fp16 else s["spec"].params
+            s["pstruct"] = self.dof.params_struct(prm)
+            s["hist"].reset()
+
     def close(self, sid):
         s = self.sessions.pop(sid)
         s["hist"].close()
@@ -193,6 +208,10 @@ class GpuExecutor:
                                cam_struct=it["cam"], params_s=it["params"])
         else:
             self.dof.batch_frame(self.ctx, items, stream=st)
+        if self.record:
+            with self.torch.cuda.stream(st):
+                for r, it in zip(reqs, items):
+                    self.records[(r.session, r.frame)] = it["out"].clone()
         ev = self.torch.cuda.Event()
         ev.record(st)
         return ev

@@ -1,8 +1,12 @@
-"""Autotuners of the ray tracer: the BVH build (PLOC search radius) and the persistent
-tracer's tree width, launch shape and scheduling.
+"""Autotuners of the ray tracer -- the BVH build (PLOC search radius), the persistent
+tracer's tree width, work order, launch shape and scheduling -- and of the 81-tap
+gathers' launch shape and main-filter form.
 
-The knobs (the tree the rays traverse: binary or 4-wide; 128-thread blocks per SM,
-idle lanes that trigger a refill, traversal steps between refill checks) change only
+The knobs (the tree the rays traverse: binary or 4-wide; the order the tracer takes
+a block's rays in: grouped by lens cell on a g x g grid, or pixel by pixel; the
+traversal stack depth, which the launch raises to what the tree needs; 128-thread
+blocks per SM, idle lanes that trigger a refill, traversal steps between refill
+checks) change only
 the speed of dof_frame, never its result (the closest hit does not depend on the
 tree's shape).
 `tune_trace` times a few frames of the caller's own session for each candidate
@@ -18,11 +22,13 @@ from __future__ import annotations
 
 SPACE = {
     "bvh_width": [4, 2],
+    "ray_grid": [4, 1, 2, 8, 12, 16],
+    "stack": [96, 64, 32],
     "blocks_per_sm": [4, 6, 8, 12, 16],
     "refill_idle": [4, 8, 12, 16, 24],
     "steps": [8, 16, 32, 64],
 }
-DEFAULT = {"bvh_width": 4, "blocks_per_sm": 8, "refill_idle": 16, "steps": 64}
+DEFAULT = {"bvh_width": 4, "ray_grid": 4, "stack": 96, "blocks_per_sm": 8, "refill_idle": 16, "steps": 64}
 
 
 def _time_frames(run_frame, frames, st):
@@ -72,6 +78,55 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None):
         if not improved:
             break
     ctx.set_trace(**best)
+    return best, seen
+
+
+GATHER_SPACE = {
+    "gather_block": [(32, 8), (16, 16), (64, 4), (32, 16), (64, 8)],
+    "main_form": [0, 1, 2],
+    "recon_block": [(32, 8), (16, 16), (64, 4), (32, 16), (64, 8)],
+}
+GATHER_DEFAULT = {"gather_block": (32, 8), "main_form": 0, "recon_block": (32, 8)}
+
+
+def tune_gathers(ctx, run_frame, frames=4, rounds=2, stream=None):
+    """The 81-tap gathers' launch shapes (block of the main filter, block of the
+    reconstruction) and the main filter's form (halo tile in shared memory up to 64 KB,
+    through L1, or halo tile up to the SM's opt-in shared memory): coordinate descent
+    over GATHER_SPACE from GATHER_DEFAULT with the same timing rules as tune_trace.
+    Returns (best settings, {settings tuple: ms per frame}); the context keeps the best."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    best = dict(GATHER_DEFAULT)
+    seen = {}
+
+    def apply(cfg):
+        ctx.set_gather(block=cfg["gather_block"], main_form=cfg["main_form"], recon_block=cfg["recon_block"])
+
+    def measure(cfg, fresh=False):
+        key = tuple(sorted(cfg.items()))
+        if key in seen and not fresh:
+            return seen[key]
+        apply(cfg)
+        seen[key] = _time_frames(run_frame, frames, st)
+        return seen[key]
+
+    best_ms = measure(best)
+    for _ in range(rounds):
+        improved = False
+        for name, values in GATHER_SPACE.items():
+            for v in values:
+                cand = dict(best, **{name: v})
+                ms = measure(cand)
+                if ms < best_ms * 0.99:
+                    ms2, inc2 = measure(cand, fresh=True), measure(best, fresh=True)
+                    if ms2 < inc2 * 0.99:
+                        best, best_ms, improved = cand, ms2, True
+                    else:
+                        best_ms = inc2
+        if not improved:
+            break
+    apply(best)
     return best, seen
 
 

@@ -312,9 +312,9 @@ def scene_bokeh(seed: int, cam_pos=(0.0, 1.2, 0.0), pitch_deg=3.0, f_m=0.085, se
 
 def scene_grass_field(seed: int, density: float = 1.0, f_m=0.035, sensor_w_m=0.036,
                       near=(1.3, 4.8), far=(8.0, 60.0)) -> Scene:
-    """Lawn field: thin blade quads and fence bars in the near field (the dolly
-    start is 0.8 m behind `near[0]`, so distances during a 16-frame dolly span
-    0.5-4.8 m), a sparse box field and icospheres (level 4, level 5 from density 2) in the far field (8-60 m,
+    """Lawn field: thin blade quads and fence bars in the near field (a 16-frame
+    dolly advances 0.75 m, so from near[0] = 1.2 m its last frames see blades at
+    0.45 m), a sparse box field and icospheres (level 4, level 5 from density 2) in the far field (8-60 m,
     sparse enough that sight lines reach the focus distance and beyond).
     density 1 gives ~500k triangles, density 4 ~2M: the blade count scales with it,
     the far field keeps its boxes per square metre and takes the rest of the
@@ -473,10 +473,14 @@ def make_workload(name: str, W: int | None = None, H: int | None = None,
             W, H = W or 3840, H or 2160
             params = default_params(spp=4, max_coc_px=64.0, seed=seed, session=session, albedo_seed=seed)
             dens = 4.0
-        height, pitch = (1.0, 8.0) if cfg == 2 else (1.0, 4.0)
+        # c2: a camera 0.7 m above the lawn sees the tall blades close to it, so during
+        # the dolly the nearest blades come within 0.45 m and the CoC radius reaches its
+        # 32 px clamp (c(0.5 m) = 31.9 px); c3's lens reaches its 64 px clamp from 1 m
+        height, pitch = (0.7, 8.0) if cfg == 2 else (1.0, 4.0)
+        near = (1.2, 4.7) if cfg == 2 else (1.3, 4.8)
         poses = dolly_path(seed, (0.0, height, 0.0), n_frames or 16, pitch_deg=pitch)
         f_m = intr["f_m"]
-        fn = lambda: scene_grass_field(seed, dens, f_m=f_m)
+        fn = lambda: scene_grass_field(seed, dens, f_m=f_m, near=near)
     elif name == "bokeh":
         # bright bokeh (not a benchmark configuration): 85 mm f/1.2 focused at 5 m
         seed = 1004 + 100 * session

@@ -81,6 +81,14 @@ class GpuRunner:
         res["stats"] = self.hist.stats()
         return res
 
+    def read_img(self, name, H2, W2):
+        """A colour image buffer as float32 (H2, W2, 4): with FP16 storage
+        (image_storage = 1) its first H2 * W2 half4 texels hold the image."""
+        if int(self.params.get("image_storage", 0)) == 1:
+            a = self.hist.read(name, np.float16)[:H2 * W2 * 4]
+            return a.reshape(H2, W2, 4).astype(np.float32)
+        return self.hist.read(name, shape=(H2, W2, 4))
+
     def read_all(self):
         H2, W2 = self.w.H // 2, self.w.W // 2
         N = H2 * W2
@@ -93,8 +101,8 @@ class GpuRunner:
         r["tile_raw"] = h.read("TILES", shape=(TH, TW, 2))
         r["tile_dil"] = h.read("TILES_DIL", shape=(TH, TW, 2))
         r["pre"] = h.read("PRE", shape=(H2, W2, 4))
-        r["main_out"] = h.read("MAIN", shape=(H2, W2, 4))
-        r["pp_med"] = h.read("PP_MED", shape=(H2, W2, 4))
+        r["main_out"] = self.read_img("MAIN", H2, W2)
+        r["pp_med"] = self.read_img("PP_MED", H2, W2)
         r["xn"] = h.read("XN", shape=(H2, W2))
         r["xf"] = h.read("XF", shape=(H2, W2))
         r["nrays"] = h.read("NRAYS", np.int32, shape=(H2, W2))
@@ -111,12 +119,12 @@ class GpuRunner:
         o[..., 10:13] = rt[3, ..., :3]
         o[..., 13] = rt[2, ..., 2]
         r["rt"] = o
-        r["crt"] = h.read("CRT", shape=(H2, W2, 4))
+        r["crt"] = self.read_img("CRT", H2, W2)
         r["ct"] = h.read("CT", shape=(H2, W2))
         r["var"] = h.read("VAR", shape=(H2, W2))
         r["var_blur"] = h.read("VAR_BLUR", shape=(H2, W2))
-        r["rt_med"] = h.read("RT_MED", shape=(H2, W2, 4))
-        r["recon"] = h.read("RECON", shape=(H2, W2, 4))
+        r["rt_med"] = self.read_img("RT_MED", H2, W2)
+        r["recon"] = self.read_img("RECON", H2, W2)
         hh = h.read("HIST", shape=(3, H2, W2, 4))
         hist = np.zeros((H2, W2, 12), np.float32)
         hist[..., 0:3] = hh[0, ..., :3]
@@ -213,9 +221,10 @@ def taint_radius(params):
 
 
 def dilate(mask, r):
+    """Binary dilation by a (2r+1)^2 square (separable running max, zero outside)."""
     if r <= 0 or not mask.any():
         return mask.copy()
-    return ndi.binary_dilation(mask, structure=np.ones((2 * r + 1, 2 * r + 1), bool))
+    return ndi.maximum_filter(mask.astype(np.uint8), size=2 * r + 1, mode="constant", cval=0).astype(bool)
 
 
 def full_res(mask_h, W, H):

@@ -150,7 +150,13 @@ def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3, gbuf_f16
         # luminance variance scales with the square of the radiance (emitters reach 8),
         # so the bound is relative to its magnitude where that exceeds 1
         var_scale = max(1.0, float(np.abs(ref["var_blur"][ok]).max())) if ok.any() else 1.0
-        assert e_ct < 1e-4 and e_var < (2e-5 if cam_moved(cam) else 1e-6) * var_scale, (e_ct, e_var, var_scale)
+        # c_t (relative to rmax): a moving camera reprojects in FP32, where pixel positions
+        # carry the spacing of FP32 at the image size (1.2e-4 px at 1920 half-resolution
+        # columns); times a CoC step of up to rmax between neighbouring pixels, that is
+        # the reprojected c_t's error (4 spacings cover the projection's rounding steps)
+        ct_tol = max(1e-4, 4.0 * float(np.spacing(np.float32(max(W2, H2))))) if cam_moved(cam) else 1e-4
+        assert e_ct < ct_tol and e_var < (2e-5 if cam_moved(cam) else 1e-6) * var_scale, (e_ct, ct_tol, e_var,
+                                                                                          var_scale)
         e_var_prev_px = np.where(ok, np.abs(got["var_blur"].astype(np.float64) - ref["var_blur"]), 0.0)
         # ---- final image (linear RGB)
         taint_f = full_res(taint_h, w.W, w.H)
@@ -391,6 +397,50 @@ def test_checkpoint_resume_bit_identical():
     assert e.value.code == -7
 
 
+@pytest.mark.parametrize("name,W,H", [("c3", 384, 216), ("c2", 322, 182)])
+def test_scheduling_knobs_do_not_change_results(name, W, H):
+    """The autotuned knobs change only speed: the tracer's work order (lens-cell grid 1
+    = pixel order, 2 .. 16), the gathers' block shapes and the main filter's form
+    (shared-memory halo tile or L1) give bit-identical hit ids, intermediates and
+    images over two frames of a moving camera (the c3 crop with its 64 px clamp takes
+    the halo tile only in the opt-in form)."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    dev = torch.device("cuda", 0)
+    w = make_workload(name, W=W, H=H, n_frames=2)
+    prm = dict(w.params)
+    osc = oracle.Scene(w.scene)
+    gbs = []
+    for f in range(2):
+        gb = oracle.gbuffer_f32(oracle.gbuffer(osc, w.camera(f), prm, w.W, w.H))
+        gbs.append({k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in gb.items()})
+    ctx = dof.Context(0)
+    sc = dof.Scene(ctx, w.scene)
+    variants = [dict(ray_grid=1), dict(ray_grid=2), dict(ray_grid=4), dict(ray_grid=8), dict(ray_grid=12),
+                dict(ray_grid=16), dict(ray_grid=8, stack=32), dict(ray_grid=8, stack=64),
+                dict(block=(16, 16), main_form=0, recon=(16, 16)), dict(block=(64, 4), main_form=1, recon=(64, 8)),
+                dict(block=(32, 16), main_form=2, recon=(32, 16)), dict(block=(64, 8), main_form=2, recon=(64, 4)),
+                dict(block=(32, 8), main_form=1, recon=(8, 32))]
+    results = []
+    for v in variants:
+        ctx.set_trace(ray_grid=v.get("ray_grid", 4), stack=v.get("stack", 96))
+        ctx.set_gather(block=v.get("block", (32, 8)), main_form=v.get("main_form", 0),
+                       recon_block=v.get("recon", (32, 8)))
+        h = dof.History(ctx, w.W, w.H, max_rays=oracle.max_rays(prm), record_rays=True)
+        outs = [dof.frame(ctx, sc, gbs[f], w.camera(f), prm, h).cpu().numpy() for f in range(2)]
+        torch.cuda.synchronize()
+        assert h.stats().device_status == 0
+        results.append((v, outs, h.read("RAY_PRIM", np.int32), h.read("MAIN", np.float32),
+                        h.read("RECON", np.float32)))
+        h.close()
+    r0 = results[0]
+    for r in results[1:]:
+        for f in range(2):
+            assert np.array_equal(r0[1][f], r[1][f]), (r[0], f)
+        for k in (2, 3, 4):
+            assert np.array_equal(r0[k], r[k]), (r[0], k)
+
+
 def test_tree_shape_does_not_change_hits():
     """The closest hit is a property of the triangles, not of the tree: PLOC or LBVH,
     binary or 4-wide traversal give bit-identical hit ids and images."""
@@ -518,32 +568,52 @@ def test_graph_equals_batch():
     graph.close()
 
 
+# Bounds of the added error against the FP64 oracle, per output, for the plain FP32
+# form and the FP16-storage form (colour image planes stored as half, FP32 arithmetic,
+# FP32 depth, CoC, ray sums and history).  Half rounding is 2^-11 relative per stored
+# value; the filters' weighted sums keep it there.
+OUTPUT_TOL = {"fp32": dict(pp_med=5e-4, crt=5e-4, rt_med=5e-4, recon=1e-3, hist=5e-4, out=2e-3),
+              "fp16": dict(pp_med=2e-3, crt=2e-3, rt_med=2e-3, recon=2e-3, hist=5e-4, out=2e-3)}
+
+
 @pytest.mark.parametrize("name,W,H,nf", [("c3", 384, 216, 2), ("c2", 322, 182, 3)])
 def test_fp16_storage_error_vs_oracle(name, W, H, nf):
-    """FP16 storage of the colour image buffers (FP32 arithmetic, FP32 depth, CoC and
-    history): the final image meets the FP32 tolerances against the FP64 oracle."""
+    """Added error against the FP64 oracle per output -- post-process median (PP), ray
+    colour and its median (RT), reconstruction, history, final image -- for the plain
+    FP32 form and the FP16-storage form; each within its bound (OUTPUT_TOL), and the
+    final image within the FP32 tolerances (max |d| <= 2e-3, PSNR >= 50 dB)."""
     w = make_workload(name, W=W, H=H, n_frames=nf)
     prm32 = dict(w.params)
     prm16 = dict(prm32, image_storage=1)
     osc = oracle.Scene(w.scene)
-    g32, g16 = GpuRunner(w, prm32), GpuRunner(w, prm16)
+    runs = {"fp32": GpuRunner(w, prm32), "fp16": GpuRunner(w, prm16)}
     ohist = oracle.History(w.W, w.H)
     taint = np.zeros((H // 2, W // 2), bool)
     for k in range(nf):
         cam = w.camera(k)
         gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, prm32, W, H))
         ref = oracle.frame(osc, cam, prm32, W, H, gb, ohist)
-        a = g32.frame(cam, gb)
-        b = g16.frame(cam, gb, read=False)
-        _, _, n_bad, mism = classify_hits(osc, w, prm32, cam, a, ref)
+        got = {form: g.frame(cam, gb) for form, g in runs.items()}
+        _, _, n_bad, mism = classify_hits(osc, w, prm32, cam, got["fp32"], ref)
         assert n_bad == 0
+        assert np.array_equal(got["fp16"]["ray_prim"], got["fp32"]["ray_prim"])
         taint = dilate(dilate(taint, 2) | mism | threshold_ties(ref, prm32, cam, w), taint_radius(prm32))
         tf = full_res(taint, W, H)
-        e32 = max_abs(a["out"][..., :3][~tf], ref["out"][..., :3][~tf])
-        e16 = max_abs(b["out"][..., :3][~tf], ref["out"][..., :3][~tf])
-        p16 = psnr(b["out"][..., :3], ref["out"][..., :3])
-        print(f"[fp16 {name}] frame={k} max_fp32={e32:.3g} max_fp16={e16:.3g} psnr_fp16={p16:.1f} tainted={tf.mean():.3g}")
-        assert e16 <= 2e-3 and p16 >= 50.0, (e16, p16)
+        ok = ~taint
+        hist_ch = [0, 1, 2, 3, 4, 5, 6, 7, 10, 11]
+        for form, g in got.items():
+            err = dict(pp_med=max_hdr(g["pp_med"], ref["pp_med"]),
+                       crt=max_hdr(g["crt"][ok], ref["crt"][ok]),
+                       rt_med=max_hdr(g["rt_med"][ok], ref["rt_med"][ok]),
+                       recon=max_hdr(g["recon"][ok], ref["recon"][ok]),
+                       hist=max_hdr(g["hist"][..., hist_ch][ok], ref["hist"][..., hist_ch][ok]),
+                       out=max_hdr(g["out"][..., :3][~tf], ref["out"][..., :3][~tf]))
+            p_out = psnr(g["out"][..., :3], ref["out"][..., :3])
+            print(f"[precision {name} {form}] frame={k} " + " ".join(f"{o}={e:.3g}" for o, e in err.items())
+                  + f" psnr_out={p_out:.1f} tainted={tf.mean():.3g}")
+            for o, e in err.items():
+                assert e <= OUTPUT_TOL[form][o], (form, o, e)
+            assert p_out >= 50.0, (form, p_out)
 
 
 def test_determinism_bit_identical():
@@ -614,6 +684,18 @@ def test_full_size_c2_two_frames():
     w = make_workload("c2", n_frames=2)
     stats = run_sequence(w, 2)
     _print(stats, "c2-full")
+    tot = sum(s["rays"] for s in stats)
+    mis = sum(s["mismatches"] for s in stats)
+    assert mis <= max(2, 1e-4 * tot), (mis, tot)
+
+
+def test_full_size_c3_two_frames():
+    """3840x2160, 1,980,930 triangles, 85 mm f/1.2, CoC radius clamp 64 px, 4 spp, frames
+    0 and 1 of the dolly at full size, in the launch configuration the benchmark times
+    (the main filter's halo and the tracer's batch as at 4K)."""
+    w = make_workload("c3", n_frames=2)
+    stats = run_sequence(w, 2)
+    _print(stats, "c3-full")
     tot = sum(s["rays"] for s in stats)
     mis = sum(s["mismatches"] for s in stats)
     assert mis <= max(2, 1e-4 * tot), (mis, tot)

@@ -41,6 +41,14 @@ class _Ctx:
     def set_trace(self, **kw):
         self.cfg.update(kw)
 
+    def set_gather(self, block=None, main_form=None, recon_block=None):
+        if block is not None:
+            self.cfg["gather_block"] = tuple(block)
+        if main_form is not None:
+            self.cfg["main_form"] = main_form
+        if recon_block is not None:
+            self.cfg["recon_block"] = tuple(recon_block)
+
     def set_ploc_radius(self, r):
         self.radius = r
 
@@ -49,8 +57,10 @@ class _Ctx:
 
 
 def _cost(cfg):
-    # separable, minimum at width 2, 6 blocks per SM, refill 12, 32 steps
-    return (1.0 + (0.3 if cfg["bvh_width"] == 4 else 0.0) + 0.05 * abs(cfg["blocks_per_sm"] - 6)
+    # separable, minimum at width 2, lens grid 8, stack 64, 6 blocks per SM, refill 12, 32 steps
+    return (1.0 + (0.3 if cfg["bvh_width"] == 4 else 0.0) + 0.04 * abs(cfg["ray_grid"] - 8)
+            + 0.001 * abs(cfg["stack"] - 64)
+            + 0.05 * abs(cfg["blocks_per_sm"] - 6)
             + 0.02 * abs(cfg["refill_idle"] - 12) + 0.001 * abs(cfg["steps"] - 32))
 
 
@@ -63,7 +73,7 @@ def test_tune_trace_finds_the_optimum_of_a_separable_cost(monkeypatch):
         clock.t += _cost(ctx.cfg)
 
     best, seen = tune.tune_trace(ctx, run_frame, frames=3, stream=types.SimpleNamespace())
-    assert best == {"bvh_width": 2, "blocks_per_sm": 6, "refill_idle": 12, "steps": 32}
+    assert best == {"bvh_width": 2, "ray_grid": 8, "stack": 64, "blocks_per_sm": 6, "refill_idle": 12, "steps": 32}
     assert ctx.cfg == best                         # the context keeps the winner
     for key, ms in seen.items():
         assert ms == pytest.approx(_cost(dict(key)))
@@ -164,3 +174,38 @@ def test_tune_trace_searches_only_the_widths_given(monkeypatch):
     best, seen = tune.tune_trace(ctx, run_frame, frames=2, stream=types.SimpleNamespace(), widths=(2,))
     assert best["bvh_width"] == 2
     assert all(dict(key)["bvh_width"] == 2 for key in seen)
+
+
+def test_tune_gathers_finds_the_optimum_and_leaves_it_on_the_context(monkeypatch):
+    clock = _Clock()
+    _fake_cuda(monkeypatch, clock)
+    ctx = _Ctx()
+    ctx.cfg.update(tune.GATHER_DEFAULT)
+    shape_cost = {(32, 8): 0.2, (16, 16): 0.1, (64, 4): 0.3, (32, 16): 0.0, (64, 8): 0.05}
+    form_cost = {0: 0.1, 1: 0.2, 2: 0.0}
+
+    recon_cost = {(32, 8): 0.1, (16, 16): 0.0, (64, 4): 0.2, (32, 16): 0.05, (64, 8): 0.3}
+
+    def run_frame(k):
+        clock.t += (1.0 + shape_cost[ctx.cfg["gather_block"]] + form_cost[ctx.cfg["main_form"]]
+                    + recon_cost[ctx.cfg["recon_block"]])
+
+    best, seen = tune.tune_gathers(ctx, run_frame, frames=2, stream=types.SimpleNamespace())
+    assert best == {"gather_block": (32, 16), "main_form": 2, "recon_block": (16, 16)}
+    assert ctx.cfg["gather_block"] == (32, 16) and ctx.cfg["main_form"] == 2 and ctx.cfg["recon_block"] == (16, 16)
+    for key in seen:
+        for name, v in dict(key).items():
+            assert v in tune.GATHER_SPACE[name]
+
+
+def test_tune_gathers_keeps_the_default_within_one_percent(monkeypatch):
+    clock = _Clock()
+    _fake_cuda(monkeypatch, clock)
+    ctx = _Ctx()
+    ctx.cfg.update(tune.GATHER_DEFAULT)
+
+    def run_frame(k):
+        clock.t += 1.0 - (0.004 if ctx.cfg["gather_block"] == (16, 16) else 0.0)
+
+    best, _ = tune.tune_gathers(ctx, run_frame, frames=2, stream=types.SimpleNamespace())
+    assert best == tune.GATHER_DEFAULT
