@@ -48,15 +48,15 @@ FLOP_PER_TRI = 48.0
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes (read + write) per launch from the last ncu capture of each kernel on the
-# workload (profiles/top_kernels_*.md, the tracer: profiles/tracer_traffic_c2_c3.md); a
-# kernel or workload changed since then has no
-# entry.  The 4K tracer was captured at 1920x1080 (same scene, lens, 4 spp) and is
-# scaled by the rays of a full launch (6.72M / 1.78M); its DRAM writes are the rays it
-# keeps for the shader that L2 does not hold, so the scaled figure is an estimate.
-PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": 10.1e6, "k_recon": 25.3e6,
-                           "k_main_filter": 10.4e6, "k_accumulate": 56.2e6, "k_composite": 63.4e6,
-                           "k_downscale_tiles": 41.7e6},
-                    "c3": {"k_trace_rays<0>": 30.7e6 * 6.72 / 1.78}}
+# workload (profiles/tracer_c3_1080p.md); a kernel or workload changed since its capture
+# has None.  The 4K tracer was captured at 1920x1080 (same scene, lens, 4 spp, rays
+# grouped by lens cell) and is scaled by the rays of a full launch (6.72M / 1.78M); its
+# DRAM writes are the rays it keeps for the shader that L2 does not hold, so the scaled
+# figure is an estimate.
+PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_recon": None,
+                           "k_main_filter": None, "k_accumulate": None, "k_composite": None,
+                           "k_downscale_tiles": None},
+                    "c3": {"k_trace_rays<0>": (21.68e6 + 10.87e6) * 6.72 / 1.78}}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
@@ -71,10 +71,9 @@ BYTES = {
     "k_trace_rays": ("R", 36.0),              # per ray: ray list 4 read, hit 8 + kept ray 24 written (BVH reads hit L2)
     "k_shade": [("M", 76.0), ("R", 32.0)],  # queue, count, first ray read, 4 x float4 written; hits + kept rays read
     "k_accumulate": ("N", 192.0),        # rt 64 + z 4 + nrays 4 + history 48 read; history 48 + 24 written
-    "k_median_rt": ("N", 72.0),          # fused: variance blur (var 4 read, 4 written), RT median
+    "k_median_rt": ("N", 80.0),          # fused: variance blur (var 4 read, 4 written), RT median
                                          # (crt 16 + nrays 4 read, 16 written), mip 0 (ct 4 read,
-                                         # 24 written)
-    "k_mips": ("N", 40.0),               # mip levels 1-3: level reads 24 (1 + 1/4 + 1/16), writes 24 / 3
+                                         # 24 written), mip levels 1-3 (24 x (1/4 + 1/16 + 1/64) written)
     "k_recon": ("N", 44.0),
     "k_composite": ("P", 45.0),          # colour 16 + depth 4 read, 16 written, + hpx inputs / 4
                                          # (one thread per hpx writes its 2x2 fpx)
@@ -91,7 +90,7 @@ def algo_bytes(kernel, units):
 
 
 # HBM-bound streaming passes and the gather passes of a frame
-STREAMING = ["k_downscale_tiles", "k_median_pp", "k_mask_compact", "k_accumulate", "k_median_rt", "k_mips",
+STREAMING = ["k_downscale_tiles", "k_median_pp", "k_mask_compact", "k_accumulate", "k_median_rt",
              "k_composite", "k_taa"]
 GATHERS = ["k_prefilter", "k_main_filter", "k_recon"]
 
@@ -431,7 +430,8 @@ def run_ours(args, rank, world):
         kavg["k_taa"] = 0.0             # no TAA launch: its timing slot only brackets nothing
     if int(prm["ray_mode"]) != 1:
         kavg["k_edges"] = 0.0
-    kavg["k_var_blur"] = 0.0             # fused into k_median_rt: its slot brackets nothing
+    for k in ("k_var_blur", "k_mips", "k_tile_dilate"):
+        kavg[k] = 0.0                    # fused into other kernels: their slots bracket nothing
     n_samples = math.ceil(args.steps / 32)
     rays_per_frame = rays / n_samples
     masked_per_frame = masked / n_samples
@@ -533,9 +533,10 @@ def run_ours(args, rank, world):
                            l2=f"inputs larger than L2: {CYCLE} distinct G-buffers cycled "
                               f"({CYCLE} x {w.W * w.H * 20 / 1e6:.0f} MB)"),
                roofline=roof, e2e=e2e, fp16_storage=fp16,
-               # counted by the library over the timed steps: per frame reset, 5 post-process,
-               # mask, trace, shade, accumulation, the fused RT resolve, mip levels 1-3, recon,
-               # composite (+ 2 edge kernels in adaptive mode, + the final TAA)
+               # counted by the library over the timed steps: per frame the downscale (with the
+               # counter reset), prefilter (with the tile dilation), main filter, median, mask,
+               # trace, shade, accumulation, the fused RT resolve (variance blur, median, mip
+               # pyramid), recon, composite (+ 2 edge kernels in adaptive mode, + the final TAA)
                gpu_launches=int(launches),
                clocks=clocks, kernel_ms=kern,
                image_passes={"streaming": {"kernels": STREAMING, "ms": round(img_ms, 4),
@@ -798,6 +799,7 @@ def run_serve(args):
                 sweep.append(dict(point(st_f, n_f, scale * offered_nominal), load=f))
             out[name] = dict(capacity_frames_per_s=round(cap, 2), overload=point(st, n_req, offered_nominal),
                              sweep=sweep)
+    n_rejected = len(srv.rejected)
     for k in list(srv.specs):
         srv.release(k)
     del ex, srv
@@ -826,7 +828,7 @@ def run_serve(args):
                                      "triangles, 40 GB device budget, continuous batching (<= 32 per launch, "
                                      "2 streams)"),
                 served=dict(p50_ms_at_half_load=half["p50_ms"], p99_ms_at_half_load=half["p99_ms"],
-                            admitted=len(admitted), rejected=len(srv.rejected)),
+                            admitted=len(admitted), rejected=n_rejected),
                 forms=out, budget_8gb=budget8, setup_s=round(setup_s, 1), clocks=clk.summary(),
                 note="value = batched FP32 capacity (served frames/s when every session always has a "
                      "request); sweep loads are fractions of it, the same offered loads for every form")

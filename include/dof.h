@@ -344,7 +344,9 @@ unsigned long long dof_launch_count(void);
 /* Synchronise `stream` and report the last frame's counters and the device status. */
 int dof_frame_stats(DofHistory *hist, void *stream, DofFrameStats *out);
 
-/* Kernels of one frame, in launch order (DOF_HIST_TIMING brackets each with events). */
+/* Timing slots of one frame, in launch order (DOF_HIST_TIMING brackets each with events).
+ * DILATE, VAR_BLUR and MIPS are fused into PREFILTER / MASK, MEDIAN_RT and MEDIAN_RT
+ * respectively: their slots bracket no kernel and count 0. */
 enum {
     DOF_K_DOWNSCALE = 0, DOF_K_DILATE, DOF_K_PREFILTER, DOF_K_MAIN, DOF_K_MEDIAN_PP, DOF_K_EDGES,
     DOF_K_MASK, DOF_K_TRACE, DOF_K_SHADE, DOF_K_ACCUM, DOF_K_VAR_BLUR, DOF_K_MEDIAN_RT, DOF_K_MIPS,

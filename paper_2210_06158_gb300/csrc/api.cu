@@ -718,14 +718,7 @@ static void shape_grid(const BatchArgs &A, const SessDesc &d, const DofHistory *
     switch (shape) {
         case SH_GATHER: gx = ((int)h->W2 + A.gather_w - 1) / A.gather_w; gy = ((int)h->H2 + A.gather_h - 1) / A.gather_h; break;
         case SH_RECON: gx = ((int)h->W2 + A.recon_w - 1) / A.recon_w; gy = ((int)h->H2 + A.recon_h - 1) / A.recon_h; break;
-        case SH_TILE8: gx = (int)h->TW; gy = (int)h->TH; break;
-        case SH_TILEDIL: gx = ((int)h->TW + 15) / 16; gy = ((int)h->TH + 15) / 16; break;
         case SH_HPX: gx = ((int)h->W2 + 31) / 32; gy = ((int)h->H2 + 7) / 8; break;
-        case SH_MIP1: case SH_MIP2: case SH_MIP3: {
-            int l = shape - SH_MIP1 + 1;
-            gx = (d.mip_w[l] + 31) / 32; gy = (d.mip_h[l] + 7) / 8;
-            break;
-        }
         case SH_FPX: gx = ((int)h->W + 31) / 32; gy = ((int)h->H + 7) / 8; break;
         default: gx = ((int)h->N + 127) / 128; gy = 1; break;   // SH_SHADE
     }
@@ -770,7 +763,6 @@ static int build_batch(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, BatchAr
 template <class AS>
 static void enqueue_step(DofCtx *ctx, const BatchArgs &A, const AS &as, bool adaptive, cudaStream_t st, DofHistory *tm) {
     const int trace_blocks = ctx->sm_count * ctx->trace_blocks_per_sm;
-    launch_reset_b(A, as, st);
     launch_tiles_b(A, as, st, tm);
     if (tm) {
         // per-kernel timing: every kernel in sequence on the caller's stream

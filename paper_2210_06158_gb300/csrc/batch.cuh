@@ -9,12 +9,7 @@
 #include "dof_internal.cuh"
 
 enum LaunchShape {
-    SH_TILE8 = 0,   // one 8x8 block per max-CoC tile
-    SH_TILEDIL,     // 16x16 tiles per block
-    SH_HPX,         // 32x8 half-resolution pixels per block
-    SH_MIP1,        // 32x8 texels of mip level 1
-    SH_MIP2,
-    SH_MIP3,
+    SH_HPX = 0,     // 32x8 half-resolution pixels per block
     SH_FPX,         // 32x8 full-resolution pixels per block
     SH_SHADE,       // 128 queue entries per block
     SH_GATHER,      // the main filter's 81-tap gather: gather_w x gather_h hpx
@@ -98,6 +93,37 @@ __device__ __forceinline__ const SessDesc &block_session(const BatchArgs &A, int
 }
 #endif
 
+#ifdef __CUDACC__
+// A2, tile dilation, for the four 8x8 tiles of a 32x8-pixel block (block origin bx, by in
+// half-resolution pixels): warp w < 4 takes tile (bx / 8 + w, by / 8) and the max of
+// (near radius, |rho|) over its (2K+1)^2 neighbourhood of raw tiles, lanes striding the
+// neighbourhood and a shuffle reduction across the warp.  Result in out[w] (shared
+// memory; the caller synchronises before reading it).  Tiles past the image's tile grid
+// are left untouched.
+__device__ __forceinline__ void dilate_block_tiles(const SessDesc &S, int bx, int by, float2 *out) {
+    const DevParams &p = S.p;
+    const unsigned lane = threadIdx.x & 31u, w = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int tx = bx / 8 + (int)w, ty = by / 8;
+    if (w >= 4 || tx >= p.tiles_w || ty >= p.tiles_h) return;
+    const int K = p.dil_k, side = 2 * K + 1;
+    float nm = 0.f, am = 0.f;
+    for (int e = (int)lane; e < side * side; e += 32) {
+        const int y = ty - K + e / side, x = tx - K + e % side;
+        if (x >= 0 && y >= 0 && x < p.tiles_w && y < p.tiles_h) {
+            const float2 v = __ldg(&S.tiles[y * p.tiles_w + x]);
+            nm = fmaxf(nm, v.x);
+            am = fmaxf(am, v.y);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nm = fmaxf(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+    }
+    if (lane == 0) out[w] = make_float2(nm, am);
+}
+#endif
+
 // device: the batch descriptor, passed by value (a __grid_constant__ kernel parameter)
 // or, for captured graphs, as a pointer to device memory that a copy refreshes per step
 #ifdef __CUDACC__
@@ -108,7 +134,7 @@ __device__ __forceinline__ const BatchArgs &batch_args(const BatchArgs *a) { ret
 // host: launch wrappers per kernel group (post.cu, trace.cu, temporal.cu, recon.cu); `A`
 // gives the launch shapes, `as` is what the kernels receive (A itself, or a device
 // pointer to a copy of it)
-template <class AS> void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A1, A2
+template <class AS> void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A1
 template <class AS> void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);     // A3 - A5
 int main_filter_tile_bytes(const BatchArgs &A);   // the main filter's launch form (post.cu)
 template <class AS>
@@ -117,4 +143,3 @@ template <class AS> void launch_trace_b(const BatchArgs &A, const AS &as, int bl
 template <class AS> void launch_temporal_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);
 template <class AS> void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A10, A11
 template <class AS> void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A12
-template <class AS> void launch_reset_b(const BatchArgs &A, const AS &as, cudaStream_t st);

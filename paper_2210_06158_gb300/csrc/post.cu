@@ -21,6 +21,14 @@ __global__ void __launch_bounds__(256) k_downscale_tiles(const __grid_constant__
     const float4 *__restrict__ color = S.color;
     const float *__restrict__ depth = S.depth;
     const float4 *__restrict__ normal = S.normal;
+    // the first block of each session zeroes the session's per-frame counters (queue
+    // length, rays, work cursor, traversal counts; not the sticky status word): nothing of
+    // this frame reads them before the ray path, which starts after this kernel
+    if (i == (int)threadIdx.x && j == (int)threadIdx.y && threadIdx.x == 0 && threadIdx.y == 0) {
+        uint32_t *c = S.counters;
+        c[0] = c[1] = c[2] = 0u;
+        c[4] = c[5] = c[6] = c[7] = 0u;
+    }
     float nm = 0.f, am = 0.f;
     if (i < cam.W2 && j < cam.H2) {
         size_t f0 = (size_t)(2 * j) * cam.W + 2 * i, f1 = f0 + cam.W;
@@ -66,40 +74,29 @@ __global__ void __launch_bounds__(256) k_downscale_tiles(const __grid_constant__
     }
 }
 
-// A2: max over the (2K+1)^2 tile neighbourhood
+// A2 + A3: the dilated max-CoC of the block's four tiles (written out for the main
+// filter), then the 9-tap bilateral prefilter, radius max(R/8, sqrt(2)/2), taps at
+// angles k pi/4
 template <class AS>
-__global__ void k_tile_dilate(const __grid_constant__ AS as_) {
-    const BatchArgs &A = batch_args(as_);
-    int tx, ty;
-    const SessDesc &S = block_session(A, SH_TILEDIL, tx, ty);
-    const DevParams &p = S.p;
-    const float2 *tiles = S.tiles;
-    float2 *dil = S.tiles_dil;
-    if (tx >= p.tiles_w || ty >= p.tiles_h) return;
-    float nm = 0.f, am = 0.f;
-    for (int y = max(ty - p.dil_k, 0); y <= min(ty + p.dil_k, p.tiles_h - 1); y++)
-        for (int x = max(tx - p.dil_k, 0); x <= min(tx + p.dil_k, p.tiles_w - 1); x++) {
-            float2 v = __ldg(&tiles[y * p.tiles_w + x]);
-            nm = fmaxf(nm, v.x);
-            am = fmaxf(am, v.y);
-        }
-    dil[ty * p.tiles_w + tx] = make_float2(nm, am);
-}
-
-// A3: 9-tap bilateral prefilter, radius max(R/8, sqrt(2)/2), taps at angles k pi/4
-template <class AS>
-__global__ void k_prefilter(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(256) k_prefilter(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const DevParams &p = S.p;
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const float4 *__restrict__ pp_in = S.pp_in;
-    const float2 *__restrict__ dil = S.tiles_dil;
     float4 *pre = S.pre;
+    __shared__ float2 dil_s[4];
+    const int bx = i - (int)threadIdx.x, by = j - (int)threadIdx.y;
+    dilate_block_tiles(S, bx, by, dil_s);
+    __syncthreads();
+    if (threadIdx.y == 0 && threadIdx.x < 4) {
+        const int tx = bx / 8 + (int)threadIdx.x, ty = by / 8;
+        if (tx < p.tiles_w && ty < p.tiles_h) S.tiles_dil[ty * p.tiles_w + tx] = dil_s[threadIdx.x];
+    }
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
-    float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
+    float R = dil_s[threadIdx.x >> 3].y;
     float rp = fmaxf(R * 0.125f, 0.70710678118654752f);
     float4 c0 = __ldg(&pp_in[q]);
     float inv = 1.f / fmaxf(1.f, fabsf(c0.w));
@@ -276,13 +273,15 @@ __global__ void k_median_pp(const __grid_constant__ AS as_) {
 
 int post_init_tables() { return upload_filter_tables(); }
 
+// A1 (and the per-frame counter reset).  The tile dilation (A2) runs inside the kernels
+// that read it (the prefilter, which also writes it out, and the mask), so its timing
+// slot brackets nothing.
 template <class AS>
 void launch_tiles_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     k_downscale_tiles<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);
+    count_launches(1);
     tmark(tm, DOF_K_DOWNSCALE, st);
-    k_tile_dilate<AS><<<A.start[SH_TILEDIL][n], dim3(16, 16), 0, st>>>(as);
-    count_launches(2);
     tmark(tm, DOF_K_DILATE, st);
 }
 

@@ -11,9 +11,14 @@ namespace {
 // A9 / A10 / A11, fused per half-resolution pixel: the 5x5 binomial blur of the
 // luminance variance (Section 3.2.3), the lower median of the ray-traced colour over the
 // valid 3x3 neighbours (invalid slots padded with -inf / +inf so the median-of-9 network
-// selects index (k-1)/2 of the k valid values), and mip level 0 of the reconstruction,
-// (rgb, h) * v and (c_t, 1) * v.  The block's neighbourhoods (variance +-2, colour and
-// ray counts +-1) are loaded once into shared memory with clamped indices.
+// selects index (k-1)/2 of the k valid values), and the mip pyramid of the
+// reconstruction: level 0, (rgb, h) * v and (c_t, 1) * v, then levels 1-3 as 2x2 box
+// averages.  The block's neighbourhoods (variance +-2, colour and ray counts +-1) are
+// loaded once into shared memory with clamped indices.  A block covers 32x8 pixels of
+// level 0 at a multiple of (32, 8), which holds every texel its 16x4 texels of level 1,
+// 8x2 of level 2 and 4x1 of level 3 average (indices clamped to each level's size stay
+// inside the block); each level is summed from the values of the level below as they are
+// stored (FP16 storage rounds them), in the order (0,0), (1,0), (0,1), (1,1).
 template <class AS>
 __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
@@ -27,6 +32,8 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
     __shared__ float t_var[12][36];
     __shared__ float4 t_crt[10][34];
     __shared__ int t_n[10][34];
+    __shared__ float4 m0a[8][32];
+    __shared__ float2 m0b[8][32];
     const int bx = i - (int)threadIdx.x, by = j - (int)threadIdx.y;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int e = tid; e < 12 * 36; e += 256) {
@@ -42,132 +49,130 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
         t_n[ty][tx] = __ldg(&nrays[qn]);
     }
     __syncthreads();
-    if (i >= W2 || j >= H2) return;
-    const size_t q = (size_t)j * W2 + i;
     const int cx = (int)threadIdx.x, cy = (int)threadIdx.y;
-    // variance blur
-    {
-        const float b[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
-        float acc = 0.f;
+    if (i < W2 && j < H2) {
+        const size_t q = (size_t)j * W2 + i;
+        // variance blur
+        {
+            const float b[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
+            float acc = 0.f;
 #pragma unroll
-        for (int dy = 0; dy < 5; dy++) {
-            float row = 0.f;
+            for (int dy = 0; dy < 5; dy++) {
+                float row = 0.f;
 #pragma unroll
-            for (int dx = 0; dx < 5; dx++) row += b[dx] * t_var[cy + dy][cx + dx];
-            acc += b[dy] * row;
-        }
-        S.var_out[q] = acc * (1.f / 256.f);
-    }
-    float4 med = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 centre = t_crt[cy + 1][cx + 1];
-    const bool valid = t_n[cy + 1][cx + 1] > 0;
-    if (valid) {
-        float4 v[9];
-        bool ok[9];
-        int k = 0, n = 0;
-#pragma unroll
-        for (int dy = 0; dy < 3; dy++)
-#pragma unroll
-            for (int dx = 0; dx < 3; dx++) {
-                const int x = i + dx - 1, y = j + dy - 1;
-                const bool in = x >= 0 && y >= 0 && x < W2 && y < H2;
-                ok[n] = in && t_n[cy + dy][cx + dx] > 0;
-                v[n] = in ? t_crt[cy + dy][cx + dx] : centre;
-                k += ok[n];
-                n++;
+                for (int dx = 0; dx < 5; dx++) row += b[dx] * t_var[cy + dy][cx + dx];
+                acc += b[dy] * row;
             }
-        int lows = 4 - (k - 1) / 2;   // -inf pads; the rest of the invalid slots get +inf
-#pragma unroll
-        for (int m = 0; m < 9; m++)
-            if (!ok[m]) {
-                float pad = lows > 0 ? -INFINITY : INFINITY;
-                lows--;
-                v[m] = make_float4(pad, pad, pad, pad);
-            }
-        float4 m9 = median9(v);
-        med = make_float4(m9.x, m9.y, m9.z, centre.w);
-    }
-    st_img(S.rt_med, q, med, hs);
-    // mip level 0 from the median as stored (FP16 storage rounds it)
-    const float vv = valid ? 1.f : 0.f;
-    st_img(S.mip0[0], q, f4scale(vv, round_img(med, hs)), hs);
-    S.mip1[0][q] = make_float2(vv * __ldg(&S.ct[q]), vv);
-}
-
-// Mip levels 1-3 in one pass: a block computes 32x8 texels of level 1 from level 0,
-// then the 16x4 of level 2 and the 8x2 of level 3 they cover, from the values it keeps
-// in shared memory exactly as they are stored (FP16 storage rounds them), with the
-// same sums in the same order as one 2x2 box average per level.
-template <class AS>
-__global__ void __launch_bounds__(256) k_mips(const __grid_constant__ AS as_) {
-    const BatchArgs &A = batch_args(as_);
-    int i, j;
-    const SessDesc &S = block_session(A, SH_MIP1, i, j);
-    const bool hs = S.p.f16;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int bx = i - tx, by = j - ty;            // block origin at level 1
-    __shared__ float4 l1a[8][32], l2a[4][16];
-    __shared__ float2 l1b[8][32], l2b[4][16];
-    // level 1 from level 0 (global)
-    if (1 < S.mip_L && i < S.mip_w[1] && j < S.mip_h[1]) {
-        const int w = S.mip_w[0], h = S.mip_h[0];
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 b = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int t = 0; t < 4; t++) {
-            const int x = min(2 * i + (t & 1), w - 1), y = min(2 * j + (t >> 1), h - 1);
-            const size_t q = (size_t)y * w + x;
-            a = f4add(a, ld_img(S.mip0[0], q, hs));
-            const float2 c = __ldg(&S.mip1[0][q]);
-            b.x += c.x; b.y += c.y;
+            S.var_out[q] = acc * (1.f / 256.f);
         }
-        const float4 v = f4scale(0.25f, a);
-        const float2 u = make_float2(0.25f * b.x, 0.25f * b.y);
-        const size_t o = (size_t)j * S.mip_w[1] + i;
-        st_img(S.mip0[1], o, v, hs);
-        S.mip1[1][o] = u;
-        l1a[ty][tx] = round_img(v, hs);
-        l1b[ty][tx] = u;
+        float4 med = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 centre = t_crt[cy + 1][cx + 1];
+        const bool valid = t_n[cy + 1][cx + 1] > 0;
+        if (valid) {
+            float4 v[9];
+            bool ok[9];
+            int k = 0, n = 0;
+#pragma unroll
+            for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+                for (int dx = 0; dx < 3; dx++) {
+                    const int x = i + dx - 1, y = j + dy - 1;
+                    const bool in = x >= 0 && y >= 0 && x < W2 && y < H2;
+                    ok[n] = in && t_n[cy + dy][cx + dx] > 0;
+                    v[n] = in ? t_crt[cy + dy][cx + dx] : centre;
+                    k += ok[n];
+                    n++;
+                }
+            int lows = 4 - (k - 1) / 2;   // -inf pads; the rest of the invalid slots get +inf
+#pragma unroll
+            for (int m = 0; m < 9; m++)
+                if (!ok[m]) {
+                    float pad = lows > 0 ? -INFINITY : INFINITY;
+                    lows--;
+                    v[m] = make_float4(pad, pad, pad, pad);
+                }
+            float4 m9 = median9(v);
+            med = make_float4(m9.x, m9.y, m9.z, centre.w);
+        }
+        st_img(S.rt_med, q, med, hs);
+        // mip level 0 from the median as stored (FP16 storage rounds it)
+        const float vv = valid ? 1.f : 0.f;
+        const float4 l0 = f4scale(vv, round_img(med, hs));
+        const float2 l0b = make_float2(vv * __ldg(&S.ct[q]), vv);
+        st_img(S.mip0[0], q, l0, hs);
+        S.mip1[0][q] = l0b;
+        m0a[cy][cx] = round_img(l0, hs);
+        m0b[cy][cx] = l0b;
+    }
+    // levels 1-3 from the block's texels of the level below (shared memory), as stored
+    __shared__ float4 m1a[4][16], m2a[2][8];
+    __shared__ float2 m1b[4][16], m2b[2][8];
+    __syncthreads();
+    const int L = S.mip_L;
+    if (1 < L && tid < 64) {
+        const int ux = tid & 15, uy = tid >> 4;          // level-1 texel of the block
+        const int i1 = bx / 2 + ux, j1 = by / 2 + uy;
+        if (i1 < S.mip_w[1] && j1 < S.mip_h[1]) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 b = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int x = min(2 * i1 + (t & 1), W2 - 1) - bx, y = min(2 * j1 + (t >> 1), H2 - 1) - by;
+                a = f4add(a, m0a[y][x]);
+                const float2 c = m0b[y][x];
+                b.x += c.x; b.y += c.y;
+            }
+            const float4 v = f4scale(0.25f, a);
+            const float2 u = make_float2(0.25f * b.x, 0.25f * b.y);
+            const size_t o = (size_t)j1 * S.mip_w[1] + i1;
+            st_img(S.mip0[1], o, v, hs);
+            S.mip1[1][o] = u;
+            m1a[uy][ux] = round_img(v, hs);
+            m1b[uy][ux] = u;
+        }
     }
     __syncthreads();
-    // level 2 from the block's level-1 texels
-    const int i2 = bx / 2 + tx, j2 = by / 2 + ty;
-    if (tx < 16 && ty < 4 && 2 < S.mip_L && i2 < S.mip_w[2] && j2 < S.mip_h[2]) {
-        const int w = S.mip_w[1], h = S.mip_h[1];
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 b = make_float2(0.f, 0.f);
+    if (2 < L && tid < 16) {
+        const int ux = tid & 7, uy = tid >> 3;           // level-2 texel of the block
+        const int i2 = bx / 4 + ux, j2 = by / 4 + uy;
+        if (i2 < S.mip_w[2] && j2 < S.mip_h[2]) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 b = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
-            const int x = min(2 * i2 + (t & 1), w - 1) - bx, y = min(2 * j2 + (t >> 1), h - 1) - by;
-            a = f4add(a, l1a[y][x]);
-            const float2 c = l1b[y][x];
-            b.x += c.x; b.y += c.y;
+            for (int t = 0; t < 4; t++) {
+                const int x = min(2 * i2 + (t & 1), S.mip_w[1] - 1) - bx / 2;
+                const int y = min(2 * j2 + (t >> 1), S.mip_h[1] - 1) - by / 2;
+                a = f4add(a, m1a[y][x]);
+                const float2 c = m1b[y][x];
+                b.x += c.x; b.y += c.y;
+            }
+            const float4 v = f4scale(0.25f, a);
+            const float2 u = make_float2(0.25f * b.x, 0.25f * b.y);
+            const size_t o = (size_t)j2 * S.mip_w[2] + i2;
+            st_img(S.mip0[2], o, v, hs);
+            S.mip1[2][o] = u;
+            m2a[uy][ux] = round_img(v, hs);
+            m2b[uy][ux] = u;
         }
-        const float4 v = f4scale(0.25f, a);
-        const float2 u = make_float2(0.25f * b.x, 0.25f * b.y);
-        const size_t o = (size_t)j2 * S.mip_w[2] + i2;
-        st_img(S.mip0[2], o, v, hs);
-        S.mip1[2][o] = u;
-        l2a[ty][tx] = round_img(v, hs);
-        l2b[ty][tx] = u;
     }
     __syncthreads();
-    // level 3 from the block's level-2 texels
-    const int i3 = bx / 4 + tx, j3 = by / 4 + ty;
-    if (tx < 8 && ty < 2 && 3 < S.mip_L && i3 < S.mip_w[3] && j3 < S.mip_h[3]) {
-        const int w = S.mip_w[2], h = S.mip_h[2];
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 b = make_float2(0.f, 0.f);
+    if (3 < L && tid < 4) {
+        const int i3 = bx / 8 + tid, j3 = by / 8;        // level-3 texel of the block
+        if (i3 < S.mip_w[3] && j3 < S.mip_h[3]) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 b = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
-            const int x = min(2 * i3 + (t & 1), w - 1) - bx / 2, y = min(2 * j3 + (t >> 1), h - 1) - by / 2;
-            a = f4add(a, l2a[y][x]);
-            const float2 c = l2b[y][x];
-            b.x += c.x; b.y += c.y;
+            for (int t = 0; t < 4; t++) {
+                const int x = min(2 * i3 + (t & 1), S.mip_w[2] - 1) - bx / 4;
+                const int y = min(2 * j3 + (t >> 1), S.mip_h[2] - 1) - by / 4;
+                a = f4add(a, m2a[y][x]);
+                const float2 c = m2b[y][x];
+                b.x += c.x; b.y += c.y;
+            }
+            const size_t o = (size_t)j3 * S.mip_w[3] + i3;
+            st_img(S.mip0[3], o, f4scale(0.25f, a), hs);
+            S.mip1[3][o] = make_float2(0.25f * b.x, 0.25f * b.y);
         }
-        const size_t o = (size_t)j3 * S.mip_w[3] + i3;
-        st_img(S.mip0[3], o, f4scale(0.25f, a), hs);
-        S.mip1[3][o] = make_float2(0.25f * b.x, 0.25f * b.y);
     }
 }
 
@@ -453,12 +458,13 @@ template <class AS>
 void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;
     dim3 b(32, 8);
+    // the variance blur, the RT median and the whole mip pyramid in one kernel (the mip
+    // timing slot brackets nothing)
     k_resolve_rt<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MEDIAN_RT, st);
-    k_mips<AS><<<A.start[SH_MIP1][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MIPS, st);
     k_recon<AS><<<A.start[SH_RECON][n], dim3(A.recon_w, A.recon_h), 0, st>>>(as);
-    count_launches(3);
+    count_launches(2);
     tmark(tm, DOF_K_RECON, st);
 }
 

@@ -179,27 +179,6 @@ void launch_temporal_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHis
     tmark(tm, DOF_K_VAR_BLUR, st);
 }
 
-// zero the per-frame counters of every session and the batch's ray cursor
-template <class AS>
-__global__ void k_reset(const __grid_constant__ AS as_) {
-    const BatchArgs &A = batch_args(as_);
-    int s = threadIdx.x;
-    if (s == 0) *A.cursor = 0u;
-    if (s < A.ns) {
-        uint32_t *c = A.s[s].counters;
-        c[0] = c[1] = c[2] = 0u;
-        c[4] = c[5] = c[6] = c[7] = 0u;
-    }
-}
-
-template <class AS>
-void launch_reset_b(const BatchArgs &A, const AS &as, cudaStream_t st) {
-    k_reset<AS><<<1, kMaxBatch, 0, st>>>(as);
-    count_launches(1);
-}
-
 // the two argument forms: by value (a kernel parameter) and from device memory (graphs)
 template void launch_temporal_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t, DofHistory *);
 template void launch_temporal_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, cudaStream_t, DofHistory *);
-template void launch_reset_b<BatchArgs>(const BatchArgs &, const BatchArgs &, cudaStream_t);
-template void launch_reset_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, cudaStream_t);

@@ -398,11 +398,15 @@ __global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ AS
     const SessDesc &S = block_session(A, SH_HPX, i, j);
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const DevParams &p = S.p;
-    const float2 *tiles_dil = S.tiles_dil;
     const float *xf = S.xf;
     int32_t *nrays = S.nrays;
     uint32_t *queue = S.queue, *first_ray = S.first_ray, *ray_pix = S.ray_pix, *counters = S.counters;
     const unsigned lane = threadIdx.x, warp = threadIdx.y;
+    // the dilated max-CoC of the block's four tiles (A2; the prefilter computes the same
+    // values on the other stream and writes them out)
+    __shared__ float2 dil_s[4];
+    dilate_block_tiles(S, i - (int)threadIdx.x, j - (int)threadIdx.y, dil_s);
+    __syncthreads();
     // each warp takes an 8x4 tile of the block's 32x8 pixels, lanes in Morton order, so
     // that the 32 consecutive rays a tracer warp takes come from a compact patch
     i = i - (int)threadIdx.x + (int)((warp & 3u) * 8u + (lane & 1u) + ((lane >> 1) & 2u) + ((lane >> 2) & 4u));
@@ -411,7 +415,7 @@ __global__ void __launch_bounds__(256) k_mask_compact(const __grid_constant__ AS
     uint32_t q = 0;
     if (i < W2 && j < H2) {
         q = (uint32_t)j * W2 + i;
-        float near_max = __ldg(&tiles_dil[(j >> 3) * p.tiles_w + (i >> 3)]).x;
+        float near_max = dil_s[warp & 3u].x;
         if (near_max >= p.mask_near_hpx) {
             if (p.ray_mode == 0) n = p.spp;
             else n = (int)fminf(fmaxf(ceilf(__ldg(&xf[q])), 1.f), p.m);

@@ -592,12 +592,29 @@ def test_fp16_storage_error_vs_oracle(name, W, H, nf):
     for k in range(nf):
         cam = w.camera(k)
         gb = oracle.gbuffer_f32(oracle.gbuffer(osc, cam, prm32, W, H))
+        hist0 = ohist.copy()
         ref = oracle.frame(osc, cam, prm32, W, H, gb, ohist)
         got = {form: g.frame(cam, gb) for form, g in runs.items()}
-        _, _, n_bad, mism = classify_hits(osc, w, prm32, cam, got["fp32"], ref)
-        assert n_bad == 0
         assert np.array_equal(got["fp16"]["ray_prim"], got["fp32"]["ray_prim"])
-        taint = dilate(dilate(taint, 2) | mism | threshold_ties(ref, prm32, cam, w), taint_radius(prm32))
+        assert np.array_equal(got["fp16"]["nrays"], got["fp32"]["nrays"])
+        # counts may differ only on mask ties (fixed mode); the oracle then takes the kernel's
+        diff_n = got["fp32"]["nrays"] != ref["nrays"]
+        assert not diff_n[~mask_ties(ref, prm32)].any()
+        force = np.where(diff_n, got["fp32"]["nrays"], -1).astype(np.int32) if diff_n.any() else None
+        if force is not None:
+            ohist = hist0.copy()
+            ref = oracle.frame(osc, cam, prm32, W, H, gb, ohist, nrays_force=force)
+        n_rays, n_mis, n_bad, _ = classify_hits(osc, w, prm32, cam, got["fp32"], ref)
+        assert n_bad == 0 and n_mis <= max(2, 1e-4 * n_rays)
+        if n_mis:
+            # either hit is valid: the oracle takes the kernels' (both forms trace the same rays)
+            mr_o = ref["ray_prim"].shape[2]
+            valid = np.arange(mr_o)[None, None, :] < ref["nrays"][..., None]
+            gp = got["fp32"]["ray_prim"][..., :mr_o]
+            hforce = np.where(valid & (gp != ref["ray_prim"]), gp, -2).astype(np.int32)
+            ohist = hist0.copy()
+            ref = oracle.frame(osc, cam, prm32, W, H, gb, ohist, nrays_force=force, hit_force=hforce)
+        taint = dilate(dilate(taint, 2) | weight_ties(ref), taint_radius(prm32))
         tf = full_res(taint, W, H)
         ok = ~taint
         hist_ch = [0, 1, 2, 3, 4, 5, 6, 7, 10, 11]
@@ -732,7 +749,7 @@ def test_host_frames_equal_device_frames():
 
 
 def test_launch_count_per_frame():
-    """The library's own launch tally (dof_launch_count): 14 kernels per frame, +2 for the
+    """The library's own launch tally (dof_launch_count): 11 kernels per frame, +2 for the
     edge measure in the adaptive mode, +1 for the final TAA; a replayed graph counts the
     kernels it holds."""
     from paper_2210_06158_gb300 import dof
@@ -741,8 +758,8 @@ def test_launch_count_per_frame():
     ctx = dof.Context(0)
     sc = dof.Scene(ctx, w.scene)
     g = dof.gbuffer(ctx, sc, w.camera(0), w.params, w.W, w.H)
-    for over, taa, want in ((dict(ray_mode=0), False, 14), (dict(ray_mode=1, m=4), False, 16),
-                            (dict(ray_mode=0, taa_alpha=0.1), True, 15)):
+    for over, taa, want in ((dict(ray_mode=0), False, 11), (dict(ray_mode=1, m=4), False, 13),
+                            (dict(ray_mode=0, taa_alpha=0.1), True, 12)):
         prm = dict(w.params, **over)
         h = dof.History(ctx, w.W, w.H, max_rays=oracle.max_rays(prm), taa=taa)
         dof.frame(ctx, sc, g, w.camera(0), prm, h)
@@ -758,5 +775,5 @@ def test_launch_count_per_frame():
     graph.launch(items)
     graph.launch(items)
     torch.cuda.synchronize()
-    assert dof.launch_count() - n0 == 2 * 14
+    assert dof.launch_count() - n0 == 2 * 11
     graph.close()
