@@ -89,9 +89,12 @@ def algo_bytes(kernel, units):
     return sum(units[u] * b for u, b in terms)
 
 
-# HBM-bound streaming passes and the gather passes of a frame
-STREAMING = ["k_downscale_tiles", "k_median_pp", "k_mask_compact", "k_accumulate", "k_median_rt",
-             "k_composite", "k_taa"]
+# HBM-bound streaming passes and the gather passes of a frame.  The mask kernel (ray
+# count, compaction, and, when the tracer takes rays grouped by lens cell, one Philox
+# lens sample per ray) is reported apart: with the grouping it is bound by that
+# arithmetic, not by its few bytes.
+STREAMING = ["k_downscale_tiles", "k_median_pp", "k_accumulate", "k_median_rt", "k_composite", "k_taa"]
+RAY_LIST = ["k_mask_compact"]
 GATHERS = ["k_prefilter", "k_main_filter", "k_recon"]
 
 
@@ -520,6 +523,7 @@ def run_ours(args, rank, world):
         return b, t
     img_bytes, img_ms = agg(STREAMING)
     gat_bytes, gat_ms = agg(GATHERS)
+    ray_bytes, ray_ms = agg(RAY_LIST)
     res = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=world, steps=args.steps,
                warmup=args.warmup, ms_per_step=round(ms_per_step, 4), higher_is_better=True, scaling="weak",
                vs_baseline=None, dtype="f32", data="synthetic",
@@ -544,7 +548,12 @@ def run_ours(args, rank, world):
                                            "frac_of_hbm": round(img_bytes / (img_ms * 1e-3) / 1e9 / hbm_peak, 4)},
                              "gathers": {"kernels": GATHERS, "ms": round(gat_ms, 4),
                                          "gbs": round(gat_bytes / (gat_ms * 1e-3) / 1e9, 1),
-                                         "bound": "L1 / issue (81-tap taps), see profiles/"}},
+                                         "bound": "L1 / issue (81-tap taps), see profiles/"},
+                             "ray_list": {"kernels": RAY_LIST, "ms": round(ray_ms, 4),
+                                          "gbs": round(ray_bytes / (ray_ms * 1e-3) / 1e9, 1) if ray_ms > 0 else None,
+                                          "lens_grid": tuned.get("ray_grid"),
+                                          "bound": "HBM in pixel order; one Philox lens sample per ray "
+                                                   "when grouped by lens cell"}},
                mrays_per_s=round(rays_per_frame / (kavg.get("k_trace_rays", 0) * 1e-3) / 1e6, 1)
                if kavg.get("k_trace_rays", 0) > 0 else None,
                rays_per_frame=int(rays_per_frame), mask_fraction=round(masked_per_frame / N, 4),
