@@ -233,6 +233,9 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return a + t
 __device__ __forceinline__ float lum709(float r, float g, float b) { return 0.2126f * r + 0.7152f * g + 0.0722f * b; }
 
 // colour image buffers: float4, or 4 x FP16 (8 bytes) when `h` (FP32 arithmetic either way)
+// hint: bring the line holding p into L1 (holds no register; p must be a valid address)
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 __device__ __forceinline__ float4 ld_img(const float4 *base, size_t i, bool h) {
     if (h) {
         uint2 u = __ldg(reinterpret_cast<const uint2 *>(base) + i);

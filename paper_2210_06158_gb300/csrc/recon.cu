@@ -317,6 +317,15 @@ __global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS
     const int W2 = cam.W2, H2 = cam.H2;
     if (i >= W2 || j >= H2) return;
     const bool hs = p.f16;
+    // the 2x2 full-resolution inputs are prefetched into L1 first (no registers held),
+    // so their misses overlap the neighbourhood's loads
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        const size_t f = (size_t)(2 * j + b) * cam.W + 2 * i;
+        prefetch_l1(&depth[f]);
+        prefetch_l1(S.gf16 ? reinterpret_cast<const void *>(reinterpret_cast<const uint2 *>(color) + f)
+                           : reinterpret_cast<const void *>(color + f));
+    }
     // accumulators of the 2x2 full-resolution pixels (a, b) -> index 2 b + a; the
     // neighbourhood is visited in raster order, so each pixel sums its four taps in
     // the order (x0, y0), (x0 + 1, y0), (x0, y0 + 1), (x0 + 1, y0 + 1)
@@ -336,7 +345,9 @@ __global__ void __launch_bounds__(256, 4) k_composite(const __grid_constant__ AS
             size_t q = (size_t)y * W2 + x;
             const float4 P = ld_img(pp_med, q, hs);
             const bool V = __ldg(&nrays[q]) > 0;
-            const float4 R = V ? ld_img(recon, q, hs) : make_float4(0.f, 0.f, 0.f, 0.f);
+            // a pixel without rays holds zeros in the reconstruction, so the load need not
+            // wait for its ray count (only pixels with rays are summed below)
+            const float4 R = ld_img(recon, q, hs);
 #pragma unroll
             for (int b = 0; b < 2; b++)
 #pragma unroll

@@ -44,10 +44,11 @@ __device__ __forceinline__ float fetch(const float4 *__restrict__ H0, const floa
         int xi = x0 + dx, yi = y0 + dy;
         if (xi < 0 || yi < 0 || xi >= W2 || yi >= H2n) continue;
         size_t q = (size_t)yi * W2 + xi;
-        float4 h0 = __ldg(&H0[q]), h1 = __ldg(&H1[q]);
+        // the three planes are requested together (the third one used to wait for the
+        // validity test on the first two)
+        const float4 h0 = __ldg(&H0[q]), h1 = __ldg(&H1[q]), h2 = __ldg(&H2[q]);
         if (!(h0.w + h1.w > 0.f)) continue;
         float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
-        float4 h2 = __ldg(&H2[q]);
         if (NEAR) {
             nh.a = f4fma(w, h0, nh.a);
             nh.bn += w * h2.x;
@@ -85,24 +86,27 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AS a
     const int W2 = cam.W2, H2 = cam.H2;
     if (i >= W2 || j >= H2) return;
     const size_t N = (size_t)W2 * H2, q = (size_t)j * W2 + i;
-    if (__ldg(&nrays[q]) <= 0) {
+    // the pixel's own planes are requested before the branch on its ray count, so the
+    // loads overlap
+    const int nr = __ldg(&nrays[q]);
+    const float zq = __ldg(&z_h[q]);
+    float4 rA = __ldg(&rt[q]), rB = __ldg(&rt[N + q]), rC = __ldg(&rt[2 * N + q]), rD = __ldg(&rt[3 * N + q]);
+    if (nr <= 0) {
         float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         hout[q] = zero; hout[N + q] = zero; hout[2 * N + q] = zero;
         st_img(crt, q, zero, p.f16);
         ct[q] = 0.f; var[q] = 0.f;
         return;
     }
-    float4 rA = __ldg(&rt[q]), rB = __ldg(&rt[N + q]), rC = __ldg(&rt[2 * N + q]);
     float h = rA.w, g = 1.f - h;
     float L = lum709(rA.x + rB.x, rA.y + rB.y, rA.z + rB.z);
     float3 dp = pixel_dir(cam, 2.f * i + 1.f, 2.f * j + 1.f);
     const float3 dO = cam.O - cam.pO;
     // near field: the G-buffer surface, relative to the previous lens centre
-    float3 relN = dO + (__ldg(&z_h[q]) / dot(dp, cam.F)) * dp;
+    float3 relN = dO + (zq / dot(dp, cam.F)) * dp;
     float3 Xf;
     if (rC.z > 0.f) {
-        float4 d = __ldg(&rt[3 * N + q]);
-        Xf = make_float3(d.x, d.y, d.z);
+        Xf = make_float3(rD.x, rD.y, rD.z);
     } else {
         float3 acc = make_float3(0.f, 0.f, 0.f);
         int cnt = 0;
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AS a
                     cnt++;
                 }
             }
-        Xf = cnt ? (1.f / (float)cnt) * acc : cam.O + (__ldg(&z_h[q]) / dot(dp, cam.F)) * dp;
+        Xf = cnt ? (1.f / (float)cnt) * acc : cam.O + (zq / dot(dp, cam.F)) * dp;
     }
     NearH nh, ndummy;
     FarH fh, fdummy;
