@@ -36,17 +36,32 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
     __shared__ float2 m0b[8][32];
     const int bx = i - (int)threadIdx.x, by = j - (int)threadIdx.y;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int e = tid; e < 12 * 36; e += 256) {
-        const int ty = e / 36, tx = e - 36 * ty;
-        const int x = min(max(bx + tx - 2, 0), W2 - 1), y = min(max(by + ty - 2, 0), H2 - 1);
-        t_var[ty][tx] = __ldg(&var[(size_t)y * W2 + x]);
-    }
-    for (int e = tid; e < 10 * 34; e += 256) {
-        const int ty = e / 34, tx = e - 34 * ty;
-        const int x = min(max(bx + tx - 1, 0), W2 - 1), y = min(max(by + ty - 1, 0), H2 - 1);
-        const size_t qn = (size_t)y * W2 + x;
-        t_crt[ty][tx] = ld_img(crt, qn, hs);
-        t_n[ty][tx] = __ldg(&nrays[qn]);
+    // the tiles: each thread's (at most two) elements of each are requested before any is
+    // stored, so the loads overlap
+    {
+        float v[2];
+        float4 c[2];
+        int nn[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int e = tid + 256 * r;
+            const int ev = min(e, 12 * 36 - 1), ec = min(e, 10 * 34 - 1);
+            const int vy = ev / 36, vx = ev - 36 * vy;
+            v[r] = __ldg(&var[(size_t)min(max(by + vy - 2, 0), H2 - 1) * W2 + min(max(bx + vx - 2, 0), W2 - 1)]);
+            const int cy2 = ec / 34, cx2 = ec - 34 * cy2;
+            const size_t qn = (size_t)min(max(by + cy2 - 1, 0), H2 - 1) * W2 + min(max(bx + cx2 - 1, 0), W2 - 1);
+            c[r] = ld_img(crt, qn, hs);
+            nn[r] = __ldg(&nrays[qn]);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int e = tid + 256 * r;
+            if (e < 12 * 36) t_var[e / 36][e % 36] = v[r];
+            if (e < 10 * 34) {
+                t_crt[e / 34][e % 34] = c[r];
+                t_n[e / 34][e % 34] = nn[r];
+            }
+        }
     }
     __syncthreads();
     const int cx = (int)threadIdx.x, cy = (int)threadIdx.y;
