@@ -932,3 +932,186 @@ def test_ring_taps_lie_on_the_aperture_shape(n):
             assert norm == pytest.approx(1.0, abs=1e-12)
             t += 1
     assert t == 81
+
+
+# ---------------------------------------------------------------------------
+# post-process filter values (Section 3.1.1-3.1.2): consequences of the weights that the
+# uniform-image fixed point does not see
+# ---------------------------------------------------------------------------
+
+def _pp_params(**kw):
+    return oracle.params(dict(default_params(), **kw))
+
+
+def _main_filter(pre, z, R):
+    """The oracle's A4 on hand-made inputs: pre (H2, W2, 4) = (rgb, rho), z (H2, W2),
+    every tile's dilated radius R."""
+    H2, W2 = z.shape
+    T = 8
+    TH, TW = -(-H2 // T), -(-W2 // T)
+    dil = np.zeros((TH, TW, 2))
+    dil[..., 0] = dil[..., 1] = R
+    pre = np.ascontiguousarray(pre, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    out = np.zeros((H2, W2, 4))
+    p = _pp_params()
+    oracle.lib().or_main_filter(C.byref(p), W2, H2, oracle._p(pre), oracle._p(z), oracle._p(dil), oracle._p(out))
+    return out
+
+
+def _prefilter(pp_in, R):
+    H2, W2 = pp_in.shape[:2]
+    TH, TW = -(-H2 // 8), -(-W2 // 8)
+    dil = np.zeros((TH, TW, 2))
+    dil[..., 0] = dil[..., 1] = R
+    pp_in = np.ascontiguousarray(pp_in, dtype=np.float64)
+    out = np.zeros((H2, W2, 4))
+    p = _pp_params()
+    oracle.lib().or_prefilter(C.byref(p), W2, H2, oracle._p(pp_in), oracle._p(dil), oracle._p(out))
+    return out
+
+
+def _ring_taps():
+    """The 81-tap layout as the paper describes it (Section 3.1.2): the centre and rings
+    k = 1..4 of 8k taps at radius k/4 of the kernel radius, evenly spaced in angle."""
+    taps = [(0.0, 0.0, 0.0)]
+    for k in range(1, 5):
+        for m in range(8 * k):
+            th = 2 * math.pi * m / (8 * k)
+            taps.append((math.cos(th), math.sin(th), k / 4.0))
+    return taps
+
+
+A_COL, B_COL = np.array([0.9, 0.2, 0.1]), np.array([0.1, 0.3, 0.8])
+
+
+def _two_regions(W2, H2, xb, left, right):
+    """Columns x <= xb take `left` = (colour, rho, z), the others `right`."""
+    pre = np.zeros((H2, W2, 4))
+    z = np.zeros((H2, W2))
+    for (sl, (col, rho, zz)) in ((np.s_[:, :xb + 1], left), (np.s_[:, xb + 1:], right)):
+        pre[sl + (np.s_[:3],)] = col
+        pre[sl + (3,)] = rho
+        z[sl] = zz
+    return pre, z
+
+
+def test_main_filter_in_focus_pixel_in_front_stays_sharp():
+    """A pixel in focus (rho 0) nearer than a blurred region beside it takes nothing of
+    that region: every tap that lands there is background for it, and a background tap
+    counts only within min(its CoC, the centre's CoC) = 0 (+ half the ramp) of the centre.
+    A foreground/background split that used the tap's own CoC for the background would
+    blur it."""
+    W2, H2, R = 64, 48, 12.0
+    pre, z = _two_regions(W2, H2, 31, (A_COL, 0.0, 2.0), (B_COL, 12.0, 10.0))
+    out = _main_filter(pre, z, R)
+    for x in range(20, 32):
+        assert np.abs(out[24, x, :3] - A_COL).max() < 1e-12, x
+
+
+def test_main_filter_foreground_bleeds_within_its_radius():
+    """A blurred foreground (rho -12, 1 m) beside an in-focus background (rho 0, 10 m):
+    background pixels within the foreground's reach take some of its colour (the
+    foreground scatters over the background, Section 3.1.2), the share falls with the
+    distance, and from the kernel radius on none is left.  A split that limited the
+    foreground's coverage by the centre's CoC would show no bleeding at all."""
+    W2, H2, R = 64, 48, 12.0
+    pre, z = _two_regions(W2, H2, 23, (A_COL, -12.0, 1.0), (B_COL, 0.0, 10.0))
+    out = _main_filter(pre, z, R)
+    share = lambda x: float((out[24, x, 0] - B_COL[0]) / (A_COL[0] - B_COL[0]))
+    shares = [share(x) for x in range(24, 24 + int(R))]
+    assert shares[0] > 0.05 and min(shares) > 0.0, shares
+    # the ring taps are discrete, so the share falls in steps: taken two columns at a
+    # time it decreases strictly
+    pairs = [0.5 * (a + b) for a, b in zip(shares[0::2], shares[1::2])]
+    assert all(a > b for a, b in zip(pairs, pairs[1:])), shares
+    for x in range(24 + int(R), W2):
+        assert np.abs(out[24, x, :3] - B_COL).max() < 1e-12, x
+
+
+def test_main_filter_sample_alpha_is_inverse_area():
+    """sampleAlpha (Section 3.1.2, 'pixel area over blur-disk area'): with the same taps
+    landing on a fully covering foreground, doubling the foreground's CoC quarters its
+    weight against the in-focus centre.  From out = (w0 B + g w0 A) / (w0 + g w0) the ratio
+    g = (out - B) / (A - out) of the two runs must be (26 / 13)^2 = 4; the boundary column
+    is chosen so that no tap's bilinear footprint straddles it."""
+    W2, H2, R = 80, 48, 12.0
+    x0, y0 = 40, 24
+    xs = [x0 + d * R * ux for (ux, uy, d) in _ring_taps()]
+    # the last foreground column c: no tap with floor(x) == c (no straddling footprint),
+    # at least a few taps on the foreground side
+    c = next(c for c in range(x0 - 2, x0 - int(R), -1)
+             if all(math.floor(x) != c for x in xs) and sum(x < c + 1 for x in xs) >= 4)
+    gs = []
+    for rho in (-13.0, -26.0):
+        pre, z = _two_regions(W2, H2, c, (A_COL, rho, 1.0), (B_COL, 0.0, 10.0))
+        out = _main_filter(pre, z, R)
+        g = (out[y0, x0, :3] - B_COL) / (A_COL - out[y0, x0, :3])
+        assert np.allclose(g, g[0], rtol=1e-9)
+        gs.append(g[0])
+    assert abs(gs[0] / gs[1] - 4.0) < 1e-9, gs
+
+
+def test_filters_with_uniform_coc_are_plain_means_of_their_taps():
+    """With one CoC everywhere (covering every tap) and one depth, the main filter's taps
+    all weigh the same and the prefilter's CoC-similarity weight is 1: each is the plain
+    mean of its bilinear samples (scipy's map_coordinates, order 1, at the tap positions
+    the paper describes; prefilter: the centre and 8 taps at angles k pi/4, radius
+    max(R/8, sqrt(2)/2))."""
+    from scipy.ndimage import map_coordinates
+    rng = np.random.default_rng(3)
+    W2, H2, R, rho = 72, 56, 9.0, 10.0
+    col = rng.uniform(0.1, 0.9, (H2, W2, 3))
+    pre = np.concatenate([col, np.full((H2, W2, 1), rho)], -1)
+    z = np.full((H2, W2), 5.0)
+    out = _main_filter(pre, z, R)
+    taps = _ring_taps()
+    for (j, i) in [(28, 36), (20, 25), (40, 50)]:
+        ys = np.array([j + d * R * uy for (ux, uy, d) in taps])
+        xs = np.array([i + d * R * ux for (ux, uy, d) in taps])
+        want = [map_coordinates(col[..., ch], [ys, xs], order=1, mode="nearest").mean() for ch in range(3)]
+        assert np.abs(out[j, i, :3] - want).max() < 1e-12, (j, i)
+    pre_out = _prefilter(pre, R)
+    rp = max(R / 8.0, math.sqrt(0.5))
+    for (j, i) in [(28, 36), (3, 4)]:
+        ys = np.array([j] + [j + rp * math.sin(k * math.pi / 4) for k in range(8)])
+        xs = np.array([i] + [i + rp * math.cos(k * math.pi / 4) for k in range(8)])
+        want = [map_coordinates(col[..., ch], [ys, xs], order=1, mode="nearest").mean() for ch in range(3)]
+        assert np.abs(pre_out[j, i, :3] - want).max() < 1e-12, (j, i)
+
+
+def test_prefilter_excludes_taps_of_a_different_coc():
+    """The prefilter's CoC-similarity weight: neighbours whose CoC differs from the
+    centre's by at least max(1, |rho_0|) take no part (the centre keeps its colour), and
+    a difference of half that takes half a weight."""
+    W2, H2, R = 32, 32, 16.0
+    col = np.zeros((H2, W2, 4))
+    col[..., :3] = B_COL
+    col[..., 3] = 12.0
+    j, i = 16, 16
+    col[j, i, :3] = A_COL
+    col[j, i, 3] = 4.0                      # |12 - 4| = 8 >= max(1, 4)
+    out = _prefilter(col, R)
+    assert np.abs(out[j, i, :3] - A_COL).max() < 1e-12
+    # neighbours at rho 6 (difference 2 = half of max(1, 4)): every tap reads rho 6 and
+    # B's colour (the taps at radius 2 hpx land on the neighbours), weight 1/2 each
+    col[..., 3] = 6.0
+    col[j, i, 3] = 4.0
+    out = _prefilter(col, R)
+    want = (A_COL + 8 * 0.5 * B_COL) / (1 + 8 * 0.5)
+    assert np.abs(out[j, i, :3] - want).max() < 1e-12
+
+
+def test_prefilter_similarity_scale_has_a_floor_of_one_pixel():
+    """The CoC difference is measured against max(1, |rho_0|): for a nearly sharp centre
+    (rho_0 = 0.5) a neighbour 0.5 away keeps half a weight (1 - 0.5 / 1), not none."""
+    W2, H2, R = 32, 32, 16.0
+    col = np.zeros((H2, W2, 4))
+    col[..., :3] = B_COL
+    col[..., 3] = 1.0
+    j, i = 16, 16
+    col[j, i, :3] = A_COL
+    col[j, i, 3] = 0.5
+    out = _prefilter(col, R)
+    want = (A_COL + 8 * 0.5 * B_COL) / (1 + 8 * 0.5)
+    assert np.abs(out[j, i, :3] - want).max() < 1e-12
