@@ -94,6 +94,24 @@ __device__ __forceinline__ void cx4(float4 &a, float4 &b) {
     b = hi;
 }
 
+__device__ __forceinline__ void cx1(float &a, float &b) {
+    const float lo = fminf(a, b), hi = fmaxf(a, b);
+    a = lo;
+    b = hi;
+}
+
+// median of 9 scalars by the same 19-exchange network as median9
+__device__ __forceinline__ float median9s(float *p) {
+    cx1(p[1], p[2]); cx1(p[4], p[5]); cx1(p[7], p[8]);
+    cx1(p[0], p[1]); cx1(p[3], p[4]); cx1(p[6], p[7]);
+    cx1(p[1], p[2]); cx1(p[4], p[5]); cx1(p[7], p[8]);
+    cx1(p[0], p[3]); cx1(p[5], p[8]); cx1(p[4], p[7]);
+    cx1(p[3], p[6]); cx1(p[1], p[4]); cx1(p[2], p[5]);
+    cx1(p[4], p[7]); cx1(p[4], p[2]); cx1(p[6], p[4]);
+    cx1(p[4], p[2]);
+    return p[4];
+}
+
 // per-channel median of 9 by the 19-exchange min/max network (Paeth; the GPU median
 // of Smith 1996 cited in Section 3.1.3)
 __device__ __forceinline__ float4 median9(float4 *p) {

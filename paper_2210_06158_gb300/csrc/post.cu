@@ -244,9 +244,12 @@ __global__ void __launch_bounds__(512) k_main_filter_tiled(const __grid_constant
     st_img(out, q, make_float4(ax * r, ay * r, az * r, bright * r), p.f16);
 }
 
-// A5: per-channel 3x3 median (clamp-to-edge)
+// A5: per-channel 3x3 median (clamp-to-edge).  The block's 34x10 neighbourhood is
+// loaded once, coalesced, into one shared-memory plane per channel; each thread then
+// selects the median of its 9 values channel by channel (an exact selection, so the
+// order of the channels changes nothing).
 template <class AS>
-__global__ void k_median_pp(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(256) k_median_pp(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_HPX, i, j);
@@ -254,19 +257,41 @@ __global__ void k_median_pp(const __grid_constant__ AS as_) {
     const float4 *__restrict__ src = S.main_;
     float4 *dst = S.pp_med;
     const bool h = S.p.f16;
-    if (i >= W2 || j >= H2) return;
-    float4 v[9];
-    int n = 0;
+    __shared__ float t[4][10][34];
+    const int bx = i - (int)threadIdx.x, by = j - (int)threadIdx.y;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    {
+        float4 v[2];
 #pragma unroll
-    for (int dy = -1; dy <= 1; dy++) {
-        int y = min(max(j + dy, 0), H2 - 1);
+        for (int r = 0; r < 2; r++) {
+            const int e = min(tid + 256 * r, 10 * 34 - 1);
+            const int ty = e / 34, tx = e - 34 * ty;
+            const int x = min(max(bx + tx - 1, 0), W2 - 1), y = min(max(by + ty - 1, 0), H2 - 1);
+            v[r] = ld_img(src, (size_t)y * W2 + x, h);
+        }
 #pragma unroll
-        for (int dx = -1; dx <= 1; dx++) {
-            int x = min(max(i + dx, 0), W2 - 1);
-            v[n++] = ld_img(src, (size_t)y * W2 + x, h);
+        for (int r = 0; r < 2; r++) {
+            const int e = tid + 256 * r;
+            if (e < 10 * 34) {
+                const int ty = e / 34, tx = e - 34 * ty;
+                t[0][ty][tx] = v[r].x; t[1][ty][tx] = v[r].y; t[2][ty][tx] = v[r].z; t[3][ty][tx] = v[r].w;
+            }
         }
     }
-    st_img(dst, (size_t)j * W2 + i, median9(v), h);
+    __syncthreads();
+    if (i >= W2 || j >= H2) return;
+    const int cx = (int)threadIdx.x, cy = (int)threadIdx.y;
+    float m[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        float a[9];
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+            for (int dx = 0; dx < 3; dx++) a[3 * dy + dx] = t[c][cy + dy][cx + dx];
+        m[c] = median9s(a);
+    }
+    st_img(dst, (size_t)j * W2 + i, make_float4(m[0], m[1], m[2], m[3]), h);
 }
 
 }  // namespace
