@@ -4,12 +4,12 @@
 // LBVH after Karras, "Maximizing Parallelism in the Construction of BVHs, Octrees,
 // and k-d Trees" (HPG 2012): 63-bit Morton codes of triangle centroids (21 bits per
 // axis: scenes with a ground plane hundreds of metres wide still resolve centimetre
-// detail), a radix sort, one thread per internal node to find its key range and
+// detail), a stable LSD radix sort written here (8-bit digits, warp-matched ranks), one
+// thread per internal node to find its key range and
 // split (ties between equal codes broken by the sorted index), then a
 // bottom-up box refit in which the second thread to reach a node merges its two
 // children (atomic arrival counter, no waiting).  Nodes hold both child boxes so that
 // traversal fetches one node per step.
-#include <cub/cub.cuh>
 
 #include "dof_internal.cuh"
 
@@ -402,6 +402,168 @@ __global__ void k_collapse(const BvhNode *nodes, int n_bin, const int2 *fin, int
     out4[w4] = o;
 }
 
+// ---------------------------------------------------------------------------
+// device exclusive scan (int) and stable LSD radix sort (64-bit keys, 32-bit values)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+// exclusive prefix of v over the 256 threads of the block; *total = the block's sum
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    int wpre = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < kScanThreads / 32; k++) {
+        const int s = warp_sums[k];
+        if (k < w) wpre += s;
+        tot += s;
+    }
+    __syncthreads();
+    total = tot;
+    return wpre + incl - v;
+}
+
+// tile-local exclusive prefix of in[0..n) into out, and each tile's sum into sums
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int *in, int *out, int n, int *sums) {
+    __shared__ int ws[kScanThreads / 32];
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int tot;
+    int pre = block_exclusive_scan(s, ws, tot);
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        if (base + k < n) out[base + k] = pre;
+        pre += v[k];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// exclusive prefix of sums[0..nb) in place, one block (each thread a consecutive chunk)
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int *sums, int nb) {
+    __shared__ int ws[kScanThreads / 32];
+    const int chunk = (nb + kScanThreads - 1) / kScanThreads;
+    const int b0 = threadIdx.x * chunk;
+    int s = 0;
+    for (int k = 0; k < chunk; k++)
+        if (b0 + k < nb) s += sums[b0 + k];
+    int tot;
+    int pre = block_exclusive_scan(s, ws, tot);
+    for (int k = 0; k < chunk; k++)
+        if (b0 + k < nb) {
+            const int v = sums[b0 + k];
+            sums[b0 + k] = pre;
+            pre += v;
+        }
+}
+
+__global__ void k_scan_add(int *out, int n, const int *sums) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / kScanTile];
+}
+
+// out[i] = in[0] + ... + in[i-1]; sums holds ceil(n / 2048) ints
+void device_exclusive_scan(const int *in, int *out, int n, int *sums, cudaStream_t st) {
+    if (n <= 0) return;
+    const int nb = (n + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<nb, kScanThreads, 0, st>>>(in, out, n, sums);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb);
+    k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, n, sums);
+}
+
+constexpr int kSortThreads = 256, kSortRounds = 8, kSortTile = kSortThreads * kSortRounds, kSortBins = 256;
+
+// per block of 2048 keys: the count of each 8-bit digit at `shift`, digit-major
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const unsigned long long *keys, int n, int shift, int *hist,
+                                                          int nblocks) {
+    __shared__ int h[kSortBins];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; r++) {
+        const long long idx = (long long)blockIdx.x * kSortTile + r * kSortThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(int)((keys[idx] >> shift) & 255ull)], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of a block's 2048 keys by their digit: offs[d * nblocks + b] is where
+// digit d of block b starts (exclusive scan of the histograms).  The block takes its keys
+// in 8 rounds of 256 in index order; within a round a key's place among equal digits is
+// its rank in its warp (lanes with the same digit, __match_any_sync) plus the counts of
+// the lower warps, and the digit's running offset carries across rounds.
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const unsigned long long *keys, const uint32_t *vals,
+                                                             unsigned long long *keys_out, uint32_t *vals_out, int n,
+                                                             int shift, const int *offs, int nblocks) {
+    __shared__ int run[kSortBins];
+    __shared__ int wcount[kSortThreads / 32][kSortBins];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    run[tid] = offs[tid * nblocks + blockIdx.x];
+    for (int r = 0; r < kSortRounds; r++) {
+        const long long idx = (long long)blockIdx.x * kSortTile + r * kSortThreads + tid;
+        const bool valid = idx < n;
+        const unsigned long long key = valid ? keys[idx] : 0ull;
+        const uint32_t val = valid ? vals[idx] : 0u;
+        const int d = valid ? (int)((key >> shift) & 255ull) : kSortBins;
+#pragma unroll
+        for (int k = 0; k < kSortBins / 32; k++) wcount[w][lane + 32 * k] = 0;
+        __syncwarp();
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        if (valid && lane == __ffs(peers) - 1) wcount[w][d] = __popc(peers);
+        __syncthreads();
+        // per digit (thread tid = digit tid): exclusive prefix of the warps' counts
+        int acc = 0;
+#pragma unroll
+        for (int k = 0; k < kSortThreads / 32; k++) {
+            const int c = wcount[k][tid];
+            wcount[k][tid] = acc;
+            acc += c;
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = run[d] + wcount[w][d] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+        run[tid] += acc;
+        __syncthreads();
+    }
+}
+
+// Stable sort of (keys, vals) by the whole 64-bit key, 8 passes of 8 bits; the result
+// ends in (keys, vals), (keys2, vals2) and hist are scratch (hist: 256 * ceil(n / 2048)
+// ints, sums: ceil(256 * ceil(n / 2048) / 2048) ints).
+void device_radix_sort_pairs(unsigned long long *keys, uint32_t *vals, unsigned long long *keys2, uint32_t *vals2,
+                             int n, int *hist, int *sums, cudaStream_t st) {
+    if (n <= 1) return;
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    unsigned long long *ki = keys, *ko = keys2;
+    uint32_t *vi = vals, *vo = vals2;
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_rs_hist<<<nb, kSortThreads, 0, st>>>(ki, n, shift, hist, nb);
+        device_exclusive_scan(hist, hist, kSortBins * nb, sums, st);
+        k_rs_scatter<<<nb, kSortThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, nb);
+        unsigned long long *tk = ki; ki = ko; ko = tk;
+        uint32_t *tv = vi; vi = vo; vo = tv;
+    }
+    // 8 passes: the sorted data are back in (keys, vals)
+}
+
 }  // namespace
 
 static inline unsigned blocks_for(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -424,8 +586,8 @@ static int ploc_build(DofScene *s, int m, int radius, int *pnode, int *pleaf, in
     ck(cudaMalloc(&keep, sizeof(int) * m), "ploc");
     ck(cudaMalloc(&pos, sizeof(int) * m), "ploc");
     ck(cudaMalloc(&cnt, sizeof(int)), "ploc");
-    ck(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, keep, pos, m, st), "ploc scan size");
-    ck(cudaMalloc(&tmp, tmp_bytes ? tmp_bytes : 16), "ploc scan temp");
+    tmp_bytes = sizeof(int) * (size_t)((m + kScanTile - 1) / kScanTile + 1);
+    ck(cudaMalloc(&tmp, tmp_bytes), "ploc scan temp");
     if (rc == DOF_OK) {
         ck(cudaMemsetAsync(cnt, 0, sizeof(int), st), "ploc");
         k_ploc_init<<<blocks_for(m, B), B, 0, st>>>(s->tris, m, cid[0], clo[0], chi[0]);
@@ -435,7 +597,7 @@ static int ploc_build(DofScene *s, int m, int radius, int *pnode, int *pleaf, in
             k_ploc_nn<<<blocks_for(count, B), B, 0, st>>>(count, radius, clo[cur], chi[cur], nn);
             k_ploc_merge<<<blocks_for(count, B), B, 0, st>>>(count, cid[cur], clo[cur], chi[cur], nn, keep, cnt,
                                                             s->nodes, pnode, pleaf, m - 1, ibuf + 6);
-            ck(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, keep, pos, count, st), "ploc scan");
+            device_exclusive_scan(keep, pos, count, static_cast<int *>(tmp), st);
             k_ploc_scatter<<<blocks_for(count, B), B, 0, st>>>(count, keep, pos, cid[cur], clo[cur], chi[cur],
                                                               cid[cur ^ 1], clo[cur ^ 1], chi[cur ^ 1]);
             int last[2];
@@ -556,11 +718,19 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
         n_small = n - n_big;
         k_morton<<<blocks_for(n, B), B, 0, st>>>(cen, (uint32_t)n, separate ? ibuf + 9 : ibuf, ibuf, separate, keys,
                                                  vals);
-        ck(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, vals, vals2, n, 0, 64, st), "sort size");
-        ck(cudaMalloc(&tmp, tmp_bytes ? tmp_bytes : 16), "sort temp");
-        if (rc != DOF_OK) goto done;
-        ck(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys2, vals, vals2, n, 0, 64, st), "sort");
-        k_sorted_tris<<<blocks_for(n, B), B, 0, st>>>(d_xyz, d_idx, d_mat, (uint32_t)n, n_verts, vals2, s->tris);
+        {
+            // scratch of the sort: the digit histograms and the scan's tile sums
+            const size_t nbk = (size_t)(n + kSortTile - 1) / kSortTile;
+            const size_t nh = (size_t)kSortBins * nbk, ns = (nh + kScanTile - 1) / kScanTile + 1;
+            tmp_bytes = sizeof(int) * (nh + ns);
+            ck(cudaMalloc(&tmp, tmp_bytes), "sort temp");
+            if (rc != DOF_OK) goto done;
+            int *hist = static_cast<int *>(tmp);
+            device_radix_sort_pairs(keys, vals, keys2, vals2, n, hist, hist + nh, st);
+            ck(cudaGetLastError(), "sort");
+        }
+        // sorted (key, triangle) pairs are in (keys, vals)
+        k_sorted_tris<<<blocks_for(n, B), B, 0, st>>>(d_xyz, d_idx, d_mat, (uint32_t)n, n_verts, vals, s->tris);
         const int m = n_small;
         int root = m >= 2 ? 0 : ~0;
         if (m >= 2) {
@@ -571,7 +741,7 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
                 if (rc == DOF_OK) rc = ploc_build(s, m, ploc_radius, pnode, pleaf, ibuf, &root, st);
                 if (rc != DOF_OK) goto done;
             } else {
-                k_karras<<<blocks_for(m - 1, B), B, 0, st>>>(keys2, m, child, pnode, pleaf, ibuf + 6);
+                k_karras<<<blocks_for(m - 1, B), B, 0, st>>>(keys, m, child, pnode, pleaf, ibuf + 6);
                 k_refit<<<blocks_for(m, B), B, 0, st>>>(s->tris, m, child, pnode, pleaf, blo, bhi, arr, s->nodes,
                                                         ibuf + 6);
             }
