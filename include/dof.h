@@ -188,6 +188,11 @@ size_t dof_ctx_bytes_in_use(const DofCtx *ctx);
  * smallest compiled capacity (32, 64, 96) that holds both this and what the batch's trees
  * can need, so a small value never overflows.  Same hits either way */
 #define DOF_OPT_TRACE_STACK         11
+/* how the binary tree is traversed: 0 (default) = one ray per lane, persistent threads with
+ * dynamic fetch; 1 = the 32 rays of a warp as one packet (one node sequence per warp, each lane
+ * testing with its own ray and best hit); packets always traverse the binary tree, whatever
+ * DOF_OPT_BVH_WIDTH says.  Same hits either way */
+#define DOF_OPT_TRACE_PACKETS       12
 int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value);
 
 /* Fill `p` with the defaults above (1 spp fixed mode, 16 px radius clamp). */

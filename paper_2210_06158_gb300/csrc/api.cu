@@ -216,6 +216,7 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->trace_refill_idle = 16;
     c->trace_steps = 64;
     c->ray_order_grid = 4;
+    c->trace_packets = 0;
     c->stack_depth = kTraversalStack;
     c->gather_w = 32;
     c->gather_h = 8;
@@ -297,6 +298,10 @@ extern "C" int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value) {
         case DOF_OPT_RAY_ORDER_GRID:
             if (value < 1 || value > 16) return dof_set_error(DOF_ERR_INVALID_ARG, "ray order grid must be 1..16");
             ctx->ray_order_grid = (int)value;
+            return DOF_OK;
+        case DOF_OPT_TRACE_PACKETS:
+            if (value != 0 && value != 1) return dof_set_error(DOF_ERR_INVALID_ARG, "trace packets must be 0 or 1");
+            ctx->trace_packets = (int)value;
             return DOF_OK;
         case DOF_OPT_GATHER_BLOCK:
         case DOF_OPT_RECON_BLOCK: {
@@ -435,8 +440,9 @@ static SceneDev scene_dev(const DofScene *s) {
     d.n_tris = (int)s->n_tree;
     d.n_large = (int)s->n_large;
     d.root = s->root;
-    // the 4-wide tree, when its traversal stack bound (3 per level) fits
-    bool wide = s->nodes4 && s->ctx->bvh_width == 4 && 3 * s->depth4 + 3 <= kTraversalStack;
+    // the 4-wide tree, when its traversal stack bound (3 per level) fits; warp packets
+    // traverse the binary tree
+    bool wide = s->nodes4 && s->ctx->bvh_width == 4 && !s->ctx->trace_packets && 3 * s->depth4 + 3 <= kTraversalStack;
     d.nodes4 = wide ? s->nodes4 : nullptr;
     d.root4 = s->root4;
     d.n_nodes4 = s->n_nodes4;
@@ -755,6 +761,7 @@ static int build_batch(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, BatchAr
     A.refill_idle = ctx->trace_refill_idle;
     A.steps_per_round = ctx->trace_steps;
     A.lens_grid = ctx->ray_order_grid;
+    A.packets = ctx->trace_packets;
     A.stack_depth = ctx->stack_depth;
     return DOF_OK;
 }
@@ -841,7 +848,7 @@ struct DofGraph {
     DofHistory *hist[kMaxBatch];
     int start[SH_COUNT][kMaxBatch + 1];
     bool adaptive, wide;
-    int trace_blocks, refill_idle, steps_per_round, lens_grid, stack_depth;
+    int trace_blocks, refill_idle, steps_per_round, lens_grid, stack_depth, packets;
     int gather_w, gather_h, main_form, recon_w, recon_h;
     int main_tile;                // the main filter's shared-memory bytes (0: through L1)
     long long kernels;            // kernel launches in one replay
@@ -889,6 +896,7 @@ extern "C" int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n
     g->refill_idle = A.refill_idle;
     g->steps_per_round = A.steps_per_round;
     g->lens_grid = A.lens_grid;
+    g->packets = A.packets;
     g->stack_depth = A.stack_depth;
     g->gather_w = A.gather_w;
     g->gather_h = A.gather_h;
@@ -947,7 +955,7 @@ extern "C" int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n
     if (memcmp(A.start, g->start, sizeof(A.start)) != 0 || adaptive != g->adaptive || all_wide(A) != g->wide ||
         ctx->sm_count * ctx->trace_blocks_per_sm != g->trace_blocks || main_filter_tile_bytes(A) != g->main_tile ||
         A.gather_w != g->gather_w || A.gather_h != g->gather_h || A.main_form != g->main_form ||
-        A.recon_w != g->recon_w || A.recon_h != g->recon_h)
+        A.recon_w != g->recon_w || A.recon_h != g->recon_h || A.packets != g->packets)
         return dof_set_error(DOF_ERR_MISMATCH, "dof_graph_launch: launch shapes differ from the captured step");
     // the kernels' scheduling knobs come from the staged copy; keep the captured ones
     A.refill_idle = g->refill_idle;

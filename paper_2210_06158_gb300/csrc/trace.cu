@@ -667,6 +667,141 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
     }
 }
 
+// Packet tracer over the binary tree: the 32 rays a warp takes traverse it together,
+// one node sequence for the warp held in a warp-uniform stack.  A child is entered
+// when the ray of any lane enters its box, and the two children go in the order that
+// most of the lanes entering both prefer.  Each lane tests boxes and triangles with
+// its own ray and its own best hit (inclusive cull), so every ray ends with the closest
+// hit that the per-ray traversal finds.  Rays grouped by lens cell leave one small
+// patch of the aperture for nearby pixels, a packet close to a pinhole frustum: the
+// warp then steps with all its lanes and one broadcast load per node, at the price of
+// the nodes that only some of its rays need.  Lanes of a warp that straddles two
+// sessions of a batch trace one session's packet after the other.
+template <int kCap, class AS>
+__global__ void __launch_bounds__(128, 7) k_trace_packets(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
+    const unsigned lane = threadIdx.x & 31;
+    __shared__ uint32_t pre[kMaxBatch];
+    if (threadIdx.x < 32) {
+        uint32_t c = lane < (unsigned)A.ns ? *((volatile uint32_t *)&A.s[lane].counters[1]) : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, c, o);
+            if ((int)lane >= o) c += v;
+        }
+        pre[lane] = c;
+    }
+    __syncthreads();
+    const uint32_t total = pre[A.ns - 1];
+    uint32_t n_visit = 0, n_tests = 0;
+    int stack[kCap];
+    while (true) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(A.cursor, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= total) break;
+        const uint32_t g = base + lane;
+        bool pending = false;           // the lane holds a ray not yet traced
+        int si = 0;
+        uint32_t r = 0;
+        Ray ray = make_ray(make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 1.f));
+        HitRec h{INFINITY, -1, -1};
+        if (g < total) {
+            int lo = 0, hi = A.ns - 1;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (pre[mid] > g) hi = mid;
+                else lo = mid + 1;
+            }
+            si = lo;
+            const SessDesc &S = A.s[si];
+            const uint32_t wq = __ldg(&S.ray_pix[g - (si > 0 ? pre[si - 1] : 0u)]);
+            const uint32_t q = wq >> 6;
+            const int sm = (int)(wq & 63u);
+            if (q >= (uint32_t)S.N || sm >= S.max_rays) {
+                atomicOr(&A.s[si].counters[3], 2u);
+            } else {
+                r = __ldg(&S.first_ray[q]) + (uint32_t)sm;
+                float3 L, dir;
+                lens_ray(S.cam, S.p, q, sm, L, dir);
+                S.ray_a[r] = make_float4(L.x, L.y, L.z, dir.x);
+                S.ray_b[r] = make_float2(dir.y, dir.z);
+                ray = make_ray(L, dir);
+                const float4 *__restrict__ tris = S.sc.tris;
+                const int n_tree = S.sc.n_tris;
+                for (int k = n_tree; k < n_tree + S.sc.n_large; k++) {
+                    n_tests++;
+                    tri_update(ray, tris, k, h);
+                }
+                pending = true;
+            }
+        }
+        while (true) {
+            const unsigned pm = __ballot_sync(0xffffffffu, pending);
+            if (pm == 0) break;
+            const int lead = __shfl_sync(0xffffffffu, si, __ffs(pm) - 1);
+            const bool act = pending && si == lead;
+            const SessDesc &S = A.s[lead];
+            uint32_t *status = &A.s[lead].counters[3];
+            const int n_tree = S.sc.n_tris;
+            if (n_tree > 0) {
+                const BvhNode *__restrict__ nodes = S.sc.nodes;
+                const float4 *__restrict__ tris = S.sc.tris;
+                const int n_nodes = n_tree - 1;
+                const long long max_steps = 4ll * n_tree + 64;
+                int node = S.sc.root, sp = 0;
+                for (long long steps = 0;; steps++) {
+                    // warp-uniform guards: a reference outside the tree or more steps than
+                    // a valid tree takes end the packet with the status set
+                    if (steps > max_steps || node >= n_nodes || (node < 0 && ~node >= n_tree)) {
+                        if (lane == 0) atomicOr(status, 2u);
+                        break;
+                    }
+                    if (node >= 0) {
+                        const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
+                        const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+                        const int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
+                        float t0, t1;
+                        bool h0, h1;
+                        box_pair(ray, a, b, c, h.t, h0, t0, h1, t1);
+                        h0 = h0 && act;
+                        h1 = h1 && act;
+                        n_visit += act ? 1u : 0u;
+                        const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+                        if (m0 && m1) {
+                            const unsigned right_first = __ballot_sync(0xffffffffu, h0 && h1 && t1 < t0);
+                            const bool rf = 2 * __popc(right_first) > __popc(m0 & m1);
+                            if (sp < kCap) stack[sp++] = rf ? ref.x : ref.y;
+                            else if (lane == 0) atomicOr(status, 1u);
+                            node = rf ? ref.y : ref.x;
+                            continue;
+                        }
+                        if (m0) { node = ref.x; continue; }
+                        if (m1) { node = ref.y; continue; }
+                    } else if (act) {
+                        n_tests++;
+                        tri_update(ray, tris, ~node, h);
+                    }
+                    if (sp == 0) break;
+                    node = stack[--sp];
+                }
+            }
+            if (act) {
+                S.hits[r] = make_int2(h.k, __float_as_int(h.t));
+                pending = false;
+            }
+        }
+    }
+    unsigned long long a = n_visit, b = n_tests;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.s[0].counters[4]), a);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&A.s[0].counters[6]), b);
+    }
+}
+
 // Shading and the per-pixel near/far split of the masked pixel queue[e]: its rays, as
 // the tracer made and kept them, are shaded at their recorded hits and reduced in
 // sample order.
@@ -768,7 +903,11 @@ void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t s
     // what every session's tree can need
     int need = A.stack_depth;
     for (int i = 0; i < A.ns; i++) need = max(need, A.s[i].sc.stack_need);
-    if (wide) {
+    if (A.packets && !wide) {
+        if (need <= 32) k_trace_packets<32, AS><<<blocks, 128, 0, st>>>(as);
+        else if (need <= 64) k_trace_packets<64, AS><<<blocks, 128, 0, st>>>(as);
+        else k_trace_packets<kStack, AS><<<blocks, 128, 0, st>>>(as);
+    } else if (wide) {
         if (need <= 32) k_trace_rays<true, 32, AS><<<blocks, 128, 0, st>>>(as);
         else if (need <= 64) k_trace_rays<true, 64, AS><<<blocks, 128, 0, st>>>(as);
         else k_trace_rays<true, kStack, AS><<<blocks, 128, 0, st>>>(as);

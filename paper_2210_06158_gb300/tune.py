@@ -6,7 +6,7 @@ The knobs (the tree the rays traverse: binary or 4-wide; the order the tracer ta
 a block's rays in: grouped by lens cell on a g x g grid, or pixel by pixel; the
 traversal stack depth, which the launch raises to what the tree needs; 128-thread
 blocks per SM, idle lanes that trigger a refill, traversal steps between refill
-checks) change only
+checks; warp packets over the binary tree instead of one ray per lane) change only
 the speed of dof_frame, never its result (the closest hit does not depend on the
 tree's shape).
 `tune_trace` times a few frames of the caller's own session for each candidate
@@ -27,8 +27,10 @@ SPACE = {
     "blocks_per_sm": [4, 6, 8, 12, 16],
     "refill_idle": [4, 8, 12, 16, 24],
     "steps": [8, 16, 32, 64],
+    "packets": [0, 1],
 }
-DEFAULT = {"bvh_width": 4, "ray_grid": 4, "stack": 96, "blocks_per_sm": 8, "refill_idle": 16, "steps": 64}
+DEFAULT = {"bvh_width": 4, "ray_grid": 4, "stack": 96, "blocks_per_sm": 8, "refill_idle": 16, "steps": 64,
+           "packets": 0}
 
 
 def _time_frames(run_frame, frames, st):

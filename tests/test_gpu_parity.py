@@ -400,10 +400,11 @@ def test_checkpoint_resume_bit_identical():
 @pytest.mark.parametrize("name,W,H", [("c3", 384, 216), ("c2", 322, 182)])
 def test_scheduling_knobs_do_not_change_results(name, W, H):
     """The autotuned knobs change only speed: the tracer's work order (lens-cell grid 1
-    = pixel order, 2 .. 16), the gathers' block shapes and the main filter's form
-    (shared-memory halo tile or L1) give bit-identical hit ids, intermediates and
-    images over two frames of a moving camera (the c3 crop with its 64 px clamp takes
-    the halo tile only in the opt-in form)."""
+    = pixel order, 2 .. 16), its traversal stack, warp packets instead of one ray per
+    lane, the gathers' block shapes and the main filter's form (shared-memory halo tile
+    or L1) give bit-identical hit ids, intermediates and images over two frames of a
+    moving camera (the c3 crop with its 64 px clamp takes the halo tile only in the
+    opt-in form)."""
     from paper_2210_06158_gb300 import dof
     import torch
     dev = torch.device("cuda", 0)
@@ -418,12 +419,13 @@ def test_scheduling_knobs_do_not_change_results(name, W, H):
     sc = dof.Scene(ctx, w.scene)
     variants = [dict(ray_grid=1), dict(ray_grid=2), dict(ray_grid=4), dict(ray_grid=8), dict(ray_grid=12),
                 dict(ray_grid=16), dict(ray_grid=8, stack=32), dict(ray_grid=8, stack=64),
+                dict(ray_grid=1, packets=1), dict(ray_grid=4, packets=1), dict(ray_grid=8, packets=1, stack=32),
                 dict(block=(16, 16), main_form=0, recon=(16, 16)), dict(block=(64, 4), main_form=1, recon=(64, 8)),
                 dict(block=(32, 16), main_form=2, recon=(32, 16)), dict(block=(64, 8), main_form=2, recon=(64, 4)),
                 dict(block=(32, 8), main_form=1, recon=(8, 32))]
     results = []
     for v in variants:
-        ctx.set_trace(ray_grid=v.get("ray_grid", 4), stack=v.get("stack", 96))
+        ctx.set_trace(ray_grid=v.get("ray_grid", 4), stack=v.get("stack", 96), packets=v.get("packets", 0))
         ctx.set_gather(block=v.get("block", (32, 8)), main_form=v.get("main_form", 0),
                        recon_block=v.get("recon", (32, 8)))
         h = dof.History(ctx, w.W, w.H, max_rays=oracle.max_rays(prm), record_rays=True)
@@ -483,9 +485,12 @@ def test_tree_shape_does_not_change_hits():
     assert results[1][4] < results[0][4]
 
 
-def test_batch_equals_alone():
+@pytest.mark.parametrize("packets", [0, 1])
+def test_batch_equals_alone(packets):
     """dof_batch_frame over sessions of different sizes, scenes, lenses, ray modes and
-    aperture shapes gives, for every session, exactly what dof_frame gives for it alone."""
+    aperture shapes gives, for every session, exactly what dof_frame gives for it alone
+    (alone: one ray per lane; batched: the same, or warp packets, whose warps straddle
+    the sessions' ray lists at their boundaries)."""
     from paper_2210_06158_gb300 import dof
     import torch
     dev = torch.device("cuda", 0)
@@ -508,7 +513,9 @@ def test_batch_equals_alone():
         sess.append(dict(w=w, prm=prm, gbs=gbs, sc=sc, alone=dof.History(ctx, W, H, mr),
                          mixed=dof.History(ctx, W, H, mr)))
     for f in range(2):
+        ctx.set_trace(packets=0)
         alone = [dof.frame(ctx, s["sc"], s["gbs"][f], s["w"].camera(f), s["prm"], s["alone"]).clone() for s in sess]
+        ctx.set_trace(packets=packets)
         mixed = dof.batch_frame(ctx, [dict(scene=s["sc"], gbuf=s["gbs"][f], cam=s["w"].camera(f), params=s["prm"],
                                            hist=s["mixed"]) for s in sess])
         torch.cuda.synchronize()

@@ -57,8 +57,9 @@ class _Ctx:
 
 
 def _cost(cfg):
-    # separable, minimum at width 2, lens grid 8, stack 64, 6 blocks per SM, refill 12, 32 steps
+    # separable, minimum at width 2, lens grid 8, stack 64, 6 blocks per SM, refill 12, 32 steps, packets
     return (1.0 + (0.3 if cfg["bvh_width"] == 4 else 0.0) + 0.04 * abs(cfg["ray_grid"] - 8)
+            + (0.1 if cfg["packets"] == 0 else 0.0)
             + 0.001 * abs(cfg["stack"] - 64)
             + 0.05 * abs(cfg["blocks_per_sm"] - 6)
             + 0.02 * abs(cfg["refill_idle"] - 12) + 0.001 * abs(cfg["steps"] - 32))
@@ -73,7 +74,8 @@ def test_tune_trace_finds_the_optimum_of_a_separable_cost(monkeypatch):
         clock.t += _cost(ctx.cfg)
 
     best, seen = tune.tune_trace(ctx, run_frame, frames=3, stream=types.SimpleNamespace())
-    assert best == {"bvh_width": 2, "ray_grid": 8, "stack": 64, "blocks_per_sm": 6, "refill_idle": 12, "steps": 32}
+    assert best == {"bvh_width": 2, "ray_grid": 8, "stack": 64, "blocks_per_sm": 6, "refill_idle": 12, "steps": 32,
+                    "packets": 1}
     assert ctx.cfg == best                         # the context keeps the winner
     for key, ms in seen.items():
         assert ms == pytest.approx(_cost(dict(key)))
