@@ -42,7 +42,8 @@ C3_STEPS = 32        # timed 4K frames of the default run's c3 sub-record
 # 10 min/max, 1 compare -> 23, x4 = 92) and sorts them (5 compares); a watertight
 # triangle test (Woop et al. 2013) is 9 subtractions, 6 shears (sub, mul) = 12,
 # 3 edge functions (2 mul + sub) = 9, 6 sign tests, det (2), T (3 mul + 3 FMA = 9),
-# 1 division -> 48.
+# 1 division -> 48.  Warp packets (k_trace_packets) count, per lane, every binary node
+# and triangle its lane tested: the union of the warp's rays' nodes.
 FLOP_PER_NODE = {2: 47.0, 4: 97.0}
 FLOP_PER_TRI = 48.0
 FP32_LANES_PER_SM = 128
@@ -53,7 +54,7 @@ FP32_LANES_PER_SM = 128
 # grouped by lens cell) and is scaled by the rays of a full launch (6.72M / 1.78M); its
 # DRAM writes are the rays it keeps for the shader that L2 does not hold, so the scaled
 # figure is an estimate.
-PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_recon": None,
+PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_trace_packets": None, "k_recon": None,
                            "k_main_filter": None, "k_accumulate": None, "k_composite": None,
                            "k_downscale_tiles": None},
                     "c3": {"k_trace_rays<0>": (21.68e6 + 10.87e6) * 6.72 / 1.78}}
@@ -495,8 +496,11 @@ def run_ours(args, rank, world):
     sm_mhz = clocks.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6 / 1e12      # TFLOP/s, FMA = 2
-    trace_flop = (visits * FLOP_PER_NODE[tuned["bvh_width"]] + tests * FLOP_PER_TRI) / n_samples
-    dom_key = f"{dom}<{1 if tuned['bvh_width'] == 4 else 0}>" if dom == "k_trace_rays" else dom
+    # warp packets always traverse the binary tree
+    wide = tuned["bvh_width"] == 4 and not tuned.get("packets")
+    trace_flop = (visits * FLOP_PER_NODE[4 if wide else 2] + tests * FLOP_PER_TRI) / n_samples
+    tracer_key = "k_trace_packets" if tuned.get("packets") else f"k_trace_rays<{1 if wide else 0}>"
+    dom_key = tracer_key if dom == "k_trace_rays" else dom
     traffic = PROFILED_TRAFFIC.get(args.config, {}).get(dom_key) if not args.size else None
     if dom == "k_trace_rays" and kavg[dom] > 0:
         achieved = trace_flop / (kavg[dom] * 1e-3) / 1e12
