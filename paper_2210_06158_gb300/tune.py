@@ -56,6 +56,10 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None):
     best = dict(DEFAULT, bvh_width=space["bvh_width"][0])
     seen = {}
 
+    def canon(cfg):
+        # warp packets traverse the binary tree whatever the width says
+        return dict(cfg, bvh_width=2) if cfg.get("packets") and 2 in space["bvh_width"] else cfg
+
     def measure(cfg, fresh=False):
         key = tuple(sorted(cfg.items()))
         if key in seen and not fresh:
@@ -69,7 +73,7 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None):
         improved = False
         for name, values in space.items():
             for v in values:
-                cand = dict(best, **{name: v})
+                cand = canon(dict(best, **{name: v}))
                 ms = measure(cand)
                 if ms < best_ms * 0.99:
                     ms2, inc2 = measure(cand, fresh=True), measure(best, fresh=True)

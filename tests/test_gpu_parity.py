@@ -23,14 +23,15 @@ def _built():
     oracle.build()
 
 
-def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3, gbuf_f16=False):
+def run_sequence(w, n_frames=1, params=None, report=None, tol_img=2e-3, gbuf_f16=False, ctx=None):
     """Frames 0..n-1 of workload w on both sides; asserts parity frame by frame.
     gbuf_f16: the kernels take colour and normal as half planes (DOF_FMT_F16) and the
-    oracle the same values widened to float."""
+    oracle the same values widened to float.  ctx: a context with its options set
+    (default: a fresh one)."""
     params = dict(params or w.params)
     w.params = params
     osc = oracle.Scene(w.scene)
-    gpu = GpuRunner(w, params)
+    gpu = GpuRunner(w, params, ctx=ctx)
     ohist = oracle.History(w.W, w.H)
     H2, W2 = w.H // 2, w.W // 2
     rt_r = taint_radius(params)
@@ -701,12 +702,23 @@ def test_host_validation_errors():
     assert small.bytes_in_use == 0
 
 
+def _bench_context(ploc_radius, **trace):
+    """A context with the tracer settings the benchmark's autotuner picks for a workload
+    on GB300 (the results do not depend on them; the launches do)."""
+    from paper_2210_06158_gb300 import dof
+    ctx = dof.Context(0)
+    ctx.set_ploc_radius(ploc_radius)
+    ctx.set_trace(**trace)
+    return ctx
+
+
 @pytest.mark.slow
 def test_full_size_c2_two_frames():
     """1920x1080, 495,802 triangles, 1 spp, frames 0 and 1 of the dolly, in the launch
-    configuration the benchmark times."""
+    configuration the benchmark times (binary tree from PLOC radius 16, pixel order,
+    warp packets)."""
     w = make_workload("c2", n_frames=2)
-    stats = run_sequence(w, 2)
+    stats = run_sequence(w, 2, ctx=_bench_context(16, bvh_width=2, ray_grid=1, packets=1))
     _print(stats, "c2-full")
     tot = sum(s["rays"] for s in stats)
     mis = sum(s["mismatches"] for s in stats)
@@ -716,9 +728,10 @@ def test_full_size_c2_two_frames():
 def test_full_size_c3_two_frames():
     """3840x2160, 1,980,930 triangles, 85 mm f/1.2, CoC radius clamp 64 px, 4 spp, frames
     0 and 1 of the dolly at full size, in the launch configuration the benchmark times
-    (the main filter's halo and the tracer's batch as at 4K)."""
+    (the main filter's halo and the tracer's batch as at 4K; binary tree from PLOC radius
+    48, rays grouped on an 8 x 8 lens grid, one ray per lane)."""
     w = make_workload("c3", n_frames=2)
-    stats = run_sequence(w, 2)
+    stats = run_sequence(w, 2, ctx=_bench_context(48, bvh_width=2, ray_grid=8, packets=0))
     _print(stats, "c3-full")
     tot = sum(s["rays"] for s in stats)
     mis = sum(s["mismatches"] for s in stats)

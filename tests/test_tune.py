@@ -211,3 +211,18 @@ def test_tune_gathers_keeps_the_default_within_one_percent(monkeypatch):
 
     best, _ = tune.tune_gathers(ctx, run_frame, frames=2, stream=types.SimpleNamespace())
     assert best == tune.GATHER_DEFAULT
+
+
+def test_tune_trace_reports_packets_with_the_binary_tree(monkeypatch):
+    """Warp packets always traverse the binary tree: a pick with packets names width 2."""
+    clock = _Clock()
+    _fake_cuda(monkeypatch, clock)
+    ctx = _Ctx()
+
+    def run_frame(k):
+        c = ctx.cfg
+        clock.t += 1.0 - (0.2 if c["packets"] else 0.0) - (0.1 if c["bvh_width"] == 4 and not c["packets"] else 0.0)
+
+    best, seen = tune.tune_trace(ctx, run_frame, frames=2, stream=types.SimpleNamespace())
+    assert best["packets"] == 1 and best["bvh_width"] == 2
+    assert all(dict(k)["bvh_width"] == 2 for k in seen if dict(k)["packets"])
