@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
 // the nodes that only some of its rays need.  Lanes of a warp that straddles two
 // sessions of a batch trace one session's packet after the other.
 template <int kCap, class AS>
-__global__ void __launch_bounds__(128, 7) k_trace_packets(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(128, 8) k_trace_packets(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     const unsigned lane = threadIdx.x & 31;
     __shared__ uint32_t pre[kMaxBatch];
@@ -693,7 +693,10 @@ __global__ void __launch_bounds__(128, 7) k_trace_packets(const __grid_constant_
     __syncthreads();
     const uint32_t total = pre[A.ns - 1];
     uint32_t n_visit = 0, n_tests = 0;
-    int stack[kCap];
+    // the warp's stack: one copy in shared memory (every lane writes the same entry and
+    // reads it back, so no lane waits on another's store)
+    __shared__ int stacks[4][kCap];
+    int *stack = stacks[threadIdx.x >> 5];
     while (true) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(A.cursor, 32u);
@@ -747,12 +750,14 @@ __global__ void __launch_bounds__(128, 7) k_trace_packets(const __grid_constant_
                 const BvhNode *__restrict__ nodes = S.sc.nodes;
                 const float4 *__restrict__ tris = S.sc.tris;
                 const int n_nodes = n_tree - 1;
-                const long long max_steps = 4ll * n_tree + 64;
+                const uint32_t max_steps = (uint32_t)min(4ll * n_tree + 64, 4294967295ll);
                 int node = S.sc.root, sp = 0;
-                for (long long steps = 0;; steps++) {
-                    // warp-uniform guards: a reference outside the tree or more steps than
-                    // a valid tree takes end the packet with the status set
-                    if (steps > max_steps || node >= n_nodes || (node < 0 && ~node >= n_tree)) {
+                for (uint32_t steps = 0;; steps++) {
+                    // warp-uniform guards: a reference outside the tree (internal nodes
+                    // 0 .. n_nodes - 1, leaves ~0 .. ~(n_tree - 1)) or more steps than a
+                    // valid tree takes end the packet with the status set
+                    if (steps >= max_steps ||
+                        ((uint32_t)node >= (uint32_t)n_nodes && (uint32_t)~node >= (uint32_t)n_tree)) {
                         if (lane == 0) atomicOr(status, 2u);
                         break;
                     }
