@@ -49,15 +49,16 @@ FLOP_PER_TRI = 48.0
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes (read + write) per launch from the last ncu capture of each kernel on the
-# workload (profiles/tracer_c3_1080p.md); a kernel or workload changed since its capture
-# has None.  The 4K tracer was captured at 1920x1080 (same scene, lens, 4 spp, rays
-# grouped by lens cell) and is scaled by the rays of a full launch (6.72M / 1.78M); its
-# DRAM writes are the rays it keeps for the shader that L2 does not hold, so the scaled
-# figure is an estimate.
-PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_trace_packets": None, "k_recon": None,
-                           "k_main_filter": None, "k_accumulate": None, "k_composite": None,
+# workload (profiles/tracer_c3_1080p.md, profiles/tracer_packets.md); a kernel or
+# workload changed since its capture has None.  The 4K tracers were captured at
+# 1920x1080 (same scene, lens, 4 spp, rays grouped by lens cell) and are scaled by the
+# rays of a full launch (6.73M / 1.78M); their DRAM writes are the rays they keep for the
+# shader that L2 does not hold, so the scaled figures are estimates.
+PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_trace_packets": 7.467e6 + 0.0,
+                           "k_recon": None, "k_main_filter": None, "k_accumulate": None, "k_composite": None,
                            "k_downscale_tiles": None},
-                    "c3": {"k_trace_rays<0>": (21.68e6 + 10.87e6) * 6.72 / 1.78}}
+                    "c3": {"k_trace_rays<0>": (21.68e6 + 10.87e6) * 6.72 / 1.78,
+                           "k_trace_packets": (19.646e6 + 4.697e6) * 6.73 / 1.78}}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
@@ -345,20 +346,33 @@ def run_ours(args, rank, world):
         dof.frame(ctx, scene, gb, None, None, h, out, cam_struct=cams[s], params_s=pstruct)
 
     # session start (untimed): the autotuners pick the BVH build (PLOC radius), the
-    # tree the rays traverse and the tracer's launch shape
+    # tree the rays traverse and the tracer's launch shape -- or --settings pins them
     t0 = time.perf_counter()
-    widths = (args.bvh_width,) if args.bvh_width else (4, 2)
-    scene, tuned_bvh, _ = tune.tune_scene(
-        ctx, w.scene, lambda sc, k: dof.frame(ctx, sc, gbs[k % CYCLE], None, None, hist, out,
-                                              cam_struct=cams[k % len(cams)], params_s=pstruct), widths=widths)
-    info = scene.info()
-    tuned, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4,
-                               widths=(args.bvh_width,) if args.bvh_width else None)
-    tuned = dict(tuned, ploc_radius=tuned_bvh["ploc_radius"])
-    # the 81-tap gathers' block shape and the main filter's form
-    gathers, _ = tune.tune_gathers(ctx, lambda k: step(k % len(cams), hist), frames=4)
-    gathers = dict(main_filter_block=list(gathers["gather_block"]), main_filter_form=gathers["main_form"],
-                   recon_block=list(gathers["recon_block"]))
+    pinned = parse_settings(args.settings)
+    if pinned:
+        ctx.set_ploc_radius(pinned["ploc_radius"])
+        scene.close()
+        scene = dof.Scene(ctx, w.scene)
+        info = scene.info()
+        tuned = {k: pinned[k] for k in tune.DEFAULT}
+        ctx.set_trace(**tuned)
+        tuned = dict(tuned, ploc_radius=pinned["ploc_radius"], pinned=True)
+        gsel = dict(gather_block=pinned["main_filter_block"], main_form=pinned["main_filter_form"],
+                    recon_block=pinned["recon_block"])
+        ctx.set_gather(block=gsel["gather_block"], main_form=gsel["main_form"], recon_block=gsel["recon_block"])
+    else:
+        widths = (args.bvh_width,) if args.bvh_width else (4, 2)
+        scene, tuned_bvh, _ = tune.tune_scene(
+            ctx, w.scene, lambda sc, k: dof.frame(ctx, sc, gbs[k % CYCLE], None, None, hist, out,
+                                                  cam_struct=cams[k % len(cams)], params_s=pstruct), widths=widths)
+        info = scene.info()
+        tuned, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4,
+                                   widths=(args.bvh_width,) if args.bvh_width else None)
+        tuned = dict(tuned, ploc_radius=tuned_bvh["ploc_radius"])
+        # the 81-tap gathers' block shape and the main filter's form
+        gsel, _ = tune.tune_gathers(ctx, lambda k: step(k % len(cams), hist), frames=4)
+    gathers = dict(main_filter_block=list(gsel["gather_block"]), main_filter_form=gsel["main_form"],
+                   recon_block=list(gsel["recon_block"]))
     tune_s = time.perf_counter() - t0
     hist.reset()
 
@@ -858,6 +872,22 @@ def run_serve(args):
     return line
 
 
+def parse_settings(text):
+    """--settings "key=value,...": the tracer's and gathers' settings as the autotuners
+    report them (config.tracer, config.gathers), the rest at their defaults; blocks as
+    WxH.  None when not given."""
+    if not text:
+        return None
+    from paper_2210_06158_gb300 import tune
+    out = dict(tune.DEFAULT, ploc_radius=48, main_filter_block=(32, 8), main_filter_form=0, recon_block=(32, 8))
+    for item in text.split(","):
+        k, v = (s.strip() for s in item.split("="))
+        if k not in out:
+            raise SystemExit(f"--settings: unknown key {k!r} (keys: {', '.join(sorted(out))})")
+        out[k] = tuple(int(x) for x in v.lower().split("x")) if k.endswith("_block") else int(v)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -874,6 +904,11 @@ def main():
                     help="WxH: the workload's scene, lens and camera path at another resolution (profiler captures)")
     ap.add_argument("--bvh-width", type=int, default=None, choices=[2, 4],
                     help="traverse this tree width instead of the autotuner's choice (profiler captures)")
+    ap.add_argument("--settings", default=None,
+                    help="pin the tracer and gather settings instead of autotuning them, e.g. "
+                         "ploc_radius=16,bvh_width=2,ray_grid=1,packets=1,main_filter_block=64x4 "
+                         "(keys as in config.tracer / config.gathers; reproduces a tuned run under a profiler); "
+                         "the main workload only, the 4K sub-record is still autotuned")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -916,6 +951,7 @@ def main():
         import copy
         a3 = copy.copy(args)
         a3.config, a3.steps = "c3", min(args.steps, C3_STEPS)
+        a3.settings = None          # --settings pins the run's main workload only
         r3, w3 = run_ours(a3, rank, world)
         keep = ("value", "unit", "steps", "warmup", "ms_per_step", "config", "roofline", "e2e", "fp16_storage",
                 "gpu_launches", "clocks", "kernel_ms", "image_passes", "mrays_per_s", "rays_per_frame",
