@@ -528,15 +528,18 @@ def test_batch_equals_alone(packets):
                                    hist=s["mixed"])] * 2)
 
 
-def test_graph_equals_batch():
+@pytest.mark.parametrize("packets", [0, 1])
+def test_graph_equals_batch(packets):
     """A captured step (CUDA graph) replayed with new cameras and G-buffers gives, frame
-    after frame, exactly what dof_batch_frame gives; launches that need other histories
-    or launch shapes are refused."""
+    after frame, exactly what dof_batch_frame gives, with either tracer (one ray per lane
+    or warp packets); launches that need other histories, launch shapes or the other
+    tracer are refused."""
     from paper_2210_06158_gb300 import dof
     import torch
     dev = torch.device("cuda", 0)
     specs = [("c1", 256, 144, {}), ("c2", 322, 182, {}), ("c1", 130, 74, dict(ray_mode=1, m=4))]
     ctx = dof.Context(0)
+    ctx.set_trace(packets=packets)
     sess = []
     nf = 3
     for k, (name, W, H, over) in enumerate(specs):
@@ -573,6 +576,9 @@ def test_graph_equals_batch():
         it["params"] = dict(it["params"], max_coc_px=2.0 * float(it["params"]["max_coc_px"]))
     with pytest.raises(dof.DofError):
         graph.launch(wider)                             # another main-filter tile (halo follows max_coc_px)
+    ctx.set_trace(packets=1 - packets)
+    with pytest.raises(dof.DofError):
+        graph.launch(items(0, "hg"))                    # captured with the other tracer
     graph.close()
 
 
