@@ -545,26 +545,38 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const unsigned long
     }
 }
 
-// Stable sort of (keys, vals) by the whole 64-bit key, 8 passes of 8 bits; the result
-// ends in (keys, vals), (keys2, vals2) and hist are scratch (hist: 256 * ceil(n / 2048)
-// ints, sums: ceil(256 * ceil(n / 2048) / 2048) ints).
+// Stable sort of (keys, vals) by the key's low `bits` bits (a multiple of 16: an even
+// number of 8-bit passes); the result ends in (keys, vals), (keys2, vals2) and hist are
+// scratch (hist: 256 * ceil(n / 2048) ints, sums: ceil(256 * ceil(n / 2048) / 2048) ints).
 void device_radix_sort_pairs(unsigned long long *keys, uint32_t *vals, unsigned long long *keys2, uint32_t *vals2,
-                             int n, int *hist, int *sums, cudaStream_t st) {
+                             int n, int *hist, int *sums, cudaStream_t st, int bits = 64) {
     if (n <= 1) return;
     const int nb = (n + kSortTile - 1) / kSortTile;
     unsigned long long *ki = keys, *ko = keys2;
     uint32_t *vi = vals, *vo = vals2;
-    for (int shift = 0; shift < 64; shift += 8) {
+    for (int shift = 0; shift < bits; shift += 8) {
         k_rs_hist<<<nb, kSortThreads, 0, st>>>(ki, n, shift, hist, nb);
         device_exclusive_scan(hist, hist, kSortBins * nb, sums, st);
         k_rs_scatter<<<nb, kSortThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, nb);
         unsigned long long *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
     }
-    // 8 passes: the sorted data are back in (keys, vals)
+    // an even number of passes: the sorted data are back in (keys, vals)
 }
 
 }  // namespace
+
+size_t sort_pairs_scratch_ints(int n) {
+    const size_t nbk = (size_t)(n + kSortTile - 1) / kSortTile;
+    const size_t nh = (size_t)kSortBins * nbk;
+    return nh + (nh + kScanTile - 1) / kScanTile + 1;
+}
+
+void sort_pairs_by_low_bits(unsigned long long *keys, uint32_t *vals, unsigned long long *keys2, uint32_t *vals2,
+                            int n, int bits, int *scratch, cudaStream_t st) {
+    const size_t nh = (size_t)kSortBins * ((n + kSortTile - 1) / kSortTile);
+    device_radix_sort_pairs(keys, vals, keys2, vals2, n, scratch, scratch + nh, st, bits);
+}
 
 static inline unsigned blocks_for(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
 

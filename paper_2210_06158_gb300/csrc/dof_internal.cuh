@@ -212,6 +212,11 @@ void count_launches(long long n);
 // rasterising G-buffer producer (raster.cu)
 void launch_prim_index(const float4 *tris, int n, int32_t *prim_k, cudaStream_t st);
 size_t raster_scratch_bytes(int W, int H, int n_tot);
+// stable sort of (keys, vals) by the keys' low `bits` bits (a multiple of 16), result in
+// (keys, vals); (keys2, vals2) and scratch (sort_pairs_scratch_ints(n) ints) are scratch
+size_t sort_pairs_scratch_ints(int n);
+void sort_pairs_by_low_bits(unsigned long long *keys, uint32_t *vals, unsigned long long *keys2, uint32_t *vals2,
+                            int n, int bits, int *scratch, cudaStream_t st);
 cudaError_t launch_raster(const DevCam &cam, const DevParams &p, const SceneDev &sc, const int32_t *prim_k,
                           void *scratch, int sm_count, float4 *color, float *depth, float4 *normal, int32_t *prim,
                           cudaStream_t st);

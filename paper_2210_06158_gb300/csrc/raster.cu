@@ -13,6 +13,14 @@
 // rasterised by the warp that set them up (the warp's 32 boxes are enumerated as one
 // list, so a warp's lanes stay busy whatever the box sizes); larger ones are queued and
 // cut into chunks of kChunkPx pixels that persistent blocks claim from a counter.
+//
+// Occlusion culling: the triangles are taken nearest first, in batches of growing size
+// (sorted by a lower bound of their distance from the lens centre).  After each batch a
+// two-level depth pyramid holds, per 16 x 16 and 128 x 128 pixel tile, the farthest
+// closest hit so far; a triangle whose bound is beyond it on every tile of its candidate
+// box is dropped whole, and a candidate pixel skips the ray test when the bound is beyond
+// the pixel's own closest hit.  Keys only decrease, so a stale read or an older pyramid
+// culls less, never wrongly; see near_bound for the margin.
 #include "geometry.cuh"
 
 #include <algorithm>
@@ -22,6 +30,8 @@ namespace {
 constexpr int kSmallPx = 4096;       // candidate pixels above which a triangle is queued
 constexpr int kChunkPx = 2048;       // pixels of one chunk of a queued triangle
 constexpr int kRastThreads = 256;
+constexpr int kHizShift1 = 4, kHizShift2 = 7;   // depth-pyramid tiles: 16 and 128 pixels
+constexpr int kHizMaxTiles1 = 16;               // boxes over more fine tiles use the coarse level
 
 // Edge functions of the image plane, scaled so that |a| + |b| = 1 (values in pixels)
 // and oriented so that a pixel centre (x, y) can see the triangle only where
@@ -36,7 +46,8 @@ struct BigTri {
     float4 e0, e1, e2;          // (a, b, c, -) per edge
     int4 box;                   // i0, j0, box width, candidate pixels
     int k;                      // sorted triangle index
-    int pad[3];
+    float tn;                   // its distance bound (near_bound)
+    int pad[2];
 };
 
 __device__ __forceinline__ float3 xyz(float4 v) { return make_float3(v.x, v.y, v.z); }
@@ -199,28 +210,125 @@ struct SmallSlot {               // one triangle of a warp's list (112 bytes)
     float e[9];
     int i0, j0, bw;
     float rbw;
+    float tn;                   // its distance bound (near_bound)
+    int pad[2];
     float4 v0, v1, v2;
 };
+
+// Lower bound of the ray-test distance t of any primary ray to the triangle, for the
+// occlusion test.  The directions are unit vectors, so t is the distance from the lens
+// centre to the hit point, at least the distance to the triangle's bounding box, which
+// is evaluated with every operation rounded down.  The test's t is a convex combination
+// of the vertices' depths along the ray (barycentric weights), evaluated in FP32; the
+// bound is shrunk by 2^-7 to stay below it.  A triangle that reaches within 60 degrees
+// of the image plane (a vertex direction more than 60 degrees off the view axis) gets 0
+// and is never culled: near the lens plane those depths can cancel.
+__device__ __forceinline__ float near_bound(const DevCam &cam, float4 v0, float4 v1, float4 v2) {
+    const float4 v[3] = {v0, v1, v2};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float3 r = make_float3(v[k].x - cam.O.x, v[k].y - cam.O.y, v[k].z - cam.O.z);
+        if (!(dot(r, cam.F) >= 0.5f * sqrtf(dot(r, r)))) return 0.f;
+    }
+    auto gap = [](float o, float a, float b, float c) {
+        const float lo = fminf(a, fminf(b, c)), hi = fmaxf(a, fmaxf(b, c));
+        return fmaxf(fmaxf(__fsub_rd(lo, o), __fsub_rd(o, hi)), 0.f);
+    };
+    const float gx = gap(cam.O.x, v0.x, v1.x, v2.x), gy = gap(cam.O.y, v0.y, v1.y, v2.y);
+    const float gz = gap(cam.O.z, v0.z, v1.z, v2.z);
+    const float s = __fadd_rd(__fadd_rd(__fmul_rd(gx, gx), __fmul_rd(gy, gy)), __fmul_rd(gz, gz));
+    const float d = __fmul_rd(__fsqrt_rd(s), 0.9921875f);
+    return d >= 0.f ? d : 0.f;
+}
+
+// the pixel's closest hit so far (from L2: the atomics update it there); +inf bits are
+// 0xFFFFFFFF, a NaN, so an untouched pixel never culls
+__device__ __forceinline__ bool occluded(const unsigned long long *keys, size_t q, float tn) {
+    const unsigned long long key = __ldcg(&keys[q]);
+    return tn > __uint_as_float((uint32_t)(key >> 32));
+}
+
+// Depth pyramid: hiz1 per 16 x 16 tile (tw1 x th1), hiz2 per 128 x 128 tile (tw2 x th2),
+// each the largest closest-hit distance of its pixels (+inf while a pixel has none).
+struct Hiz {
+    const float *l1, *l2;
+    int tw1, th1, tw2, th2;
+};
+
+// true when every tile of the pixel box [i0, i1] x [j0, j1] has all its pixels' closest
+// hits nearer than tn (fine tiles when the box spans few of them, else coarse ones)
+__device__ bool hiz_occluded(const Hiz &z, int i0, int j0, int i1, int j1, float tn) {
+    if (!(tn > 0.f)) return false;
+    int x0 = i0 >> kHizShift1, x1 = i1 >> kHizShift1, y0 = j0 >> kHizShift1, y1 = j1 >> kHizShift1;
+    const float *lv = z.l1;
+    int tw = z.tw1;
+    if ((x1 - x0 + 1) * (y1 - y0 + 1) > kHizMaxTiles1) {
+        x0 = i0 >> kHizShift2; x1 = i1 >> kHizShift2; y0 = j0 >> kHizShift2; y1 = j1 >> kHizShift2;
+        lv = z.l2;
+        tw = z.tw2;
+    }
+    for (int y = y0; y <= y1; y++)
+        for (int x = x0; x <= x1; x++)
+            if (!(tn > __ldcg(&lv[y * tw + x]))) return false;
+    return true;
+}
+
+// one 16 x 16 block per fine tile: the largest closest hit of its pixels
+__global__ void __launch_bounds__(256) k_hiz1(const unsigned long long *keys, int W, int H, float *hiz1, int tw1) {
+    __shared__ float wmax[8];
+    const int i = blockIdx.x * 16 + (threadIdx.x & 15), j = blockIdx.y * 16 + (threadIdx.x >> 4);
+    float t = -INFINITY;
+    if (i < W && j < H) {
+        const float v = __uint_as_float((uint32_t)(__ldcg(&keys[(size_t)j * W + i]) >> 32));
+        t = v == v ? v : INFINITY;       // no hit yet: +inf
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = wmax[0];
+#pragma unroll
+        for (int k = 1; k < 8; k++) m = fmaxf(m, wmax[k]);
+        hiz1[blockIdx.y * tw1 + blockIdx.x] = m;
+    }
+}
+
+// coarse tiles: the largest of their 8 x 8 fine tiles
+__global__ void k_hiz2(const float *hiz1, int tw1, int th1, float *hiz2, int tw2, int th2) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= tw2 || y >= th2) return;
+    float m = -INFINITY;
+    for (int b = 0; b < 8; b++)
+        for (int a = 0; a < 8; a++) {
+            const int fx = 8 * x + a, fy = 8 * y + b;
+            if (fx < tw1 && fy < th1) m = fmaxf(m, hiz1[fy * tw1 + fx]);
+        }
+    hiz2[y * tw2 + x] = m;
+}
 
 // Setup of every triangle; the small ones are rasterised here, the others queued.
 // `split` warps serve each group of 32 triangles (each sets the group up and takes every
 // split-th stretch of 32 of its candidate pixels), so that scenes with few triangles
 // still occupy the GPU.
-__global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDev sc, int n_tot, int split,
-                                                              unsigned long long *keys, BigTri *big,
+__global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDev sc, const uint32_t *order,
+                                                              int count, int split, const float *tnear, Hiz hiz,
+                                                              bool use_hiz, unsigned long long *keys, BigTri *big,
                                                               uint32_t *n_big) {
     __shared__ SmallSlot slot[kRastThreads];
     __shared__ int excl[kRastThreads];
     const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
     const int gw = blockIdx.x * (kRastThreads / 32) + (threadIdx.x >> 5);
     const int part = gw % split;
-    const int k = (gw / split) * 32 + lane;
+    const int idx = (gw / split) * 32 + lane;
+    const int k = idx < count ? (int)__ldg(&order[idx]) : 0;
     int npx = 0;
-    if (k < n_tot) {
+    if (idx < count) {
         const float4 *tp = sc.tris + 3 * (size_t)k;
         const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
         TriSetup S;
-        if (tri_setup(cam, v0, v1, v2, S)) {
+        const float tn = __ldg(&tnear[k]);
+        if (tri_setup(cam, v0, v1, v2, S) && !(use_hiz && hiz_occluded(hiz, S.i0, S.j0, S.i1, S.j1, tn))) {
             const int bw = S.i1 - S.i0 + 1, bh = S.j1 - S.j0 + 1;
             const long long n = (long long)bw * bh;
             if (n > kSmallPx) {
@@ -232,7 +340,8 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDe
                     B.e2 = make_float4(S.e[6], S.e[7], S.e[8], 0.f);
                     B.box = make_int4(S.i0, S.j0, bw, (int)n);
                     B.k = k;
-                    B.pad[0] = B.pad[1] = B.pad[2] = 0;
+                    B.tn = tn;
+                    B.pad[0] = B.pad[1] = 0;
                     big[b] = B;
                 }
             } else {
@@ -241,6 +350,7 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDe
 #pragma unroll
                 for (int q = 0; q < 9; q++) o.e[q] = S.e[q];
                 o.i0 = S.i0; o.j0 = S.j0; o.bw = bw; o.rbw = 1.f / (float)bw;
+                o.tn = tn;
                 o.v0 = v0; o.v1 = v1; o.v2 = v2;
             }
         }
@@ -265,7 +375,8 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_small(DevCam cam, SceneDe
         int q, r;
         divmod(w - excl[wbase + l], o.bw, o.rbw, q, r);
         const int i = o.i0 + r, j = o.j0 + q;
-        if (edges_pass(o.e, i + 0.5f, j + 0.5f)) test_pixel(cam, keys, i, j, o.v0, o.v1, o.v2);
+        if (edges_pass(o.e, i + 0.5f, j + 0.5f) && !occluded(keys, (size_t)j * cam.W + i, o.tn))
+            test_pixel(cam, keys, i, j, o.v0, o.v1, o.v2);
     }
 }
 
@@ -319,6 +430,7 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_big(DevCam cam, SceneDev 
     __shared__ float e[9];
     __shared__ float4 v[3];
     __shared__ int box[4];
+    __shared__ float tn;
     __shared__ uint32_t claim[2];
     const uint32_t total = *n_chunks;
     const int nb = (int)*n_big;
@@ -339,6 +451,7 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_big(DevCam cam, SceneDev 
                 e[3] = B.e1.x; e[4] = B.e1.y; e[5] = B.e1.z;
                 e[6] = B.e2.x; e[7] = B.e2.y; e[8] = B.e2.z;
                 box[0] = B.box.x; box[1] = B.box.y; box[2] = B.box.z; box[3] = B.box.w;
+                tn = B.tn;
                 const float4 *tp = sc.tris + 3 * (size_t)B.k;
                 v[0] = __ldg(tp); v[1] = __ldg(tp + 1); v[2] = __ldg(tp + 2);
             }
@@ -354,7 +467,8 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_big(DevCam cam, SceneDev 
         for (int w = first + threadIdx.x; w < last; w += kRastThreads) {
             const int q = w / bw, r = w - q * bw;
             const int i = box[0] + r, j = box[1] + q;
-            if (edges_pass(e, i + 0.5f, j + 0.5f)) test_pixel(cam, keys, i, j, v[0], v[1], v[2]);
+            if (edges_pass(e, i + 0.5f, j + 0.5f) && !occluded(keys, (size_t)j * cam.W + i, tn))
+                test_pixel(cam, keys, i, j, v[0], v[1], v[2]);
         }
         __syncthreads();
     }
@@ -389,6 +503,19 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_resolve(DevCam cam, DevPa
     normal[q] = make_float4(n.x, n.y, n.z, 0.f);
 }
 
+// per triangle: its distance bound, and the sort key (the bound's bits: non-negative
+// floats order as unsigned integers) with its index
+__global__ void k_tri_near(DevCam cam, SceneDev sc, int n_tot, float *tnear, unsigned long long *skeys,
+                           uint32_t *svals) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_tot) return;
+    const float4 *tp = sc.tris + 3 * (size_t)k;
+    const float tn = near_bound(cam, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
+    tnear[k] = tn;
+    skeys[k] = (unsigned long long)__float_as_uint(tn);
+    svals[k] = (uint32_t)k;
+}
+
 // inverse of the tree order: triangle id -> sorted index
 __global__ void k_prim_index(const float4 *tris, int n, int32_t *prim_k) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -404,10 +531,20 @@ void launch_prim_index(const float4 *tris, int n, int32_t *prim_k, cudaStream_t 
     }
 }
 
+// triangles of the depth-ordered batches: the nearest 1/32, then 1/32, 1/16, 1/8, 1/4
+// and the farthest half
+constexpr int kBatches = 6;
+__host__ inline int batch_end(int b, int n) { return b + 1 >= kBatches ? n : (int)((long long)n >> (kBatches - 1 - b)); }
+
 // Scratch of one call, from the context's stream-ordered pool.
 size_t raster_scratch_bytes(int W, int H, int n_tot) {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    return up(8 * (size_t)W * H) + up(sizeof(BigTri) * (size_t)n_tot) + up(4 * ((size_t)n_tot + 1)) + 256;
+    const size_t n = (size_t)n_tot;
+    const size_t t1 = (size_t)((W + 15) >> kHizShift1) * ((H + 15) >> kHizShift1);
+    const size_t t2 = (size_t)((W + 127) >> kHizShift2) * ((H + 127) >> kHizShift2);
+    return up(8 * (size_t)W * H) + up(sizeof(BigTri) * n) + up(4 * (n + 1)) + up(16 * kBatches) +
+           up(4 * n) + 2 * up(8 * n) + 2 * up(4 * n) + up(4 * sort_pairs_scratch_ints(n_tot)) + up(4 * t1) +
+           up(4 * t2);
 }
 
 cudaError_t launch_raster(const DevCam &cam, const DevParams &p, const SceneDev &sc, const int32_t *prim_k,
@@ -422,23 +559,62 @@ cudaError_t launch_raster(const DevCam &cam, const DevParams &p, const SceneDev 
     base += up(sizeof(BigTri) * (size_t)n_tot);
     uint32_t *chunk_start = reinterpret_cast<uint32_t *>(base);
     base += up(4 * ((size_t)n_tot + 1));
-    uint32_t *counters = reinterpret_cast<uint32_t *>(base);   // n_big, n_chunks, cursor
+    uint32_t *counters = reinterpret_cast<uint32_t *>(base);   // per batch: n_big, n_chunks, cursor
+    base += up(16 * kBatches);
+    const size_t n = (size_t)n_tot;
+    float *tnear = reinterpret_cast<float *>(base);
+    base += up(4 * n);
+    unsigned long long *skeys = reinterpret_cast<unsigned long long *>(base);
+    base += up(8 * n);
+    unsigned long long *skeys2 = reinterpret_cast<unsigned long long *>(base);
+    base += up(8 * n);
+    uint32_t *order = reinterpret_cast<uint32_t *>(base);
+    base += up(4 * n);
+    uint32_t *order2 = reinterpret_cast<uint32_t *>(base);
+    base += up(4 * n);
+    int *sort_scratch = reinterpret_cast<int *>(base);
+    base += up(4 * sort_pairs_scratch_ints(n_tot));
+    Hiz hiz;
+    hiz.tw1 = (cam.W + 15) >> kHizShift1; hiz.th1 = (cam.H + 15) >> kHizShift1;
+    hiz.tw2 = (cam.W + 127) >> kHizShift2; hiz.th2 = (cam.H + 127) >> kHizShift2;
+    float *hiz1 = reinterpret_cast<float *>(base);
+    base += up(4 * (size_t)hiz.tw1 * hiz.th1);
+    float *hiz2 = reinterpret_cast<float *>(base);
+    hiz.l1 = hiz1;
+    hiz.l2 = hiz2;
     cudaError_t e = cudaMemsetAsync(keys, 0xFF, 8 * (size_t)cam.W * cam.H, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 16 * kBatches, st);
     if (e != cudaSuccess) return e;
     if (n_tot > 0) {
-        // at least 32 warps per SM: groups of 32 triangles are split over several warps
-        const int groups = (n_tot + 31) / 32;
-        const int split = std::min(16, std::max(1, (32 * sm_count + groups - 1) / groups));
-        const int warps = groups * split;
-        k_rast_small<<<(warps + kRastThreads / 32 - 1) / (kRastThreads / 32), kRastThreads, 0, st>>>(
-            cam, sc, n_tot, split, keys, big, counters);
-        k_big_chunks<<<1, 1024, 0, st>>>(big, counters, chunk_start, counters + 1);
-        k_rast_big<<<4 * sm_count, kRastThreads, 0, st>>>(cam, sc, keys, big, counters, chunk_start, counters + 1,
-                                                         counters + 2);
+        // the triangles nearest first
+        k_tri_near<<<(n_tot + 255) / 256, 256, 0, st>>>(cam, sc, n_tot, tnear, skeys, order);
+        sort_pairs_by_low_bits(skeys, order, skeys2, order2, n_tot, 32, sort_scratch, st);
+        for (int bt = 0, b0 = 0; bt < kBatches; bt++) {
+            const int b1 = batch_end(bt, n_tot);
+            if (b1 <= b0) continue;
+            uint32_t *cb = counters + 4 * bt;
+            // at least 32 warps per SM: groups of 32 triangles are split over several warps
+            const int groups = (b1 - b0 + 31) / 32;
+            const int split = std::min(16, std::max(1, (32 * sm_count + groups - 1) / groups));
+            const int warps = groups * split;
+            k_rast_small<<<(warps + kRastThreads / 32 - 1) / (kRastThreads / 32), kRastThreads, 0, st>>>(
+                cam, sc, order + b0, b1 - b0, split, tnear, hiz, b0 > 0, keys, big, cb);
+            k_big_chunks<<<1, 1024, 0, st>>>(big, cb, chunk_start, cb + 1);
+            k_rast_big<<<4 * sm_count, kRastThreads, 0, st>>>(cam, sc, keys, big, cb, chunk_start, cb + 1, cb + 2);
+            count_launches(3);
+            b0 = b1;
+            if (b0 < n_tot) {
+                // the depth pyramid for the next batch
+                k_hiz1<<<dim3(hiz.tw1, hiz.th1), 256, 0, st>>>(keys, cam.W, cam.H, hiz1, hiz.tw1);
+                k_hiz2<<<dim3((hiz.tw2 + 15) / 16, (hiz.th2 + 15) / 16), dim3(16, 16), 0, st>>>(
+                    hiz1, hiz.tw1, hiz.th1, hiz2, hiz.tw2, hiz.th2);
+                count_launches(2);
+            }
+        }
+        count_launches(1);
     }
     dim3 b(32, 8), g((cam.W + 31) / 32, (cam.H + 7) / 8);
     k_rast_resolve<<<g, b, 0, st>>>(cam, p, sc, keys, prim_k, color, depth, normal, prim);
-    count_launches(n_tot > 0 ? 4 : 1);
+    count_launches(1);
     return cudaGetLastError();
 }
