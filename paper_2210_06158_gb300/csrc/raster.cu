@@ -532,9 +532,11 @@ void launch_prim_index(const float4 *tris, int n, int32_t *prim_k, cudaStream_t 
 }
 
 // triangles of the depth-ordered batches: the nearest 1/32, then 1/32, 1/16, 1/8, 1/4
-// and the farthest half
+// and the farthest half; scenes under kSortedMin triangles run as one batch in scene
+// order (the sort and the launches would cost more than they save)
 constexpr int kBatches = 6;
-__host__ inline int batch_end(int b, int n) { return b + 1 >= kBatches ? n : (int)((long long)n >> (kBatches - 1 - b)); }
+constexpr int kSortedMin = 65536;
+__host__ inline int batch_end(int b, int nb, int n) { return b + 1 >= nb ? n : (int)((long long)n >> (nb - 1 - b)); }
 
 // Scratch of one call, from the context's stream-ordered pool.
 size_t raster_scratch_bytes(int W, int H, int n_tot) {
@@ -587,10 +589,11 @@ cudaError_t launch_raster(const DevCam &cam, const DevParams &p, const SceneDev 
     if (e != cudaSuccess) return e;
     if (n_tot > 0) {
         // the triangles nearest first
+        const int nbat = n_tot >= kSortedMin ? kBatches : 1;
         k_tri_near<<<(n_tot + 255) / 256, 256, 0, st>>>(cam, sc, n_tot, tnear, skeys, order);
-        sort_pairs_by_low_bits(skeys, order, skeys2, order2, n_tot, 32, sort_scratch, st);
-        for (int bt = 0, b0 = 0; bt < kBatches; bt++) {
-            const int b1 = batch_end(bt, n_tot);
+        if (nbat > 1) sort_pairs_by_low_bits(skeys, order, skeys2, order2, n_tot, 32, sort_scratch, st);
+        for (int bt = 0, b0 = 0; bt < nbat; bt++) {
+            const int b1 = batch_end(bt, nbat, n_tot);
             if (b1 <= b0) continue;
             uint32_t *cb = counters + 4 * bt;
             // at least 32 warps per SM: groups of 32 triangles are split over several warps
