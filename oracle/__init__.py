@@ -143,6 +143,8 @@ def _declare(L):
     L.or_binomial5.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
     L.or_sobel5.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.or_albedo.argtypes = [C.c_uint32, C.c_int, vp]
+    L.or_fmix32.restype = C.c_uint32
+    L.or_fmix32.argtypes = [C.c_uint32]
     L.or_shade.argtypes = [vp, C.POINTER(OrParams), C.c_int, vp, vp, C.c_double, vp, vp]
     # individual stages
     L.or_downscale.argtypes = [C.POINTER(OrCamera), C.POINTER(OrParams), C.c_int, C.c_int,

@@ -348,8 +348,9 @@ int or_hit_check(const OrScene *s, const double o_in[3], const double d_in[3], i
     return O.state == PROBE_CLEAN ? 1 : 2;
 }
 
-/* murmur3's 32-bit finaliser (Appleby) */
-static uint32_t fmix32(uint32_t h) {
+/* murmur3's 32-bit finaliser (Appleby): two xor-shift / multiply rounds and a last
+ * xor-shift.  For an empty key, MurmurHash3_x86_32(seed) is exactly this of the seed. */
+uint32_t or_fmix32(uint32_t h) {
     h ^= h >> 16; h *= 0x85EBCA6BU; h ^= h >> 13; h *= 0xC2B2AE35U; h ^= h >> 16;
     return h;
 }
@@ -357,9 +358,9 @@ static uint32_t fmix32(uint32_t h) {
 /* Per-triangle albedo in [0.1, 0.9]^3 from an integer hash of (seed, triangle id):
  * the stand-in for the paper's scene materials. */
 void or_albedo(uint32_t seed, int prim, double col[3]) {
-    uint32_t base = fmix32(seed);
+    uint32_t base = or_fmix32(seed);
     for (int c = 0; c < 3; c++) {
-        uint32_t h = fmix32(base ^ (uint32_t)(3 * prim + c));
+        uint32_t h = or_fmix32(base ^ (uint32_t)(3 * prim + c));
         col[c] = 0.1 + 0.8 * ((double)(h >> 8) * (1.0 / 16777216.0));
     }
 }

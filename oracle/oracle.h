@@ -93,6 +93,7 @@ double or_plane_t(const OrScene *s, int prim, const double o[3], const double d[
 void or_shade(const OrScene *s, const OrParams *p, int prim, const double o[3],
               const double d[3], double t, double col[3], double nrm[3]);
 void or_albedo(uint32_t seed, int prim, double col[3]);
+uint32_t or_fmix32(uint32_t h);
 
 /* ---------------- camera / lens (or_camera.c) ---------------- */
 double or_coc(const OrCamera *c, int W, double z);

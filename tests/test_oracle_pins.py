@@ -1115,3 +1115,28 @@ def test_prefilter_similarity_scale_has_a_floor_of_one_pixel():
     out = _prefilter(col, R)
     want = (A_COL + 8 * 0.5 * B_COL) / (1 + 8 * 0.5)
     assert np.abs(out[j, i, :3] - want).max() < 1e-12
+
+
+def test_albedo_hash_matches_murmur3_test_vectors():
+    """The albedo hash is murmur3's 32-bit finaliser.  For an empty key,
+    MurmurHash3_x86_32 is the finaliser of the seed, and its published test vectors
+    fix three values: seed 0 -> 0, seed 1 -> 0x514E28B7, seed 0xFFFFFFFF -> 0x81F16F39.
+    The per-triangle albedo of seed 0 and triangle 0 then reads the finaliser of 0, 1
+    and 2 (channel c takes 3 prim + c), so channel 0 is the range's floor 0.1 and
+    channel 1 is fixed by the seed-1 vector."""
+    L = oracle.lib()
+    assert L.or_fmix32(0) == 0
+    assert L.or_fmix32(1) == 0x514E28B7
+    assert L.or_fmix32(0xFFFFFFFF) == 0x81F16F39
+    col = np.zeros(3)
+    L.or_albedo(0, 0, col.ctypes.data_as(C.c_void_p))
+    assert col[0] == 0.1
+    assert col[1] == pytest.approx(0.1 + 0.8 * (0x514E28B7 >> 8) / 2.0 ** 24, abs=1e-15)
+    assert col[2] == pytest.approx(0.1 + 0.8 * (L.or_fmix32(2) >> 8) / 2.0 ** 24, abs=1e-15)
+    # every albedo lies in [0.1, 0.9) and the channels of many triangles fill it evenly
+    cols = np.zeros((4096, 3))
+    for k in range(4096):
+        L.or_albedo(7, k, cols[k].ctypes.data_as(C.c_void_p))
+    assert cols.min() >= 0.1 and cols.max() < 0.9
+    assert abs(cols.mean() - 0.5) < 0.01
+    assert abs(np.corrcoef(cols[:, 0], cols[:, 1])[0, 1]) < 0.05
