@@ -8,6 +8,7 @@
 namespace {
 
 constexpr int kStack = kTraversalStack;   // >= the tree depth (checked at upload)
+constexpr int kTraceThreads = 128;        // threads of a tracer block (4 warps)
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC 2011); only the first two output words are used
@@ -542,7 +543,7 @@ __device__ __forceinline__ void lens_ray(const DevCam &cam, const DevParams &p, 
 // closest hit of each ray: (sorted triangle index or -1, t).  kWide: every session of
 // the batch traverses its 4-wide tree, else every session its binary tree.
 template <bool kWide, int kCap, class AS>
-__global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(kTraceThreads, 7) k_trace_rays(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     // inclusive prefix of the sessions' ray counts (the batch's concatenated ray list)
@@ -678,7 +679,7 @@ __global__ void __launch_bounds__(128, 7) k_trace_rays(const __grid_constant__ A
 // the nodes that only some of its rays need.  Lanes of a warp that straddles two
 // sessions of a batch trace one session's packet after the other.
 template <int kCap, class AS>
-__global__ void __launch_bounds__(128, 8) k_trace_packets(const __grid_constant__ AS as_) {
+__global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     const unsigned lane = threadIdx.x & 31;
     __shared__ uint32_t pre[kMaxBatch];
@@ -695,7 +696,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_packets(const __grid_constant_
     uint32_t n_visit = 0, n_tests = 0;
     // the warp's stack: one copy in shared memory (every lane writes the same entry and
     // reads it back, so no lane waits on another's store)
-    __shared__ int stacks[4][kCap];
+    __shared__ int stacks[kTraceThreads / 32][kCap];
     int *stack = stacks[threadIdx.x >> 5];
     while (true) {
         uint32_t base = 0;
@@ -909,17 +910,17 @@ void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t s
     int need = A.stack_depth;
     for (int i = 0; i < A.ns; i++) need = max(need, A.s[i].sc.stack_need);
     if (A.packets && !wide) {
-        if (need <= 32) k_trace_packets<32, AS><<<blocks, 128, 0, st>>>(as);
-        else if (need <= 64) k_trace_packets<64, AS><<<blocks, 128, 0, st>>>(as);
-        else k_trace_packets<kStack, AS><<<blocks, 128, 0, st>>>(as);
+        if (need <= 32) k_trace_packets<32, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else if (need <= 64) k_trace_packets<64, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else k_trace_packets<kStack, AS><<<blocks, kTraceThreads, 0, st>>>(as);
     } else if (wide) {
-        if (need <= 32) k_trace_rays<true, 32, AS><<<blocks, 128, 0, st>>>(as);
-        else if (need <= 64) k_trace_rays<true, 64, AS><<<blocks, 128, 0, st>>>(as);
-        else k_trace_rays<true, kStack, AS><<<blocks, 128, 0, st>>>(as);
+        if (need <= 32) k_trace_rays<true, 32, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else if (need <= 64) k_trace_rays<true, 64, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else k_trace_rays<true, kStack, AS><<<blocks, kTraceThreads, 0, st>>>(as);
     } else {
-        if (need <= 32) k_trace_rays<false, 32, AS><<<blocks, 128, 0, st>>>(as);
-        else if (need <= 64) k_trace_rays<false, 64, AS><<<blocks, 128, 0, st>>>(as);
-        else k_trace_rays<false, kStack, AS><<<blocks, 128, 0, st>>>(as);
+        if (need <= 32) k_trace_rays<false, 32, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else if (need <= 64) k_trace_rays<false, 64, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else k_trace_rays<false, kStack, AS><<<blocks, kTraceThreads, 0, st>>>(as);
     }
     tmark(tm, DOF_K_TRACE, st);
     k_shade<AS><<<A.start[SH_SHADE][A.ns], 128, 0, st>>>(as);
