@@ -180,7 +180,9 @@ size_t dof_ctx_bytes_in_use(const DofCtx *ctx);
 #define DOF_OPT_GATHER_BLOCK        8
 /* the main filter's reads: 0 (default) = the block's halo tile staged in shared memory when
  * it fits in 64 KB, else through L1; 1 = always through L1; 2 = the halo tile whenever it
- * fits in the SM's opt-in shared memory.  Same results either way */
+ * fits in the SM's opt-in shared memory; 3 = through L1, each thread taking a column of four
+ * pixels of one 8 x 8 tile (they share the tile's radius, so their taps share texel rows).
+ * Same results either way */
 #define DOF_OPT_MAIN_FILTER_FORM    9
 /* block of the reconstruction's 81-tap gather, encoded as DOF_OPT_GATHER_BLOCK (default 32 x 8) */
 #define DOF_OPT_RECON_BLOCK         10

@@ -323,7 +323,7 @@ extern "C" int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value) {
             ctx->stack_depth = (int)value;
             return DOF_OK;
         case DOF_OPT_MAIN_FILTER_FORM:
-            if (value < 0 || value > 2) return dof_set_error(DOF_ERR_INVALID_ARG, "main filter form must be 0, 1 or 2");
+            if (value < 0 || value > 3) return dof_set_error(DOF_ERR_INVALID_ARG, "main filter form must be 0..3");
             ctx->main_form = (int)value;
             return DOF_OK;
         default:
@@ -722,7 +722,13 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
 
 static void shape_grid(const BatchArgs &A, const SessDesc &d, const DofHistory *h, int shape, int &gx, int &gy) {
     switch (shape) {
-        case SH_GATHER: gx = ((int)h->W2 + A.gather_w - 1) / A.gather_w; gy = ((int)h->H2 + A.gather_h - 1) / A.gather_h; break;
+        case SH_GATHER: {
+            // the column-strip form of the main filter: each thread takes four rows
+            const int rows = A.main_form == 3 ? 4 * A.gather_h : A.gather_h;
+            gx = ((int)h->W2 + A.gather_w - 1) / A.gather_w;
+            gy = ((int)h->H2 + rows - 1) / rows;
+            break;
+        }
         case SH_RECON: gx = ((int)h->W2 + A.recon_w - 1) / A.recon_w; gy = ((int)h->H2 + A.recon_h - 1) / A.recon_h; break;
         case SH_HPX: gx = ((int)h->W2 + 31) / 32; gy = ((int)h->H2 + 7) / 8; break;
         case SH_FPX: gx = ((int)h->W + 31) / 32; gy = ((int)h->H + 7) / 8; break;

@@ -67,10 +67,11 @@ __device__ __forceinline__ void bilinear4z(const float4 *__restrict__ img, const
     int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
     int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
     size_t qa = (size_t)ya * w, qb = (size_t)yb * w;
-    float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+    float w00 = __fmul_rn(1.f - fx, 1.f - fy), w10 = __fmul_rn(fx, 1.f - fy), w01 = __fmul_rn(1.f - fx, fy),
+          w11 = __fmul_rn(fx, fy);
     out = f4fma(w11, __ldg(&img[qb + xb]), f4fma(w01, __ldg(&img[qb + xa]),
                 f4fma(w10, __ldg(&img[qa + xb]), f4scale(w00, __ldg(&img[qa + xa])))));
-    zo = w00 * __ldg(&z[qa + xa]) + w10 * __ldg(&z[qa + xb]) + w01 * __ldg(&z[qb + xa]) + w11 * __ldg(&z[qb + xb]);
+    zo = fmaf(w11, __ldg(&z[qb + xb]), fmaf(w01, __ldg(&z[qb + xa]), fmaf(w10, __ldg(&z[qa + xb]), __fmul_rn(w00, __ldg(&z[qa + xa])))));
 }
 
 // Bilinear fetch of (rgb, rho) and z without clamping: the caller guarantees that
@@ -82,9 +83,10 @@ __device__ __forceinline__ void bilinear4z_interior(const float4 *__restrict__ i
     int q = __float2int_rz(yf) * w + __float2int_rz(xf);
     const float4 *p = img + q;
     const float *pz = z + q;
-    float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+    float w00 = __fmul_rn(1.f - fx, 1.f - fy), w10 = __fmul_rn(fx, 1.f - fy), w01 = __fmul_rn(1.f - fx, fy),
+          w11 = __fmul_rn(fx, fy);
     out = f4fma(w11, __ldg(p + w + 1), f4fma(w01, __ldg(p + w), f4fma(w10, __ldg(p + 1), f4scale(w00, __ldg(p)))));
-    zo = w00 * __ldg(pz) + w10 * __ldg(pz + 1) + w01 * __ldg(pz + w) + w11 * __ldg(pz + w + 1);
+    zo = fmaf(w11, __ldg(pz + w + 1), fmaf(w01, __ldg(pz + w), fmaf(w10, __ldg(pz + 1), __fmul_rn(w00, __ldg(pz)))));
 }
 
 __device__ __forceinline__ void cx4(float4 &a, float4 &b) {

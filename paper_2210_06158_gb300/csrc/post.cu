@@ -116,31 +116,48 @@ __global__ void __launch_bounds__(256) k_prefilter(const __grid_constant__ AS as
 // dilated max CoC R; foreground/background weights with the coverage ramp D and
 // sampleAlpha; normalised weighted sum plus the share of bright samples.  Blocks whose
 // whole footprint (+-rmax + 1) lies inside the image take taps without index clamping.
+// Accumulators of one pixel of the main filter.
+struct MainAcc {
+    float ax, ay, az, bright, wsum;
+};
+
+// One tap of the main filter: its bilinear sample s (rgb, signed CoC) and depth zi at
+// distance dist from the pixel (depth z0, |CoC| r0).  Every form of the filter adds its
+// taps through this one function.  Each rounding is written out (explicit FMAs, or
+// products and sums that the compiler may not contract), as are the tap positions and
+// depth sums in the callers, so that all forms give the same bits whatever the
+// surrounding code lets the compiler fuse.
+__device__ __forceinline__ void main_tap_add(const DevParams &p, float dist, float z0, float r0, float4 s, float zi,
+                                             MainAcc &m) {
+    const float ri = fabsf(s.w);
+    const float wf = sat(__fmul_rn(__fsub_rn(z0, zi), p.inv_depth_range));
+    const float rr = fmaxf(ri, p.inv_sqrt_area);
+    const float a = __fdividef(p.inv_area, __fmul_rn(rr, rr));
+    const float Df = sat(fmaf(__fsub_rn(ri, dist), p.inv_cover_ramp, 0.5f));
+    const float Db = sat(fmaf(__fsub_rn(fminf(ri, r0), dist), p.inv_cover_ramp, 0.5f));
+    const float W = __fmul_rn(fmaf(wf, Df, __fmul_rn(__fsub_rn(1.f, wf), Db)), a);
+    const float lum = fmaf(0.0722f, s.z, fmaf(0.7152f, s.y, __fmul_rn(0.2126f, s.x)));
+    m.ax = fmaf(W, s.x, m.ax);
+    m.ay = fmaf(W, s.y, m.ay);
+    m.az = fmaf(W, s.z, m.az);
+    m.bright = fmaf(W, sat(__fmul_rn(__fsub_rn(lum, p.bright_lum), p.inv_bright_ramp)), m.bright);
+    m.wsum = __fadd_rn(m.wsum, W);
+}
+
 template <bool CLAMP>
 __device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const DevParams &p, const float4 *__restrict__ pre,
-                                          const float *__restrict__ z_h, float R, float z0, float r0, float &ax,
-                                          float &ay, float &az, float &bright, float &wsum) {
-    const float kInvSqrtA = p.inv_sqrt_area, kInvA = p.inv_area;
+                                          const float *__restrict__ z_h, float R, float z0, float r0, MainAcc &m) {
     const int ring = p.ring;
 #pragma unroll 3
     for (int t = 0; t < 81; t++) {
-        float3 u = c_rings[ring][t];
-        float dist = u.z * R;
-        float x = i + dist * u.x, y = j + dist * u.y;
+        const float3 u = c_rings[ring][t];
+        const float dist = __fmul_rn(u.z, R);
+        const float x = fmaf(dist, u.x, (float)i), y = fmaf(dist, u.y, (float)j);
         float4 s;
         float zi;
         if (CLAMP) bilinear4z(pre, z_h, W2, H2, x, y, s, zi);
         else bilinear4z_interior(pre, z_h, W2, x, y, s, zi);
-        float ri = fabsf(s.w);
-        float wf = sat((z0 - zi) * p.inv_depth_range);
-        float rr = fmaxf(ri, kInvSqrtA);
-        float a = __fdividef(kInvA, rr * rr);
-        float Df = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
-        float Db = sat((fminf(ri, r0) - dist) * p.inv_cover_ramp + 0.5f);
-        float W = (wf * Df + (1.f - wf) * Db) * a;
-        ax += W * s.x; ay += W * s.y; az += W * s.z;
-        bright += W * sat((lum709(s.x, s.y, s.z) - p.bright_lum) * p.inv_bright_ramp);
-        wsum += W;
+        main_tap_add(p, dist, z0, r0, s, zi, m);
     }
 }
 
@@ -164,11 +181,114 @@ __global__ void __launch_bounds__(512) k_main_filter(const __grid_constant__ AS 
     float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
     float z0 = __ldg(&z_h[q]);
     float r0 = fabsf(__ldg(&pre[q]).w);
-    float ax = 0.f, ay = 0.f, az = 0.f, bright = 0.f, wsum = 0.f;
-    if (interior) main_taps<false>(i, j, W2, H2, p, pre, z_h, R, z0, r0, ax, ay, az, bright, wsum);
-    else main_taps<true>(i, j, W2, H2, p, pre, z_h, R, z0, r0, ax, ay, az, bright, wsum);
-    float r = 1.f / wsum;
-    st_img(out, q, make_float4(ax * r, ay * r, az * r, bright * r), p.f16);
+    MainAcc m{0.f, 0.f, 0.f, 0.f, 0.f};
+    if (interior) main_taps<false>(i, j, W2, H2, p, pre, z_h, R, z0, r0, m);
+    else main_taps<true>(i, j, W2, H2, p, pre, z_h, R, z0, r0, m);
+    float r = 1.f / m.wsum;
+    st_img(out, q, make_float4(m.ax * r, m.ay * r, m.az * r, m.bright * r), p.f16);
+}
+
+// A4 by columns of four pixels: R is the dilated maximum of the pixel's 8 x 8 tile, so
+// the four pixels (i, 4jt .. 4jt + 3) of one tile column take every tap at the same x
+// (same x weights) and, as long as floor(y + r) = floor(y) + r, at consecutive texel
+// rows.  The thread then reads the five rows y0 .. y0 + 4 once (two texels each) instead
+// of four rows pairs, and finishes pixel r when row r + 1 arrives; otherwise (the rare
+// tap whose rows are not consecutive in FP32) each pixel reads its own two rows.  Every
+// pixel sums its texels in the same order and with the same weights as the other forms.
+template <bool CLAMP>
+__device__ __forceinline__ void main_strip_taps(int i, int jb, int W2, int H2, const DevParams &p,
+                                                const float4 *__restrict__ pre, const float *__restrict__ z_h, float R,
+                                                const float *z0, const float *r0, MainAcc *m) {
+    const int ring = p.ring;
+#pragma unroll 1
+    for (int t = 0; t < 81; t++) {
+        const float3 u = c_rings[ring][t];
+        const float dist = __fmul_rn(u.z, R);
+        const float x = fmaf(dist, u.x, (float)i);
+        const float xf = floorf(x), fx = x - xf;
+        const int x0 = (int)xf;
+        float fy[4];
+        int y0[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const float y = fmaf(dist, u.y, (float)(jb + r));
+            const float yf = floorf(y);
+            fy[r] = y - yf;
+            y0[r] = (int)yf;
+        }
+        if (y0[1] == y0[0] + 1 && y0[2] == y0[0] + 2 && y0[3] == y0[0] + 3) {
+            const int xa = CLAMP ? min(max(x0, 0), W2 - 1) : x0, xb = CLAMP ? min(max(x0 + 1, 0), W2 - 1) : x0 + 1;
+            auto row = [&](int k, float4 &a, float4 &b, float &za, float &zb) {
+                const int y = CLAMP ? min(max(y0[0] + k, 0), H2 - 1) : y0[0] + k;
+                const size_t q = (size_t)y * W2;
+                a = __ldg(&pre[q + xa]); b = __ldg(&pre[q + xb]);
+                za = __ldg(&z_h[q + xa]); zb = __ldg(&z_h[q + xb]);
+            };
+            float4 a0, b0;
+            float za0, zb0;
+            row(0, a0, b0, za0, zb0);
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                float4 a1, b1;
+                float za1, zb1;
+                row(r + 1, a1, b1, za1, zb1);
+                const float w00 = __fmul_rn(1.f - fx, 1.f - fy[r]), w10 = __fmul_rn(fx, 1.f - fy[r]);
+                const float w01 = __fmul_rn(1.f - fx, fy[r]), w11 = __fmul_rn(fx, fy[r]);
+                const float4 s = f4fma(w11, b1, f4fma(w01, a1, f4fma(w10, b0, f4scale(w00, a0))));
+                const float zi = fmaf(w11, zb1, fmaf(w01, za1, fmaf(w10, zb0, __fmul_rn(w00, za0))));
+                main_tap_add(p, dist, z0[r], r0[r], s, zi, m[r]);
+                a0 = a1; b0 = b1; za0 = za1; zb0 = zb1;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const float y = fmaf(dist, u.y, (float)(jb + r));
+                float4 s;
+                float zi;
+                if (CLAMP) bilinear4z(pre, z_h, W2, H2, x, y, s, zi);
+                else bilinear4z_interior(pre, z_h, W2, x, y, s, zi);
+                main_tap_add(p, dist, z0[r], r0[r], s, zi, m[r]);
+            }
+        }
+    }
+}
+
+template <class AS>
+__global__ void __launch_bounds__(512) k_main_filter_strip(const __grid_constant__ AS as_) {
+    const BatchArgs &A = batch_args(as_);
+    int i, jt;
+    const SessDesc &S = block_session(A, SH_GATHER, i, jt);
+    const DevParams &p = S.p;
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float4 *__restrict__ pre = S.pre;
+    const float *__restrict__ z_h = S.z_h;
+    const float2 *__restrict__ dil = S.tiles_dil;
+    float4 *out = S.main_;
+    const int reach = (int)ceilf(p.rmax_hpx) + 2;
+    const int jb = 4 * jt;
+    const int bx = i - (int)threadIdx.x, by = 4 * (jt - (int)threadIdx.y);
+    const bool interior = bx - reach >= 0 && by - reach >= 0 && bx + (int)blockDim.x + reach < W2 &&
+                          by + 4 * (int)blockDim.y + reach < H2;
+    if (i >= W2 || jb >= H2) return;
+    const float R = __ldg(&dil[(jb >> 3) * p.tiles_w + (i >> 3)]).y;
+    float z0[4], r0[4];
+    MainAcc m[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const size_t q = (size_t)min(jb + r, H2 - 1) * W2 + i;
+        z0[r] = __ldg(&z_h[q]);
+        r0[r] = fabsf(__ldg(&pre[q]).w);
+        m[r] = MainAcc{0.f, 0.f, 0.f, 0.f, 0.f};
+    }
+    if (interior) main_strip_taps<false>(i, jb, W2, H2, p, pre, z_h, R, z0, r0, m);
+    else main_strip_taps<true>(i, jb, W2, H2, p, pre, z_h, R, z0, r0, m);
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        if (jb + r >= H2) break;
+        const float rw = 1.f / m[r].wsum;
+        st_img(out, (size_t)(jb + r) * W2 + i, make_float4(m[r].ax * rw, m[r].ay * rw, m[r].az * rw, m[r].bright * rw),
+               p.f16);
+    }
 }
 
 // A4 with the block's neighbourhood staged in shared memory: the block's pixels (the
@@ -214,34 +334,25 @@ __global__ void __launch_bounds__(512) k_main_filter_tiled(const __grid_constant
     const float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
     const float z0 = __ldg(&z_h[q]);
     const float r0 = fabsf(__ldg(&pre[q]).w);
-    const float kInvSqrtA = p.inv_sqrt_area, kInvA = p.inv_area;
     const int ring = p.ring;
-    float ax = 0.f, ay = 0.f, az = 0.f, bright = 0.f, wsum = 0.f;
+    MainAcc m{0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 3
     for (int t = 0; t < 81; t++) {
         const float3 u = c_rings[ring][t];
-        const float dist = u.z * R;
-        const float x = i + dist * u.x, y = j + dist * u.y;
+        const float dist = __fmul_rn(u.z, R);
+        const float x = fmaf(dist, u.x, (float)i), y = fmaf(dist, u.y, (float)j);
         const float xf = floorf(x), yf = floorf(y);
         const float fx = x - xf, fy = y - yf;
         const int b = ((int)yf - oy) * tw + ((int)xf - ox);
-        const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+        const float w00 = __fmul_rn(1.f - fx, 1.f - fy), w10 = __fmul_rn(fx, 1.f - fy);
+        const float w01 = __fmul_rn(1.f - fx, fy), w11 = __fmul_rn(fx, fy);
         const float4 s = f4fma(w11, sm_pre[b + tw + 1], f4fma(w01, sm_pre[b + tw], f4fma(w10, sm_pre[b + 1],
                                f4scale(w00, sm_pre[b]))));
-        const float zi = w00 * sm_z[b] + w10 * sm_z[b + 1] + w01 * sm_z[b + tw] + w11 * sm_z[b + tw + 1];
-        const float ri = fabsf(s.w);
-        const float wf = sat((z0 - zi) * p.inv_depth_range);
-        const float rr = fmaxf(ri, kInvSqrtA);
-        const float a = __fdividef(kInvA, rr * rr);
-        const float Df = sat((ri - dist) * p.inv_cover_ramp + 0.5f);
-        const float Db = sat((fminf(ri, r0) - dist) * p.inv_cover_ramp + 0.5f);
-        const float W = (wf * Df + (1.f - wf) * Db) * a;
-        ax += W * s.x; ay += W * s.y; az += W * s.z;
-        bright += W * sat((lum709(s.x, s.y, s.z) - p.bright_lum) * p.inv_bright_ramp);
-        wsum += W;
+        const float zi = fmaf(w11, sm_z[b + tw + 1], fmaf(w01, sm_z[b + tw], fmaf(w10, sm_z[b + 1], __fmul_rn(w00, sm_z[b]))));
+        main_tap_add(p, dist, z0, r0, s, zi, m);
     }
-    const float r = 1.f / wsum;
-    st_img(out, q, make_float4(ax * r, ay * r, az * r, bright * r), p.f16);
+    const float r = 1.f / m.wsum;
+    st_img(out, q, make_float4(m.ax * r, m.ay * r, m.az * r, m.bright * r), p.f16);
 }
 
 // A5: per-channel 3x3 median (clamp-to-edge).  The block's 34x10 neighbourhood is
@@ -329,7 +440,7 @@ static int smem_optin_bytes() {
 // form through L1 runs: always for form 1, else when a session's halo tile exceeds the
 // form's limit (64 KB for form 0, the SM's opt-in shared memory for form 2).
 int main_filter_tile_bytes(const BatchArgs &A) {
-    if (A.main_form == 1) return 0;
+    if (A.main_form == 1 || A.main_form == 3) return 0;
     int bytes = 0;
     for (int s = 0; s < A.ns; s++) bytes = max(bytes, main_tile_bytes(A.s[s].p.rmax_hpx, A.gather_w, A.gather_h));
     const int limit = A.main_form == 2 ? smem_optin_bytes() : kMainTileAutoBytes;
@@ -351,6 +462,8 @@ void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *
             attr_set = true;
         }
         k_main_filter_tiled<AS><<<A.start[SH_GATHER][n], gb, tile_bytes, st>>>(as);
+    } else if (A.main_form == 3) {
+        k_main_filter_strip<AS><<<A.start[SH_GATHER][n], gb, 0, st>>>(as);
     } else {
         k_main_filter<AS><<<A.start[SH_GATHER][n], gb, 0, st>>>(as);
     }

@@ -251,7 +251,7 @@ class Context:
         (reconstruction) = (width, height) in half-resolution pixels (width >= 8, whole
         warps, 64..512 threads) -- and the main filter's form: 0 = halo tile in shared
         memory when it fits in 64 KB, 1 = through L1, 2 = halo tile up to the SM's opt-in
-        shared memory (no effect on results)."""
+        shared memory, 3 = through L1 by columns of four pixels (no effect on results)."""
         for opt, b in ((8, block), (10, recon_block)):
             if b is not None:
                 w, h = (int(v) for v in b)

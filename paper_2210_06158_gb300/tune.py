@@ -89,7 +89,7 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None):
 
 GATHER_SPACE = {
     "gather_block": [(32, 8), (16, 16), (64, 4), (32, 16), (64, 8)],
-    "main_form": [0, 1, 2],
+    "main_form": [0, 1, 2, 3],
     "recon_block": [(32, 8), (16, 16), (64, 4), (32, 16), (64, 8)],
 }
 GATHER_DEFAULT = {"gather_block": (32, 8), "main_form": 0, "recon_block": (32, 8)}
@@ -98,7 +98,8 @@ GATHER_DEFAULT = {"gather_block": (32, 8), "main_form": 0, "recon_block": (32, 8
 def tune_gathers(ctx, run_frame, frames=4, rounds=2, stream=None):
     """The 81-tap gathers' launch shapes (block of the main filter, block of the
     reconstruction) and the main filter's form (halo tile in shared memory up to 64 KB,
-    through L1, or halo tile up to the SM's opt-in shared memory): coordinate descent
+    through L1, halo tile up to the SM's opt-in shared memory, or columns of four pixels
+    through L1): coordinate descent
     over GATHER_SPACE from GATHER_DEFAULT with the same timing rules as tune_trace.
     Returns (best settings, {settings tuple: ms per frame}); the context keeps the best."""
     import torch

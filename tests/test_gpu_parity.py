@@ -402,10 +402,10 @@ def test_checkpoint_resume_bit_identical():
 def test_scheduling_knobs_do_not_change_results(name, W, H):
     """The autotuned knobs change only speed: the tracer's work order (lens-cell grid 1
     = pixel order, 2 .. 16), its traversal stack, warp packets instead of one ray per
-    lane, the gathers' block shapes and the main filter's form (shared-memory halo tile
-    or L1) give bit-identical hit ids, intermediates and images over two frames of a
-    moving camera (the c3 crop with its 64 px clamp takes the halo tile only in the
-    opt-in form)."""
+    lane, the gathers' block shapes and the main filter's form (shared-memory halo tile,
+    L1, or columns of four pixels through L1) give bit-identical hit ids, intermediates
+    and images over two frames of a moving camera (the c3 crop with its 64 px clamp
+    takes the halo tile only in the opt-in form)."""
     from paper_2210_06158_gb300 import dof
     import torch
     dev = torch.device("cuda", 0)
@@ -423,7 +423,8 @@ def test_scheduling_knobs_do_not_change_results(name, W, H):
                 dict(ray_grid=1, packets=1), dict(ray_grid=4, packets=1), dict(ray_grid=8, packets=1, stack=32),
                 dict(block=(16, 16), main_form=0, recon=(16, 16)), dict(block=(64, 4), main_form=1, recon=(64, 8)),
                 dict(block=(32, 16), main_form=2, recon=(32, 16)), dict(block=(64, 8), main_form=2, recon=(64, 4)),
-                dict(block=(32, 8), main_form=1, recon=(8, 32))]
+                dict(block=(32, 8), main_form=1, recon=(8, 32)), dict(block=(32, 8), main_form=3),
+                dict(block=(64, 4), main_form=3, recon=(16, 16)), dict(block=(16, 8), main_form=3)]
     results = []
     for v in variants:
         ctx.set_trace(ray_grid=v.get("ray_grid", 4), stack=v.get("stack", 96), packets=v.get("packets", 0))
