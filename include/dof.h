@@ -353,7 +353,8 @@ int dof_frame_stats(DofHistory *hist, void *stream, DofFrameStats *out);
 
 /* Timing slots of one frame, in launch order (DOF_HIST_TIMING brackets each with events).
  * DILATE, VAR_BLUR and MIPS are fused into PREFILTER / MASK, MEDIAN_RT and MEDIAN_RT
- * respectively: their slots bracket no kernel and count 0. */
+ * respectively: their slots bracket no kernel and count 0.  TRACE times whichever tracer
+ * runs (one ray per lane, or warp packets with DOF_OPT_TRACE_PACKETS). */
 enum {
     DOF_K_DOWNSCALE = 0, DOF_K_DILATE, DOF_K_PREFILTER, DOF_K_MAIN, DOF_K_MEDIAN_PP, DOF_K_EDGES,
     DOF_K_MASK, DOF_K_TRACE, DOF_K_SHADE, DOF_K_ACCUM, DOF_K_VAR_BLUR, DOF_K_MEDIAN_RT, DOF_K_MIPS,

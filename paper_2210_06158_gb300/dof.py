@@ -25,6 +25,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "BUDGET", -4: "CUDA", -5: "TIMEOUT",
 DOF_HIST_RECORD_RAYS = 1
 DOF_HIST_TIMING = 2
 DOF_HIST_TAA = 4
+# timing slots (dof_kernel_times), named after the kernels they bracket; k_trace_rays
+# times whichever tracer runs, and the fused slots (dilate, variance blur, mips) read 0
 KERNELS = ["k_downscale_tiles", "k_tile_dilate", "k_prefilter", "k_main_filter", "k_median_pp", "k_edges",
            "k_mask_compact", "k_trace_rays", "k_shade", "k_accumulate", "k_var_blur", "k_median_rt", "k_mips", "k_recon",
            "k_composite", "k_taa"]
