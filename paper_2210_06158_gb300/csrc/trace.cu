@@ -1,7 +1,8 @@
 // Ray side of libdof: G-buffer producer (pinhole primary visibility), ray mask with
 // warp-aggregated compaction into a ray queue (Section 3.2.1, Eq. 2-4), and the
-// persistent thin-lens ray kernel (Section 3.2.2): Philox lens samples, closest hit
-// through the LBVH, Lambert shading and the per-pixel near/far split.
+// persistent thin-lens ray kernels (Section 3.2.2): Philox lens samples, closest hit
+// through the device BVH (one ray per lane, or the 32 rays of a warp as one packet),
+// Lambert shading and the per-pixel near/far split.
 #include "batch.cuh"
 #include "geometry.cuh"
 
