@@ -33,6 +33,17 @@ DEFAULT = {"bvh_width": 4, "ray_grid": 4, "stack": 96, "blocks_per_sm": 8, "refi
            "packets": 0}
 
 
+def _warm(run_frame, frames, st):
+    """Frames 0 .. frames - 1 untimed, so that the session's history is in its steady
+    state before any candidate is timed (in the adaptive mode of Eq. 4 the first frames
+    of a fresh history trace fewer rays)."""
+    for f in range(frames):
+        run_frame(f)
+    sync = getattr(st, "synchronize", None)
+    if sync is not None:
+        sync()
+
+
 def _time_frames(run_frame, frames, st):
     """Warm-up frame 0, then the CUDA-event time of frames 0 .. frames - 1 (ms per frame)."""
     import torch
@@ -68,6 +79,7 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None):
         seen[key] = _time_frames(run_frame, frames, st)
         return seen[key]
 
+    _warm(run_frame, frames, st)
     best_ms = measure(best)
     for _ in range(rounds):
         improved = False
@@ -118,6 +130,7 @@ def tune_gathers(ctx, run_frame, frames=4, rounds=2, stream=None):
         seen[key] = _time_frames(run_frame, frames, st)
         return seen[key]
 
+    _warm(run_frame, frames, st)
     best_ms = measure(best)
     for _ in range(rounds):
         improved = False
@@ -154,6 +167,8 @@ def tune_scene(ctx, host_scene, run_frame, radii=None, widths=(4, 2), frames=4, 
     for r in (radii or SCENE_RADII):
         ctx.set_ploc_radius(r)
         sc = dof.Scene(ctx, host_scene)
+        if not seen:
+            _warm(lambda f: run_frame(sc, f), frames, st)
         for wdt in widths:
             ctx.set_bvh_width(wdt)
             ms = _time_frames(lambda f: run_frame(sc, f), frames, st)

@@ -140,9 +140,11 @@ def test_tune_trace_times_every_candidate_on_the_same_frames(monkeypatch):
         clock.t += 1.0 + 0.1 * k       # later frames cost more
 
     tune.tune_trace(ctx, run_frame, frames=3, stream=types.SimpleNamespace())
-    assert len(calls) % 4 == 0
-    for m in range(len(calls) // 4):
-        assert calls[4 * m:4 * m + 4] == [0, 0, 1, 2]   # warm-up, then frames 0 .. 2
+    assert calls[:3] == [0, 1, 2]                        # the session warmed up once
+    timed = calls[3:]
+    assert len(timed) % 4 == 0
+    for m in range(len(timed) // 4):
+        assert timed[4 * m:4 * m + 4] == [0, 0, 1, 2]   # warm-up, then frames 0 .. 2
 
 
 def test_tune_trace_rejects_a_win_that_a_second_timing_does_not_confirm(monkeypatch):
@@ -226,3 +228,21 @@ def test_tune_trace_reports_packets_with_the_binary_tree(monkeypatch):
     best, seen = tune.tune_trace(ctx, run_frame, frames=2, stream=types.SimpleNamespace())
     assert best["packets"] == 1 and best["bvh_width"] == 2
     assert all(dict(k)["bvh_width"] == 2 for k in seen if dict(k)["packets"])
+
+
+def test_tune_trace_is_not_fooled_by_a_warming_session(monkeypatch):
+    """A fresh session's first frames can be cheaper (adaptive ray counts start from an
+    empty history): the tuner warms the session up before it times the incumbent, so the
+    optimum still wins."""
+    clock = _Clock()
+    _fake_cuda(monkeypatch, clock)
+    ctx = _Ctx()
+    calls = [0]
+
+    def run_frame(k):
+        calls[0] += 1
+        clock.t += _cost(ctx.cfg) * (0.4 if calls[0] <= 4 else 1.0)
+
+    best, _ = tune.tune_trace(ctx, run_frame, frames=3, stream=types.SimpleNamespace())
+    assert best == {"bvh_width": 2, "ray_grid": 8, "stack": 64, "blocks_per_sm": 6, "refill_idle": 12, "steps": 32,
+                    "packets": 1}
