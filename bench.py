@@ -799,6 +799,10 @@ def run_serve(args):
                                poses=w.poses, intr=w.intr)
         srv.admit(k, specs[k])
     setup_s = time.time() - t0
+    # start-up: the tracer's settings tuned on batched steps of the admitted sessions
+    t1 = time.time()
+    tracer = ex.tune()
+    tracer = dict(tracer, tune_s=round(time.time() - t1, 2))
     admitted = {k: v for k, v in specs.items() if k in srv.specs}
     nominal = {k: v.fps for k, v in admitted.items()}
     offered_nominal = sum(nominal.values())
@@ -843,6 +847,7 @@ def run_serve(args):
     torch.cuda.synchronize()
     # admission under a budget that binds: 8 GB admits only part of the 64 sessions
     ex8 = GpuExecutor(budget_bytes=8 << 30, gbuf_ring=2)
+    ex8.ctx.set_trace(**{k: v for k, v in tracer.items() if k != "tune_s"})
     srv8 = Server(ex8, max_batch=32)
     specs8 = {k: SessionSpec(f"s{k}", w.W, w.H, 30.0 if k % 2 == 0 else 60.0, scene=w.scene, params=w.params,
                              poses=w.poses, intr=w.intr) for k, w in enumerate(ws)}
@@ -863,7 +868,7 @@ def run_serve(args):
                 config=dict(workload="serving: 64 sessions, Poisson frame requests (nominal 30/60 fps), "
                                      f"{duration:g} s per point, 1280x720..3840x2160, lawn scenes 100k-2M "
                                      "triangles, 40 GB device budget, continuous batching (<= 32 per launch, "
-                                     "2 streams)"),
+                                     "2 streams)", tracer=tracer),
                 served=dict(p50_ms_at_half_load=half["p50_ms"], p99_ms_at_half_load=half["p99_ms"],
                             admitted=len(admitted), rejected=n_rejected),
                 forms=out, budget_8gb=budget8, setup_s=round(setup_s, 1), clocks=clk.summary(),

@@ -226,6 +226,9 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->ploc_radius = 48;
     c->bvh_width = 4;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    preload_trace_kernels();
+    preload_post_kernels();
+    preload_recon_kernels();
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();

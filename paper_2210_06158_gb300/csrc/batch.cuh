@@ -141,6 +141,9 @@ int main_filter_tile_bytes(const BatchArgs &A);   // the main filter's launch fo
 template <class AS>
 void launch_mask_b(const BatchArgs &A, const AS &as, bool any_adaptive, cudaStream_t st, DofHistory *timing);
 template <class AS> void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t st, DofHistory *timing);
+void preload_trace_kernels();
+void preload_post_kernels();
+void preload_recon_kernels();
 template <class AS> void launch_temporal_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);
 template <class AS> void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A10, A11
 template <class AS> void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *timing);  // A12

@@ -447,6 +447,18 @@ int main_filter_tile_bytes(const BatchArgs &A) {
     return bytes <= limit ? bytes : 0;
 }
 
+// the main filter's forms loaded now (which one runs depends on the batch's radii)
+void preload_post_kernels() {
+    cudaFuncAttributes a;
+    cudaFuncGetAttributes(&a, k_main_filter<BatchArgs>);
+    cudaFuncGetAttributes(&a, k_main_filter_tiled<BatchArgs>);
+    cudaFuncGetAttributes(&a, k_main_filter_strip<BatchArgs>);
+    cudaFuncGetAttributes(&a, k_main_filter<const BatchArgs *>);
+    cudaFuncGetAttributes(&a, k_main_filter_tiled<const BatchArgs *>);
+    cudaFuncGetAttributes(&a, k_main_filter_strip<const BatchArgs *>);
+    cudaGetLastError();
+}
+
 template <class AS>
 void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *tm) {
     const int n = A.ns;

@@ -932,5 +932,29 @@ void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t s
 // the two argument forms: by value (a kernel parameter) and from device memory (graphs)
 template void launch_mask_b<BatchArgs>(const BatchArgs &, const BatchArgs &, bool, cudaStream_t, DofHistory *);
 template void launch_mask_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, bool, cudaStream_t, DofHistory *);
+// Every tracer instance and the adaptive-mode kernels loaded on the current device now
+// (with lazy module loading a kernel is otherwise loaded at its first launch: a batch
+// whose trees need another stack capacity, or the first adaptive session, would stall a
+// frame on the load).
+void preload_trace_kernels() {
+    cudaFuncAttributes a;
+#define DOF_PRELOAD(AS)                                                        \
+    cudaFuncGetAttributes(&a, k_trace_packets<32, AS>);                        \
+    cudaFuncGetAttributes(&a, k_trace_packets<64, AS>);                        \
+    cudaFuncGetAttributes(&a, k_trace_packets<kStack, AS>);                    \
+    cudaFuncGetAttributes(&a, k_trace_rays<true, 32, AS>);                     \
+    cudaFuncGetAttributes(&a, k_trace_rays<true, 64, AS>);                     \
+    cudaFuncGetAttributes(&a, k_trace_rays<true, kStack, AS>);                 \
+    cudaFuncGetAttributes(&a, k_trace_rays<false, 32, AS>);                    \
+    cudaFuncGetAttributes(&a, k_trace_rays<false, 64, AS>);                    \
+    cudaFuncGetAttributes(&a, k_trace_rays<false, kStack, AS>);                \
+    cudaFuncGetAttributes(&a, k_blur_zn<AS>);                                  \
+    cudaFuncGetAttributes(&a, k_edges<AS>);
+    DOF_PRELOAD(BatchArgs)
+    DOF_PRELOAD(const BatchArgs *)
+#undef DOF_PRELOAD
+    cudaGetLastError();
+}
+
 template void launch_trace_b<BatchArgs>(const BatchArgs &, const BatchArgs &, int, cudaStream_t, DofHistory *);
 template void launch_trace_b<const BatchArgs *>(const BatchArgs &, const BatchArgs *const &, int, cudaStream_t, DofHistory *);

@@ -170,6 +170,28 @@ class GpuExecutor:
                                   pstruct=dof.params_struct(prm))
         torch.cuda.synchronize()
 
+    def tune(self, frames=2, max_batch=32):
+        """Autotune the tracer (tune.tune_trace) on batched steps of the admitted sessions
+        (up to max_batch of them, one frame each), as a server does at start-up; the
+        context keeps the pick and every history starts afresh.  Returns the pick."""
+        from . import tune
+        sids = list(self.sessions)[:max_batch]
+        st = self.streams[0]
+
+        def step(k):
+            items = []
+            for sid in sids:
+                s = self.sessions[sid]
+                items.append(dict(scene=s["scene"], gbuf=s["gbs"][k % self.ring], cam=self.camera(s, k),
+                                  params=s["pstruct"], hist=s["hist"], out=s["out"]))
+            self.dof.batch_frame(self.ctx, items, stream=st)
+
+        best, _ = tune.tune_trace(self.ctx, step, frames=frames, stream=st)
+        self.torch.cuda.synchronize()
+        for s in self.sessions.values():
+            s["hist"].reset()
+        return best
+
     def set_form(self, per_frame=False, fp16=False):
         """Switch every admitted session to the given form (batched or per-frame, FP16 or
         FP32 image storage) and start its history afresh."""

@@ -1,6 +1,6 @@
 """Served frames (continuous batching over dof_batch_frame, two streams) equal the
-frames of each session run alone: every served frame, in the batched FP32 form and in
-the batched FP16-storage form."""
+frames of each session run alone: every served frame, in the batched FP32 form (with
+the tracer tuned at start-up) and in the batched FP16-storage form."""
 
 import pytest
 
@@ -24,6 +24,9 @@ def test_every_served_frame_equals_alone(fp16):
         poses = w.poses if len(w.poses) >= 3 else w.poses * 3
         specs[k] = SessionSpec(name, W, H, fps, scene=w.scene, params=dict(w.params), poses=poses, intr=w.intr)
         assert srv.admit(k, specs[k])
+    if not fp16:
+        pick = ex.tune(frames=1)                  # start-up tuning (histories start afresh)
+        assert set(pick) >= {"bvh_width", "ray_grid", "packets"}
     st = srv.run(poisson_arrivals(5, specs, duration_s=0.5))
     assert st["frames"] > 10 and st["failed"] == 0
     assert st["mean_batch"] > 1.0                 # requests did share launches
