@@ -45,6 +45,18 @@ C3_STEPS = 32        # timed 4K frames of the default run's c3 sub-record
 # 1 division -> 48.  Warp packets (k_trace_packets) count, per lane, every binary node
 # and triangle its lane tested: the union of the warp's rays' nodes.
 FLOP_PER_NODE = {2: 47.0, 4: 97.0}
+# The 81-tap gathers are bound by issue slots and L1 together; their roofline, when one of
+# them is the frame's dominant kernel, counts FP32 operations (FMA = 2) per pixel that takes
+# taps against the FP32 peak.
+# * Main filter (every hpx N), per tap: position 5 (product, 2 FMA), fractions 2, weights 6,
+#   sample 4 texels x 4 channels FMA = 32, depth 8, weight W 14 (difference, product,
+#   max, reciprocal-multiply, 2 coverage FMA, 3 clamps as 6 min/max, blend), 4 colour and
+#   1 bright accumulation FMA = 10, luminance 5 -> 82.
+# * Reconstruction (hpx with rays M; the Eq. 5 blend below 2^-24 skips its taps, so this
+#   is an upper bound of the work), per tap: position 5, per level (two levels) fractions
+#   2 + weights 7 + 4 texels x (4 colour + 2 coverage) FMA = 48 -> 57 x 2 = 114, coverage
+#   ratio 1, weight D 4, 4 + 1 accumulation FMA = 10 -> 134.
+FLOP_PER_GATHER = {"k_main_filter": ("N", 81 * 82.0), "k_recon": ("M", 81 * 134.0)}
 FLOP_PER_TRI = 48.0
 FP32_LANES_PER_SM = 128
 
@@ -523,6 +535,15 @@ def run_ours(args, rank, world):
                 "peak_source": f"derived: 2 x {FP32_LANES_PER_SM} FP32 lanes x {n_sm} SMs x {sm_mhz:.0f} MHz",
                 "algorithmic_flop": int(trace_flop), "node_visits_per_ray": round(visits / max(1, rays), 2),
                 "tri_tests_per_ray": round(tests / max(1, rays), 2)}
+    elif dom in FLOP_PER_GATHER and kavg[dom] > 0:
+        unit, per = FLOP_PER_GATHER[dom]
+        flop = per * units[unit]
+        achieved = flop / (kavg[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": traffic,
+                "peak_source": f"derived: 2 x {FP32_LANES_PER_SM} FP32 lanes x {n_sm} SMs x {sm_mhz:.0f} MHz",
+                "algorithmic_flop": int(flop),
+                "note": "81-tap gather, bound by issue slots and L1 together: FP32 operations counted per tap"}
     elif dom in BYTES:
         algo = algo_bytes(dom, units)
         achieved = algo / (kavg[dom] * 1e-3) / 1e9

@@ -18,6 +18,7 @@ the cost on a virtual clock (host-only tests of the scheduling logic).
 from __future__ import annotations
 
 import collections
+import gc
 import math
 import time
 from dataclasses import dataclass, field
@@ -278,6 +279,18 @@ class Server:
         """Serve `arrivals` (list of (time_s, session id), sorted by time, times relative
         to the start of the run) to completion.  Returns the statistics: frames, dropped,
         failed, p50/p99 latency (ms), frames/s, and per-session completed frame numbers."""
+        # no cyclic garbage collection while serving: a full pass over the process's
+        # objects can hold the loop for tens of milliseconds and lands in the tail latency
+        gc_was_on = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            return self._run(arrivals)
+        finally:
+            if gc_was_on:
+                gc.enable()
+
+    def _run(self, arrivals):
         base = self.ex.clock()
         arrivals = collections.deque((t + base, sid) for t, sid in arrivals if sid in self.specs)
         pending = collections.OrderedDict()     # session -> Request (newest only)
