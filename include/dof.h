@@ -195,6 +195,10 @@ size_t dof_ctx_bytes_in_use(const DofCtx *ctx);
  * testing with its own ray and best hit); packets always traverse the binary tree, whatever
  * DOF_OPT_BVH_WIDTH says.  Same hits either way */
 #define DOF_OPT_TRACE_PACKETS       12
+/* passes of tree rotations after the BVH build of scenes uploaded afterwards, 0..16
+ * (default 0): each swaps, bottom-up, a child with a grandchild where that shrinks the
+ * child's box.  Same hits either way */
+#define DOF_OPT_BVH_ROTATIONS       13
 int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value);
 
 /* Fill `p` with the defaults above (1 spp fixed mode, 16 px radius clamp). */

@@ -225,6 +225,7 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->main_form = 0;
     c->ploc_radius = 48;
     c->bvh_width = 4;
+    c->bvh_rotations = 0;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     preload_trace_kernels();
     preload_post_kernels();
@@ -305,6 +306,10 @@ extern "C" int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value) {
         case DOF_OPT_TRACE_PACKETS:
             if (value != 0 && value != 1) return dof_set_error(DOF_ERR_INVALID_ARG, "trace packets must be 0 or 1");
             ctx->trace_packets = (int)value;
+            return DOF_OK;
+        case DOF_OPT_BVH_ROTATIONS:
+            if (value < 0 || value > 16) return dof_set_error(DOF_ERR_INVALID_ARG, "BVH rotation passes must be 0..16");
+            ctx->bvh_rotations = (int)value;
             return DOF_OK;
         case DOF_OPT_GATHER_BLOCK:
         case DOF_OPT_RECON_BLOCK: {
@@ -389,7 +394,7 @@ extern "C" int dof_scene_upload(DofCtx *ctx, const float *xyz, uint32_t n_verts,
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_xyz, xyz, sizeof(float) * 3 * (size_t)n_verts, cudaMemcpyHostToDevice, st), "upload");
     if (rc == DOF_OK) rc = dof_cuda_check(cudaMemcpyAsync(d_idx, tri_idx, sizeof(uint32_t) * 3 * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
     if (rc == DOF_OK && tri_mat) rc = dof_cuda_check(cudaMemcpyAsync(d_mat, tri_mat, sizeof(uint32_t) * (size_t)n_tris, cudaMemcpyHostToDevice, st), "upload");
-    if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, ctx->bvh_builder, ctx->ploc_radius, st);
+    if (rc == DOF_OK) rc = launch_bvh_build(s, d_xyz, n_verts, d_idx, d_mat, ctx->bvh_builder, ctx->ploc_radius, ctx->bvh_rotations, st);
     if (rc == DOF_OK) {
         launch_prim_index(s->tris, (int)n_tris, s->prim_k, st);
         rc = dof_cuda_check(cudaStreamSynchronize(st), "scene triangle index");

@@ -227,6 +227,139 @@ __global__ void k_refit(const float4 *tris, int n, const int4 *child, const int 
     }
 }
 
+// half the surface area of a box
+__device__ __forceinline__ float half_area(float4 lo, float4 hi) {
+    float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// Tree rotations (Kensler, "Tree Rotations for Improving Bounding Volume Hierarchies",
+// 2008), one bottom-up pass synchronised like the refit: at each internal node p with
+// children L and R, swapping R with a child of L (or L with a child of R) changes the
+// box of one child only, so the swap that shrinks that child's surface area the most is
+// made, when it shrinks it by more than 2^-16 of p's area.  Every subtree keeps its
+// leaves and every box is the exact union of its children's, so the closest hit of a ray
+// is unchanged; the parents of the two moved subtrees are updated.
+__device__ __forceinline__ void node_child(const BvhNode &nd, int c, float4 &lo, float4 &hi, int &ref) {
+    if (c == 0) {
+        lo = make_float4(nd.a.x, nd.a.y, nd.a.z, 0.f); hi = make_float4(nd.a.w, nd.b.x, nd.b.y, 0.f); ref = nd.r.x;
+    } else {
+        lo = make_float4(nd.b.z, nd.b.w, nd.c.x, 0.f); hi = make_float4(nd.c.y, nd.c.z, nd.c.w, 0.f); ref = nd.r.y;
+    }
+}
+
+__device__ __forceinline__ BvhNode make_node(float4 l0, float4 h0, int r0, float4 l1, float4 h1, int r1) {
+    BvhNode nd;
+    nd.a = make_float4(l0.x, l0.y, l0.z, h0.x);
+    nd.b = make_float4(h0.y, h0.z, l1.x, l1.y);
+    nd.c = make_float4(l1.z, h1.x, h1.y, h1.z);
+    nd.r = make_int4(r0, r1, 0, 0);
+    return nd;
+}
+
+__device__ __forceinline__ float union_area(float4 l0, float4 h0, float4 l1, float4 h1) {
+    return half_area(make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f),
+                     make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f));
+}
+
+__device__ __forceinline__ void set_parent(int ref, int p, int n, int *parent_node, int *parent_leaf, int *bad) {
+    if (ref < 0 ? ~ref >= n : ref >= n - 1) { atomicExch(bad, 7); return; }
+    if (ref < 0) parent_leaf[~ref] = p;
+    else parent_node[ref] = p;
+}
+
+// a node as other threads of the pass last wrote it (from L2, not a stale L1 line)
+__device__ __forceinline__ BvhNode ld_node_cg(const BvhNode *nd) {
+    const float4 *q = reinterpret_cast<const float4 *>(nd);
+    BvhNode o;
+    o.a = __ldcg(q);
+    o.b = __ldcg(q + 1);
+    o.c = __ldcg(q + 2);
+    o.r = __ldcg(reinterpret_cast<const int4 *>(q + 3));
+    return o;
+}
+
+__global__ void k_rotate(int n, BvhNode *nodes, int *parent_node, int *parent_leaf, int *arrivals, int *bad) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int p = __ldcg(&parent_leaf[k]);
+    for (int level = 0; p >= 0; level++) {
+        if (p >= n - 1 || level > 160) { atomicExch(bad, 7); return; }
+        __threadfence();
+        if (atomicAdd(&arrivals[p], 1) == 0) return;   // the sibling finishes this node
+        __threadfence();
+        const BvhNode np = ld_node_cg(&nodes[p]);
+        float4 lL, hL, lR, hR;
+        int L, R;
+        node_child(np, 0, lL, hL, L);
+        node_child(np, 1, lR, hR, R);
+        const float areaL = half_area(lL, hL), areaR = half_area(lR, hR);
+        const float thresh = union_area(lL, hL, lR, hR) * (1.f / 65536.f);
+        float best = thresh;
+        int kind = -1;                      // 0, 1: R with a child of L; 2, 3: L with a child of R
+        BvhNode nL, nR;
+        float4 la, ha, lb, hb, lc, hc, ld, hd;
+        int ra = 0, rb = 0, rc = 0, rd = 0;
+        if (L >= 0) {
+            if (L >= n - 1) { atomicExch(bad, 7); return; }
+            nL = ld_node_cg(&nodes[L]);
+            node_child(nL, 0, la, ha, ra);
+            node_child(nL, 1, lb, hb, rb);
+            const float g0 = areaL - union_area(lR, hR, lb, hb);   // R <-> LL: L = (R, LR)
+            const float g1 = areaL - union_area(la, ha, lR, hR);   // R <-> LR: L = (LL, R)
+            if (g0 > best) { best = g0; kind = 0; }
+            if (g1 > best) { best = g1; kind = 1; }
+        }
+        if (R >= 0) {
+            if (R >= n - 1) { atomicExch(bad, 7); return; }
+            nR = ld_node_cg(&nodes[R]);
+            node_child(nR, 0, lc, hc, rc);
+            node_child(nR, 1, ld, hd, rd);
+            const float g2 = areaR - union_area(lL, hL, ld, hd);   // L <-> RL: R = (L, RR)
+            const float g3 = areaR - union_area(lc, hc, lL, hL);   // L <-> RR: R = (RL, L)
+            if (g2 > best) { best = g2; kind = 2; }
+            if (g3 > best) { best = g3; kind = 3; }
+        }
+        if (kind == 0 || kind == 1) {
+            // the child of L that moves up to p (m) and the one that stays with R
+            const float4 lm = kind == 0 ? la : lb, hm = kind == 0 ? ha : hb;
+            const int rm = kind == 0 ? ra : rb;
+            const float4 ls = kind == 0 ? lb : la, hs = kind == 0 ? hb : ha;
+            const int rs = kind == 0 ? rb : ra;
+            const BvhNode newL = kind == 0 ? make_node(lR, hR, R, ls, hs, rs) : make_node(ls, hs, rs, lR, hR, R);
+            float4 lN, hN;
+            int dummy;
+            node_child(newL, 0, lN, hN, dummy);
+            float4 l2, h2;
+            node_child(newL, 1, l2, h2, dummy);
+            lN = make_float4(fminf(lN.x, l2.x), fminf(lN.y, l2.y), fminf(lN.z, l2.z), 0.f);
+            hN = make_float4(fmaxf(hN.x, h2.x), fmaxf(hN.y, h2.y), fmaxf(hN.z, h2.z), 0.f);
+            nodes[L] = newL;
+            nodes[p] = make_node(lN, hN, L, lm, hm, rm);
+            set_parent(R, L, n, parent_node, parent_leaf, bad);
+            set_parent(rm, p, n, parent_node, parent_leaf, bad);
+        } else if (kind == 2 || kind == 3) {
+            const float4 lm = kind == 2 ? lc : ld, hm = kind == 2 ? hc : hd;
+            const int rm = kind == 2 ? rc : rd;
+            const float4 ls = kind == 2 ? ld : lc, hs = kind == 2 ? hd : hc;
+            const int rs = kind == 2 ? rd : rc;
+            const BvhNode newR = kind == 2 ? make_node(lL, hL, L, ls, hs, rs) : make_node(ls, hs, rs, lL, hL, L);
+            float4 lN, hN, l2, h2;
+            int dummy;
+            node_child(newR, 0, lN, hN, dummy);
+            node_child(newR, 1, l2, h2, dummy);
+            lN = make_float4(fminf(lN.x, l2.x), fminf(lN.y, l2.y), fminf(lN.z, l2.z), 0.f);
+            hN = make_float4(fmaxf(hN.x, h2.x), fmaxf(hN.y, h2.y), fmaxf(hN.z, h2.z), 0.f);
+            nodes[R] = newR;
+            nodes[p] = make_node(lm, hm, rm, lN, hN, R);
+            set_parent(L, R, n, parent_node, parent_leaf, bad);
+            set_parent(rm, p, n, parent_node, parent_leaf, bad);
+        }
+        __threadfence();
+        p = __ldcg(&parent_node[p]);
+    }
+}
+
 // tree depth (levels from the root to the deepest leaf, root = 1)
 __global__ void k_depth(int n, const int *parent_node, const int *parent_leaf, int *depth) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -244,11 +377,6 @@ __global__ void k_depth(int n, const int *parent_node, const int *parent_leaf, i
 // surface area of the merged box; mutual nearest neighbours merge into a new node;
 // the cluster array is compacted (order preserved) and the steps repeat.
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float half_area(float4 lo, float4 hi) {
-    float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
-    return dx * dy + dy * dz + dz * dx;
-}
 
 __global__ void k_ploc_init(const float4 *tris, int m, int *cid, float4 *clo, float4 *chi) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -684,7 +812,7 @@ static int collapse4(DofScene *s, int root, int n_bin, int *ibuf, cudaStream_t s
 }
 
 int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const uint32_t *d_idx,
-                     const uint32_t *d_mat, int builder, int ploc_radius, cudaStream_t st) {
+                     const uint32_t *d_mat, int builder, int ploc_radius, int rotations, cudaStream_t st) {
     const int n = (int)s->n_tris;
     const int B = 256;
     int rc = DOF_OK;
@@ -756,6 +884,10 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
                 k_karras<<<blocks_for(m - 1, B), B, 0, st>>>(keys, m, child, pnode, pleaf, ibuf + 6);
                 k_refit<<<blocks_for(m, B), B, 0, st>>>(s->tris, m, child, pnode, pleaf, blo, bhi, arr, s->nodes,
                                                         ibuf + 6);
+            }
+            for (int pass = 0; pass < rotations; pass++) {
+                ck(cudaMemsetAsync(arr, 0, sizeof(int) * (m - 1), st), "memset");
+                k_rotate<<<blocks_for(m, B), B, 0, st>>>(m, s->nodes, pnode, pleaf, arr, ibuf + 6);
             }
             k_depth<<<blocks_for(m, B), B, 0, st>>>(m, pnode, pleaf, ibuf + 7);
         }

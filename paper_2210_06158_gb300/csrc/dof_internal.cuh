@@ -98,6 +98,7 @@ struct DofCtx {
     size_t budget;
     int sm_count;
     int bvh_builder;               // DOF_BVH_PLOC or DOF_BVH_LBVH
+    int bvh_rotations;             // passes of tree rotations after the build
     int trace_blocks_per_sm, trace_refill_idle, trace_steps, ray_order_grid, trace_packets;
     int gather_w, gather_h, main_form;   // main filter launch shape and form
     int recon_w, recon_h;                // reconstruction launch shape
@@ -202,7 +203,7 @@ void dof_free(DofCtx *ctx, void *ptr, size_t bytes);
 
 // launch wrappers (one per kernel group, defined in the .cu files)
 int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const uint32_t *d_idx,
-                     const uint32_t *d_mat, int builder, int ploc_radius, cudaStream_t st);
+                     const uint32_t *d_mat, int builder, int ploc_radius, int rotations, cudaStream_t st);
 void launch_primary(const DevCam &cam, const DevParams &p, SceneDev sc, float4 *color, float *depth,
                     float4 *normal, int32_t *prim, uint32_t *status, cudaStream_t st);
 // host-side tally of this library's kernel launches (dof_launch_count); each launch

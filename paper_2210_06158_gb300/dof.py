@@ -233,6 +233,10 @@ class Context:
         """PLOC search radius for scenes uploaded afterwards (tree quality vs build time)."""
         _check(lib().dof_ctx_set_option(self.ptr, 5, int(r)))
 
+    def set_bvh_rotations(self, passes: int):
+        """Passes of tree rotations after the BVH build of scenes uploaded afterwards."""
+        _check(lib().dof_ctx_set_option(self.ptr, 13, int(passes)))
+
     def set_bvh_width(self, width: int):
         """Tree the rays traverse: 4 (collapsed 4-wide nodes, default) or 2 (binary)."""
         _check(lib().dof_ctx_set_option(self.ptr, 6, int(width)))

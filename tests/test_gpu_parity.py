@@ -447,7 +447,8 @@ def test_scheduling_knobs_do_not_change_results(name, W, H):
 
 def test_tree_shape_does_not_change_hits():
     """The closest hit is a property of the triangles, not of the tree: PLOC or LBVH,
-    binary or 4-wide traversal give bit-identical hit ids and images."""
+    with or without tree rotations, binary or 4-wide traversal give bit-identical hit
+    ids and images."""
     from paper_2210_06158_gb300 import dof
     import torch
     dev = torch.device("cuda", 0)
@@ -459,9 +460,10 @@ def test_tree_shape_does_not_change_hits():
         gb = oracle.gbuffer_f32(oracle.gbuffer(osc, w.camera(f), prm, w.W, w.H))
         gbs.append({k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in gb.items()})
     results = []
-    for builder in ("ploc", "lbvh"):
+    for builder, rot in (("ploc", 0), ("lbvh", 0), ("ploc", 4), ("lbvh", 2)):
         ctx = dof.Context(0)
         ctx.set_bvh_builder(builder)
+        ctx.set_bvh_rotations(rot)
         sc = dof.Scene(ctx, w.scene)
         info = sc.info()
         assert info.n_nodes4 > 0 and 0 < info.depth4 <= info.depth
@@ -474,7 +476,7 @@ def test_tree_shape_does_not_change_hits():
                 outs.append(dof.frame(ctx, sc, gbs[f], w.camera(f), prm, h).cpu().numpy())
             torch.cuda.synchronize()
             assert h.stats().device_status == 0
-            results.append((builder, width, outs, h.read("RAY_PRIM", np.int32), h.stats().node_visits))
+            results.append((f"{builder}/rot{rot}", width, outs, h.read("RAY_PRIM", np.int32), h.stats().node_visits))
             h.close()
         sc.close()
     b0 = results[0]
