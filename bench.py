@@ -373,13 +373,19 @@ def run_ours(args, rank, world):
                     recon_block=pinned["recon_block"])
         ctx.set_gather(block=gsel["gather_block"], main_form=gsel["main_form"], recon_block=gsel["recon_block"])
     else:
-        widths = (args.bvh_width,) if args.bvh_width else (4, 2)
+        # the tracer first (on the default tree), then the tree under that tracer (the
+        # trees' quality differs between radii, and by traversal), then the tracer again
+        # on the chosen tree
+        fixed_width = (args.bvh_width,) if args.bvh_width else None
+        first, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4, widths=fixed_width)
+        widths = (args.bvh_width,) if args.bvh_width else ((2,) if first.get("packets") else (4, 2))
+        scene.close()
         scene, tuned_bvh, _ = tune.tune_scene(
             ctx, w.scene, lambda sc, k: dof.frame(ctx, sc, gbs[k % CYCLE], None, None, hist, out,
                                                   cam_struct=cams[k % len(cams)], params_s=pstruct), widths=widths)
         info = scene.info()
-        tuned, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4,
-                                   widths=(args.bvh_width,) if args.bvh_width else None)
+        tuned, _ = tune.tune_trace(ctx, lambda k: step(k % len(cams), hist), frames=4, rounds=1,
+                                   widths=fixed_width or ((2,) if first.get("packets") else None), start=first)
         tuned = dict(tuned, ploc_radius=tuned_bvh["ploc_radius"])
         # the 81-tap gathers' block shape and the main filter's form
         gsel, _ = tune.tune_gathers(ctx, lambda k: step(k % len(cams), hist), frames=4)

@@ -57,14 +57,18 @@ def _time_frames(run_frame, frames, st):
     return e0.elapsed_time(e1) / frames
 
 
-def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None):
+def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None, start=None):
     """run_frame(k) enqueues frame k of a representative session on `stream` (or the
-    current stream); `widths` restricts the tree widths searched (default: all).
-    Returns (best settings, {settings tuple: ms per frame})."""
+    current stream); `widths` restricts the tree widths searched (default: all); `start`
+    is the search's starting point (default: DEFAULT).  Returns (best settings,
+    {settings tuple: ms per frame})."""
     import torch
     st = stream if stream is not None else torch.cuda.current_stream()
     space = dict(SPACE, bvh_width=list(widths)) if widths else SPACE
-    best = dict(DEFAULT, bvh_width=space["bvh_width"][0])
+    best = dict(start or DEFAULT)
+    best = {k: best[k] for k in DEFAULT}
+    if best["bvh_width"] not in space["bvh_width"]:
+        best["bvh_width"] = space["bvh_width"][0]
     seen = {}
 
     def canon(cfg):

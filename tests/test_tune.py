@@ -246,3 +246,19 @@ def test_tune_trace_is_not_fooled_by_a_warming_session(monkeypatch):
     best, _ = tune.tune_trace(ctx, run_frame, frames=3, stream=types.SimpleNamespace())
     assert best == {"bvh_width": 2, "ray_grid": 8, "stack": 64, "blocks_per_sm": 6, "refill_idle": 12, "steps": 32,
                     "packets": 1}
+
+
+def test_tune_trace_starts_from_a_given_point(monkeypatch):
+    """A second search starts from the first one's pick (and stays there when no move
+    beats it)."""
+    clock = _Clock()
+    _fake_cuda(monkeypatch, clock)
+    ctx = _Ctx()
+
+    def run_frame(k):
+        clock.t += _cost(ctx.cfg)
+
+    first, _ = tune.tune_trace(ctx, run_frame, frames=2, stream=types.SimpleNamespace())
+    again, seen = tune.tune_trace(ctx, run_frame, frames=2, rounds=1, stream=types.SimpleNamespace(), start=first)
+    assert again == first
+    assert tuple(sorted(first.items())) in seen
