@@ -220,9 +220,9 @@ struct SmallSlot {               // one triangle of a warp's list (112 bytes)
 // centre to the hit point, at least the distance to the triangle's bounding box, which
 // is evaluated with every operation rounded down.  The test's t is a convex combination
 // of the vertices' depths along the ray (barycentric weights), evaluated in FP32; the
-// bound is shrunk by 2^-7 to stay below it.  A triangle that reaches within 60 degrees
-// of the image plane (a vertex direction more than 60 degrees off the view axis) gets 0
-// and is never culled: near the lens plane those depths can cancel.
+// bound is shrunk by 2^-7 to stay below it.  A triangle with a vertex direction more than
+// 60 degrees off the view axis (within 30 degrees of the lens plane) gets 0 and is never
+// culled: near the lens plane those depths can cancel.
 __device__ __forceinline__ float near_bound(const DevCam &cam, float4 v0, float4 v1, float4 v2) {
     const float4 v[3] = {v0, v1, v2};
 #pragma unroll

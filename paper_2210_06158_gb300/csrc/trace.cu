@@ -674,11 +674,12 @@ __global__ void __launch_bounds__(kTraceThreads, 7) k_trace_rays(const __grid_co
 // when the ray of any lane enters its box, and the two children go in the order that
 // most of the lanes entering both prefer.  Each lane tests boxes and triangles with
 // its own ray and its own best hit (inclusive cull), so every ray ends with the closest
-// hit that the per-ray traversal finds.  Rays grouped by lens cell leave one small
-// patch of the aperture for nearby pixels, a packet close to a pinhole frustum: the
-// warp then steps with all its lanes and one broadcast load per node, at the price of
-// the nodes that only some of its rays need.  Lanes of a warp that straddles two
-// sessions of a batch trace one session's packet after the other.
+// hit that the per-ray traversal finds.  A warp's rays come from a compact patch of
+// pixels (pixel order: with several rays per pixel, the cones of a few pixels through
+// their focus points) or of pixels and aperture (lens-cell order, close to a pinhole
+// frustum): the warp then steps with all its lanes and one broadcast load per node, at
+// the price of the nodes that only some of its rays need.  Lanes of a warp that
+// straddles two sessions of a batch trace one session's packet after the other.
 template <int kCap, class AS>
 __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
