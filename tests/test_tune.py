@@ -262,3 +262,20 @@ def test_tune_trace_starts_from_a_given_point(monkeypatch):
     again, seen = tune.tune_trace(ctx, run_frame, frames=2, rounds=1, stream=types.SimpleNamespace(), start=first)
     assert again == first
     assert tuple(sorted(first.items())) in seen
+
+
+def test_bench_settings_pin_every_tuned_key():
+    """bench.py --settings: the keys the tuners report, blocks as WxH, the rest at their
+    defaults; an unknown key is refused."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    assert bench.parse_settings(None) is None
+    s = bench.parse_settings("ploc_radius=96, bvh_width=2,ray_grid=1,packets=1,main_filter_block=64x4,"
+                             "main_filter_form=3")
+    assert s["ploc_radius"] == 96 and s["packets"] == 1 and s["ray_grid"] == 1
+    assert s["main_filter_block"] == (64, 4) and s["main_filter_form"] == 3
+    assert s["recon_block"] == (32, 8) and s["stack"] == tune.DEFAULT["stack"]
+    assert set(tune.DEFAULT) <= set(s)
+    with pytest.raises(SystemExit):
+        bench.parse_settings("radius=3")
