@@ -806,3 +806,36 @@ def test_launch_count_per_frame():
     torch.cuda.synchronize()
     assert dof.launch_count() - n0 == 2 * 11
     graph.close()
+
+
+@pytest.mark.parametrize("grid", [1, 8])
+def test_packets_in_adaptive_mode_equal_one_ray_per_lane(grid):
+    """In the adaptive mode of Eq. 4 (up to m rays per pixel, as many as the edge measure
+    and the history's variance ask for) warp packets give, over three frames of a moving
+    camera, the hit ids, ray counts and images of the per-ray tracer bit for bit."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    dev = torch.device("cuda", 0)
+    w = make_workload("c2", W=322, H=182, n_frames=3)
+    prm = dict(w.params, ray_mode=1, m=12)
+    osc = oracle.Scene(w.scene)
+    gbs = []
+    for f in range(3):
+        gb = oracle.gbuffer_f32(oracle.gbuffer(osc, w.camera(f), prm, w.W, w.H))
+        gbs.append({k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in gb.items()})
+    ctx = dof.Context(0)
+    sc = dof.Scene(ctx, w.scene)
+    results = []
+    for packets in (0, 1):
+        ctx.set_trace(bvh_width=2, ray_grid=grid, packets=packets)
+        h = dof.History(ctx, w.W, w.H, max_rays=12, record_rays=True)
+        outs = [dof.frame(ctx, sc, gbs[f], w.camera(f), prm, h).cpu().numpy() for f in range(3)]
+        torch.cuda.synchronize()
+        st = h.stats()
+        assert st.device_status == 0 and st.rays > st.masked_pixels     # several rays per pixel
+        results.append((outs, h.read("RAY_PRIM", np.int32), h.read("NRAYS", np.int32)))
+        h.close()
+    for f in range(3):
+        assert np.array_equal(results[0][0][f], results[1][0][f]), f
+    assert np.array_equal(results[0][1], results[1][1])
+    assert np.array_equal(results[0][2], results[1][2])
