@@ -401,8 +401,8 @@ def test_checkpoint_resume_bit_identical():
 @pytest.mark.parametrize("name,W,H", [("c3", 384, 216), ("c2", 322, 182)])
 def test_scheduling_knobs_do_not_change_results(name, W, H):
     """The autotuned knobs change only speed: the tracer's work order (lens-cell grid 1
-    = pixel order, 2 .. 16), its traversal stack, warp packets instead of one ray per
-    lane, the gathers' block shapes and the main filter's form (shared-memory halo tile,
+    = pixel order, 2 .. 16), its traversal stack, the tree's width, warp packets
+    instead of one ray per lane, the gathers' block shapes and the main filter's form (shared-memory halo tile,
     L1, or columns of four pixels through L1) give bit-identical hit ids, intermediates
     and images over two frames of a moving camera (the c3 crop with its 64 px clamp
     takes the halo tile only in the opt-in form)."""
@@ -421,13 +421,15 @@ def test_scheduling_knobs_do_not_change_results(name, W, H):
     variants = [dict(ray_grid=1), dict(ray_grid=2), dict(ray_grid=4), dict(ray_grid=8), dict(ray_grid=12),
                 dict(ray_grid=16), dict(ray_grid=8, stack=32), dict(ray_grid=8, stack=64),
                 dict(ray_grid=1, packets=1), dict(ray_grid=4, packets=1), dict(ray_grid=8, packets=1, stack=32),
+                dict(ray_grid=1, width=2), dict(ray_grid=8, width=2, stack=32),
                 dict(block=(16, 16), main_form=0, recon=(16, 16)), dict(block=(64, 4), main_form=1, recon=(64, 8)),
                 dict(block=(32, 16), main_form=2, recon=(32, 16)), dict(block=(64, 8), main_form=2, recon=(64, 4)),
                 dict(block=(32, 8), main_form=1, recon=(8, 32)), dict(block=(32, 8), main_form=3),
                 dict(block=(64, 4), main_form=3, recon=(16, 16)), dict(block=(16, 8), main_form=3)]
     results = []
     for v in variants:
-        ctx.set_trace(ray_grid=v.get("ray_grid", 4), stack=v.get("stack", 96), packets=v.get("packets", 0))
+        ctx.set_trace(ray_grid=v.get("ray_grid", 4), stack=v.get("stack", 96), packets=v.get("packets", 0),
+                      bvh_width=v.get("width", 4))
         ctx.set_gather(block=v.get("block", (32, 8)), main_form=v.get("main_form", 0),
                        recon_block=v.get("recon", (32, 8)))
         h = dof.History(ctx, w.W, w.H, max_rays=oracle.max_rays(prm), record_rays=True)
