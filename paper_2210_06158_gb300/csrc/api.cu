@@ -537,8 +537,7 @@ static void history_free(DofHistory *h) {
     dof_free(c, h->recon, 16 * N); dof_free(c, h->ct, 4 * N); dof_free(c, h->var, 4 * N);
     for (int l = 0; l < 4; l++) {
         size_t n = (size_t)h->mip_w[l] * h->mip_h[l];
-        dof_free(c, h->mip0[l], 16 * n);
-        dof_free(c, h->mip1[l], 8 * n);
+        dof_free(c, h->mip[l], 32 * n);
     }
     for (int k = 0; k < 2; k++) {
         dof_free(c, h->hist[k], 48 * N);
@@ -604,8 +603,7 @@ extern "C" int dof_history_create(DofCtx *ctx, uint32_t width, uint32_t height, 
     A((void **)&h->recon, 16 * N); A((void **)&h->ct, 4 * N); A((void **)&h->var, 4 * N);
     for (int l = 0; l < 4; l++) {
         size_t n = (size_t)h->mip_w[l] * h->mip_h[l];
-        A((void **)&h->mip0[l], 16 * n);
-        A((void **)&h->mip1[l], 8 * n);
+        A((void **)&h->mip[l], 32 * n);
     }
     for (int k = 0; k < 2; k++) {
         A((void **)&h->hist[k], 48 * N);
@@ -710,7 +708,7 @@ static int make_desc(DofCtx *ctx, const DofFrameReq &r, SessDesc &d) {
     int L = (int)ceilf(r.params->lod_max) + 1;
     d.mip_L = L < 1 ? 1 : (L > 4 ? 4 : L);
     for (int l = 0; l < 4; l++) {
-        d.mip0[l] = h->mip0[l]; d.mip1[l] = h->mip1[l]; d.mip_w[l] = h->mip_w[l]; d.mip_h[l] = h->mip_h[l];
+        d.mip[l] = h->mip[l]; d.mip_w[l] = h->mip_w[l]; d.mip_h[l] = h->mip_h[l];
     }
     d.hist_in = h->hist[h->cur];
     d.hist_out = h->hist[h->cur ^ 1];
@@ -865,6 +863,8 @@ struct DofGraph {
     int trace_blocks, refill_idle, steps_per_round, lens_grid, stack_depth, packets;
     int gather_w, gather_h, main_form, recon_w, recon_h;
     int main_tile;                // the main filter's shared-memory bytes (0: through L1)
+    int store_mode;               // image_storage_mode of the captured step
+    bool taa;                     // the captured step has the final TAA pass
     long long kernels;            // kernel launches in one replay
     BatchArgs *d_args;            // read by the captured kernels
     BatchArgs *h_stage;           // pinned source of the captured copy
@@ -907,6 +907,8 @@ extern "C" int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n
     g->wide = all_wide(A);
     g->trace_blocks = ctx->sm_count * ctx->trace_blocks_per_sm;
     g->main_tile = main_filter_tile_bytes(A);
+    g->store_mode = image_storage_mode(A);
+    g->taa = any_taa(A);
     g->refill_idle = A.refill_idle;
     g->steps_per_round = A.steps_per_round;
     g->lens_grid = A.lens_grid;
@@ -969,7 +971,8 @@ extern "C" int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n
     if (memcmp(A.start, g->start, sizeof(A.start)) != 0 || adaptive != g->adaptive || all_wide(A) != g->wide ||
         ctx->sm_count * ctx->trace_blocks_per_sm != g->trace_blocks || main_filter_tile_bytes(A) != g->main_tile ||
         A.gather_w != g->gather_w || A.gather_h != g->gather_h || A.main_form != g->main_form ||
-        A.recon_w != g->recon_w || A.recon_h != g->recon_h || A.packets != g->packets)
+        A.recon_w != g->recon_w || A.recon_h != g->recon_h || A.packets != g->packets ||
+        image_storage_mode(A) != g->store_mode || any_taa(A) != g->taa)
         return dof_set_error(DOF_ERR_MISMATCH, "dof_graph_launch: launch shapes differ from the captured step");
     // the kernels' scheduling knobs come from the staged copy; keep the captured ones
     A.refill_idle = g->refill_idle;

@@ -44,8 +44,7 @@ struct SessDesc {
     int2 *hits;
     float4 *ray_a;
     float2 *ray_b;
-    float4 *mip0[4];
-    float2 *mip1[4];
+    float4 *mip[4];
     int mip_w[4], mip_h[4], mip_L;
     // history ping-pong
     const float4 *hist_in;
@@ -63,11 +62,25 @@ struct BatchArgs {
     int gather_w, gather_h;        // block of the main filter (SH_GATHER), <= 512 threads
     int recon_w, recon_h;          // block of the reconstruction (SH_RECON), <= 512 threads
     int main_form;                 // main filter: 0 halo tile up to 64 KB, 1 through L1, 2 halo tile up
-                                   // to the SM's opt-in shared memory
+                                   // to the SM's opt-in shared memory, 3 columns of four pixels
     int start[SH_COUNT][kMaxBatch + 1];
     uint32_t *cursor;              // device word: ray cursor of the persistent tracer
     SessDesc s[kMaxBatch];
 };
+
+// The image storage of a launch's sessions: 0 every session FP32, 1 every session FP16,
+// 2 mixed (kernels specialised on it take each session's own from its parameters).
+inline int image_storage_mode(const BatchArgs &A) {
+    int n16 = 0;
+    for (int i = 0; i < A.ns; i++) n16 += A.s[i].p.f16 != 0;
+    return n16 == 0 ? 0 : (n16 == A.ns ? 1 : 2);
+}
+// whether any session of the launch takes the final TAA pass
+inline bool any_taa(const BatchArgs &A) {
+    for (int i = 0; i < A.ns; i++)
+        if (A.s[i].taa) return true;
+    return false;
+}
 
 #ifdef __CUDACC__
 // session of a flat block index for `shape`; *local = the block's index in that session

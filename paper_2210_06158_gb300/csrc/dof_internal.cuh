@@ -156,8 +156,8 @@ struct DofHistory {
     float4 *rt;                    // 4 planes of N
     float4 *crt, *rt_med, *recon;
     float *ct, *var;
-    float4 *mip0[4];               // (rgb, h) * valid per level
-    float2 *mip1[4];               // (c_t, 1) * valid per level
+    float4 *mip[4];                // per level, 32 bytes per texel: (rgb, h) * valid and
+                                   // (c_t, 1) * valid, laid out by st_mip
     int mip_w[4], mip_h[4];
     // final TAA (DOF_HIST_TAA): composited image of the frame, resolved images (ping-pong)
     float4 *comp, *taa[2];
@@ -266,6 +266,23 @@ __device__ __forceinline__ void st_img(float4 *base, size_t i, float4 v, bool h)
         reinterpret_cast<uint2 *>(base)[i] = u;
     } else {
         base[i] = v;
+    }
+}
+
+// One texel i of a level of the reconstruction's pyramid (n texels, 32 bytes each from a
+// 256-byte aligned base): the colour a = (rgb, h) * valid and b = (c_t, 1) * valid.
+// FP32 storage keeps two planes, a at base[i] and b at float2 index i after the n
+// colours.  FP16 storage keeps one 16-byte record per texel, a as half4 then b, so a tap
+// reads a texel with one load.  (A 32-byte FP32 record read by one 256-bit load made
+// the reconstruction slower: a quarter of every record was padding through L1.)
+__device__ __forceinline__ void st_mip(float4 *base, size_t n, size_t i, float4 a, float2 b, bool h) {
+    if (h) {
+        __half2 x = __floats2half2_rn(a.x, a.y), y = __floats2half2_rn(a.z, a.w);
+        base[i] = make_float4(__uint_as_float(*reinterpret_cast<uint32_t *>(&x)),
+                              __uint_as_float(*reinterpret_cast<uint32_t *>(&y)), b.x, b.y);
+    } else {
+        base[i] = a;
+        reinterpret_cast<float2 *>(base + n)[i] = b;
     }
 }
 

@@ -114,8 +114,7 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
         const float vv = valid ? 1.f : 0.f;
         const float4 l0 = f4scale(vv, round_img(med, hs));
         const float2 l0b = make_float2(vv * __ldg(&S.ct[q]), vv);
-        st_img(S.mip0[0], q, l0, hs);
-        S.mip1[0][q] = l0b;
+        st_mip(S.mip[0], (size_t)W2 * H2, q, l0, l0b, hs);
         m0a[cy][cx] = round_img(l0, hs);
         m0b[cy][cx] = l0b;
     }
@@ -140,8 +139,7 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
             const float4 v = f4scale(0.25f, a);
             const float2 u = make_float2(0.25f * b.x, 0.25f * b.y);
             const size_t o = (size_t)j1 * S.mip_w[1] + i1;
-            st_img(S.mip0[1], o, v, hs);
-            S.mip1[1][o] = u;
+            st_mip(S.mip[1], (size_t)S.mip_w[1] * S.mip_h[1], o, v, u, hs);
             m1a[uy][ux] = round_img(v, hs);
             m1b[uy][ux] = u;
         }
@@ -164,8 +162,7 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
             const float4 v = f4scale(0.25f, a);
             const float2 u = make_float2(0.25f * b.x, 0.25f * b.y);
             const size_t o = (size_t)j2 * S.mip_w[2] + i2;
-            st_img(S.mip0[2], o, v, hs);
-            S.mip1[2][o] = u;
+            st_mip(S.mip[2], (size_t)S.mip_w[2] * S.mip_h[2], o, v, u, hs);
             m2a[uy][ux] = round_img(v, hs);
             m2b[uy][ux] = u;
         }
@@ -185,8 +182,8 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
                 b.x += c.x; b.y += c.y;
             }
             const size_t o = (size_t)j3 * S.mip_w[3] + i3;
-            st_img(S.mip0[3], o, f4scale(0.25f, a), hs);
-            S.mip1[3][o] = make_float2(0.25f * b.x, 0.25f * b.y);
+            st_mip(S.mip[3], (size_t)S.mip_w[3] * S.mip_h[3], o, f4scale(0.25f, a), make_float2(0.25f * b.x, 0.25f * b.y),
+                   hs);
         }
     }
 }
@@ -195,18 +192,35 @@ __global__ void __launch_bounds__(256) k_resolve_rt(const __grid_constant__ AS a
 // 2^l (x + 0.5) - 0.5 in half-resolution pixels, so a half-resolution position x maps
 // to x 2^-l + (2^-l - 1) / 2 in level texels.
 struct MipLevel {
-    const float4 *m0;
-    const float2 *m1;
+    const float4 *m;     // the colour plane (FP32 storage) or the records (FP16)
+    const float2 *m1;    // FP32 storage: the (c_t, 1) plane
     int w, h;
     float s, c;
 };
 
 __device__ __forceinline__ MipLevel mip_level(const SessDesc &S, int l) {
     MipLevel L;
-    L.m0 = S.mip0[l]; L.m1 = S.mip1[l]; L.w = S.mip_w[l]; L.h = S.mip_h[l];
+    L.m = S.mip[l]; L.w = S.mip_w[l]; L.h = S.mip_h[l];
+    L.m1 = reinterpret_cast<const float2 *>(L.m + (size_t)L.w * L.h);
     L.s = 1.f / (float)(1 << l);
     L.c = 0.5f * L.s - 0.5f;
     return L;
+}
+
+// texel i of a level as st_mip stored it
+template <bool H>
+__device__ __forceinline__ void ld_mip(const MipLevel &L, int i, float4 &a, float2 &b) {
+    if (H) {
+        const float4 t = __ldg(L.m + i);
+        uint32_t ux = __float_as_uint(t.x), uy = __float_as_uint(t.y);
+        const float2 fa = __half22float2(*reinterpret_cast<__half2 *>(&ux));
+        const float2 fb = __half22float2(*reinterpret_cast<__half2 *>(&uy));
+        a = make_float4(fa.x, fa.y, fb.x, fb.y);
+        b = make_float2(t.z, t.w);
+    } else {
+        a = __ldg(L.m + i);
+        b = __ldg(L.m1 + i);
+    }
 }
 
 // Bilinear sample of one level at (x, y), scaled by the level's trilinear weight wl and
@@ -229,12 +243,16 @@ __device__ __forceinline__ void bilin_acc(const MipLevel &L, float x, float y, f
         xa = x0; xb = x0 + 1;
         qa = y0 * w; qb = qa + w;
     }
-    a = f4fma(w00, ld_img(L.m0, qa + xa, H), a);
-    a = f4fma(w10, ld_img(L.m0, qa + xb, H), a);
-    a = f4fma(w01, ld_img(L.m0, qb + xa, H), a);
-    a = f4fma(w11, ld_img(L.m0, qb + xb, H), a);
-    const float2 c00 = __ldg(&L.m1[qa + xa]), c10 = __ldg(&L.m1[qa + xb]);
-    const float2 c01 = __ldg(&L.m1[qb + xa]), c11 = __ldg(&L.m1[qb + xb]);
+    float4 a00, a10, a01, a11;
+    float2 c00, c10, c01, c11;
+    ld_mip<H>(L, qa + xa, a00, c00);
+    ld_mip<H>(L, qa + xb, a10, c10);
+    ld_mip<H>(L, qb + xa, a01, c01);
+    ld_mip<H>(L, qb + xb, a11, c11);
+    a = f4fma(w00, a00, a);
+    a = f4fma(w10, a10, a);
+    a = f4fma(w01, a01, a);
+    a = f4fma(w11, a11, a);
     b.x = fmaf(w11, c11.x, fmaf(w01, c01.x, fmaf(w10, c10.x, fmaf(w00, c00.x, b.x))));
     b.y = fmaf(w11, c11.y, fmaf(w01, c01.y, fmaf(w10, c10.y, fmaf(w00, c00.y, b.y))));
 }
@@ -263,13 +281,16 @@ __device__ __forceinline__ void recon_taps(const MipLevel &L0, const MipLevel &L
 }
 
 // A11: reconstruction.  Blocks whose footprint (+-rmax + 2, at every level) lies
-// inside the image take taps without index clamping.
-template <class AS>
-__global__ void __launch_bounds__(512) k_recon(const __grid_constant__ AS as_) {
+// inside the image take taps without index clamping.  kStore: the launch's image storage
+// (image_storage_mode); the specialised instances hold the code of one storage only, and
+// with it fewer registers.
+template <class AS, int kStore>
+__global__ void __launch_bounds__(512, 2) k_recon(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_RECON, i, j);
     const DevParams &p = S.p;
+    const bool f16 = kStore == 2 ? p.f16 != 0 : kStore == 1;
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const int mL = S.mip_L;
     const float4 *__restrict__ med = S.rt_med;
@@ -283,13 +304,13 @@ __global__ void __launch_bounds__(512) k_recon(const __grid_constant__ AS as_) {
                           by + (int)blockDim.y + reach < H2;
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
-    if (__ldg(&nrays[q]) <= 0) { st_img(out, q, make_float4(0.f, 0.f, 0.f, 0.f), p.f16); return; }
-    const float4 o = ld_img(med, q, p.f16);
+    if (__ldg(&nrays[q]) <= 0) { st_img(out, q, make_float4(0.f, 0.f, 0.f, 0.f), f16); return; }
+    const float4 o = ld_img(med, q, f16);
     const float b = fminf(fmaxf(__ldg(&var_blur[q]) * p.var_w_recon, 0.f), p.b_max);
     // Eq. 5 blends by b: below 2^-24 the filtered term changes the result by less than
     // the rounding of the 81-tap sum itself, so the taps are not taken
     if (!(b >= 5.9604645e-8f)) {
-        st_img(out, q, make_float4(o.x + 0.f, o.y + 0.f, o.z + 0.f, o.w + 0.f), p.f16);
+        st_img(out, q, make_float4(o.x + 0.f, o.y + 0.f, o.z + 0.f, o.w + 0.f), f16);
         return;
     }
     float R = __ldg(&ct[q]);
@@ -301,7 +322,7 @@ __global__ void __launch_bounds__(512) k_recon(const __grid_constant__ AS as_) {
     const MipLevel L0 = mip_level(S, l0), L1 = mip_level(S, l1);
     float4 num = make_float4(0.f, 0.f, 0.f, 0.f);
     float den = 0.f;
-    if (p.f16) {
+    if (f16) {
         if (interior) recon_taps<false, true>(L0, L1, i, j, R, t, p.inv_cover_ramp, p.ring, num, den);
         else recon_taps<true, true>(L0, L1, i, j, R, t, p.inv_cover_ramp, p.ring, num, den);
     } else {
@@ -309,7 +330,7 @@ __global__ void __launch_bounds__(512) k_recon(const __grid_constant__ AS as_) {
         else recon_taps<true, false>(L0, L1, i, j, R, t, p.inv_cover_ramp, p.ring, num, den);
     }
     float4 f = den > 0.f ? f4scale(1.f / den, num) : o;
-    st_img(out, q, make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b)), p.f16);
+    st_img(out, q, make_float4(lerpf(o.x, f.x, b), lerpf(o.y, f.y, b), lerpf(o.z, f.z, b), lerpf(o.w, f.w, b)), f16);
 }
 
 // A12: composite.  One thread per half-resolution pixel (i, j) writes its 2x2
@@ -489,16 +510,28 @@ void launch_recon_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistor
     k_resolve_rt<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_MEDIAN_RT, st);
     tmark(tm, DOF_K_MIPS, st);
-    k_recon<AS><<<A.start[SH_RECON][n], dim3(A.recon_w, A.recon_h), 0, st>>>(as);
+    const dim3 rg(A.start[SH_RECON][n]), rb(A.recon_w, A.recon_h);
+    switch (image_storage_mode(A)) {
+    case 0: k_recon<AS, 0><<<rg, rb, 0, st>>>(as); break;
+    case 1: k_recon<AS, 1><<<rg, rb, 0, st>>>(as); break;
+    default: k_recon<AS, 2><<<rg, rb, 0, st>>>(as); break;
+    }
     count_launches(2);
     tmark(tm, DOF_K_RECON, st);
 }
 
-// the final TAA loaded now (it runs only once a session asks for it)
+// the final TAA and the reconstruction's storage instances loaded now (a kernel first
+// launched in a later frame would otherwise stall that frame on its load)
 void preload_recon_kernels() {
     cudaFuncAttributes a;
     cudaFuncGetAttributes(&a, k_taa<BatchArgs>);
     cudaFuncGetAttributes(&a, k_taa<const BatchArgs *>);
+    cudaFuncGetAttributes(&a, k_recon<BatchArgs, 0>);
+    cudaFuncGetAttributes(&a, k_recon<BatchArgs, 1>);
+    cudaFuncGetAttributes(&a, k_recon<BatchArgs, 2>);
+    cudaFuncGetAttributes(&a, k_recon<const BatchArgs *, 0>);
+    cudaFuncGetAttributes(&a, k_recon<const BatchArgs *, 1>);
+    cudaFuncGetAttributes(&a, k_recon<const BatchArgs *, 2>);
     cudaGetLastError();
 }
 
@@ -508,10 +541,9 @@ void launch_composite_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHi
     dim3 b(32, 8);
     k_composite<AS><<<A.start[SH_HPX][n], b, 0, st>>>(as);
     tmark(tm, DOF_K_COMPOSITE, st);
-    bool any_taa = false;
-    for (int i = 0; i < n; i++) any_taa |= A.s[i].taa != 0;
-    if (any_taa) k_taa<AS><<<A.start[SH_FPX][n], b, 0, st>>>(as);
-    count_launches(any_taa ? 2 : 1);
+    const bool taa = any_taa(A);
+    if (taa) k_taa<AS><<<A.start[SH_FPX][n], b, 0, st>>>(as);
+    count_launches(taa ? 2 : 1);
     tmark(tm, DOF_K_TAA, st);
 }
 
