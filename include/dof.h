@@ -384,6 +384,9 @@ int dof_kernel_times(DofHistory *hist, void *stream, float *ms, uint32_t *frames
  *   CRT    float4 N (rgb, h)             CT, VAR, VAR_BLUR float N
  *   RT_MED float4 N                       RECON   float4 N (rgb, h)
  *   HIST   float4 3N: planes (An, h), (Af, g), (Bn, Bf, mu1, var) -- luminance mean and variance
+ * With DOF_STORAGE_F16 the colour buffers MAIN, PP_MED, CRT, RT_MED and RECON hold N half4
+ * in their first 8N bytes, and PRE holds per pixel a 16-byte record: (r, g) and (b, 0) as
+ * half2, then rho and the depth as floats.
  * *dev_ptr is owned by the history and valid until the next call that uses it. */
 enum {
     DOF_BUF_PP_IN = 0, DOF_BUF_Z_H, DOF_BUF_TILES, DOF_BUF_TILES_DIL, DOF_BUF_PRE,

@@ -59,6 +59,35 @@ __device__ __forceinline__ float4 bilinear4(const float4 *__restrict__ img, int 
     return f4fma(w11, d, f4fma(w01, c, f4fma(w10, b, f4scale(w00, a))));
 }
 
+// The prefilter's output texel (rgb, rho) and the depth z as the main filter reads them.
+// FP32 storage: (rgb, rho) in pre, z in z_h.  FP16 storage: one 16-byte record per
+// texel in pre, (r, g) and (b, 0) as half2, then rho and z as floats, so that a tap
+// reads a texel with one load (rho and z keep FP32: the filter's weights compare them).
+__device__ __forceinline__ float4 pre_record(float4 c, float z) {
+    __half2 rg = __floats2half2_rn(c.x, c.y), b0 = __floats2half2_rn(c.z, 0.f);
+    return make_float4(__uint_as_float(*reinterpret_cast<uint32_t *>(&rg)),
+                       __uint_as_float(*reinterpret_cast<uint32_t *>(&b0)), c.w, z);
+}
+__device__ __forceinline__ void pre_unpack(float4 t, float4 &c, float &z) {
+    uint32_t ux = __float_as_uint(t.x), uy = __float_as_uint(t.y);
+    const float2 rg = __half22float2(*reinterpret_cast<__half2 *>(&ux));
+    const float2 b0 = __half22float2(*reinterpret_cast<__half2 *>(&uy));
+    c = make_float4(rg.x, rg.y, b0.x, t.z);
+    z = t.w;
+}
+template <bool H>
+__device__ __forceinline__ void ld_pre(const float4 *__restrict__ pre, const float *__restrict__ z_h, size_t i,
+                                       float4 &c, float &z) {
+    if (H) {
+        pre_unpack(__ldg(pre + i), c, z);
+    } else {
+        c = __ldg(pre + i);
+        z = __ldg(z_h + i);
+    }
+}
+
+// Bilinear fetch of (rgb, rho) and z from the prefilter's output (ld_pre), clamp to edge.
+template <bool H>
 __device__ __forceinline__ void bilinear4z(const float4 *__restrict__ img, const float *__restrict__ z, int w, int h,
                                            float x, float y, float4 &out, float &zo) {
     float xf = floorf(x), yf = floorf(y);
@@ -69,24 +98,34 @@ __device__ __forceinline__ void bilinear4z(const float4 *__restrict__ img, const
     size_t qa = (size_t)ya * w, qb = (size_t)yb * w;
     float w00 = __fmul_rn(1.f - fx, 1.f - fy), w10 = __fmul_rn(fx, 1.f - fy), w01 = __fmul_rn(1.f - fx, fy),
           w11 = __fmul_rn(fx, fy);
-    out = f4fma(w11, __ldg(&img[qb + xb]), f4fma(w01, __ldg(&img[qb + xa]),
-                f4fma(w10, __ldg(&img[qa + xb]), f4scale(w00, __ldg(&img[qa + xa])))));
-    zo = fmaf(w11, __ldg(&z[qb + xb]), fmaf(w01, __ldg(&z[qb + xa]), fmaf(w10, __ldg(&z[qa + xb]), __fmul_rn(w00, __ldg(&z[qa + xa])))));
+    float4 c00, c10, c01, c11;
+    float z00, z10, z01, z11;
+    ld_pre<H>(img, z, qa + xa, c00, z00);
+    ld_pre<H>(img, z, qa + xb, c10, z10);
+    ld_pre<H>(img, z, qb + xa, c01, z01);
+    ld_pre<H>(img, z, qb + xb, c11, z11);
+    out = f4fma(w11, c11, f4fma(w01, c01, f4fma(w10, c10, f4scale(w00, c00))));
+    zo = fmaf(w11, z11, fmaf(w01, z01, fmaf(w10, z10, __fmul_rn(w00, z00))));
 }
 
 // Bilinear fetch of (rgb, rho) and z without clamping: the caller guarantees that
 // floor(x), floor(y) and their +1 neighbours lie inside the image.
+template <bool H>
 __device__ __forceinline__ void bilinear4z_interior(const float4 *__restrict__ img, const float *__restrict__ z, int w,
                                                     float x, float y, float4 &out, float &zo) {
     float xf = floorf(x), yf = floorf(y);
     float fx = x - xf, fy = y - yf;
-    int q = __float2int_rz(yf) * w + __float2int_rz(xf);
-    const float4 *p = img + q;
-    const float *pz = z + q;
+    const size_t q = (size_t)(__float2int_rz(yf) * w + __float2int_rz(xf));
     float w00 = __fmul_rn(1.f - fx, 1.f - fy), w10 = __fmul_rn(fx, 1.f - fy), w01 = __fmul_rn(1.f - fx, fy),
           w11 = __fmul_rn(fx, fy);
-    out = f4fma(w11, __ldg(p + w + 1), f4fma(w01, __ldg(p + w), f4fma(w10, __ldg(p + 1), f4scale(w00, __ldg(p)))));
-    zo = fmaf(w11, __ldg(pz + w + 1), fmaf(w01, __ldg(pz + w), fmaf(w10, __ldg(pz + 1), __fmul_rn(w00, __ldg(pz)))));
+    float4 c00, c10, c01, c11;
+    float z00, z10, z01, z11;
+    ld_pre<H>(img, z, q, c00, z00);
+    ld_pre<H>(img, z, q + 1, c10, z10);
+    ld_pre<H>(img, z, q + w, c01, z01);
+    ld_pre<H>(img, z, q + w + 1, c11, z11);
+    out = f4fma(w11, c11, f4fma(w01, c01, f4fma(w10, c10, f4scale(w00, c00))));
+    zo = fmaf(w11, z11, fmaf(w01, z01, fmaf(w10, z10, __fmul_rn(w00, z00))));
 }
 
 __device__ __forceinline__ void cx4(float4 &a, float4 &b) {

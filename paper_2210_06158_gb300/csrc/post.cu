@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(256) k_prefilter(const __grid_constant__ AS as
         ax += w * s.x; ay += w * s.y; az += w * s.z; ws += w;
     }
     float r = 1.f / ws;
-    pre[q] = make_float4(ax * r, ay * r, az * r, c0.w);
+    const float4 v = make_float4(ax * r, ay * r, az * r, c0.w);
+    pre[q] = p.f16 ? pre_record(v, __ldg(&S.z_h[q])) : v;
 }
 
 // A4: 81-tap main filter (Eq. 1).  Rings k = 1..4 of 8k taps at radius kR/4 of the
@@ -144,7 +145,7 @@ __device__ __forceinline__ void main_tap_add(const DevParams &p, float dist, flo
     m.wsum = __fadd_rn(m.wsum, W);
 }
 
-template <bool CLAMP>
+template <bool CLAMP, bool H>
 __device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const DevParams &p, const float4 *__restrict__ pre,
                                           const float *__restrict__ z_h, float R, float z0, float r0, MainAcc &m) {
     const int ring = p.ring;
@@ -155,18 +156,28 @@ __device__ __forceinline__ void main_taps(int i, int j, int W2, int H2, const De
         const float x = fmaf(dist, u.x, (float)i), y = fmaf(dist, u.y, (float)j);
         float4 s;
         float zi;
-        if (CLAMP) bilinear4z(pre, z_h, W2, H2, x, y, s, zi);
-        else bilinear4z_interior(pre, z_h, W2, x, y, s, zi);
+        if (CLAMP) bilinear4z<H>(pre, z_h, W2, H2, x, y, s, zi);
+        else bilinear4z_interior<H>(pre, z_h, W2, x, y, s, zi);
         main_tap_add(p, dist, z0, r0, s, zi, m);
     }
 }
 
-template <class AS>
+// the pixel's own depth and |CoC| from the prefilter's output (ld_pre)
+__device__ __forceinline__ void pre_centre(const float4 *__restrict__ pre, const float *__restrict__ z_h, size_t q,
+                                           bool f16, float &z0, float &r0) {
+    const float4 t = __ldg(&pre[q]);
+    z0 = f16 ? t.w : __ldg(&z_h[q]);
+    r0 = fabsf(f16 ? t.z : t.w);
+}
+
+// kStore: the launch's image storage (image_storage_mode) in all three forms
+template <class AS, int kStore>
 __global__ void __launch_bounds__(512) k_main_filter(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_GATHER, i, j);
     const DevParams &p = S.p;
+    const bool f16 = kStore == 2 ? p.f16 != 0 : kStore == 1;
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const float4 *__restrict__ pre = S.pre;
     const float *__restrict__ z_h = S.z_h;
@@ -179,13 +190,18 @@ __global__ void __launch_bounds__(512) k_main_filter(const __grid_constant__ AS 
     if (i >= W2 || j >= H2) return;
     size_t q = (size_t)j * W2 + i;
     float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
-    float z0 = __ldg(&z_h[q]);
-    float r0 = fabsf(__ldg(&pre[q]).w);
+    float z0, r0;
+    pre_centre(pre, z_h, q, f16, z0, r0);
     MainAcc m{0.f, 0.f, 0.f, 0.f, 0.f};
-    if (interior) main_taps<false>(i, j, W2, H2, p, pre, z_h, R, z0, r0, m);
-    else main_taps<true>(i, j, W2, H2, p, pre, z_h, R, z0, r0, m);
+    if (f16) {
+        if (interior) main_taps<false, true>(i, j, W2, H2, p, pre, z_h, R, z0, r0, m);
+        else main_taps<true, true>(i, j, W2, H2, p, pre, z_h, R, z0, r0, m);
+    } else {
+        if (interior) main_taps<false, false>(i, j, W2, H2, p, pre, z_h, R, z0, r0, m);
+        else main_taps<true, false>(i, j, W2, H2, p, pre, z_h, R, z0, r0, m);
+    }
     float r = 1.f / m.wsum;
-    st_img(out, q, make_float4(m.ax * r, m.ay * r, m.az * r, m.bright * r), p.f16);
+    st_img(out, q, make_float4(m.ax * r, m.ay * r, m.az * r, m.bright * r), f16);
 }
 
 // A4 by columns of four pixels: R is the dilated maximum of the pixel's 8 x 8 tile, so
@@ -195,7 +211,7 @@ __global__ void __launch_bounds__(512) k_main_filter(const __grid_constant__ AS 
 // of four rows pairs, and finishes pixel r when row r + 1 arrives; otherwise (the rare
 // tap whose rows are not consecutive in FP32) each pixel reads its own two rows.  Every
 // pixel sums its texels in the same order and with the same weights as the other forms.
-template <bool CLAMP>
+template <bool CLAMP, bool H>
 __device__ __forceinline__ void main_strip_taps(int i, int jb, int W2, int H2, const DevParams &p,
                                                 const float4 *__restrict__ pre, const float *__restrict__ z_h, float R,
                                                 const float *z0, const float *r0, MainAcc *m) {
@@ -221,8 +237,8 @@ __device__ __forceinline__ void main_strip_taps(int i, int jb, int W2, int H2, c
             auto row = [&](int k, float4 &a, float4 &b, float &za, float &zb) {
                 const int y = CLAMP ? min(max(y0[0] + k, 0), H2 - 1) : y0[0] + k;
                 const size_t q = (size_t)y * W2;
-                a = __ldg(&pre[q + xa]); b = __ldg(&pre[q + xb]);
-                za = __ldg(&z_h[q + xa]); zb = __ldg(&z_h[q + xb]);
+                ld_pre<H>(pre, z_h, q + xa, a, za);
+                ld_pre<H>(pre, z_h, q + xb, b, zb);
             };
             float4 a0, b0;
             float za0, zb0;
@@ -245,20 +261,21 @@ __device__ __forceinline__ void main_strip_taps(int i, int jb, int W2, int H2, c
                 const float y = fmaf(dist, u.y, (float)(jb + r));
                 float4 s;
                 float zi;
-                if (CLAMP) bilinear4z(pre, z_h, W2, H2, x, y, s, zi);
-                else bilinear4z_interior(pre, z_h, W2, x, y, s, zi);
+                if (CLAMP) bilinear4z<H>(pre, z_h, W2, H2, x, y, s, zi);
+                else bilinear4z_interior<H>(pre, z_h, W2, x, y, s, zi);
                 main_tap_add(p, dist, z0[r], r0[r], s, zi, m[r]);
             }
         }
     }
 }
 
-template <class AS>
+template <class AS, int kStore>
 __global__ void __launch_bounds__(512) k_main_filter_strip(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, jt;
     const SessDesc &S = block_session(A, SH_GATHER, i, jt);
     const DevParams &p = S.p;
+    const bool f16 = kStore == 2 ? p.f16 != 0 : kStore == 1;
     const int W2 = S.cam.W2, H2 = S.cam.H2;
     const float4 *__restrict__ pre = S.pre;
     const float *__restrict__ z_h = S.z_h;
@@ -276,18 +293,22 @@ __global__ void __launch_bounds__(512) k_main_filter_strip(const __grid_constant
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         const size_t q = (size_t)min(jb + r, H2 - 1) * W2 + i;
-        z0[r] = __ldg(&z_h[q]);
-        r0[r] = fabsf(__ldg(&pre[q]).w);
+        pre_centre(pre, z_h, q, f16, z0[r], r0[r]);
         m[r] = MainAcc{0.f, 0.f, 0.f, 0.f, 0.f};
     }
-    if (interior) main_strip_taps<false>(i, jb, W2, H2, p, pre, z_h, R, z0, r0, m);
-    else main_strip_taps<true>(i, jb, W2, H2, p, pre, z_h, R, z0, r0, m);
+    if (f16) {
+        if (interior) main_strip_taps<false, true>(i, jb, W2, H2, p, pre, z_h, R, z0, r0, m);
+        else main_strip_taps<true, true>(i, jb, W2, H2, p, pre, z_h, R, z0, r0, m);
+    } else {
+        if (interior) main_strip_taps<false, false>(i, jb, W2, H2, p, pre, z_h, R, z0, r0, m);
+        else main_strip_taps<true, false>(i, jb, W2, H2, p, pre, z_h, R, z0, r0, m);
+    }
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         if (jb + r >= H2) break;
         const float rw = 1.f / m[r].wsum;
         st_img(out, (size_t)(jb + r) * W2 + i, make_float4(m[r].ax * rw, m[r].ay * rw, m[r].az * rw, m[r].bright * rw),
-               p.f16);
+               f16);
     }
 }
 
@@ -299,43 +320,17 @@ __global__ void __launch_bounds__(512) k_main_filter_strip(const __grid_constant
 constexpr int kMainTileAutoBytes = 64 * 1024;
 
 __host__ __device__ inline int main_tile_halo(float rmax_hpx) { return (int)ceilf(rmax_hpx) + 2; }
-__host__ __device__ inline int main_tile_bytes(float rmax_hpx, int bw, int bh) {
+// the staged tile: (rgb, rho) and z per texel, or with FP16 storage the 16-byte records
+__host__ __device__ inline int main_tile_bytes(float rmax_hpx, int bw, int bh, bool f16) {
     const int h = main_tile_halo(rmax_hpx);
-    return (bw + 2 * h) * (bh + 2 * h) * (int)(sizeof(float4) + sizeof(float));
+    return (bw + 2 * h) * (bh + 2 * h) * (int)(f16 ? sizeof(float4) : sizeof(float4) + sizeof(float));
 }
 
-template <class AS>
-__global__ void __launch_bounds__(512) k_main_filter_tiled(const __grid_constant__ AS as_) {
-    extern __shared__ float4 sm_pre[];
-    const BatchArgs &A = batch_args(as_);
-    int i, j;
-    const SessDesc &S = block_session(A, SH_GATHER, i, j);
-    const DevParams &p = S.p;
-    const int W2 = S.cam.W2, H2 = S.cam.H2;
-    const float4 *__restrict__ pre = S.pre;
-    const float *__restrict__ z_h = S.z_h;
-    const float2 *__restrict__ dil = S.tiles_dil;
-    float4 *out = S.main_;
-    const int h = main_tile_halo(p.rmax_hpx);
-    const int bw = (int)blockDim.x, bh = (int)blockDim.y;
-    const int tw = bw + 2 * h, th = bh + 2 * h;
-    float *sm_z = reinterpret_cast<float *>(sm_pre + tw * th);
-    const int ox = i - (int)threadIdx.x - h, oy = j - (int)threadIdx.y - h;
-    for (int e = (int)(threadIdx.y * blockDim.x + threadIdx.x); e < tw * th; e += bw * bh) {
-        const int ty = e / tw, tx = e - ty * tw;
-        const int x = min(max(ox + tx, 0), W2 - 1), y = min(max(oy + ty, 0), H2 - 1);
-        const size_t g = (size_t)y * W2 + x;
-        sm_pre[e] = __ldg(&pre[g]);
-        sm_z[e] = __ldg(&z_h[g]);
-    }
-    __syncthreads();
-    if (i >= W2 || j >= H2) return;
-    const size_t q = (size_t)j * W2 + i;
-    const float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
-    const float z0 = __ldg(&z_h[q]);
-    const float r0 = fabsf(__ldg(&pre[q]).w);
+// the 81 taps of pixel (i, j) from the staged tile (origin (ox, oy), width tw)
+template <bool H>
+__device__ __forceinline__ void main_tile_taps(const float4 *sm_pre, const float *sm_z, int tw, int ox, int oy, int i,
+                                               int j, const DevParams &p, float R, float z0, float r0, MainAcc &m) {
     const int ring = p.ring;
-    MainAcc m{0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 3
     for (int t = 0; t < 81; t++) {
         const float3 u = c_rings[ring][t];
@@ -346,13 +341,59 @@ __global__ void __launch_bounds__(512) k_main_filter_tiled(const __grid_constant
         const int b = ((int)yf - oy) * tw + ((int)xf - ox);
         const float w00 = __fmul_rn(1.f - fx, 1.f - fy), w10 = __fmul_rn(fx, 1.f - fy);
         const float w01 = __fmul_rn(1.f - fx, fy), w11 = __fmul_rn(fx, fy);
-        const float4 s = f4fma(w11, sm_pre[b + tw + 1], f4fma(w01, sm_pre[b + tw], f4fma(w10, sm_pre[b + 1],
-                               f4scale(w00, sm_pre[b]))));
-        const float zi = fmaf(w11, sm_z[b + tw + 1], fmaf(w01, sm_z[b + tw], fmaf(w10, sm_z[b + 1], __fmul_rn(w00, sm_z[b]))));
+        float4 c00, c10, c01, c11;
+        float z00, z10, z01, z11;
+        if (H) {
+            pre_unpack(sm_pre[b], c00, z00);
+            pre_unpack(sm_pre[b + 1], c10, z10);
+            pre_unpack(sm_pre[b + tw], c01, z01);
+            pre_unpack(sm_pre[b + tw + 1], c11, z11);
+        } else {
+            c00 = sm_pre[b]; c10 = sm_pre[b + 1]; c01 = sm_pre[b + tw]; c11 = sm_pre[b + tw + 1];
+            z00 = sm_z[b]; z10 = sm_z[b + 1]; z01 = sm_z[b + tw]; z11 = sm_z[b + tw + 1];
+        }
+        const float4 s = f4fma(w11, c11, f4fma(w01, c01, f4fma(w10, c10, f4scale(w00, c00))));
+        const float zi = fmaf(w11, z11, fmaf(w01, z01, fmaf(w10, z10, __fmul_rn(w00, z00))));
         main_tap_add(p, dist, z0, r0, s, zi, m);
     }
+}
+
+template <class AS, int kStore>
+__global__ void __launch_bounds__(512) k_main_filter_tiled(const __grid_constant__ AS as_) {
+    extern __shared__ float4 sm_pre[];
+    const BatchArgs &A = batch_args(as_);
+    int i, j;
+    const SessDesc &S = block_session(A, SH_GATHER, i, j);
+    const DevParams &p = S.p;
+    const bool f16 = kStore == 2 ? p.f16 != 0 : kStore == 1;
+    const int W2 = S.cam.W2, H2 = S.cam.H2;
+    const float4 *__restrict__ pre = S.pre;
+    const float *__restrict__ z_h = S.z_h;
+    const float2 *__restrict__ dil = S.tiles_dil;
+    float4 *out = S.main_;
+    const int h = main_tile_halo(p.rmax_hpx);
+    const int bw = (int)blockDim.x, bh = (int)blockDim.y;
+    const int tw = bw + 2 * h, th = bh + 2 * h;
+    float *sm_z = reinterpret_cast<float *>(sm_pre + tw * th);     // FP32 storage only
+    const int ox = i - (int)threadIdx.x - h, oy = j - (int)threadIdx.y - h;
+    for (int e = (int)(threadIdx.y * blockDim.x + threadIdx.x); e < tw * th; e += bw * bh) {
+        const int ty = e / tw, tx = e - ty * tw;
+        const int x = min(max(ox + tx, 0), W2 - 1), y = min(max(oy + ty, 0), H2 - 1);
+        const size_t g = (size_t)y * W2 + x;
+        sm_pre[e] = __ldg(&pre[g]);
+        if (!f16) sm_z[e] = __ldg(&z_h[g]);
+    }
+    __syncthreads();
+    if (i >= W2 || j >= H2) return;
+    const size_t q = (size_t)j * W2 + i;
+    const float R = __ldg(&dil[(j >> 3) * p.tiles_w + (i >> 3)]).y;
+    float z0, r0;
+    pre_centre(pre, z_h, q, f16, z0, r0);
+    MainAcc m{0.f, 0.f, 0.f, 0.f, 0.f};
+    if (f16) main_tile_taps<true>(sm_pre, sm_z, tw, ox, oy, i, j, p, R, z0, r0, m);
+    else main_tile_taps<false>(sm_pre, sm_z, tw, ox, oy, i, j, p, R, z0, r0, m);
     const float r = 1.f / m.wsum;
-    st_img(out, q, make_float4(m.ax * r, m.ay * r, m.az * r, m.bright * r), p.f16);
+    st_img(out, q, make_float4(m.ax * r, m.ay * r, m.az * r, m.bright * r), f16);
 }
 
 // A5: per-channel 3x3 median (clamp-to-edge).  The block's 34x10 neighbourhood is
@@ -442,21 +483,39 @@ static int smem_optin_bytes() {
 int main_filter_tile_bytes(const BatchArgs &A) {
     if (A.main_form == 1 || A.main_form == 3) return 0;
     int bytes = 0;
-    for (int s = 0; s < A.ns; s++) bytes = max(bytes, main_tile_bytes(A.s[s].p.rmax_hpx, A.gather_w, A.gather_h));
+    for (int s = 0; s < A.ns; s++)
+        bytes = max(bytes, main_tile_bytes(A.s[s].p.rmax_hpx, A.gather_w, A.gather_h, A.s[s].p.f16 != 0));
     const int limit = A.main_form == 2 ? smem_optin_bytes() : kMainTileAutoBytes;
     return bytes <= limit ? bytes : 0;
 }
 
-// the main filter's forms loaded now (which one runs depends on the batch's radii)
-void preload_post_kernels() {
+// The main filter's forms loaded now, on the current device (which one runs depends on
+// the batch's radii, form and storage), the staged form allowed the SM's opt-in shared
+// memory.
+template <class AS, int kStore>
+static void preload_main_filter() {
     cudaFuncAttributes a;
-    cudaFuncGetAttributes(&a, k_main_filter<BatchArgs>);
-    cudaFuncGetAttributes(&a, k_main_filter_tiled<BatchArgs>);
-    cudaFuncGetAttributes(&a, k_main_filter_strip<BatchArgs>);
-    cudaFuncGetAttributes(&a, k_main_filter<const BatchArgs *>);
-    cudaFuncGetAttributes(&a, k_main_filter_tiled<const BatchArgs *>);
-    cudaFuncGetAttributes(&a, k_main_filter_strip<const BatchArgs *>);
+    cudaFuncGetAttributes(&a, k_main_filter<AS, kStore>);
+    cudaFuncGetAttributes(&a, k_main_filter_strip<AS, kStore>);
+    cudaFuncSetAttribute(k_main_filter_tiled<AS, kStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_optin_bytes());
+}
+void preload_post_kernels() {
+    preload_main_filter<BatchArgs, 0>();
+    preload_main_filter<BatchArgs, 1>();
+    preload_main_filter<BatchArgs, 2>();
+    preload_main_filter<const BatchArgs *, 0>();
+    preload_main_filter<const BatchArgs *, 1>();
+    preload_main_filter<const BatchArgs *, 2>();
     cudaGetLastError();
+}
+
+template <class AS, int kStore>
+static void launch_main_filter(const BatchArgs &A, const AS &as, int tile_bytes, cudaStream_t st) {
+    const dim3 grid(A.start[SH_GATHER][A.ns]), gb(A.gather_w, A.gather_h);
+    if (tile_bytes > 0) k_main_filter_tiled<AS, kStore><<<grid, gb, tile_bytes, st>>>(as);
+    else if (A.main_form == 3) k_main_filter_strip<AS, kStore><<<grid, gb, 0, st>>>(as);
+    else k_main_filter<AS, kStore><<<grid, gb, 0, st>>>(as);
 }
 
 template <class AS>
@@ -466,18 +525,10 @@ void launch_pp_b(const BatchArgs &A, const AS &as, cudaStream_t st, DofHistory *
     tmark(tm, DOF_K_PREFILTER, st);
     // the shared-memory form when every session's halo tile fits
     const int tile_bytes = main_filter_tile_bytes(A);
-    const dim3 gb(A.gather_w, A.gather_h);
-    if (tile_bytes > 0) {
-        static bool attr_set = false;    // per argument form (one instantiation each)
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_main_filter_tiled<AS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_bytes());
-            attr_set = true;
-        }
-        k_main_filter_tiled<AS><<<A.start[SH_GATHER][n], gb, tile_bytes, st>>>(as);
-    } else if (A.main_form == 3) {
-        k_main_filter_strip<AS><<<A.start[SH_GATHER][n], gb, 0, st>>>(as);
-    } else {
-        k_main_filter<AS><<<A.start[SH_GATHER][n], gb, 0, st>>>(as);
+    switch (image_storage_mode(A)) {
+    case 0: launch_main_filter<AS, 0>(A, as, tile_bytes, st); break;
+    case 1: launch_main_filter<AS, 1>(A, as, tile_bytes, st); break;
+    default: launch_main_filter<AS, 2>(A, as, tile_bytes, st); break;
     }
     tmark(tm, DOF_K_MAIN, st);
     k_median_pp<AS><<<A.start[SH_HPX][n], dim3(32, 8), 0, st>>>(as);

@@ -367,7 +367,7 @@ __global__ void k_edges(const __grid_constant__ AS as_) {
 // pixel order), cells taken in Morton order, so the 32 rays a tracer warp takes leave
 // nearby lens points for nearby pixels and stay close together through the blurred near
 // field.  The grouping changes no result: every ray is traced independently.
-constexpr int kMaxLensGrid = 16, kMaxLensCells = 256;
+constexpr int kMaxLensGrid = 16, kMaxLensCells = kMaxLensGrid * kMaxLensGrid;
 
 __device__ __forceinline__ int morton2(int x, int y) {
     int m = 0;

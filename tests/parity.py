@@ -89,6 +89,15 @@ class GpuRunner:
             return a.reshape(H2, W2, 4).astype(np.float32)
         return self.hist.read(name, shape=(H2, W2, 4))
 
+    def read_pre(self, H2, W2):
+        """The prefilter's output (rgb, rho) as float32 (H2, W2, 4): with FP16 storage
+        each texel is a 16-byte record, (r, g) and (b, 0) as half2, then rho and z."""
+        if int(self.params.get("image_storage", 0)) == 1:
+            raw = self.hist.read("PRE", np.uint32).reshape(H2, W2, 4)
+            rgb = raw[..., :2].copy().view(np.float16).reshape(H2, W2, 4)[..., :3].astype(np.float32)
+            return np.concatenate([rgb, raw[..., 2:3].view(np.float32)], axis=-1)
+        return self.hist.read("PRE", shape=(H2, W2, 4))
+
     def read_all(self):
         H2, W2 = self.w.H // 2, self.w.W // 2
         N = H2 * W2
@@ -100,7 +109,7 @@ class GpuRunner:
         r["z_h"] = h.read("Z_H", shape=(H2, W2))
         r["tile_raw"] = h.read("TILES", shape=(TH, TW, 2))
         r["tile_dil"] = h.read("TILES_DIL", shape=(TH, TW, 2))
-        r["pre"] = h.read("PRE", shape=(H2, W2, 4))
+        r["pre"] = self.read_pre(H2, W2)
         r["main_out"] = self.read_img("MAIN", H2, W2)
         r["pp_med"] = self.read_img("PP_MED", H2, W2)
         r["xn"] = h.read("XN", shape=(H2, W2))
