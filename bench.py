@@ -422,9 +422,16 @@ def run_ours(args, rank, world):
     ms_per_step = ms / args.steps
     value = job_value(args.steps, ms, world)
 
-    # ---- the FP16-storage variant over the same steps (another session history)
+    # ---- the FP16-storage variant over the same steps (another session history), with
+    # the gathers' launch settings tuned for it (its texels are smaller)
     p16 = dof.params_struct(dict(prm, image_storage=1))
     h16 = dof.History(ctx, w.W, w.H, max_rays=spp, taa=args.taa)
+    if pinned:
+        gsel16 = gsel
+    else:
+        gsel16, _ = tune.tune_gathers(ctx, lambda k: dof.frame(ctx, scene, gbs[k % CYCLE], None, None, h16, out,
+                                                              cam_struct=cams[k % len(cams)], params_s=p16), frames=4)
+        h16.reset()
     for s in range(args.warmup):
         dof.frame(ctx, scene, gbs[s % CYCLE], None, None, h16, out, cam_struct=cams[s], params_s=p16)
     torch.cuda.synchronize()
@@ -436,8 +443,12 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     ms16 = max_over_ranks(f0.elapsed_time(f1))
     fp16 = {"ms_per_step": round(ms16 / args.steps, 4), "value": round(job_value(args.steps, ms16, world), 2),
-            "unit": "frames/s", "storage": "colour image buffers FP16, FP32 arithmetic/depth/CoC/history"}
+            "unit": "frames/s", "storage": "colour image buffers FP16, FP32 arithmetic/depth/CoC/history",
+            "gathers": dict(main_filter_block=list(gsel16["gather_block"]), main_filter_form=gsel16["main_form"],
+                            recon_block=list(gsel16["recon_block"]))}
     del h16
+    # the FP32 session's gather settings again for the instrumented pass
+    ctx.set_gather(block=gsel["gather_block"], main_form=gsel["main_form"], recon_block=gsel["recon_block"])
 
     # ---- instrumented pass: per-kernel device times over the same kind of steps
     htime = dof.History(ctx, w.W, w.H, max_rays=spp, timing=True, taa=args.taa)
@@ -675,12 +686,20 @@ def run_batch(args):
             dof.frame(ctx, s["sc"], s["gbs"][f], None, None, s["hs"], s["out"], cam_struct=s["cams"][f],
                       params_s=s["p"])
 
-    # the autotuner picks the tracer's tree and launch shape on the batch (untimed)
+    # the autotuners pick the tracer's tree and launch shape and the gathers' launch
+    # settings on the batch, and the gathers' again for the FP16-storage batch (untimed)
     t0 = time.perf_counter()
     tuned, _ = tune.tune_trace(ctx, batched, frames=2)
+    gsel16, _ = tune.tune_gathers(ctx, batched16, frames=2)
+    gsel, _ = tune.tune_gathers(ctx, batched, frames=2)
     tune_s = time.perf_counter() - t0
     for s in S:
         s["hb"].reset()
+        s["h16"].reset()
+
+    def gathers(g):
+        return dict(main_filter_block=list(g["gather_block"]), main_filter_form=g["main_form"],
+                    recon_block=list(g["recon_block"]))
 
     def graph_items(step):
         f = step % 8
@@ -693,8 +712,11 @@ def run_batch(args):
         graph.launch(graph_items(step))
 
     res = {}
-    for name, fn in (("batched", batched), ("batched_graph", batched_graph), ("batched_fp16", batched16),
-                     ("per_frame", single)):
+    for name, fn in (("batched", batched), ("batched_graph", batched_graph), ("per_frame", single),
+                     ("batched_fp16", batched16)):
+        if name == "batched_fp16":
+            ctx.set_gather(block=gsel16["gather_block"], main_form=gsel16["main_form"],
+                           recon_block=gsel16["recon_block"])
         for k in range(args.warmup):
             fn(k)
         torch.cuda.synchronize()
@@ -717,7 +739,7 @@ def run_batch(args):
                                      f"1280x720/1920x1080/2560x1440 cycled ({px / 1e6:.1f} Mpx per step), 8-frame dollies, "
                                      "one dof_batch_frame (one launch per pass) per step",
                             l2="inputs larger than L2: 256 distinct G-buffers",
-                            tracer=dict(tuned, tune_s=round(tune_s, 2))),
+                            tracer=dict(tuned, tune_s=round(tune_s, 2)), gathers=gathers(gsel)),
                 per_frame_form=dict(frames_per_s=round(res["per_frame"]["frames_per_s"], 2),
                                     ms_per_step=round(res["per_frame"]["ms_per_step"], 3),
                                     note="plain FP32, one dof_frame per session"),
@@ -726,7 +748,8 @@ def run_batch(args):
                                         note="the same step captured once as a CUDA graph and replayed"),
                 batched_fp16_form=dict(frames_per_s=round(res["batched_fp16"]["frames_per_s"], 2),
                                        ms_per_step=round(res["batched_fp16"]["ms_per_step"], 3),
-                                       note="FP16 storage of the colour image buffers, FP32 arithmetic"),
+                                       note="FP16 storage of the colour image buffers, FP32 arithmetic",
+                                       gathers=gathers(gsel16)),
                 gpu_launches=res["batched"]["launches"], clocks=res["batched"]["clocks"])
     return line
 
@@ -826,10 +849,16 @@ def run_serve(args):
                                poses=w.poses, intr=w.intr)
         srv.admit(k, specs[k])
     setup_s = time.time() - t0
-    # start-up: the tracer's settings tuned on batched steps of the admitted sessions
+    # start-up: the tracer's and the gathers' settings tuned on batched steps of the
+    # admitted sessions (the gathers' once per image storage)
     t1 = time.time()
     tracer = ex.tune()
     tracer = dict(tracer, tune_s=round(time.time() - t1, 2))
+    gathers = dict(ex.gathers)
+
+    def gather_rec(g):
+        return dict(main_filter_block=list(g["gather_block"]), main_filter_form=g["main_form"],
+                    recon_block=list(g["recon_block"]))
     admitted = {k: v for k, v in specs.items() if k in srv.specs}
     nominal = {k: v.fps for k, v in admitted.items()}
     offered_nominal = sum(nominal.values())
@@ -875,6 +904,8 @@ def run_serve(args):
     # admission under a budget that binds: 8 GB admits only part of the 64 sessions
     ex8 = GpuExecutor(budget_bytes=8 << 30, gbuf_ring=2)
     ex8.ctx.set_trace(**{k: v for k, v in tracer.items() if k != "tune_s"})
+    ex8.gathers = gathers
+    ex8.set_form(per_frame=False, fp16=False)
     srv8 = Server(ex8, max_batch=32)
     specs8 = {k: SessionSpec(f"s{k}", w.W, w.H, 30.0 if k % 2 == 0 else 60.0, scene=w.scene, params=w.params,
                              poses=w.poses, intr=w.intr) for k, w in enumerate(ws)}
@@ -895,7 +926,8 @@ def run_serve(args):
                 config=dict(workload="serving: 64 sessions, Poisson frame requests (nominal 30/60 fps), "
                                      f"{duration:g} s per point, 1280x720..3840x2160, lawn scenes 100k-2M "
                                      "triangles, 40 GB device budget, continuous batching (<= 32 per launch, "
-                                     "2 streams)", tracer=tracer),
+                                     "2 streams)", tracer=tracer,
+                            gathers={"fp32": gather_rec(gathers[False]), "fp16": gather_rec(gathers[True])}),
                 served=dict(p50_ms_at_half_load=half["p50_ms"], p99_ms_at_half_load=half["p99_ms"],
                             admitted=len(admitted), rejected=n_rejected),
                 forms=out, budget_8gb=budget8, setup_s=round(setup_s, 1), clocks=clk.summary(),

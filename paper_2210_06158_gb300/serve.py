@@ -126,6 +126,7 @@ class GpuExecutor:
         from . import dof
         self.torch, self.dof = torch, dof
         self.per_frame, self.fp16 = per_frame, fp16
+        self.gathers = {}              # image storage (fp16) -> the gathers' tuned settings
         self.record = record
         self.records = {}
         self.ctx = dof.Context(device, mem_budget_bytes=budget_bytes)
@@ -146,7 +147,7 @@ class GpuExecutor:
     def estimate_bytes(self, spec):
         hpx = (spec.width // 2) * (spec.height // 2)
         mr = int(spec.params.get("spp", 1)) if int(spec.params.get("ray_mode", 0)) == 0 else int(spec.params.get("m", 1))
-        return int(hpx * (400 + 36 * mr) + spec.scene.n_tris * 112)
+        return int(hpx * (411 + 36 * mr) + spec.scene.n_tris * 112)
 
     def open(self, sid, spec):
         from synth.scenes import Camera
@@ -172,9 +173,12 @@ class GpuExecutor:
         torch.cuda.synchronize()
 
     def tune(self, frames=2, max_batch=32):
-        """Autotune the tracer (tune.tune_trace) on batched steps of the admitted sessions
-        (up to max_batch of them, one frame each), as a server does at start-up; the
-        context keeps the pick and every history starts afresh.  Returns the pick."""
+        """Autotune the tracer (tune.tune_trace) and then the gathers' launch settings
+        (tune.tune_gathers, once per image storage: FP16 texels are smaller) on batched
+        steps of the admitted sessions (up to max_batch of them, one frame each), as a
+        server does at start-up.  The context keeps the tracer's pick and the gathers'
+        pick of the current form (set_form applies the pick of its storage); every
+        history starts afresh.  Returns the tracer's pick."""
         from . import tune
         sids = list(self.sessions)[:max_batch]
         st = self.streams[0]
@@ -188,9 +192,11 @@ class GpuExecutor:
             self.dof.batch_frame(self.ctx, items, stream=st)
 
         best, _ = tune.tune_trace(self.ctx, step, frames=frames, stream=st)
-        self.torch.cuda.synchronize()
-        for s in self.sessions.values():
-            s["hist"].reset()
+        fp16 = self.fp16
+        for f16 in (not fp16, fp16):
+            self.set_form(self.per_frame, f16)
+            self.gathers[f16], _ = tune.tune_gathers(self.ctx, step, frames=frames, stream=st)
+        self.set_form(self.per_frame, fp16)
         return best
 
     def set_form(self, per_frame=False, fp16=False):
@@ -198,6 +204,9 @@ class GpuExecutor:
         FP32 image storage) and start its history afresh."""
         self.torch.cuda.synchronize()
         self.per_frame, self.fp16 = per_frame, fp16
+        g = self.gathers.get(fp16)
+        if g is not None:
+            self.ctx.set_gather(block=g["gather_block"], main_form=g["main_form"], recon_block=g["recon_block"])
         for s in self.sessions.values():
             prm = dict(s["spec"].params, image_storage=1) if fp16 else s["spec"].params
             s["pstruct"] = self.dof.params_struct(prm)

@@ -1,6 +1,6 @@
 """Served frames (continuous batching over dof_batch_frame, two streams) equal the
 frames of each session run alone: every served frame, in the batched FP32 form (with
-the tracer tuned at start-up) and in the batched FP16-storage form."""
+the tracer and the gathers tuned at start-up) and in the batched FP16-storage form."""
 
 import pytest
 
@@ -27,6 +27,7 @@ def test_every_served_frame_equals_alone(fp16):
     if not fp16:
         pick = ex.tune(frames=1)                  # start-up tuning (histories start afresh)
         assert set(pick) >= {"bvh_width", "ray_grid", "packets"}
+        assert set(ex.gathers) == {False, True}   # the gathers' picks per image storage
     st = srv.run(poisson_arrivals(5, specs, duration_s=0.5))
     assert st["frames"] > 10 and st["failed"] == 0
     assert st["mean_batch"] > 1.0                 # requests did share launches
