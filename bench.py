@@ -320,6 +320,8 @@ def run_ours(args, rank, world):
     if args.taa:
         w.jitter = True
         prm["taa_alpha"] = 0.1
+    if args.image_storage == "f16":
+        prm["image_storage"] = 1
     spp = int(prm["spp"])
     ctx = dof.Context(local)
     stream = torch.cuda.current_stream()
@@ -586,7 +588,8 @@ def run_ours(args, rank, world):
                config=dict(workload=f"{w.name}: {w.W}x{w.H}, {info.n_tris} triangles (lawn + box field), "
                                     f"{w.intr['f_m'] * 1000:.0f} mm f/{w.intr['f_number']:g} focus "
                                     f"{w.intr['focus_m']:g} m, CoC radius <= {prm['max_coc_px']:g} px, {spp} spp, "
-                                    f"16-frame dolly" + (", camera jitter + final TAA (blend 0.1)" if args.taa else ""),
+                                    f"16-frame dolly" + (", camera jitter + final TAA (blend 0.1)" if args.taa else "")
+                                    + (", FP16 image storage" if args.image_storage == "f16" else ""),
                            resolution=[w.W, w.H], triangles=info.n_tris, spp=spp, bvh_depth=info.depth,
                            tracer=dict(tuned, tune_s=round(tune_s, 2)), gathers=gathers,
                            parallelism="replicas" if world > 1 else "single-gpu",
@@ -966,6 +969,8 @@ def main():
                     help="camera jitter (Halton 2, 3) and the final TAA pass with blend 0.1")
     ap.add_argument("--size", default=None,
                     help="WxH: the workload's scene, lens and camera path at another resolution (profiler captures)")
+    ap.add_argument("--image-storage", default="f32", choices=["f32", "f16"],
+                    help="colour image buffers of the timed session (f16: the FP16-storage form; profiler captures)")
     ap.add_argument("--bvh-width", type=int, default=None, choices=[2, 4],
                     help="traverse this tree width instead of the autotuner's choice (profiler captures)")
     ap.add_argument("--settings", default=None,
