@@ -360,6 +360,30 @@ __global__ void k_rotate(int n, BvhNode *nodes, int *parent_node, int *parent_le
     }
 }
 
+// Structure check of the finished binary tree, before any traversal relies on it: every
+// child reference in range (internal nodes 0 .. n_nodes - 1, leaves ~0 .. ~(n_tree - 1)),
+// and every internal node except the root, and every leaf, referenced by exactly one
+// internal node, the root by none.  Nodes on a cycle would take their one reference from
+// inside the cycle, so none is reachable from the root: a traversal from the root visits
+// each node at most once and reads only in-range nodes and triangles.
+__global__ void k_tree_refs(const BvhNode *nodes, int n_nodes, int n_tree, int *ref_node, int *ref_leaf, int *bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_nodes) return;
+    const int4 r = nodes[i].r;
+    const int c[2] = {r.x, r.y};
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        if (c[e] >= 0 ? c[e] >= n_nodes : ~c[e] >= n_tree) { atomicExch(bad, 8); continue; }
+        atomicAdd(c[e] >= 0 ? &ref_node[c[e]] : &ref_leaf[~c[e]], 1);
+    }
+}
+__global__ void k_tree_counts(int n_nodes, int n_tree, int root, const int *ref_node, const int *ref_leaf, int *bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && (root < 0 || root >= n_nodes)) atomicExch(bad, 9);
+    if (i < n_nodes && ref_node[i] != (i == root ? 0 : 1)) atomicExch(bad, 9);
+    if (i < n_tree && ref_leaf[i] != 1) atomicExch(bad, 9);
+}
+
 // tree depth (levels from the root to the deepest leaf, root = 1)
 __global__ void k_depth(int n, const int *parent_node, const int *parent_leaf, int *depth) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -890,6 +914,13 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
                 k_rotate<<<blocks_for(m, B), B, 0, st>>>(m, s->nodes, pnode, pleaf, arr, ibuf + 6);
             }
             k_depth<<<blocks_for(m, B), B, 0, st>>>(m, pnode, pleaf, ibuf + 7);
+            // the structure the packet tracer relies on (k_tree_refs); the sort's second
+            // buffers count the leaves' references
+            ck(cudaMemsetAsync(arr, 0, sizeof(int) * (m - 1), st), "memset");
+            ck(cudaMemsetAsync(vals2, 0, sizeof(int) * m, st), "memset");
+            int *ref_leaf = reinterpret_cast<int *>(vals2);
+            k_tree_refs<<<blocks_for(m - 1, B), B, 0, st>>>(s->nodes, m - 1, m, arr, ref_leaf, ibuf + 6);
+            k_tree_counts<<<blocks_for(m, B), B, 0, st>>>(m - 1, m, root, arr, ref_leaf, ibuf + 6);
         }
         s->root = root;
         ck(cudaGetLastError(), "bvh kernels");

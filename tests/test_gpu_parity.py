@@ -841,3 +841,35 @@ def test_packets_in_adaptive_mode_equal_one_ray_per_lane(grid):
         assert np.array_equal(results[0][0][f], results[1][0][f]), f
     assert np.array_equal(results[0][1], results[1][1])
     assert np.array_equal(results[0][2], results[1][2])
+
+
+def test_packets_on_tiny_trees_equal_one_ray_per_lane():
+    """Warp packets on the smallest trees -- no triangle, one (the root is a leaf), two,
+    seven, and 64 and 200 with shared-edge and coplanar ties -- give the per-ray tracer's
+    hit ids and images bit for bit with the device status clear.  The packet loop has no
+    per-step guard: it relies on the structure check each tree passes at upload."""
+    from paper_2210_06158_gb300 import dof
+    import torch
+    ctx = dof.Context(0)
+    pose = camera_pose((0.0, 0.0, 0.0), pitch_deg=0.0)
+    cam = Camera.from_poses(dict(f_m=0.085, f_number=1.2, focus_m=30.0, sensor_w_m=0.036), pose)
+    W, H = 128, 72
+    prm = default_params(spp=4, mask_near_hpx=0.0, max_coc_px=16.0)
+    for n in [0, 1, 2, 7, 64, 200]:
+        sc = dof.Scene(ctx, tiny_scene(700 + n, n, ties=n >= 8))
+        gb = dof.gbuffer(ctx, sc, cam, prm, W, H)
+        del gb["prim"]
+        results = []
+        for packets in (0, 1):
+            ctx.set_trace(bvh_width=2, ray_grid=4, packets=packets)
+            h = dof.History(ctx, W, H, max_rays=4, record_rays=True)
+            out = dof.frame(ctx, sc, gb, cam, prm, h).cpu().numpy()
+            torch.cuda.synchronize()
+            st = h.stats()
+            assert st.device_status == 0, (n, packets)
+            assert n == 0 or st.rays > 0, n
+            results.append((out, h.read("RAY_PRIM", np.int32)))
+            h.close()
+        assert np.array_equal(results[0][0], results[1][0]), n
+        assert np.array_equal(results[0][1], results[1][1]), n
+        sc.close()
