@@ -66,11 +66,11 @@ FP32_LANES_PER_SM = 128
 # 1920x1080 (same scene, lens, 4 spp, rays grouped by lens cell) and are scaled by the
 # rays of a full launch (6.73M / 1.78M); their DRAM writes are the rays they keep for the
 # shader that L2 does not hold, so the scaled figures are estimates.
-PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_trace_packets": 7.467e6 + 0.0,
-                           "k_recon": 27.253e6 + 1.536e3, "k_main_filter": None, "k_accumulate": None, "k_composite": None,
+PROFILED_TRAFFIC = {"c2": {"k_trace_rays<1>": None, "k_trace_rays<0>": None, "k_trace_packets": 7.486e6 + 0.0,
+                           "k_recon": 27.234e6 + 13.8e3, "k_main_filter": None, "k_accumulate": None, "k_composite": None,
                            "k_downscale_tiles": None},
                     "c3": {"k_trace_rays<0>": (21.68e6 + 10.87e6) * 6.72 / 1.78,
-                           "k_trace_packets": (19.646e6 + 4.697e6) * 6.73 / 1.78}}
+                           "k_trace_packets": (19.363e6 + 3.338e6) * 6.723 / 1.778}}
 
 # Algorithmic (compulsory) DRAM bytes of each kernel per unit (FP32 layouts): per
 # half-resolution pixel N, per masked pixel M, per ray R, per full-resolution pixel P.
