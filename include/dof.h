@@ -219,6 +219,10 @@ const char *dof_last_error(void);
  *   xyz      host, n_verts * 3 floats
  *   tri_idx  host, n_tris * 3 vertex indices (< n_verts, checked)
  *   tri_mat  host, n_tris material ids (0 diffuse with hash albedo, 1 emitter), or NULL
+ * The finished binary tree is checked before the call returns: every child reference
+ * in range, and every node but the root, and every leaf, referenced exactly once.  A
+ * tree that fails returns DOF_ERR_DEVICE_CHECK; the warp-packet traversal relies on the
+ * check instead of a per-step guard.
  * The call copies the data, builds on `stream` and synchronises that stream before
  * returning (the scene is then immutable and usable from any stream).  The library
  * owns the returned scene; release it with dof_scene_destroy. */
