@@ -23,9 +23,8 @@ __device__ __forceinline__ bool project_prev(const DevCam &c, float3 rel, float 
 struct NearH {
     float4 a;          // sum w (An, h)
     float bn, m1;      // sum w Bn, sum w mu1
-    float wv[4], x[4]; // per tap: w, and its (mu1, variance) for the second variance pass
-    float v[4];
-    int n;
+    float wv[4], x[4]; // per tap: w (0 for a dropped tap), and its (mu1, variance) for the
+    float v[4];        // second variance pass; indexed by the unrolled tap, so in registers
 };
 struct FarH { float4 a; float bf; };            // (Af, g), Bf
 
@@ -53,7 +52,7 @@ __device__ __forceinline__ float fetch(const float4 *__restrict__ H0, const floa
             nh.a = f4fma(w, h0, nh.a);
             nh.bn += w * h2.x;
             nh.m1 += w * h2.z;
-            nh.wv[nh.n] = w; nh.x[nh.n] = h2.z; nh.v[nh.n] = h2.w; nh.n++;
+            nh.wv[t] = w; nh.x[t] = h2.z; nh.v[t] = h2.w;
         } else {
             fh.a = f4fma(w, h1, fh.a);
             fh.bf += w * h2.y;
@@ -125,7 +124,9 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AS a
     }
     NearH nh, ndummy;
     FarH fh, fdummy;
-    nh.a = make_float4(0.f, 0.f, 0.f, 0.f); nh.bn = nh.m1 = 0.f; nh.n = 0;
+    nh.a = make_float4(0.f, 0.f, 0.f, 0.f); nh.bn = nh.m1 = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; t++) nh.wv[t] = nh.x[t] = nh.v[t] = 0.f;
     ndummy = nh;
     fh.a = nh.a; fh.bf = 0.f;
     fdummy = fh;
@@ -151,7 +152,9 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AS a
     float m1 = a * nh.m1 + kn * L;
     float dl = L - m1;
     float v = kn * dl * dl;
-    for (int t = 0; t < nh.n; t++) {
+    // the taps in order; a dropped tap (w = 0, x = v = 0) adds exactly +0
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
         float dx = nh.x[t] - m1;
         v += a * nh.wv[t] * (nh.v[t] + dx * dx);
     }
