@@ -283,9 +283,11 @@ __device__ __forceinline__ void recon_taps(const MipLevel &L0, const MipLevel &L
 // A11: reconstruction.  Blocks whose footprint (+-rmax + 2, at every level) lies
 // inside the image take taps without index clamping.  kStore: the launch's image storage
 // (image_storage_mode); the specialised instances hold the code of one storage only, and
-// with it fewer registers.
+// with it fewer registers.  72 registers hold either storage's taps without spilling
+// (three 256-thread blocks per SM; a cap of 64 spilled the FP32 form's state through
+// L1, the unit that bounds it, and was 1-2% slower).
 template <class AS, int kStore>
-__global__ void __launch_bounds__(512, 2) k_recon(const __grid_constant__ AS as_) {
+__global__ void __maxnreg__(72) k_recon(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     int i, j;
     const SessDesc &S = block_session(A, SH_RECON, i, j);
