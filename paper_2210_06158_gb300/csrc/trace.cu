@@ -763,9 +763,8 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
                         const int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
                         float t0, t1;
                         bool h0, h1;
-                        box_pair(ray, a, b, c, h.t, h0, t0, h1, t1);
-                        h0 = h0 && act;
-                        h1 = h1 && act;
+                        // a lane without act enters no box: its best distance reads -1
+                        box_pair(ray, a, b, c, act ? h.t : -1.f, h0, t0, h1, t1);
                         n_visit += act ? 1u : 0u;
                         const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
                         if (m0 && m1) {
