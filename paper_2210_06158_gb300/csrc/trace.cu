@@ -62,8 +62,8 @@ __device__ __forceinline__ bool box_hit_o(const Ray &r, float3 lo, float3 hi, fl
     return tmin <= tmax * 1.0000005f;
 }
 
-// both child boxes of a binary node, the octant's instance chosen by conditional
-// branches (uniform across a warp whose rays share the octant)
+// both child boxes of a binary node, the octant's instance chosen by one multiway
+// branch (uniform across a warp whose rays share the octant)
 __device__ __forceinline__ void box_pair(const Ray &r, const float4 &a, const float4 &b, const float4 &c,
                                          float tbest, bool &h0, float &t0, bool &h1, float &t1) {
     const float3 lo0 = make_float3(a.x, a.y, a.z), hi0 = make_float3(a.w, b.x, b.y);
@@ -73,13 +73,15 @@ __device__ __forceinline__ void box_pair(const Ray &r, const float4 &a, const fl
         h0 = box_hit_o<X, Y, Z>(r, lo0, hi0, tbest, t0);        \
         h1 = box_hit_o<X, Y, Z>(r, lo1, hi1, tbest, t1);        \
     }
-    const int o = r.oct;
-    if (o & 4) {
-        if (o & 2) { if (o & 1) DOF_BOX_PAIR(true, true, true) else DOF_BOX_PAIR(false, true, true) }
-        else { if (o & 1) DOF_BOX_PAIR(true, false, true) else DOF_BOX_PAIR(false, false, true) }
-    } else {
-        if (o & 2) { if (o & 1) DOF_BOX_PAIR(true, true, false) else DOF_BOX_PAIR(false, true, false) }
-        else { if (o & 1) DOF_BOX_PAIR(true, false, false) else DOF_BOX_PAIR(false, false, false) }
+    switch (r.oct & 7) {
+    case 0: DOF_BOX_PAIR(false, false, false) break;
+    case 1: DOF_BOX_PAIR(true, false, false) break;
+    case 2: DOF_BOX_PAIR(false, true, false) break;
+    case 3: DOF_BOX_PAIR(true, true, false) break;
+    case 4: DOF_BOX_PAIR(false, false, true) break;
+    case 5: DOF_BOX_PAIR(true, false, true) break;
+    case 6: DOF_BOX_PAIR(false, true, true) break;
+    default: DOF_BOX_PAIR(true, true, true) break;
     }
 #undef DOF_BOX_PAIR
 }
