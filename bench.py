@@ -325,6 +325,8 @@ def run_ours(args, rank, world):
     spp = int(prm["spp"])
     ctx = dof.Context(local)
     stream = torch.cuda.current_stream()
+    # the packet tracer's visit counters only in the instrumented pass below
+    ctx.set_trace(stats=False)
 
     t0 = time.perf_counter()
     scene = dof.Scene(ctx, w.scene)
@@ -452,7 +454,9 @@ def run_ours(args, rank, world):
     # the FP32 session's gather settings again for the instrumented pass
     ctx.set_gather(block=gsel["gather_block"], main_form=gsel["main_form"], recon_block=gsel["recon_block"])
 
-    # ---- instrumented pass: per-kernel device times over the same kind of steps
+    # ---- instrumented pass: per-kernel device times and the tracer's node visits and
+    # triangle tests over the same kind of steps
+    ctx.set_trace(stats=True)
     htime = dof.History(ctx, w.W, w.H, max_rays=spp, timing=True, taa=args.taa)
     for s in range(args.warmup):
         step(s, htime)
@@ -486,6 +490,7 @@ def run_ours(args, rank, world):
     masked_per_frame = masked / n_samples
 
     # ---- end to end through the C ABI with host buffers
+    ctx.set_trace(stats=False)
     pin = []
     for g in gbs:
         pin.append(dict(color=g["color"].cpu().pin_memory(), depth=g["depth"].cpu().pin_memory()))
@@ -655,6 +660,7 @@ def run_batch(args):
     _build.build()
     dev = torch.device("cuda", 0)
     ctx = dof.Context(0)
+    ctx.set_trace(stats=False)          # no node-visit counters in these timings
     ws = batch_sessions(32, RES, 200_000, 1_000_000, seed=4)
     S = []
     for w in ws:
@@ -770,6 +776,7 @@ def run_budget(args):
     dev = torch.device("cuda", 0)
     w = make_workload("c2")
     ctx = dof.Context(0)
+    ctx.set_trace(stats=False)          # no node-visit counters in these timings
     scene = dof.Scene(ctx, w.scene)
     gbs = []
     for k in range(CYCLE):

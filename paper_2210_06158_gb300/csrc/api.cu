@@ -217,6 +217,7 @@ extern "C" int dof_ctx_create(int device, size_t mem_budget_bytes, DofCtx **out)
     c->trace_steps = 64;
     c->ray_order_grid = 4;
     c->trace_packets = 0;
+    c->trace_stats = 1;
     c->stack_depth = kTraversalStack;
     c->gather_w = 32;
     c->gather_h = 8;
@@ -306,6 +307,10 @@ extern "C" int dof_ctx_set_option(DofCtx *ctx, int option, int64_t value) {
         case DOF_OPT_TRACE_PACKETS:
             if (value != 0 && value != 1) return dof_set_error(DOF_ERR_INVALID_ARG, "trace packets must be 0 or 1");
             ctx->trace_packets = (int)value;
+            return DOF_OK;
+        case DOF_OPT_TRACE_STATS:
+            if (value != 0 && value != 1) return dof_set_error(DOF_ERR_INVALID_ARG, "trace stats must be 0 or 1");
+            ctx->trace_stats = (int)value;
             return DOF_OK;
         case DOF_OPT_BVH_ROTATIONS:
             if (value < 0 || value > 16) return dof_set_error(DOF_ERR_INVALID_ARG, "BVH rotation passes must be 0..16");
@@ -774,6 +779,7 @@ static int build_batch(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n, BatchAr
     A.steps_per_round = ctx->trace_steps;
     A.lens_grid = ctx->ray_order_grid;
     A.packets = ctx->trace_packets;
+    A.stats = ctx->trace_stats;
     A.stack_depth = ctx->stack_depth;
     return DOF_OK;
 }
@@ -860,7 +866,7 @@ struct DofGraph {
     DofHistory *hist[kMaxBatch];
     int start[SH_COUNT][kMaxBatch + 1];
     bool adaptive, wide;
-    int trace_blocks, refill_idle, steps_per_round, lens_grid, stack_depth, packets;
+    int trace_blocks, refill_idle, steps_per_round, lens_grid, stack_depth, packets, stats;
     int gather_w, gather_h, main_form, recon_w, recon_h;
     int main_tile;                // the main filter's shared-memory bytes (0: through L1)
     int store_mode;               // image_storage_mode of the captured step
@@ -913,6 +919,7 @@ extern "C" int dof_graph_create(DofCtx *ctx, const DofFrameReq *reqs, uint32_t n
     g->steps_per_round = A.steps_per_round;
     g->lens_grid = A.lens_grid;
     g->packets = A.packets;
+    g->stats = A.stats;
     g->stack_depth = A.stack_depth;
     g->gather_w = A.gather_w;
     g->gather_h = A.gather_h;
@@ -971,7 +978,7 @@ extern "C" int dof_graph_launch(DofGraph *g, const DofFrameReq *reqs, uint32_t n
     if (memcmp(A.start, g->start, sizeof(A.start)) != 0 || adaptive != g->adaptive || all_wide(A) != g->wide ||
         ctx->sm_count * ctx->trace_blocks_per_sm != g->trace_blocks || main_filter_tile_bytes(A) != g->main_tile ||
         A.gather_w != g->gather_w || A.gather_h != g->gather_h || A.main_form != g->main_form ||
-        A.recon_w != g->recon_w || A.recon_h != g->recon_h || A.packets != g->packets ||
+        A.recon_w != g->recon_w || A.recon_h != g->recon_h || A.packets != g->packets || A.stats != g->stats ||
         image_storage_mode(A) != g->store_mode || any_taa(A) != g->taa)
         return dof_set_error(DOF_ERR_MISMATCH, "dof_graph_launch: launch shapes differ from the captured step");
     // the kernels' scheduling knobs come from the staged copy; keep the captured ones

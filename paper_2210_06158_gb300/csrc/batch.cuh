@@ -58,6 +58,7 @@ struct BatchArgs {
     int refill_idle, steps_per_round;   // tracer scheduling
     int lens_grid;                 // tracer work order: lens-cell grid of the mask kernel (1 = pixel order)
     int packets;                   // 1: the binary tree traversed by warp packets (k_trace_packets)
+    int stats;                     // 1: the packet tracer counts node visits and triangle tests
     int stack_depth;               // requested traversal stack entries (the launch takes an instance >= the need)
     int gather_w, gather_h;        // block of the main filter (SH_GATHER), <= 512 threads
     int recon_w, recon_h;          // block of the reconstruction (SH_RECON), <= 512 threads

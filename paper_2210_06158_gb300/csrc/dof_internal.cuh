@@ -99,7 +99,7 @@ struct DofCtx {
     int sm_count;
     int bvh_builder;               // DOF_BVH_PLOC or DOF_BVH_LBVH
     int bvh_rotations;             // passes of tree rotations after the build
-    int trace_blocks_per_sm, trace_refill_idle, trace_steps, ray_order_grid, trace_packets;
+    int trace_blocks_per_sm, trace_refill_idle, trace_steps, ray_order_grid, trace_packets, trace_stats;
     int gather_w, gather_h, main_form;   // main filter launch shape and form
     int recon_w, recon_h;                // reconstruction launch shape
     int stack_depth;                     // requested traversal stack entries (raised to the tree's need)

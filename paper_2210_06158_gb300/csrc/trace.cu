@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kTraceThreads, 7) k_trace_rays(const __grid_co
 // frustum): the warp then steps with all its lanes and one broadcast load per node, at
 // the price of the nodes that only some of its rays need.  Lanes of a warp that
 // straddles two sessions of a batch trace one session's packet after the other.
-template <int kCap, class AS>
+template <int kCap, bool kStats, class AS>
 __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid_constant__ AS as_) {
     const BatchArgs &A = batch_args(as_);
     const unsigned lane = threadIdx.x & 31;
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
                         bool h0, h1;
                         // a lane without act enters no box: its best distance reads -1
                         box_pair(ray, a, b, c, act ? h.t : -1.f, h0, t0, h1, t1);
-                        n_visit += act ? 1u : 0u;
+                        if (kStats) n_visit += act ? 1u : 0u;
                         const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
                         if (m0 && m1) {
                             const unsigned right_first = __ballot_sync(0xffffffffu, h0 && h1 && t1 < t0);
@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
                         if (m0) { node = ref.x; continue; }
                         if (m1) { node = ref.y; continue; }
                     } else if (act) {
-                        n_tests++;
+                        if (kStats) n_tests++;
                         tri_update(ray, tris, ~node, h);
                     }
                     if (sp == 0) break;
@@ -793,6 +793,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
             }
         }
     }
+    if (!kStats) return;
     unsigned long long a = n_visit, b = n_tests;
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -905,10 +906,14 @@ void launch_trace_b(const BatchArgs &A, const AS &as, int blocks, cudaStream_t s
     // what every session's tree can need
     int need = A.stack_depth;
     for (int i = 0; i < A.ns; i++) need = max(need, A.s[i].sc.stack_need);
-    if (A.packets && !wide) {
-        if (need <= 32) k_trace_packets<32, AS><<<blocks, kTraceThreads, 0, st>>>(as);
-        else if (need <= 64) k_trace_packets<64, AS><<<blocks, kTraceThreads, 0, st>>>(as);
-        else k_trace_packets<kStack, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+    if (A.packets && !wide && A.stats) {
+        if (need <= 32) k_trace_packets<32, true, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else if (need <= 64) k_trace_packets<64, true, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else k_trace_packets<kStack, true, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+    } else if (A.packets && !wide) {
+        if (need <= 32) k_trace_packets<32, false, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else if (need <= 64) k_trace_packets<64, false, AS><<<blocks, kTraceThreads, 0, st>>>(as);
+        else k_trace_packets<kStack, false, AS><<<blocks, kTraceThreads, 0, st>>>(as);
     } else if (wide) {
         if (need <= 32) k_trace_rays<true, 32, AS><<<blocks, kTraceThreads, 0, st>>>(as);
         else if (need <= 64) k_trace_rays<true, 64, AS><<<blocks, kTraceThreads, 0, st>>>(as);
@@ -934,9 +939,12 @@ template void launch_mask_b<const BatchArgs *>(const BatchArgs &, const BatchArg
 void preload_trace_kernels() {
     cudaFuncAttributes a;
 #define DOF_PRELOAD(AS)                                                        \
-    cudaFuncGetAttributes(&a, k_trace_packets<32, AS>);                        \
-    cudaFuncGetAttributes(&a, k_trace_packets<64, AS>);                        \
-    cudaFuncGetAttributes(&a, k_trace_packets<kStack, AS>);                    \
+    cudaFuncGetAttributes(&a, k_trace_packets<32, true, AS>);                  \
+    cudaFuncGetAttributes(&a, k_trace_packets<64, true, AS>);                  \
+    cudaFuncGetAttributes(&a, k_trace_packets<kStack, true, AS>);              \
+    cudaFuncGetAttributes(&a, k_trace_packets<32, false, AS>);                 \
+    cudaFuncGetAttributes(&a, k_trace_packets<64, false, AS>);                 \
+    cudaFuncGetAttributes(&a, k_trace_packets<kStack, false, AS>);             \
     cudaFuncGetAttributes(&a, k_trace_rays<true, 32, AS>);                     \
     cudaFuncGetAttributes(&a, k_trace_rays<true, 64, AS>);                     \
     cudaFuncGetAttributes(&a, k_trace_rays<true, kStack, AS>);                 \

@@ -242,13 +242,15 @@ class Context:
         _check(lib().dof_ctx_set_option(self.ptr, 6, int(width)))
 
     def set_trace(self, blocks_per_sm=None, refill_idle=None, steps=None, bvh_width=None, ray_grid=None, stack=None,
-                  packets=None):
+                  packets=None, stats=None):
         """Launch shape / scheduling of the persistent tracer, the tree it traverses, the
         order it takes the rays in (lens-cell grid; 1 = pixel order), its traversal
-        stack depth (raised to what the tree needs) and whether a warp's rays traverse
-        the binary tree as one packet -- no effect on results."""
+        stack depth (raised to what the tree needs), whether a warp's rays traverse
+        the binary tree as one packet, and whether that packet tracer counts node
+        visits and triangle tests for stats() -- no effect on results."""
         for opt, v in ((2, blocks_per_sm), (3, refill_idle), (4, steps), (6, bvh_width), (7, ray_grid), (11, stack),
-                       (12, None if packets is None else int(bool(packets)))):
+                       (12, None if packets is None else int(bool(packets))),
+                       (14, None if stats is None else int(bool(stats)))):
             if v is not None:
                 _check(lib().dof_ctx_set_option(self.ptr, opt, int(v)))
 

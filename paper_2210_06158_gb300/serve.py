@@ -130,6 +130,7 @@ class GpuExecutor:
         self.record = record
         self.records = {}
         self.ctx = dof.Context(device, mem_budget_bytes=budget_bytes)
+        self.ctx.set_trace(stats=False)    # served frames need no node-visit counters
         self.device = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(2)]
         self.sessions = {}

@@ -421,6 +421,7 @@ def test_scheduling_knobs_do_not_change_results(name, W, H):
     variants = [dict(ray_grid=1), dict(ray_grid=2), dict(ray_grid=4), dict(ray_grid=8), dict(ray_grid=12),
                 dict(ray_grid=16), dict(ray_grid=8, stack=32), dict(ray_grid=8, stack=64),
                 dict(ray_grid=1, packets=1), dict(ray_grid=4, packets=1), dict(ray_grid=8, packets=1, stack=32),
+                dict(ray_grid=4, packets=1, stats=0),
                 dict(ray_grid=1, width=2), dict(ray_grid=8, width=2, stack=32),
                 dict(block=(16, 16), main_form=0, recon=(16, 16)), dict(block=(64, 4), main_form=1, recon=(64, 8)),
                 dict(block=(32, 16), main_form=2, recon=(32, 16)), dict(block=(64, 8), main_form=2, recon=(64, 4)),
@@ -429,13 +430,16 @@ def test_scheduling_knobs_do_not_change_results(name, W, H):
     results = []
     for v in variants:
         ctx.set_trace(ray_grid=v.get("ray_grid", 4), stack=v.get("stack", 96), packets=v.get("packets", 0),
-                      bvh_width=v.get("width", 4))
+                      bvh_width=v.get("width", 4), stats=v.get("stats", 1))
         ctx.set_gather(block=v.get("block", (32, 8)), main_form=v.get("main_form", 0),
                        recon_block=v.get("recon", (32, 8)))
         h = dof.History(ctx, w.W, w.H, max_rays=oracle.max_rays(prm), record_rays=True)
         outs = [dof.frame(ctx, sc, gbs[f], w.camera(f), prm, h).cpu().numpy() for f in range(2)]
         torch.cuda.synchronize()
-        assert h.stats().device_status == 0
+        st = h.stats()
+        assert st.device_status == 0
+        # the packet tracer's counters only when asked for (the rays are counted either way)
+        assert (st.node_visits > 0) == (v.get("stats", 1) == 1) and st.rays > 0
         results.append((v, outs, h.read("RAY_PRIM", np.int32), h.read("MAIN", np.float32),
                         h.read("RECON", np.float32)))
         h.close()
