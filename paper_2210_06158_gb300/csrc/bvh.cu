@@ -365,8 +365,12 @@ __global__ void k_rotate(int n, BvhNode *nodes, int *parent_node, int *parent_le
 // and every internal node except the root, and every leaf, referenced by exactly one
 // internal node, the root by none.  Nodes on a cycle would take their one reference from
 // inside the cycle, so none is reachable from the root: a traversal from the root visits
-// each node at most once and reads only in-range nodes and triangles.
-__global__ void k_tree_refs(const BvhNode *nodes, int n_nodes, int n_tree, int *ref_node, int *ref_leaf, int *bad) {
+// each node at most once and reads only in-range nodes and triangles.  The parents are
+// recorded from the same references (parent_node / parent_leaf, -1 beforehand), so the
+// depth that k_depth then walks up from every leaf is the depth of the tree the traversal
+// reads: a leaf below a cycle walks to k_depth's cap, which the traversal stack rejects.
+__global__ void k_tree_refs(const BvhNode *nodes, int n_nodes, int n_tree, int *ref_node, int *ref_leaf,
+                            int *parent_node, int *parent_leaf, int *bad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_nodes) return;
     const int4 r = nodes[i].r;
@@ -375,6 +379,8 @@ __global__ void k_tree_refs(const BvhNode *nodes, int n_nodes, int n_tree, int *
     for (int e = 0; e < 2; e++) {
         if (c[e] >= 0 ? c[e] >= n_nodes : ~c[e] >= n_tree) { atomicExch(bad, 8); continue; }
         atomicAdd(c[e] >= 0 ? &ref_node[c[e]] : &ref_leaf[~c[e]], 1);
+        if (c[e] >= 0) parent_node[c[e]] = i;
+        else parent_leaf[~c[e]] = i;
     }
 }
 __global__ void k_tree_counts(int n_nodes, int n_tree, int root, const int *ref_node, const int *ref_leaf, int *bad) {
@@ -913,14 +919,16 @@ int launch_bvh_build(DofScene *s, const float *d_xyz, uint32_t n_verts, const ui
                 ck(cudaMemsetAsync(arr, 0, sizeof(int) * (m - 1), st), "memset");
                 k_rotate<<<blocks_for(m, B), B, 0, st>>>(m, s->nodes, pnode, pleaf, arr, ibuf + 6);
             }
-            k_depth<<<blocks_for(m, B), B, 0, st>>>(m, pnode, pleaf, ibuf + 7);
-            // the structure the packet tracer relies on (k_tree_refs); the sort's second
-            // buffers count the leaves' references
+            // the structure the packet tracer relies on (k_tree_refs), then the depth of
+            // that structure; the sort's second buffers count the leaves' references
             ck(cudaMemsetAsync(arr, 0, sizeof(int) * (m - 1), st), "memset");
             ck(cudaMemsetAsync(vals2, 0, sizeof(int) * m, st), "memset");
+            ck(cudaMemsetAsync(pnode, 0xFF, sizeof(int) * (m - 1), st), "memset");
+            ck(cudaMemsetAsync(pleaf, 0xFF, sizeof(int) * m, st), "memset");
             int *ref_leaf = reinterpret_cast<int *>(vals2);
-            k_tree_refs<<<blocks_for(m - 1, B), B, 0, st>>>(s->nodes, m - 1, m, arr, ref_leaf, ibuf + 6);
+            k_tree_refs<<<blocks_for(m - 1, B), B, 0, st>>>(s->nodes, m - 1, m, arr, ref_leaf, pnode, pleaf, ibuf + 6);
             k_tree_counts<<<blocks_for(m, B), B, 0, st>>>(m - 1, m, root, arr, ref_leaf, ibuf + 6);
+            k_depth<<<blocks_for(m, B), B, 0, st>>>(m, pnode, pleaf, ibuf + 7);
         }
         s->root = root;
         ck(cudaGetLastError(), "bvh kernels");

@@ -749,7 +749,6 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
             const int lead = __shfl_sync(0xffffffffu, si, __ffs(pm) - 1);
             const bool act = pending && si == lead;
             const SessDesc &S = A.s[lead];
-            uint32_t *status = &A.s[lead].counters[3];
             const int n_tree = S.sc.n_tris;
             if (n_tree > 0) {
                 const BvhNode *__restrict__ nodes = S.sc.nodes;
@@ -757,7 +756,9 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
                 int node = S.sc.root, sp = 0;
                 // no per-step guard: the tree passed the structure check at upload (every
                 // reference in range, every node but the root referenced once), so the
-                // packet enters each node at most once and ends within the tree's size
+                // packet enters each node at most once and ends within the tree's size;
+                // the stack holds one entry per level at most, and the launch's capacity
+                // covers the depth measured on those references
                 for (;;) {
                     if (node >= 0) {
                         const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
@@ -772,8 +773,8 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
                         if (m0 && m1) {
                             const unsigned right_first = __ballot_sync(0xffffffffu, h0 && h1 && t1 < t0);
                             const bool rf = 2 * __popc(right_first) > __popc(m0 & m1);
-                            if (sp < kCap) stack[sp++] = rf ? ref.x : ref.y;
-                            else if (lane == 0) atomicOr(status, 1u);
+                            // at most one entry per level above the node: sp < depth <= kCap
+                            stack[sp++] = rf ? ref.x : ref.y;
                             node = rf ? ref.y : ref.x;
                             continue;
                         }
