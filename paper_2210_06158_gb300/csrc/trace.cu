@@ -117,6 +117,19 @@ __device__ __forceinline__ void tri_update(const Ray &ray, const float4 *__restr
     }
 }
 
+// tri_update against the bound tb, which is h.t for a lane of the packet's session and
+// -1 for the others (no triangle passes, so their hit records stay as they are)
+__device__ __forceinline__ void tri_update_bound(const Ray &ray, const float4 *__restrict__ tris, int k, float &tb,
+                                                 HitRec &h) {
+    const float4 *tp = tris + 3 * (size_t)k;
+    float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+    float t = tri_hit(ray, v0, v1, v2, tb);
+    if (t > 0.f) {
+        int prim = __float_as_int(v0.w);
+        if (t < tb || (t == tb && prim < h.prim)) { h.t = t; h.prim = prim; h.k = k; tb = t; }
+    }
+}
+
 // Returns true when the query has ended (stack empty or a guard tripped).
 template <int kCap>
 __device__ __forceinline__ bool step4(const Ray &ray, const Bvh4Node *__restrict__ nodes4, int n4,
@@ -754,6 +767,9 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
                 const BvhNode *__restrict__ nodes = S.sc.nodes;
                 const float4 *__restrict__ tris = S.sc.tris;
                 int node = S.sc.root, sp = 0;
+                // the best distance the lane tests boxes and triangles against: its own
+                // for a lane of this session, -1 (nothing passes) for the others
+                float tb = act ? h.t : -1.f;
                 // no per-step guard: the tree passed the structure check at upload (every
                 // reference in range, every node but the root referenced once), so the
                 // packet enters each node at most once and ends within the tree's size;
@@ -766,8 +782,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
                         const int4 ref = __ldg(reinterpret_cast<const int4 *>(np + 3));
                         float t0, t1;
                         bool h0, h1;
-                        // a lane without act enters no box: its best distance reads -1
-                        box_pair(ray, a, b, c, act ? h.t : -1.f, h0, t0, h1, t1);
+                        box_pair(ray, a, b, c, tb, h0, t0, h1, t1);
                         if (kStats) n_visit += act ? 1u : 0u;
                         const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
                         if (m0 && m1) {
@@ -780,9 +795,9 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_packets(const __grid
                         }
                         if (m0) { node = ref.x; continue; }
                         if (m1) { node = ref.y; continue; }
-                    } else if (act) {
-                        if (kStats) n_tests++;
-                        tri_update(ray, tris, ~node, h);
+                    } else {
+                        if (kStats && act) n_tests++;
+                        tri_update_bound(ray, tris, ~node, tb, h);
                     }
                     if (sp == 0) break;
                     node = stack[--sp];
