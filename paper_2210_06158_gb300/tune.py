@@ -104,9 +104,9 @@ def tune_trace(ctx, run_frame, frames=6, rounds=2, stream=None, widths=None, sta
 
 
 GATHER_SPACE = {
-    "gather_block": [(32, 8), (16, 16), (64, 4), (32, 16), (64, 8)],
+    "gather_block": [(32, 8), (16, 16), (64, 4), (32, 4), (16, 8), (32, 16), (64, 8)],
     "main_form": [0, 1, 2, 3],
-    "recon_block": [(32, 8), (16, 16), (64, 4), (32, 16), (64, 8)],
+    "recon_block": [(32, 8), (16, 16), (64, 4), (32, 4), (16, 8), (32, 16), (64, 8)],
 }
 GATHER_DEFAULT = {"gather_block": (32, 8), "main_form": 0, "recon_block": (32, 8)}
 

@@ -185,10 +185,12 @@ def test_tune_gathers_finds_the_optimum_and_leaves_it_on_the_context(monkeypatch
     _fake_cuda(monkeypatch, clock)
     ctx = _Ctx()
     ctx.cfg.update(tune.GATHER_DEFAULT)
-    shape_cost = {(32, 8): 0.2, (16, 16): 0.1, (64, 4): 0.3, (32, 16): 0.0, (64, 8): 0.05}
+    shape_cost = {(32, 8): 0.2, (16, 16): 0.1, (64, 4): 0.3, (32, 4): 0.25, (16, 8): 0.15, (32, 16): 0.0,
+                  (64, 8): 0.05}
     form_cost = {0: 0.1, 1: 0.2, 2: 0.0, 3: 0.15}
 
-    recon_cost = {(32, 8): 0.1, (16, 16): 0.0, (64, 4): 0.2, (32, 16): 0.05, (64, 8): 0.3}
+    recon_cost = {(32, 8): 0.1, (16, 16): 0.0, (64, 4): 0.2, (32, 4): 0.12, (16, 8): 0.02, (32, 16): 0.05,
+                  (64, 8): 0.3}
 
     def run_frame(k):
         clock.t += (1.0 + shape_cost[ctx.cfg["gather_block"]] + form_cost[ctx.cfg["main_form"]]
